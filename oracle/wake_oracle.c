@@ -1,0 +1,634 @@
+/*
+ * wake_oracle.c -- FP64 CPU oracle of the gridless quasistatic wake model.
+ *
+ * TEST INFRASTRUCTURE ONLY (see wake_oracle.h).  Plain sequential C: one
+ * stable merge sort, sequential sums, the App. A shooting recursion and the
+ * second-order Adams-Bashforth push, in the order of Sec. III (sort, gather
+ * sources, psi and its derivatives, u_z and gamma, B_theta^(p), evolve).
+ *
+ * Conventions (electrons q = -1, m = 1, so psibar = 1 + psi):
+ *   ring i in radius order, weight w_i, self weight what_i;
+ *   S(rho) = sum_{rho_j < rho} w_j                      (Eq. dpsi_dr)
+ *   I(rho) = n min(rho, rho_max)^2 / 2                  (ion column, enclosed)
+ *   d_rho psi  = (S - I) / rho                          (Eq. dpsi_dr + ions)
+ *   psi(rho)   = sum_j w_j ln max(rho, rho_j) + psi_ion (Eq. psi + ions)
+ *   d_zeta psi = -sum_{rho_j > rho} w_j u_j / (rho_j psibar_j)
+ *                (the zeta derivative of Eq. psi at fixed rho, using
+ *                 Eq. plasma_particle_motion_2; see the note at
+ *                 zeta_derivative() on the sign of Eq. dpsi_dzeta)
+ * At a ring the partial sums use the self weight what_i in place of w_i
+ * (Sec. II, "key algorithmic adjustments").
+ */
+#include "wake_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_2PI 6.283185307179586476925286766559
+
+/* ---------------------------------------------------------------------- */
+/* ion column: uniform density n on rho <= rho_max, immobile               */
+/* ---------------------------------------------------------------------- */
+
+/* Ion charge enclosed within rho (per unit length and per 2 pi). */
+static double ion_enclosed(double rho, double n, double rho_max)
+{
+    double c = rho < rho_max ? rho : rho_max;
+    return 0.5 * n * c * c;
+}
+
+/* Ion-column part of psi: Eq. psi applied to the continuous ion column,
+   normalised so that psi -> 0 at infinity once the (neutralising) electron
+   sum is added: d/drho psi_ion = -I(rho)/rho, psi_ion ~ -(n rho_max^2/2) ln rho
+   outside the column. */
+static double ion_psi(double rho, double n, double rho_max)
+{
+    double q = 0.5 * n * rho_max * rho_max;
+    if (rho <= rho_max)
+        return 0.25 * n * (rho_max * rho_max - rho * rho) - q * log(rho_max);
+    return -q * log(rho);
+}
+
+/* ---------------------------------------------------------------------- */
+/* small helpers                                                           */
+/* ---------------------------------------------------------------------- */
+
+/* First index i in the increasing array a[0..n) with a[i] >= x. */
+static int64_t lower_bound(const double *a, int64_t n, double x)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+/* Stable bottom-up merge sort of ids[0..n) by key[id]; equal keys keep
+   their input order (the previous slice's order, Sec. III). */
+static void stable_sort_ids(int32_t n, int32_t *ids, const double *key, int32_t *tmp)
+{
+    int32_t *src = ids, *dst = tmp;
+    for (int32_t width = 1; width < n; width *= 2) {
+        for (int32_t lo = 0; lo < n; lo += 2 * width) {
+            int32_t mid = lo + width < n ? lo + width : n;
+            int32_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int32_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi)
+                dst[k++] = (key[src[j]] < key[src[i]]) ? src[j++] : src[i++];
+            while (i < mid)
+                dst[k++] = src[i++];
+            while (j < hi)
+                dst[k++] = src[j++];
+        }
+        int32_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != ids)
+        memcpy(ids, src, (size_t)n * sizeof(int32_t));
+}
+
+/* Beam particles of one slice sorted by (r, index), with the exclusive
+   prefix P[p] = sum_{q < p} qw[q] (P has m+1 entries).  The enclosed beam
+   charge strictly below rho is P[lower_bound(r, rho)]. */
+typedef struct {
+    int64_t m;
+    double *r, *P;
+    int64_t *idx;
+} beam_slice;
+
+/* a beam particle of one slice: radius, charge x weight, caller index */
+typedef struct { double r; double qw; int64_t idx; } bpart;
+
+static int bpart_cmp(const void *x, const void *y)
+{
+    const bpart *a = (const bpart *)x, *b = (const bpart *)y;
+    if (a->r < b->r) return -1;
+    if (a->r > b->r) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+static int beam_slice_build(beam_slice *bs, int64_t m, const bpart *parts_in)
+{
+    bs->m = m;
+    bs->r = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    bs->P = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    bs->idx = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    bpart *parts = (bpart *)malloc((size_t)(m + 1) * sizeof(bpart));
+    if (!bs->r || !bs->P || !bs->idx || !parts) {
+        free(parts);
+        return ORC_ENOMEM;
+    }
+    if (m > 0)
+        memcpy(parts, parts_in, (size_t)m * sizeof(bpart));
+    qsort(parts, (size_t)m, sizeof(bpart), bpart_cmp);
+    double acc = 0.0;
+    for (int64_t p = 0; p < m; ++p) {
+        bs->r[p] = parts[p].r;
+        bs->idx[p] = parts[p].idx;
+        bs->P[p] = acc;
+        acc += parts[p].qw;
+    }
+    bs->P[m] = acc;
+    free(parts);
+    return ORC_OK;
+}
+
+static void beam_slice_free(beam_slice *bs)
+{
+    free(bs->r);
+    free(bs->P);
+    free(bs->idx);
+    bs->r = bs->P = NULL;
+    bs->idx = NULL;
+}
+
+/* Beam field (Sec. II, the B_theta^(b) equation integrated from the axis):
+   rho B^(b) = int_0^rho q n_b rho' drho'; a beam macroparticle of weight W in
+   a slice of thickness dxi is a ring of density W / (2 pi rho dxi) delta, so
+   B^(b)(rho) = Q(rho) / (2 pi dxi rho) with Q the charge strictly below rho. */
+static double beam_field(const beam_slice *bs, double rho, double dxi)
+{
+    if (bs->m == 0 || !(rho > 0.0))
+        return 0.0;
+    double Q = bs->P[lower_bound(bs->r, bs->m, rho)];
+    return Q / (ORC_2PI * dxi * rho);
+}
+
+/* ---------------------------------------------------------------------- */
+/* ring initialisation                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Sec. II: rho_j0 = sum_{k<j} drho_k + drho_j/2 (cell centre), weight
+   w_j = n rho_j0 drho_j (Eq. macroparticle_weight) and the self weight
+   what_j = n (rho_j0 drho_j / 2 - drho_j^2 / 8), the charge of the cell below
+   the ring ("key algorithmic adjustments"; with n = 1 it is w_j/2 - drho_j^2/8). */
+void orc_ring_init(int32_t n, const double *edges, double density,
+                   double *rho0, double *drho, double *w, double *what)
+{
+    for (int32_t j = 0; j < n; ++j) {
+        double d = edges[j + 1] - edges[j];
+        double c = 0.5 * (edges[j] + edges[j + 1]);
+        if (rho0) rho0[j] = c;
+        if (drho) drho[j] = d;
+        if (w) w[j] = density * c * d;
+        if (what) what[j] = density * (0.5 * c * d - 0.125 * d * d);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* App. A: shooting solution of the B^(p) recursion                        */
+/* ---------------------------------------------------------------------- */
+
+/* Eq. ai_bi with b_0 = 0, a_N = 0, solved as in App. A: a_i = K_i a_0 + T_i,
+   b_i = U_i a_0 + P_i, (K,U,T,P)_0 = (1,0,0,0), both pairs advanced by the
+   matrix of Eq. ai_bi (the (T,P) pair also by its source vector), then
+   a_0 = -T_N / K_N (Eq. app1_a0).  Ring i (1-based in the paper) is rho[i-1]
+   here; region k lies between rings k and k+1. */
+int orc_bp_shooting(int32_t n, const double *rho, const double *A, const double *B,
+                    const double *C, double *a, double *b)
+{
+    double *K = (double *)malloc((size_t)(n + 1) * 4 * sizeof(double));
+    if (!K)
+        return ORC_ENOMEM;
+    double *U = K + (n + 1), *T = U + (n + 1), *P = T + (n + 1);
+    K[0] = 1.0; U[0] = 0.0; T[0] = 0.0; P[0] = 0.0;
+    for (int32_t i = 1; i <= n; ++i) {
+        double r = rho[i - 1], Ai = A[i - 1], Bi = B[i - 1], Ci = C[i - 1];
+        double m11 = 1.0 + 0.5 * Ai * r;
+        double m12 = 0.5 * Ai / r;
+        double m21 = -0.5 * Ai * r * r * r;
+        double m22 = 1.0 - 0.5 * Ai * r;
+        double s1 = 0.25 * (2.0 * Bi + Ai * Ci);
+        double s2 = 0.25 * r * (4.0 * Ci - 2.0 * Bi * r - Ai * Ci * r);
+        K[i] = m11 * K[i - 1] + m12 * U[i - 1];
+        U[i] = m21 * K[i - 1] + m22 * U[i - 1];
+        T[i] = m11 * T[i - 1] + m12 * P[i - 1] + s1;
+        P[i] = m21 * T[i - 1] + m22 * P[i - 1] + s2;
+    }
+    double a0 = -T[n] / K[n];
+    for (int32_t k = 0; k <= n; ++k) {
+        a[k] = K[k] * a0 + T[k];
+        b[k] = U[k] * a0 + P[k];
+    }
+    free(K);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* one slice                                                               */
+/* ---------------------------------------------------------------------- */
+
+/* Work arrays of a slice, all in radius order (index i = sorted position). */
+typedef struct {
+    int32_t n;
+    double *r, *u, *w, *wh;          /* ring state and weights */
+    double *S, *L, *T;               /* exclusive prefix sums, [n+1] */
+    double *t;                       /* w u / (rho psibar) */
+    double *psi, *dpr, *dpz, *psib, *gam, *uz, *bb, *A, *B, *C, *bp;
+    double *a, *b;                   /* [n+1] */
+    double Wtot, Ltot, Ttot;
+    int32_t *tmp;
+} slice_ws;
+
+static int ws_alloc(slice_ws *s, int32_t n)
+{
+    memset(s, 0, sizeof(*s));
+    s->n = n;
+    size_t m = (size_t)n + 1;
+    double *blk = (double *)calloc(m * 22, sizeof(double));
+    s->tmp = (int32_t *)malloc(m * sizeof(int32_t));
+    if (!blk || !s->tmp) {
+        free(blk);
+        free(s->tmp);
+        return ORC_ENOMEM;
+    }
+    double **fields[] = {&s->r, &s->u, &s->w, &s->wh, &s->S, &s->L, &s->T, &s->t,
+                         &s->psi, &s->dpr, &s->dpz, &s->psib, &s->gam, &s->uz,
+                         &s->bb, &s->A, &s->B, &s->C, &s->bp, &s->a, &s->b};
+    for (size_t f = 0; f < sizeof(fields) / sizeof(fields[0]); ++f)
+        *fields[f] = blk + f * m;
+    return ORC_OK;
+}
+
+static void ws_free(slice_ws *s)
+{
+    free(s->r);
+    free(s->tmp);
+    memset(s, 0, sizeof(*s));
+}
+
+/* Eq. dpsi_dzeta.  Differentiating Eq. psi in zeta at fixed rho with
+   d rho_i / d zeta = -u_i / psibar_i (Eq. plasma_particle_motion_2) gives
+   d_zeta psi = + sum_i q_i w_i u_i/(rho_i psibar_i)
+                - sum_{rho_i<rho} q_i w_i u_i/(rho_i psibar_i),
+   the printed equation with the opposite overall sign.  The true partial
+   derivative is used (it is what E_z = -d_zeta psi of Eq. lorentz_gauge_1 and
+   the B_i coefficient of Eq. b_coeffs_2 need).  With q = -1 this is
+   -sum_{rho_j >= rho} t_j, t_j = w_j u_j / (rho_j psibar_j); at ring i the
+   ring's own term enters the partial sum with what_i / w_i. */
+static double zeta_derivative(double suffix_above, double t_self, double w_self,
+                              double wh_self)
+{
+    return -(suffix_above + (1.0 - wh_self / w_self) * t_self);
+}
+
+/* All ring fields of one slice (Sec. III order: sources, psi and its
+   derivatives, u_z and gamma, B_theta^(p)).  order[] holds the previous
+   radius order on entry and the new one on exit. */
+static int slice_core(slice_ws *s, int32_t *order, const double *rho_id,
+                      const double *ur_id, const double *w_id, const double *wh_id,
+                      double dens, double rho_max, const beam_slice *bs, double dxi)
+{
+    int32_t n = s->n;
+    /* sort by radius, stable w.r.t. the previous order */
+    stable_sort_ids(n, order, rho_id, s->tmp);
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t id = order[i];
+        s->r[i] = rho_id[id];
+        s->u[i] = ur_id[id];
+        s->w[i] = w_id[id];
+        s->wh[i] = wh_id[id];
+    }
+    /* gather the beam source at the rings */
+    for (int32_t i = 0; i < n; ++i)
+        s->bb[i] = beam_field(bs, s->r[i], dxi);
+    /* radial prefix sums of charge and of charge x ln rho (Eqs. dpsi_dr, psi) */
+    double accS = 0.0, accL = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        s->S[i] = accS;
+        s->L[i] = accL;
+        accS += s->w[i];
+        accL += s->w[i] * log(s->r[i]);
+    }
+    s->S[n] = accS;
+    s->L[n] = accL;
+    s->Wtot = accS;
+    s->Ltot = accL;
+    /* psi, d_rho psi (self weight), psibar, gamma, u_z
+       (Eqs. psi, dpsi_dr, plasma_particle_motion_3/4) */
+    for (int32_t i = 0; i < n; ++i) {
+        double r = s->r[i], u = s->u[i];
+        s->psi[i] = (s->Ltot - s->L[i]) + s->S[i] * log(r) + ion_psi(r, dens, rho_max);
+        s->dpr[i] = (s->S[i] + s->wh[i] - ion_enclosed(r, dens, rho_max)) / r;
+        double pb = 1.0 + s->psi[i];
+        s->psib[i] = pb;
+        s->gam[i] = (1.0 + u * u + pb * pb) / (2.0 * pb);
+        s->uz[i] = (1.0 + u * u - pb * pb) / (2.0 * pb);
+        s->t[i] = s->w[i] * u / (r * pb);
+    }
+    /* current prefix sum and d_zeta psi (Eq. dpsi_dzeta, see zeta_derivative) */
+    double accT = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        s->T[i] = accT;
+        accT += s->t[i];
+    }
+    s->T[n] = accT;
+    s->Ttot = accT;
+    for (int32_t i = 0; i < n; ++i) {
+        double above = s->Ttot - s->T[i + 1];
+        s->dpz[i] = zeta_derivative(above, s->t[i], s->w[i], s->wh[i]);
+    }
+    /* coefficients A_i, B_i, C_i (Eqs. b_coeffs_1..3 with q = -1, m = 1, no
+       laser); the beam field enters B_i, the plasma field is the unknown */
+    for (int32_t i = 0; i < n; ++i) {
+        double r = s->r[i], u = s->u[i], w = s->w[i], pb = s->psib[i];
+        double g = s->gam[i], dpr = s->dpr[i], dpz = s->dpz[i];
+        double wr = w / r;
+        s->A[i] = wr / pb;
+        s->B[i] = -wr * g * dpr / (pb * pb)
+                  + wr * s->bb[i] / pb
+                  + (w / (r * r)) * u * u / (pb * pb)
+                  + wr * u * u * dpr / (pb * pb * pb)
+                  - wr * u * dpz / (pb * pb);
+        s->C[i] = -wr * (g / pb - 1.0 - u * u / (pb * pb));
+    }
+    /* B_theta^(p): App. A shooting, then the field at each ring.  B^(p) jumps
+       across a ring (the C_i term makes rho B jump by C_i rho_i); the matrix
+       and source vector of Eq. ai_bi follow from the jump conditions exactly
+       when the ring sees the mean of the two one-sided values, which is the
+       value used for the ring itself. */
+    int rc = orc_bp_shooting(n, s->r, s->A, s->B, s->C, s->a, s->b);
+    if (rc)
+        return rc;
+    for (int32_t i = 0; i < n; ++i) {
+        double r = s->r[i];
+        s->bp[i] = 0.5 * ((s->a[i] + s->a[i + 1]) * r + (s->b[i] + s->b[i + 1]) / r);
+    }
+    return ORC_OK;
+}
+
+/* Fields at an arbitrary radius x (Eqs. b_theta_plasma..dpsi_dzeta sampled
+   off the rings, the "arbitrary radial resolution" remark of Sec. II): no
+   self weight, region k = number of rings strictly below x. */
+static void fields_at(const slice_ws *s, const beam_slice *bs, double dens,
+                      double rho_max, double dxi, double x,
+                      double *psi, double *dpr, double *dpz, double *bp, double *bb)
+{
+    int64_t k = lower_bound(s->r, s->n, x);
+    if (!(x > 0.0)) {
+        /* on the axis: every ring is outside, d_rho psi and B vanish */
+        *psi = s->Ltot + ion_psi(0.0, dens, rho_max);
+        *dpr = 0.0;
+        *dpz = -(s->Ttot - s->T[0]);
+        *bp = 0.0;
+        *bb = 0.0;
+        return;
+    }
+    double S = s->S[k];
+    *psi = (s->Ltot - s->L[k]) + S * log(x) + ion_psi(x, dens, rho_max);
+    *dpr = (S - ion_enclosed(x, dens, rho_max)) / x;
+    *dpz = -(s->Ttot - s->T[k]);
+    *bp = s->a[k] * x + s->b[k] / x;
+    *bb = beam_field(bs, x, dxi);
+}
+
+static int ring_fields_ok(const slice_ws *s)
+{
+    for (int32_t i = 0; i < s->n; ++i) {
+        if (!(s->psib[i] > 0.0) || !isfinite(s->psi[i]) || !isfinite(s->dpr[i]) ||
+            !isfinite(s->dpz[i]) || !isfinite(s->bp[i]) || !isfinite(s->bb[i]) ||
+            !isfinite(s->gam[i]))
+            return 0;
+    }
+    return 1;
+}
+
+int orc_slice_fields(int32_t n, const double *rho, const double *ur,
+                     const double *w, const double *what, double density, double rho_max,
+                     int64_t m, const double *beam_r, const double *beam_qw, double dxi,
+                     orc_slice_out *out)
+{
+    if (n < 1 || !rho || !ur || !w || !what || !out || !(dxi > 0.0))
+        return ORC_EINVAL;
+    slice_ws s;
+    if (ws_alloc(&s, n))
+        return ORC_ENOMEM;
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    bpart *parts = (bpart *)malloc((size_t)(m + 1) * sizeof(bpart));
+    beam_slice bs = {0, NULL, NULL, NULL};
+    if (!order || !parts) {
+        free(order);
+        free(parts);
+        ws_free(&s);
+        return ORC_ENOMEM;
+    }
+    for (int64_t p = 0; p < m; ++p) {
+        parts[p].r = beam_r[p];
+        parts[p].qw = beam_qw[p];
+        parts[p].idx = p;
+    }
+    int rc = beam_slice_build(&bs, m, parts);
+    free(parts);
+    if (!rc) {
+        for (int32_t i = 0; i < n; ++i)
+            order[i] = i;
+        rc = slice_core(&s, order, rho, ur, w, what, density, rho_max, &bs, dxi);
+    }
+    if (!rc) {
+        for (int32_t i = 0; i < n; ++i) {
+            int32_t id = order[i];
+            if (out->order) out->order[i] = id;
+            if (out->psi) out->psi[id] = s.psi[i];
+            if (out->dpsidr) out->dpsidr[id] = s.dpr[i];
+            if (out->dpsidz) out->dpsidz[id] = s.dpz[i];
+            if (out->psibar) out->psibar[id] = s.psib[i];
+            if (out->gamma) out->gamma[id] = s.gam[i];
+            if (out->uz) out->uz[id] = s.uz[i];
+            if (out->bb) out->bb[id] = s.bb[i];
+            if (out->A) out->A[id] = s.A[i];
+            if (out->B) out->B[id] = s.B[i];
+            if (out->C) out->C[id] = s.C[i];
+            if (out->bp) out->bp[id] = s.bp[i];
+        }
+        for (int32_t k = 0; k <= n; ++k) {
+            if (out->a) out->a[k] = s.a[k];
+            if (out->b) out->b[k] = s.b[k];
+        }
+        for (int64_t q = 0; q < out->nq; ++q) {
+            double psi, dpr, dpz, bp, bb;
+            fields_at(&s, &bs, density, rho_max, dxi, out->rq[q], &psi, &dpr, &dpz, &bp, &bb);
+            if (out->q_ez) out->q_ez[q] = -dpz;
+            if (out->q_wr) out->q_wr[q] = -dpr;
+            if (out->q_bt) out->q_bt[q] = bp + bb;
+            if (out->q_psi) out->q_psi[q] = psi;
+            if (out->q_bp) out->q_bp[q] = bp;
+            if (out->q_bb) out->q_bb[q] = bb;
+            if (out->q_dpsidr) out->q_dpsidr[q] = dpr;
+            if (out->q_dpsidz) out->q_dpsidz[q] = dpz;
+        }
+        if (!ring_fields_ok(&s))
+            rc = ORC_ENONFINITE;
+    }
+    beam_slice_free(&bs);
+    free(order);
+    ws_free(&s);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* the whole window                                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Nearest slice of a beam particle (the beam-grid spacing equals the solver
+   step, Sec. III): s = floor(xi/dxi + 1/2). */
+static int64_t nearest_slice(double xi, double dxi)
+{
+    return (int64_t)floor(xi / dxi + 0.5);
+}
+
+int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
+{
+    if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
+        (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
+        return ORC_EINVAL;
+    for (int32_t j = 0; j < p->n_rings; ++j)
+        if (!(p->edges[j + 1] > p->edges[j]))
+            return ORC_EINVAL;
+    if (p->edges[0] != 0.0)
+        return ORC_EINVAL;
+    int32_t n = p->n_rings, ns = p->n_steps;
+    int32_t nrun = (max_slices > 0 && max_slices < ns) ? max_slices : ns;
+    double rho_max = p->edges[n], dens = p->density, dxi = p->dxi;
+    out->status = ORC_OK;
+    out->fail_slice = -1;
+    out->slices_run = 0;
+
+    /* state by ring id */
+    double *st = (double *)calloc((size_t)n * 6, sizeof(double));
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *cnt = (int64_t *)calloc((size_t)ns + 2, sizeof(int64_t));
+    bpart *parts = (bpart *)malloc((size_t)(p->n_beam + 1) * sizeof(bpart));
+    slice_ws s;
+    int rc = ws_alloc(&s, n);
+    if (!st || !order || !cnt || !parts || rc) {
+        free(st); free(order); free(cnt); free(parts);
+        if (!rc) ws_free(&s);
+        return ORC_ENOMEM;
+    }
+    double *rho = st, *ur = st + n, *w = st + 2 * n, *wh = st + 3 * n;
+    double *fr_prev = st + 4 * n, *fu_prev = st + 5 * n;
+    orc_ring_init(n, p->edges, dens, rho, NULL, w, wh);
+    for (int32_t j = 0; j < n; ++j)
+        order[j] = j;
+
+    /* bin the beam by nearest slice (counting sort, stable in caller order) */
+    for (int64_t k = 0; k < p->n_beam; ++k) {
+        int64_t sl = nearest_slice(p->beam_xi[k], dxi);
+        if (sl >= 0 && sl < ns)
+            cnt[sl + 1]++;
+    }
+    for (int32_t sl = 0; sl < ns; ++sl)
+        cnt[sl + 1] += cnt[sl];
+    {
+        int64_t *fill = (int64_t *)malloc(((size_t)ns + 1) * sizeof(int64_t));
+        if (!fill) {
+            rc = ORC_ENOMEM;
+        } else {
+            memcpy(fill, cnt, ((size_t)ns + 1) * sizeof(int64_t));
+            for (int64_t k = 0; k < p->n_beam; ++k) {
+                int64_t sl = nearest_slice(p->beam_xi[k], dxi);
+                if (sl >= 0 && sl < ns) {
+                    bpart *bp = &parts[fill[sl]++];
+                    bp->r = p->beam_r[k];
+                    bp->qw = p->beam_qw[k];
+                    bp->idx = k;
+                }
+            }
+            free(fill);
+        }
+    }
+    /* particles outside the window get zero fields */
+    for (int64_t k = 0; k < p->n_beam; ++k) {
+        if (out->ez) out->ez[k] = 0.0;
+        if (out->wr) out->wr[k] = 0.0;
+        if (out->bt) out->bt[k] = 0.0;
+        if (out->psi) out->psi[k] = 0.0;
+    }
+
+    int have_prev = 0;
+    for (int32_t sl = 0; sl < nrun && !rc; ++sl) {
+        beam_slice bs = {0, NULL, NULL, NULL};
+        rc = beam_slice_build(&bs, cnt[sl + 1] - cnt[sl], parts + cnt[sl]);
+        if (rc)
+            break;
+        rc = slice_core(&s, order, rho, ur, w, wh, dens, rho_max, &bs, dxi);
+        if (rc) {
+            beam_slice_free(&bs);
+            break;
+        }
+        size_t row = (size_t)sl * (size_t)n;
+        for (int32_t i = 0; i < n; ++i) {
+            int32_t id = order[i];
+            if (out->ring_r) out->ring_r[row + id] = s.r[i];
+            if (out->ring_ur) out->ring_ur[row + id] = s.u[i];
+            if (out->ring_psi) out->ring_psi[row + id] = s.psi[i];
+            if (out->ring_dpsidr) out->ring_dpsidr[row + id] = s.dpr[i];
+            if (out->ring_dpsidz) out->ring_dpsidz[row + id] = s.dpz[i];
+            if (out->ring_bp) out->ring_bp[row + id] = s.bp[i];
+            if (out->ring_bb) out->ring_bb[row + id] = s.bb[i];
+            if (out->ring_psibar) out->ring_psibar[row + id] = s.psib[i];
+            if (out->ring_gamma) out->ring_gamma[row + id] = s.gam[i];
+            if (out->ring_uz) out->ring_uz[row + id] = s.uz[i];
+        }
+        /* fields on the beam particles of this slice */
+        for (int64_t q = 0; q < bs.m; ++q) {
+            double psi, dpr, dpz, bpv, bbv;
+            fields_at(&s, &bs, dens, rho_max, dxi, bs.r[q], &psi, &dpr, &dpz, &bpv, &bbv);
+            int64_t k = bs.idx[q];
+            if (out->ez) out->ez[k] = -dpz;
+            if (out->wr) out->wr[k] = -dpr;
+            if (out->bt) out->bt[k] = bpv + bbv;
+            if (out->psi) out->psi[k] = psi;
+        }
+        beam_slice_free(&bs);
+        out->slices_run = sl + 1;
+        if (!ring_fields_ok(&s)) {
+            out->status = ORC_ENONFINITE;
+            out->fail_slice = sl;
+            break;
+        }
+        /* evolve rho, u_r to the next slice (Eqs. plasma_particle_motion_1,2
+           with xi = -zeta; second-order Adams-Bashforth, Sec. III; forward
+           Euler on the first step) */
+        for (int32_t i = 0; i < n; ++i) {
+            int32_t id = order[i];
+            double pb = s.psib[i];
+            double fr = s.u[i] / pb;
+            double fu = s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]);
+            if (have_prev) {
+                rho[id] = s.r[i] + dxi * (1.5 * fr - 0.5 * fr_prev[id]);
+                ur[id] = s.u[i] + dxi * (1.5 * fu - 0.5 * fu_prev[id]);
+            } else {
+                rho[id] = s.r[i] + dxi * fr;
+                ur[id] = s.u[i] + dxi * fu;
+            }
+            fr_prev[id] = fr;
+            fu_prev[id] = fu;
+            /* crossing the axis: the ring reappears at -rho moving the other
+               way; f_rho and f_u are odd in rho, so the history flips too */
+            if (rho[id] < 0.0) {
+                rho[id] = -rho[id];
+                ur[id] = -ur[id];
+                fr_prev[id] = -fr_prev[id];
+                fu_prev[id] = -fu_prev[id];
+            }
+        }
+        have_prev = 1;
+    }
+    if (out->final_r)
+        memcpy(out->final_r, rho, (size_t)n * sizeof(double));
+    if (out->final_ur)
+        memcpy(out->final_ur, ur, (size_t)n * sizeof(double));
+    free(st);
+    free(order);
+    free(cnt);
+    free(parts);
+    ws_free(&s);
+    return rc;
+}

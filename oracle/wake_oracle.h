@@ -1,0 +1,85 @@
+/*
+ * wake_oracle.h -- FP64 CPU oracle of the gridless quasistatic wake model.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, sequential reference
+ * that the CUDA path is checked against.  Only tests, the smoke check and the
+ * benchmark's CPU-baseline/reference legs may load it; the product library
+ * never links or calls it, and it shares no code with the CUDA sources.
+ *
+ * Model: Sec. II of the paper (gridless quasistatic model), electrons only
+ * (q = -1, m = 1) over an immobile uniform ion column of density n filling
+ * rho <= rho_max = edges[N] (the Baxevanis-Stupakov limit named at the end of
+ * Sec. II), no laser.  xi = -zeta; one step advances xi by dxi.
+ */
+#ifndef WAKE_ORACLE_H
+#define WAKE_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 4 };
+
+typedef struct {
+    int32_t n_rings;          /* N >= 1 */
+    const double *edges;      /* N+1 cell edges, edges[0]=0, strictly increasing */
+    double density;           /* uniform n of electrons and of the ion column */
+    int64_t n_beam;           /* beam macroparticles (all beams concatenated) */
+    const double *beam_xi;    /* [n_beam] */
+    const double *beam_r;     /* [n_beam] >= 0 */
+    const double *beam_qw;    /* [n_beam] charge sign x weight */
+    double dxi;               /* step in xi (> 0) */
+    int32_t n_steps;          /* slices in the window */
+} orc_problem;
+
+typedef struct {
+    /* per beam particle, caller order (NULL: skip).  Particles whose
+       nearest slice is outside the window get 0. */
+    double *ez, *wr, *bt, *psi;
+    /* per slice and ring id, [n_steps][n_rings] (NULL: skip); values at the
+       start of the slice (before the push). */
+    double *ring_r, *ring_ur, *ring_psi, *ring_dpsidr, *ring_dpsidz, *ring_bp,
+           *ring_bb, *ring_psibar, *ring_gamma, *ring_uz;
+    /* ring state by id after the last slice run (NULL: skip) */
+    double *final_r, *final_ur;
+    int32_t status;       /* ORC_OK or ORC_ENONFINITE */
+    int32_t fail_slice;   /* first slice whose fields failed the guard, else -1 */
+    int32_t slices_run;
+} orc_outputs;
+
+/* Fields of one slice for a given ring state; everything per ring is indexed
+   by ring id, per-region coefficients in radius order. */
+typedef struct {
+    double *psi, *dpsidr, *dpsidz, *psibar, *gamma, *uz, *bb, *A, *B, *C, *bp;
+    double *a, *b;            /* [N+1] B_theta^(p) = a_k rho + b_k / rho in region k */
+    int32_t *order;           /* [N] ring ids in radius order */
+    /* optional query points */
+    int64_t nq;
+    const double *rq;
+    double *q_ez, *q_wr, *q_bt, *q_psi, *q_bp, *q_bb, *q_dpsidr, *q_dpsidz;
+} orc_slice_out;
+
+/* Ring initialisation (Sec. II, ring macroparticles and Eq. macroparticle_weight;
+   the self weight of the "key algorithmic adjustments"). */
+void orc_ring_init(int32_t n, const double *edges, double density,
+                   double *rho0, double *drho, double *w, double *what);
+
+/* One slice: fields at every ring and (optionally) at query radii. */
+int orc_slice_fields(int32_t n, const double *rho, const double *ur,
+                     const double *w, const double *what, double density, double rho_max,
+                     int64_t m, const double *beam_r, const double *beam_qw, double dxi,
+                     orc_slice_out *out);
+
+/* App. A shooting solve of the B_theta^(p) recursion (Eq. ai_bi): rings in
+   radius order (rho[0] < ... < rho[n-1]); returns a[0..n], b[0..n]. */
+int orc_bp_shooting(int32_t n, const double *rho, const double *A, const double *B,
+                    const double *C, double *a, double *b);
+
+/* Whole window (or its first max_slices slices when max_slices > 0). */
+int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

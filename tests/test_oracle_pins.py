@@ -1,0 +1,440 @@
+"""Pins of the FP64 oracle to facts other than its own formulas.
+
+Each test checks the oracle against something the paper or the mathematics
+fixes independently of how the oracle computes it: the ODE and boundary
+conditions that define psi (Eq. phi_b_eq_1 integrated, Eq. dpsi_dr/psi),
+finite differences of psi along the ring motion (Eq. dpsi_dzeta), the jump
+conditions behind Eq. ai_bi solved by dense elimination, Ampere's law
+(Eq. maxwell_qsa_4), Lorentz-force integration of u_z against the constant of
+motion (Eqs. cold_plasma_constant, plasma_particle_motion_3), the linear
+closed form, and convergence orders.  A dropped term, wrong sign, wrong index
+or transposed operand in the oracle fails at least one of these.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_16623_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _random_state(n=40, seed=11, r_max=3.0, u_scale=0.3, density=1.0):
+    edges, rho, ur = W.random_ring_state(n, seed, r_max=r_max, u_scale=u_scale)
+    _, _, w, wh = oracle.ring_init(edges, density)
+    return edges, rho, ur, w, wh
+
+
+def _between_ring_points(rho, n_per_gap=3, rmin=1e-3):
+    rs = np.sort(rho)
+    pts = []
+    for lo, hi in zip(rs[:-1], rs[1:]):
+        for f in np.linspace(0.2, 0.8, n_per_gap):
+            pts.append(lo + f * (hi - lo))
+    pts.append(0.5 * rs[0])
+    return np.array([p for p in pts if p > rmin])
+
+
+# --------------------------------------------------------------------------
+# psi and d_rho psi: the ODE, jumps and boundary conditions that define them
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("density", [1.0, 2.5])
+def test_psi_solves_poisson_with_ring_jumps(density):
+    """Between rings (1/rho) d(rho d psi)/drho = -n (ion column) or 0 outside
+    it; rho d psi/drho jumps by w_j at ring j; psi and d psi/drho vanish
+    outside the neutral column; rho d psi/drho -> 0 on the axis."""
+    edges, rho, ur, w, wh = _random_state(density=density)
+    r_max = edges[-1]
+    x = _between_ring_points(rho)
+    h = 1e-6 * np.minimum(1.0, x)
+    sf = oracle.slice_fields(rho, ur, w, wh, density, r_max, rq=np.concatenate([x - h, x, x + h]))
+    m = x.shape[0]
+    psi_m, psi_0, psi_p = sf["q_psi"][:m], sf["q_psi"][m:2 * m], sf["q_psi"][2 * m:]
+    dpr_m, dpr_0, dpr_p = sf["q_dpsidr"][:m], sf["q_dpsidr"][m:2 * m], sf["q_dpsidr"][2 * m:]
+    # d psi / d rho by central difference
+    fd = (psi_p - psi_m) / (2 * h)
+    assert np.max(np.abs(fd - dpr_0)) < 1e-6 * max(1.0, np.max(np.abs(dpr_0)))
+    # Poisson operator between rings
+    lap = ((x + h) * dpr_p - (x - h) * dpr_m) / (2 * h * x)
+    src = np.where(x < r_max, -density, 0.0)
+    assert np.max(np.abs(lap - src)) < 1e-5 * density
+    # jumps of rho d psi/drho across each ring equal its weight
+    eps = 1e-9
+    sj = oracle.slice_fields(rho, ur, w, wh, density, r_max,
+                             rq=np.concatenate([rho * (1 - eps), rho * (1 + eps)]))
+    n = rho.shape[0]
+    jump = rho * (1 + eps) * sj["q_dpsidr"][n:] - rho * (1 - eps) * sj["q_dpsidr"][:n]
+    # ion charge in the shell [rho(1-eps), rho(1+eps)] inside the column
+    ion_jump = np.where(rho < r_max, 2.0 * density * rho ** 2 * eps, 0.0)
+    assert np.allclose(jump + ion_jump, w, rtol=1e-6, atol=1e-10)
+    # outside everything: neutral, psi and its gradient vanish
+    far = np.array([1.01, 2.0, 10.0]) * max(r_max, rho.max())
+    sf_far = oracle.slice_fields(rho, ur, w, wh, density, r_max, rq=far)
+    assert np.max(np.abs(sf_far["q_psi"])) < 1e-12 * density * r_max ** 2
+    assert np.max(np.abs(sf_far["q_dpsidr"])) < 1e-12 * density * r_max
+    # regular on the axis
+    near = np.array([1e-9, 1e-7])
+    sf_ax = oracle.slice_fields(rho, ur, w, wh, density, r_max, rq=near)
+    assert np.all(np.abs(near * sf_ax["q_dpsidr"]) < 1e-12)
+
+
+def test_psi_is_minus_integral_of_gauss_field():
+    """psi(rho) = -int_rho^inf d psi/drho, with d psi/drho from Gauss's law
+    (enclosed electron minus ion charge over rho), by adaptive quadrature."""
+    from scipy import integrate
+    edges, rho, ur, w, wh = _random_state(n=12, seed=5)
+    r_max = edges[-1]
+
+    def gauss(x):
+        return (np.sum(w[rho < x]) - 0.5 * min(x, r_max) ** 2) / x
+
+    top = max(r_max, rho.max())
+    brk = sorted(set(list(rho) + [r_max]))
+    x = np.array([0.3, 0.9, 1.7, 2.4])
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, r_max, rq=x)
+    for xi, psi in zip(x, sf["q_psi"]):
+        pts = [p for p in brk if xi < p < top]
+        val, _ = integrate.quad(gauss, xi, top, points=pts or None, limit=400,
+                                epsabs=1e-13, epsrel=1e-12)
+        assert abs(-val - psi) < 1e-10
+
+
+@pytest.mark.parametrize("edges", [W.edges_uniform(200, 5.0),
+                                   W.edges_refined(288, 0.05, 1712, 6.0),
+                                   W.edges_geometric(3000, 1e-5, 6.0)],
+                         ids=["uniform", "refined", "geometric"])
+def test_unperturbed_plasma_has_no_radial_field_at_rings(edges):
+    """A uniform neutral plasma at rest: the self weight makes the enclosed
+    electron charge at each ring equal the ion charge, so d psi/drho = 0 at
+    every ring (Gauss), for any spacing; d psi/dzeta = 0 (no motion)."""
+    rho0, _, w, wh = oracle.ring_init(edges)
+    sf = oracle.slice_fields(rho0, np.zeros_like(rho0), w, wh, 1.0, edges[-1])
+    scale = edges[-1]
+    assert np.max(np.abs(sf["dpsidr"])) < 5e-13 * scale
+    assert np.max(np.abs(sf["dpsidz"])) == 0.0
+    # total electron charge equals the ion column's
+    assert abs(w.sum() - 0.5 * edges[-1] ** 2) < 1e-12 * edges[-1] ** 2
+
+
+def test_unperturbed_offset_is_second_order_in_ring_spacing():
+    """Discrete rings against a continuous ion column leave psi = O(drho^2)
+    at the rings, which drives an O(drho^2) response of the plasma at rest:
+    halving the spacing cuts every spurious field by ~4."""
+    res = []
+    for n in (100, 200, 400):
+        edges = W.edges_uniform(n, 5.0)
+        steps = 500
+        pxi = np.arange(steps) * 0.02
+        out = oracle.run(edges, pxi, np.zeros(steps), np.zeros(steps), 0.02, steps,
+                         beam_fields=("ez",), ring_dumps=("r", "psi"))
+        r = out.rings["r"]
+        res.append((np.abs(out.rings["psi"][0]).max(), np.abs(out.beam["ez"]).max(),
+                    np.abs(r - r[0]).max()))
+    res = np.array(res)
+    ratio = res[:-1] / res[1:]
+    assert np.all(ratio > 3.3) and np.all(ratio < 4.7), ratio
+
+
+# --------------------------------------------------------------------------
+# d_zeta psi: finite difference along the ring motion
+# --------------------------------------------------------------------------
+def test_dzeta_psi_matches_finite_difference_of_psi():
+    """Moving every ring by d rho/d zeta = -u/psibar (Eq. plasma_particle_motion_2)
+    and differencing psi at fixed rho reproduces d psi/d zeta (pins the sign
+    reading of Eq. dpsi_dzeta)."""
+    edges, rho, ur, w, wh = _random_state(n=40, seed=3)
+    x = _between_ring_points(rho, n_per_gap=2)
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1], rq=x)
+    errs = []
+    for eps in (1e-4, 1e-5):
+        moved = rho + eps * ur / sf["psibar"]          # zeta -> zeta - eps
+        sfm = oracle.slice_fields(moved, ur, w, wh, 1.0, edges[-1], rq=x)
+        fd = (sf["q_psi"] - sfm["q_psi"]) / eps
+        errs.append(np.max(np.abs(fd - sf["q_dpsidz"])))
+    scale = np.max(np.abs(sf["q_dpsidz"]))
+    assert errs[1] < 2e-5 * scale
+    assert errs[0] / errs[1] > 5.0     # first-order convergence of the difference
+
+
+def test_fields_at_ring_blend_one_sided_limits_with_self_weight():
+    """At ring i each discontinuous field is the one-sided limit from below
+    plus what_i/w_i of its jump (the self-weight rule); psi is continuous."""
+    edges, rho, ur, w, wh = _random_state(n=30, seed=9)
+    eps = 1e-10
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1],
+                             rq=np.concatenate([rho * (1 - eps), rho * (1 + eps)]))
+    n = rho.shape[0]
+    f = wh / w
+    for key, qkey in (("dpsidr", "q_dpsidr"), ("dpsidz", "q_dpsidz")):
+        lo, hi = sf[qkey][:n], sf[qkey][n:]
+        blend = lo + f * (hi - lo)
+        assert np.allclose(sf[key], blend, rtol=1e-6, atol=1e-7), key
+    assert np.allclose(sf["psi"], sf["q_psi"][:n], atol=1e-8)
+    # B^(p) at the ring is the mean of its one-sided limits
+    lo, hi = sf["q_bp"][:n], sf["q_bp"][n:]
+    assert np.allclose(sf["bp"], 0.5 * (lo + hi), rtol=1e-6, atol=1e-9)
+
+
+def test_quasistatic_invariant_gamma_minus_uz():
+    """gamma - u_z = 1 + psi = psibar at every ring (Eq. cold_plasma_constant)."""
+    edges, rho, ur, w, wh = _random_state(n=60, seed=21, u_scale=2.0)
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1])
+    assert np.allclose(sf["gamma"] - sf["uz"], 1.0 + sf["psi"], rtol=0, atol=1e-12)
+    assert np.allclose(sf["psibar"], 1.0 + sf["psi"], rtol=0, atol=0)
+
+
+# --------------------------------------------------------------------------
+# B_theta^(p): closed form, dense elimination, jump conditions, Ampere
+# --------------------------------------------------------------------------
+def test_bp_one_ring_closed_form():
+    g = json.load(open(os.path.join(GOLDEN, "one_ring_bp.json")))
+    a, b = oracle.bp_shooting(g["rho"], g["A"], g["B"], g["C"])
+    assert np.allclose(a, g["a"], rtol=1e-14, atol=1e-16)
+    assert np.allclose(b, g["b"], rtol=1e-14, atol=1e-16)
+
+
+def _jump_system(rho, A, B, C):
+    """Dense 2N+2 system: b_0 = 0, a_N = 0, and at ring i (1-based)
+    [rho B] = C_i rho_i and [2a] = A_i (mean of one-sided B) + B_i, with the
+    unknowns ordered (a_0, b_0, a_1, b_1, ..., a_N, b_N)."""
+    n = rho.shape[0]
+    M = np.zeros((2 * n + 2, 2 * n + 2))
+    v = np.zeros(2 * n + 2)
+    M[0, 1] = 1.0
+    M[1, 2 * n] = 1.0
+    for i in range(1, n + 1):
+        r = rho[i - 1]
+        ia, ib, ja, jb = 2 * (i - 1), 2 * (i - 1) + 1, 2 * i, 2 * i + 1
+        row = 2 * i
+        M[row, ja] += r * r; M[row, jb] += 1.0
+        M[row, ia] -= r * r; M[row, ib] -= 1.0
+        v[row] = C[i - 1] * r
+        row += 1
+        M[row, ja] += 2.0; M[row, ia] -= 2.0
+        for col, coef in ((ia, r), (ib, 1.0 / r), (ja, r), (jb, 1.0 / r)):
+            M[row, col] -= 0.5 * A[i - 1] * coef
+        v[row] = B[i - 1]
+    sol = np.linalg.solve(M, v)
+    return sol[0::2], sol[1::2]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bp_shooting_matches_dense_jump_solve(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = 30
+    rho = np.sort(rng.uniform(0.05, 3.0, n))
+    A = rng.uniform(0.0, 0.2, n)
+    B = rng.normal(0.0, 0.1, n)
+    C = rng.normal(0.0, 0.05, n)
+    a, b = oracle.bp_shooting(rho, A, B, C)
+    ad, bd = _jump_system(rho, A, B, C)
+    scale = max(np.abs(ad).max(), np.abs(bd).max())
+    assert np.max(np.abs(a - ad)) < 1e-10 * scale
+    assert np.max(np.abs(b - bd)) < 1e-10 * scale
+
+
+def test_slice_bp_satisfies_jump_and_boundary_conditions():
+    edges, rho, ur, w, wh = _random_state(n=50, seed=4, u_scale=0.5)
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1])
+    order = sf["order"]
+    r = rho[order]
+    A, B, C = sf["A"][order], sf["B"][order], sf["C"][order]
+    a, b = sf["a"], sf["b"]
+    scale = np.abs(a).max() + np.abs(b).max()
+    assert abs(b[0]) == 0.0 and abs(a[-1]) < 1e-10 * scale
+    rb = (a[1:] - a[:-1]) * r ** 2 + (b[1:] - b[:-1])
+    assert np.allclose(rb, C * r, atol=1e-10 * scale)
+    bl = a[:-1] * r + b[:-1] / r
+    br = a[1:] * r + b[1:] / r
+    assert np.allclose(2 * (a[1:] - a[:-1]), A * 0.5 * (bl + br) + B, atol=1e-10 * scale)
+
+
+def _nonlinear_wake(dxi, span, n_b0=0.5, sigma_r=0.3, n_rings=400, n_r=64):
+    """Noise-free driver.  B^(b) at a ring is a step function of its radius
+    (the enclosed count of discrete beam radii), so a ring crossing a beam
+    radius costs a first-order error; convergence tests use many radii."""
+    steps = int(round(span / dxi))
+    drv = W.sampled_gaussian_beam(dxi, steps, n_b0, sigma_r, 0.6, 2.4, n_r=n_r)
+    return W.Wake("pin", W.edges_uniform(n_rings, 5.0), [drv], dxi, steps)
+
+
+def test_ampere_law_for_plasma_field_converges_second_order():
+    """rho B^(p)(rho) = -sum_{rho_i<rho} w_i u_z,i/psibar_i + d/dzeta int_0^rho rho' d_zeta psi
+    (Eq. maxwell_qsa_4 with the beam term removed), the zeta derivative taken
+    by central differences across slices behind the driver."""
+    rq = np.linspace(0.05, 4.5, 37)
+    errs = []
+    for dxi in (0.02, 0.01, 0.005):
+        wk = _nonlinear_wake(dxi, 9.0)
+        _, _, w, wh = oracle.ring_init(wk.edges)
+        res = oracle.run_wake(wk, beam_fields=(), ring_dumps=("r", "ur", "psibar", "uz"))
+        assert res.status == 0
+        n = int(round(8.0 / dxi))
+        R = res.rings
+        sf = oracle.slice_fields(R["r"][n], R["ur"][n], w, wh, 1.0, 5.0, rq=rq)
+
+        def zint(k):
+            t = w * R["ur"][k] / (R["r"][k] * R["psibar"][k])
+            return -np.sum(t[None, :] * np.minimum(rq[:, None], R["r"][k][None, :]) ** 2 / 2, axis=1)
+
+        jz = np.array([-np.sum((w * R["uz"][n] / R["psibar"][n])[R["r"][n] < x]) for x in rq])
+        rhs = jz - (zint(n + 1) - zint(n - 1)) / (2 * dxi)
+        lhs = rq * sf["q_bp"]
+        errs.append(np.max(np.abs(lhs - rhs)) / np.max(np.abs(lhs)))
+    assert errs[-1] < 5e-4, errs
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+def test_lorentz_force_integration_matches_algebraic_uz():
+    """du_z/dxi = -(gamma E_z + u_r B_theta)/psibar along each ring (Lorentz
+    force with d xi/dt = psibar/gamma) reproduces the algebraic u_z of
+    Eq. plasma_particle_motion_3, converging at second order."""
+    errs = []
+    for dxi in (0.02, 0.01, 0.005):
+        wk = _nonlinear_wake(dxi, 12.0)
+        res = oracle.run_wake(wk, beam_fields=(),
+                              ring_dumps=("ur", "psibar", "uz", "gamma", "dpsidz", "bp", "bb"))
+        R = res.rings
+        f = -(R["gamma"] * (-R["dpsidz"]) + R["ur"] * (R["bp"] + R["bb"])) / R["psibar"]
+        uz = R["uz"][0][None, :] + np.concatenate(
+            [np.zeros((1, f.shape[1])), np.cumsum(0.5 * (f[1:] + f[:-1]) * dxi, axis=0)])
+        errs.append(np.max(np.abs(uz - R["uz"])))
+    scale = np.max(np.abs(R["uz"]))
+    assert errs[-1] < 5e-5 * scale / 0.08, errs
+    assert errs[0] / errs[1] > 2.8 and errs[1] / errs[2] > 2.8, errs
+
+
+# --------------------------------------------------------------------------
+# the integrator
+# --------------------------------------------------------------------------
+def test_adams_bashforth_is_second_order():
+    """Ring radii at xi = 8 against a dxi/8 reference: error drops ~4x per
+    halving of dxi (Euler start, AB2 after)."""
+    def radii(dxi):
+        wk = _nonlinear_wake(dxi, 8.0, n_r=4096)
+        res = oracle.run_wake(wk, beam_fields=())
+        return res.final_r
+    ref = radii(0.0025)
+    errs = [np.max(np.abs(radii(d) - ref)) for d in (0.04, 0.02, 0.01)]
+    assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3, errs
+
+
+# --------------------------------------------------------------------------
+# the whole wake against linear theory
+# --------------------------------------------------------------------------
+def _axis_ez(n_b0, n_rings, dxi, sigma_r=0.5, sigma_z=1.0, span=20.0, xi_d=4.0):
+    steps = int(round(span / dxi))
+    pxi = np.arange(steps) * dxi
+    beams_xi, beams_r, beams_qw = [pxi], [np.zeros(steps)], [np.zeros(steps)]
+    if n_b0 > 0:
+        drv = W.sampled_gaussian_beam(dxi, steps, n_b0, sigma_r, sigma_z, xi_d, n_r=256)
+        beams_xi.insert(0, drv.xi)
+        beams_r.insert(0, drv.r)
+        beams_qw.insert(0, drv.q * drv.w)
+    res = oracle.run(W.edges_uniform(n_rings, 5.0), np.concatenate(beams_xi),
+                     np.concatenate(beams_r), np.concatenate(beams_qw), dxi, steps,
+                     beam_fields=("ez",))
+    return pxi, res.beam["ez"][-steps:]
+
+
+def _fit(pxi, ez, xi_d=4.0, lo=9.0, hi=19.9):
+    m = (pxi > lo) & (pxi < hi)
+    Amat = np.stack([np.cos(pxi[m] - xi_d), np.sin(pxi[m] - xi_d)], 1)
+    c, *_ = np.linalg.lstsq(Amat, ez[m], rcond=None)
+    return math.hypot(*c), math.atan2(c[1], c[0])
+
+
+def test_linear_wake_matches_closed_form():
+    """E_z on axis behind a weak Gaussian driver: amplitude and phase of the
+    linear closed form, with the O(drho^2) response of the undriven column
+    subtracted; the remaining deviation is O(n_b0)."""
+    g = json.load(open(os.path.join(GOLDEN, "linear_wake.json")))["cases"]
+    pxi, base = _axis_ez(0.0, 400, 0.01)
+    dev = {}
+    for case in g[:2]:
+        pxi, ez = _axis_ez(case["n_b0"], 400, 0.01)
+        amp, ph = _fit(pxi, ez - base)
+        dev[case["n_b0"]] = (amp / case["Ez_axis_amplitude"] - 1.0, ph)
+    d_small, ph_small = dev[0.005]
+    d_big, ph_big = dev[0.05]
+    assert abs(d_small) < 0.01 and abs(ph_small) < 0.01, dev
+    assert abs(d_big) < 0.025 and abs(ph_big) < 0.03, dev
+    # the deviation grows with the driver strength (nonlinear correction)
+    assert abs(d_big) > abs(d_small)
+
+
+# --------------------------------------------------------------------------
+# beam source and binning
+# --------------------------------------------------------------------------
+def test_beam_field_is_gauss_count_and_excludes_self():
+    rng = np.random.Generator(np.random.PCG64(8))
+    m = 300
+    br = rng.uniform(0.0, 2.0, m)
+    bq = -rng.uniform(0.5, 1.5, m)
+    edges, rho, ur, w, wh = _random_state(n=20, seed=8)
+    dxi = 0.05
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1], br, bq, dxi, rq=br)
+    for k in range(0, m, 7):
+        Q = bq[br < br[k]].sum()
+        assert abs(sf["q_bb"][k] - Q / (2 * math.pi * dxi * br[k])) < 1e-12 * max(1, abs(Q))
+    for i in range(rho.shape[0]):
+        Q = bq[br < rho[i]].sum()
+        assert abs(sf["bb"][i] - Q / (2 * math.pi * dxi * rho[i])) < 1e-12 * max(1, abs(Q))
+
+
+def test_nearest_slice_binning():
+    """A particle belongs to slice floor(xi/dxi + 1/2) (beam-grid spacing =
+    solver step, Sec. III); particles whose slice lies outside the window get
+    zero fields.  One charged particle in slice 1 makes the beam field of that
+    slice large, so the probes show which slice they landed in."""
+    dxi, steps = 0.1, 5
+    edges = W.edges_uniform(10, 1.0)
+    probes = {0.0499: 0, 0.0501: 1, 0.1: 1, 0.1499: 1, 0.1501: 2, -0.0499: 0,
+              -0.0501: None, 0.4499: 4, 0.4501: None}
+    xi = np.array([0.1] + list(probes))
+    r = np.array([0.25] + [0.5] * len(probes))
+    qw = np.array([-1.0] + [0.0] * len(probes))
+    res = oracle.run(edges, xi, r, qw, dxi, steps, beam_fields=("bt", "psi"))
+    bt, psi = res.beam["bt"][1:], res.beam["psi"][1:]
+    in_one = [k for k, sl in enumerate(probes.values()) if sl == 1]
+    for k, sl in enumerate(probes.values()):
+        if sl is None:
+            assert bt[k] == 0.0 and psi[k] == 0.0
+        elif sl == 1:
+            # beam field -1/(2 pi dxi r) partly shielded by the plasma response
+            assert bt[k] == bt[in_one[0]] and bt[k] < -1.0
+        else:
+            assert abs(bt[k]) < 0.1 and psi[k] != 0.0
+
+
+def test_charge_conservation_and_neutrality_through_a_run():
+    wk = _nonlinear_wake(0.02, 10.0, n_b0=2.0)
+    _, _, w, wh = oracle.ring_init(wk.edges)
+    res = oracle.run_wake(wk, beam_fields=(), ring_dumps=("r", "ur"))
+    assert res.status == 0
+    assert abs(w.sum() - 12.5) < 1e-12
+    for n in (100, 300, 499):
+        r, u = res.rings["r"][n], res.rings["ur"][n]
+        far = np.array([1.001, 3.0]) * max(5.0, r.max())
+        sf = oracle.slice_fields(r, u, w, wh, 1.0, 5.0, rq=far)
+        assert np.max(np.abs(sf["q_psi"])) < 1e-11
+        assert np.max(np.abs(sf["q_dpsidr"])) < 1e-12
+        assert np.all(r >= 0.0)
+
+
+def test_axis_crossing_reflects_and_stays_finite():
+    """A strong narrow driver throws rings through the axis; they come back at
+    rho >= 0 and the march completes."""
+    dxi = 0.01
+    drv = W.sampled_gaussian_beam(dxi, 800, 5.0, 0.15, 0.5, 2.0, n_r=64)
+    wk = W.Wake("axis", W.edges_uniform(300, 5.0), [drv], dxi, 800)
+    res = oracle.run_wake(wk, beam_fields=(), ring_dumps=("r", "ur"))
+    assert res.status == 0
+    r = res.rings["r"]
+    assert np.all(r >= 0.0) and np.all(np.isfinite(r))
+    crossed = np.any(np.diff(np.sign(res.rings["ur"]), axis=0) != 0, axis=0)
+    assert crossed.any()
