@@ -1,0 +1,341 @@
+"""Benchmark of the gridless quasistatic wake hot path on one or more GPUs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass of the whole hot path over the batched workload: 256
+independent wakes (log-uniform 500-8000 rings, 1000-6000 slices), each
+prepared on the device (ring initialisation, nearest-slice binning and radial
+sort of its beam) and then marched through its window in one persistent
+launch (sort, prefix sums, psi and derivatives, B_theta, fields on the beam
+particles, AB2 push).  The metric is ring-slice updates per second: one ring
+advanced one slice, summed over the slices each wake actually ran (a wake
+stops early if its quasistatic model breaks down, psibar <= 0).
+
+With torchrun (N > 1) every rank solves its own batch of 256 wakes (weak
+scaling, no collective on the data path) and rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_16623_gb300 import workloads as W  # noqa: E402
+
+METRIC = "ring-slice updates/s (batched FP32 vs plain FP64, 1 GB300); p50/p99 wake latency"
+UNIT = "ring-slices/s"
+# algorithmic floating-point operations per ring-slice update of the march
+# (the arithmetic of steps a3-a10 as written in the oracle, divides and logs
+# counted once; see the design doc for the itemisation)
+FLOPS_PER_RING_SLICE = 128
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
+SMS, FP32_LANES = 152, 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def _clock_summary(path, gpu_index):
+    try:
+        rows = [l.strip().split(",") for l in open(path) if l.strip()]
+    except Exception:
+        return None
+    rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(gpu_index)]
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    reasons = set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        for name, v in zip(names, r[5:9]):
+            if v.lower() in ("active", "1"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _workload(n_wakes, rank):
+    return [W.batched_wake(k + 256 * rank) for k in range(n_wakes)]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_16623_gb300 import wake as wm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.current_stream()
+    wakes = _workload(args.n_wakes, rank)
+    gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream) for wk in wakes]
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        for g in gs:
+            g.reset()
+        if ev is not None:
+            ev[1].record(stream)
+        wm.wake_batch_run(gs)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # work actually done per step (wakes may stop at a model breakdown)
+    ring_slices = 0
+    stopped = 0
+    for g, wk in zip(gs, wakes):
+        nxt, st, fl = g.progress()
+        ring_slices += wk.n_rings * nxt
+        stopped += int(st != 0)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{os.getpid()}.csv")
+    proc, fh = _clock_sampler(clk_path) if rank == 0 else (None, None)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(evs[k])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    if proc is not None:
+        proc.terminate()
+        proc.wait()
+        fh.close()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    march_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms, float(ring_slices)], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm_ = t.clone()
+        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+        tot_ms_max = float(mx[0])
+        rs_all = float(sm_[1])
+    else:
+        tot_ms_max = tot_ms
+        rs_all = float(ring_slices)
+    value = rs_all * args.steps / (tot_ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), rank-local
+    e2e = None
+    if not args.skip_e2e:
+        pinned = []
+        h2d = 0
+        for wk in wakes:
+            bl = []
+            for b in wk.beams:
+                t = [torch.from_numpy(a).pin_memory() for a in (b.xi, b.r, b.w)]
+                bl.append(type("B", (), {"xi": t[0], "r": t[1], "w": t[2], "q": b.q}))
+                h2d += 3 * 8 * b.n
+            pinned.append(bl)
+        outs = [{k: torch.empty(g.n_beam, dtype=torch.float32).pin_memory() for k in ("ez", "wr")} for g in gs]
+        d2h = sum(g.n_beam for g in gs) * 2 * 4
+        from paper_2603_16623_gb300.wake import _check, load
+        lib = load()
+
+        def e2e_step():
+            for g, bl in zip(gs, pinned):
+                g.reset(bl)
+            wm.wake_batch_run(gs)
+            for g, o in zip(gs, outs):
+                _check(lib.wake_get_beam_fields(g.handle, o["ez"].data_ptr(), o["wr"].data_ptr(), None, None, 0))
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t1 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t1) / n_e2e
+        if ws > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t[0])
+        e2e = {"value": rs_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e2e_s * 1e3}
+
+    # ---- plain FP64 one-wake-per-launch on a bounded sample (the spec denominator)
+    plain = None
+    if not args.skip_plain and rank == 0:
+        sample = wakes[: args.plain_wakes]
+        hs = [wm.Wake.from_workload(wk, precision="fp64", stream=stream.cuda_stream) for wk in sample]
+        for h in hs:
+            h.step_slices(20)
+        torch.cuda.synchronize()
+        for h in hs:
+            h.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h in hs:
+            h.step_slices(args.plain_slices)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        done = sum(wk.n_rings * h.progress()[0] for wk, h in zip(sample, hs))
+        plain_v = done / (e0.elapsed_time(e1) / 1e3)
+        plain = {"value": plain_v, "unit": UNIT,
+                 "sample": f"first {args.plain_slices} slices of wakes 0-{len(sample) - 1}, one wake per launch",
+                 "ratio_batched_mixed_over_plain_fp64": value / ws / plain_v}
+        for h in hs:
+            h.close()
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
+    cpu = None
+    if not args.skip_cpu and rank == 0 and ws == 1:
+        cpu = cpu_sample(args.cpu_seconds)
+
+    peaks = _peaks()
+    clocks = _clock_summary(clk_path, local) if rank == 0 else None
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    march_avg_ms = sum(march_ms) / len(march_ms)
+    achieved = FLOPS_PER_RING_SLICE * ring_slices / (march_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "march_kernel<PrecMixed>", "peak_basis":
+                    f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff (mixed)", "data": "synthetic",
+            "config": {"workload": f"batched: {args.n_wakes} independent wakes per GPU, log-uniform 500-8000 "
+                                   "rings, 1000-6000 slices of 0.01, 50k-500k beam particles",
+                       "n_wakes": args.n_wakes, "precision": "mixed", "block_threads": 256,
+                       "ring_slices_per_step": ring_slices, "wakes_stopped_by_breakdown": stopped,
+                       "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
+            "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + 1),
+            "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "clocks": clocks,
+            "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
+            "wall_s": wall,
+        }
+        print(json.dumps(line))
+    for g in gs:
+        g.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_sample(seconds: float):
+    """The FP64 oracle, as it stands, on the first slices of the batched
+    wakes until about `seconds` of single-core CPU time."""
+    import oracle
+    done = 0
+    t0 = time.perf_counter()
+    used = []
+    k = 0
+    slices = 400
+    while time.perf_counter() - t0 < seconds and k < 256:
+        wk = W.batched_wake(k)
+        res = oracle.run_wake(wk, max_slices=slices, beam_fields=())
+        done += wk.n_rings * res.slices_run
+        used.append(k)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {slices} slices of batched wakes 0-{used[-1]} ({done} ring-slices, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    # each step: the oracle on a bounded sample of the workload
+    import oracle
+    oracle.build()
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_sample(0.5)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_sample(per_step)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched: {args.n_wakes} independent wakes, log-uniform 500-8000 rings, "
+                                   "1000-6000 slices of 0.01, 50k-500k beam particles",
+                       "n_wakes": args.n_wakes},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-wakes", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--plain-wakes", type=int, default=4)
+    ap.add_argument("--plain-slices", type=int, default=300)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * wake.h -- C ABI of the GB300 gridless quasistatic wake solver (libwake.so).
+ *
+ * The solver advances the plasma-electron ring macroparticles of an
+ * axisymmetric plasma column through the co-moving window, one slice of
+ * thickness dxi at a time, as in Sec. II-III of arXiv 2603.16623 (gridless
+ * quasistatic model): per slice it sorts the rings by radius, forms the radial
+ * prefix sums of their charge and current, evaluates psi, d_rho psi,
+ * d_zeta psi, the beam field B_theta^(b) and the plasma field B_theta^(p)
+ * (Eq. ai_bi / App. A), the fields on the beam macroparticles of the slice,
+ * and advances ring radii and momenta with second-order Adams-Bashforth.
+ *
+ * Units: the paper's normalised plasma units (lengths k_p^-1, densities n0,
+ * fields m_e c omega_p / e).  xi = -zeta, xi = 0 is the head of the window;
+ * slice s covers xi in [(s-1/2) dxi, (s+1/2) dxi).  Plasma electrons
+ * (q = -1, m = 1) move over an immobile uniform ion column of density
+ * `density` filling rho <= r_edges[n_rings].
+ *
+ * Conventions for every entry point:
+ *   - Return value: a wake_status; nothing throws across the ABI.  On error
+ *     wake_last_error() returns a thread-local message.
+ *   - Ownership: the caller owns every array it passes.  wake_init copies its
+ *     inputs to the device; afterwards the handle owns all device state until
+ *     wake_destroy.  Output arrays are written, never kept.
+ *   - Streams: work is enqueued on the CUDA stream given to wake_init
+ *     (cudaStream_t passed as void*, NULL = legacy default stream).  Calls that
+ *     return data to host memory synchronise that stream.
+ *   - Precision: WAKE_FP64 computes everything in double and returns double
+ *     arrays; WAKE_MIXED computes pushes and field evaluation in float with
+ *     compensated (float-float) prefix sums and returns float arrays.
+ *     "real" below means double for WAKE_FP64 and float for WAKE_MIXED.
+ */
+#ifndef GBWAKE_WAKE_H
+#define GBWAKE_WAKE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int wake_status;
+enum {
+    WAKE_OK = 0,
+    WAKE_EINVAL = 1,      /* bad argument or unsupported size                 */
+    WAKE_ENOMEM = 2,      /* device allocation failed                         */
+    WAKE_ECUDA = 3,       /* a CUDA call failed                               */
+    WAKE_ENONFINITE = 4,  /* a slice produced psibar <= 0 or a non-finite field;
+                             the wake stopped there (see wake_get_progress)   */
+    WAKE_ETIMEOUT = 5,    /* a bounded device-side wait gave up               */
+    WAKE_EBUSY = 6        /* admission refused (memory budget / capacity)     */
+};
+
+enum { WAKE_FP64 = 0, WAKE_MIXED = 1 };
+
+/* flags of wake_config */
+enum {
+    WAKE_DUMP_RING_R = 1,      /* keep ring radii at the start of every slice  */
+    WAKE_DUMP_RING_FIELDS = 2  /* keep psi, d_rho psi, d_zeta psi, B^(p), B^(b)
+                                  and u_r at every ring and slice (tests)      */
+};
+
+/* Plasma column (Sec. II, ring macroparticles): ring j fills the cell
+   [r_edges[j], r_edges[j+1]); it starts at the cell centre with u_r = 0 and
+   weight density * centre * width (Eq. macroparticle_weight). */
+typedef struct {
+    int32_t n_rings;          /* 1 <= n_rings <= wake_max_rings()                */
+    const double *r_edges;    /* host, n_rings+1 values, r_edges[0] = 0,
+                                 strictly increasing                            */
+    double density;           /* uniform plasma (= ion column) density, > 0     */
+} wake_plasma_desc;
+
+/* A beam species (ultra-relativistic, frozen during a wake solve, Sec. II).
+   Each macroparticle is a charged ring of `w` real particles in the slice
+   nearest to its xi; its B_theta^(b) is that of the enclosed charge. */
+typedef struct {
+    int64_t n;                /* macroparticles (>= 0)                          */
+    const double *xi;         /* host [n]                                       */
+    const double *r;          /* host [n], >= 0                                 */
+    const double *w;          /* host [n], weights (real particles, n0 k_p^-3)  */
+    double q;                 /* charge sign of the species, e.g. -1            */
+} wake_beam_desc;
+
+typedef struct {
+    double dxi;               /* slice thickness, > 0                            */
+    int32_t n_steps;          /* slices in the window, >= 1                      */
+    int32_t precision;        /* WAKE_FP64 or WAKE_MIXED                         */
+    int32_t flags;            /* WAKE_DUMP_* bits                                */
+    int32_t block_threads;    /* threads per wake (multiple of 32, 64..512);
+                                 0 = library default                            */
+} wake_config;
+
+typedef struct wake_handle wake_handle;
+
+/* Copies the plasma and the beams to the device, initialises the rings
+   (Sec. II: cell centres, weights, self weights) and bins and radially sorts
+   the beam macroparticles by slice (once per solve: the beam is frozen).
+   Beams are concatenated in order; "beam particle k" below indexes that
+   concatenation.  Errors: EINVAL (bad sizes, edges, dxi, a slice holding
+   more than wake_max_slice_particles() particles), ENOMEM, ECUDA.
+   On success *out receives a handle at slice 0. */
+wake_status wake_init(const wake_config *cfg, const wake_plasma_desc *plasma,
+                      const wake_beam_desc *beams, int32_t n_beams,
+                      void *cuda_stream, wake_handle **out);
+
+/* Puts the wake back at slice 0 without reallocating: if beams is not NULL,
+   first uploads a new set of beam macroparticles from host arrays (same
+   number of species and the same particle counts as at wake_init; the
+   charge signs may change), then re-initialises the rings and re-bins and
+   re-sorts the beam on the device (the same a0/a1 preparation as wake_init).
+   Asynchronous on the handle's stream; the host arrays must stay valid until
+   the stream reaches this point (use pinned memory for overlap).  A slice
+   holding more than wake_max_slice_particles() particles is reported later
+   by wake_get_progress as status WAKE_EINVAL (the march does not run).
+   Errors: EINVAL (different species count or sizes), ECUDA. */
+wake_status wake_reset(wake_handle *h, const wake_beam_desc *beams, int32_t n_beams);
+
+/* Advances the wake by up to n_slices slices (fewer at the end of the
+   window); for each slice: sort, B^(b) at the rings, psi and its derivatives
+   (Eqs. dpsi_dr, psi, dpsi_dzeta), u_z and gamma, B^(p) (Eq. ai_bi), fields
+   at that slice's beam particles, then the AB2 push to the next slice.
+   Asynchronous on the handle's stream; resumable.  A slice that fails the
+   guard (psibar <= 0 or a non-finite field) stops the wake: its beam fields
+   are written, no push is done, and wake_get_progress reports
+   WAKE_ENONFINITE.  Errors: EINVAL, ECUDA. */
+wake_status wake_step_slices(wake_handle *h, int32_t n_slices);
+
+/* Fields at the current slice (the one the next wake_step_slices would
+   solve) at n arbitrary radii r (Eqs. b_theta_plasma..dpsi_dzeta sampled off
+   the rings): ez = E_z = -d_zeta psi, wr = E_r - B_theta = -d_rho psi,
+   bt = B_theta^(p) + B_theta^(b), psi.  The ring state is not advanced.
+   r and the outputs are host arrays (device_ptrs = 0) or device arrays
+   (device_ptrs = 1); outputs are "real"; any output may be NULL.
+   Errors: EINVAL (n < 0, window finished), ECUDA. */
+wake_status wake_fields_at(wake_handle *h, int64_t n, const double *r, void *ez, void *wr,
+                           void *bt, void *psi, int32_t device_ptrs);
+
+/* Fields on every beam particle at its own slice (filled as slices are
+   solved; 0 for particles outside the window or not yet reached), in the
+   caller's beam order: E_z, W_r = E_r - B_theta, B_theta, psi ("real",
+   NULL = skip).  Host (device_ptrs = 0) or device (1) arrays.
+   Errors: EINVAL, ECUDA. */
+wake_status wake_get_beam_fields(wake_handle *h, void *ez, void *wr, void *bt, void *psi,
+                                 int32_t device_ptrs);
+
+/* Runs the rest of the window and returns E_z and W_r per beam particle in
+   caller order (host arrays of "real", NULL = skip) and, if the handle was
+   created with WAKE_DUMP_RING_R and ring_r is not NULL, the ring radii at
+   the start of every slice, [n_steps][n_rings] by ring index ("real").
+   Returns ENONFINITE if the wake stopped early (outputs still written). */
+wake_status wake_run(wake_handle *h, void *beam_ez, void *beam_wr, void *ring_r);
+
+/* Runs the rest of the window of n handles in ONE persistent launch (one
+   thread block walks one wake; blocks take wakes largest-first).  All
+   handles must share precision, stream and block_threads.  Returns OK when
+   the launch was enqueued; per-wake outcome via wake_get_progress. */
+wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
+
+/* Progress of a wake (synchronises its stream): next slice to solve,
+   status (OK or ENONFINITE) and the failing slice (-1 if none). */
+wake_status wake_get_progress(wake_handle *h, int32_t *next_slice, int32_t *status,
+                              int32_t *fail_slice);
+
+/* Ring state by ring index (synchronises): radii and radial momenta at the
+   current slice ("real" host arrays of n_rings, NULL = skip).  A cheap
+   checkpoint of a resumable solve. */
+wake_status wake_get_ring_state(wake_handle *h, void *rho, void *ur);
+
+/* Dumps kept with WAKE_DUMP_RING_FIELDS, [n_steps][n_rings] by ring index,
+   "real" host arrays (NULL = skip). */
+wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, void *dpsidr,
+                                void *dpsidz, void *bp, void *bb);
+
+void wake_destroy(wake_handle *h);
+
+const char *wake_last_error(void);
+int32_t wake_max_rings(int32_t precision);          /* rings per wake supported */
+int64_t wake_max_slice_particles(int32_t precision); /* beam particles per slice */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBWAKE_WAKE_H */

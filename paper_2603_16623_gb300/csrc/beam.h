@@ -1,0 +1,22 @@
+// beam.h -- host launchers of the beam preparation kernels (beam.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbwake {
+cudaError_t launch_fold_charge(double* qw, const double* w, double q, int64_t n, cudaStream_t st);
+cudaError_t launch_bin_count(const double* xi, int64_t n, double dxi, int32_t n_steps, int32_t* slot,
+                             int32_t* cnt, cudaStream_t st);
+cudaError_t launch_excl_scan(const int32_t* cnt, int32_t n, int32_t* off, int32_t* max_count, cudaStream_t st);
+cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, const int32_t* off, int32_t* fill,
+                               int32_t* binned_idx, cudaStream_t st);
+size_t slice_sort_smem(int32_t m_pad);
+cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st);
+template <class R>
+cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
+                              int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t* ctl,
+                              cudaStream_t st);
+template <class R>
+cudaError_t launch_scatter_out(const int32_t* idx, const int32_t* nbin, int64_t nb_max, const R* src, R* dst,
+                               cudaStream_t st);
+}  // namespace gbwake

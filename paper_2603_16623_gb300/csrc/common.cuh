@@ -1,0 +1,246 @@
+// common.cuh -- device utilities of the wake solver: float-float arithmetic,
+// the two precision policies, and block-wide scans for associative (not
+// necessarily commutative) operators in either direction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbwake {
+
+// ---------------------------------------------------------------------------
+// float-float ("ff"): an unevaluated sum hi + lo of two floats (~48-bit
+// significand).  Knuth's TwoSum and the FMA-based exact product; nothing here
+// multiplies and adds in one expression except through fmaf.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    ff t = ff_two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = ff_fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    ff s = ff_two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float ff_to_f(ff a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ ff ff_from_d(double d) {
+    float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+
+// ---------------------------------------------------------------------------
+// precision policies
+//   PrecF64   : everything in double (the plain path)
+//   PrecMixed : state, pushes and field evaluation in float; radial prefix
+//               sums, psi and d_rho psi assembled in float-float
+// ---------------------------------------------------------------------------
+struct PrecF64 {
+    using R = double;
+    using A = double;
+    static constexpr bool kShooting = true;
+};
+struct PrecMixed {
+    using R = float;
+    using A = ff;
+    static constexpr bool kShooting = false;
+};
+
+// accumulator helpers, overloaded on the accumulator type
+__device__ __forceinline__ double acc_zero(double) { return 0.0; }
+__device__ __forceinline__ ff acc_zero(ff) { return {0.f, 0.f}; }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ int64_t acc_add(int64_t a, int64_t b) { return a + b; }
+__device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ double acc_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ ff acc_sub(ff a, ff b) { return ff_sub(a, b); }
+__device__ __forceinline__ double acc_add_r(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_add_r(ff a, float b) { return ff_add_f(a, b); }
+__device__ __forceinline__ double acc_mul_r(double a, double b) { return a * b; }
+__device__ __forceinline__ ff acc_mul_r(ff a, float b) { return ff_mul_f(a, b); }
+__device__ __forceinline__ double acc_to_r(double a) { return a; }
+__device__ __forceinline__ float acc_to_r(ff a) { return ff_to_f(a); }
+__device__ __forceinline__ double acc_from_d(double d, double) { return d; }
+__device__ __forceinline__ ff acc_from_d(double d, ff) { return ff_from_d(d); }
+// exact square of a real as an accumulator
+__device__ __forceinline__ double acc_sq(double x) { return x * x; }
+__device__ __forceinline__ ff acc_sq(float x) { return ff_two_prod(x, x); }
+
+__device__ __forceinline__ double real_log(double x) { return log(x); }
+__device__ __forceinline__ float real_log(float x) { return logf(x); }
+__device__ __forceinline__ bool real_finite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool real_finite(float x) { return isfinite(x); }
+
+// ---------------------------------------------------------------------------
+// shuffles for the scanned types
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double shfl_up_t(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_dn_t(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ int64_t shfl_up_t(int64_t v, int o) {
+    return (int64_t)__shfl_up_sync(0xffffffffu, (long long)v, o);
+}
+__device__ __forceinline__ int64_t shfl_dn_t(int64_t v, int o) {
+    return (int64_t)__shfl_down_sync(0xffffffffu, (long long)v, o);
+}
+__device__ __forceinline__ float shfl_up_t(float v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_dn_t(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ ff shfl_up_t(ff v, int o) { return {shfl_up_t(v.hi, o), shfl_up_t(v.lo, o)}; }
+__device__ __forceinline__ ff shfl_dn_t(ff v, int o) { return {shfl_dn_t(v.hi, o), shfl_dn_t(v.lo, o)}; }
+
+template <class T>
+struct Pair {
+    T x, y;
+};
+template <class T>
+__device__ __forceinline__ Pair<T> shfl_up_t(Pair<T> v, int o) { return {shfl_up_t(v.x, o), shfl_up_t(v.y, o)}; }
+template <class T>
+__device__ __forceinline__ Pair<T> shfl_dn_t(Pair<T> v, int o) { return {shfl_dn_t(v.x, o), shfl_dn_t(v.y, o)}; }
+
+// 2x2 matrix and the affine map x -> M x + c
+template <class R>
+struct Mat2 {
+    R m00, m01, m10, m11;
+};
+template <class R>
+struct Aff2 {
+    R m00, m01, m10, m11, c0, c1;
+};
+template <class R>
+__device__ __forceinline__ Mat2<R> shfl_up_t(Mat2<R> v, int o) {
+    return {shfl_up_t(v.m00, o), shfl_up_t(v.m01, o), shfl_up_t(v.m10, o), shfl_up_t(v.m11, o)};
+}
+template <class R>
+__device__ __forceinline__ Mat2<R> shfl_dn_t(Mat2<R> v, int o) {
+    return {shfl_dn_t(v.m00, o), shfl_dn_t(v.m01, o), shfl_dn_t(v.m10, o), shfl_dn_t(v.m11, o)};
+}
+template <class R>
+__device__ __forceinline__ Aff2<R> shfl_up_t(Aff2<R> v, int o) {
+    return {shfl_up_t(v.m00, o), shfl_up_t(v.m01, o), shfl_up_t(v.m10, o),
+            shfl_up_t(v.m11, o), shfl_up_t(v.c0, o), shfl_up_t(v.c1, o)};
+}
+template <class R>
+__device__ __forceinline__ Aff2<R> shfl_dn_t(Aff2<R> v, int o) {
+    return {shfl_dn_t(v.m00, o), shfl_dn_t(v.m01, o), shfl_dn_t(v.m10, o),
+            shfl_dn_t(v.m11, o), shfl_dn_t(v.c0, o), shfl_dn_t(v.c1, o)};
+}
+
+// ---------------------------------------------------------------------------
+// operators: op(a, b) = "a, then b" where a covers the earlier elements of
+// the scan order
+// ---------------------------------------------------------------------------
+struct OpAdd {
+    template <class T>
+    __device__ __forceinline__ T operator()(T a, T b) const { return acc_add(a, b); }
+};
+struct OpAddPair {
+    template <class T>
+    __device__ __forceinline__ Pair<T> operator()(Pair<T> a, Pair<T> b) const {
+        return {acc_add(a.x, b.x), acc_add(a.y, b.y)};
+    }
+};
+// matrix product, later element on the left: result = b * a
+struct OpMatLeft {
+    template <class R>
+    __device__ __forceinline__ Mat2<R> operator()(Mat2<R> a, Mat2<R> b) const {
+        return {b.m00 * a.m00 + b.m01 * a.m10, b.m00 * a.m01 + b.m01 * a.m11,
+                b.m10 * a.m00 + b.m11 * a.m10, b.m10 * a.m01 + b.m11 * a.m11};
+    }
+};
+// composition of affine maps, a applied first: x -> Mb (Ma x + ca) + cb
+struct OpAffThen {
+    template <class R>
+    __device__ __forceinline__ Aff2<R> operator()(Aff2<R> a, Aff2<R> b) const {
+        return {b.m00 * a.m00 + b.m01 * a.m10, b.m00 * a.m01 + b.m01 * a.m11,
+                b.m10 * a.m00 + b.m11 * a.m10, b.m10 * a.m01 + b.m11 * a.m11,
+                b.m00 * a.c0 + b.m01 * a.c1 + b.c0, b.m10 * a.c0 + b.m11 * a.c1 + b.c1};
+    }
+};
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan.  REV = false: thread order 0, 1, ...;
+// REV = true: the scan runs from the last thread down.  blockDim.x must be a
+// multiple of 32 (<= 1024).  sbuf must hold 33 values of T in shared memory.
+// Returns the exclusive fold of the earlier threads' values; `total` gets the
+// fold over the whole block.  Contains barriers: every thread must call.
+// ---------------------------------------------------------------------------
+template <bool REV, class T, class Op>
+__device__ __forceinline__ T warp_incl_scan(T v, Op op) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        T o = REV ? shfl_dn_t(v, off) : shfl_up_t(v, off);
+        bool take = REV ? (lane + off < 32) : (lane >= off);
+        if (take) v = op(o, v);
+    }
+    return v;
+}
+
+template <bool REV, class T, class Op>
+__device__ T block_excl_scan(T v, Op op, T ident, T* sbuf, T& total) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    T inc = warp_incl_scan<REV>(v, op);
+    T lex = REV ? shfl_dn_t(inc, 1) : shfl_up_t(inc, 1);
+    if (REV ? (lane == 31) : (lane == 0)) lex = ident;
+    if (REV ? (lane == 0) : (lane == 31)) sbuf[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T wv = lane < nw ? sbuf[lane] : ident;
+        T winc = warp_incl_scan<REV>(wv, op);
+        T wex = REV ? shfl_dn_t(winc, 1) : shfl_up_t(winc, 1);
+        if (REV ? (lane == 31) : (lane == 0)) wex = ident;
+        __syncwarp();
+        if (lane < nw) sbuf[lane] = wex;
+        if (lane == (REV ? 0 : 31)) sbuf[32] = winc;
+    }
+    __syncthreads();
+    T res = op(sbuf[warp], lex);
+    total = sbuf[32];
+    __syncthreads();
+    return res;
+}
+
+// first index i in [0, n) with a[i] >= x (n if none)
+template <class R>
+__device__ __forceinline__ int lower_bound_dev(const R* a, int n, R x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace gbwake

@@ -1,0 +1,489 @@
+// march.cuh -- the per-slice march of one wake per thread block.
+//
+// One block owns one wake.  Rings live in radius order in the wake's device
+// arrays; thread t owns the contiguous chunk [t*K, t*K+K) of sorted
+// positions (K = ceil(n / blockDim)).  Each slice runs the chain of Sec. III:
+//   a2 sort (check; bitonic sort in shared memory only if out of order)
+//   a3 B^(b) at the rings (binary search in the slice's sorted beam radii)
+//   a4 block scan of (sum w, sum w ln rho)                   (Eqs. dpsi_dr, psi)
+//   a5 psi, d_rho psi (self weight), psibar, gamma            (Eq. plasma_particle_motion_3/4)
+//   a6 block scan of t = w u/(rho psibar) -> d_zeta psi        (Eq. dpsi_dzeta)
+//   a7 A, B, C                                                (Eqs. b_coeffs_1..3)
+//   a8 B^(p): FP64 = App. A shooting as an affine-map scan;
+//            mixed = regular/decaying homogeneous solutions + discrete Green's
+//            function (same discrete solution, no growing-mode cancellation)
+//   a9 fields on the beam particles of the slice
+//   a10 AB2 push with axis reflection
+#pragma once
+
+#include "common.cuh"
+
+namespace gbwake {
+
+// control words of a wake (device ints)
+enum { CTL_NEXT = 0, CTL_STATUS = 1, CTL_FAIL = 2, CTL_BUF = 3, CTL_PREV = 4, CTL_N = 8 };
+
+enum { MODE_MARCH = 0, MODE_QUERY = 1 };
+
+constexpr int kScanBytes = 33 * 64;  // block-scan scratch (33 values of <= 64 B)
+
+template <class P>
+struct WakeDev {
+    using R = typename P::R;
+    using A = typename P::A;
+    int32_t n, n_steps, n_pad, pad0;
+    double dxi, density, rho_max;
+    const R* w;   // [n] by ring id
+    const R* wh;  // [n] by ring id
+    R* rho[2];
+    R* ur[2];
+    R* frho[2];
+    R* fur[2];
+    int32_t* rid[2];
+    // per-ring scratch, sorted order
+    R *bb, *psib, *gam, *dpr, *tt, *cA, *cB, *cC;
+    // per-region arrays [n+1]
+    A *regS, *regL;
+    R *regT, *ak, *bk, *Ra, *Rb, *Da, *Db;
+    // binned beam
+    int64_t nb;
+    const int32_t* boff;  // [n_steps+1]
+    const R *br, *bE, *bQs, *bTot;
+    R *out_ez, *out_wr, *out_bt, *out_psi;
+    // dumps [n_steps][n] by ring id (nullable)
+    R *dump_r, *dump_ur, *dump_psi, *dump_dpr, *dump_dpz, *dump_bp, *dump_bb;
+    int32_t* ctl;
+    // query mode
+    int64_t nq;
+    const double* rq;
+    R *q_ez, *q_wr, *q_bt, *q_psi;
+};
+
+// ion column: enclosed charge n min(x, rho_max)^2 / 2 and its potential
+template <class A, class R>
+__device__ __forceinline__ A ion_enclosed(R x, R rmax, R half_n, A Imax) {
+    if (x < rmax) return acc_mul_r(acc_sq(x), half_n);
+    return Imax;
+}
+template <class A, class R>
+__device__ __forceinline__ A ion_psi(R x, R rmax, R quarter_n, A Imax, A c0) {
+    if (x <= rmax) return acc_sub(c0, acc_mul_r(acc_sq(x), quarter_n));
+    return acc_mul_r(Imax, -real_log(x));
+}
+
+__device__ __forceinline__ double acc_add_prod(double a, double x, double y) { return a + x * y; }
+__device__ __forceinline__ ff acc_add_prod(ff a, float x, float y) { return ff_add(a, ff_two_prod(x, y)); }
+
+template <class P>
+__global__ void __launch_bounds__(512)
+march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ order,
+             int32_t max_slices, int32_t mode, int32_t mb_cap) {
+    using R = typename P::R;
+    using A = typename P::A;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_ctl[CTL_N];
+
+    const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
+    const int T = blockDim.x;
+    const int tid = threadIdx.x;
+    const int n = W.n;
+    const int K = (n + T - 1) / T;
+    const int p0 = min(n, tid * K);
+    const int p1 = min(n, p0 + K);
+
+    unsigned char* sscan = smem;
+    R* keys = reinterpret_cast<R*>(smem + kScanBytes);
+    int32_t* vals = reinterpret_cast<int32_t*>(keys + W.n_pad);
+    R* sR = keys;      // sorted ring radii (after the sort)
+    R* sB = keys + n;  // staged beam radii of the slice
+
+    if (tid < CTL_N) s_ctl[tid] = W.ctl[tid];
+    __syncthreads();
+    if (s_ctl[CTL_STATUS] != 0) return;
+    int slice = s_ctl[CTL_NEXT];
+    int buf = s_ctl[CTL_BUF];
+    int has_prev = s_ctl[CTL_PREV];
+    int status = 0, fail = -1;
+    const int s_end = mode == MODE_MARCH ? min(W.n_steps, slice + max_slices) : slice + 1;
+
+    const double dens_d = W.density, rmax_d = W.rho_max;
+    const R rmax = (R)rmax_d;
+    const R half_n = (R)(0.5 * dens_d), quarter_n = (R)(0.25 * dens_d);
+    const A Imax = acc_from_d(0.5 * dens_d * rmax_d * rmax_d, A());
+    const A c0 = acc_from_d(0.25 * dens_d * rmax_d * rmax_d - 0.5 * dens_d * rmax_d * rmax_d * log(rmax_d), A());
+    const R dxi = (R)W.dxi;
+    const R inv_2pi_dxi = (R)(1.0 / (6.283185307179586476925286766559 * W.dxi));
+    const A zeroA = acc_zero(A());
+
+    for (; slice < s_end; ++slice) {
+        R* rho = W.rho[buf];
+        // ---------------- a2: sort by radius (stable w.r.t. previous order)
+        bool ok = true;
+        for (int p = p0; p < p1; ++p)
+            if (p + 1 < n && rho[p + 1] < rho[p]) ok = false;
+        if (!__syncthreads_and(ok)) {
+            for (int i = tid; i < W.n_pad; i += T) {
+                keys[i] = i < n ? rho[i] : (R)INFINITY;
+                vals[i] = i;
+            }
+            __syncthreads();
+            for (int k = 2; k <= W.n_pad; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int i = tid; i < W.n_pad; i += T) {
+                        int ixj = i ^ j;
+                        if (ixj > i) {
+                            R ki = keys[i], kj = keys[ixj];
+                            int vi = vals[i], vj = vals[ixj];
+                            bool gt = (ki > kj) || (ki == kj && vi > vj);
+                            if (gt == ((i & k) == 0)) {
+                                keys[i] = kj; keys[ixj] = ki;
+                                vals[i] = vj; vals[ixj] = vi;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            const int nb = buf ^ 1;
+            for (int p = tid; p < n; p += T) {
+                int src = vals[p];
+                W.rho[nb][p] = W.rho[buf][src];
+                W.ur[nb][p] = W.ur[buf][src];
+                W.frho[nb][p] = W.frho[buf][src];
+                W.fur[nb][p] = W.fur[buf][src];
+                W.rid[nb][p] = W.rid[buf][src];
+            }
+            buf = nb;
+            rho = W.rho[buf];
+            __syncthreads();
+        }
+        R* ur = W.ur[buf];
+        R* frho = W.frho[buf];
+        R* fur = W.fur[buf];
+        const int32_t* rid = W.rid[buf];
+
+        // ---------------- stage ring radii and this slice's beam radii
+        const bool have_beam = W.nb > 0 && slice < W.n_steps;
+        int b0 = 0, m = 0;
+        R qtot = 0;
+        if (have_beam) {
+            b0 = W.boff[slice];
+            m = W.boff[slice + 1] - b0;
+            qtot = W.bTot[slice];
+        }
+        const bool staged = m <= mb_cap;
+        for (int p = tid; p < n; p += T) sR[p] = rho[p];
+        if (staged)
+            for (int q = tid; q < m; q += T) sB[q] = W.br[b0 + q];
+        __syncthreads();
+        const R* beamR = staged ? sB : (W.br + b0);
+
+        // ---------------- a3 + a4: beam field at rings, local sums
+        Pair<A> loc = {zeroA, zeroA};
+        for (int p = p0; p < p1; ++p) {
+            R r = sR[p];
+            int id = rid[p];
+            R w = W.w[id];
+            R bbv = 0;
+            if (m > 0 && r > (R)0) {
+                int lb = lower_bound_dev(beamR, m, r);
+                R Q = lb < m ? W.bE[b0 + lb] : qtot;
+                bbv = Q * inv_2pi_dxi / r;
+            }
+            W.bb[p] = bbv;
+            loc.x = acc_add_r(loc.x, w);
+            loc.y = acc_add_prod(loc.y, w, real_log(r));
+        }
+        Pair<A> tot;
+        Pair<A> ex = block_excl_scan<false>(loc, OpAddPair(), Pair<A>{zeroA, zeroA},
+                                            reinterpret_cast<Pair<A>*>(sscan), tot);
+        const A Wtot = tot.x, Ltot = tot.y;
+
+        // ---------------- a5: psi, d_rho psi, psibar, gamma, t
+        A S = ex.x, L = ex.y;
+        A tl = zeroA;
+        for (int p = p0; p < p1; ++p) {
+            R r = sR[p];
+            R u = ur[p];
+            int id = rid[p];
+            R w = W.w[id], wh = W.wh[id];
+            R lnr = real_log(r);
+            A Lsuf = acc_sub(Ltot, L);
+            W.regS[p] = S;
+            W.regL[p] = Lsuf;
+            A psiA = acc_add(acc_add(Lsuf, acc_mul_r(S, lnr)), ion_psi(r, rmax, quarter_n, Imax, c0));
+            R psi = acc_to_r(psiA);
+            A encl = acc_sub(acc_add_r(S, wh), ion_enclosed(r, rmax, half_n, Imax));
+            R dprv = acc_to_r(encl) / r;
+            R pb = (R)1 + psi;
+            R g = ((R)1 + u * u + pb * pb) / ((R)2 * pb);
+            R t = w * u / (r * pb);
+            W.psib[p] = pb;
+            W.gam[p] = g;
+            W.dpr[p] = dprv;
+            W.tt[p] = t;
+            if (mode == MODE_MARCH && W.dump_psi) {
+                size_t row = (size_t)slice * n + id;
+                W.dump_psi[row] = psi;
+                W.dump_dpr[row] = dprv;
+            }
+            S = acc_add_r(S, w);
+            L = acc_add_prod(L, w, lnr);
+            tl = acc_add_r(tl, t);
+        }
+        if (tid == 0) {
+            W.regS[n] = Wtot;
+            W.regL[n] = zeroA;
+            W.regT[n] = (R)0;
+        }
+        A Ttot;
+        A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot);
+
+        // ---------------- a6 + a7: d_zeta psi, A, B, C
+        {
+            A Tacc = Tex;
+            for (int p = p0; p < p1; ++p) {
+                R r = sR[p];
+                R u = ur[p];
+                int id = rid[p];
+                R w = W.w[id], wh = W.wh[id];
+                R t = W.tt[p];
+                W.regT[p] = acc_to_r(acc_sub(Ttot, Tacc));
+                Tacc = acc_add_r(Tacc, t);
+                R above = acc_to_r(acc_sub(Ttot, Tacc));
+                R dpz = -(above + ((R)1 - wh / w) * t);
+                R pb = W.psib[p], g = W.gam[p], dprv = W.dpr[p], bbv = W.bb[p];
+                R wr = w / r, pb2 = pb * pb;
+                R Ac = wr / pb;
+                R Bc = -wr * g * dprv / pb2 + wr * bbv / pb + (w / (r * r)) * u * u / pb2 +
+                       wr * u * u * dprv / (pb2 * pb) - wr * u * dpz / pb2;
+                R Cc = -wr * (g / pb - (R)1 - u * u / pb2);
+                W.cA[p] = Ac;
+                W.cB[p] = Bc;
+                W.cC[p] = Cc;
+                W.tt[p] = dpz;  // t no longer needed: keep d_zeta psi
+                if (mode == MODE_MARCH && W.dump_dpz) W.dump_dpz[(size_t)slice * n + id] = dpz;
+            }
+        }
+
+        // ---------------- a8: B_theta^(p) region coefficients a_k, b_k
+        if constexpr (P::kShooting) {
+            // App. A: (K,U)_k and (T,P)_k from the prefix of affine maps
+            Aff2<R> Floc = {1, 0, 0, 1, 0, 0};
+            for (int p = p0; p < p1; ++p) {
+                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
+                Aff2<R> E = {(R)1 + (R)0.5 * Ac * r, (R)0.5 * Ac / r, -(R)0.5 * Ac * r * r * r,
+                             (R)1 - (R)0.5 * Ac * r, (R)0.25 * ((R)2 * Bc + Ac * Cc),
+                             (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r)};
+                Floc = OpAffThen()(Floc, E);
+            }
+            Aff2<R> Ftot;
+            Aff2<R> F = block_excl_scan<false>(Floc, OpAffThen(), Aff2<R>{1, 0, 0, 1, 0, 0},
+                                               reinterpret_cast<Aff2<R>*>(sscan), Ftot);
+            const R a0 = -Ftot.c0 / Ftot.m00;
+            if (tid == 0) {
+                W.ak[0] = a0;
+                W.bk[0] = 0;
+            }
+            for (int p = p0; p < p1; ++p) {
+                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
+                Aff2<R> E = {(R)1 + (R)0.5 * Ac * r, (R)0.5 * Ac / r, -(R)0.5 * Ac * r * r * r,
+                             (R)1 - (R)0.5 * Ac * r, (R)0.25 * ((R)2 * Bc + Ac * Cc),
+                             (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r)};
+                F = OpAffThen()(F, E);
+                W.ak[p + 1] = F.m00 * a0 + F.c0;
+                W.bk[p + 1] = F.m10 * a0 + F.c1;
+            }
+        } else {
+            // regular solution R_k (R_0 = (1,0)) forward, decaying solution D_k
+            // (D_n = (0,1)) backward, then x_k = -G_k R_k + H_k D_k with the
+            // ring sources c_p = gamma_p R_{p+1} + delta_p D_{p+1},
+            // G_k = sum_{p>=k} gamma_p, H_k = sum_{p<k} delta_p.
+            const Mat2<R> I2 = {1, 0, 0, 1};
+            Mat2<R> Mf = I2, Mb = I2;
+            for (int p = p0; p < p1; ++p) {
+                R r = sR[p], hA = (R)0.5 * W.cA[p];
+                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
+                Mf = OpMatLeft()(Mf, M);
+            }
+            for (int p = p1 - 1; p >= p0; --p) {
+                R r = sR[p], hA = (R)0.5 * W.cA[p];
+                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};  // inverse (det 1)
+                Mb = OpMatLeft()(Mb, Mi);
+            }
+            Mat2<R> tf, tb;
+            Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
+            Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
+            if (tid == 0) {
+                W.Ra[0] = 1;
+                W.Rb[0] = 0;
+                W.Da[n] = 0;
+                W.Db[n] = 1;
+            }
+            for (int p = p0; p < p1; ++p) {
+                R r = sR[p], hA = (R)0.5 * W.cA[p];
+                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
+                Yf = OpMatLeft()(Yf, M);
+                W.Ra[p + 1] = Yf.m00;
+                W.Rb[p + 1] = Yf.m10;
+            }
+            A gl = zeroA, dl = zeroA;
+            for (int p = p1 - 1; p >= p0; --p) {
+                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
+                R hA = (R)0.5 * Ac;
+                R d0 = Yb.m01, d1 = Yb.m11;        // D_{p+1}
+                R q0 = W.Ra[p + 1], q1 = W.Rb[p + 1];  // R_{p+1}
+                R s0 = (R)0.25 * ((R)2 * Bc + Ac * Cc);
+                R s1 = (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r);
+                R wr = q0 * d1 - q1 * d0;
+                R gp = (s0 * d1 - s1 * d0) / wr;
+                R dp = (q0 * s1 - q1 * s0) / wr;
+                W.cB[p] = gp;  // reuse: gamma_p
+                W.cC[p] = dp;  // reuse: delta_p
+                gl = acc_add_r(gl, gp);
+                dl = acc_add_r(dl, dp);
+                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
+                Yb = OpMatLeft()(Yb, Mi);
+                W.Da[p] = Yb.m01;
+                W.Db[p] = Yb.m11;
+            }
+            Pair<A> gd_tot;
+            Pair<A> gd = block_excl_scan<false>(Pair<A>{gl, dl}, OpAddPair(), Pair<A>{zeroA, zeroA},
+                                                reinterpret_cast<Pair<A>*>(sscan), gd_tot);
+            // the scan's barriers order the R/D writes above before these reads
+            A Gex = gd.x, Hex = gd.y;
+            for (int p = p0; p < p1; ++p) {
+                R G = acc_to_r(acc_sub(gd_tot.x, Gex));
+                R H = acc_to_r(Hex);
+                W.ak[p] = -G * W.Ra[p] + H * W.Da[p];
+                W.bk[p] = -G * W.Rb[p] + H * W.Db[p];
+                Gex = acc_add_r(Gex, W.cB[p]);
+                Hex = acc_add_r(Hex, W.cC[p]);
+            }
+            if (tid == 0) {
+                R H = acc_to_r(gd_tot.y);
+                W.ak[n] = H * W.Da[n];
+                W.bk[n] = H * W.Db[n];
+            }
+        }
+        __syncthreads();
+
+        // ---------------- B^(p) at the rings, guard, dumps
+        bool bad = false;
+        for (int p = p0; p < p1; ++p) {
+            R r = sR[p];
+            R bpv = (R)0.5 * ((W.ak[p] + W.ak[p + 1]) * r + (W.bk[p] + W.bk[p + 1]) / r);
+            W.cA[p] = bpv;  // reuse: B^(p) at the ring
+            R pb = W.psib[p];
+            if (!(pb > (R)0) || !real_finite(pb) || !real_finite(W.dpr[p]) || !real_finite(W.tt[p]) ||
+                !real_finite(bpv) || !real_finite(W.bb[p]) || !real_finite(W.gam[p]))
+                bad = true;
+            if (mode == MODE_MARCH) {
+                int id = rid[p];
+                size_t row = (size_t)slice * n + id;
+                if (W.dump_r) W.dump_r[row] = r;
+                if (W.dump_ur) {
+                    W.dump_ur[row] = ur[p];
+                    W.dump_bp[row] = bpv;
+                    W.dump_bb[row] = W.bb[p];
+                }
+            }
+        }
+        bad = __syncthreads_or(bad);
+
+        // ---------------- a9: fields on beam particles (or query radii)
+        {
+            const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
+            for (int64_t q = tid; q < nq; q += T) {
+                R x;
+                if (mode == MODE_MARCH) x = staged ? beamR[q] : W.br[b0 + q];
+                else x = (R)W.rq[q];
+                R psi, dprv, dpz, bpv, bbv;
+                if (x > (R)0) {
+                    int k = lower_bound_dev(sR, n, x);
+                    A Sk = W.regS[k];
+                    psi = acc_to_r(acc_add(acc_add(W.regL[k], acc_mul_r(Sk, real_log(x))),
+                                           ion_psi(x, rmax, quarter_n, Imax, c0)));
+                    dprv = acc_to_r(acc_sub(Sk, ion_enclosed(x, rmax, half_n, Imax))) / x;
+                    dpz = -W.regT[k];
+                    bpv = W.ak[k] * x + W.bk[k] / x;
+                    if (mode == MODE_MARCH) {
+                        bbv = W.bQs[b0 + q] * inv_2pi_dxi / x;
+                    } else {
+                        bbv = 0;
+                        if (m > 0) {
+                            int lb = lower_bound_dev(beamR, m, x);
+                            R Q = lb < m ? W.bE[b0 + lb] : qtot;
+                            bbv = Q * inv_2pi_dxi / x;
+                        }
+                    }
+                } else {
+                    psi = acc_to_r(acc_add(W.regL[0], ion_psi((R)0, rmax, quarter_n, Imax, c0)));
+                    dprv = 0;
+                    dpz = -W.regT[0];
+                    bpv = 0;
+                    bbv = 0;
+                }
+                if (mode == MODE_MARCH) {
+                    int64_t o = b0 + q;
+                    W.out_ez[o] = -dpz;
+                    W.out_wr[o] = -dprv;
+                    W.out_bt[o] = bpv + bbv;
+                    W.out_psi[o] = psi;
+                } else {
+                    if (W.q_ez) W.q_ez[q] = -dpz;
+                    if (W.q_wr) W.q_wr[q] = -dprv;
+                    if (W.q_bt) W.q_bt[q] = bpv + bbv;
+                    if (W.q_psi) W.q_psi[q] = psi;
+                }
+            }
+        }
+        if (mode != MODE_MARCH) break;
+        if (bad) {
+            status = 4;
+            fail = slice;
+            ++slice;
+            break;
+        }
+
+        // ---------------- a10: AB2 push to the next slice
+        for (int p = p0; p < p1; ++p) {
+            R r = sR[p], u = ur[p];
+            R pb = W.psib[p];
+            R fr = u / pb;
+            R fu = W.gam[p] * W.dpr[p] / pb - (W.cA[p] + W.bb[p]);
+            R rn, un;
+            if (has_prev) {
+                rn = r + dxi * ((R)1.5 * fr - (R)0.5 * frho[p]);
+                un = u + dxi * ((R)1.5 * fu - (R)0.5 * fur[p]);
+            } else {
+                rn = r + dxi * fr;
+                un = u + dxi * fu;
+            }
+            if (rn < (R)0) {
+                rn = -rn;
+                un = -un;
+                fr = -fr;
+                fu = -fu;
+            }
+            rho[p] = rn;
+            ur[p] = un;
+            frho[p] = fr;
+            fur[p] = fu;
+        }
+        has_prev = 1;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
+        W.ctl[CTL_BUF] = buf;
+        W.ctl[CTL_PREV] = has_prev;
+        if (status) {
+            W.ctl[CTL_STATUS] = status;
+            W.ctl[CTL_FAIL] = fail;
+        }
+    }
+}
+
+}  // namespace gbwake

@@ -1,0 +1,20 @@
+// march.h -- host launchers of the ring kernels (march.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "march.cuh"
+
+namespace gbwake {
+template <class P>
+cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
+                         int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st);
+template <class R>
+cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* ur, R* frho,
+                             R* fur, int32_t* rid, cudaStream_t st);
+template <class R>
+cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_t n, cudaStream_t st);
+// shared memory of the march kernel for rings up to n_max with slices up to m_max
+// staged; returns the bytes and the staging capacity mb_cap
+size_t march_smem(int32_t n_max, int32_t n_pad_max, size_t real_bytes, int32_t m_max, int32_t* mb_cap);
+}  // namespace gbwake

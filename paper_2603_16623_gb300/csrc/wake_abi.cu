@@ -1,0 +1,632 @@
+// wake_abi.cu -- the C ABI of libwake.so (include/wake.h).
+//
+// Host side only: argument checks, device allocation owned by the handle,
+// kernel launches on the handle's stream, and copies to and from caller
+// buffers.  Every step of the solve itself runs in the kernels of march.cu
+// and beam.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wake.h"
+#include "beam.h"
+#include "march.h"
+
+using namespace gbwake;
+
+namespace {
+
+thread_local std::string g_err;
+
+wake_status fail(wake_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define WK_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(WAKE_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                                   \
+    } while (0)
+
+constexpr int32_t kMaxRings = 8192;
+constexpr int32_t kMaxSliceParticles = 8192;
+constexpr int32_t kDefaultThreads = 256;
+
+int32_t next_pow2(int32_t v) {
+    int32_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct wake_handle {
+    int32_t prec = WAKE_FP64;
+    int32_t n = 0, n_steps = 0, n_pad = 0, threads = kDefaultThreads, flags = 0;
+    double dxi = 0, density = 1, rho_max = 0;
+    cudaStream_t st = nullptr;
+    int64_t nb_total = 0;  // beam particles given by the caller
+    std::vector<void*> allocs;
+    std::vector<int64_t> beam_n;            // particles per species
+    std::vector<double> beam_q;             // charge sign per species
+    double *d_edges = nullptr, *d_xi = nullptr, *d_r = nullptr, *d_w = nullptr, *d_qw = nullptr;
+    int32_t *d_slot = nullptr, *d_cnt = nullptr, *d_fill = nullptr, *d_boff = nullptr, *d_dmax = nullptr;
+    void* d_desc = nullptr;                 // device WakeDev<P>
+    std::vector<unsigned char> desc_host;   // host copy of the descriptor
+    int32_t* d_ctl = nullptr;
+    int32_t* d_bidx = nullptr;
+    void* d_out[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* d_dump[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* d_rho[2] = {nullptr, nullptr};
+    void* d_ur[2] = {nullptr, nullptr};
+    int32_t* d_rid[2] = {nullptr, nullptr};
+    size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
+};
+
+namespace {
+
+wake_status dalloc(wake_handle* h, size_t bytes, void** out) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WAKE_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->allocs.push_back(p);
+    e = cudaMemsetAsync(p, 0, bytes, h->st);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+    *out = p;
+    return WAKE_OK;
+}
+
+template <class T>
+wake_status dalloc_t(wake_handle* h, size_t count, T** out) {
+    void* p = nullptr;
+    wake_status s = dalloc(h, count * sizeof(T), &p);
+    *out = static_cast<T*>(p);
+    return s;
+}
+
+void free_all(wake_handle* h) {
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+#define WK_TRY(expr)                      \
+    do {                                  \
+        wake_status s_ = (expr);          \
+        if (s_ != WAKE_OK) return s_;     \
+    } while (0)
+
+// Enqueues the a0/a1 preparation of a wake: control words, ring
+// initialisation, charge folding, nearest-slice binning and per-slice radial
+// sort of the (device-resident) beam, cleared outputs.  Asynchronous.
+template <class P>
+wake_status prepare_impl(wake_handle* h) {
+    using R = typename P::R;
+    WakeDev<P> D;
+    std::memcpy(&D, h->desc_host.data(), sizeof(D));
+    const int32_t n = h->n, ns = h->n_steps;
+    WK_CUDA(launch_reset_ctl(h->d_ctl, h->st));
+    WK_CUDA(launch_ring_init<R>(h->d_edges, n, h->density, const_cast<R*>(D.w), const_cast<R*>(D.wh), D.rho[0],
+                                D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->st));
+    const size_t rb = h->real_bytes();
+    WK_CUDA(cudaMemsetAsync(h->d_boff, 0, ((size_t)ns + 1) * sizeof(int32_t), h->st));
+    WK_CUDA(cudaMemsetAsync(const_cast<R*>(D.bTot), 0, (size_t)ns * rb, h->st));
+    if (h->nb_total > 0) {
+        int64_t off = 0;
+        for (size_t b = 0; b < h->beam_n.size(); ++b) {
+            WK_CUDA(launch_fold_charge(h->d_qw + off, h->d_w + off, h->beam_q[b], h->beam_n[b], h->st));
+            off += h->beam_n[b];
+        }
+        WK_CUDA(cudaMemsetAsync(h->d_cnt, 0, (size_t)ns * sizeof(int32_t), h->st));
+        WK_CUDA(cudaMemsetAsync(h->d_fill, 0, (size_t)ns * sizeof(int32_t), h->st));
+        WK_CUDA(launch_bin_count(h->d_xi, h->nb_total, h->dxi, ns, h->d_slot, h->d_cnt, h->st));
+        WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, h->st));
+        WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, h->d_boff, h->d_fill, h->d_bidx, h->st));
+        WK_CUDA(launch_slice_sort<R>(h->d_boff, ns, h->d_r, h->d_qw, h->d_bidx, const_cast<R*>(D.br),
+                                     const_cast<R*>(D.bE), const_cast<R*>(D.bQs), const_cast<R*>(D.bTot),
+                                     kMaxSliceParticles, h->d_ctl, h->st));
+        for (int k = 0; k < 4; ++k)
+            WK_CUDA(cudaMemsetAsync(h->d_out[k], 0, (size_t)h->nb_total * rb, h->st));
+    }
+    for (int k = 0; k < 7; ++k)
+        if (h->d_dump[k]) WK_CUDA(cudaMemsetAsync(h->d_dump[k], 0, (size_t)ns * n * rb, h->st));
+    return WAKE_OK;
+}
+
+template <class P>
+wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_desc* plasma,
+                      const wake_beam_desc* beams, int32_t n_beams) {
+    using R = typename P::R;
+    using A = typename P::A;
+    (void)cfg;
+    const int32_t n = h->n;
+    const int32_t ns = h->n_steps;
+    WakeDev<P> D;
+    std::memset(&D, 0, sizeof(D));
+    D.n = n;
+    D.n_steps = ns;
+    D.n_pad = h->n_pad;
+    D.dxi = h->dxi;
+    D.density = h->density;
+    D.rho_max = h->rho_max;
+
+    // plasma column and ring state
+    WK_TRY(dalloc_t(h, (size_t)n + 1, &h->d_edges));
+    WK_CUDA(cudaMemcpyAsync(h->d_edges, plasma->r_edges, ((size_t)n + 1) * sizeof(double),
+                            cudaMemcpyHostToDevice, h->st));
+    R *w, *wh;
+    WK_TRY(dalloc_t(h, n, &w));
+    WK_TRY(dalloc_t(h, n, &wh));
+    D.w = w;
+    D.wh = wh;
+    for (int b = 0; b < 2; ++b) {
+        WK_TRY(dalloc_t(h, n, &D.rho[b]));
+        WK_TRY(dalloc_t(h, n, &D.ur[b]));
+        WK_TRY(dalloc_t(h, n, &D.frho[b]));
+        WK_TRY(dalloc_t(h, n, &D.fur[b]));
+        WK_TRY(dalloc_t(h, n, &D.rid[b]));
+        h->d_rho[b] = D.rho[b];
+        h->d_ur[b] = D.ur[b];
+        h->d_rid[b] = D.rid[b];
+    }
+    R** scratch[] = {&D.bb, &D.psib, &D.gam, &D.dpr, &D.tt, &D.cA, &D.cB, &D.cC};
+    for (R** sp : scratch) WK_TRY(dalloc_t(h, n, sp));
+    WK_TRY(dalloc_t(h, (size_t)n + 1, &D.regS));
+    WK_TRY(dalloc_t(h, (size_t)n + 1, &D.regL));
+    R** regions[] = {&D.regT, &D.ak, &D.bk, &D.Ra, &D.Rb, &D.Da, &D.Db};
+    for (R** sp : regions) WK_TRY(dalloc_t(h, (size_t)n + 1, sp));
+    WK_TRY(dalloc_t(h, CTL_N, &D.ctl));
+    h->d_ctl = D.ctl;
+
+    // beam: device-resident raw inputs, binned arrays, outputs
+    int64_t nb = 0;
+    for (int32_t b = 0; b < n_beams; ++b) {
+        h->beam_n.push_back(beams[b].n);
+        h->beam_q.push_back(beams[b].q);
+        nb += beams[b].n;
+    }
+    h->nb_total = nb;
+    WK_TRY(dalloc_t(h, (size_t)ns + 1, &h->d_boff));
+    D.boff = h->d_boff;
+    R *bTot, *br, *bE, *bQs;
+    WK_TRY(dalloc_t(h, (size_t)ns, &bTot));
+    WK_TRY(dalloc_t(h, (size_t)nb, &br));
+    WK_TRY(dalloc_t(h, (size_t)nb, &bE));
+    WK_TRY(dalloc_t(h, (size_t)nb, &bQs));
+    D.bTot = bTot;
+    D.br = br;
+    D.bE = bE;
+    D.bQs = bQs;
+    if (nb > 0) {
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_xi));
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_r));
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_w));
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_qw));
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_slot));
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_bidx));
+        WK_TRY(dalloc_t(h, (size_t)ns, &h->d_cnt));
+        WK_TRY(dalloc_t(h, (size_t)ns, &h->d_fill));
+        WK_TRY(dalloc_t(h, 1, &h->d_dmax));
+        int64_t off = 0;
+        for (int32_t b = 0; b < n_beams; ++b) {
+            size_t bytes = beams[b].n * sizeof(double);
+            if (beams[b].n == 0) continue;
+            WK_CUDA(cudaMemcpyAsync(h->d_xi + off, beams[b].xi, bytes, cudaMemcpyHostToDevice, h->st));
+            WK_CUDA(cudaMemcpyAsync(h->d_r + off, beams[b].r, bytes, cudaMemcpyHostToDevice, h->st));
+            WK_CUDA(cudaMemcpyAsync(h->d_w + off, beams[b].w, bytes, cudaMemcpyHostToDevice, h->st));
+            off += beams[b].n;
+        }
+    }
+    D.nb = nb;
+    for (int k = 0; k < 4; ++k) {
+        R* o;
+        WK_TRY(dalloc_t(h, (size_t)nb, &o));
+        h->d_out[k] = o;
+    }
+    D.out_ez = (R*)h->d_out[0];
+    D.out_wr = (R*)h->d_out[1];
+    D.out_bt = (R*)h->d_out[2];
+    D.out_psi = (R*)h->d_out[3];
+    const size_t dump_n = (size_t)ns * n;
+    if (h->flags & (WAKE_DUMP_RING_R | WAKE_DUMP_RING_FIELDS)) {
+        WK_TRY(dalloc_t(h, dump_n, &D.dump_r));
+        h->d_dump[0] = D.dump_r;
+    }
+    if (h->flags & WAKE_DUMP_RING_FIELDS) {
+        R** dumps[] = {&D.dump_ur, &D.dump_psi, &D.dump_dpr, &D.dump_dpz, &D.dump_bp, &D.dump_bb};
+        for (int k = 0; k < 6; ++k) {
+            WK_TRY(dalloc_t(h, dump_n, dumps[k]));
+            h->d_dump[k + 1] = *dumps[k];
+        }
+    }
+    (void)sizeof(A);
+    h->desc_host.resize(sizeof(D));
+    std::memcpy(h->desc_host.data(), &D, sizeof(D));
+    WK_TRY(dalloc(h, sizeof(D), &h->d_desc));
+    WK_CUDA(cudaMemcpyAsync(h->d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, h->st));
+    WK_TRY(prepare_impl<P>(h));
+    int32_t ctl[CTL_N];
+    WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    if (ctl[CTL_STATUS] == WAKE_EINVAL)
+        return fail(WAKE_EINVAL, "slice %d holds more than %d beam particles; use a smaller dxi", ctl[CTL_FAIL],
+                    kMaxSliceParticles);
+    return WAKE_OK;
+}
+
+template <class P>
+wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
+    int32_t mb_cap = 0;
+    size_t smem = march_smem(h->n, h->n_pad, h->real_bytes(), kMaxSliceParticles, &mb_cap);
+    WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
+    return WAKE_OK;
+}
+
+wake_status check_handle(const wake_handle* h) {
+    if (!h) return fail(WAKE_EINVAL, "null handle");
+    return WAKE_OK;
+}
+
+template <class P>
+wake_status fields_at_impl(wake_handle* h, int64_t n, const double* r, void* ez, void* wr, void* bt, void* psi,
+                           int32_t device_ptrs) {
+    using R = typename P::R;
+    if (n == 0) return WAKE_OK;
+    WakeDev<P> D;
+    std::memcpy(&D, h->desc_host.data(), sizeof(D));
+    void* outs_user[4] = {ez, wr, bt, psi};
+    std::vector<void*> tmp;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->st);
+        for (void* p : tmp) cudaFree(p);
+    };
+    double* d_r = nullptr;
+    if (device_ptrs) {
+        d_r = const_cast<double*>(r);
+    } else {
+        if (cudaMalloc(&d_r, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(WAKE_ENOMEM, "query staging allocation failed");
+        }
+        tmp.push_back(d_r);
+        cudaMemcpyAsync(d_r, r, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+    }
+    R* d_out[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k) {
+        if (!outs_user[k]) continue;
+        if (device_ptrs) {
+            d_out[k] = static_cast<R*>(outs_user[k]);
+        } else {
+            if (cudaMalloc(&d_out[k], n * sizeof(R)) != cudaSuccess) {
+                cudaGetLastError();
+                cleanup();
+                return fail(WAKE_ENOMEM, "query output allocation failed");
+            }
+            tmp.push_back(d_out[k]);
+        }
+    }
+    D.nq = n;
+    D.rq = d_r;
+    D.q_ez = d_out[0];
+    D.q_wr = d_out[1];
+    D.q_bt = d_out[2];
+    D.q_psi = d_out[3];
+    void* d_desc = nullptr;
+    if (cudaMalloc(&d_desc, sizeof(D)) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(WAKE_ENOMEM, "query descriptor allocation failed");
+    }
+    tmp.push_back(d_desc);
+    cudaMemcpyAsync(d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, h->st);
+    wake_status s = launch_one<P>(h, static_cast<const WakeDev<P>*>(d_desc), 1, MODE_QUERY);
+    if (s == WAKE_OK && !device_ptrs) {
+        for (int k = 0; k < 4; ++k)
+            if (outs_user[k])
+                cudaMemcpyAsync(outs_user[k], d_out[k], n * sizeof(R), cudaMemcpyDeviceToHost, h->st);
+    }
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    cleanup();
+    if (s != WAKE_OK) return s;
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_fields_at: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
+template <class R>
+wake_status beam_fields_impl(wake_handle* h, void* const outs_user[4], int32_t device_ptrs) {
+    const int64_t nb = h->nb_total;
+    if (nb == 0) return WAKE_OK;
+    R* tmp = nullptr;
+    if (!device_ptrs) {
+        if (cudaMalloc(&tmp, nb * sizeof(R)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(WAKE_ENOMEM, "beam output staging allocation failed");
+        }
+    }
+    wake_status st = WAKE_OK;
+    for (int k = 0; k < 4 && st == WAKE_OK; ++k) {
+        if (!outs_user[k]) continue;
+        R* dst = device_ptrs ? static_cast<R*>(outs_user[k]) : tmp;
+        cudaError_t e = cudaMemsetAsync(dst, 0, nb * sizeof(R), h->st);
+        if (e == cudaSuccess)
+            e = launch_scatter_out<R>(h->d_bidx, h->d_boff + h->n_steps, nb, static_cast<const R*>(h->d_out[k]),
+                                      dst, h->st);
+        if (e == cudaSuccess && !device_ptrs)
+            e = cudaMemcpyAsync(outs_user[k], tmp, nb * sizeof(R), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess && !device_ptrs) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) st = fail(WAKE_ECUDA, "wake_get_beam_fields: %s", cudaGetErrorString(e));
+    }
+    if (tmp) {
+        cudaStreamSynchronize(h->st);
+        cudaFree(tmp);
+    }
+    return st;
+}
+
+template <class P>
+wake_status batch_impl(int32_t n, wake_handle* const* hs) {
+    cudaStream_t st = hs[0]->st;
+    std::vector<WakeDev<P>> descs(n);
+    std::vector<int32_t> order(n);
+    int32_t n_max = 0, pad_max = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        std::memcpy(&descs[i], hs[i]->desc_host.data(), sizeof(WakeDev<P>));
+        order[i] = i;
+        n_max = std::max(n_max, hs[i]->n);
+        pad_max = std::max(pad_max, hs[i]->n_pad);
+    }
+    // largest work first: blocks are dispatched roughly in index order
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (int64_t)hs[a]->n * hs[a]->n_steps > (int64_t)hs[b]->n * hs[b]->n_steps;
+    });
+    const size_t desc_bytes = sizeof(WakeDev<P>) * (size_t)n;
+    void* d_buf = nullptr;
+    WK_CUDA(cudaMallocAsync(&d_buf, desc_bytes + sizeof(int32_t) * (size_t)n, st));
+    WK_CUDA(cudaMemcpyAsync(d_buf, descs.data(), desc_bytes, cudaMemcpyHostToDevice, st));
+    int32_t* d_order = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_buf) + desc_bytes);
+    WK_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st));
+    int32_t mb_cap = 0;
+    size_t smem = march_smem(n_max, pad_max, hs[0]->real_bytes(), kMaxSliceParticles, &mb_cap);
+    cudaError_t e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
+                                    hs[0]->threads, smem, mb_cap, st);
+    cudaFreeAsync(d_buf, st);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wake_last_error(void) { return g_err.c_str(); }
+
+int32_t wake_max_rings(int32_t precision) {
+    (void)precision;
+    return kMaxRings;
+}
+
+int64_t wake_max_slice_particles(int32_t precision) {
+    (void)precision;
+    return kMaxSliceParticles;
+}
+
+wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, const wake_beam_desc* beams,
+                      int32_t n_beams, void* cuda_stream, wake_handle** out) {
+    if (!out) return fail(WAKE_EINVAL, "wake_init: out is NULL");
+    *out = nullptr;
+    if (!cfg || !plasma) return fail(WAKE_EINVAL, "wake_init: cfg and plasma are required");
+    if (cfg->precision != WAKE_FP64 && cfg->precision != WAKE_MIXED)
+        return fail(WAKE_EINVAL, "wake_init: unknown precision %d", cfg->precision);
+    if (!(cfg->dxi > 0.0) || !std::isfinite(cfg->dxi)) return fail(WAKE_EINVAL, "wake_init: dxi must be > 0");
+    if (cfg->n_steps < 1) return fail(WAKE_EINVAL, "wake_init: n_steps must be >= 1");
+    int32_t threads = cfg->block_threads ? cfg->block_threads : kDefaultThreads;
+    if (threads < 64 || threads > 512 || threads % 32)
+        return fail(WAKE_EINVAL, "wake_init: block_threads must be a multiple of 32 in [64, 512]");
+    const int32_t n = plasma->n_rings;
+    if (n < 1 || n > kMaxRings) return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]", kMaxRings);
+    if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");
+    if (!(plasma->density > 0.0) || !std::isfinite(plasma->density))
+        return fail(WAKE_EINVAL, "wake_init: density must be > 0");
+    if (plasma->r_edges[0] != 0.0) return fail(WAKE_EINVAL, "wake_init: r_edges[0] must be 0");
+    for (int32_t j = 0; j < n; ++j)
+        if (!(plasma->r_edges[j + 1] > plasma->r_edges[j]) || !std::isfinite(plasma->r_edges[j + 1]))
+            return fail(WAKE_EINVAL, "wake_init: r_edges must be finite and strictly increasing (index %d)", j + 1);
+    if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(WAKE_EINVAL, "wake_init: bad beams");
+    int64_t nb = 0;
+    for (int32_t b = 0; b < n_beams; ++b) {
+        if (beams[b].n < 0) return fail(WAKE_EINVAL, "wake_init: beam %d has n < 0", b);
+        if (beams[b].n > 0 && (!beams[b].xi || !beams[b].r || !beams[b].w))
+            return fail(WAKE_EINVAL, "wake_init: beam %d arrays are NULL", b);
+        for (int64_t k = 0; k < beams[b].n; ++k)
+            if (!(beams[b].r[k] >= 0.0) || !std::isfinite(beams[b].xi[k]) || !std::isfinite(beams[b].w[k]))
+                return fail(WAKE_EINVAL, "wake_init: beam %d particle %lld has r < 0 or non-finite data", b,
+                            (long long)k);
+        nb += beams[b].n;
+    }
+    if (nb > (int64_t)0x7fffffff) return fail(WAKE_EINVAL, "wake_init: more than 2^31-1 beam particles");
+
+    wake_handle* h = new wake_handle();
+    h->prec = cfg->precision;
+    h->n = n;
+    h->n_steps = cfg->n_steps;
+    h->n_pad = next_pow2(std::max(n, 2));
+    h->threads = threads;
+    h->flags = cfg->flags;
+    h->dxi = cfg->dxi;
+    h->density = plasma->density;
+    h->rho_max = plasma->r_edges[n];
+    h->st = static_cast<cudaStream_t>(cuda_stream);
+    wake_status s = h->prec == WAKE_FP64 ? init_impl<PrecF64>(h, cfg, plasma, beams, n_beams)
+                                         : init_impl<PrecMixed>(h, cfg, plasma, beams, n_beams);
+    if (s != WAKE_OK) {
+        std::string keep = g_err;
+        free_all(h);
+        delete h;
+        g_err = keep;
+        return s;
+    }
+    *out = h;
+    return WAKE_OK;
+}
+
+wake_status wake_reset(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams) {
+    WK_TRY(check_handle(h));
+    if (beams) {
+        if (n_beams != (int32_t)h->beam_n.size())
+            return fail(WAKE_EINVAL, "wake_reset: %d species given, %zu at init", n_beams, h->beam_n.size());
+        int64_t off = 0;
+        for (int32_t b = 0; b < n_beams; ++b) {
+            if (beams[b].n != h->beam_n[b])
+                return fail(WAKE_EINVAL, "wake_reset: species %d has %lld particles, %lld at init", b,
+                            (long long)beams[b].n, (long long)h->beam_n[b]);
+            if (beams[b].n > 0 && (!beams[b].xi || !beams[b].r || !beams[b].w))
+                return fail(WAKE_EINVAL, "wake_reset: species %d arrays are NULL", b);
+        }
+        for (int32_t b = 0; b < n_beams; ++b) {
+            size_t bytes = beams[b].n * sizeof(double);
+            if (beams[b].n == 0) continue;
+            WK_CUDA(cudaMemcpyAsync(h->d_xi + off, beams[b].xi, bytes, cudaMemcpyHostToDevice, h->st));
+            WK_CUDA(cudaMemcpyAsync(h->d_r + off, beams[b].r, bytes, cudaMemcpyHostToDevice, h->st));
+            WK_CUDA(cudaMemcpyAsync(h->d_w + off, beams[b].w, bytes, cudaMemcpyHostToDevice, h->st));
+            h->beam_q[b] = beams[b].q;
+            off += beams[b].n;
+        }
+    }
+    if (h->prec == WAKE_FP64) return prepare_impl<PrecF64>(h);
+    return prepare_impl<PrecMixed>(h);
+}
+
+wake_status wake_step_slices(wake_handle* h, int32_t n_slices) {
+    WK_TRY(check_handle(h));
+    if (n_slices < 0) return fail(WAKE_EINVAL, "wake_step_slices: n_slices < 0");
+    if (n_slices == 0) return WAKE_OK;
+    if (h->prec == WAKE_FP64)
+        return launch_one<PrecF64>(h, static_cast<const WakeDev<PrecF64>*>(h->d_desc), n_slices, MODE_MARCH);
+    return launch_one<PrecMixed>(h, static_cast<const WakeDev<PrecMixed>*>(h->d_desc), n_slices, MODE_MARCH);
+}
+
+wake_status wake_get_progress(wake_handle* h, int32_t* next_slice, int32_t* status, int32_t* fail_slice) {
+    WK_TRY(check_handle(h));
+    int32_t ctl[CTL_N];
+    WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    if (next_slice) *next_slice = ctl[CTL_NEXT];
+    if (status) *status = ctl[CTL_STATUS];
+    if (fail_slice) *fail_slice = ctl[CTL_FAIL];
+    return WAKE_OK;
+}
+
+wake_status wake_fields_at(wake_handle* h, int64_t n, const double* r, void* ez, void* wr, void* bt, void* psi,
+                           int32_t device_ptrs) {
+    WK_TRY(check_handle(h));
+    if (n < 0 || (n > 0 && !r)) return fail(WAKE_EINVAL, "wake_fields_at: bad query array");
+    int32_t next = 0, status = 0;
+    WK_TRY(wake_get_progress(h, &next, &status, nullptr));
+    if (status != 0) return fail(WAKE_ENONFINITE, "wake_fields_at: the wake stopped at a non-finite slice");
+    if (h->prec == WAKE_FP64) return fields_at_impl<PrecF64>(h, n, r, ez, wr, bt, psi, device_ptrs);
+    return fields_at_impl<PrecMixed>(h, n, r, ez, wr, bt, psi, device_ptrs);
+}
+
+wake_status wake_get_beam_fields(wake_handle* h, void* ez, void* wr, void* bt, void* psi, int32_t device_ptrs) {
+    WK_TRY(check_handle(h));
+    void* outs[4] = {ez, wr, bt, psi};
+    if (h->prec == WAKE_FP64) return beam_fields_impl<double>(h, outs, device_ptrs);
+    return beam_fields_impl<float>(h, outs, device_ptrs);
+}
+
+wake_status wake_run(wake_handle* h, void* beam_ez, void* beam_wr, void* ring_r) {
+    WK_TRY(check_handle(h));
+    WK_TRY(wake_step_slices(h, h->n_steps));
+    WK_TRY(wake_get_beam_fields(h, beam_ez, beam_wr, nullptr, nullptr, 0));
+    if (ring_r && h->d_dump[0])
+        WK_CUDA(cudaMemcpyAsync(ring_r, h->d_dump[0], (size_t)h->n_steps * h->n * h->real_bytes(),
+                                cudaMemcpyDeviceToHost, h->st));
+    int32_t status = 0;
+    WK_TRY(wake_get_progress(h, nullptr, &status, nullptr));
+    if (status != 0) return fail(WAKE_ENONFINITE, "wake_run: the wake stopped at a non-finite slice");
+    return WAKE_OK;
+}
+
+wake_status wake_batch_run(int32_t n, wake_handle* const* handles) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_run: bad handle array");
+    if (n == 0) return WAKE_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_run: handle %d is NULL", i);
+        if (handles[i]->prec != handles[0]->prec || handles[i]->st != handles[0]->st ||
+            handles[i]->threads != handles[0]->threads)
+            return fail(WAKE_EINVAL, "wake_batch_run: handles must share precision, stream and block_threads");
+    }
+    if (handles[0]->prec == WAKE_FP64) return batch_impl<PrecF64>(n, handles);
+    return batch_impl<PrecMixed>(n, handles);
+}
+
+wake_status wake_get_ring_state(wake_handle* h, void* rho, void* ur) {
+    WK_TRY(check_handle(h));
+    int32_t ctl[CTL_N];
+    WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    const int b = ctl[CTL_BUF];
+    const size_t rb = h->real_bytes();
+    void* tmp = nullptr;
+    if (cudaMalloc(&tmp, (size_t)h->n * rb) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WAKE_ENOMEM, "ring state staging allocation failed");
+    }
+    void* outs[2] = {rho, ur};
+    void* srcs[2] = {h->d_rho[b], h->d_ur[b]};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (!outs[k]) continue;
+        if (h->prec == WAKE_FP64)
+            e = launch_gather_by_id<double>(h->d_rid[b], (const double*)srcs[k], (double*)tmp, h->n, h->st);
+        else
+            e = launch_gather_by_id<float>(h->d_rid[b], (const float*)srcs[k], (float*)tmp, h->n, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(outs[k], tmp, (size_t)h->n * rb, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    }
+    cudaStreamSynchronize(h->st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_get_ring_state: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
+wake_status wake_get_ring_dumps(wake_handle* h, void* r, void* ur, void* psi, void* dpsidr, void* dpsidz, void* bp,
+                                void* bb) {
+    WK_TRY(check_handle(h));
+    void* outs[7] = {r, ur, psi, dpsidr, dpsidz, bp, bb};
+    const size_t bytes = (size_t)h->n_steps * h->n * h->real_bytes();
+    for (int k = 0; k < 7; ++k) {
+        if (!outs[k]) continue;
+        if (!h->d_dump[k]) return fail(WAKE_EINVAL, "wake_get_ring_dumps: dump %d was not requested at init", k);
+        WK_CUDA(cudaMemcpyAsync(outs[k], h->d_dump[k], bytes, cudaMemcpyDeviceToHost, h->st));
+    }
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    return WAKE_OK;
+}
+
+void wake_destroy(wake_handle* h) {
+    if (!h) return;
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+"""Python binding of libwake.so (include/wake.h): argument marshalling only.
+
+The functions keep the C names (wake_init, wake_step_slices, wake_fields_at,
+wake_get_beam_fields, wake_run, wake_batch_run, ...); `Wake` wraps a handle.
+Every step of the solve runs in the library's CUDA kernels: if the library
+cannot be loaded (not built, no CUDA runtime) the import of the handle-level
+API raises -- there is no CPU fallback.
+
+Host arrays are numpy; device arrays are torch CUDA tensors (their
+data_ptr() is passed with device_ptrs=1).  Outputs are float64 for
+precision "fp64" and float32 for "mixed".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENONFINITE, WAKE_ETIMEOUT, WAKE_EBUSY = range(7)
+WAKE_FP64, WAKE_MIXED = 0, 1
+WAKE_DUMP_RING_R, WAKE_DUMP_RING_FIELDS = 1, 2
+PRECISION = {"fp64": WAKE_FP64, "mixed": WAKE_MIXED}
+_STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "EBUSY"}
+
+
+class WakeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_dp = C.POINTER(C.c_double)
+
+
+class wake_plasma_desc(C.Structure):
+    _fields_ = [("n_rings", C.c_int32), ("r_edges", _dp), ("density", C.c_double)]
+
+
+class wake_beam_desc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("xi", _dp), ("r", _dp), ("w", _dp), ("q", C.c_double)]
+
+
+class wake_config(C.Structure):
+    _fields_ = [("dxi", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
+                ("flags", C.c_int32), ("block_threads", C.c_int32)]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "wake_init": ([C.POINTER(wake_config), C.POINTER(wake_plasma_desc), C.POINTER(wake_beam_desc), C.c_int32,
+                   _vp, C.POINTER(_vp)], C.c_int),
+    "wake_reset": ([_vp, C.POINTER(wake_beam_desc), C.c_int32], C.c_int),
+    "wake_step_slices": ([_vp, C.c_int32], C.c_int),
+    "wake_fields_at": ([_vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_int32], C.c_int),
+    "wake_get_beam_fields": ([_vp, _vp, _vp, _vp, _vp, C.c_int32], C.c_int),
+    "wake_run": ([_vp, _vp, _vp, _vp], C.c_int),
+    "wake_batch_run": ([C.c_int32, C.POINTER(_vp)], C.c_int),
+    "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+    "wake_get_ring_state": ([_vp, _vp, _vp], C.c_int),
+    "wake_get_ring_dumps": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "wake_destroy": ([_vp], None),
+    "wake_last_error": ([], C.c_char_p),
+    "wake_max_rings": ([C.c_int32], C.c_int32),
+    "wake_max_slice_particles": ([C.c_int32], C.c_int64),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libwake.so (building it first if needed).  Raises if it cannot
+    be loaded: the solver has no other implementation."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise OSError(f"{path} is missing; run python -m paper_2603_16623_gb300.build")
+            _build.build()
+        lib = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != WAKE_OK:
+        msg = load().wake_last_error()
+        raise WakeError(status, msg.decode() if msg else "")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Wake:
+    """One wake solve on the GPU (a wake_handle)."""
+
+    def __init__(self, edges, beams: Sequence = (), dxi: float = 0.01, n_steps: int = 1000,
+                 precision: str = "mixed", density: float = 1.0, flags: int = 0,
+                 block_threads: int = 0, stream=None):
+        lib = load()
+        self.precision = precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.edges = _f64(edges)
+        self.n_rings = self.edges.shape[0] - 1
+        self.n_steps = int(n_steps)
+        self._keep = [self.edges]
+        descs = (wake_beam_desc * max(1, len(beams)))()
+        self.n_beam = 0
+        for i, b in enumerate(beams):
+            xi, r, w = _f64(b.xi), _f64(b.r), _f64(b.w)
+            self._keep += [xi, r, w]
+            descs[i] = wake_beam_desc(xi.shape[0], _dptr(xi), _dptr(r), _dptr(w), float(b.q))
+            self.n_beam += xi.shape[0]
+        cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads))
+        plasma = wake_plasma_desc(self.n_rings, _dptr(self.edges), float(density))
+        if stream is None:
+            stream = _default_stream()
+        self.stream = stream
+        h = _vp()
+        _check(lib.wake_init(C.byref(cfg), C.byref(plasma), descs, len(beams), stream, C.byref(h)))
+        self.handle = h
+        self._keep = None
+
+    @classmethod
+    def from_workload(cls, wake, **kw) -> "Wake":
+        return cls(wake.edges, wake.beams, wake.dxi, wake.n_steps, density=wake.density, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().wake_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, beams: Optional[Sequence] = None):
+        """Back to slice 0 (a0/a1 redone on the device).  beams: None to keep
+        the device-resident beams, else a sequence of objects with xi, r, w, q
+        (numpy arrays, or pinned torch CPU tensors for asynchronous upload)."""
+        if beams is None:
+            _check(load().wake_reset(self.handle, None, 0))
+            return
+        descs = (wake_beam_desc * max(1, len(beams)))()
+        keep = []
+        for i, b in enumerate(beams):
+            ptrs = []
+            for a in (b.xi, b.r, b.w):
+                if hasattr(a, "data_ptr"):
+                    ptrs.append(C.cast(C.c_void_p(a.data_ptr()), _dp))
+                    n = a.numel()
+                else:
+                    a = _f64(a)
+                    keep.append(a)
+                    ptrs.append(_dptr(a))
+                    n = a.shape[0]
+            descs[i] = wake_beam_desc(n, ptrs[0], ptrs[1], ptrs[2], float(b.q))
+        _check(load().wake_reset(self.handle, descs, len(beams)))
+        self._reset_keep = keep
+
+    def step_slices(self, n: int):
+        _check(load().wake_step_slices(self.handle, int(n)))
+
+    def progress(self):
+        nxt, st, fl = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().wake_get_progress(self.handle, C.byref(nxt), C.byref(st), C.byref(fl)))
+        return nxt.value, st.value, fl.value
+
+    def fields_at(self, r) -> Dict[str, np.ndarray]:
+        """Fields at the current slice at host radii r (numpy)."""
+        r = _f64(r)
+        n = r.shape[0]
+        out = {k: np.zeros(n, dtype=self.dtype) for k in ("ez", "wr", "bt", "psi")}
+        _check(load().wake_fields_at(self.handle, n, r.ctypes.data, out["ez"].ctypes.data, out["wr"].ctypes.data,
+                                     out["bt"].ctypes.data, out["psi"].ctypes.data, 0))
+        return out
+
+    def fields_at_device(self, r_dev, outs: Dict[str, object]):
+        """Device variant: r_dev a float64 CUDA tensor, outs torch tensors."""
+        ptr = lambda k: outs[k].data_ptr() if k in outs and outs[k] is not None else None
+        _check(load().wake_fields_at(self.handle, r_dev.numel(), r_dev.data_ptr(), ptr("ez"), ptr("wr"),
+                                     ptr("bt"), ptr("psi"), 1))
+
+    def beam_fields(self, which: Iterable[str] = ("ez", "wr", "bt", "psi")) -> Dict[str, np.ndarray]:
+        which = list(which)
+        out = {k: np.zeros(self.n_beam, dtype=self.dtype) for k in which}
+        p = [out[k].ctypes.data if k in out else None for k in ("ez", "wr", "bt", "psi")]
+        _check(load().wake_get_beam_fields(self.handle, *p, 0))
+        return out
+
+    def beam_fields_device(self, outs: Dict[str, object]):
+        p = [outs[k].data_ptr() if k in outs and outs[k] is not None else None for k in ("ez", "wr", "bt", "psi")]
+        _check(load().wake_get_beam_fields(self.handle, *p, 1))
+
+    def run(self, ring_r: bool = False):
+        """Rest of the window; returns (status, ez, wr, ring_r or None)."""
+        ez = np.zeros(self.n_beam, dtype=self.dtype)
+        wr = np.zeros(self.n_beam, dtype=self.dtype)
+        rr = np.zeros((self.n_steps, self.n_rings), dtype=self.dtype) if ring_r else None
+        st = load().wake_run(self.handle, ez.ctypes.data, wr.ctypes.data, rr.ctypes.data if rr is not None else None)
+        if st not in (WAKE_OK, WAKE_ENONFINITE):
+            _check(st)
+        return st, ez, wr, rr
+
+    def ring_state(self):
+        rho = np.zeros(self.n_rings, dtype=self.dtype)
+        ur = np.zeros(self.n_rings, dtype=self.dtype)
+        _check(load().wake_get_ring_state(self.handle, rho.ctypes.data, ur.ctypes.data))
+        return rho, ur
+
+    def ring_dumps(self, which=("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb")) -> Dict[str, np.ndarray]:
+        keys = ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb")
+        out = {k: np.zeros((self.n_steps, self.n_rings), dtype=self.dtype) for k in which}
+        p = [out[k].ctypes.data if k in out else None for k in keys]
+        _check(load().wake_get_ring_dumps(self.handle, *p))
+        return out
+
+
+def wake_batch_run(wakes: List[Wake]):
+    """All wakes' remaining slices in one persistent launch."""
+    arr = (_vp * len(wakes))(*[w.handle for w in wakes])
+    _check(load().wake_batch_run(len(wakes), arr))
+
+
+def wake_max_rings(precision: str = "mixed") -> int:
+    return int(load().wake_max_rings(PRECISION[precision]))
+
+
+def wake_max_slice_particles(precision: str = "mixed") -> int:
+    return int(load().wake_max_slice_particles(PRECISION[precision]))

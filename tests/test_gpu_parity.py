@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (norm-wise per field: max |gpu - oracle| / max |oracle| over the
+compared array): 1e-10 for the FP64 path; 1e-5 for the mixed path on E_z and
+on ring radii over the first 1000 steps.  Sizes span several rings per
+thread and ragged tails (ring counts not multiples of the block size).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_16623_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2603_16623_gb300 import wake
+    wake.load()
+    yield
+
+
+def _wake_mod():
+    from paper_2603_16623_gb300 import wake
+    return wake
+
+
+def nerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / den) if den > 0 else float(np.max(np.abs(a - b)))
+
+
+def gpu_run(wk, precision, threads=0, dumps=True):
+    wm = _wake_mod()
+    flags = wm.WAKE_DUMP_RING_FIELDS if dumps else 0
+    g = wm.Wake.from_workload(wk, precision=precision, flags=flags, block_threads=threads)
+    st, _, _, _ = g.run()
+    out = {"status": st, "progress": g.progress(), "beam": g.beam_fields()}
+    if dumps:
+        out["rings"] = g.ring_dumps()
+    out["final"] = g.ring_state()
+    g.close()
+    return out
+
+
+def oracle_run(wk, dumps=True):
+    keys = ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb") if dumps else ()
+    return oracle.run_wake(wk, ring_dumps=keys)
+
+
+def axis_wake(n_rings=300, steps=800, dxi=0.01):
+    drv = W.gaussian_beam(60_000, 5.0, 0.15, 0.5, 2.0, seed=21)
+    return W.Wake("axis", W.edges_uniform(n_rings, 5.0), [drv], dxi, steps)
+
+
+# ---------------------------------------------------------------------------
+# FP64 path
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("threads", [64, 256, 512])
+def test_fp64_linear_wake_matches_oracle(threads):
+    wk = W.linear_wake()
+    ref = oracle_run(wk)
+    got = gpu_run(wk, "fp64", threads)
+    assert got["status"] == ref.status == 0
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+
+
+def test_fp64_ring_crossings_and_axis_reflection_match_oracle():
+    wk = axis_wake()
+    ref = oracle_run(wk)
+    assert ref.status == 0
+    crossed = np.any(np.diff(np.sign(ref.rings["ur"]), axis=0) != 0)
+    assert crossed
+    got = gpu_run(wk, "fp64", 128)
+    assert got["status"] == 0
+    for k in ("r", "ur", "psi", "dpsidz", "bp"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_fp64_blowout_workload_matches_oracle():
+    """The full blowout workload: 2000 refined rings, 4000 steps, driver and
+    witness."""
+    wk = W.blowout_wake()
+    ref = oracle_run(wk, dumps=False)
+    got = gpu_run(wk, "fp64", 256, dumps=False)
+    assert got["status"] == ref.status == 0
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+    assert nerr(got["final"][0], ref.final_r) < FP64_TOL
+
+
+def test_fp64_guard_stops_at_the_oracle_slice():
+    """A strong driver drives psibar through zero behind the first bubble:
+    both sides stop at the same slice."""
+    wk = W.batched_wake(3)
+    wk = W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, 1700)
+    ref = oracle_run(wk, dumps=False)
+    got = gpu_run(wk, "fp64", 256, dumps=False)
+    assert ref.status == 4
+    assert got["status"] == 4
+    assert got["progress"][2] == ref.fail_slice
+
+
+# ---------------------------------------------------------------------------
+# mixed path
+# ---------------------------------------------------------------------------
+def test_mixed_linear_wake_within_tolerance():
+    wk = W.linear_wake()
+    ref = oracle_run(wk)
+    got = gpu_run(wk, "mixed", 256)
+    assert got["status"] == 0
+    assert nerr(got["beam"]["ez"], ref.beam["ez"]) < MIXED_TOL
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    assert nerr(got["beam"]["wr"], ref.beam["wr"]) < MIXED_TOL
+
+
+def test_mixed_blowout_first_1000_steps_within_tolerance():
+    wk = W.blowout_wake()
+    wk = W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, 1000)
+    ref = oracle_run(wk)
+    got = gpu_run(wk, "mixed", 256)
+    assert got["status"] == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    assert nerr(got["beam"]["ez"], ref.beam["ez"]) < MIXED_TOL
+
+
+def test_mixed_ring_crossings_within_tolerance():
+    wk = axis_wake()
+    ref = oracle_run(wk)
+    got = gpu_run(wk, "mixed", 128)
+    assert got["status"] == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    assert nerr(got["beam"]["ez"], ref.beam["ez"]) < MIXED_TOL
+
+
+# ---------------------------------------------------------------------------
+# fields at arbitrary radii, resumability, batching, edge cases, errors
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", 2e-5)])
+def test_fields_at_matches_oracle_slice(precision, tol):
+    wm = _wake_mod()
+    wk = axis_wake(steps=400)
+    g = wm.Wake.from_workload(wk, precision=precision, block_threads=128)
+    g.step_slices(250)
+    rho, ur = g.ring_state()
+    slice_n = g.progress()[0]
+    assert slice_n == 250
+    rq = np.concatenate([[0.0, 1e-4], np.linspace(0.01, 6.0, 333), np.sort(rho)[:50] * (1 + 1e-3)])
+    got = g.fields_at(rq)
+    b = wk.beams[0]
+    s = np.floor(b.xi / wk.dxi + 0.5)
+    m = s == slice_n
+    _, _, w, wh = oracle.ring_init(wk.edges)
+    ref = oracle.slice_fields(rho.astype(np.float64), ur.astype(np.float64), w, wh, 1.0, 5.0,
+                              b.r[m], b.q * b.w[m], wk.dxi, rq=rq)
+    for k, rk in (("ez", "q_ez"), ("wr", "q_wr"), ("bt", "q_bt"), ("psi", "q_psi")):
+        assert nerr(got[k], ref[rk]) < tol, k
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_slices_is_resumable(precision):
+    wm = _wake_mod()
+    wk = axis_wake(steps=500)
+    a = wm.Wake.from_workload(wk, precision=precision)
+    a.step_slices(123)
+    a.step_slices(77)
+    a.step_slices(1000)
+    b = wm.Wake.from_workload(wk, precision=precision)
+    b.step_slices(500)
+    ra, rb = a.ring_state(), b.ring_state()
+    assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+    fa, fb = a.beam_fields(), b.beam_fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_launch_equals_alone(precision):
+    wm = _wake_mod()
+    wakes = []
+    for k, (n, steps, nb0) in enumerate([(700, 300, 2.0), (257, 450, 0.3), (1500, 200, 8.0), (64, 600, 1.0)]):
+        drv = W.gaussian_beam(20_000, nb0, 0.3, 0.6, 2.4, seed=50 + k)
+        wakes.append(W.Wake(f"b{k}", W.edges_uniform(n, 6.0), [drv], 0.01, steps))
+    alone = []
+    for wk in wakes:
+        g = wm.Wake.from_workload(wk, precision=precision)
+        g.step_slices(10 ** 6)
+        alone.append((g.beam_fields(), g.ring_state(), g.progress()))
+        g.close()
+    gs = [wm.Wake.from_workload(wk, precision=precision) for wk in wakes]
+    wm.wake_batch_run(gs)
+    for g, (bf, rs, pr) in zip(gs, alone):
+        assert g.progress() == pr
+        got = g.beam_fields()
+        for k in bf:
+            assert np.array_equal(got[k], bf[k]), k
+        st = g.ring_state()
+        assert np.array_equal(st[0], rs[0])
+        g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
+def test_edge_cases(precision, tol):
+    wm = _wake_mod()
+    # one ring; no beam; particles outside the window; one step
+    cases = [
+        W.Wake("one", W.edges_uniform(1, 2.0), [W.gaussian_beam(500, 0.5, 0.3, 0.5, 1.5, seed=3)], 0.02, 200),
+        W.Wake("nobeam", W.edges_uniform(37, 3.0), [], 0.02, 50),
+        W.Wake("outside", W.edges_uniform(33, 3.0), [W.gaussian_beam(300, 0.5, 0.3, 0.2, 40.0, seed=4)], 0.02, 20),
+        W.Wake("single", W.edges_uniform(100, 3.0), [W.gaussian_beam(900, 0.5, 0.3, 0.5, 0.0, seed=5)], 0.02, 1),
+    ]
+    for wk in cases:
+        ref = oracle_run(wk)
+        got = gpu_run(wk, precision)
+        assert got["status"] == ref.status == 0, wk.name
+        assert nerr(got["rings"]["r"], ref.rings["r"]) < tol, wk.name
+        if wk.n_beam:
+            for k in ("ez", "wr"):
+                if np.max(np.abs(ref.beam[k])) > 0:
+                    assert nerr(got["beam"][k], ref.beam[k]) < tol, (wk.name, k)
+                else:
+                    assert np.all(got["beam"][k] == 0), (wk.name, k)
+
+
+def test_invalid_arguments_are_rejected():
+    wm = _wake_mod()
+    with pytest.raises(wm.WakeError) as e:
+        wm.Wake(np.array([0.0, 1.0, 1.0]), [], 0.01, 10)
+    assert e.value.status == wm.WAKE_EINVAL
+    with pytest.raises(wm.WakeError):
+        wm.Wake(np.array([0.1, 1.0]), [], 0.01, 10)
+    with pytest.raises(wm.WakeError):
+        wm.Wake(W.edges_uniform(10, 1.0), [], -0.01, 10)
+    with pytest.raises(wm.WakeError):
+        wm.Wake(W.edges_uniform(wm.wake_max_rings() + 1, 1.0), [], 0.01, 10)
+    dense = W.Beam(xi=np.zeros(9000), r=np.linspace(0, 1, 9000), w=np.ones(9000))
+    with pytest.raises(wm.WakeError) as e:
+        wm.Wake(W.edges_uniform(10, 1.0), [dense], 0.01, 10)
+    assert e.value.status == wm.WAKE_EINVAL
