@@ -126,6 +126,21 @@ __device__ __forceinline__ Pair<T> shfl_up_t(Pair<T> v, int o) { return {shfl_up
 template <class T>
 __device__ __forceinline__ Pair<T> shfl_dn_t(Pair<T> v, int o) { return {shfl_dn_t(v.x, o), shfl_dn_t(v.y, o)}; }
 
+// two accumulators and an integer count scanned together
+template <class T>
+struct Trip {
+    T x, y;
+    int64_t c;
+};
+template <class T>
+__device__ __forceinline__ Trip<T> shfl_up_t(Trip<T> v, int o) {
+    return {shfl_up_t(v.x, o), shfl_up_t(v.y, o), shfl_up_t(v.c, o)};
+}
+template <class T>
+__device__ __forceinline__ Trip<T> shfl_dn_t(Trip<T> v, int o) {
+    return {shfl_dn_t(v.x, o), shfl_dn_t(v.y, o), shfl_dn_t(v.c, o)};
+}
+
 // 2x2 matrix and the affine map x -> M x + c
 template <class R>
 struct Mat2 {
@@ -166,6 +181,12 @@ struct OpAddPair {
     template <class T>
     __device__ __forceinline__ Pair<T> operator()(Pair<T> a, Pair<T> b) const {
         return {acc_add(a.x, b.x), acc_add(a.y, b.y)};
+    }
+};
+struct OpAddTrip {
+    template <class T>
+    __device__ __forceinline__ Trip<T> operator()(Trip<T> a, Trip<T> b) const {
+        return {acc_add(a.x, b.x), acc_add(a.y, b.y), a.c + b.c};
     }
 };
 // matrix product, later element on the left: result = b * a

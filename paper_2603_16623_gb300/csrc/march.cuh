@@ -36,6 +36,7 @@ struct WakeDev {
     const R* w;   // [n] by ring id
     const R* wh;  // [n] by ring id
     R* rho[2];
+    R* rho_lo;    // low part of rho (mixed path: rho = rho + rho_lo in float-float)
     R* ur[2];
     R* frho[2];
     R* fur[2];

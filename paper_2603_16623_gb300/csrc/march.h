@@ -4,14 +4,20 @@
 #include <stdint.h>
 
 #include "march.cuh"
+#include "march_fast.cuh"
 
 namespace gbwake {
 template <class P>
 cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
                          int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st);
+// the on-chip march (mixed precision, 8 rings per thread, <= 512 threads)
+constexpr int kFastK = 8;
+constexpr int kFastMaxThreads = 512;
+cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                              int32_t max_slices, int32_t mode, int32_t threads, cudaStream_t st);
 template <class R>
-cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* ur, R* frho,
-                             R* fur, int32_t* rid, cudaStream_t st);
+cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
+                             R* frho, R* fur, int32_t* rid, cudaStream_t st);
 template <class R>
 cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_t n, cudaStream_t st);
 // shared memory of the march kernel for rings up to n_max with slices up to m_max

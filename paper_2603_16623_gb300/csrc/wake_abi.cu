@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/wake.h"
@@ -74,6 +75,7 @@ struct wake_handle {
     void* d_rho[2] = {nullptr, nullptr};
     void* d_ur[2] = {nullptr, nullptr};
     int32_t* d_rid[2] = {nullptr, nullptr};
+    int32_t fast_threads = 0;               // > 0: the on-chip march serves this wake
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
 };
 
@@ -126,7 +128,7 @@ wake_status prepare_impl(wake_handle* h) {
     const int32_t n = h->n, ns = h->n_steps;
     WK_CUDA(launch_reset_ctl(h->d_ctl, h->st));
     WK_CUDA(launch_ring_init<R>(h->d_edges, n, h->density, const_cast<R*>(D.w), const_cast<R*>(D.wh), D.rho[0],
-                                D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->st));
+                                D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->st));
     const size_t rb = h->real_bytes();
     WK_CUDA(cudaMemsetAsync(h->d_boff, 0, ((size_t)ns + 1) * sizeof(int32_t), h->st));
     WK_CUDA(cudaMemsetAsync(const_cast<R*>(D.bTot), 0, (size_t)ns * rb, h->st));
@@ -188,6 +190,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         h->d_ur[b] = D.ur[b];
         h->d_rid[b] = D.rid[b];
     }
+    WK_TRY(dalloc_t(h, n, &D.rho_lo));
     R** scratch[] = {&D.bb, &D.psib, &D.gam, &D.dpr, &D.tt, &D.cA, &D.cB, &D.cC};
     for (R** sp : scratch) WK_TRY(dalloc_t(h, n, sp));
     WK_TRY(dalloc_t(h, (size_t)n + 1, &D.regS));
@@ -273,8 +276,28 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     return WAKE_OK;
 }
 
+int32_t fast_threads_for(int32_t prec, int32_t n) {
+    if (prec != WAKE_MIXED || n > kFastK * kFastMaxThreads) return 0;
+    int32_t t = (n + kFastK - 1) / kFastK;
+    t = ((t + 31) / 32) * 32;
+    return t < 32 ? 32 : t;
+}
+
+// auxiliary streams for concurrent batched launches of different block sizes
+cudaStream_t aux_stream(int i) {
+    static cudaStream_t pool[8] = {nullptr};
+    if (!pool[i]) cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking);
+    return pool[i];
+}
+
 template <class P>
 wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
+    if constexpr (std::is_same<P, PrecMixed>::value) {
+        if (h->fast_threads > 0) {
+            WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->st));
+            return WAKE_OK;
+        }
+    }
     int32_t mb_cap = 0;
     size_t smem = march_smem(h->n, h->n_pad, h->real_bytes(), kMaxSliceParticles, &mb_cap);
     WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
@@ -383,8 +406,8 @@ wake_status beam_fields_impl(wake_handle* h, void* const outs_user[4], int32_t d
 }
 
 template <class P>
-wake_status batch_impl(int32_t n, wake_handle* const* hs) {
-    cudaStream_t st = hs[0]->st;
+wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threads, cudaStream_t st) {
+    const int32_t n = (int32_t)hs.size();
     std::vector<WakeDev<P>> descs(n);
     std::vector<int32_t> order(n);
     int32_t n_max = 0, pad_max = 0;
@@ -404,13 +427,60 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
     WK_CUDA(cudaMemcpyAsync(d_buf, descs.data(), desc_bytes, cudaMemcpyHostToDevice, st));
     int32_t* d_order = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_buf) + desc_bytes);
     WK_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st));
+    cudaError_t e;
+    if constexpr (std::is_same<P, PrecMixed>::value) {
+        if (fast_threads > 0) {
+            e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
+                                  fast_threads, st);
+            cudaFreeAsync(d_buf, st);
+            if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
+            return WAKE_OK;
+        }
+    }
     int32_t mb_cap = 0;
     size_t smem = march_smem(n_max, pad_max, hs[0]->real_bytes(), kMaxSliceParticles, &mb_cap);
-    cudaError_t e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
-                                    hs[0]->threads, smem, mb_cap, st);
+    e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH, hs[0]->threads,
+                        smem, mb_cap, st);
     cudaFreeAsync(d_buf, st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
     return WAKE_OK;
+}
+
+template <class P>
+wake_status batch_impl(int32_t n, wake_handle* const* hs) {
+    cudaStream_t st = hs[0]->st;
+    // one bucket per kernel configuration, each on its own stream, ordered
+    // after the work already queued on the handles' stream and joined back
+    std::vector<int32_t> keys;
+    std::vector<std::vector<wake_handle*>> buckets;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t key = hs[i]->fast_threads;
+        auto it = std::find(keys.begin(), keys.end(), key);
+        if (it == keys.end()) {
+            keys.push_back(key);
+            buckets.emplace_back();
+            it = keys.end() - 1;
+        }
+        buckets[it - keys.begin()].push_back(hs[i]);
+    }
+    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], keys[0], st);
+    cudaEvent_t start;
+    WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    WK_CUDA(cudaEventRecord(start, st));
+    wake_status res = WAKE_OK;
+    for (size_t b = 0; b < buckets.size(); ++b) {
+        cudaStream_t as = aux_stream((int)(b % 8));
+        WK_CUDA(cudaStreamWaitEvent(as, start, 0));
+        wake_status r = batch_bucket<P>(buckets[b], keys[b], as);
+        if (r != WAKE_OK) res = r;
+        cudaEvent_t done;
+        WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        WK_CUDA(cudaEventRecord(done, as));
+        WK_CUDA(cudaStreamWaitEvent(st, done, 0));
+        cudaEventDestroy(done);
+    }
+    cudaEventDestroy(start);
+    return res;
 }
 
 }  // namespace
@@ -475,6 +545,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->density = plasma->density;
     h->rho_max = plasma->r_edges[n];
     h->st = static_cast<cudaStream_t>(cuda_stream);
+    h->fast_threads = fast_threads_for(h->prec, n);
     wake_status s = h->prec == WAKE_FP64 ? init_impl<PrecF64>(h, cfg, plasma, beams, n_beams)
                                          : init_impl<PrecMixed>(h, cfg, plasma, beams, n_beams);
     if (s != WAKE_OK) {
