@@ -161,10 +161,20 @@ wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
 wake_status wake_get_progress(wake_handle *h, int32_t *next_slice, int32_t *status,
                               int32_t *fail_slice);
 
-/* Ring state by ring index (synchronises): radii and radial momenta at the
-   current slice ("real" host arrays of n_rings, NULL = skip).  A cheap
-   checkpoint of a resumable solve. */
-wake_status wake_get_ring_state(wake_handle *h, void *rho, void *ur);
+/* Ring state by ring index (synchronises): radii, radial momenta and the
+   AB2 history (d rho/d xi and d u_r/d xi of the previous slice) at the
+   current slice, as double host arrays of n_rings (NULL = skip).  Together
+   with wake_get_progress this is a checkpoint of a resumable solve. */
+wake_status wake_get_ring_state(wake_handle *h, double *rho, double *ur, double *f_rho,
+                                double *f_ur);
+
+/* Restores a checkpoint: the wake continues from `slice` (0 <= slice <=
+   n_steps) with the given ring state by ring index (double host arrays of
+   n_rings; rho >= 0).  f_rho and f_ur are the AB2 history; pass both NULL
+   to start the next step with forward Euler.  Clears the stopped status.
+   Errors: EINVAL, ENOMEM, ECUDA. */
+wake_status wake_set_ring_state(wake_handle *h, int32_t slice, const double *rho, const double *ur,
+                                const double *f_rho, const double *f_ur);
 
 /* Dumps kept with WAKE_DUMP_RING_FIELDS, [n_steps][n_rings] by ring index,
    "real" host arrays (NULL = skip). */

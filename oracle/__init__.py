@@ -4,5 +4,5 @@ TEST INFRASTRUCTURE ONLY: used by tests/, by the smoke check and by the
 benchmark's CPU-baseline and reference legs.  The product library never
 imports it.
 """
-from .oracle import (OracleResult, build, ring_init, slice_fields, bp_shooting,  # noqa: F401
+from .oracle import (OracleResult, build, ring_init, slice_fields, bp_shooting, bp_solve,  # noqa: F401
                      run, run_wake, lib_path)

@@ -30,7 +30,7 @@ class _Problem(C.Structure):
 
 
 _RING_DUMPS = ["ring_r", "ring_ur", "ring_psi", "ring_dpsidr", "ring_dpsidz", "ring_bp",
-               "ring_bb", "ring_psibar", "ring_gamma", "ring_uz"]
+               "ring_bb", "ring_psibar", "ring_gamma", "ring_uz", "ring_frprev", "ring_fuprev"]
 
 
 class _Outputs(C.Structure):
@@ -82,6 +82,8 @@ def _lib():
         lib.orc_slice_fields.restype = C.c_int
         lib.orc_bp_shooting.argtypes = [C.c_int32, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.orc_bp_shooting.restype = C.c_int
+        lib.orc_bp_solve.argtypes = [C.c_int32, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_bp_solve.restype = C.c_int
         lib.orc_ring_init.argtypes = [C.c_int32, _dp, C.c_double, _dp, _dp, _dp, _dp]
         lib.orc_ring_init.restype = None
         _lib_handle = lib
@@ -116,6 +118,17 @@ def bp_shooting(rho, A, B, Cc):
     rc = _lib().orc_bp_shooting(n, _ptr(rho), _ptr(A), _ptr(B), _ptr(Cc), _ptr(a), _ptr(b))
     if rc:
         raise RuntimeError(f"orc_bp_shooting failed ({rc})")
+    return a, b
+
+
+def bp_solve(rho, A, B, Cc):
+    rho, A, B, Cc = (_f64(x) for x in (rho, A, B, Cc))
+    n = rho.shape[0]
+    a = np.empty(n + 1)
+    b = np.empty(n + 1)
+    rc = _lib().orc_bp_solve(n, _ptr(rho), _ptr(A), _ptr(B), _ptr(Cc), _ptr(a), _ptr(b))
+    if rc:
+        raise RuntimeError(f"orc_bp_solve failed ({rc})")
     return a, b
 
 
@@ -173,7 +186,8 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     """March the whole window (or its first max_slices slices).
 
     beam_fields: subset of ez, wr, bt, psi (per particle, caller order).
-    ring_dumps: subset of r, ur, psi, dpsidr, dpsidz, bp, bb, psibar, gamma, uz
+    ring_dumps: subset of r, ur, psi, dpsidr, dpsidz, bp, bb, psibar, gamma, uz,
+    frprev, fuprev
     ([slices, rings] by ring id, values at the start of each slice)."""
     edges = _f64(edges)
     bxi, br, bqw = _f64(beam_xi), _f64(beam_r), _f64(beam_qw)

@@ -220,6 +220,106 @@ int orc_bp_shooting(int32_t n, const double *rho, const double *A, const double 
     return ORC_OK;
 }
 
+/* Banded Gaussian elimination with partial pivoting (the textbook band LU,
+   e.g. Golub & Van Loan, Sec. 4.3): n unknowns, kl sub- and ku
+   super-diagonals; row r keeps columns [r - kl, r + ku + kl] (room for the
+   fill-in of row swaps) at ab[r * W + (c - r + kl)], W = 2 kl + ku + 1.
+   Solves in place: x returned in rhs.  Returns ORC_EINVAL if singular. */
+static int band_solve(int64_t n, int kl, int ku, double *ab, double *rhs)
+{
+    const int W = 2 * kl + ku + 1;
+#define AB(r, c) ab[(r) * W + ((c) - (r) + kl)]
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t last_r = k + kl < n - 1 ? k + kl : n - 1;
+        int64_t last_c = k + kl + ku < n - 1 ? k + kl + ku : n - 1;
+        int64_t p = k;
+        double best = fabs(AB(k, k));
+        for (int64_t r = k + 1; r <= last_r; ++r)
+            if (fabs(AB(r, k)) > best) {
+                best = fabs(AB(r, k));
+                p = r;
+            }
+        if (!(best > 0.0))
+            return ORC_EINVAL;
+        if (p != k) {
+            for (int64_t c = k; c <= last_c; ++c) {
+                double t = AB(k, c);
+                AB(k, c) = AB(p, c);
+                AB(p, c) = t;
+            }
+            double t = rhs[k];
+            rhs[k] = rhs[p];
+            rhs[p] = t;
+        }
+        for (int64_t r = k + 1; r <= last_r; ++r) {
+            double f = AB(r, k) / AB(k, k);
+            if (f == 0.0)
+                continue;
+            AB(r, k) = 0.0;
+            for (int64_t c = k + 1; c <= last_c; ++c)
+                AB(r, c) -= f * AB(k, c);
+            rhs[r] -= f * rhs[k];
+        }
+    }
+    for (int64_t k = n - 1; k >= 0; --k) {
+        int64_t last_c = k + kl + ku < n - 1 ? k + kl + ku : n - 1;
+        double sum = rhs[k];
+        for (int64_t c = k + 1; c <= last_c; ++c)
+            sum -= AB(k, c) * rhs[c];
+        rhs[k] = sum / AB(k, k);
+    }
+#undef AB
+    return ORC_OK;
+}
+
+/* Eq. ai_bi with b_0 = 0 and a_N = 0, solved directly as the linear system
+   it defines (unknowns a_0, b_0, ..., a_N, b_N; rows: b_0 = 0, the two rows
+   of Eq. ai_bi for each ring, a_N = 0) by banded elimination.  Same
+   solution as the App. A shooting, which amplifies rounding by the growth
+   of the homogeneous solution (~e^rho_max) and loses digits on wide
+   plasma columns. */
+int orc_bp_solve(int32_t n, const double *rho, const double *A, const double *B,
+                 const double *C, double *a, double *b)
+{
+    const int64_t m = 2 * (int64_t)n + 2;
+    const int kl = 2, ku = 1, W = 2 * kl + ku + 1;
+    double *ab = (double *)calloc((size_t)(m * W), sizeof(double));
+    double *x = (double *)calloc((size_t)m, sizeof(double));
+    if (!ab || !x) {
+        free(ab);
+        free(x);
+        return ORC_ENOMEM;
+    }
+#define SET(r, c, v) ab[(r) * W + ((c) - (r) + kl)] = (v)
+    SET(0, 1, 1.0);  /* b_0 = 0 */
+    for (int32_t i = 1; i <= n; ++i) {
+        double r = rho[i - 1], Ai = A[i - 1], Bi = B[i - 1], Ci = C[i - 1];
+        int64_t ra = 2 * (int64_t)i - 1, rb = 2 * (int64_t)i;
+        int64_t ca0 = 2 * (int64_t)(i - 1), cb0 = ca0 + 1, ca1 = ca0 + 2, cb1 = ca0 + 3;
+        /* a_i - (1 + A r/2) a_{i-1} - (A/(2r)) b_{i-1} = (2B + AC)/4 */
+        SET(ra, ca0, -(1.0 + 0.5 * Ai * r));
+        SET(ra, cb0, -(0.5 * Ai / r));
+        SET(ra, ca1, 1.0);
+        x[ra] = 0.25 * (2.0 * Bi + Ai * Ci);
+        /* b_i + (A r^3/2) a_{i-1} - (1 - A r/2) b_{i-1} = r (4C - 2Br - ACr)/4 */
+        SET(rb, ca0, 0.5 * Ai * r * r * r);
+        SET(rb, cb0, -(1.0 - 0.5 * Ai * r));
+        SET(rb, cb1, 1.0);
+        x[rb] = 0.25 * r * (4.0 * Ci - 2.0 * Bi * r - Ai * Ci * r);
+    }
+    SET(m - 1, m - 2, 1.0);  /* a_N = 0 */
+#undef SET
+    int rc = band_solve(m, kl, ku, ab, x);
+    if (!rc)
+        for (int32_t k = 0; k <= n; ++k) {
+            a[k] = x[2 * k];
+            b[k] = x[2 * k + 1];
+        }
+    free(ab);
+    free(x);
+    return rc;
+}
+
 /* ---------------------------------------------------------------------- */
 /* one slice                                                               */
 /* ---------------------------------------------------------------------- */
@@ -348,12 +448,13 @@ static int slice_core(slice_ws *s, int32_t *order, const double *rho_id,
                   - wr * u * dpz / (pb * pb);
         s->C[i] = -wr * (g / pb - 1.0 - u * u / (pb * pb));
     }
-    /* B_theta^(p): App. A shooting, then the field at each ring.  B^(p) jumps
-       across a ring (the C_i term makes rho B jump by C_i rho_i); the matrix
-       and source vector of Eq. ai_bi follow from the jump conditions exactly
-       when the ring sees the mean of the two one-sided values, which is the
-       value used for the ring itself. */
-    int rc = orc_bp_shooting(n, s->r, s->A, s->B, s->C, s->a, s->b);
+    /* B_theta^(p): the system of Eq. ai_bi with its two boundary conditions
+       (orc_bp_solve), then the field at each ring.  B^(p) jumps across a ring
+       (the C_i term makes rho B jump by C_i rho_i); the matrix and source
+       vector of Eq. ai_bi follow from the jump conditions exactly when the
+       ring sees the mean of the two one-sided values, which is the value
+       used for the ring itself. */
+    int rc = orc_bp_solve(n, s->r, s->A, s->B, s->C, s->a, s->b);
     if (rc)
         return rc;
     for (int32_t i = 0; i < n; ++i) {
@@ -575,6 +676,8 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
             if (out->ring_psibar) out->ring_psibar[row + id] = s.psib[i];
             if (out->ring_gamma) out->ring_gamma[row + id] = s.gam[i];
             if (out->ring_uz) out->ring_uz[row + id] = s.uz[i];
+            if (out->ring_frprev) out->ring_frprev[row + id] = have_prev ? fr_prev[id] : 0.0;
+            if (out->ring_fuprev) out->ring_fuprev[row + id] = have_prev ? fu_prev[id] : 0.0;
         }
         /* fields on the beam particles of this slice */
         for (int64_t q = 0; q < bs.m; ++q) {

@@ -41,6 +41,9 @@ typedef struct {
        start of the slice (before the push). */
     double *ring_r, *ring_ur, *ring_psi, *ring_dpsidr, *ring_dpsidz, *ring_bp,
            *ring_bb, *ring_psibar, *ring_gamma, *ring_uz;
+    /* AB2 history at the start of each slice (the previous slice's
+       d rho/dxi and d u_r/dxi; 0 at slice 0), [n_steps][n_rings] by id */
+    double *ring_frprev, *ring_fuprev;
     /* ring state by id after the last slice run (NULL: skip) */
     double *final_r, *final_ur;
     int32_t status;       /* ORC_OK or ORC_ENONFINITE */
@@ -75,6 +78,12 @@ int orc_slice_fields(int32_t n, const double *rho, const double *ur,
    radius order (rho[0] < ... < rho[n-1]); returns a[0..n], b[0..n]. */
 int orc_bp_shooting(int32_t n, const double *rho, const double *A, const double *B,
                     const double *C, double *a, double *b);
+
+/* The same system solved directly (banded elimination with partial
+   pivoting); this is what the oracle's slices use: it stays accurate on wide
+   plasma columns where the shooting loses digits to the growing mode. */
+int orc_bp_solve(int32_t n, const double *rho, const double *A, const double *B,
+                 const double *C, double *a, double *b);
 
 /* Whole window (or its first max_slices slices when max_slices > 0). */
 int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out);

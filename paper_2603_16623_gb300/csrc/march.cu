@@ -30,6 +30,76 @@ __global__ void gather_by_id_kernel(const int32_t* __restrict__ rid, const R* __
     for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) dst[rid[p]] = src[p];
 }
 
+// checkpoint export: sorted state -> double arrays by ring id
+template <class R>
+__global__ void export_state_kernel(const int32_t* __restrict__ rid, const R* __restrict__ rho,
+                                    const R* __restrict__ rho_lo, const R* __restrict__ ur,
+                                    const R* __restrict__ frho, const R* __restrict__ fur, int32_t n,
+                                    double* o_rho, double* o_ur, double* o_fr, double* o_fu) {
+    for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        int32_t id = rid[p];
+        if (o_rho) o_rho[id] = (double)rho[p] + (rho_lo ? (double)rho_lo[p] : 0.0);
+        if (o_ur) o_ur[id] = (double)ur[p];
+        if (o_fr) o_fr[id] = (double)frho[p];
+        if (o_fu) o_fu[id] = (double)fur[p];
+    }
+}
+
+// checkpoint import: double arrays by ring id -> state in id order (buffer 0)
+template <class R>
+__global__ void import_state_kernel(const double* __restrict__ i_rho, const double* __restrict__ i_ur,
+                                    const double* __restrict__ i_fr, const double* __restrict__ i_fu, int32_t n,
+                                    R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, int32_t* ctl,
+                                    int32_t slice) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        R hi = (R)i_rho[j];
+        rho[j] = hi;
+        rho_lo[j] = (R)(i_rho[j] - (double)hi);
+        ur[j] = (R)i_ur[j];
+        frho[j] = i_fr ? (R)i_fr[j] : (R)0;
+        fur[j] = i_fu ? (R)i_fu[j] : (R)0;
+        rid[j] = j;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < CTL_N) {
+        int v = 0;
+        if (threadIdx.x == CTL_NEXT) v = slice;
+        if (threadIdx.x == CTL_FAIL) v = -1;
+        if (threadIdx.x == CTL_PREV) v = i_fr != nullptr;
+        ctl[threadIdx.x] = v;
+    }
+}
+
+template <class R>
+cudaError_t launch_export_state(const int32_t* rid, const R* rho, const R* rho_lo, const R* ur, const R* frho,
+                                const R* fur, int32_t n, double* o_rho, double* o_ur, double* o_fr, double* o_fu,
+                                cudaStream_t st) {
+    export_state_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(rid, rho, rho_lo, ur, frho, fur, n, o_rho, o_ur, o_fr,
+                                                           o_fu);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_import_state(const double* i_rho, const double* i_ur, const double* i_fr, const double* i_fu,
+                                int32_t n, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, int32_t* ctl,
+                                int32_t slice, cudaStream_t st) {
+    import_state_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(i_rho, i_ur, i_fr, i_fu, n, rho, rho_lo, ur, frho, fur,
+                                                           rid, ctl, slice);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_export_state<double>(const int32_t*, const double*, const double*, const double*,
+                                                 const double*, const double*, int32_t, double*, double*, double*,
+                                                 double*, cudaStream_t);
+template cudaError_t launch_export_state<float>(const int32_t*, const float*, const float*, const float*,
+                                                const float*, const float*, int32_t, double*, double*, double*,
+                                                double*, cudaStream_t);
+template cudaError_t launch_import_state<double>(const double*, const double*, const double*, const double*, int32_t,
+                                                 double*, double*, double*, double*, double*, int32_t*, int32_t*,
+                                                 int32_t, cudaStream_t);
+template cudaError_t launch_import_state<float>(const double*, const double*, const double*, const double*, int32_t,
+                                                float*, float*, float*, float*, float*, int32_t*, int32_t*, int32_t,
+                                                cudaStream_t);
+
 size_t march_smem(int32_t n_max, int32_t n_pad_max, size_t real_bytes, int32_t m_max, int32_t* mb_cap) {
     const int32_t kStageTarget = 8192;
     int32_t mb = m_max < kStageTarget ? m_max : kStageTarget;

@@ -20,6 +20,14 @@ cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* 
                              R* frho, R* fur, int32_t* rid, cudaStream_t st);
 template <class R>
 cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_t n, cudaStream_t st);
+template <class R>
+cudaError_t launch_export_state(const int32_t* rid, const R* rho, const R* rho_lo, const R* ur, const R* frho,
+                                const R* fur, int32_t n, double* o_rho, double* o_ur, double* o_fr, double* o_fu,
+                                cudaStream_t st);
+template <class R>
+cudaError_t launch_import_state(const double* i_rho, const double* i_ur, const double* i_fr, const double* i_fu,
+                                int32_t n, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, int32_t* ctl,
+                                int32_t slice, cudaStream_t st);
 // shared memory of the march kernel for rings up to n_max with slices up to m_max
 // staged; returns the bytes and the staging capacity mb_cap
 size_t march_smem(int32_t n_max, int32_t n_pad_max, size_t real_bytes, int32_t m_max, int32_t* mb_cap);

@@ -483,6 +483,46 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
     return res;
 }
 
+template <class P>
+wake_status state_io(wake_handle* h, bool export_, int32_t slice, double* rho, double* ur, double* fr, double* fu,
+                     const double* irho, const double* iur, const double* ifr, const double* ifu) {
+    using R = typename P::R;
+    WakeDev<P> D;
+    std::memcpy(&D, h->desc_host.data(), sizeof(D));
+    const size_t bytes = (size_t)h->n * sizeof(double);
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, 4 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WAKE_ENOMEM, "ring state staging allocation failed");
+    }
+    double* t[4] = {tmp, tmp + h->n, tmp + 2 * h->n, tmp + 3 * h->n};
+    cudaError_t e = cudaSuccess;
+    if (export_) {
+        int32_t ctl[CTL_N];
+        e = cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        const int b = ctl[CTL_BUF];
+        double* outs[4] = {rho, ur, fr, fu};
+        if (e == cudaSuccess)
+            e = launch_export_state<R>(D.rid[b], D.rho[b], h->fast_threads > 0 ? D.rho_lo : nullptr, D.ur[b],
+                                       D.frho[b], D.fur[b], h->n, t[0], t[1], t[2], t[3], h->st);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            if (outs[k]) e = cudaMemcpyAsync(outs[k], t[k], bytes, cudaMemcpyDeviceToHost, h->st);
+    } else {
+        const double* ins[4] = {irho, iur, ifr, ifu};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            if (ins[k]) e = cudaMemcpyAsync(t[k], ins[k], bytes, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess)
+            e = launch_import_state<R>(t[0], t[1], ifr ? t[2] : nullptr, ifu ? t[3] : nullptr, h->n, D.rho[0],
+                                       D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->d_ctl, slice, h->st);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(h->st);
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "ring state transfer: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -650,34 +690,26 @@ wake_status wake_batch_run(int32_t n, wake_handle* const* handles) {
     return batch_impl<PrecMixed>(n, handles);
 }
 
-wake_status wake_get_ring_state(wake_handle* h, void* rho, void* ur) {
+wake_status wake_get_ring_state(wake_handle* h, double* rho, double* ur, double* f_rho, double* f_ur) {
     WK_TRY(check_handle(h));
-    int32_t ctl[CTL_N];
-    WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
-    WK_CUDA(cudaStreamSynchronize(h->st));
-    const int b = ctl[CTL_BUF];
-    const size_t rb = h->real_bytes();
-    void* tmp = nullptr;
-    if (cudaMalloc(&tmp, (size_t)h->n * rb) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(WAKE_ENOMEM, "ring state staging allocation failed");
-    }
-    void* outs[2] = {rho, ur};
-    void* srcs[2] = {h->d_rho[b], h->d_ur[b]};
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        if (!outs[k]) continue;
-        if (h->prec == WAKE_FP64)
-            e = launch_gather_by_id<double>(h->d_rid[b], (const double*)srcs[k], (double*)tmp, h->n, h->st);
-        else
-            e = launch_gather_by_id<float>(h->d_rid[b], (const float*)srcs[k], (float*)tmp, h->n, h->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(outs[k], tmp, (size_t)h->n * rb, cudaMemcpyDeviceToHost, h->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    }
-    cudaStreamSynchronize(h->st);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_get_ring_state: %s", cudaGetErrorString(e));
-    return WAKE_OK;
+    if (h->prec == WAKE_FP64)
+        return state_io<PrecF64>(h, true, 0, rho, ur, f_rho, f_ur, nullptr, nullptr, nullptr, nullptr);
+    return state_io<PrecMixed>(h, true, 0, rho, ur, f_rho, f_ur, nullptr, nullptr, nullptr, nullptr);
+}
+
+wake_status wake_set_ring_state(wake_handle* h, int32_t slice, const double* rho, const double* ur,
+                                const double* f_rho, const double* f_ur) {
+    WK_TRY(check_handle(h));
+    if (slice < 0 || slice > h->n_steps) return fail(WAKE_EINVAL, "wake_set_ring_state: slice out of range");
+    if (!rho || !ur) return fail(WAKE_EINVAL, "wake_set_ring_state: rho and ur are required");
+    if ((f_rho == nullptr) != (f_ur == nullptr))
+        return fail(WAKE_EINVAL, "wake_set_ring_state: give both AB2 history arrays or neither");
+    for (int32_t j = 0; j < h->n; ++j)
+        if (!(rho[j] >= 0.0) || !std::isfinite(rho[j]) || !std::isfinite(ur[j]))
+            return fail(WAKE_EINVAL, "wake_set_ring_state: ring %d has rho < 0 or non-finite state", j);
+    if (h->prec == WAKE_FP64)
+        return state_io<PrecF64>(h, false, slice, nullptr, nullptr, nullptr, nullptr, rho, ur, f_rho, f_ur);
+    return state_io<PrecMixed>(h, false, slice, nullptr, nullptr, nullptr, nullptr, rho, ur, f_rho, f_ur);
 }
 
 wake_status wake_get_ring_dumps(wake_handle* h, void* r, void* ur, void* psi, void* dpsidr, void* dpsidz, void* bp,

@@ -60,7 +60,8 @@ _SIGS = {
     "wake_run": ([_vp, _vp, _vp, _vp], C.c_int),
     "wake_batch_run": ([C.c_int32, C.POINTER(_vp)], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
-    "wake_get_ring_state": ([_vp, _vp, _vp], C.c_int),
+    "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
+    "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "wake_get_ring_dumps": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_destroy": ([_vp], None),
     "wake_last_error": ([], C.c_char_p),
@@ -231,11 +232,21 @@ class Wake:
             _check(st)
         return st, ez, wr, rr
 
-    def ring_state(self):
-        rho = np.zeros(self.n_rings, dtype=self.dtype)
-        ur = np.zeros(self.n_rings, dtype=self.dtype)
-        _check(load().wake_get_ring_state(self.handle, rho.ctypes.data, ur.ctypes.data))
-        return rho, ur
+    def ring_state(self, history: bool = False):
+        """(rho, u_r) by ring index as float64; with history=True also the AB2
+        history (f_rho, f_u)."""
+        arrs = [np.zeros(self.n_rings) for _ in range(4)]
+        _check(load().wake_get_ring_state(self.handle, *[a.ctypes.data for a in arrs]))
+        return tuple(arrs) if history else (arrs[0], arrs[1])
+
+    def set_ring_state(self, slice_: int, rho, ur, f_rho=None, f_ur=None):
+        """Restore a checkpoint: continue from slice_ with this ring state."""
+        rho, ur = _f64(rho), _f64(ur)
+        fr = _f64(f_rho) if f_rho is not None else None
+        fu = _f64(f_ur) if f_ur is not None else None
+        _check(load().wake_set_ring_state(self.handle, int(slice_), rho.ctypes.data, ur.ctypes.data,
+                                          fr.ctypes.data if fr is not None else None,
+                                          fu.ctypes.data if fu is not None else None))
 
     def ring_dumps(self, which=("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb")) -> Dict[str, np.ndarray]:
         keys = ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb")

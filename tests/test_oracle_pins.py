@@ -237,6 +237,45 @@ def test_bp_shooting_matches_dense_jump_solve(seed):
     assert np.max(np.abs(b - bd)) < 1e-10 * scale
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bp_banded_solve_matches_dense_jump_solve(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = 30
+    rho = np.sort(rng.uniform(0.05, 3.0, n))
+    A = rng.uniform(0.0, 0.2, n)
+    B = rng.normal(0.0, 0.1, n)
+    C = rng.normal(0.0, 0.05, n)
+    a, b = oracle.bp_solve(rho, A, B, C)
+    ad, bd = _jump_system(rho, A, B, C)
+    scale = max(np.abs(ad).max(), np.abs(bd).max())
+    assert np.max(np.abs(a - ad)) < 1e-12 * scale
+    assert np.max(np.abs(b - bd)) < 1e-12 * scale
+    g = json.load(open(os.path.join(GOLDEN, "one_ring_bp.json")))
+    a1, b1 = oracle.bp_solve(g["rho"], g["A"], g["B"], g["C"])
+    assert np.allclose(a1, g["a"], rtol=1e-14, atol=1e-16) and np.allclose(b1, g["b"], rtol=1e-14, atol=1e-16)
+
+
+def test_shooting_loses_digits_on_wide_columns_banded_solve_does_not():
+    """Uniform column of 400 rings out to rho_max = 30 at rest-like
+    coefficients (A = w/rho): the homogeneous solution grows ~e^30, so the
+    App. A shooting error is ~1e-16 x 1e13 while the banded solve keeps the
+    dense solve's accuracy."""
+    edges = W.edges_uniform(120, 30.0)
+    rho0, _, w, _ = oracle.ring_init(edges)
+    A = w / rho0
+    rng = np.random.Generator(np.random.PCG64(4))
+    B = 1e-3 * rng.normal(size=rho0.shape[0]) * np.exp(-rho0)
+    C = np.zeros_like(rho0)
+    ad, bd = _jump_system(rho0, A, B, C)
+    scale = np.max(np.abs(ad * rho0.max()))
+    a_b, b_b = oracle.bp_solve(rho0, A, B, C)
+    a_s, b_s = oracle.bp_shooting(rho0, A, B, C)
+    err_band = np.max(np.abs(a_b - ad)) / scale
+    err_shoot = np.max(np.abs(a_s - ad)) / scale
+    assert err_band < 1e-10
+    assert err_shoot > 1e3 * err_band
+
+
 def test_slice_bp_satisfies_jump_and_boundary_conditions():
     edges, rho, ur, w, wh = _random_state(n=50, seed=4, u_scale=0.5)
     sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1])
