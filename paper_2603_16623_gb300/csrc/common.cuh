@@ -36,6 +36,13 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
     s.lo = __fadd_rn(s.lo, t.lo);
     return ff_fast_two_sum(s.hi, s.lo);
 }
+// Accumulation add ("sloppy" float-float add): the error stays ~2^-46 of
+// |a| + |b|; used where a running sum meets one more term.
+__device__ __forceinline__ ff ff_acc(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return ff_fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 __device__ __forceinline__ ff ff_add_f(ff a, float b) {
@@ -46,6 +53,13 @@ __device__ __forceinline__ ff ff_add_f(ff a, float b) {
 __device__ __forceinline__ ff ff_two_prod(float a, float b) {
     float p = __fmul_rn(a, b);
     return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_fast_two_sum(p, e);
 }
 __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
     float p = __fmul_rn(a.hi, b);
@@ -68,12 +82,10 @@ __device__ __forceinline__ ff ff_from_d(double d) {
 struct PrecF64 {
     using R = double;
     using A = double;
-    static constexpr bool kShooting = true;
 };
 struct PrecMixed {
     using R = float;
     using A = ff;
-    static constexpr bool kShooting = false;
 };
 
 // accumulator helpers, overloaded on the accumulator type
@@ -81,7 +93,9 @@ __device__ __forceinline__ double acc_zero(double) { return 0.0; }
 __device__ __forceinline__ ff acc_zero(ff) { return {0.f, 0.f}; }
 __device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
 __device__ __forceinline__ int64_t acc_add(int64_t a, int64_t b) { return a + b; }
-__device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }
+// accumulations and scans of float-float values use the accumulation add
+// (its error stays ~2^-46 of the operands' magnitudes)
+__device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_acc(a, b); }
 __device__ __forceinline__ double acc_sub(double a, double b) { return a - b; }
 __device__ __forceinline__ ff acc_sub(ff a, ff b) { return ff_sub(a, b); }
 __device__ __forceinline__ double acc_add_r(double a, double b) { return a + b; }
@@ -250,6 +264,84 @@ __device__ T block_excl_scan(T v, Op op, T ident, T* sbuf, T& total) {
     total = sbuf[32];
     __syncthreads();
     return res;
+}
+
+// One pass of two sums in opposite directions: fx scanned from thread 0 up,
+// ry from the last thread down (same barriers as one scan).  Returns the
+// exclusive forward sum of fx and the exclusive reverse (suffix) sum of ry;
+// totals in tx, ty.  sbuf holds 33 Pair<T>.
+template <class T>
+__device__ Pair<T> block_excl_scan_fwd_rev(T fx, T ry, T zero, Pair<T>* sbuf, T& tx, T& ty) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    T ix = warp_incl_scan<false>(fx, OpAdd());
+    T iy = warp_incl_scan<true>(ry, OpAdd());
+    T ex = shfl_up_t(ix, 1), ey = shfl_dn_t(iy, 1);
+    if (lane == 0) ex = zero;
+    if (lane == 31) ey = zero;
+    if (lane == 31) sbuf[warp].x = ix;
+    if (lane == 0) sbuf[warp].y = iy;
+    __syncthreads();
+    if (warp == 0) {
+        T wx = lane < nw ? sbuf[lane].x : zero;
+        T wy = lane < nw ? sbuf[lane].y : zero;
+        T sx = warp_incl_scan<false>(wx, OpAdd());
+        T sy = warp_incl_scan<true>(wy, OpAdd());
+        T qx = shfl_up_t(sx, 1), qy = shfl_dn_t(sy, 1);
+        if (lane == 0) qx = zero;
+        if (lane == 31) qy = zero;
+        __syncwarp();
+        if (lane < nw) {
+            sbuf[lane].x = qx;
+            sbuf[lane].y = qy;
+        }
+        if (lane == 31) sbuf[32].x = sx;
+        if (lane == 0) sbuf[32].y = sy;
+    }
+    __syncthreads();
+    Pair<T> res = {acc_add(sbuf[warp].x, ex), acc_add(sbuf[warp].y, ey)};
+    tx = sbuf[32].x;
+    ty = sbuf[32].y;
+    __syncthreads();
+    return res;
+}
+
+// Forward product scan of mf and reverse product scan of mr in one pass
+// (op: later element on the left).  sbuf holds 33 Pair<Mat2<R>>.
+template <class R>
+__device__ void block_excl_scan_mat_fwd_rev(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>>* sbuf, Mat2<R>& ef,
+                                            Mat2<R>& er) {
+    const Mat2<R> I2 = {1, 0, 0, 1};
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    Mat2<R> ix = warp_incl_scan<false>(mf, OpMatLeft());
+    Mat2<R> iy = warp_incl_scan<true>(mr, OpMatLeft());
+    Mat2<R> ex = shfl_up_t(ix, 1), ey = shfl_dn_t(iy, 1);
+    if (lane == 0) ex = I2;
+    if (lane == 31) ey = I2;
+    if (lane == 31) sbuf[warp].x = ix;
+    if (lane == 0) sbuf[warp].y = iy;
+    __syncthreads();
+    if (warp == 0) {
+        Mat2<R> wx = lane < nw ? sbuf[lane].x : I2;
+        Mat2<R> wy = lane < nw ? sbuf[lane].y : I2;
+        Mat2<R> sx = warp_incl_scan<false>(wx, OpMatLeft());
+        Mat2<R> sy = warp_incl_scan<true>(wy, OpMatLeft());
+        Mat2<R> qx = shfl_up_t(sx, 1), qy = shfl_dn_t(sy, 1);
+        if (lane == 0) qx = I2;
+        if (lane == 31) qy = I2;
+        __syncwarp();
+        if (lane < nw) {
+            sbuf[lane].x = qx;
+            sbuf[lane].y = qy;
+        }
+    }
+    __syncthreads();
+    ef = OpMatLeft()(sbuf[warp].x, ex);
+    er = OpMatLeft()(sbuf[warp].y, ey);
+    __syncthreads();
 }
 
 // first index i in [0, n) with a[i] >= x (n if none)

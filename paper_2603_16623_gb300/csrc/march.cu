@@ -7,16 +7,31 @@ namespace gbwake {
 // n * centre * width (Eq. macroparticle_weight), self weight
 // n * (centre * width / 2 - width^2 / 8) (the charge of the cell below the
 // ring), at rest; computed in FP64 and rounded once to the state precision.
+// float-float split of an FP64 value
+__device__ __forceinline__ float2 split_ff(double v) {
+    float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
 template <class R>
 __global__ void ring_init_kernel(const double* __restrict__ edges, int32_t n, double density, R* w, R* wh,
-                                 R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid) {
+                                 R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab) {
     for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         double d = edges[j + 1] - edges[j];
         double c = 0.5 * (edges[j] + edges[j + 1]);
-        w[j] = (R)(density * c * d);
-        wh[j] = (R)(density * (0.5 * c * d - 0.125 * d * d));
+        double wj = density * c * d;
+        double whj = density * (0.5 * c * d - 0.125 * d * d);
+        w[j] = (R)wj;
+        wh[j] = (R)whj;
         rho[j] = (R)c;
-        rho_lo[j] = (R)(c - (double)(R)c);
+        rho_lo[j] = (R)(c - (double)(R)c);  // mixed path: rho = rho + rho_lo
+        if (ctab) {     // mixed path: per-ring constants, float-float from FP64
+            double l0 = log(c);
+            float2 a = split_ff(c), b = split_ff(l0), e = split_ff(wj), f = split_ff(whj), g = split_ff(wj * l0);
+            ctab[3 * j] = make_float4(a.x, a.y, b.x, b.y);
+            ctab[3 * j + 1] = make_float4(e.x, e.y, f.x, f.y);
+            ctab[3 * j + 2] = make_float4(g.x, g.y, 0.f, 0.f);
+        }
         ur[j] = 0;
         frho[j] = 0;
         fur[j] = 0;
@@ -31,14 +46,16 @@ __global__ void gather_by_id_kernel(const int32_t* __restrict__ rid, const R* __
 }
 
 // checkpoint export: sorted state -> double arrays by ring id
+// (the mixed on-chip march keeps rho as rho + rho_lo)
 template <class R>
 __global__ void export_state_kernel(const int32_t* __restrict__ rid, const R* __restrict__ rho,
                                     const R* __restrict__ rho_lo, const R* __restrict__ ur,
                                     const R* __restrict__ frho, const R* __restrict__ fur, int32_t n,
-                                    double* o_rho, double* o_ur, double* o_fr, double* o_fu) {
+                                    const float4* __restrict__ ctab, double* o_rho, double* o_ur, double* o_fr,
+                                    double* o_fu) {
     for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         int32_t id = rid[p];
-        if (o_rho) o_rho[id] = (double)rho[p] + (rho_lo ? (double)rho_lo[p] : 0.0);
+        if (o_rho) o_rho[id] = (double)rho[p] + (ctab ? (double)rho_lo[p] : 0.0);
         if (o_ur) o_ur[id] = (double)ur[p];
         if (o_fr) o_fr[id] = (double)frho[p];
         if (o_fu) o_fu[id] = (double)fur[p];
@@ -49,8 +66,8 @@ __global__ void export_state_kernel(const int32_t* __restrict__ rid, const R* __
 template <class R>
 __global__ void import_state_kernel(const double* __restrict__ i_rho, const double* __restrict__ i_ur,
                                     const double* __restrict__ i_fr, const double* __restrict__ i_fu, int32_t n,
-                                    R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, int32_t* ctl,
-                                    int32_t slice) {
+                                    const float4* __restrict__ ctab, R* rho, R* rho_lo, R* ur, R* frho, R* fur,
+                                    int32_t* rid, int32_t* ctl, int32_t slice) {
     for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         R hi = (R)i_rho[j];
         rho[j] = hi;
@@ -71,34 +88,34 @@ __global__ void import_state_kernel(const double* __restrict__ i_rho, const doub
 
 template <class R>
 cudaError_t launch_export_state(const int32_t* rid, const R* rho, const R* rho_lo, const R* ur, const R* frho,
-                                const R* fur, int32_t n, double* o_rho, double* o_ur, double* o_fr, double* o_fu,
-                                cudaStream_t st) {
-    export_state_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(rid, rho, rho_lo, ur, frho, fur, n, o_rho, o_ur, o_fr,
-                                                           o_fu);
+                                const R* fur, int32_t n, const float4* ctab, double* o_rho, double* o_ur,
+                                double* o_fr, double* o_fu, cudaStream_t st) {
+    export_state_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(rid, rho, rho_lo, ur, frho, fur, n, ctab, o_rho, o_ur,
+                                                           o_fr, o_fu);
     return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_import_state(const double* i_rho, const double* i_ur, const double* i_fr, const double* i_fu,
-                                int32_t n, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, int32_t* ctl,
-                                int32_t slice, cudaStream_t st) {
-    import_state_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(i_rho, i_ur, i_fr, i_fu, n, rho, rho_lo, ur, frho, fur,
-                                                           rid, ctl, slice);
+                                int32_t n, const float4* ctab, R* rho, R* rho_lo, R* ur, R* frho, R* fur,
+                                int32_t* rid, int32_t* ctl, int32_t slice, cudaStream_t st) {
+    import_state_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(i_rho, i_ur, i_fr, i_fu, n, ctab, rho, rho_lo, ur,
+                                                           frho, fur, rid, ctl, slice);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_export_state<double>(const int32_t*, const double*, const double*, const double*,
-                                                 const double*, const double*, int32_t, double*, double*, double*,
-                                                 double*, cudaStream_t);
+                                                 const double*, const double*, int32_t, const float4*, double*,
+                                                 double*, double*, double*, cudaStream_t);
 template cudaError_t launch_export_state<float>(const int32_t*, const float*, const float*, const float*,
-                                                const float*, const float*, int32_t, double*, double*, double*,
-                                                double*, cudaStream_t);
+                                                const float*, const float*, int32_t, const float4*, double*,
+                                                double*, double*, double*, cudaStream_t);
 template cudaError_t launch_import_state<double>(const double*, const double*, const double*, const double*, int32_t,
-                                                 double*, double*, double*, double*, double*, int32_t*, int32_t*,
-                                                 int32_t, cudaStream_t);
+                                                 const float4*, double*, double*, double*, double*, double*,
+                                                 int32_t*, int32_t*, int32_t, cudaStream_t);
 template cudaError_t launch_import_state<float>(const double*, const double*, const double*, const double*, int32_t,
-                                                float*, float*, float*, float*, float*, int32_t*, int32_t*, int32_t,
-                                                cudaStream_t);
+                                                const float4*, float*, float*, float*, float*, float*, int32_t*,
+                                                int32_t*, int32_t, cudaStream_t);
 
 size_t march_smem(int32_t n_max, int32_t n_pad_max, size_t real_bytes, int32_t m_max, int32_t* mb_cap) {
     const int32_t kStageTarget = 8192;
@@ -120,21 +137,28 @@ cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int3
     return cudaGetLastError();
 }
 
-cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                              int32_t max_slices, int32_t mode, int32_t threads, cudaStream_t st) {
-    size_t smem = fast_smem_bytes(threads, kFastK);
-    cudaError_t e = cudaFuncSetAttribute(march_fast_kernel<kFastK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+template <int K>
+static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                                 int32_t max_slices, int32_t mode, int32_t threads, cudaStream_t st) {
+    size_t smem = fast_smem_bytes(threads, K);
+    cudaError_t e =
+        cudaFuncSetAttribute(march_fast_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    march_fast_kernel<kFastK><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode);
+    march_fast_kernel<K><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode);
     return cudaGetLastError();
+}
+
+cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                              int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, cudaStream_t st) {
+    if (k_rings == 4) return launch_fast_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, st);
+    return launch_fast_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, st);
 }
 
 template <class R>
 cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
-                             R* frho, R* fur, int32_t* rid, cudaStream_t st) {
+                             R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st) {
     int grid = (n + 255) / 256;
-    ring_init_kernel<R><<<grid, 256, 0, st>>>(edges, n, density, w, wh, rho, rho_lo, ur, frho, fur, rid);
+    ring_init_kernel<R><<<grid, 256, 0, st>>>(edges, n, density, w, wh, rho, rho_lo, ur, frho, fur, rid, ctab);
     return cudaGetLastError();
 }
 
@@ -150,9 +174,9 @@ template cudaError_t launch_march<PrecF64>(const WakeDev<PrecF64>*, const int32_
 template cudaError_t launch_march<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t, int32_t,
                                              int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_ring_init<double>(const double*, int32_t, double, double*, double*, double*, double*,
-                                              double*, double*, double*, int32_t*, cudaStream_t);
+                                              double*, double*, double*, int32_t*, float4*, cudaStream_t);
 template cudaError_t launch_ring_init<float>(const double*, int32_t, double, float*, float*, float*, float*, float*,
-                                             float*, float*, int32_t*, cudaStream_t);
+                                             float*, float*, int32_t*, float4*, cudaStream_t);
 template cudaError_t launch_gather_by_id<double>(const int32_t*, const double*, double*, int32_t, cudaStream_t);
 template cudaError_t launch_gather_by_id<float>(const int32_t*, const float*, float*, int32_t, cudaStream_t);
 

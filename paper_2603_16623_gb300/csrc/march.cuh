@@ -9,9 +9,10 @@
 //   a5 psi, d_rho psi (self weight), psibar, gamma            (Eq. plasma_particle_motion_3/4)
 //   a6 block scan of t = w u/(rho psibar) -> d_zeta psi        (Eq. dpsi_dzeta)
 //   a7 A, B, C                                                (Eqs. b_coeffs_1..3)
-//   a8 B^(p): FP64 = App. A shooting as an affine-map scan;
-//            mixed = regular/decaying homogeneous solutions + discrete Green's
-//            function (same discrete solution, no growing-mode cancellation)
+//   a8 B^(p): the discrete solution of Eq. ai_bi with b_0 = 0, a_N = 0 from
+//            the regular (forward) and decaying (backward) homogeneous
+//            solutions and the discrete Green's function; the same solution
+//            as App. A's shooting without its growing-mode cancellation
 //   a9 fields on the beam particles of the slice
 //   a10 AB2 push with axis reflection
 #pragma once
@@ -35,6 +36,9 @@ struct WakeDev {
     double dxi, density, rho_max;
     const R* w;   // [n] by ring id
     const R* wh;  // [n] by ring id
+    // mixed path: per-ring constants by id, 3 float4 each, split float-float
+    // from FP64: {rho0, ln rho0}, {w, what}, {w ln rho0, 0}
+    const float4* ctab;
     R* rho[2];
     R* rho_lo;    // low part of rho (mixed path: rho = rho + rho_lo in float-float)
     R* ur[2];
@@ -268,34 +272,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         }
 
         // ---------------- a8: B_theta^(p) region coefficients a_k, b_k
-        if constexpr (P::kShooting) {
-            // App. A: (K,U)_k and (T,P)_k from the prefix of affine maps
-            Aff2<R> Floc = {1, 0, 0, 1, 0, 0};
-            for (int p = p0; p < p1; ++p) {
-                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
-                Aff2<R> E = {(R)1 + (R)0.5 * Ac * r, (R)0.5 * Ac / r, -(R)0.5 * Ac * r * r * r,
-                             (R)1 - (R)0.5 * Ac * r, (R)0.25 * ((R)2 * Bc + Ac * Cc),
-                             (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r)};
-                Floc = OpAffThen()(Floc, E);
-            }
-            Aff2<R> Ftot;
-            Aff2<R> F = block_excl_scan<false>(Floc, OpAffThen(), Aff2<R>{1, 0, 0, 1, 0, 0},
-                                               reinterpret_cast<Aff2<R>*>(sscan), Ftot);
-            const R a0 = -Ftot.c0 / Ftot.m00;
-            if (tid == 0) {
-                W.ak[0] = a0;
-                W.bk[0] = 0;
-            }
-            for (int p = p0; p < p1; ++p) {
-                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
-                Aff2<R> E = {(R)1 + (R)0.5 * Ac * r, (R)0.5 * Ac / r, -(R)0.5 * Ac * r * r * r,
-                             (R)1 - (R)0.5 * Ac * r, (R)0.25 * ((R)2 * Bc + Ac * Cc),
-                             (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r)};
-                F = OpAffThen()(F, E);
-                W.ak[p + 1] = F.m00 * a0 + F.c0;
-                W.bk[p + 1] = F.m10 * a0 + F.c1;
-            }
-        } else {
+        {
             // regular solution R_k (R_0 = (1,0)) forward, decaying solution D_k
             // (D_n = (0,1)) backward, then x_k = -G_k R_k + H_k D_k with the
             // ring sources c_p = gamma_p R_{p+1} + delta_p D_{p+1},
@@ -348,21 +325,27 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 W.Da[p] = Yb.m01;
                 W.Db[p] = Yb.m11;
             }
-            Pair<A> gd_tot;
-            Pair<A> gd = block_excl_scan<false>(Pair<A>{gl, dl}, OpAddPair(), Pair<A>{zeroA, zeroA},
-                                                reinterpret_cast<Pair<A>*>(sscan), gd_tot);
+            // G_k = sum_{p >= k} gamma_p as a true suffix sum (a total minus a
+            // prefix would cancel where G_k is small and R_k ~ e^rho is large)
+            A g_tot, d_tot;
+            Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
             // the scan's barriers order the R/D writes above before these reads
-            A Gex = gd.x, Hex = gd.y;
+            A Gsuf = gd.y;  // sum of gamma over rings >= p1
+            for (int p = p1 - 1; p >= p0; --p) {
+                Gsuf = acc_add_r(Gsuf, W.cB[p]);  // sum over rings >= p
+                R G = acc_to_r(Gsuf);
+                W.ak[p] = -G * W.Ra[p];
+                W.bk[p] = -G * W.Rb[p];
+            }
+            A Hex = gd.x;   // sum of delta over rings < p
             for (int p = p0; p < p1; ++p) {
-                R G = acc_to_r(acc_sub(gd_tot.x, Gex));
                 R H = acc_to_r(Hex);
-                W.ak[p] = -G * W.Ra[p] + H * W.Da[p];
-                W.bk[p] = -G * W.Rb[p] + H * W.Db[p];
-                Gex = acc_add_r(Gex, W.cB[p]);
+                W.ak[p] += H * W.Da[p];
+                W.bk[p] += H * W.Db[p];
                 Hex = acc_add_r(Hex, W.cC[p]);
             }
             if (tid == 0) {
-                R H = acc_to_r(gd_tot.y);
+                R H = acc_to_r(d_tot);
                 W.ak[n] = H * W.Da[n];
                 W.bk[n] = H * W.Db[n];
             }

@@ -10,24 +10,24 @@ namespace gbwake {
 template <class P>
 cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
                          int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st);
-// the on-chip march (mixed precision, 8 rings per thread, <= 512 threads)
-constexpr int kFastK = 8;
+// the on-chip march (mixed precision, k_rings = 4 or 8 rings per thread,
+// <= 512 threads)
 constexpr int kFastMaxThreads = 512;
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                              int32_t max_slices, int32_t mode, int32_t threads, cudaStream_t st);
+                              int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, cudaStream_t st);
 template <class R>
 cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
-                             R* frho, R* fur, int32_t* rid, cudaStream_t st);
+                             R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st);
 template <class R>
 cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_t n, cudaStream_t st);
 template <class R>
 cudaError_t launch_export_state(const int32_t* rid, const R* rho, const R* rho_lo, const R* ur, const R* frho,
-                                const R* fur, int32_t n, double* o_rho, double* o_ur, double* o_fr, double* o_fu,
-                                cudaStream_t st);
+                                const R* fur, int32_t n, const float4* ctab, double* o_rho, double* o_ur,
+                                double* o_fr, double* o_fu, cudaStream_t st);
 template <class R>
 cudaError_t launch_import_state(const double* i_rho, const double* i_ur, const double* i_fr, const double* i_fu,
-                                int32_t n, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, int32_t* ctl,
-                                int32_t slice, cudaStream_t st);
+                                int32_t n, const float4* ctab, R* rho, R* rho_lo, R* ur, R* frho, R* fur,
+                                int32_t* rid, int32_t* ctl, int32_t slice, cudaStream_t st);
 // shared memory of the march kernel for rings up to n_max with slices up to m_max
 // staged; returns the bytes and the staging capacity mb_cap
 size_t march_smem(int32_t n_max, int32_t n_pad_max, size_t real_bytes, int32_t m_max, int32_t* mb_cap);

@@ -76,6 +76,7 @@ struct wake_handle {
     void* d_ur[2] = {nullptr, nullptr};
     int32_t* d_rid[2] = {nullptr, nullptr};
     int32_t fast_threads = 0;               // > 0: the on-chip march serves this wake
+    int32_t fast_k = 8;                     // its rings per thread
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
 };
 
@@ -128,7 +129,8 @@ wake_status prepare_impl(wake_handle* h) {
     const int32_t n = h->n, ns = h->n_steps;
     WK_CUDA(launch_reset_ctl(h->d_ctl, h->st));
     WK_CUDA(launch_ring_init<R>(h->d_edges, n, h->density, const_cast<R*>(D.w), const_cast<R*>(D.wh), D.rho[0],
-                                D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->st));
+                                D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], const_cast<float4*>(D.ctab),
+                                h->st));
     const size_t rb = h->real_bytes();
     WK_CUDA(cudaMemsetAsync(h->d_boff, 0, ((size_t)ns + 1) * sizeof(int32_t), h->st));
     WK_CUDA(cudaMemsetAsync(const_cast<R*>(D.bTot), 0, (size_t)ns * rb, h->st));
@@ -191,6 +193,11 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         h->d_rid[b] = D.rid[b];
     }
     WK_TRY(dalloc_t(h, n, &D.rho_lo));
+    if (h->fast_threads > 0) {
+        float4* ct;
+        WK_TRY(dalloc_t(h, (size_t)3 * n, &ct));
+        D.ctab = ct;
+    }
     R** scratch[] = {&D.bb, &D.psib, &D.gam, &D.dpr, &D.tt, &D.cA, &D.cB, &D.cC};
     for (R** sp : scratch) WK_TRY(dalloc_t(h, n, sp));
     WK_TRY(dalloc_t(h, (size_t)n + 1, &D.regS));
@@ -276,9 +283,14 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     return WAKE_OK;
 }
 
+// rings per thread of the on-chip march: 4 while that fits one block (more
+// threads, shorter per-thread chains), else 8
+int32_t fast_k_for(int32_t n) { return n <= 4 * kFastMaxThreads ? 4 : 8; }
+
 int32_t fast_threads_for(int32_t prec, int32_t n) {
-    if (prec != WAKE_MIXED || n > kFastK * kFastMaxThreads) return 0;
-    int32_t t = (n + kFastK - 1) / kFastK;
+    if (prec != WAKE_MIXED || n > 8 * kFastMaxThreads) return 0;
+    const int32_t k = fast_k_for(n);
+    int32_t t = (n + k - 1) / k;
     t = ((t + 31) / 32) * 32;
     return t < 32 ? 32 : t;
 }
@@ -294,7 +306,7 @@ template <class P>
 wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (h->fast_threads > 0) {
-            WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->st));
+            WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->st));
             return WAKE_OK;
         }
     }
@@ -431,7 +443,7 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (fast_threads > 0) {
             e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
-                                  fast_threads, st);
+                                  fast_threads, hs[0]->fast_k, st);
             cudaFreeAsync(d_buf, st);
             if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
             return WAKE_OK;
@@ -454,7 +466,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
     std::vector<int32_t> keys;
     std::vector<std::vector<wake_handle*>> buckets;
     for (int32_t i = 0; i < n; ++i) {
-        int32_t key = hs[i]->fast_threads;
+        int32_t key = hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0);
         auto it = std::find(keys.begin(), keys.end(), key);
         if (it == keys.end()) {
             keys.push_back(key);
@@ -463,7 +475,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
         }
         buckets[it - keys.begin()].push_back(hs[i]);
     }
-    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], keys[0], st);
+    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st);
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
@@ -471,7 +483,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
     for (size_t b = 0; b < buckets.size(); ++b) {
         cudaStream_t as = aux_stream((int)(b % 8));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
-        wake_status r = batch_bucket<P>(buckets[b], keys[b], as);
+        wake_status r = batch_bucket<P>(buckets[b], buckets[b][0]->fast_threads, as);
         if (r != WAKE_OK) res = r;
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -504,8 +516,8 @@ wake_status state_io(wake_handle* h, bool export_, int32_t slice, double* rho, d
         const int b = ctl[CTL_BUF];
         double* outs[4] = {rho, ur, fr, fu};
         if (e == cudaSuccess)
-            e = launch_export_state<R>(D.rid[b], D.rho[b], h->fast_threads > 0 ? D.rho_lo : nullptr, D.ur[b],
-                                       D.frho[b], D.fur[b], h->n, t[0], t[1], t[2], t[3], h->st);
+            e = launch_export_state<R>(D.rid[b], D.rho[b], D.rho_lo, D.ur[b], D.frho[b], D.fur[b], h->n, D.ctab,
+                                       t[0], t[1], t[2], t[3], h->st);
         for (int k = 0; k < 4 && e == cudaSuccess; ++k)
             if (outs[k]) e = cudaMemcpyAsync(outs[k], t[k], bytes, cudaMemcpyDeviceToHost, h->st);
     } else {
@@ -513,8 +525,9 @@ wake_status state_io(wake_handle* h, bool export_, int32_t slice, double* rho, d
         for (int k = 0; k < 4 && e == cudaSuccess; ++k)
             if (ins[k]) e = cudaMemcpyAsync(t[k], ins[k], bytes, cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess)
-            e = launch_import_state<R>(t[0], t[1], ifr ? t[2] : nullptr, ifu ? t[3] : nullptr, h->n, D.rho[0],
-                                       D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->d_ctl, slice, h->st);
+            e = launch_import_state<R>(t[0], t[1], ifr ? t[2] : nullptr, ifu ? t[3] : nullptr, h->n, D.ctab,
+                                       D.rho[0], D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], h->d_ctl, slice,
+                                       h->st);
     }
     cudaError_t e2 = cudaStreamSynchronize(h->st);
     cudaFree(tmp);
@@ -586,6 +599,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->rho_max = plasma->r_edges[n];
     h->st = static_cast<cudaStream_t>(cuda_stream);
     h->fast_threads = fast_threads_for(h->prec, n);
+    h->fast_k = fast_k_for(n);
     wake_status s = h->prec == WAKE_FP64 ? init_impl<PrecF64>(h, cfg, plasma, beams, n_beams)
                                          : init_impl<PrecMixed>(h, cfg, plasma, beams, n_beams);
     if (s != WAKE_OK) {
