@@ -148,6 +148,33 @@ static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_
     return cudaGetLastError();
 }
 
+cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                                 int32_t max_slices, int32_t mode, int32_t threads, int32_t cl, cudaStream_t st) {
+    size_t smem = fast_smem_bytes(threads, kClusterK);
+    auto kern = march_cluster_kernel<kClusterK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (cl > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_wakes * cl), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, d_wakes, d_order, max_slices, mode);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                               int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, cudaStream_t st) {
     if (k_rings == 4) return launch_fast_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, st);

@@ -141,16 +141,16 @@ __device__ __forceinline__ int ring_rank(const float* rh, int n, float x, bool s
 
 // Fields at radius x > 0 of the current slice from the region tables
 // (Eqs. b_theta_plasma..dpsi_dzeta off the rings): d_rho psi, d_zeta psi,
-// B^(p), psi.
+// B^(p), psi.  kl = number of rings (of this table's nl) below x; kl = nl
+// means beyond every ring.
 template <int K>
-__device__ __forceinline__ void fast_fields_at(const FastSmem& sm, int n, int TK, float x, float rmax, float half_n,
-                                            float quarter_n, ff Wtot, ff Imax, ff c0, float* dpr, float* dpz,
-                                            float* bp, float* psi) {
+__device__ __forceinline__ void fast_fields_region(const FastSmem& sm, int nl, int TK, int kl, float x, float rmax,
+                                                   float half_n, float quarter_n, ff Wtot, ff Imax, ff c0,
+                                                   float* dpr, float* dpz, float* bp, float* psi) {
     using SW = Swz<K>;
-    const int k = ring_rank<K>(sm.rh, n, x, true);
-    const int a = k < TK ? SW::at(k) : TK;
+    const int a = kl < TK ? SW::at(kl) : TK;
     const float cx = fminf(x, rmax);
-    if (k < n) {
+    if (kl < nl) {
         const float rk = sm.rh[a];
         const float ck = fminf(rk, rmax);
         // S_k - I(x): near ring k from D_k = S_k - I(rho_k) (both small in a
@@ -174,6 +174,15 @@ __device__ __forceinline__ void fast_fields_at(const FastSmem& sm, int n, int TK
     *dpz = -sm.T[a];
     *bp = sm.a[a] * x + sm.b[a] / x;
 }
+
+template <int K>
+__device__ __forceinline__ void fast_fields_at(const FastSmem& sm, int n, int TK, float x, float rmax, float half_n,
+                                               float quarter_n, ff Wtot, ff Imax, ff c0, float* dpr, float* dpz,
+                                               float* bp, float* psi) {
+    const int k = ring_rank<K>(sm.rh, n, x, true);
+    fast_fields_region<K>(sm, n, TK, k, x, rmax, half_n, quarter_n, Wtot, Imax, c0, dpr, dpz, bp, psi);
+}
+
 template <int K>
 __global__ void __launch_bounds__(512)
 march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* __restrict__ order,

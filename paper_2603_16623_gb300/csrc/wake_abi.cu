@@ -77,6 +77,7 @@ struct wake_handle {
     int32_t* d_rid[2] = {nullptr, nullptr};
     int32_t fast_threads = 0;               // > 0: the on-chip march serves this wake
     int32_t fast_k = 8;                     // its rings per thread
+    int32_t fast_cl = 1;                    // CTAs per wake (thread-block cluster if > 1)
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
 };
 
@@ -283,14 +284,18 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     return WAKE_OK;
 }
 
-// rings per thread of the on-chip march: 4 while that fits one block (more
-// threads, shorter per-thread chains), else 8
-int32_t fast_k_for(int32_t n) { return n <= 4 * kFastMaxThreads ? 4 : 8; }
+// The on-chip march: one CTA of up to 512 threads x 4 rings for wakes up to
+// 2048 rings; beyond, a thread-block cluster of ceil(n / 2048) such CTAs
+// (up to 16, the largest cluster GB300 allows).
+constexpr int32_t kRingsPerCta = 4 * kFastMaxThreads;
+constexpr int32_t kMaxClusterCtas = 16;
+int32_t fast_k_for(int32_t n) { (void)n; return 4; }
+int32_t fast_cl_for(int32_t n) { return (n + kRingsPerCta - 1) / kRingsPerCta; }
 
 int32_t fast_threads_for(int32_t prec, int32_t n) {
-    if (prec != WAKE_MIXED || n > 8 * kFastMaxThreads) return 0;
-    const int32_t k = fast_k_for(n);
-    int32_t t = (n + k - 1) / k;
+    if (prec != WAKE_MIXED || fast_cl_for(n) > kMaxClusterCtas) return 0;
+    if (fast_cl_for(n) > 1) return kFastMaxThreads;
+    int32_t t = (n + 3) / 4;
     t = ((t + 31) / 32) * 32;
     return t < 32 ? 32 : t;
 }
@@ -305,6 +310,10 @@ cudaStream_t aux_stream(int i) {
 template <class P>
 wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
     if constexpr (std::is_same<P, PrecMixed>::value) {
+        if (h->fast_threads > 0 && h->fast_cl > 1) {
+            WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_cl, h->st));
+            return WAKE_OK;
+        }
         if (h->fast_threads > 0) {
             WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->st));
             return WAKE_OK;
@@ -442,8 +451,12 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     cudaError_t e;
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (fast_threads > 0) {
-            e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
-                                  fast_threads, hs[0]->fast_k, st);
+            if (hs[0]->fast_cl > 1)
+                e = launch_march_cluster(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
+                                         fast_threads, hs[0]->fast_cl, st);
+            else
+                e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
+                                      fast_threads, hs[0]->fast_k, st);
             cudaFreeAsync(d_buf, st);
             if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
             return WAKE_OK;
@@ -466,7 +479,8 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
     std::vector<int32_t> keys;
     std::vector<std::vector<wake_handle*>> buckets;
     for (int32_t i = 0; i < n; ++i) {
-        int32_t key = hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0);
+        int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
+                      (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
         auto it = std::find(keys.begin(), keys.end(), key);
         if (it == keys.end()) {
             keys.push_back(key);
@@ -600,6 +614,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->st = static_cast<cudaStream_t>(cuda_stream);
     h->fast_threads = fast_threads_for(h->prec, n);
     h->fast_k = fast_k_for(n);
+    h->fast_cl = fast_cl_for(n);
     wake_status s = h->prec == WAKE_FP64 ? init_impl<PrecF64>(h, cfg, plasma, beams, n_beams)
                                          : init_impl<PrecMixed>(h, cfg, plasma, beams, n_beams);
     if (s != WAKE_OK) {

@@ -50,12 +50,13 @@ def nerr(a, b):
     return float(np.max(np.abs(a - b)) / den) if den > 0 else float(np.max(np.abs(a - b)))
 
 
-def unambiguous(wk, ring_r_ref, ring_r_gpu, slice_of=None, margin=5.0):
+def unambiguous(wk, ring_r_ref, ring_r_gpu, margin=5.0):
     """Mask of beam particles whose radial place among the rings is decided
     the same way at the precision of the run: a particle closer to a ring
-    than `margin` times the ring radii's GPU-oracle difference at its slice
-    (+1e-6 relative) could fall on either side of that ring, where d_zeta psi
-    and B^(p) jump by that ring's contribution; both values are correct."""
+    than `margin` times that ring's GPU-oracle radius difference at the
+    particle's slice (+1e-6 relative) could fall on either side of it, where
+    d_zeta psi and B^(p) jump by that ring's contribution; both values are
+    correct."""
     xi = np.concatenate([b.xi for b in wk.beams])
     r = np.concatenate([b.r for b in wk.beams])
     sl = np.floor(xi / wk.dxi + 0.5).astype(np.int64)
@@ -65,12 +66,13 @@ def unambiguous(wk, ring_r_ref, ring_r_gpu, slice_of=None, margin=5.0):
         if s < 0 or s >= nrun:
             continue
         m = np.nonzero(sl == s)[0]
-        rings = np.sort(ring_r_ref[s])
-        dev = np.max(np.abs(ring_r_gpu[s] - ring_r_ref[s]))
-        tol = margin * dev + 1e-6 * r[m]
+        order = np.argsort(ring_r_ref[s], kind="stable")
+        rings = ring_r_ref[s][order]
+        dev = np.abs(ring_r_gpu[s] - ring_r_ref[s])[order]
         j = np.clip(np.searchsorted(rings, r[m]), 1, rings.shape[0] - 1)
-        d = np.minimum(np.abs(r[m] - rings[j - 1]), np.abs(r[m] - rings[j]))
-        ok[m] = d > tol
+        lo_d, hi_d = np.abs(r[m] - rings[j - 1]), np.abs(r[m] - rings[j])
+        amb = (lo_d <= margin * dev[j - 1] + 1e-6 * r[m]) | (hi_d <= margin * dev[j] + 1e-6 * r[m])
+        ok[m] = ~amb
     return ok
 
 
@@ -177,6 +179,18 @@ def test_mixed_ring_crossings_within_tolerance():
     _mixed_window_check(axis_wake(steps=500), 128)
 
 
+def test_mixed_cluster_wakes_match_oracle():
+    """Wakes wider than one CTA run on a thread-block cluster (2048 rings per
+    CTA): a nearly empty second CTA (2049 rings), three CTAs with a wide
+    driver pushing rings across the first CTA boundary (ring 2048 sits at
+    rho ~ 2.5 inside the blowout sheath), and four full CTAs."""
+    cases = [(2049, 5.0, 0.5, 0.5), (4915, 6.0, 2.0, 1.0), (8192, 6.0, 1.0, 0.6)]
+    for n, r_max, nb0, sr in cases:
+        drv = W.gaussian_beam(40_000, nb0, sr, 0.6, 2.4, seed=n)
+        wk = W.Wake(f"cl{n}", W.edges_uniform(n, r_max), [drv], 0.01, 300)
+        _mixed_window_check(wk, 0)
+
+
 # ---------------------------------------------------------------------------
 # one-step parity on chaotic wakes at full size
 # ---------------------------------------------------------------------------
@@ -217,9 +231,23 @@ def test_one_step_parity_on_chaotic_wakes(case, precision):
         assert g.progress()[:2] == (n + 1, 0)
         d = g.ring_dumps()
         rho, ur = g.ring_state()
-        e = {k: nerr(d[k][n], R[k][n]) for k in ("psi", "dpsidr", "dpsidz", "bp", "bb")}
-        e["r"] = nerr(rho, R["r"][n + 1])
-        e["ur"] = nerr(ur, R["ur"][n + 1])
+        keep = np.ones(wk.n_rings, dtype=bool)
+        if precision == "mixed":
+            # rings closer than float resolution to a neighbour may be sorted
+            # either way; swapping such a pair changes only the two rings'
+            # self-weighted fields (the transfer matrices of rings at equal
+            # radius commute), so they are left out of the per-ring compare
+            order = np.argsort(R["r"][n], kind="stable")
+            rs = R["r"][n][order]
+            close = np.diff(rs) <= 5e-7 * rs[1:]
+            tied = np.zeros(wk.n_rings, dtype=bool)
+            tied[order[1:][close]] = True
+            tied[order[:-1][close]] = True
+            assert tied.mean() < 0.01, (name, n, tied.sum())
+            keep = ~tied
+        e = {k: nerr(d[k][n][keep], R[k][n][keep]) for k in ("psi", "dpsidr", "dpsidz", "bp", "bb")}
+        e["r"] = nerr(rho[keep], R["r"][n + 1][keep])
+        e["ur"] = nerr(ur[keep], R["ur"][n + 1][keep])
         m = sl == n
         if m.any():
             bf = g.beam_fields()
@@ -306,7 +334,8 @@ def test_step_slices_is_resumable(precision):
 def test_batched_launch_equals_alone(precision):
     wm = _wake_mod()
     wakes = []
-    for k, (n, steps, nb0) in enumerate([(700, 300, 2.0), (257, 450, 0.3), (1500, 200, 8.0), (64, 600, 1.0)]):
+    for k, (n, steps, nb0) in enumerate([(700, 300, 2.0), (257, 450, 0.3), (1500, 200, 8.0), (64, 600, 1.0),
+                                         (3000, 150, 2.0), (2500, 100, 1.0)]):
         drv = W.gaussian_beam(20_000, nb0, 0.3, 0.6, 2.4, seed=50 + k)
         wakes.append(W.Wake(f"b{k}", W.edges_uniform(n, 6.0), [drv], 0.01, steps))
     alone = []
