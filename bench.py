@@ -37,10 +37,12 @@ from paper_2603_16623_gb300 import workloads as W  # noqa: E402
 
 METRIC = "ring-slice updates/s (batched FP32 vs plain FP64, 1 GB300); p50/p99 wake latency"
 UNIT = "ring-slices/s"
-# algorithmic floating-point operations per ring-slice update of the march
-# (the arithmetic of steps a3-a10 as written in the oracle, divides and logs
-# counted once; see the design doc for the itemisation)
-FLOPS_PER_RING_SLICE = 128
+# algorithmic floating-point operations per ring-slice update of the march:
+# the arithmetic of steps a3-a10 as the oracle writes it (each +, -, *, /
+# and log counted once): beam field 2, prefix sums 4, psi/d_rho psi/psibar/
+# gamma/t 21, d_zeta psi 6, A/B/C 27, B_theta^(p) recursion and value 44,
+# AB2 push 13
+FLOPS_PER_RING_SLICE = 117
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
 SMS, FP32_LANES = 152, 128
 
@@ -108,6 +110,8 @@ def run_ours(args):
     wakes = _workload(args.n_wakes, rank)
     gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream) for wk in wakes]
     torch.cuda.synchronize()
+    # one march launch per distinct (threads, rings per thread, blocks per wake)
+    n_march_launches = len({g.launch_config() for g in gs})
 
     def step(ev=None):
         if ev is not None:
@@ -243,7 +247,7 @@ def run_ours(args):
     achieved = FLOPS_PER_RING_SLICE * ring_slices / (march_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "march_kernel<PrecMixed>", "peak_basis":
+                "kernel": "march_fast_kernel<4> + march_cluster_kernel<4> (batched march)", "peak_basis":
                     f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
     if rank == 0:
         line = {
@@ -252,10 +256,11 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff (mixed)", "data": "synthetic",
             "config": {"workload": f"batched: {args.n_wakes} independent wakes per GPU, log-uniform 500-8000 "
                                    "rings, 1000-6000 slices of 0.01, 50k-500k beam particles",
-                       "n_wakes": args.n_wakes, "precision": "mixed", "block_threads": 256,
+                       "n_wakes": args.n_wakes, "precision": "mixed",
+                       "launches": sorted({g.launch_config() for g in gs}),
                        "ring_slices_per_step": ring_slices, "wakes_stopped_by_breakdown": stopped,
                        "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
-            "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + 1),
+            "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + n_march_launches),
             "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
             "wall_s": wall,

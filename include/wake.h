@@ -181,6 +181,12 @@ wake_status wake_set_ring_state(wake_handle *h, int32_t slice, const double *rho
 wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, void *dpsidr,
                                 void *dpsidz, void *bp, void *bb);
 
+/* How the march kernels serve this wake: threads per block, rings per
+   thread, and thread blocks per wake (> 1: a thread-block cluster).  For
+   batched launches, wakes with equal triples share one launch. */
+wake_status wake_get_launch_config(wake_handle *h, int32_t *threads, int32_t *rings_per_thread,
+                                   int32_t *blocks_per_wake);
+
 void wake_destroy(wake_handle *h);
 
 const char *wake_last_error(void);

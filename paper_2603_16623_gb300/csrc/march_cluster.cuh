@@ -44,20 +44,21 @@ __device__ __forceinline__ FastSmem rmt_sm(cg::cluster_group& cl, const FastSmem
     return o;
 }
 
-// exchange of a block-scan total across the cluster: returns the fold of the
-// totals of ranks < mine (forward) and the fold of all ranks; slot is this
-// CTA's __shared__ publication slot for this call site
+// Exchange of a block-scan total across the cluster.  Each CTA stores its
+// total into every peer's receive array (remote stores need no round trip),
+// one cluster barrier makes them visible, and each CTA folds locally: the
+// totals of ranks < mine (forward) and of all ranks, in rank order.  recv is
+// this call site's __shared__ array of 16 slots.
 template <class T, class Op>
-__device__ void cluster_fold_fwd(cg::cluster_group& cl, T tot, T ident, Op op, T* slot, T* s_pre, T* s_all) {
+__device__ void cluster_fold_fwd(cg::cluster_group& cl, T tot, T ident, Op op, T* recv, T* s_pre, T* s_all) {
     const int rank = cl.block_rank(), size = cl.num_blocks();
-    if (threadIdx.x == 0) *slot = tot;
+    if (threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = tot;
     cl.sync();
     if (threadIdx.x == 0) {
         T pre = ident, all = ident;
         for (int r = 0; r < size; ++r) {
-            T v = *rmt(cl, slot, r);
-            if (r < rank) pre = op(pre, v);
-            all = op(all, v);
+            if (r < rank) pre = op(pre, recv[r]);
+            all = op(all, recv[r]);
         }
         *s_pre = pre;
         *s_all = all;
@@ -68,16 +69,15 @@ __device__ void cluster_fold_fwd(cg::cluster_group& cl, T tot, T ident, Op op, T
 // the same for a reverse scan: fold of the totals of ranks > mine, taken
 // from the last rank down
 template <class T, class Op>
-__device__ void cluster_fold_rev(cg::cluster_group& cl, T tot, T ident, Op op, T* slot, T* s_pre, T* s_all) {
+__device__ void cluster_fold_rev(cg::cluster_group& cl, T tot, T ident, Op op, T* recv, T* s_pre, T* s_all) {
     const int rank = cl.block_rank(), size = cl.num_blocks();
-    if (threadIdx.x == 0) *slot = tot;
+    if (threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = tot;
     cl.sync();
     if (threadIdx.x == 0) {
         T pre = ident, all = ident;
         for (int r = size - 1; r >= 0; --r) {
-            T v = *rmt(cl, slot, r);
-            if (r > rank) pre = op(pre, v);
-            all = op(all, v);
+            if (r > rank) pre = op(pre, recv[r]);
+            all = op(all, recv[r]);
         }
         *s_pre = pre;
         *s_all = all;
@@ -85,13 +85,14 @@ __device__ void cluster_fold_rev(cg::cluster_group& cl, T tot, T ident, Op op, T
     __syncthreads();
 }
 
-// cluster-wide AND of a block-uniform flag
-__device__ __forceinline__ bool cluster_all(cg::cluster_group& cl, bool v, int* slot, int* s_out) {
-    if (threadIdx.x == 0) *slot = v ? 1 : 0;
+// cluster-wide AND of a block-uniform flag (push-style, as above)
+__device__ __forceinline__ bool cluster_all(cg::cluster_group& cl, bool v, int* recv, int* s_out) {
+    const int rank = cl.block_rank(), size = cl.num_blocks();
+    if (threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = v ? 1 : 0;
     cl.sync();
     if (threadIdx.x == 0) {
         int a = 1;
-        for (int r = 0; r < (int)cl.num_blocks(); ++r) a &= *rmt(cl, slot, r);
+        for (int r = 0; r < size; ++r) a &= recv[r];
         *s_out = a;
     }
     __syncthreads();
@@ -191,11 +192,12 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     __shared__ int s_ctl[CTL_N];
     __shared__ float s_first[16];
     __shared__ float s_edge[2];  // this CTA's first and last radius
-    __shared__ int s_vote, s_vote_out;
-    __shared__ Trip<ff> x1_slot, x1_pre, x1_all;
-    __shared__ ff x2_slot, x2_pre, x2_all;
-    __shared__ Mat2<float> x3f_slot, x3f_pre, x3f_all, x3r_slot, x3r_pre, x3r_all;
-    __shared__ ff x4f_slot, x4f_pre, x4f_all, x4r_slot, x4r_pre, x4r_all;
+    __shared__ float4 s_sortv[16];
+    __shared__ int s_gvote[16], s_vote_out;
+    __shared__ Trip<ff> x1_slot[16], x1_pre, x1_all;
+    __shared__ ff x2_slot[16], x2_pre, x2_all;
+    __shared__ Mat2<float> x3f_slot[16], x3f_pre, x3f_all, x3r_slot[16], x3r_pre, x3r_all;
+    __shared__ ff x4f_slot[16], x4f_pre, x4f_all, x4r_slot[16], x4r_pre, x4r_all;
 
     cg::cluster_group cl = cg::this_cluster();
     const int crank = cl.block_rank();
@@ -284,18 +286,19 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             }
             if (p0 + K < nl && sm.rh[SW::at(p0 + K)] < prev) ok = false;
             bool blk = __syncthreads_and(ok);
-            if (tid == 0) {
-                s_edge[0] = sm.rh[SW::at(0)];
-                s_edge[1] = sm.rh[SW::at(nl - 1)];
-            }
-            // block votes and CTA boundaries
-            if (tid == 0) s_vote = blk ? 1 : 0;
+            // block votes and CTA boundaries: every CTA pushes (vote, first
+            // radius, last radius) into each peer's slot of its rank, one
+            // cluster barrier, then every CTA checks all of them locally
+            if (tid < csize)
+                *rmt(cl, &s_sortv[crank], tid) =
+                    make_float4(blk ? 1.f : 0.f, sm.rh[SW::at(0)], sm.rh[SW::at(nl - 1)], 0.f);
             cl.sync();
             if (tid == 0) {
                 int all = 1;
                 for (int r = 0; r < csize; ++r) {
-                    all &= *rmt(cl, &s_vote, r);
-                    if (r + 1 < csize && *rmt(cl, &s_edge[1], r) > *rmt(cl, &s_edge[0], r + 1)) all = 0;
+                    const float4 v = s_sortv[r];
+                    if (v.x == 0.f) all = 0;
+                    if (r + 1 < csize && v.z > s_sortv[r + 1].y) all = 0;
                 }
                 s_vote_out = all;
             }
@@ -384,7 +387,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         Trip<A> tot1;
         Trip<A> ex1 = block_excl_scan<false>(Trip<A>{sw, sl, cnt}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
                                              reinterpret_cast<Trip<A>*>(sscan), tot1);
-        cluster_fold_fwd(cl, tot1, Trip<A>{zeroA, zeroA, 0}, OpAddTrip(), &x1_slot, &x1_pre, &x1_all);
+        cluster_fold_fwd(cl, tot1, Trip<A>{zeroA, zeroA, 0}, OpAddTrip(), x1_slot, &x1_pre, &x1_all);
         ex1 = OpAddTrip()(x1_pre, ex1);
         const A Wtot = x1_all.x, Ltot = x1_all.y;
 
@@ -434,7 +437,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         }
         A Ttot_blk;
         A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot_blk);
-        cluster_fold_fwd(cl, Ttot_blk, zeroA, OpAdd(), &x2_slot, &x2_pre, &x2_all);
+        cluster_fold_fwd(cl, Ttot_blk, zeroA, OpAdd(), x2_slot, &x2_pre, &x2_all);
         Tex = ff_acc(x2_pre, Tex);
         const A Ttot = x2_all;
 
@@ -494,8 +497,8 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             __syncthreads();
             Mat2<R> tf = tmp[0], tb = tmp[1];
             __syncthreads();
-            cluster_fold_fwd(cl, tf, I2, OpMatLeft(), &x3f_slot, &x3f_pre, &x3f_all);
-            cluster_fold_rev(cl, tb, I2, OpMatLeft(), &x3r_slot, &x3r_pre, &x3r_all);
+            cluster_fold_fwd(cl, tf, I2, OpMatLeft(), x3f_slot, &x3f_pre, &x3f_all);
+            cluster_fold_rev(cl, tb, I2, OpMatLeft(), x3r_slot, &x3r_pre, &x3r_all);
             Yf = OpMatLeft()(x3f_pre, Yf);
             Yb = OpMatLeft()(x3r_pre, Yb);
         }
@@ -543,8 +546,8 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         }
         A g_tot, d_tot;
         Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
-        cluster_fold_fwd(cl, d_tot, zeroA, OpAdd(), &x4f_slot, &x4f_pre, &x4f_all);
-        cluster_fold_rev(cl, g_tot, zeroA, OpAdd(), &x4r_slot, &x4r_pre, &x4r_all);
+        cluster_fold_fwd(cl, d_tot, zeroA, OpAdd(), x4f_slot, &x4f_pre, &x4f_all);
+        cluster_fold_rev(cl, g_tot, zeroA, OpAdd(), x4r_slot, &x4r_pre, &x4r_all);
         gd.x = ff_acc(x4f_pre, gd.x);
         gd.y = ff_acc(x4r_pre, gd.y);
         {
@@ -668,7 +671,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 }
             }
         }
-        bad = !cluster_all(cl, !__syncthreads_or(bad), &s_vote, &s_vote_out);
+        bad = !cluster_all(cl, !__syncthreads_or(bad), s_gvote, &s_vote_out);
         if (mode != MODE_MARCH) break;
         if (bad) {
             status = 4;

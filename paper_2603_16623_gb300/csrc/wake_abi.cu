@@ -300,11 +300,34 @@ int32_t fast_threads_for(int32_t prec, int32_t n) {
     return t < 32 ? 32 : t;
 }
 
-// auxiliary streams for concurrent batched launches of different block sizes
-cudaStream_t aux_stream(int i) {
-    static cudaStream_t pool[8] = {nullptr};
-    if (!pool[i]) cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking);
-    return pool[i];
+// Auxiliary streams for concurrent batched launches of different kernel
+// configurations.  The first kHighPrioStreams get the device's greatest
+// priority so that the blocks of the longest buckets (launched first) are
+// dispatched ahead of short ones when the SMs are full.
+constexpr int kAuxStreams = 32, kHighPrioStreams = 4;
+cudaError_t aux_stream(int i, cudaStream_t* out) {
+    static cudaStream_t pool[kAuxStreams] = {nullptr};
+    static int pool_dev[kAuxStreams];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (pool[i] && pool_dev[i] != dev) {
+        // created for another device: make a new one on the current device
+        pool[i] = nullptr;
+    }
+    if (!pool[i]) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamCreateWithPriority(&pool[i], cudaStreamNonBlocking, i < kHighPrioStreams ? greatest : least);
+        if (e != cudaSuccess) {
+            pool[i] = nullptr;
+            return e;
+        }
+        pool_dev[i] = dev;
+    }
+    *out = pool[i];
+    return cudaSuccess;
 }
 
 template <class P>
@@ -490,12 +513,25 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
         buckets[it - keys.begin()].push_back(hs[i]);
     }
     if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st);
+    // longest critical path first: slices x rings per CTA of the bucket's
+    // longest wake
+    std::vector<double> cost(buckets.size(), 0.0);
+    for (size_t b = 0; b < buckets.size(); ++b)
+        for (const wake_handle* h : buckets[b]) {
+            const int32_t cl = (h->fast_threads > 0 && h->fast_cl > 1) ? h->fast_cl : 1;
+            cost[b] = std::max(cost[b], (double)h->n_steps * (double)(h->n + cl - 1) / cl);
+        }
+    std::vector<size_t> border(buckets.size());
+    for (size_t b = 0; b < border.size(); ++b) border[b] = b;
+    std::stable_sort(border.begin(), border.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
     wake_status res = WAKE_OK;
-    for (size_t b = 0; b < buckets.size(); ++b) {
-        cudaStream_t as = aux_stream((int)(b % 8));
+    for (size_t i = 0; i < border.size(); ++i) {
+        const size_t b = border[i];
+        cudaStream_t as = nullptr;
+        WK_CUDA(aux_stream((int)(i % kAuxStreams), &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
         wake_status r = batch_bucket<P>(buckets[b], buckets[b][0]->fast_threads, as);
         if (r != WAKE_OK) res = r;
@@ -752,6 +788,16 @@ wake_status wake_get_ring_dumps(wake_handle* h, void* r, void* ur, void* psi, vo
         WK_CUDA(cudaMemcpyAsync(outs[k], h->d_dump[k], bytes, cudaMemcpyDeviceToHost, h->st));
     }
     WK_CUDA(cudaStreamSynchronize(h->st));
+    return WAKE_OK;
+}
+
+wake_status wake_get_launch_config(wake_handle* h, int32_t* threads, int32_t* rings_per_thread,
+                                   int32_t* blocks_per_wake) {
+    WK_TRY(check_handle(h));
+    const bool fast = h->fast_threads > 0;
+    if (threads) *threads = fast ? h->fast_threads : h->threads;
+    if (rings_per_thread) *rings_per_thread = fast ? h->fast_k : (h->n + h->threads - 1) / h->threads;
+    if (blocks_per_wake) *blocks_per_wake = fast ? h->fast_cl : 1;
     return WAKE_OK;
 }
 

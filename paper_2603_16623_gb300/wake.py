@@ -63,6 +63,7 @@ _SIGS = {
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "wake_get_ring_dumps": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "wake_get_launch_config": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_destroy": ([_vp], None),
     "wake_last_error": ([], C.c_char_p),
     "wake_max_rings": ([C.c_int32], C.c_int32),
@@ -247,6 +248,12 @@ class Wake:
         _check(load().wake_set_ring_state(self.handle, int(slice_), rho.ctypes.data, ur.ctypes.data,
                                           fr.ctypes.data if fr is not None else None,
                                           fu.ctypes.data if fu is not None else None))
+
+    def launch_config(self):
+        """(threads per block, rings per thread, blocks per wake)."""
+        t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().wake_get_launch_config(self.handle, C.byref(t), C.byref(k), C.byref(c)))
+        return t.value, k.value, c.value
 
     def ring_dumps(self, which=("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb")) -> Dict[str, np.ndarray]:
         keys = ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb")
