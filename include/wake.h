@@ -187,6 +187,28 @@ wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, vo
 wake_status wake_get_launch_config(wake_handle *h, int32_t *threads, int32_t *rings_per_thread,
                                    int32_t *blocks_per_wake);
 
+/* wake_fields_at without any allocation.  The paper has no counterpart:
+   this entry exists for callers that cannot allocate while they run -- a
+   host code that owns the device's memory through its own pool allocator,
+   or a latency-critical loop that must not let cudaMalloc/cudaFree
+   synchronise the device.  Same fields, same kernels and same results as
+   wake_fields_at at the current slice; r and the outputs are HOST arrays
+   ("real" outputs, any may be NULL), n <= WAKE_STATIC_MAX_QUERIES.
+   The per-call scratch (query radii, outputs, launch descriptor, about
+   2.5 MiB) is one static device array of the library, not memory of the
+   handle or of the caller.  The first call on each device looks up its
+   address with cudaGetSymbolAddress, so make one call (n = 0 does only
+   this set-up) before any stream capture.  The handle's device must be
+   current.  There is one scratch array per device and process: calls that
+   overlapped would race on it, so a call made while another is in
+   progress in this process returns WAKE_EBUSY.  Synchronises the handle's
+   stream before returning.
+   Errors: EINVAL (n < 0 or n > WAKE_STATIC_MAX_QUERIES, NULL r, handle on
+   another device), EBUSY, ENONFINITE (the wake stopped), ECUDA. */
+#define WAKE_STATIC_MAX_QUERIES 65536
+wake_status wake_fields_at_static(wake_handle *h, int64_t n, const double *r, void *ez, void *wr,
+                                  void *bt, void *psi);
+
 void wake_destroy(wake_handle *h);
 
 const char *wake_last_error(void);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -588,6 +589,97 @@ wake_status state_io(wake_handle* h, bool export_, int32_t slice, double* rho, d
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Scratch for wake_fields_at_static, the variant of wake_fields_at that
+// allocates nothing.  Its callers are the ones that cannot allocate while
+// they run: a host code that has handed the device's memory to its own pool
+// allocator (a cudaMalloc there fails or fragments that pool), and a
+// latency-critical loop in which cudaMalloc/cudaFree would synchronise the
+// device and stall the caller's other streams.  The per-call scratch that
+// wake_fields_at allocates -- the query radii, the four output arrays and
+// the launch descriptor -- sits in this one file-scope device array instead,
+// sized for WAKE_STATIC_MAX_QUERIES queries.  There is one copy of it per
+// device and process, so two calls in flight at once would race on it; a
+// call made while another is in progress in this process is refused with
+// WAKE_EBUSY, and each call waits for its own stream before it returns.
+constexpr size_t kStaticDescBytes = 1024;  // launch descriptor, padded
+constexpr size_t kStaticQueryBytes = (size_t)WAKE_STATIC_MAX_QUERIES * sizeof(double);
+constexpr size_t kStaticScratchBytes = kStaticDescBytes + 5 * kStaticQueryBytes;  // r + 4 outputs
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static_assert(sizeof(WakeDev<PrecF64>) <= kStaticDescBytes && sizeof(WakeDev<PrecMixed>) <= kStaticDescBytes,
+              "launch descriptor does not fit its static slot");
+
+constexpr int kStaticMaxDevices = 64;
+unsigned char* g_static_addr[kStaticMaxDevices] = {nullptr};  // symbol address, per device
+std::atomic<int> g_static_busy{0};
+
+// Device address of the static scratch on the current device, looked up
+// with cudaGetSymbolAddress the first time for each device.
+wake_status static_scratch(unsigned char** out) {
+    int dev = 0;
+    WK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices)
+        return fail(WAKE_EINVAL, "wake_fields_at_static: device %d is beyond the %d supported", dev,
+                    kStaticMaxDevices);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(WAKE_ECUDA, "wake_fields_at_static: cudaGetSymbolAddress of the static scratch failed: %s",
+                        cudaGetErrorString(e));
+        }
+        g_static_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_static_addr[dev];
+    return WAKE_OK;
+}
+
+template <class P>
+wake_status fields_at_static_impl(wake_handle* h, int64_t n, const double* r, void* const outs_user[4],
+                                  unsigned char* base) {
+    using R = typename P::R;
+    WakeDev<P> D;
+    std::memcpy(&D, h->desc_host.data(), sizeof(D));
+    double* d_r = reinterpret_cast<double*>(base + kStaticDescBytes);
+    R* d_out[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k)
+        if (outs_user[k]) d_out[k] = reinterpret_cast<R*>(base + kStaticDescBytes + (1 + k) * kStaticQueryBytes);
+    D.nq = n;
+    D.rq = d_r;
+    D.q_ez = d_out[0];
+    D.q_wr = d_out[1];
+    D.q_bt = d_out[2];
+    D.q_psi = d_out[3];
+    // every step is queued on the handle's stream; on any error the stream
+    // is drained before returning so that nothing still uses the scratch
+    auto drain = [&](wake_status s) {
+        cudaStreamSynchronize(h->st);
+        return s;
+    };
+    cudaError_t e = cudaMemcpyAsync(d_r, r, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base, &D, sizeof(D), cudaMemcpyHostToDevice, h->st);
+    // the output slots start at zero, so no value of an earlier call can be
+    // returned for a query the kernel does not write
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (d_out[k]) e = cudaMemsetAsync(d_out[k], 0, (size_t)n * sizeof(R), h->st);
+    if (e != cudaSuccess)
+        return drain(fail(WAKE_ECUDA, "wake_fields_at_static: staging failed: %s", cudaGetErrorString(e)));
+    wake_status s = launch_one<P>(h, reinterpret_cast<const WakeDev<P>*>(base), 1, MODE_QUERY);
+    if (s != WAKE_OK) return drain(s);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (outs_user[k])
+            e = cudaMemcpyAsync(outs_user[k], d_out[k], (size_t)n * sizeof(R), cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e2 = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_fields_at_static: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* wake_last_error(void) { return g_err.c_str(); }
@@ -799,6 +891,36 @@ wake_status wake_get_launch_config(wake_handle* h, int32_t* threads, int32_t* ri
     if (rings_per_thread) *rings_per_thread = fast ? h->fast_k : (h->n + h->threads - 1) / h->threads;
     if (blocks_per_wake) *blocks_per_wake = fast ? h->fast_cl : 1;
     return WAKE_OK;
+}
+
+wake_status wake_fields_at_static(wake_handle* h, int64_t n, const double* r, void* ez, void* wr, void* bt,
+                                  void* psi) {
+    WK_TRY(check_handle(h));
+    if (n < 0 || (n > 0 && !r)) return fail(WAKE_EINVAL, "wake_fields_at_static: bad query array");
+    if (n > WAKE_STATIC_MAX_QUERIES)
+        return fail(WAKE_EINVAL, "wake_fields_at_static: %lld queries exceed the static scratch limit of %d",
+                    (long long)n, (int)WAKE_STATIC_MAX_QUERIES);
+    int sdev = 0, cdev = 0;
+    WK_CUDA(cudaStreamGetDevice(h->st, &sdev));
+    WK_CUDA(cudaGetDevice(&cdev));
+    if (sdev != cdev)
+        return fail(WAKE_EINVAL, "wake_fields_at_static: the handle's device %d is not the current device %d", sdev,
+                    cdev);
+    int expected = 0;
+    if (!g_static_busy.compare_exchange_strong(expected, 1))
+        return fail(WAKE_EBUSY, "wake_fields_at_static: another call is using the static scratch");
+    struct Release {
+        ~Release() { g_static_busy.store(0); }
+    } release;
+    unsigned char* base = nullptr;
+    WK_TRY(static_scratch(&base));
+    int32_t status = 0;
+    WK_TRY(wake_get_progress(h, nullptr, &status, nullptr));
+    if (status != 0) return fail(WAKE_ENONFINITE, "wake_fields_at_static: the wake stopped at a non-finite slice");
+    if (n == 0) return WAKE_OK;
+    void* outs[4] = {ez, wr, bt, psi};
+    if (h->prec == WAKE_FP64) return fields_at_static_impl<PrecF64>(h, n, r, outs, base);
+    return fields_at_static_impl<PrecMixed>(h, n, r, outs, base);
 }
 
 void wake_destroy(wake_handle* h) {

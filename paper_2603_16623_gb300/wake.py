@@ -23,6 +23,7 @@ from . import build as _build
 WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENONFINITE, WAKE_ETIMEOUT, WAKE_EBUSY = range(7)
 WAKE_FP64, WAKE_MIXED = 0, 1
 WAKE_DUMP_RING_R, WAKE_DUMP_RING_FIELDS = 1, 2
+WAKE_STATIC_MAX_QUERIES = 65536  # queries per wake_fields_at_static call
 PRECISION = {"fp64": WAKE_FP64, "mixed": WAKE_MIXED}
 _STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "EBUSY"}
 
@@ -64,6 +65,7 @@ _SIGS = {
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "wake_get_ring_dumps": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_get_launch_config": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+    "wake_fields_at_static": ([_vp, C.c_int64, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_destroy": ([_vp], None),
     "wake_last_error": ([], C.c_char_p),
     "wake_max_rings": ([C.c_int32], C.c_int32),
@@ -204,6 +206,17 @@ class Wake:
         out = {k: np.zeros(n, dtype=self.dtype) for k in ("ez", "wr", "bt", "psi")}
         _check(load().wake_fields_at(self.handle, n, r.ctypes.data, out["ez"].ctypes.data, out["wr"].ctypes.data,
                                      out["bt"].ctypes.data, out["psi"].ctypes.data, 0))
+        return out
+
+    def fields_at_static(self, r) -> Dict[str, np.ndarray]:
+        """fields_at through the entry point that allocates nothing (its
+        scratch is a static device array of the library): host radii r,
+        at most WAKE_STATIC_MAX_QUERIES of them."""
+        r = _f64(r)
+        n = r.shape[0]
+        out = {k: np.zeros(n, dtype=self.dtype) for k in ("ez", "wr", "bt", "psi")}
+        _check(load().wake_fields_at_static(self.handle, n, r.ctypes.data, out["ez"].ctypes.data,
+                                            out["wr"].ctypes.data, out["bt"].ctypes.data, out["psi"].ctypes.data))
         return out
 
     def fields_at_device(self, r_dev, outs: Dict[str, object]):
