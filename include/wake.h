@@ -86,8 +86,15 @@ typedef struct {
     int32_t n_steps;          /* slices in the window, >= 1                      */
     int32_t precision;        /* WAKE_FP64 or WAKE_MIXED                         */
     int32_t flags;            /* WAKE_DUMP_* bits                                */
-    int32_t block_threads;    /* threads per wake (multiple of 32, 64..512);
-                                 0 = library default                            */
+    int32_t block_threads;    /* FP64: threads per wake (multiple of 32,
+                                 64..512); 0 = library default                  */
+    int32_t rings_per_thread; /* MIXED: 4 or 8 rings per thread; 0 = automatic  */
+    int32_t cluster_ctas;     /* MIXED: CTAs per wake, 1..16 (> 1: a thread-
+                                 block cluster); 0 = automatic.  The threads
+                                 per CTA follow: ceil(n / (rings_per_thread x
+                                 cluster_ctas)) rounded up to a multiple of 32,
+                                 at most 512, and no CTA may be left empty.
+                                 Both must be 0 for WAKE_FP64.                  */
 } wake_config;
 
 typedef struct wake_handle wake_handle;

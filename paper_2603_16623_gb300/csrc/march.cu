@@ -148,10 +148,11 @@ static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                                 int32_t max_slices, int32_t mode, int32_t threads, int32_t cl, cudaStream_t st) {
-    size_t smem = fast_smem_bytes(threads, kClusterK);
-    auto kern = march_cluster_kernel<kClusterK>;
+template <int K>
+static cudaError_t launch_cluster_k(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                                    int32_t max_slices, int32_t mode, int32_t threads, int32_t cl, cudaStream_t st) {
+    size_t smem = fast_smem_bytes(threads, K);
+    auto kern = march_cluster_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (cl > 8) {
@@ -173,6 +174,13 @@ cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_
     e = cudaLaunchKernelEx(&cfg, kern, d_wakes, d_order, max_slices, mode);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                                 int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
+                                 cudaStream_t st) {
+    if (k_rings == 4) return launch_cluster_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, st);
+    return launch_cluster_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, st);
 }
 
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,

@@ -16,10 +16,11 @@ cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int3
 constexpr int kFastMaxThreads = 512;
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                               int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, cudaStream_t st);
-// the cluster march: clusters of cl CTAs of `threads` threads, 4 rings each
-constexpr int kClusterK = 4;
+// the cluster march: clusters of cl CTAs of `threads` threads, k_rings = 4
+// or 8 rings per thread
 cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                                 int32_t max_slices, int32_t mode, int32_t threads, int32_t cl, cudaStream_t st);
+                                 int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
+                                 cudaStream_t st);
 template <class R>
 cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
                              R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st);

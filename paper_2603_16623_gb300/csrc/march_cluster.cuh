@@ -2,15 +2,22 @@
 // cluster: CTA c of the cluster holds the sorted ring positions
 // [c*T*K, (c+1)*T*K) in its shared memory (same layout as march_fast.cuh).
 // The per-slice chain is that of march_fast.cuh; what crosses CTAs goes
-// through distributed shared memory:
-//   - block-scan totals (each CTA folds the totals of its predecessors, or
-//     successors for the reverse scans, in rank order: deterministic);
-//   - the sortedness vote and, when rings crossed, the sort: a local bitonic
-//     sort in every CTA, then odd-even merge-split rounds between neighbour
-//     CTAs (merge path over the two sorted ranges) until sorted;
-//   - beam counts (atomic adds into the owning CTA), beam-particle and query
-//     lookups (binary search in the owning CTA's radii), and the region
-//     table entry just past each CTA's last ring.
+// through distributed shared memory, pushed by remote stores into each
+// peer's receive slots and read locally after one cluster barrier:
+//   - the sortedness vote, every CTA's first and last radius and the guard
+//     of the previous slice (one exchange at the top of each slice; the AB2
+//     push of a slice waits in the dead region-table arrays and becomes the
+//     state only if no CTA failed the guard);
+//   - the four block-scan totals (each CTA folds the totals of its
+//     predecessors, or successors for the reverse scans, in rank order:
+//     deterministic), the two matrix scans and the two Green's-function sums
+//     sharing one exchange each;
+//   - the region table entry just past each CTA's last ring.
+// Beam counting and the fields on beam particles stay inside each CTA: each
+// CTA takes the particles (or query radii) between the previous CTA's last
+// radius and its own, whose rings and regions it holds.  When rings crossed, a local
+// bitonic sort in every CTA is followed by odd-even merge-split rounds
+// between neighbour CTAs (merge path over the two sorted ranges).
 // Every cluster barrier is reached in cluster-uniform control flow.
 #pragma once
 
@@ -44,82 +51,81 @@ __device__ __forceinline__ FastSmem rmt_sm(cg::cluster_group& cl, const FastSmem
     return o;
 }
 
-// Exchange of a block-scan total across the cluster.  Each CTA stores its
-// total into every peer's receive array (remote stores need no round trip),
-// one cluster barrier makes them visible, and each CTA folds locally: the
-// totals of ranks < mine (forward) and of all ranks, in rank order.  recv is
-// this call site's __shared__ array of 16 slots.
-template <class T, class Op>
-__device__ void cluster_fold_fwd(cg::cluster_group& cl, T tot, T ident, Op op, T* recv, T* s_pre, T* s_all) {
+// Push of one value per CTA: every CTA stores v into slot [its rank] of
+// each peer's recv array (threads 0..size-1, one peer each).  The values are
+// read after the next cluster barrier.
+template <class T>
+__device__ __forceinline__ void cluster_push(cg::cluster_group& cl, T* recv, const T& v) {
     const int rank = cl.block_rank(), size = cl.num_blocks();
-    if (threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = tot;
-    cl.sync();
+    if ((int)threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = v;
+}
+
+// Folds of the received totals in rank order: over ranks < mine (pre) and
+// over all ranks (all).  Every thread computes them from shared memory.
+template <class T, class Op>
+__device__ __forceinline__ void fold_fwd(const T* recv, int rank, int size, T ident, Op op, T& pre, T& all) {
+    pre = ident;
+    all = ident;
+    for (int r = 0; r < size; ++r) {
+        if (r == rank) pre = all;
+        all = op(all, recv[r]);
+    }
+}
+
+// the same for a reverse scan: over ranks > mine, from the last rank down
+template <class T, class Op>
+__device__ __forceinline__ void fold_rev(const T* recv, int rank, int size, T ident, Op op, T& pre, T& all) {
+    pre = ident;
+    all = ident;
+    for (int r = size - 1; r >= 0; --r) {
+        if (r == rank) pre = all;
+        all = op(all, recv[r]);
+    }
+}
+
+// The same folds by thread 0 into shared memory, read by every thread after
+// a block barrier (keeps the fold's registers out of the callers' peak).
+template <class T, class Op>
+__device__ __forceinline__ void fold_fwd_shared(const T* recv, int rank, int size, T ident, Op op, T* s_pre,
+                                                T* s_all) {
     if (threadIdx.x == 0) {
-        T pre = ident, all = ident;
-        for (int r = 0; r < size; ++r) {
-            if (r < rank) pre = op(pre, recv[r]);
-            all = op(all, recv[r]);
-        }
+        T pre, all;
+        fold_fwd(recv, rank, size, ident, op, pre, all);
         *s_pre = pre;
         *s_all = all;
     }
     __syncthreads();
 }
 
-// the same for a reverse scan: fold of the totals of ranks > mine, taken
-// from the last rank down
 template <class T, class Op>
-__device__ void cluster_fold_rev(cg::cluster_group& cl, T tot, T ident, Op op, T* recv, T* s_pre, T* s_all) {
-    const int rank = cl.block_rank(), size = cl.num_blocks();
-    if (threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = tot;
-    cl.sync();
+__device__ __forceinline__ void fold_rev_shared(const T* recv, int rank, int size, T ident, Op op, T* s_pre,
+                                                T* s_all) {
     if (threadIdx.x == 0) {
-        T pre = ident, all = ident;
-        for (int r = size - 1; r >= 0; --r) {
-            if (r > rank) pre = op(pre, recv[r]);
-            all = op(all, recv[r]);
-        }
+        T pre, all;
+        fold_rev(recv, rank, size, ident, op, pre, all);
         *s_pre = pre;
         *s_all = all;
     }
     __syncthreads();
 }
 
-// cluster-wide AND of a block-uniform flag (push-style, as above)
-__device__ __forceinline__ bool cluster_all(cg::cluster_group& cl, bool v, int* recv, int* s_out) {
-    const int rank = cl.block_rank(), size = cl.num_blocks();
-    if (threadIdx.x < size) *rmt(cl, &recv[rank], threadIdx.x) = v ? 1 : 0;
-    cl.sync();
-    if (threadIdx.x == 0) {
-        int a = 1;
-        for (int r = 0; r < size; ++r) a &= recv[r];
-        *s_out = a;
-    }
-    __syncthreads();
-    return *s_out != 0;
-}
-
-// global sorted position -> (owner rank, local slot address)
+// block-uniform: are the radii rh (this CTA's rings) in order?
 template <int K>
-__device__ __forceinline__ void owner_of(int p, int TK, int* rank, int* addr) {
-    *rank = p / TK;
-    int l = p - *rank * TK;
-    *addr = Swz<K>::at(l);
-}
-
-// number of rings in the cluster with radius < x (strict) or <= x
-template <int K>
-__device__ int cluster_rank(cg::cluster_group& cl, const FastSmem& sm, const float* s_first, int csize, int n,
-                            int TK, float x, bool strict) {
-    int c = -1;
-    for (int r = 0; r < csize; ++r) {
-        float f = s_first[r];
-        if (strict ? (f < x) : (f <= x)) c = r;
+__device__ __forceinline__ bool block_sorted(const float* rh, int nl, int p0) {
+    using SW = Swz<K>;
+    bool ok = true;
+    float prev = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int p = p0 + k;
+        if (p < nl) {
+            float v = rh[SW::at(p)];
+            if (v < prev) ok = false;
+            prev = v;
+        }
     }
-    if (c < 0) return 0;
-    const int nl = min(TK, n - c * TK);
-    const float* rh = rmt(cl, sm.rh, c);
-    return c * TK + ring_rank<K>(rh, nl, x, strict);
+    if (p0 + K < nl && rh[SW::at(p0 + K)] < prev) ok = false;
+    return __syncthreads_and(ok);
 }
 
 // Odd-even merge-split round between neighbour CTAs (left = even ranks when
@@ -190,14 +196,15 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     using SW = Swz<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
-    __shared__ float s_first[16];
-    __shared__ float s_edge[2];  // this CTA's first and last radius
-    __shared__ float4 s_sortv[16];
-    __shared__ int s_gvote[16], s_vote_out;
-    __shared__ Trip<ff> x1_slot[16], x1_pre, x1_all;
-    __shared__ ff x2_slot[16], x2_pre, x2_all;
-    __shared__ Mat2<float> x3f_slot[16], x3f_pre, x3f_all, x3r_slot[16], x3r_pre, x3r_all;
-    __shared__ ff x4f_slot[16], x4f_pre, x4f_all, x4r_slot[16], x4r_pre, x4r_all;
+    __shared__ float4 s_xch[16];   // per rank: (in order?, first radius, last radius, failed the guard?)
+    __shared__ float s_last[16];   // last radius held by every CTA, this slice
+    __shared__ float s_edge[2];    // this CTA's first and last radius (merge rounds)
+    __shared__ int s_vote_out;
+    __shared__ float2 s_nab;       // (a, b) of the next CTA's first region
+    __shared__ Trip<ff> x1[16], f1[2];
+    __shared__ ff x2[16], f2[2];
+    __shared__ Mat2<float> x3f[16], x3r[16], f3[4];
+    __shared__ ff x4f[16], x4r[16], f4[4];
 
     cg::cluster_group cl = cg::this_cluster();
     const int crank = cl.block_rank();
@@ -208,11 +215,11 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     const int tid = threadIdx.x;
     const int n = W.n;
     const int TK = T * K;
-    const int base = crank * TK;            // global position of local slot 0
-    const int nl = max(0, min(TK, n - base));  // rings held by this CTA
-    const int p0 = tid * K;                 // local positions [p0, p0 + K)
+    const int base = crank * TK;               // global position of local slot 0
+    const int nl = max(0, min(TK, n - base));  // rings held by this CTA (>= 1)
+    const int p0 = tid * K;                    // local positions [p0, p0 + K)
     const int cap = TK + 8;
-    const int owner_last = (n - 1) / TK;    // CTA holding the last ring (and region n)
+    const bool last_cta = crank == csize - 1;  // holds the last ring and region n
     const float4* __restrict__ ctab = W.ctab;
 
     unsigned char* sscan = smem;
@@ -229,7 +236,6 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     sm.D = sm.T + cap;
     sm.S = sm.D + cap;
     sm.psi = sm.S + cap;
-    int32_t* t_cnt = reinterpret_cast<int32_t*>(sm.a);
 
     if (tid < CTL_N) s_ctl[tid] = W.ctl[tid];
     __syncthreads();
@@ -251,7 +257,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         sm.fu[a] = W.fur[buf][g];
         sm.id[a] = W.rid[buf][g];
     }
-    cl.sync();
+    __syncthreads();
 
     const double dens_d = W.density, rmax_d = W.rho_max;
     const R rmax = (R)rmax_d;
@@ -270,65 +276,78 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     R s0v[K], s1v[K], hav[K];
     R tv[K];
 
-    for (; slice < s_end; ++slice) {
-        // ---------------- a2: sort by radius if out of order (cluster-wide)
+    bool pending = false;   // the table arrays a, b, T, D, S hold the push of slice - 1
+    bool blk_bad = false;   // this CTA failed the guard at slice - 1
+    int has_prev_before = has_prev;
+
+    for (;;) {
+        // ---------------- exchange: order vote, edges, guard of the push
         {
-            bool ok = true;
-            R prev = -INFINITY;
+            const float* vr = pending ? sm.a : sm.rh;  // the state this slice would start from
+            const bool srt = block_sorted<K>(vr, nl, p0);
+            if (tid < csize)
+                *rmt(cl, &s_xch[crank], tid) =
+                    make_float4(srt ? 1.f : 0.f, vr[SW::at(0)], vr[SW::at(nl - 1)], blk_bad ? 1.f : 0.f);
+        }
+        cl.sync();
+        bool any_bad = false, all_sorted = true;
+        for (int r = 0; r < csize; ++r) {
+            const float4 v = s_xch[r];
+            if (v.w != 0.f) any_bad = true;
+            if (v.x == 0.f) all_sorted = false;
+            if (r + 1 < csize && v.z > s_xch[r + 1].y) all_sorted = false;
+        }
+        if (any_bad) {  // slice - 1 failed the guard: its push is void
+            status = 4;
+            fail = slice - 1;
+            has_prev = has_prev_before;
+            break;
+        }
+        if (pending) {  // commit the push of slice - 1
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 int p = p0 + k;
                 if (p < nl) {
-                    R v = sm.rh[SW::at(p)];
-                    if (v < prev) ok = false;
-                    prev = v;
+                    const int a = SW::at(p);
+                    sm.rh[a] = sm.a[a];
+                    sm.rl[a] = sm.b[a];
+                    sm.u[a] = sm.T[a];
+                    sm.fr[a] = sm.D[a];
+                    sm.fu[a] = sm.S[a];
                 }
             }
-            if (p0 + K < nl && sm.rh[SW::at(p0 + K)] < prev) ok = false;
-            bool blk = __syncthreads_and(ok);
-            // block votes and CTA boundaries: every CTA pushes (vote, first
-            // radius, last radius) into each peer's slot of its rank, one
-            // cluster barrier, then every CTA checks all of them locally
-            if (tid < csize)
-                *rmt(cl, &s_sortv[crank], tid) =
-                    make_float4(blk ? 1.f : 0.f, sm.rh[SW::at(0)], sm.rh[SW::at(nl - 1)], 0.f);
-            cl.sync();
-            if (tid == 0) {
-                int all = 1;
-                for (int r = 0; r < csize; ++r) {
-                    const float4 v = s_sortv[r];
-                    if (v.x == 0.f) all = 0;
-                    if (r + 1 < csize && v.z > s_sortv[r + 1].y) all = 0;
-                }
-                s_vote_out = all;
-            }
+            pending = false;
             __syncthreads();
-            if (!s_vote_out) {
-                // local sort of every CTA's range, then merge-split rounds
-                const int nl_pad = nl < 2 ? 2 : 1 << (32 - __clz(nl - 1));
-                fast_sort<K>(sm, nl, nl_pad, cap);
-                for (int round = 0; round < 2 * csize + 2; ++round) {
-                    if (tid == 0) {
-                        s_edge[0] = sm.rh[SW::at(0)];
-                        s_edge[1] = sm.rh[SW::at(nl - 1)];
-                    }
-                    cl.sync();
-                    if (tid == 0) {
-                        int all = 1;
-                        for (int r = 0; r + 1 < csize; ++r)
-                            if (*rmt(cl, &s_edge[1], r) > *rmt(cl, &s_edge[0], r + 1)) all = 0;
-                        s_vote_out = all;
-                    }
-                    __syncthreads();
-                    const bool sorted = s_vote_out != 0;
-                    cl.sync();  // everyone has read the edges before they change
-                    if (sorted) break;
-                    cluster_merge_round<K>(cl, sm, n, TK, round & 1);
-                }
-            }
         }
-        // replicated first radius of every CTA (for locating a radius)
-        if (tid < csize) s_first[tid] = *rmt(cl, &sm.rh[SW::at(0)], tid);
+        if (slice >= s_end) break;
+
+        // ---------------- a2: sort by radius if out of order (cluster-wide)
+        if (!all_sorted) {
+            // local sort of every CTA's range, then merge-split rounds
+            const int nl_pad = nl < 2 ? 2 : 1 << (32 - __clz(nl - 1));
+            near_sort<K>(sm, nl, nl_pad, cap);
+            for (int round = 0;; ++round) {
+                if (tid == 0) {
+                    s_edge[0] = sm.rh[SW::at(0)];
+                    s_edge[1] = sm.rh[SW::at(nl - 1)];
+                }
+                cl.sync();
+                if (tid == 0) {
+                    int all = 1;
+                    for (int r = 0; r + 1 < csize; ++r)
+                        if (*rmt(cl, &s_edge[1], r) > *rmt(cl, &s_edge[0], r + 1)) all = 0;
+                    s_vote_out = all;
+                }
+                __syncthreads();
+                // (csize rounds sort any order; the bound is a safeguard)
+                if (s_vote_out || round == 2 * csize + 2) break;
+                cl.sync();  // everyone has read the edges before they change
+                cluster_merge_round<K>(cl, sm, n, TK, round & 1);
+            }
+            if (tid < csize) s_last[tid] = *rmt(cl, &s_edge[1], tid);
+        } else if (tid < csize) {
+            s_last[tid] = s_xch[tid].z;
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int p = p0 + k;
@@ -342,9 +361,11 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             }
             ir[k] = __frcp_rn(rh[k]);
         }
-        __syncthreads();
 
         // ---------------- a3: beam particles count into their radial place
+        // (a particle counts at the first ring above it; the particles of
+        // this CTA's rings lie between the previous CTA's last radius and
+        // this CTA's last radius, a contiguous range of the sorted slice)
         int b0 = 0, m = 0;
         R qtot = 0;
         if (W.nb > 0 && slice < n_steps) {
@@ -352,18 +373,18 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             m = W.boff[slice + 1] - b0;
             qtot = W.bTot[slice];
         }
-        if (m > 0) {
+        int32_t* t_cnt = reinterpret_cast<int32_t*>(sm.a);  // the tables are dead here
+        if (m > 0)
             for (int i = tid; i < cap; i += T) t_cnt[i] = 0;
-            cl.sync();
-            for (int q = crank * T + tid; q < m; q += csize * T) {
-                int rk = cluster_rank<K>(cl, sm, s_first, csize, n, TK, W.br[b0 + q], false);
-                if (rk < n) {
-                    int r2, a2;
-                    owner_of<K>(rk, TK, &r2, &a2);
-                    atomicAdd(rmt(cl, &t_cnt[a2], r2), 1);
-                }
+        __syncthreads();  // (also publishes s_last)
+        if (m > 0) {
+            const float* br = W.br + b0;
+            const float lo_r = crank > 0 ? s_last[crank - 1] : -INFINITY, hi_r = s_last[crank];
+            for (int q = tid; q < m; q += T) {
+                const float x = br[q];
+                if (x >= lo_r && x < hi_r) atomicAdd(&t_cnt[SW::at(ring_rank<K>(sm.rh, nl, x, false))], 1);
             }
-            cl.sync();
+            __syncthreads();
         }
 
         // ---------------- a4: scan of (sum w, sum w ln rho, counts)
@@ -384,12 +405,21 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 if (m > 0) cnt += t_cnt[a];
             }
         }
-        Trip<A> tot1;
-        Trip<A> ex1 = block_excl_scan<false>(Trip<A>{sw, sl, cnt}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
-                                             reinterpret_cast<Trip<A>*>(sscan), tot1);
-        cluster_fold_fwd(cl, tot1, Trip<A>{zeroA, zeroA, 0}, OpAddTrip(), x1_slot, &x1_pre, &x1_all);
-        ex1 = OpAddTrip()(x1_pre, ex1);
-        const A Wtot = x1_all.x, Ltot = x1_all.y;
+        Trip<A> ex1;
+        A Wtot, Ltot;
+        {
+            Trip<A> tot1, pre1, all1;
+            ex1 = block_excl_scan<false>(Trip<A>{sw, sl, cnt}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
+                                         reinterpret_cast<Trip<A>*>(sscan), tot1);
+            cluster_push(cl, x1, tot1);
+            cl.sync();
+            fold_fwd_shared(x1, crank, csize, Trip<A>{zeroA, zeroA, 0}, OpAddTrip(), &f1[0], &f1[1]);
+            pre1 = f1[0];
+            all1 = f1[1];
+            ex1 = OpAddTrip()(pre1, ex1);
+            Wtot = all1.x;
+            Ltot = all1.y;
+        }
 
         // ---------------- a5: psi, d_rho psi, psibar, gamma, t; beam field
         A S = ex1.x, L = ex1.y;
@@ -435,11 +465,17 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 pbv[k] = 1.f; ipb[k] = 1.f; dprv[k] = 0.f; tv[k] = 0.f; bbv[k] = 0.f;
             }
         }
-        A Ttot_blk;
-        A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot_blk);
-        cluster_fold_fwd(cl, Ttot_blk, zeroA, OpAdd(), x2_slot, &x2_pre, &x2_all);
-        Tex = ff_acc(x2_pre, Tex);
-        const A Ttot = x2_all;
+        A Tex, Ttot;
+        {
+            A Ttot_blk, pre2;
+            Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot_blk);
+            cluster_push(cl, x2, Ttot_blk);
+            cl.sync();
+            fold_fwd_shared(x2, crank, csize, zeroA, OpAdd(), &f2[0], &f2[1]);
+            pre2 = f2[0];
+            Ttot = f2[1];
+            Tex = ff_acc(pre2, Tex);
+        }
 
         // ---------------- a6 + a7
         Mat2<R> Mf = I2, Mb = I2;
@@ -489,18 +525,26 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         Mat2<R> Yf, Yb;
         block_excl_scan_mat_fwd_rev(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb);
         {
-            // this CTA's block totals: the inclusive fold of its last thread
-            // (forward) and of its thread 0 (reverse), via shared memory
-            Mat2<R>* tmp = reinterpret_cast<Mat2<R>*>(sscan);
-            if (tid == T - 1) tmp[0] = OpMatLeft()(Yf, Mf);
-            if (tid == 0) tmp[1] = OpMatLeft()(Yb, Mb);
-            __syncthreads();
-            Mat2<R> tf = tmp[0], tb = tmp[1];
-            __syncthreads();
-            cluster_fold_fwd(cl, tf, I2, OpMatLeft(), x3f_slot, &x3f_pre, &x3f_all);
-            cluster_fold_rev(cl, tb, I2, OpMatLeft(), x3r_slot, &x3r_pre, &x3r_all);
-            Yf = OpMatLeft()(x3f_pre, Yf);
-            Yb = OpMatLeft()(x3r_pre, Yb);
+            // this CTA's block totals are the inclusive folds of its last
+            // thread (forward) and of its thread 0 (reverse): those threads
+            // push them to every CTA
+            if (tid == T - 1) {
+                const Mat2<R> tf = OpMatLeft()(Yf, Mf);
+                for (int r = 0; r < csize; ++r) *rmt(cl, &x3f[crank], r) = tf;
+            }
+            if (tid == 0) {
+                const Mat2<R> tb = OpMatLeft()(Yb, Mb);
+                for (int r = 0; r < csize; ++r) *rmt(cl, &x3r[crank], r) = tb;
+            }
+            cl.sync();
+            if (tid == 32 % T) {
+                Mat2<R> pre, all;
+                fold_rev(x3r, crank, csize, I2, OpMatLeft(), pre, all);
+                f3[2] = pre;
+            }
+            fold_fwd_shared(x3f, crank, csize, I2, OpMatLeft(), &f3[0], &f3[1]);
+            Yf = OpMatLeft()(f3[0], Yf);
+            Yb = OpMatLeft()(f3[2], Yb);
         }
         R Rra[K], Rrb[K], Dda[K], Ddb[K];
         {
@@ -546,10 +590,23 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         }
         A g_tot, d_tot;
         Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
-        cluster_fold_fwd(cl, d_tot, zeroA, OpAdd(), x4f_slot, &x4f_pre, &x4f_all);
-        cluster_fold_rev(cl, g_tot, zeroA, OpAdd(), x4r_slot, &x4r_pre, &x4r_all);
-        gd.x = ff_acc(x4f_pre, gd.x);
-        gd.y = ff_acc(x4r_pre, gd.y);
+        A all4f;
+        {
+            if (tid < csize) {
+                *rmt(cl, &x4f[crank], tid) = d_tot;
+                *rmt(cl, &x4r[crank], tid) = g_tot;
+            }
+            cl.sync();
+            if (tid == 32 % T) {
+                A pre, all;
+                fold_rev(x4r, crank, csize, zeroA, OpAdd(), pre, all);
+                f4[2] = pre;
+            }
+            fold_fwd_shared(x4f, crank, csize, zeroA, OpAdd(), &f4[0], &f4[1]);
+            all4f = f4[1];
+            gd.x = ff_acc(f4[0], gd.x);
+            gd.y = ff_acc(f4[2], gd.y);
+        }
         {
             R Gk[K];
             A Gsuf = gd.y;
@@ -577,16 +634,18 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                     Dpb = Ddb[k];
                 }
             }
-            if (crank == owner_last && p0 < nl && p0 + K >= nl) {  // region n
+            if (last_cta && p0 < nl && p0 + K >= nl) {  // region n
                 const int a = nl < TK ? SW::at(nl) : TK;
                 sm.a[a] = 0.f;
-                sm.b[a] = ff_to_f(x4f_all);
+                sm.b[a] = ff_to_f(all4f);
                 sm.T[a] = 0.f;
                 sm.D[a] = ff_to_f(ff_acc(Wtot, ff_neg(Imax)));
                 sm.S[a] = ff_to_f(Wtot);
                 sm.psi[a] = 0.f;
             }
         }
+        // the next CTA's first region, for B^(p) at this CTA's last ring
+        if (tid == 0 && crank > 0) *rmt(cl, &s_nab, crank - 1) = make_float2(sm.a[SW::at(0)], sm.b[SW::at(0)]);
         cl.sync();
 
         // ---------------- B^(p) at the rings and the guard
@@ -603,13 +662,13 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                     int a1 = SW::at(p + 1);
                     a1v = sm.a[a1];
                     b1v = sm.b[a1];
-                } else if (base + p + 1 == n) {  // region n, in this CTA
+                } else if (last_cta) {  // region n
                     int a1 = nl < TK ? SW::at(nl) : TK;
                     a1v = sm.a[a1];
                     b1v = sm.b[a1];
                 } else {  // first region of the next CTA
-                    a1v = *rmt(cl, &sm.a[SW::at(0)], crank + 1);
-                    b1v = *rmt(cl, &sm.b[SW::at(0)], crank + 1);
+                    a1v = s_nab.x;
+                    b1v = s_nab.y;
                 }
                 R r = rh[k];
                 bpv[k] = 0.5f * ((sm.a[a] + a1v) * r + (sm.b[a] + b1v) * ir[k]);
@@ -630,20 +689,23 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         }
 
         // ---------------- a9: fields on the beam particles (or query radii)
+        // Region k (radii in (rho_{k-1}, rho_k]) lives in the CTA holding
+        // ring k, region n in the last CTA: this CTA serves the radii in
+        // (previous CTA's last radius, its own last radius].
         {
+            const float lo_r = crank > 0 ? s_last[crank - 1] : -INFINITY;
+            const float hi_r = last_cta ? INFINITY : s_last[crank];
             const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
-            for (int64_t q = crank * T + tid; q < nq; q += (int64_t)csize * T) {
+            for (int64_t q = tid; q < nq; q += T) {
                 R x = mode == MODE_MARCH ? W.br[b0 + q] : (R)W.rq[q];
+                // a radius belongs here if lo_r < x <= hi_r (CTA 0 also
+                // takes a NaN query, which no comparison places)
+                if (!(x > lo_r && x <= hi_r) && !(crank == 0 && x != x)) continue;
                 R psi, dpr, dpz, bp, bb = 0.f;
                 if (x > 0.f) {
-                    const int k = cluster_rank<K>(cl, sm, s_first, csize, n, TK, x, true);
-                    // region k lives in the CTA holding ring k (region n: the
-                    // CTA holding the last ring), at its local index
-                    const int ro = k < n ? k / TK : owner_last;
-                    const FastSmem so = rmt_sm(cl, sm, ro);
-                    const int nl_o = min(TK, n - ro * TK);
-                    fast_fields_region<K>(so, nl_o, TK, k - ro * TK, x, rmax, half_n, quarter_n, Wtot, Imax, c0,
-                                          &dpr, &dpz, &bp, &psi);
+                    const int kl = ring_rank<K>(sm.rh, nl, x, true);
+                    fast_fields_region<K>(sm, nl, TK, kl, x, rmax, half_n, quarter_n, Wtot, Imax, c0, &dpr, &dpz,
+                                          &bp, &psi);
                     if (mode == MODE_MARCH) {
                         bb = W.bQs[b0 + q] * inv_2pi_dxi / x;
                     } else if (m > 0) {
@@ -671,16 +733,12 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 }
             }
         }
-        bad = !cluster_all(cl, !__syncthreads_or(bad), s_gvote, &s_vote_out);
+        blk_bad = __syncthreads_or(bad);  // (every read of the tables is done)
         if (mode != MODE_MARCH) break;
-        if (bad) {
-            status = 4;
-            fail = slice;
-            ++slice;
-            break;
-        }
 
-        // ---------------- a10: AB2 push
+        // ---------------- a10: AB2 push into the table arrays (dead after
+        // a9); it becomes the state at the next exchange unless some CTA
+        // failed the guard
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int p = p0 + k;
@@ -706,18 +764,21 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                     fr = -fr;
                     fu = -fu;
                 }
-                sm.rh[a] = rr.hi;
-                sm.rl[a] = rr.lo;
-                sm.u[a] = un;
-                sm.fr[a] = fr;
-                sm.fu[a] = fu;
+                sm.a[a] = rr.hi;
+                sm.b[a] = rr.lo;
+                sm.T[a] = un;
+                sm.D[a] = fr;
+                sm.S[a] = fu;
             }
         }
+        has_prev_before = has_prev;
         has_prev = 1;
-        cl.sync();
+        pending = true;
+        ++slice;
+        __syncthreads();  // the pushed state is read across threads next
     }
+    cl.sync();  // no CTA leaves while a peer may still touch its shared memory
 
-    cl.sync();
     for (int p = tid; p < nl; p += T) {
         int a = SW::at(p), g = base + p;
         W.rho[buf][g] = sm.rh[a];

@@ -125,6 +125,128 @@ __device__ __noinline__ void fast_sort(const FastSmem& sm, int n, int n_pad, int
     __syncthreads();
 }
 
+// (key, previous position) pairs in the order of the stable sort
+struct KeySrc {
+    float key;
+    int src;
+};
+__device__ __forceinline__ bool ks_less(const KeySrc& a, const KeySrc& b) {
+    return a.key < b.key || (a.key == b.key && a.src < b.src);
+}
+__device__ __forceinline__ void ks_order(KeySrc& a, KeySrc& b) {
+    if (ks_less(b, a)) {
+        KeySrc t = a;
+        a = b;
+        b = t;
+    }
+}
+// sorts v[0, K) ascending (K a power of two): bitonic network, static indices
+template <int K>
+__device__ __forceinline__ void ks_sort(KeySrc (&v)[K]) {
+#pragma unroll
+    for (int k2 = 2; k2 <= K; k2 <<= 1)
+#pragma unroll
+        for (int j = k2 >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    if ((i & k2) == 0) ks_order(v[i], v[l]);
+                    else ks_order(v[l], v[i]);
+                }
+            }
+}
+// v ascending is a bitonic sequence after a half-cleaner: finish it
+template <int K>
+__device__ __forceinline__ void ks_bitonic_finish(KeySrc (&v)[K]) {
+#pragma unroll
+    for (int j = K >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const int l = i ^ j;
+            if (l > i) ks_order(v[i], v[l]);
+        }
+}
+
+// Re-sort of the ring state by (rho, previous position) after a push in
+// which few rings crossed: every thread sorts its K rings in registers, then
+// odd-even merge-split rounds between neighbouring threads' runs move rings
+// K places per round; after kNearRounds without order it falls back to the
+// full bitonic sort.  The permutation is the same as the bitonic sort's:
+// both are the stable sort.
+constexpr int kNearRounds = 8;
+template <int K>
+__device__ __noinline__ void near_sort(const FastSmem& sm, int n, int n_pad, int cap) {
+    using SW = Swz<K>;
+    const int T = blockDim.x, tid = threadIdx.x, p0 = tid * K;
+    float* skey = sm.a;  // scratch: the region tables are dead during the sort
+    int32_t* ssrc = reinterpret_cast<int32_t*>(sm.b);
+    KeySrc v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int p = p0 + k;
+        v[k].key = p < n ? sm.rh[SW::at(p)] : INFINITY;
+        v[k].src = p;
+    }
+    ks_sort<K>(v);
+    bool sorted = false;
+    for (int round = 0; round < kNearRounds; ++round) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            skey[p0 + k] = v[k].key;
+            ssrc[p0 + k] = v[k].src;
+        }
+        __syncthreads();
+        const bool ok = tid + 1 >= T || !ks_less(KeySrc{skey[p0 + K], ssrc[p0 + K]}, v[K - 1]);
+        if (__syncthreads_and(ok)) {
+            sorted = true;
+            break;
+        }
+        const bool left = (tid & 1) == (round & 1);
+        const int partner = left ? tid + 1 : tid - 1;
+        if (partner >= 0 && partner < T) {
+            KeySrc w[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {  // the partner's run, reversed
+                const int q = partner * K + (K - 1 - k);
+                w[k] = KeySrc{skey[q], ssrc[q]};
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {  // half-cleaner: K smallest or K largest
+                const bool lt = ks_less(v[k], w[k]);
+                if (left ? !lt : lt) v[k] = w[k];
+            }
+            ks_bitonic_finish<K>(v);
+        }
+        __syncthreads();
+    }
+    if (!sorted) {
+        fast_sort<K>(sm, n, n_pad, cap);
+        return;
+    }
+    float g_rh[K], g_rl[K], g_u[K], g_fr[K], g_fu[K];
+    int g_id[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (p0 + k < n) {
+            const int a = SW::at(v[k].src);
+            g_rh[k] = sm.rh[a]; g_rl[k] = sm.rl[a]; g_u[k] = sm.u[a];
+            g_fr[k] = sm.fr[a]; g_fu[k] = sm.fu[a]; g_id[k] = sm.id[a];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int p = p0 + k;
+        if (p < n) {
+            const int a = SW::at(p);
+            sm.rh[a] = g_rh[k]; sm.rl[a] = g_rl[k]; sm.u[a] = g_u[k];
+            sm.fr[a] = g_fr[k]; sm.fu[a] = g_fu[k]; sm.id[a] = g_id[k];
+        }
+    }
+    __syncthreads();
+}
+
 // number of sorted rings with radius < x (strict) or <= x
 template <int K>
 __device__ __forceinline__ int ring_rank(const float* rh, int n, float x, bool strict) {
@@ -271,7 +393,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 }
             }
             if (p0 + K < n && sm.rh[SW::at(p0 + K)] < prev) ok = false;
-            if (!__syncthreads_and(ok)) fast_sort<K>(sm, n, W.n_pad, cap);
+            if (!__syncthreads_and(ok)) near_sort<K>(sm, n, W.n_pad, cap);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {

@@ -285,20 +285,49 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     return WAKE_OK;
 }
 
-// The on-chip march: one CTA of up to 512 threads x 4 rings for wakes up to
-// 2048 rings; beyond, a thread-block cluster of ceil(n / 2048) such CTAs
-// (up to 16, the largest cluster GB300 allows).
+// The on-chip march (mixed precision).  Automatic shape: one CTA of up to
+// 512 threads x 4 rings for wakes up to 2048 rings; beyond, a thread-block
+// cluster of ceil(n / 2048) such CTAs (up to 16, the largest cluster GB300
+// allows).  A caller (or the autotuner) may instead fix the rings per thread
+// (4 or 8) and the CTAs per wake; the threads per CTA then follow from n.
 constexpr int32_t kRingsPerCta = 4 * kFastMaxThreads;
 constexpr int32_t kMaxClusterCtas = 16;
-int32_t fast_k_for(int32_t n) { (void)n; return 4; }
-int32_t fast_cl_for(int32_t n) { return (n + kRingsPerCta - 1) / kRingsPerCta; }
 
-int32_t fast_threads_for(int32_t prec, int32_t n) {
-    if (prec != WAKE_MIXED || fast_cl_for(n) > kMaxClusterCtas) return 0;
-    if (fast_cl_for(n) > 1) return kFastMaxThreads;
-    int32_t t = (n + 3) / 4;
+struct FastShape {
+    int32_t threads = 0, k = 4, cl = 1;  // threads == 0: not served by the on-chip march
+};
+
+wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want_cl, FastShape* out) {
+    FastShape f;
+    if (prec != WAKE_MIXED) {
+        if (want_k || want_cl)
+            return fail(WAKE_EINVAL, "wake_init: rings_per_thread and cluster_ctas apply to WAKE_MIXED only");
+        *out = f;
+        return WAKE_OK;
+    }
+    if (want_k != 0 && want_k != 4 && want_k != 8) return fail(WAKE_EINVAL, "wake_init: rings_per_thread must be 0, 4 or 8");
+    if (want_cl < 0 || want_cl > kMaxClusterCtas)
+        return fail(WAKE_EINVAL, "wake_init: cluster_ctas must be in [0, %d]", kMaxClusterCtas);
+    f.k = want_k ? want_k : 4;
+    f.cl = want_cl ? want_cl : (n + f.k * kFastMaxThreads - 1) / (f.k * kFastMaxThreads);
+    if (f.cl > kMaxClusterCtas) {
+        if (want_k || want_cl)
+            return fail(WAKE_EINVAL, "wake_init: %d rings need more than %d CTAs of %d x %d rings", n, kMaxClusterCtas,
+                        kFastMaxThreads, f.k);
+        *out = FastShape{};  // automatic: beyond the on-chip march
+        return WAKE_OK;
+    }
+    const int32_t per_cta = (n + f.cl - 1) / f.cl;
+    int32_t t = (per_cta + f.k - 1) / f.k;
     t = ((t + 31) / 32) * 32;
-    return t < 32 ? 32 : t;
+    f.threads = t < 32 ? 32 : t;
+    if (f.threads > kFastMaxThreads)
+        return fail(WAKE_EINVAL, "wake_init: %d rings do not fit %d CTA(s) of %d threads x %d rings", n, f.cl,
+                    kFastMaxThreads, f.k);
+    if (f.cl > 1 && (int64_t)f.threads * f.k * (f.cl - 1) >= n)
+        return fail(WAKE_EINVAL, "wake_init: %d rings leave the last of %d CTAs empty", n, f.cl);
+    *out = f;
+    return WAKE_OK;
 }
 
 // Auxiliary streams for concurrent batched launches of different kernel
@@ -335,7 +364,7 @@ template <class P>
 wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (h->fast_threads > 0 && h->fast_cl > 1) {
-            WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_cl, h->st));
+            WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->fast_cl, h->st));
             return WAKE_OK;
         }
         if (h->fast_threads > 0) {
@@ -477,7 +506,7 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
         if (fast_threads > 0) {
             if (hs[0]->fast_cl > 1)
                 e = launch_march_cluster(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
-                                         fast_threads, hs[0]->fast_cl, st);
+                                         fast_threads, hs[0]->fast_k, hs[0]->fast_cl, st);
             else
                 e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
                                       fast_threads, hs[0]->fast_k, st);
@@ -740,9 +769,17 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->density = plasma->density;
     h->rho_max = plasma->r_edges[n];
     h->st = static_cast<cudaStream_t>(cuda_stream);
-    h->fast_threads = fast_threads_for(h->prec, n);
-    h->fast_k = fast_k_for(n);
-    h->fast_cl = fast_cl_for(n);
+    FastShape shape;
+    {
+        wake_status fs = fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
+        if (fs != WAKE_OK) {
+            delete h;
+            return fs;
+        }
+    }
+    h->fast_threads = shape.threads;
+    h->fast_k = shape.k;
+    h->fast_cl = shape.cl;
     wake_status s = h->prec == WAKE_FP64 ? init_impl<PrecF64>(h, cfg, plasma, beams, n_beams)
                                          : init_impl<PrecMixed>(h, cfg, plasma, beams, n_beams);
     if (s != WAKE_OK) {

@@ -47,7 +47,8 @@ class wake_beam_desc(C.Structure):
 
 class wake_config(C.Structure):
     _fields_ = [("dxi", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
-                ("flags", C.c_int32), ("block_threads", C.c_int32)]
+                ("flags", C.c_int32), ("block_threads", C.c_int32), ("rings_per_thread", C.c_int32),
+                ("cluster_ctas", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -127,7 +128,7 @@ class Wake:
 
     def __init__(self, edges, beams: Sequence = (), dxi: float = 0.01, n_steps: int = 1000,
                  precision: str = "mixed", density: float = 1.0, flags: int = 0,
-                 block_threads: int = 0, stream=None):
+                 block_threads: int = 0, stream=None, rings_per_thread: int = 0, cluster_ctas: int = 0):
         lib = load()
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32
@@ -142,7 +143,8 @@ class Wake:
             self._keep += [xi, r, w]
             descs[i] = wake_beam_desc(xi.shape[0], _dptr(xi), _dptr(r), _dptr(w), float(b.q))
             self.n_beam += xi.shape[0]
-        cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads))
+        cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads),
+                          int(rings_per_thread), int(cluster_ctas))
         plasma = wake_plasma_desc(self.n_rings, _dptr(self.edges), float(density))
         if stream is None:
             stream = _default_stream()

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2603_16623_gb300 import build as wbuild
@@ -46,3 +47,26 @@ def test_product_does_not_touch_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), f
                 assert "wake_oracle" not in src and "liboracle" not in src, f
+
+
+@pytest.mark.parametrize("precision,n,k,cl,why", [
+    ("mixed", 1000, 5, 0, "rings_per_thread"),
+    ("mixed", 1000, 4, 17, "cluster_ctas"),
+    ("fp64", 1000, 4, 0, "WAKE_MIXED only"),
+    ("mixed", 100, 4, 4, "empty"),
+    ("mixed", 8192, 4, 2, "do not fit"),
+    ("mixed", 70000, 4, 16, "n_rings"),
+])
+def test_launch_shape_is_validated_on_the_host(precision, n, k, cl, why):
+    """Invalid (rings per thread, CTAs per wake) choices fail in wake_init
+    with EINVAL before any device work."""
+    from paper_2603_16623_gb300 import wake as wm
+    lib = wm.load()
+    edges = np.linspace(0.0, 5.0, n + 1)
+    cfg = wm.wake_config(0.01, 10, wm.PRECISION[precision], 0, 0, k, cl)
+    plasma = wm.wake_plasma_desc(n, edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0)
+    h = ctypes.c_void_p()
+    st = lib.wake_init(ctypes.byref(cfg), ctypes.byref(plasma), None, 0, None, ctypes.byref(h))
+    assert st == wm.WAKE_EINVAL
+    assert not h.value
+    assert why in lib.wake_last_error().decode()

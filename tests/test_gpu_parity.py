@@ -76,10 +76,13 @@ def unambiguous(wk, ring_r_ref, ring_r_gpu, margin=5.0):
     return ok
 
 
-def gpu_run(wk, precision, threads=0, dumps=True):
+def gpu_run(wk, precision, threads=0, dumps=True, shape=(0, 0)):
     wm = _wake_mod()
     flags = wm.WAKE_DUMP_RING_FIELDS if dumps else 0
-    g = wm.Wake.from_workload(wk, precision=precision, flags=flags, block_threads=threads)
+    g = wm.Wake.from_workload(wk, precision=precision, flags=flags, block_threads=threads,
+                              rings_per_thread=shape[0], cluster_ctas=shape[1])
+    if shape != (0, 0):
+        assert g.launch_config()[1:] == shape
     st, _, _, _ = g.run()
     out = {"status": st, "progress": g.progress(), "beam": g.beam_fields()}
     if dumps:
@@ -155,9 +158,13 @@ def test_fp64_guard_stops_at_the_oracle_slice():
 # ---------------------------------------------------------------------------
 # mixed path
 # ---------------------------------------------------------------------------
-def _mixed_window_check(wk, threads):
+def _mixed_window_check(wk, threads, shapes=((0, 0),)):
     ref = oracle_run(wk)
-    got = gpu_run(wk, "mixed", threads)
+    for shape in shapes:
+        _mixed_window_compare(wk, ref, gpu_run(wk, "mixed", threads, shape=shape))
+
+
+def _mixed_window_compare(wk, ref, got):
     assert got["status"] == 0
     assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
     ok = unambiguous(wk, ref.rings["r"], got["rings"]["r"])
@@ -189,6 +196,20 @@ def test_mixed_cluster_wakes_match_oracle():
         drv = W.gaussian_beam(40_000, nb0, sr, 0.6, 2.4, seed=n)
         wk = W.Wake(f"cl{n}", W.edges_uniform(n, r_max), [drv], 0.01, 300)
         _mixed_window_check(wk, 0)
+
+
+def test_mixed_explicit_launch_shapes_match_oracle():
+    """Every (rings per thread, CTAs per wake) shape the caller may pick gives
+    the oracle's wake: 8 rings per thread in one CTA, clusters of 2-6 CTAs of
+    4 or 8 rings per thread.  (With n_b0 = 2 and sigma_r = 1 the 6000-ring
+    wake's trajectories part from the oracle's after ~140 slices in every
+    shape alike, the automatic one included: that wake's sensitivity, not a
+    shape's error; hence the milder driver there.)"""
+    for n, nb0, sr, shapes in ((3000, 2.0, 1.0, ((8, 1), (4, 3), (8, 2))),
+                               (6000, 1.0, 0.6, ((8, 2), (4, 6), (8, 3)))):
+        drv = W.gaussian_beam(40_000, nb0, sr, 0.6, 2.4, seed=n)
+        wk = W.Wake(f"shape{n}", W.edges_uniform(n, 6.0), [drv], 0.01, 300)
+        _mixed_window_check(wk, 0, shapes)
 
 
 # ---------------------------------------------------------------------------
