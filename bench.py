@@ -116,8 +116,7 @@ def run_ours(args):
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        for g in gs:
-            g.reset()
+        wm.wake_batch_reset(gs)
         if ev is not None:
             ev[1].record(stream)
         wm.wake_batch_run(gs)
@@ -187,8 +186,7 @@ def run_ours(args):
         lib = load()
 
         def e2e_step():
-            for g, bl in zip(gs, pinned):
-                g.reset(bl)
+            wm.wake_batch_reset(gs, pinned)
             wm.wake_batch_run(gs)
             for g, o in zip(gs, outs):
                 _check(lib.wake_get_beam_fields(g.handle, o["ez"].data_ptr(), o["wr"].data_ptr(), None, None, 0))

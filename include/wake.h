@@ -122,6 +122,15 @@ wake_status wake_init(const wake_config *cfg, const wake_plasma_desc *plasma,
    Errors: EINVAL (different species count or sizes), ECUDA. */
 wake_status wake_reset(wake_handle *h, const wake_beam_desc *beams, int32_t n_beams);
 
+/* wake_reset of n wakes at once (a0/a1 of Sec. II for each), the wakes'
+   preparations running concurrently on the library's auxiliary streams,
+   ordered after the work already queued on the handles' (common) stream and
+   joined back into it.  beams[i] (may be NULL, or beams itself NULL) gives
+   wake i new beam arrays with n_beams[i] species, under wake_reset's rules.
+   Errors: EINVAL (NULL handle, different streams, bad beams), ECUDA. */
+wake_status wake_batch_reset(int32_t n, wake_handle *const *handles, const wake_beam_desc *const *beams,
+                             const int32_t *n_beams);
+
 /* Advances the wake by up to n_slices slices (fewer at the end of the
    window); for each slice: sort, B^(b) at the rings, psi and its derivatives
    (Eqs. dpsi_dr, psi, dpsi_dzeta), u_z and gamma, B^(p) (Eq. ai_bi), fields

@@ -308,10 +308,11 @@ __device__ Pair<T> block_excl_scan_fwd_rev(T fx, T ry, T zero, Pair<T>* sbuf, T&
 }
 
 // Forward product scan of mf and reverse product scan of mr in one pass
-// (op: later element on the left).  sbuf holds 33 Pair<Mat2<R>>.
-template <class R>
-__device__ void block_excl_scan_mat_fwd_rev(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>>* sbuf, Mat2<R>& ef,
-                                            Mat2<R>& er) {
+// (op: later element on the left).  sbuf holds 33 Pair<Mat2<R>>.  With
+// TOT, tf and tr receive the block's forward and reverse products.
+template <bool TOT, class R>
+__device__ __forceinline__ void block_excl_scan_mat_fwd_rev_t(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>>* sbuf,
+                                                              Mat2<R>& ef, Mat2<R>& er, Mat2<R>& tf, Mat2<R>& tr) {
     const Mat2<R> I2 = {1, 0, 0, 1};
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -337,11 +338,24 @@ __device__ void block_excl_scan_mat_fwd_rev(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>
             sbuf[lane].x = qx;
             sbuf[lane].y = qy;
         }
+        if (lane == 31) sbuf[32].x = sx;
+        if (lane == 0) sbuf[32].y = sy;
     }
     __syncthreads();
     ef = OpMatLeft()(sbuf[warp].x, ex);
     er = OpMatLeft()(sbuf[warp].y, ey);
+    if (TOT) {
+        tf = sbuf[32].x;
+        tr = sbuf[32].y;
+    }
     __syncthreads();
+}
+
+template <class R>
+__device__ void block_excl_scan_mat_fwd_rev(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>>* sbuf, Mat2<R>& ef,
+                                            Mat2<R>& er) {
+    Mat2<R> tf, tr;
+    block_excl_scan_mat_fwd_rev_t<false>(mf, mr, sbuf, ef, er, tf, tr);
 }
 
 // first index i in [0, n) with a[i] >= x (n if none)

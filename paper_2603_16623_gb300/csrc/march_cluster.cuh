@@ -131,57 +131,84 @@ __device__ __forceinline__ bool block_sorted(const float* rh, int nl, int p0) {
 // Odd-even merge-split round between neighbour CTAs (left = even ranks when
 // parity 0, odd when 1): each CTA of a pair rebuilds its range from the merge
 // of the two sorted ranges (ties: left first, which keeps the sort stable).
+// Each thread finds its first merged position by a merge-path search and
+// records where its outputs come from; the state is then gathered into the
+// dead region tables (b, T, D, S, psi; ids in registers) and written back
+// once every CTA has read the old ranges.
 template <int K>
 __device__ void cluster_merge_round(cg::cluster_group& cl, const FastSmem& sm, int n, int TK, int parity) {
+    using SW = Swz<K>;
     const int rank = cl.block_rank(), size = cl.num_blocks();
     const int tid = threadIdx.x;
     int left = -1;
     if ((rank & 1) == parity && rank + 1 < size) left = rank;
     else if (rank >= 1 && ((rank - 1) & 1) == parity) left = rank - 1;
-    float g_rh[K], g_rl[K], g_u[K], g_fr[K], g_fu[K];
+    int32_t* code = reinterpret_cast<int32_t*>(sm.a);  // source: i < nA from A, else nA + j from B
     int g_id[K];
     const bool active = left >= 0;
     int my_n = 0;
     if (active) {
         const int nA = min(TK, n - left * TK);
         const int nB = min(TK, n - (left + 1) * TK);
-        FastSmem A = rmt_sm(cl, sm, left), B = rmt_sm(cl, sm, left + 1);
+        const float* Arh = rmt(cl, sm.rh, left);
+        const float* Brh = rmt(cl, sm.rh, left + 1);
         const int off = (rank == left) ? 0 : nA;  // merged position of my local 0
         my_n = (rank == left) ? nA : nB;
-        int d = off + tid * K;
+        const int d = off + tid * K;
         if (tid * K < my_n) {
             // merge path: i = number of A elements among the first d merged
             int lo = max(0, d - nB), hi = min(d, nA);
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
-                if (A.rh[Swz<K>::at(mid)] <= B.rh[Swz<K>::at(d - 1 - mid)]) lo = mid + 1;
+                if (Arh[SW::at(mid)] <= Brh[SW::at(d - 1 - mid)]) lo = mid + 1;
                 else hi = mid;
             }
             int i = lo, j = d - lo;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 if (tid * K + k < my_n) {
-                    bool takeA = i < nA && (j >= nB || A.rh[Swz<K>::at(i)] <= B.rh[Swz<K>::at(j)]);
-                    const FastSmem& S = takeA ? A : B;
-                    int a = Swz<K>::at(takeA ? i : j);
-                    g_rh[k] = S.rh[a]; g_rl[k] = S.rl[a]; g_u[k] = S.u[a];
-                    g_fr[k] = S.fr[a]; g_fu[k] = S.fu[a]; g_id[k] = S.id[a];
+                    const bool takeA = i < nA && (j >= nB || Arh[SW::at(i)] <= Brh[SW::at(j)]);
+                    code[tid * K + k] = takeA ? i : nA + j;
                     if (takeA) ++i;
                     else ++j;
                 }
             }
         }
+        __syncthreads();
+        const FastSmem A = rmt_sm(cl, sm, left), B = rmt_sm(cl, sm, left + 1);
+        for (int l = tid; l < my_n; l += blockDim.x) {
+            const int c = code[l];
+            const FastSmem& S = c < nA ? A : B;
+            const int a = SW::at(c < nA ? c : c - nA);
+            sm.b[l] = S.rh[a];
+            sm.T[l] = S.rl[a];
+            sm.D[l] = S.u[a];
+            sm.S[l] = S.fr[a];
+            sm.psi[l] = S.fu[a];
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = tid * K + k;
+            if (l < my_n) {
+                const int c = code[l];
+                g_id[k] = (c < nA ? A : B).id[SW::at(c < nA ? c : c - nA)];
+            }
+        }
     }
     cl.sync();  // every read of the old ranges is done
     if (active) {
+        for (int l = tid; l < my_n; l += blockDim.x) {
+            const int a = SW::at(l);
+            sm.rh[a] = sm.b[l];
+            sm.rl[a] = sm.T[l];
+            sm.u[a] = sm.D[l];
+            sm.fr[a] = sm.S[l];
+            sm.fu[a] = sm.psi[l];
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            int l = tid * K + k;
-            if (l < my_n) {
-                int a = Swz<K>::at(l);
-                sm.rh[a] = g_rh[k]; sm.rl[a] = g_rl[k]; sm.u[a] = g_u[k];
-                sm.fr[a] = g_fr[k]; sm.fu[a] = g_fu[k]; sm.id[a] = g_id[k];
-            }
+            const int l = tid * K + k;
+            if (l < my_n) sm.id[SW::at(l)] = g_id[k];
         }
     }
     cl.sync();
@@ -325,7 +352,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         if (!all_sorted) {
             // local sort of every CTA's range, then merge-split rounds
             const int nl_pad = nl < 2 ? 2 : 1 << (32 - __clz(nl - 1));
-            near_sort<K>(sm, nl, nl_pad, cap);
+            resort<K>(sm, nl, nl_pad, cap);
             for (int round = 0;; ++round) {
                 if (tid == 0) {
                     s_edge[0] = sm.rh[SW::at(0)];
@@ -523,18 +550,13 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
 
         // ---------------- a8: B_theta^(p)
         Mat2<R> Yf, Yb;
-        block_excl_scan_mat_fwd_rev(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb);
         {
-            // this CTA's block totals are the inclusive folds of its last
-            // thread (forward) and of its thread 0 (reverse): those threads
-            // push them to every CTA
-            if (tid == T - 1) {
-                const Mat2<R> tf = OpMatLeft()(Yf, Mf);
-                for (int r = 0; r < csize; ++r) *rmt(cl, &x3f[crank], r) = tf;
-            }
-            if (tid == 0) {
-                const Mat2<R> tb = OpMatLeft()(Yb, Mb);
-                for (int r = 0; r < csize; ++r) *rmt(cl, &x3r[crank], r) = tb;
+            // this CTA's forward and reverse products go to every CTA
+            Mat2<R> tf, tb;
+            block_excl_scan_mat_fwd_rev_t<true>(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb, tf, tb);
+            if (tid < csize) {
+                *rmt(cl, &x3f[crank], tid) = tf;
+                *rmt(cl, &x3r[crank], tid) = tb;
             }
             cl.sync();
             if (tid == 32 % T) {

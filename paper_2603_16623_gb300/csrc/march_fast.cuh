@@ -71,60 +71,6 @@ struct FastSmem {
     float *a, *b, *T, *D, *S, *psi;  // region tables
 };
 
-// Bitonic sort of the ring state by (rho, previous position): stable with
-// respect to the previous order.  Out of line: it runs only when rings cross.
-template <int K>
-__device__ __noinline__ void fast_sort(const FastSmem& sm, int n, int n_pad, int cap) {
-    using SW = Swz<K>;
-    const int T = blockDim.x, tid = threadIdx.x, p0 = tid * K;
-    float* key = sm.a;  // scratch: the region tables are dead during the sort
-    int32_t* idx = reinterpret_cast<int32_t*>(sm.a + 2 * cap);
-    for (int i = tid; i < n_pad; i += T) {
-        key[i] = i < n ? sm.rh[SW::at(i)] : INFINITY;
-        idx[i] = i;
-    }
-    __syncthreads();
-    for (int k2 = 2; k2 <= n_pad; k2 <<= 1) {
-        for (int j = k2 >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < n_pad; i += T) {
-                int ixj = i ^ j;
-                if (ixj > i) {
-                    float ki = key[i], kj = key[ixj];
-                    int vi = idx[i], vj = idx[ixj];
-                    bool gt = (ki > kj) || (ki == kj && vi > vj);
-                    if (gt == ((i & k2) == 0)) {
-                        key[i] = kj; key[ixj] = ki;
-                        idx[i] = vj; idx[ixj] = vi;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    float g_rh[K], g_rl[K], g_u[K], g_fr[K], g_fu[K];
-    int g_id[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        int p = p0 + k;
-        if (p < n) {
-            int a = SW::at(idx[p]);
-            g_rh[k] = sm.rh[a]; g_rl[k] = sm.rl[a]; g_u[k] = sm.u[a];
-            g_fr[k] = sm.fr[a]; g_fu[k] = sm.fu[a]; g_id[k] = sm.id[a];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        int p = p0 + k;
-        if (p < n) {
-            int a = SW::at(p);
-            sm.rh[a] = g_rh[k]; sm.rl[a] = g_rl[k]; sm.u[a] = g_u[k];
-            sm.fr[a] = g_fr[k]; sm.fu[a] = g_fu[k]; sm.id[a] = g_id[k];
-        }
-    }
-    __syncthreads();
-}
-
 // (key, previous position) pairs in the order of the stable sort
 struct KeySrc {
     float key;
@@ -156,7 +102,7 @@ __device__ __forceinline__ void ks_sort(KeySrc (&v)[K]) {
                 }
             }
 }
-// v ascending is a bitonic sequence after a half-cleaner: finish it
+// a bitonic v (after a half-cleaner) into ascending order
 template <int K>
 __device__ __forceinline__ void ks_bitonic_finish(KeySrc (&v)[K]) {
 #pragma unroll
@@ -168,83 +114,106 @@ __device__ __forceinline__ void ks_bitonic_finish(KeySrc (&v)[K]) {
         }
 }
 
-// Re-sort of the ring state by (rho, previous position) after a push in
-// which few rings crossed: every thread sorts its K rings in registers, then
-// odd-even merge-split rounds between neighbouring threads' runs move rings
-// K places per round; after kNearRounds without order it falls back to the
-// full bitonic sort.  The permutation is the same as the bitonic sort's:
-// both are the stable sort.
+// Re-sort of the ring state by (rho, previous position), i.e. the sort that
+// is stable with respect to the previous order, after a push in which rings
+// crossed.  Every thread sorts its K rings' keys in registers, then odd-even
+// merge-split rounds between neighbouring threads' runs move rings up to K
+// places per round, which suffices when rings crossed by few places; after
+// kNearRounds rounds still out of order, a bitonic sort of the same keys.
+// Either way the permutation is the stable sort's.  Keys and indices live in
+// the dead region tables (a..D) and the state is gathered through S and psi,
+// so that it adds few registers to the march loop.
 constexpr int kNearRounds = 8;
 template <int K>
-__device__ __noinline__ void near_sort(const FastSmem& sm, int n, int n_pad, int cap) {
+__device__ __forceinline__ void resort(const FastSmem& sm, int n, int n_pad, int cap) {
     using SW = Swz<K>;
     const int T = blockDim.x, tid = threadIdx.x, p0 = tid * K;
-    float* skey = sm.a;  // scratch: the region tables are dead during the sort
-    int32_t* ssrc = reinterpret_cast<int32_t*>(sm.b);
-    KeySrc v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int p = p0 + k;
-        v[k].key = p < n ? sm.rh[SW::at(p)] : INFINITY;
-        v[k].src = p;
-    }
-    ks_sort<K>(v);
+    float* key = sm.a;                                         // [n_pad] over a, b
+    int32_t* idx = reinterpret_cast<int32_t*>(sm.a + 2 * cap);  // [n_pad] over T, D
     bool sorted = false;
-    for (int round = 0; round < kNearRounds; ++round) {
+    {
+        KeySrc v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            skey[p0 + k] = v[k].key;
-            ssrc[p0 + k] = v[k].src;
+            const int p = p0 + k;
+            v[k].key = p < n ? sm.rh[SW::at(p)] : INFINITY;
+            v[k].src = p;
+        }
+        ks_sort<K>(v);
+        for (int round = 0; round <= kNearRounds; ++round) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                key[p0 + k] = v[k].key;
+                idx[p0 + k] = v[k].src;
+            }
+            __syncthreads();
+            const bool ok = tid + 1 >= T || !ks_less(KeySrc{key[p0 + K], idx[p0 + K]}, v[K - 1]);
+            if (__syncthreads_and(ok)) {
+                sorted = true;
+                break;
+            }
+            if (round == kNearRounds) break;
+            const bool left = (tid & 1) == (round & 1);
+            const int partner = left ? tid + 1 : tid - 1;
+            if (partner >= 0 && partner < T) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {  // half-cleaner against the partner's run, reversed
+                    const int q = partner * K + (K - 1 - k);
+                    const KeySrc w = {key[q], idx[q]};
+                    const bool lt = ks_less(v[k], w);
+                    if (left ? !lt : lt) v[k] = w;
+                }
+                ks_bitonic_finish<K>(v);
+            }
+            __syncthreads();
+        }
+    }
+    if (!sorted) {  // bitonic sort of (key, index) from the previous order, padded to n_pad
+        for (int i = tid; i < n_pad; i += T) {
+            key[i] = i < n ? sm.rh[SW::at(i)] : INFINITY;
+            idx[i] = i;
         }
         __syncthreads();
-        const bool ok = tid + 1 >= T || !ks_less(KeySrc{skey[p0 + K], ssrc[p0 + K]}, v[K - 1]);
-        if (__syncthreads_and(ok)) {
-            sorted = true;
-            break;
+        for (int k2 = 2; k2 <= n_pad; k2 <<= 1) {
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < n_pad; i += T) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const float ki = key[i], kj = key[ixj];
+                        const int vi = idx[i], vj = idx[ixj];
+                        const bool gt = (ki > kj) || (ki == kj && vi > vj);
+                        if (gt == ((i & k2) == 0)) {
+                            key[i] = kj;
+                            key[ixj] = ki;
+                            idx[i] = vj;
+                            idx[ixj] = vi;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
         }
-        const bool left = (tid & 1) == (round & 1);
-        const int partner = left ? tid + 1 : tid - 1;
-        if (partner >= 0 && partner < T) {
-            KeySrc w[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {  // the partner's run, reversed
-                const int q = partner * K + (K - 1 - k);
-                w[k] = KeySrc{skey[q], ssrc[q]};
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) {  // half-cleaner: K smallest or K largest
-                const bool lt = ks_less(v[k], w[k]);
-                if (left ? !lt : lt) v[k] = w[k];
-            }
-            ks_bitonic_finish<K>(v);
+    }
+    // gather the state into sorted order, two arrays per pass through S, psi
+    float* g0 = sm.S;
+    float* g1 = sm.psi;
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+        float* x0 = pass == 0 ? sm.rh : pass == 1 ? sm.u : sm.fu;
+        float* x1 = pass == 0 ? sm.rl : pass == 1 ? sm.fr : reinterpret_cast<float*>(sm.id);
+        for (int i = tid; i < n; i += T) {
+            const int a = SW::at(idx[i]);
+            g0[i] = x0[a];
+            g1[i] = x1[a];
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += T) {
+            const int a = SW::at(i);
+            x0[a] = g0[i];
+            x1[a] = g1[i];
         }
         __syncthreads();
     }
-    if (!sorted) {
-        fast_sort<K>(sm, n, n_pad, cap);
-        return;
-    }
-    float g_rh[K], g_rl[K], g_u[K], g_fr[K], g_fu[K];
-    int g_id[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (p0 + k < n) {
-            const int a = SW::at(v[k].src);
-            g_rh[k] = sm.rh[a]; g_rl[k] = sm.rl[a]; g_u[k] = sm.u[a];
-            g_fr[k] = sm.fr[a]; g_fu[k] = sm.fu[a]; g_id[k] = sm.id[a];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int p = p0 + k;
-        if (p < n) {
-            const int a = SW::at(p);
-            sm.rh[a] = g_rh[k]; sm.rl[a] = g_rl[k]; sm.u[a] = g_u[k];
-            sm.fr[a] = g_fr[k]; sm.fu[a] = g_fu[k]; sm.id[a] = g_id[k];
-        }
-    }
-    __syncthreads();
 }
 
 // number of sorted rings with radius < x (strict) or <= x
@@ -393,7 +362,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 }
             }
             if (p0 + K < n && sm.rh[SW::at(p0 + K)] < prev) ok = false;
-            if (!__syncthreads_and(ok)) near_sort<K>(sm, n, W.n_pad, cap);
+            if (!__syncthreads_and(ok)) resort<K>(sm, n, W.n_pad, cap);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {

@@ -123,38 +123,70 @@ void free_all(wake_handle* h) {
 // Enqueues the a0/a1 preparation of a wake: control words, ring
 // initialisation, charge folding, nearest-slice binning and per-slice radial
 // sort of the (device-resident) beam, cleared outputs.  Asynchronous.
+// New beam arrays for wake_reset: same species count and sizes as at init.
+wake_status check_new_beams(const wake_handle* h, const wake_beam_desc* beams, int32_t n_beams) {
+    if (!beams) return WAKE_OK;
+    if (n_beams != (int32_t)h->beam_n.size())
+        return fail(WAKE_EINVAL, "wake_reset: %d species given, %zu at init", n_beams, h->beam_n.size());
+    for (int32_t b = 0; b < n_beams; ++b) {
+        if (beams[b].n != h->beam_n[b])
+            return fail(WAKE_EINVAL, "wake_reset: species %d has %lld particles, %lld at init", b,
+                        (long long)beams[b].n, (long long)h->beam_n[b]);
+        if (beams[b].n > 0 && (!beams[b].xi || !beams[b].r || !beams[b].w))
+            return fail(WAKE_EINVAL, "wake_reset: species %d arrays are NULL", b);
+    }
+    return WAKE_OK;
+}
+
+// Enqueues the host-to-device copies of checked new beam arrays on st.
+wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams, cudaStream_t st) {
+    if (!beams) return WAKE_OK;
+    int64_t off = 0;
+    for (int32_t b = 0; b < n_beams; ++b) {
+        const size_t bytes = beams[b].n * sizeof(double);
+        if (beams[b].n > 0) {
+            WK_CUDA(cudaMemcpyAsync(h->d_xi + off, beams[b].xi, bytes, cudaMemcpyHostToDevice, st));
+            WK_CUDA(cudaMemcpyAsync(h->d_r + off, beams[b].r, bytes, cudaMemcpyHostToDevice, st));
+            WK_CUDA(cudaMemcpyAsync(h->d_w + off, beams[b].w, bytes, cudaMemcpyHostToDevice, st));
+        }
+        h->beam_q[b] = beams[b].q;
+        off += beams[b].n;
+    }
+    return WAKE_OK;
+}
+
 template <class P>
-wake_status prepare_impl(wake_handle* h) {
+wake_status prepare_impl(wake_handle* h, cudaStream_t st) {
     using R = typename P::R;
     WakeDev<P> D;
     std::memcpy(&D, h->desc_host.data(), sizeof(D));
     const int32_t n = h->n, ns = h->n_steps;
-    WK_CUDA(launch_reset_ctl(h->d_ctl, h->st));
+    WK_CUDA(launch_reset_ctl(h->d_ctl, st));
     WK_CUDA(launch_ring_init<R>(h->d_edges, n, h->density, const_cast<R*>(D.w), const_cast<R*>(D.wh), D.rho[0],
                                 D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], const_cast<float4*>(D.ctab),
-                                h->st));
+                                st));
     const size_t rb = h->real_bytes();
-    WK_CUDA(cudaMemsetAsync(h->d_boff, 0, ((size_t)ns + 1) * sizeof(int32_t), h->st));
-    WK_CUDA(cudaMemsetAsync(const_cast<R*>(D.bTot), 0, (size_t)ns * rb, h->st));
+    WK_CUDA(cudaMemsetAsync(h->d_boff, 0, ((size_t)ns + 1) * sizeof(int32_t), st));
+    WK_CUDA(cudaMemsetAsync(const_cast<R*>(D.bTot), 0, (size_t)ns * rb, st));
     if (h->nb_total > 0) {
         int64_t off = 0;
         for (size_t b = 0; b < h->beam_n.size(); ++b) {
-            WK_CUDA(launch_fold_charge(h->d_qw + off, h->d_w + off, h->beam_q[b], h->beam_n[b], h->st));
+            WK_CUDA(launch_fold_charge(h->d_qw + off, h->d_w + off, h->beam_q[b], h->beam_n[b], st));
             off += h->beam_n[b];
         }
-        WK_CUDA(cudaMemsetAsync(h->d_cnt, 0, (size_t)ns * sizeof(int32_t), h->st));
-        WK_CUDA(cudaMemsetAsync(h->d_fill, 0, (size_t)ns * sizeof(int32_t), h->st));
-        WK_CUDA(launch_bin_count(h->d_xi, h->nb_total, h->dxi, ns, h->d_slot, h->d_cnt, h->st));
-        WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, h->st));
-        WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, h->d_boff, h->d_fill, h->d_bidx, h->st));
+        WK_CUDA(cudaMemsetAsync(h->d_cnt, 0, (size_t)ns * sizeof(int32_t), st));
+        WK_CUDA(cudaMemsetAsync(h->d_fill, 0, (size_t)ns * sizeof(int32_t), st));
+        WK_CUDA(launch_bin_count(h->d_xi, h->nb_total, h->dxi, ns, h->d_slot, h->d_cnt, st));
+        WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, st));
+        WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, h->d_boff, h->d_fill, h->d_bidx, st));
         WK_CUDA(launch_slice_sort<R>(h->d_boff, ns, h->d_r, h->d_qw, h->d_bidx, const_cast<R*>(D.br),
                                      const_cast<R*>(D.bE), const_cast<R*>(D.bQs), const_cast<R*>(D.bTot),
-                                     kMaxSliceParticles, h->d_ctl, h->st));
+                                     kMaxSliceParticles, h->d_ctl, st));
         for (int k = 0; k < 4; ++k)
-            WK_CUDA(cudaMemsetAsync(h->d_out[k], 0, (size_t)h->nb_total * rb, h->st));
+            WK_CUDA(cudaMemsetAsync(h->d_out[k], 0, (size_t)h->nb_total * rb, st));
     }
     for (int k = 0; k < 7; ++k)
-        if (h->d_dump[k]) WK_CUDA(cudaMemsetAsync(h->d_dump[k], 0, (size_t)ns * n * rb, h->st));
+        if (h->d_dump[k]) WK_CUDA(cudaMemsetAsync(h->d_dump[k], 0, (size_t)ns * n * rb, st));
     return WAKE_OK;
 }
 
@@ -275,7 +307,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     std::memcpy(h->desc_host.data(), &D, sizeof(D));
     WK_TRY(dalloc(h, sizeof(D), &h->d_desc));
     WK_CUDA(cudaMemcpyAsync(h->d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, h->st));
-    WK_TRY(prepare_impl<P>(h));
+    WK_TRY(prepare_impl<P>(h, h->st));
     int32_t ctl[CTL_N];
     WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
     WK_CUDA(cudaStreamSynchronize(h->st));
@@ -795,29 +827,57 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
 
 wake_status wake_reset(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams) {
     WK_TRY(check_handle(h));
-    if (beams) {
-        if (n_beams != (int32_t)h->beam_n.size())
-            return fail(WAKE_EINVAL, "wake_reset: %d species given, %zu at init", n_beams, h->beam_n.size());
-        int64_t off = 0;
-        for (int32_t b = 0; b < n_beams; ++b) {
-            if (beams[b].n != h->beam_n[b])
-                return fail(WAKE_EINVAL, "wake_reset: species %d has %lld particles, %lld at init", b,
-                            (long long)beams[b].n, (long long)h->beam_n[b]);
-            if (beams[b].n > 0 && (!beams[b].xi || !beams[b].r || !beams[b].w))
-                return fail(WAKE_EINVAL, "wake_reset: species %d arrays are NULL", b);
-        }
-        for (int32_t b = 0; b < n_beams; ++b) {
-            size_t bytes = beams[b].n * sizeof(double);
-            if (beams[b].n == 0) continue;
-            WK_CUDA(cudaMemcpyAsync(h->d_xi + off, beams[b].xi, bytes, cudaMemcpyHostToDevice, h->st));
-            WK_CUDA(cudaMemcpyAsync(h->d_r + off, beams[b].r, bytes, cudaMemcpyHostToDevice, h->st));
-            WK_CUDA(cudaMemcpyAsync(h->d_w + off, beams[b].w, bytes, cudaMemcpyHostToDevice, h->st));
-            h->beam_q[b] = beams[b].q;
-            off += beams[b].n;
+    WK_TRY(check_new_beams(h, beams, n_beams));
+    WK_TRY(upload_beams(h, beams, n_beams, h->st));
+    if (h->prec == WAKE_FP64) return prepare_impl<PrecF64>(h, h->st);
+    return prepare_impl<PrecMixed>(h, h->st);
+}
+
+wake_status wake_batch_reset(int32_t n, wake_handle* const* handles, const wake_beam_desc* const* beams,
+                             const int32_t* n_beams) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_reset: bad handle array");
+    if (n == 0) return WAKE_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_reset: handle %d is NULL", i);
+        if (handles[i]->st != handles[0]->st)
+            return fail(WAKE_EINVAL, "wake_batch_reset: handles must share one stream");
+        if (beams && beams[i]) {
+            if (!n_beams) return fail(WAKE_EINVAL, "wake_batch_reset: n_beams is required with beams");
+            WK_TRY(check_new_beams(handles[i], beams[i], n_beams[i]));
         }
     }
-    if (h->prec == WAKE_FP64) return prepare_impl<PrecF64>(h);
-    return prepare_impl<PrecMixed>(h);
+    // each wake's preparation on one of the auxiliary streams, ordered
+    // after the work already queued on the handles' stream and joined back
+    cudaStream_t st = handles[0]->st;
+    cudaEvent_t start;
+    WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    WK_CUDA(cudaEventRecord(start, st));
+    const int32_t n_streams = n < kAuxStreams ? n : kAuxStreams;
+    wake_status res = WAKE_OK;
+    for (int32_t j = 0; j < n_streams; ++j) {
+        cudaStream_t as = nullptr;
+        WK_CUDA(aux_stream(j, &as));
+        WK_CUDA(cudaStreamWaitEvent(as, start, 0));
+    }
+    for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
+        wake_handle* h = handles[i];
+        cudaStream_t as = nullptr;
+        WK_CUDA(aux_stream(i % n_streams, &as));
+        if (beams && beams[i]) res = upload_beams(h, beams[i], n_beams[i], as);
+        if (res == WAKE_OK)
+            res = h->prec == WAKE_FP64 ? prepare_impl<PrecF64>(h, as) : prepare_impl<PrecMixed>(h, as);
+    }
+    for (int32_t j = 0; j < n_streams; ++j) {
+        cudaStream_t as = nullptr;
+        WK_CUDA(aux_stream(j, &as));
+        cudaEvent_t done;
+        WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        WK_CUDA(cudaEventRecord(done, as));
+        WK_CUDA(cudaStreamWaitEvent(st, done, 0));
+        cudaEventDestroy(done);
+    }
+    cudaEventDestroy(start);
+    return res;
 }
 
 wake_status wake_step_slices(wake_handle* h, int32_t n_slices) {

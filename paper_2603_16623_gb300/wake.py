@@ -61,6 +61,7 @@ _SIGS = {
     "wake_get_beam_fields": ([_vp, _vp, _vp, _vp, _vp, C.c_int32], C.c_int),
     "wake_run": ([_vp, _vp, _vp, _vp], C.c_int),
     "wake_batch_run": ([C.c_int32, C.POINTER(_vp)], C.c_int),
+    "wake_batch_reset": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -176,20 +177,7 @@ class Wake:
         if beams is None:
             _check(load().wake_reset(self.handle, None, 0))
             return
-        descs = (wake_beam_desc * max(1, len(beams)))()
-        keep = []
-        for i, b in enumerate(beams):
-            ptrs = []
-            for a in (b.xi, b.r, b.w):
-                if hasattr(a, "data_ptr"):
-                    ptrs.append(C.cast(C.c_void_p(a.data_ptr()), _dp))
-                    n = a.numel()
-                else:
-                    a = _f64(a)
-                    keep.append(a)
-                    ptrs.append(_dptr(a))
-                    n = a.shape[0]
-            descs[i] = wake_beam_desc(n, ptrs[0], ptrs[1], ptrs[2], float(b.q))
+        descs, keep = _beam_descs(beams)
         _check(load().wake_reset(self.handle, descs, len(beams)))
         self._reset_keep = keep
 
@@ -276,6 +264,50 @@ class Wake:
         p = [out[k].ctypes.data if k in out else None for k in keys]
         _check(load().wake_get_ring_dumps(self.handle, *p))
         return out
+
+
+def _beam_descs(beams):
+    """wake_beam_desc array for beams given as numpy arrays (kept alive by the
+    returned list) or pinned torch CPU tensors."""
+    descs = (wake_beam_desc * max(1, len(beams)))()
+    keep = []
+    for i, b in enumerate(beams):
+        ptrs = []
+        n = 0
+        for a in (b.xi, b.r, b.w):
+            if hasattr(a, "data_ptr"):
+                ptrs.append(C.cast(C.c_void_p(a.data_ptr()), _dp))
+                n = a.numel()
+            else:
+                a = _f64(a)
+                keep.append(a)
+                ptrs.append(_dptr(a))
+                n = a.shape[0]
+        descs[i] = wake_beam_desc(n, ptrs[0], ptrs[1], ptrs[2], float(b.q))
+    return descs, keep
+
+
+def wake_batch_reset(wakes: List[Wake], beams: Optional[Sequence] = None):
+    """reset() of many wakes at once, their preparations running concurrently.
+    beams: None, or one entry per wake (None or a beam sequence as in reset)."""
+    n = len(wakes)
+    arr = (_vp * max(1, n))(*[w.handle for w in wakes])
+    if beams is None:
+        _check(load().wake_batch_reset(n, arr, None, None))
+        return
+    dps = (C.POINTER(wake_beam_desc) * max(1, n))()
+    counts = (C.c_int32 * max(1, n))()
+    keep = []
+    for i, bs in enumerate(beams):
+        if bs is None:
+            continue
+        descs, k = _beam_descs(bs)
+        keep += [descs, k]
+        dps[i] = C.cast(descs, C.POINTER(wake_beam_desc))
+        counts[i] = len(bs)
+    _check(load().wake_batch_reset(n, arr, dps, counts))
+    for w in wakes:
+        w._reset_keep = keep
 
 
 def wake_batch_run(wakes: List[Wake]):

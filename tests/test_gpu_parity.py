@@ -374,6 +374,25 @@ def test_batched_launch_equals_alone(precision):
             assert np.array_equal(got[k], bf[k]), k
         st = g.ring_state()
         assert np.array_equal(st[0], rs[0])
+    # a batched reset (with new beams for some wakes, the old ones for the
+    # rest) then a second batched run repeats every wake exactly
+    new_beams = [None] * len(wakes)
+    for i in (1, 4):
+        b = W.gaussian_beam(20_000, 1.5, 0.4, 0.6, 2.4, seed=900 + i)
+        new_beams[i] = [b]
+        wk = wakes[i]
+        g = wm.Wake(wk.edges, [b], wk.dxi, wk.n_steps, precision=precision)
+        g.step_slices(10 ** 6)
+        alone[i] = (g.beam_fields(), g.ring_state(), g.progress())
+        g.close()
+    wm.wake_batch_reset(gs, new_beams)
+    wm.wake_batch_run(gs)
+    for g, (bf, rs, pr) in zip(gs, alone):
+        assert g.progress() == pr
+        got = g.beam_fields()
+        for k in bf:
+            assert np.array_equal(got[k], bf[k]), k
+        assert np.array_equal(g.ring_state()[0], rs[0])
         g.close()
 
 
