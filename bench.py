@@ -94,7 +94,20 @@ def _peaks():
 
 
 def _workload(n_wakes, rank):
+    """Rank r's share: its own n_wakes wakes (weak scaling, no overlap)."""
     return [W.batched_wake(k + 256 * rank) for k in range(n_wakes)]
+
+
+def _reduce_max_sum(tot_ms, ring_slices, device):
+    """Across ranks: the largest timed milliseconds and the total ring-slices."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([tot_ms, float(ring_slices)], device=device, dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm_ = t.clone()
+    dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm_[1])
 
 
 def run_ours(args):
@@ -156,13 +169,7 @@ def run_ours(args):
     prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
     tot_ms = sum(step_ms)
     if ws > 1:
-        t = torch.tensor([tot_ms, float(ring_slices)], device="cuda", dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = t.clone()
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        tot_ms_max = float(mx[0])
-        rs_all = float(sm_[1])
+        tot_ms_max, rs_all = _reduce_max_sum(tot_ms, ring_slices, "cuda")
     else:
         tot_ms_max = tot_ms
         rs_all = float(ring_slices)
