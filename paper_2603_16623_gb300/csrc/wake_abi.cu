@@ -44,7 +44,8 @@ wake_status fail(wake_status st, const char* fmt, ...) {
                         __FILE__, __LINE__);                                                   \
     } while (0)
 
-constexpr int32_t kMaxRings = 8192;
+constexpr int32_t kMaxRings = 8192;           // FP64 path (one CTA per wake, sort in shared memory)
+constexpr int32_t kMaxRingsMixed = 65536;     // mixed path: a 16-CTA cluster of 512 threads x 8 rings
 constexpr int32_t kMaxSliceParticles = 8192;
 constexpr int32_t kDefaultThreads = 256;
 
@@ -320,7 +321,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
 // The on-chip march (mixed precision).  Automatic shape: one CTA of up to
 // 512 threads x 4 rings for wakes up to 2048 rings; beyond, a thread-block
 // cluster of ceil(n / 2048) such CTAs (up to 16, the largest cluster GB300
-// allows).  A caller (or the autotuner) may instead fix the rings per thread
+// allows); beyond 32,768 rings, 8 rings per thread.  A caller (or the autotuner) may instead fix the rings per thread
 // (4 or 8) and the CTAs per wake; the threads per CTA then follow from n.
 constexpr int32_t kRingsPerCta = 4 * kFastMaxThreads;
 constexpr int32_t kMaxClusterCtas = 16;
@@ -340,7 +341,9 @@ wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want
     if (want_k != 0 && want_k != 4 && want_k != 8) return fail(WAKE_EINVAL, "wake_init: rings_per_thread must be 0, 4 or 8");
     if (want_cl < 0 || want_cl > kMaxClusterCtas)
         return fail(WAKE_EINVAL, "wake_init: cluster_ctas must be in [0, %d]", kMaxClusterCtas);
-    f.k = want_k ? want_k : 4;
+    // automatic: 4 rings per thread while a cluster of at most 16 such CTAs
+    // holds the wake, else 8 (up to 16 x 512 x 8 = 65,536 rings)
+    f.k = want_k ? want_k : (n <= kMaxClusterCtas * kRingsPerCta ? 4 : 8);
     f.cl = want_cl ? want_cl : (n + f.k * kFastMaxThreads - 1) / (f.k * kFastMaxThreads);
     if (f.cl > kMaxClusterCtas) {
         if (want_k || want_cl)
@@ -746,8 +749,7 @@ extern "C" {
 const char* wake_last_error(void) { return g_err.c_str(); }
 
 int32_t wake_max_rings(int32_t precision) {
-    (void)precision;
-    return kMaxRings;
+    return precision == WAKE_MIXED ? kMaxRingsMixed : kMaxRings;
 }
 
 int64_t wake_max_slice_particles(int32_t precision) {
@@ -768,7 +770,8 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     if (threads < 64 || threads > 512 || threads % 32)
         return fail(WAKE_EINVAL, "wake_init: block_threads must be a multiple of 32 in [64, 512]");
     const int32_t n = plasma->n_rings;
-    if (n < 1 || n > kMaxRings) return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]", kMaxRings);
+    const int32_t max_rings = wake_max_rings(cfg->precision);
+    if (n < 1 || n > max_rings) return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]", max_rings);
     if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");
     if (!(plasma->density > 0.0) || !std::isfinite(plasma->density))
         return fail(WAKE_EINVAL, "wake_init: density must be > 0");

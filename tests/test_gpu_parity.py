@@ -212,6 +212,31 @@ def test_mixed_explicit_launch_shapes_match_oracle():
         _mixed_window_check(wk, 0, shapes)
 
 
+def test_mixed_large_wake_65536_rings_first_slices():
+    """The 65,536-ring wake (log-spaced down to 1e-5, 2M driver + 2M witness
+    particles, d xi = 0.002) on its automatic shape, a 16-CTA cluster of 512
+    threads x 8 rings: the first 1200 slices (through the driver's centre)
+    against the oracle, ring radii and the fields on every driver particle
+    of those slices."""
+    wm = _wake_mod()
+    wk = W.large_wake(n_steps=1200)
+    ref = oracle.run_wake(wk, ring_dumps=("r",))
+    g = wm.Wake.from_workload(wk, precision="mixed", flags=wm.WAKE_DUMP_RING_R)
+    assert g.launch_config() == (512, 8, 16)
+    st, _, _, _ = g.run()
+    assert st == 0
+    got_r = g.ring_dumps(which=("r",))["r"]
+    assert nerr(got_r, ref.rings["r"]) < MIXED_TOL
+    bf = g.beam_fields()
+    ok = unambiguous(wk, ref.rings["r"], got_r)
+    xi = np.concatenate([b.xi for b in wk.beams])
+    inside = np.floor(xi / wk.dxi + 0.5) < wk.n_steps
+    assert ok[inside].mean() > 0.95
+    for k in ("ez", "wr"):
+        assert nerr(bf[k][ok & inside], ref.beam[k][ok & inside]) < MIXED_TOL, k
+    g.close()
+
+
 # ---------------------------------------------------------------------------
 # one-step parity on chaotic wakes at full size
 # ---------------------------------------------------------------------------
