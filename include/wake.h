@@ -56,8 +56,12 @@ enum { WAKE_FP64 = 0, WAKE_MIXED = 1 };
 /* flags of wake_config */
 enum {
     WAKE_DUMP_RING_R = 1,      /* keep ring radii at the start of every slice  */
-    WAKE_DUMP_RING_FIELDS = 2  /* keep psi, d_rho psi, d_zeta psi, B^(p), B^(b)
+    WAKE_DUMP_RING_FIELDS = 2, /* keep psi, d_rho psi, d_zeta psi, B^(p), B^(b)
                                   and u_r at every ring and slice (tests)      */
+    WAKE_INIT_ASYNC = 4        /* wake_init returns without waiting for the
+                                  device: a slice denser than
+                                  wake_max_slice_particles() is reported by
+                                  wake_get_progress as status WAKE_EINVAL     */
 };
 
 /* Plasma column (Sec. II, ring macroparticles): ring j fills the cell
@@ -172,6 +176,26 @@ wake_status wake_run(wake_handle *h, void *beam_ez, void *beam_wr, void *ring_r)
    the launch was enqueued; per-wake outcome via wake_get_progress. */
 wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
 
+/* Advances every wake by up to max_slices slices (fewer at the end of a
+   window or after a stop), in the launches of wake_batch_run.  With
+   time_budget_ns > 0 each wake's launch also stops at the first slice
+   boundary at least that long after its start (it always does one slice):
+   the step of a continuous-batching loop, whose wakes of different sizes
+   then finish a step together.  Asynchronous on the handles' stream.
+   Errors: EINVAL (NULL handle, mixed precision/stream/block_threads,
+   negative limits), ECUDA. */
+wake_status wake_batch_step(int32_t n, wake_handle *const *handles, int32_t max_slices,
+                            int64_t time_budget_ns);
+
+/* Next slice and status (0, or the WAKE_* code that stopped the wake) of n
+   wakes sharing one stream, with one gather and one synchronisation of that
+   stream.  Errors: EINVAL, ECUDA. */
+wake_status wake_batch_progress(int32_t n, wake_handle *const *handles, int32_t *next_slice,
+                                int32_t *status);
+
+/* Device bytes the handle holds (for admission by a memory budget). */
+wake_status wake_get_device_bytes(wake_handle *h, int64_t *bytes);
+
 /* Progress of a wake (synchronises its stream): next slice to solve,
    status (OK or ENONFINITE) and the failing slice (-1 if none). */
 wake_status wake_get_progress(wake_handle *h, int32_t *next_slice, int32_t *status,
@@ -225,6 +249,9 @@ wake_status wake_get_launch_config(wake_handle *h, int32_t *threads, int32_t *ri
 wake_status wake_fields_at_static(wake_handle *h, int64_t n, const double *r, void *ez, void *wr,
                                   void *bt, void *psi);
 
+/* Releases the handle; its device memory returns to the library's pool in
+   stream order (after the work already queued on the handle's stream), so
+   the call does not wait for the device. */
 void wake_destroy(wake_handle *h);
 
 const char *wake_last_error(void);

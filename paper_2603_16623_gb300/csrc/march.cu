@@ -189,6 +189,20 @@ cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* 
     return launch_fast_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, st);
 }
 
+// (next slice, status) of n wakes into out[2n], one thread per wake
+__global__ void gather_ctl_kernel(const int32_t* const* __restrict__ ctls, int32_t n, int32_t* __restrict__ out) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        out[2 * i] = ctls[i][CTL_NEXT];
+        out[2 * i + 1] = ctls[i][CTL_STATUS];
+    }
+}
+
+cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* out, cudaStream_t st) {
+    gather_ctl_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctls, n, out);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
                              R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st) {

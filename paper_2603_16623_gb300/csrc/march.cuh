@@ -62,7 +62,16 @@ struct WakeDev {
     int64_t nq;
     const double* rq;
     R *q_ez, *q_wr, *q_bt, *q_psi;
+    // > 0: a march launch stops at the first slice boundary this many ns
+    // after its start (on-chip kernels; batched steps of a serving loop)
+    int64_t budget_ns;
 };
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // ion column: enclosed charge n min(x, rho_max)^2 / 2 and its potential
 template <class A, class R>

@@ -21,6 +21,8 @@ cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* 
 cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                  int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
                                  cudaStream_t st);
+// gathers (next slice, status) of n wakes' control words into out[2n]
+cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* out, cudaStream_t st);
 template <class R>
 cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
                              R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st);

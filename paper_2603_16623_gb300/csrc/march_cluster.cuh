@@ -226,7 +226,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     __shared__ float4 s_xch[16];   // per rank: (in order?, first radius, last radius, failed the guard?)
     __shared__ float s_last[16];   // last radius held by every CTA, this slice
     __shared__ float s_edge[2];    // this CTA's first and last radius (merge rounds)
-    __shared__ int s_vote_out;
+    __shared__ int s_vote_out, s_stop;
     __shared__ float2 s_nab;       // (a, b) of the next CTA's first region
     __shared__ Trip<ff> x1[16], f1[2];
     __shared__ ff x2[16], f2[2];
@@ -303,6 +303,8 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     R s0v[K], s1v[K], hav[K];
     R tv[K];
 
+    const int slice0 = slice;
+    uint64_t t_start = 0;
     bool pending = false;   // the table arrays a, b, T, D, S hold the push of slice - 1
     bool blk_bad = false;   // this CTA failed the guard at slice - 1
     int has_prev_before = has_prev;
@@ -310,17 +312,26 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     for (;;) {
         // ---------------- exchange: order vote, edges, guard of the push
         {
+            // time budget: thread 0 of the cluster's rank 0 decides for all
+            // (flag 2 of the exchange); read after block_sorted's barrier
+            if (W.budget_ns > 0 && crank == 0 && tid == 0) {
+                const uint64_t now = global_ns();
+                if (slice == slice0) t_start = now;
+                s_stop = slice > slice0 && now - t_start >= (uint64_t)W.budget_ns;
+            }
             const float* vr = pending ? sm.a : sm.rh;  // the state this slice would start from
             const bool srt = block_sorted<K>(vr, nl, p0);
+            const bool stop = W.budget_ns > 0 && crank == 0 && s_stop;
             if (tid < csize)
-                *rmt(cl, &s_xch[crank], tid) =
-                    make_float4(srt ? 1.f : 0.f, vr[SW::at(0)], vr[SW::at(nl - 1)], blk_bad ? 1.f : 0.f);
+                *rmt(cl, &s_xch[crank], tid) = make_float4(srt ? 1.f : 0.f, vr[SW::at(0)], vr[SW::at(nl - 1)],
+                                                           (blk_bad ? 1.f : 0.f) + (stop ? 2.f : 0.f));
         }
         cl.sync();
         bool any_bad = false, all_sorted = true;
+        const bool stop_now = s_xch[0].w >= 2.f;
         for (int r = 0; r < csize; ++r) {
             const float4 v = s_xch[r];
-            if (v.w != 0.f) any_bad = true;
+            if (v.w == 1.f || v.w == 3.f) any_bad = true;
             if (v.x == 0.f) all_sorted = false;
             if (r + 1 < csize && v.z > s_xch[r + 1].y) all_sorted = false;
         }
@@ -346,7 +357,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             pending = false;
             __syncthreads();
         }
-        if (slice >= s_end) break;
+        if (slice >= s_end || stop_now) break;
 
         // ---------------- a2: sort by radius if out of order (cluster-wide)
         if (!all_sorted) {

@@ -283,6 +283,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
     using SW = Swz<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
+    __shared__ int s_stop;
 
     const WakeDev<PrecMixed>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
     const int T = blockDim.x;
@@ -347,7 +348,15 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
     R s0v[K], s1v[K], hav[K];   // B^(p) ring sources c_p and A_p / 2
     R tv[K];                    // t, then d_zeta psi
 
+    const int slice0 = slice;
+    uint64_t t_start = 0;
     for (; slice < s_end; ++slice) {
+        // time budget (thread 0 decides, read after the order check's barrier)
+        if (W.budget_ns > 0 && tid == 0) {
+            const uint64_t now = global_ns();
+            if (slice == slice0) t_start = now;
+            s_stop = slice > slice0 && now - t_start >= (uint64_t)W.budget_ns;
+        }
         // ---------------- a2: sort by radius if out of order
         {
             bool ok = true;
@@ -362,7 +371,9 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 }
             }
             if (p0 + K < n && sm.rh[SW::at(p0 + K)] < prev) ok = false;
-            if (!__syncthreads_and(ok)) resort<K>(sm, n, W.n_pad, cap);
+            const bool in_order = __syncthreads_and(ok);
+            if (W.budget_ns > 0 && s_stop) break;
+            if (!in_order) resort<K>(sm, n, W.n_pad, cap);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -64,6 +65,7 @@ struct wake_handle {
     cudaStream_t st = nullptr;
     int64_t nb_total = 0;  // beam particles given by the caller
     std::vector<void*> allocs;
+    size_t alloc_bytes = 0;                 // device bytes held (wake_get_device_bytes)
     std::vector<int64_t> beam_n;            // particles per species
     std::vector<double> beam_q;             // charge sign per species
     double *d_edges = nullptr, *d_xi = nullptr, *d_r = nullptr, *d_w = nullptr, *d_qw = nullptr;
@@ -85,15 +87,48 @@ struct wake_handle {
 
 namespace {
 
+// Device memory of the handles comes from one stream-ordered memory pool per
+// device that keeps what is freed (release threshold: unlimited), so that a
+// serving loop creating and destroying wakes allocates at pool speed.
+cudaError_t wake_pool(cudaMemPool_t* out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&pools[dev], &props);
+        if (e != cudaSuccess) {
+            pools[dev] = nullptr;
+            return e;
+        }
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
 wake_status dalloc(wake_handle* h, size_t bytes, void** out) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = wake_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p, bytes, pool, h->st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(WAKE_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return fail(WAKE_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     h->allocs.push_back(p);
+    h->alloc_bytes += bytes;
     e = cudaMemsetAsync(p, 0, bytes, h->st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
     *out = p;
@@ -108,11 +143,12 @@ wake_status dalloc_t(wake_handle* h, size_t count, T** out) {
     return s;
 }
 
+// Returns the handle's memory to the pool, ordered after the work queued on
+// its stream (no host synchronisation).
 void free_all(wake_handle* h) {
-    if (h->st) cudaStreamSynchronize(h->st);
-    else cudaDeviceSynchronize();
-    for (void* p : h->allocs) cudaFree(p);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->st);
     h->allocs.clear();
+    h->alloc_bytes = 0;
 }
 
 #define WK_TRY(expr)                      \
@@ -309,6 +345,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     WK_TRY(dalloc(h, sizeof(D), &h->d_desc));
     WK_CUDA(cudaMemcpyAsync(h->d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, h->st));
     WK_TRY(prepare_impl<P>(h, h->st));
+    if (h->flags & WAKE_INIT_ASYNC) return WAKE_OK;  // a dense slice shows in wake_get_progress
     int32_t ctl[CTL_N];
     WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
     WK_CUDA(cudaStreamSynchronize(h->st));
@@ -515,13 +552,15 @@ wake_status beam_fields_impl(wake_handle* h, void* const outs_user[4], int32_t d
 }
 
 template <class P>
-wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threads, cudaStream_t st) {
+wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threads, cudaStream_t st,
+                         int32_t max_slices, int64_t budget_ns) {
     const int32_t n = (int32_t)hs.size();
     std::vector<WakeDev<P>> descs(n);
     std::vector<int32_t> order(n);
     int32_t n_max = 0, pad_max = 0;
     for (int32_t i = 0; i < n; ++i) {
         std::memcpy(&descs[i], hs[i]->desc_host.data(), sizeof(WakeDev<P>));
+        descs[i].budget_ns = budget_ns;
         order[i] = i;
         n_max = std::max(n_max, hs[i]->n);
         pad_max = std::max(pad_max, hs[i]->n_pad);
@@ -540,10 +579,10 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (fast_threads > 0) {
             if (hs[0]->fast_cl > 1)
-                e = launch_march_cluster(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
+                e = launch_march_cluster(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
                                          fast_threads, hs[0]->fast_k, hs[0]->fast_cl, st);
             else
-                e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH,
+                e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
                                       fast_threads, hs[0]->fast_k, st);
             cudaFreeAsync(d_buf, st);
             if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
@@ -552,7 +591,7 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     }
     int32_t mb_cap = 0;
     size_t smem = march_smem(n_max, pad_max, hs[0]->real_bytes(), kMaxSliceParticles, &mb_cap);
-    e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, 1 << 30, MODE_MARCH, hs[0]->threads,
+    e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH, hs[0]->threads,
                         smem, mb_cap, st);
     cudaFreeAsync(d_buf, st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
@@ -560,7 +599,7 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
 }
 
 template <class P>
-wake_status batch_impl(int32_t n, wake_handle* const* hs) {
+wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, int64_t budget_ns) {
     cudaStream_t st = hs[0]->st;
     // one bucket per kernel configuration, each on its own stream, ordered
     // after the work already queued on the handles' stream and joined back
@@ -577,7 +616,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
         }
         buckets[it - keys.begin()].push_back(hs[i]);
     }
-    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st);
+    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st, max_slices, budget_ns);
     // longest critical path first: slices x rings per CTA of the bucket's
     // longest wake
     std::vector<double> cost(buckets.size(), 0.0);
@@ -598,7 +637,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs) {
         cudaStream_t as = nullptr;
         WK_CUDA(aux_stream((int)(i % kAuxStreams), &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
-        wake_status r = batch_bucket<P>(buckets[b], buckets[b][0]->fast_threads, as);
+        wake_status r = batch_bucket<P>(buckets[b], buckets[b][0]->fast_threads, as, max_slices, budget_ns);
         if (r != WAKE_OK) res = r;
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -934,17 +973,62 @@ wake_status wake_run(wake_handle* h, void* beam_ez, void* beam_wr, void* ring_r)
     return WAKE_OK;
 }
 
-wake_status wake_batch_run(int32_t n, wake_handle* const* handles) {
-    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_run: bad handle array");
-    if (n == 0) return WAKE_OK;
+wake_status wake_batch_step(int32_t n, wake_handle* const* handles, int32_t max_slices, int64_t time_budget_ns) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_step: bad handle array");
+    if (max_slices < 0 || time_budget_ns < 0) return fail(WAKE_EINVAL, "wake_batch_step: negative limit");
+    if (n == 0 || max_slices == 0) return WAKE_OK;
     for (int32_t i = 0; i < n; ++i) {
-        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_run: handle %d is NULL", i);
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_step: handle %d is NULL", i);
         if (handles[i]->prec != handles[0]->prec || handles[i]->st != handles[0]->st ||
             handles[i]->threads != handles[0]->threads)
-            return fail(WAKE_EINVAL, "wake_batch_run: handles must share precision, stream and block_threads");
+            return fail(WAKE_EINVAL, "wake_batch_step: handles must share precision, stream and block_threads");
     }
-    if (handles[0]->prec == WAKE_FP64) return batch_impl<PrecF64>(n, handles);
-    return batch_impl<PrecMixed>(n, handles);
+    if (handles[0]->prec == WAKE_FP64) return batch_impl<PrecF64>(n, handles, max_slices, time_budget_ns);
+    return batch_impl<PrecMixed>(n, handles, max_slices, time_budget_ns);
+}
+
+wake_status wake_batch_run(int32_t n, wake_handle* const* handles) {
+    return wake_batch_step(n, handles, 1 << 30, 0);
+}
+
+wake_status wake_batch_progress(int32_t n, wake_handle* const* handles, int32_t* next_slice, int32_t* status) {
+    if (n < 0 || (n > 0 && (!handles || !next_slice || !status)))
+        return fail(WAKE_EINVAL, "wake_batch_progress: bad arrays");
+    if (n == 0) return WAKE_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_progress: handle %d is NULL", i);
+        if (handles[i]->st != handles[0]->st) return fail(WAKE_EINVAL, "wake_batch_progress: handles must share a stream");
+    }
+    cudaStream_t st = handles[0]->st;
+    std::vector<const int32_t*> ctls(n);
+    for (int32_t i = 0; i < n; ++i) ctls[i] = handles[i]->d_ctl;
+    std::vector<int32_t> out(2 * (size_t)n);
+    void* d = nullptr;
+    const size_t pbytes = sizeof(const int32_t*) * (size_t)n, obytes = sizeof(int32_t) * 2 * (size_t)n;
+    cudaMemPool_t pool = nullptr;
+    WK_CUDA(wake_pool(&pool));
+    WK_CUDA(cudaMallocFromPoolAsync(&d, pbytes + obytes, pool, st));
+    const int32_t** d_ctls = static_cast<const int32_t**>(d);
+    int32_t* d_out = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d) + pbytes);
+    cudaError_t e = cudaMemcpyAsync(d_ctls, ctls.data(), pbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_gather_ctl(d_ctls, n, d_out, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), d_out, obytes, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_batch_progress: %s", cudaGetErrorString(e));
+    for (int32_t i = 0; i < n; ++i) {
+        next_slice[i] = out[2 * (size_t)i];
+        status[i] = out[2 * (size_t)i + 1];
+    }
+    return WAKE_OK;
+}
+
+wake_status wake_get_device_bytes(wake_handle* h, int64_t* bytes) {
+    WK_TRY(check_handle(h));
+    if (!bytes) return fail(WAKE_EINVAL, "wake_get_device_bytes: bytes is NULL");
+    *bytes = (int64_t)h->alloc_bytes;
+    return WAKE_OK;
 }
 
 wake_status wake_get_ring_state(wake_handle* h, double* rho, double* ur, double* f_rho, double* f_ur) {

@@ -1,0 +1,176 @@
+"""Continuous batching of independent wake solves on one GPU.
+
+Requests (a plasma column, beams and a xi window each) arrive over time.  A
+request is admitted as soon as the device-memory budget allows (first come,
+first served); its wake is created on the device without waiting for it
+(WAKE_INIT_ASYNC) and joins the running batch at the next step.  Each step
+advances every admitted wake through one batched launch per launch shape for
+about `step_ns` of device time (wake_batch_step with a time budget, so wakes
+of different sizes end a step together); one gathered progress read per step
+tells which wakes finished (or stopped at a model breakdown).  Finished wakes
+hand back the fields on their beam particles and free their memory, and the
+next requests in line take their place.  Ring state and beams stay on the
+device for the whole solve.
+
+Everything on the device is the library's (libwake.so); this module only
+schedules: admission, steps, retirement and latency bookkeeping.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import wake as wm
+
+
+def estimate_device_bytes(n_rings: int, n_beam: int, n_steps: int) -> int:
+    """Upper bound of the device bytes a mixed-precision wake takes (the
+    arrays wake_init allocates: ~180 B per ring, ~68 B per beam particle,
+    16 B per slice, plus per-allocation rounding)."""
+    return 192 * n_rings + 72 * n_beam + 16 * (n_steps + 1) + (64 << 10)
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float            # seconds on the server clock
+    edges: np.ndarray
+    beams: Sequence           # objects with xi, r, w, q (numpy or pinned torch tensors)
+    dxi: float
+    n_steps: int
+    out_ez: Optional[object] = None   # caller's result buffers (numpy or pinned torch), optional
+    out_wr: Optional[object] = None
+    # filled by the server
+    admitted: float = float("nan")
+    finished: float = float("nan")
+    status: int = -1
+    slices_done: int = 0
+
+    @property
+    def n_rings(self) -> int:
+        return int(self.edges.shape[0] - 1)
+
+    @property
+    def n_beam(self) -> int:
+        return int(sum((b.xi.numel() if hasattr(b.xi, "numel") else b.xi.shape[0]) for b in self.beams))
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class ServeStats:
+    completed: List[Request] = field(default_factory=list)
+    steps: int = 0
+    max_active: int = 0
+    max_queue: int = 0
+    peak_bytes: int = 0
+
+    def summary(self) -> Dict[str, float]:
+        lat = np.array([r.latency for r in self.completed])
+        rs = sum(r.n_rings * r.slices_done for r in self.completed)
+        t0 = min(r.arrival for r in self.completed)
+        t1 = max(r.finished for r in self.completed)
+        return {"requests": len(self.completed), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "ring_slices": int(rs), "ring_slices_per_s": rs / (t1 - t0), "span_s": t1 - t0,
+                "steps": self.steps, "max_active": self.max_active, "max_queue": self.max_queue,
+                "peak_device_bytes": self.peak_bytes,
+                "stopped_by_breakdown": int(sum(r.status == wm.WAKE_ENONFINITE for r in self.completed))}
+
+
+class WakeServer:
+    """Admits, steps and retires wakes; see the module docstring."""
+
+    def __init__(self, memory_budget: int, step_ns: int = 4_000_000, stream=None,
+                 clock: Optional[Callable[[], float]] = None):
+        self.budget = int(memory_budget)
+        self.step_ns = int(step_ns)
+        self.stream = stream
+        self.clock = clock or time.perf_counter
+        self.queue: collections.deque = collections.deque()
+        self.active: List[tuple] = []   # (request, Wake, estimated bytes)
+        self.used = 0
+        self.stats = ServeStats()
+
+    def submit(self, req: Request):
+        self.queue.append(req)
+        self.stats.max_queue = max(self.stats.max_queue, len(self.queue))
+
+    def _admit(self):
+        while self.queue:
+            req = self.queue[0]
+            est = estimate_device_bytes(req.n_rings, req.n_beam, req.n_steps)
+            if self.active and self.used + est > self.budget:
+                break
+            self.queue.popleft()
+            w = wm.Wake(req.edges, req.beams, req.dxi, req.n_steps, precision="mixed",
+                        flags=wm.WAKE_INIT_ASYNC, stream=self.stream)
+            req.admitted = self.clock()
+            self.used += est
+            self.active.append((req, w, est))
+        self.stats.max_active = max(self.stats.max_active, len(self.active))
+        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
+
+    def step(self) -> List[Request]:
+        """One scheduling round: admit, advance, retire.  Returns the
+        requests that finished in this round."""
+        self._admit()
+        if not self.active:
+            return []
+        wakes = [w for _, w, _ in self.active]
+        wm.wake_batch_step(wakes, 1 << 30, self.step_ns)
+        nxt, st = wm.wake_batch_progress(wakes)
+        self.stats.steps += 1
+        done, keep = [], []
+        for (req, w, est), n, s in zip(self.active, nxt, st):
+            if s != 0 or n >= req.n_steps:
+                done.append((req, w, est, int(n), int(s)))
+            else:
+                keep.append((req, w, est))
+        self.active = keep
+        out = []
+        for req, w, est, n, s in done:
+            if req.out_ez is not None or req.out_wr is not None:
+                ptr = lambda a: (a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data) if a is not None else None
+                wm._check(wm.load().wake_get_beam_fields(w.handle, ptr(req.out_ez), ptr(req.out_wr), None, None, 0))
+            req.finished = self.clock()
+            req.status = s
+            req.slices_done = min(n, req.n_steps)
+            w.close()
+            self.used -= est
+            self.stats.completed.append(req)
+            out.append(req)
+        return out
+
+    def idle(self) -> bool:
+        return not self.queue and not self.active
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, n))
+
+
+def run_stream(server: WakeServer, requests: Sequence[Request]) -> ServeStats:
+    """Feeds requests to the server at their arrival times (server clock)
+    and steps until all are done."""
+    pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+    while pending or not server.idle():
+        now = server.clock()
+        while pending and pending[0].arrival <= now:
+            server.submit(pending.popleft())
+        if server.idle():
+            # nothing to do before the next arrival
+            wait = pending[0].arrival - server.clock()
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+            continue
+        server.step()
+    return server.stats

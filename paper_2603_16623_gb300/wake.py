@@ -22,7 +22,7 @@ from . import build as _build
 
 WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENONFINITE, WAKE_ETIMEOUT, WAKE_EBUSY = range(7)
 WAKE_FP64, WAKE_MIXED = 0, 1
-WAKE_DUMP_RING_R, WAKE_DUMP_RING_FIELDS = 1, 2
+WAKE_DUMP_RING_R, WAKE_DUMP_RING_FIELDS, WAKE_INIT_ASYNC = 1, 2, 4
 WAKE_STATIC_MAX_QUERIES = 65536  # queries per wake_fields_at_static call
 PRECISION = {"fp64": WAKE_FP64, "mixed": WAKE_MIXED}
 _STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "EBUSY"}
@@ -62,6 +62,9 @@ _SIGS = {
     "wake_run": ([_vp, _vp, _vp, _vp], C.c_int),
     "wake_batch_run": ([C.c_int32, C.POINTER(_vp)], C.c_int),
     "wake_batch_reset": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
+    "wake_batch_step": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.c_int64], C.c_int),
+    "wake_batch_progress": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
+    "wake_get_device_bytes": ([_vp, C.POINTER(C.c_int64)], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -137,13 +140,12 @@ class Wake:
         self.n_rings = self.edges.shape[0] - 1
         self.n_steps = int(n_steps)
         self._keep = [self.edges]
-        descs = (wake_beam_desc * max(1, len(beams)))()
-        self.n_beam = 0
-        for i, b in enumerate(beams):
-            xi, r, w = _f64(b.xi), _f64(b.r), _f64(b.w)
-            self._keep += [xi, r, w]
-            descs[i] = wake_beam_desc(xi.shape[0], _dptr(xi), _dptr(r), _dptr(w), float(b.q))
-            self.n_beam += xi.shape[0]
+        # beams: numpy arrays, or pinned float64 torch CPU tensors (uploaded
+        # asynchronously: the caller keeps them alive until the stream has
+        # passed wake_init's copies)
+        descs, keep = _beam_descs(beams)
+        self._keep += keep
+        self.n_beam = int(sum(d.n for d in descs[:len(beams)]))
         cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads),
                           int(rings_per_thread), int(cluster_ctas))
         plasma = wake_plasma_desc(self.n_rings, _dptr(self.edges), float(density))
@@ -252,6 +254,11 @@ class Wake:
                                           fr.ctypes.data if fr is not None else None,
                                           fu.ctypes.data if fu is not None else None))
 
+    def device_bytes(self) -> int:
+        b = C.c_int64()
+        _check(load().wake_get_device_bytes(self.handle, C.byref(b)))
+        return int(b.value)
+
     def launch_config(self):
         """(threads per block, rings per thread, blocks per wake)."""
         t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
@@ -308,6 +315,23 @@ def wake_batch_reset(wakes: List[Wake], beams: Optional[Sequence] = None):
     _check(load().wake_batch_reset(n, arr, dps, counts))
     for w in wakes:
         w._reset_keep = keep
+
+
+def wake_batch_step(wakes: List[Wake], max_slices: int, time_budget_ns: int = 0):
+    """Advance every wake by up to max_slices slices (and, with a budget, for
+    about time_budget_ns on the device); asynchronous."""
+    arr = (_vp * max(1, len(wakes)))(*[w.handle for w in wakes])
+    _check(load().wake_batch_step(len(wakes), arr, int(max_slices), int(time_budget_ns)))
+
+
+def wake_batch_progress(wakes: List[Wake]):
+    """(next_slice, status) int32 arrays of the wakes, one synchronisation."""
+    n = len(wakes)
+    arr = (_vp * max(1, n))(*[w.handle for w in wakes])
+    nxt = np.zeros(max(1, n), dtype=np.int32)
+    st = np.zeros(max(1, n), dtype=np.int32)
+    _check(load().wake_batch_progress(n, arr, nxt.ctypes.data, st.ctypes.data))
+    return nxt[:n], st[:n]
 
 
 def wake_batch_run(wakes: List[Wake]):

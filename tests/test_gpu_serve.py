@@ -1,0 +1,106 @@
+"""Continuous batching (paper_2603_16623_gb300/serve.py) on the GPU: every
+request's result is the same alone and in the mix, however it was split
+into steps and whatever shared the device with it."""
+import numpy as np
+import pytest
+
+from paper_2603_16623_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2603_16623_gb300 import wake
+    wake.load()
+    yield
+
+
+def _mix():
+    """Ten wakes of different sizes (one needs a two-CTA cluster) and windows."""
+    out = []
+    for k, (n, steps, nb0) in enumerate([(300, 420, 1.0), (900, 260, 4.0), (2600, 180, 2.0), (64, 500, 0.5),
+                                         (1500, 333, 8.0), (700, 150, 0.2), (1200, 610, 3.0), (450, 90, 1.5),
+                                         (2048, 240, 6.0), (128, 700, 12.0)]):
+        drv = W.gaussian_beam(8_000 + 1000 * k, nb0, 0.3, 0.5, 1.6, seed=700 + k)
+        out.append(W.Wake(f"s{k}", W.edges_uniform(n, 6.0), [drv], 0.01, steps))
+    return out
+
+
+class _Clock:
+    def __init__(self, dt):
+        self.t, self.dt = 0.0, dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def _alone(wk):
+    from paper_2603_16623_gb300 import wake as wm
+    g = wm.Wake.from_workload(wk, precision="mixed")
+    g.step_slices(wk.n_steps)
+    nxt, st, _ = g.progress()
+    bf = g.beam_fields(("ez", "wr"))
+    g.close()
+    return nxt, st, bf
+
+
+def test_served_requests_equal_alone():
+    from paper_2603_16623_gb300 import serve
+    wakes = _mix()
+    ref = [_alone(wk) for wk in wakes]
+    reqs = []
+    for i, wk in enumerate(wakes):
+        arrival = 0.0 if i < 5 else 0.02 * (i - 4)  # a burst, then a trickle
+        reqs.append(serve.Request(rid=i, arrival=arrival, edges=wk.edges, beams=wk.beams, dxi=wk.dxi,
+                                  n_steps=wk.n_steps, out_ez=np.zeros(wk.n_beam, np.float32),
+                                  out_wr=np.zeros(wk.n_beam, np.float32)))
+    # a budget of about three wakes forces queueing; short steps make
+    # requests join and leave the batch mid-flight
+    budget = 3 * max(serve.estimate_device_bytes(w.n_rings, w.n_beam, w.n_steps) for w in wakes)
+    srv = serve.WakeServer(budget, step_ns=300_000, clock=_Clock(0.001))
+    stats = serve.run_stream(srv, reqs)
+    assert len(stats.completed) == len(wakes)
+    assert stats.steps > len(wakes)
+    assert stats.max_queue >= 2
+    for req, wk, (nxt, st, bf) in zip(reqs, wakes, ref):
+        assert req.status == st, req.rid
+        assert req.slices_done == min(nxt, wk.n_steps), req.rid
+        assert np.array_equal(req.out_ez, bf["ez"]), req.rid
+        assert np.array_equal(req.out_wr, bf["wr"]), req.rid
+    s = stats.summary()
+    assert s["requests"] == len(wakes) and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_batch_step_limits_and_progress():
+    from paper_2603_16623_gb300 import wake as wm
+    wakes = _mix()[:6]
+    gs = [wm.Wake.from_workload(wk, precision="mixed") for wk in wakes]
+    wm.wake_batch_step(gs, 7)
+    nxt, st = wm.wake_batch_progress(gs)
+    assert list(nxt) == [min(7, wk.n_steps) for wk in wakes] and not st.any()
+    # a short time budget stops every wake after at least one more slice
+    wm.wake_batch_step(gs, 1 << 30, 50_000)
+    nxt2, st2 = wm.wake_batch_progress(gs)
+    assert all(b > a for a, b in zip(nxt, nxt2))
+    wm.wake_batch_step(gs, 1 << 30)
+    nxt3, st3 = wm.wake_batch_progress(gs)
+    for g, wk, n, s in zip(gs, wakes, nxt3, st3):
+        alone = _alone(wk)
+        assert (n, s) == alone[:2]
+        assert np.array_equal(g.beam_fields(("ez",))["ez"], alone[2]["ez"])
+        g.close()
+
+
+def test_device_bytes_estimate_bounds_the_allocation():
+    from paper_2603_16623_gb300 import serve, wake as wm
+    for wk in _mix()[:4] + [W.batched_wake(5)]:
+        g = wm.Wake.from_workload(wk, precision="mixed", flags=wm.WAKE_INIT_ASYNC)
+        got = g.device_bytes()
+        est = serve.estimate_device_bytes(wk.n_rings, wk.n_beam, wk.n_steps)
+        assert 0 < got <= est, (wk.name, got, est)
+        g.close()
