@@ -175,11 +175,10 @@ def run_ours(args):
         rs_all = float(ring_slices)
     value = rs_all * args.steps / (tot_ms_max / 1e3)
 
-    # ---- end to end through the C ABI with host buffers (pinned), rank-local
-    e2e = None
-    if not args.skip_e2e:
-        pinned = []
-        h2d = 0
+    # pinned host copies of the beams (end-to-end and serving runs)
+    pinned = []
+    h2d = 0
+    if not (args.skip_e2e and args.skip_serve):
         for wk in wakes:
             bl = []
             for b in wk.beams:
@@ -187,6 +186,10 @@ def run_ours(args):
                 bl.append(type("B", (), {"xi": t[0], "r": t[1], "w": t[2], "q": b.q}))
                 h2d += 3 * 8 * b.n
             pinned.append(bl)
+
+    # ---- end to end through the C ABI with host buffers (pinned), rank-local
+    e2e = None
+    if not args.skip_e2e:
         outs = [{k: torch.empty(g.n_beam, dtype=torch.float32).pin_memory() for k in ("ez", "wr")} for g in gs]
         d2h = sum(g.n_beam for g in gs) * 2 * 4
         from paper_2603_16623_gb300.wake import _check, load
@@ -214,6 +217,11 @@ def run_ours(args):
             e2e_s = float(t[0])
         e2e = {"value": rs_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_s * 1e3}
+
+    # ---- serving: Poisson arrivals of batched-workload wakes, continuous batching
+    serving = None
+    if not args.skip_serve:
+        serving = serve_bench(args, wakes, pinned, stream, rank)
 
     # ---- plain FP64 one-wake-per-launch on a bounded sample (the spec denominator)
     plain = None
@@ -266,7 +274,8 @@ def run_ours(args):
                        "ring_slices_per_step": ring_slices, "wakes_stopped_by_breakdown": stopped,
                        "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
             "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + n_march_launches),
-            "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "serving": serving,
+            "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
             "wall_s": wall,
         }
@@ -275,6 +284,40 @@ def run_ours(args):
         g.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def serve_bench(args, wakes, pinned, stream, rank):
+    """Continuous batching under a Poisson stream: requests drawn (seeded) from
+    the batched workload's wakes arrive at args.serve_rate per second; the
+    server admits them under a device-memory budget and steps the running
+    batch; latency = result on the host minus arrival."""
+    import torch
+    from paper_2603_16623_gb300 import serve
+    rng = np.random.Generator(np.random.PCG64(4 + 1000 * rank))
+    n_req = args.serve_requests
+    pick = rng.integers(0, len(wakes), n_req)
+    arrivals = serve.poisson_arrivals(n_req, args.serve_rate, 4 + 1000 * rank)
+    # one pinned result buffer per distinct wake: requests for the same wake
+    # compute the same fields, so they may share it
+    outs = [(torch.empty(wk.n_beam, dtype=torch.float32).pin_memory(),
+             torch.empty(wk.n_beam, dtype=torch.float32).pin_memory()) for wk in wakes]
+    reqs = []
+    for i, (k, t) in enumerate(zip(pick, arrivals)):
+        wk = wakes[int(k)]
+        reqs.append(serve.Request(rid=i, arrival=float(t), edges=wk.edges, beams=pinned[int(k)], dxi=wk.dxi,
+                                  n_steps=wk.n_steps, out_ez=outs[int(k)][0], out_wr=outs[int(k)][1]))
+    t0 = time.perf_counter()
+    srv = serve.WakeServer(int(args.serve_budget_gb * (1 << 30)), step_ns=int(args.serve_step_us * 1e3),
+                           stream=stream.cuda_stream, clock=lambda: time.perf_counter() - t0)
+    stats = serve.run_stream(srv, reqs)
+    torch.cuda.synchronize()
+    out = stats.summary()
+    out.update({"arrival_rate_per_s": args.serve_rate, "memory_budget_gb": args.serve_budget_gb,
+                "step_us": args.serve_step_us,
+                "requests_from": f"{len(wakes)} batched-workload wakes, drawn with seed 4",
+                "offered_ring_slices_per_s": float(sum(wakes[int(k)].n_rings * wakes[int(k)].n_steps
+                                                       for k in pick) / arrivals[-1])})
+    return out
 
 
 def cpu_sample(seconds: float):
@@ -340,6 +383,11 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-step-us", type=float, default=4000.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
