@@ -151,7 +151,7 @@ static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_
 template <int K>
 static cudaError_t launch_cluster_k(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                     int32_t max_slices, int32_t mode, int32_t threads, int32_t cl, cudaStream_t st) {
-    size_t smem = fast_smem_bytes(threads, K);
+    size_t smem = cluster_smem_bytes(threads, K);
     auto kern = march_cluster_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -109,6 +109,12 @@ __device__ __forceinline__ void fold_rev_shared(const T* recv, int rank, int siz
     __syncthreads();
 }
 
+// shared memory of the cluster march: the fast march's arrays plus one
+// array of per-ring beam counts (which other CTAs add into)
+__host__ __device__ inline size_t cluster_smem_bytes(int T, int K) {
+    return fast_smem_bytes(T, K) + 4 * ((size_t)T * K + 8);
+}
+
 // block-uniform: are the radii rh (this CTA's rings) in order?
 template <int K>
 __device__ __forceinline__ bool block_sorted(const float* rh, int nl, int p0) {
@@ -263,6 +269,10 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     sm.D = sm.T + cap;
     sm.S = sm.D + cap;
     sm.psi = sm.S + cap;
+    // beam particles counted at each ring position; zero between uses (other
+    // CTAs add into it in the distributed count)
+    int32_t* cnt_a = reinterpret_cast<int32_t*>(sm.psi + cap);
+    for (int i = tid; i < cap; i += blockDim.x) cnt_a[i] = 0;
 
     if (tid < CTL_N) s_ctl[tid] = W.ctl[tid];
     __syncthreads();
@@ -411,18 +421,89 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             m = W.boff[slice + 1] - b0;
             qtot = W.bTot[slice];
         }
-        int32_t* t_cnt = reinterpret_cast<int32_t*>(sm.a);  // the tables are dead here
-        if (m > 0)
-            for (int i = tid; i < cap; i += T) t_cnt[i] = 0;
-        __syncthreads();  // (also publishes s_last)
-        if (m > 0) {
-            const float* br = W.br + b0;
-            const float lo_r = crank > 0 ? s_last[crank - 1] : -INFINITY, hi_r = s_last[crank];
-            for (int q = tid; q < m; q += T) {
-                const float x = br[q];
-                if (x >= lo_r && x < hi_r) atomicAdd(&t_cnt[SW::at(ring_rank<K>(sm.rh, nl, x, false))], 1);
+        // Two ways, chosen alike by every CTA: when the slice holds at most a
+        // CTA's worth of particles, each CTA counts the particles of its own
+        // rings (those between the previous CTA's last radius and its own);
+        // else the slice's particles are split evenly over the CTAs, which
+        // add into the owning CTA's counts (a cluster barrier then orders the
+        // adds before the scan).  Each thread takes a contiguous run of the
+        // radius-sorted particles, along which ranks and owners only grow,
+        // and adds once per run of particles at the same place.
+        __syncthreads();  // (publishes s_last)
+        // Usually the slice's radii fit the dead region tables: they are
+        // staged there and every thread finds, for each of its rings, how
+        // many particles lie strictly below it (a search for the first ring,
+        // short walks for the next); cnt_a then holds that number itself.
+        const bool staged = m > 0 && m <= kFastArrays / 2 * cap;
+        const bool dist = m > T && csize > 1;
+        if (staged) {
+            float* pr = sm.a;  // a, b, T, D, S, psi: 6 cap contiguous floats
+            for (int i0 = tid; i0 < m; i0 += kPartBatch * T) {
+                float v[kPartBatch];  // loads in flight together
+#pragma unroll
+                for (int j = 0; j < kPartBatch; ++j) v[j] = i0 + j * T < m ? __ldg(W.br + b0 + i0 + j * T) : 0.f;
+#pragma unroll
+                for (int j = 0; j < kPartBatch; ++j)
+                    if (i0 + j * T < m) pr[i0 + j * T] = v[j];
             }
             __syncthreads();
+            int L = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int p = p0 + k;
+                if (p < nl) {
+                    L = k == 0 ? lower_bound_from(pr, m, 0, rh[k]) : lower_bound_from(pr, m, L, rh[k]);
+                    cnt_a[SW::at(p)] = L;
+                }
+            }
+            __syncthreads();  // the staged radii are overwritten from a5 on
+        } else if (m > 0) {
+            const float* br = W.br + b0;
+            const int mc = dist ? (m + csize - 1) / csize : m;
+            const int c0q = dist ? crank * mc : 0;
+            const int c1q = dist ? min(m, c0q + mc) : m;
+            const int per = (c1q - c0q + T - 1) / T;
+            const int q0 = c0q + tid * per, q1 = min(c1q, q0 + per);
+            int o = dist ? 0 : crank;                // owner CTA of the current run
+            const float lo_own = crank > 0 ? s_last[crank - 1] : -INFINITY;
+            int lo = 0, at_lo = -1, cnt = 0;
+            bool past = false;
+            for (int qb = q0; qb < q1 && !past; qb += kPartBatch) {
+                float xb[kPartBatch];  // radii loaded together, then walked
+#pragma unroll
+                for (int j = 0; j < kPartBatch; ++j) xb[j] = qb + j < q1 ? br[qb + j] : INFINITY;
+#pragma unroll
+                for (int j = 0; j < kPartBatch; ++j) {
+                    const float x = xb[j];
+                    if (!dist && !(x >= lo_own)) continue;
+                    // owner: the first CTA whose last radius is above x
+                    int o2 = o;
+                    while (o2 < csize && !(x < s_last[o2])) ++o2;
+                    if (o2 >= csize || (!dist && o2 != crank)) {  // beyond (or outside this CTA)
+                        past = true;
+                        break;
+                    }
+                    if (o2 != o) {
+                        if (cnt) atomicAdd(o == crank ? &cnt_a[SW::at(at_lo)] : rmt(cl, &cnt_a[SW::at(at_lo)], o), cnt);
+                        o = o2;
+                        lo = 0;
+                        at_lo = -1;
+                        cnt = 0;
+                    }
+                    const int nl_o = min(TK, n - o * TK);
+                    const float* rh_o = o == crank ? sm.rh : rmt(cl, sm.rh, o);
+                    lo = ring_rank_from<K>(rh_o, nl_o, lo, x, false);
+                    if (lo != at_lo) {
+                        if (cnt) atomicAdd(o == crank ? &cnt_a[SW::at(at_lo)] : rmt(cl, &cnt_a[SW::at(at_lo)], o), cnt);
+                        at_lo = lo;
+                        cnt = 0;
+                    }
+                    ++cnt;
+                }
+            }
+            if (cnt) atomicAdd(o == crank ? &cnt_a[SW::at(at_lo)] : rmt(cl, &cnt_a[SW::at(at_lo)], o), cnt);
+            if (dist) cl.sync();
+            else __syncthreads();
         }
 
         // ---------------- a4: scan of (sum w, sum w ln rho, counts)
@@ -440,7 +521,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 lp[k] = log1pf(dl * __frcp_rn(c.r0.hi));
                 sw = ff_acc(sw, c.w);
                 sl = ff_acc(sl, ff_acc(c.wl0, ff_two_prod(c.w.hi, lp[k])));
-                if (m > 0) cnt += t_cnt[a];
+                if (m > 0 && !staged) cnt += cnt_a[a];
             }
         }
         Trip<A> ex1;
@@ -468,7 +549,10 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             int p = p0 + k;
             if (p < nl) {
                 const int a = SW::at(p);
-                if (m > 0) lb += t_cnt[a];
+                if (m > 0) {
+                    lb = staged ? cnt_a[a] : lb + cnt_a[a];
+                    cnt_a[a] = 0;  // read for the last time this slice
+                }
                 RingConst c = ring_const(ctab, idv[k]);
                 R r = rh[k], u = ur[k];
                 A rf = {r, sm.rl[a]};
@@ -728,37 +812,92 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         {
             const float lo_r = crank > 0 ? s_last[crank - 1] : -INFINITY;
             const float hi_r = last_cta ? INFINITY : s_last[crank];
-            const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
-            for (int64_t q = tid; q < nq; q += T) {
-                R x = mode == MODE_MARCH ? W.br[b0 + q] : (R)W.rq[q];
-                // a radius belongs here if lo_r < x <= hi_r (CTA 0 also
-                // takes a NaN query, which no comparison places)
-                if (!(x > lo_r && x <= hi_r) && !(crank == 0 && x != x)) continue;
-                R psi, dpr, dpz, bp, bb = 0.f;
-                if (x > 0.f) {
-                    const int kl = ring_rank<K>(sm.rh, nl, x, true);
-                    fast_fields_region<K>(sm, nl, TK, kl, x, rmax, half_n, quarter_n, Wtot, Imax, c0, &dpr, &dpz,
-                                          &bp, &psi);
-                    if (mode == MODE_MARCH) {
-                        bb = W.bQs[b0 + q] * inv_2pi_dxi / x;
-                    } else if (m > 0) {
-                        int l2 = lower_bound_dev(W.br + b0, m, x);
-                        R Q = l2 < m ? W.bE[b0 + l2] : qtot;
-                        bb = Q * inv_2pi_dxi / x;
+            if (mode == MODE_MARCH) {
+                // the particles split as in a3 (own range, or an even share
+                // of the slice with the owner's tables read remotely);
+                // region k (radii in (rho_{k-1}, rho_k]) lives in the CTA
+                // holding ring k, region n in the last CTA
+                const int mc = dist ? (m + csize - 1) / csize : m;
+                const int c0q = dist ? crank * mc : 0;
+                const int c1q = dist ? min(m, c0q + mc) : m;
+                const int per = (c1q - c0q + T - 1) / T;
+                const int q0 = c0q + tid * per, q1 = min(c1q, q0 + per);
+                int o = crank, kr = 0;  // owner of the current run and its tables
+                FastSmem so = sm;
+                int nl_o = nl;
+                bool past = false;
+                for (int qb = q0; qb < q1 && !past; qb += kPartBatch) {
+                  float xb[kPartBatch], qb_s[kPartBatch];  // loaded together, then evaluated
+#pragma unroll
+                  for (int j = 0; j < kPartBatch; ++j) {
+                      xb[j] = qb + j < q1 ? W.br[b0 + qb + j] : INFINITY;
+                      qb_s[j] = qb + j < q1 ? W.bQs[b0 + qb + j] : 0.f;
+                  }
+#pragma unroll
+                  for (int j = 0; j < kPartBatch; ++j) {
+                    const int q = qb + j;
+                    const R x = xb[j];
+                    if (q >= q1) {
+                        past = true;
+                        break;
                     }
-                } else {
-                    psi = ff_to_f(ff_add(Ltot, c0));
-                    dpr = 0.f;
-                    dpz = -ff_to_f(Ttot);
-                    bp = 0.f;
+                    if (!dist && !(x > lo_r)) continue;
+                    int o2 = dist && q == q0 ? 0 : o;  // owners only grow along the run
+                    while (o2 + 1 < csize && !(x <= s_last[o2])) ++o2;
+                    if (!dist && o2 != crank) {
+                        past = true;
+                        break;
+                    }
+                    if (o2 != o) {
+                        o = o2;
+                        so = o == crank ? sm : rmt_sm(cl, sm, o);
+                        nl_o = min(TK, n - o * TK);
+                        kr = 0;
+                    }
+                    R psi, dpr, dpz, bp, bb = 0.f;
+                    if (x > 0.f) {
+                        kr = ring_rank_from<K>(so.rh, nl_o, kr, x, true);
+                        fast_fields_region<K>(so, nl_o, TK, kr, x, rmax, half_n, quarter_n, Wtot, Imax, c0, &dpr,
+                                              &dpz, &bp, &psi);
+                        bb = qb_s[j] * inv_2pi_dxi / x;
+                    } else {
+                        psi = ff_to_f(ff_add(Ltot, c0));
+                        dpr = 0.f;
+                        dpz = -ff_to_f(Ttot);
+                        bp = 0.f;
+                    }
+                    const int64_t o_idx = b0 + q;
+                    W.out_ez[o_idx] = -dpz;
+                    W.out_wr[o_idx] = -dpr;
+                    W.out_bt[o_idx] = bp + bb;
+                    W.out_psi[o_idx] = psi;
+                  }
                 }
-                if (mode == MODE_MARCH) {
-                    int64_t o = b0 + q;
-                    W.out_ez[o] = -dpz;
-                    W.out_wr[o] = -dpr;
-                    W.out_bt[o] = bp + bb;
-                    W.out_psi[o] = psi;
-                } else {
+                // no CTA may overwrite its tables (the push lands there)
+                // while another still reads them
+                if (dist) cl.sync();
+            } else {
+                for (int64_t q = tid; q < W.nq; q += T) {
+                    const R x = (R)W.rq[q];
+                    // a radius belongs here if lo_r < x <= hi_r (CTA 0 also
+                    // takes a NaN query, which no comparison places)
+                    if (!(x > lo_r && x <= hi_r) && !(crank == 0 && x != x)) continue;
+                    R psi, dpr, dpz, bp, bb = 0.f;
+                    if (x > 0.f) {
+                        const int kl = ring_rank<K>(sm.rh, nl, x, true);
+                        fast_fields_region<K>(sm, nl, TK, kl, x, rmax, half_n, quarter_n, Wtot, Imax, c0, &dpr,
+                                              &dpz, &bp, &psi);
+                        if (m > 0) {
+                            int l2 = lower_bound_dev(W.br + b0, m, x);
+                            R Q = l2 < m ? W.bE[b0 + l2] : qtot;
+                            bb = Q * inv_2pi_dxi / x;
+                        }
+                    } else {
+                        psi = ff_to_f(ff_add(Ltot, c0));
+                        dpr = 0.f;
+                        dpz = -ff_to_f(Ttot);
+                        bp = 0.f;
+                    }
                     if (W.q_ez) W.q_ez[q] = -dpz;
                     if (W.q_wr) W.q_wr[q] = -dpr;
                     if (W.q_bt) W.q_bt[q] = bp + bb;

@@ -124,6 +124,8 @@ __device__ __forceinline__ void ks_bitonic_finish(KeySrc (&v)[K]) {
 // the dead region tables (a..D) and the state is gathered through S and psi,
 // so that it adds few registers to the march loop.
 constexpr int kNearRounds = 8;
+// beam particles whose radii (and charges) one thread loads together in a3/a9
+constexpr int kPartBatch = 8;
 template <int K>
 __device__ __forceinline__ void resort(const FastSmem& sm, int n, int n_pad, int cap) {
     using SW = Swz<K>;
@@ -225,6 +227,57 @@ __device__ __forceinline__ int ring_rank(const float* rh, int n, float x, bool s
         int mid = (lo + hi) >> 1;
         float v = rh[SW::at(mid)];
         if (strict ? (v < x) : (v <= x)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Rank of x among the sorted radii rh[0, n) (how many are < x, or <= x when
+// !strict), given a rank `from` that does not exceed it: galloping from
+// `from` (steps 1, 2, 4, ...), then a binary search inside the last step.
+// Along a run of increasing radii successive ranks are close, so this costs
+// O(log distance) instead of O(log n).
+template <int K>
+__device__ __forceinline__ int ring_rank_from(const float* rh, int n, int from, float x, bool strict) {
+    using SW = Swz<K>;
+    auto below = [&](int i) {
+        const float v = rh[SW::at(i)];
+        return strict ? (v < x) : (v <= x);
+    };
+    if (from >= n || !below(from)) return from;
+    int lo = from, step = 1;  // invariant: below(lo)
+    int hi = lo + 1;
+    while (hi < n && below(hi)) {
+        lo = hi;
+        step <<= 1;
+        hi = lo + step;
+    }
+    if (hi > n) hi = n;
+    ++lo;  // the answer is in [lo, hi]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (below(mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// First index i >= from of the sorted a[0, n) with a[i] >= x, given that
+// a[from - 1] < x (or from = 0): galloping then a binary search, as above.
+__device__ __forceinline__ int lower_bound_from(const float* a, int n, int from, float x) {
+    if (from >= n || !(a[from] < x)) return from;
+    int lo = from, step = 1;
+    int hi = lo + 1;
+    while (hi < n && a[hi] < x) {
+        lo = hi;
+        step <<= 1;
+        hi = lo + step;
+    }
+    if (hi > n) hi = n;
+    ++lo;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -400,11 +453,30 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
         if (m > 0) {
             for (int i = tid; i < cap; i += T) t_cnt[i] = 0;
             __syncthreads();
-            for (int q = tid; q < m; q += T) {
-                // the first ring strictly above the particle counts it
-                int lo = ring_rank<K>(sm.rh, n, W.br[b0 + q], false);
-                if (lo < n) atomicAdd(&t_cnt[SW::at(lo)], 1);
+            // the first ring strictly above a particle counts it.  Each
+            // thread takes a contiguous run of the slice's radius-sorted
+            // particles (ranks along it only grow) and adds once per run of
+            // particles at the same place.
+            const int per = (m + T - 1) / T;
+            const int q1 = min(m, (tid + 1) * per);
+            int lo = 0, at_lo = -1, cnt = 0;
+            for (int qb = tid * per; qb < q1 && lo < n; qb += kPartBatch) {
+                float xb[kPartBatch];  // radii loaded together, then walked
+#pragma unroll
+                for (int j = 0; j < kPartBatch; ++j) xb[j] = qb + j < q1 ? W.br[b0 + qb + j] : INFINITY;
+#pragma unroll
+                for (int j = 0; j < kPartBatch; ++j) {
+                    lo = ring_rank_from<K>(sm.rh, n, lo, xb[j], false);
+                    if (lo >= n) break;
+                    if (lo != at_lo) {
+                        if (cnt) atomicAdd(&t_cnt[SW::at(at_lo)], cnt);
+                        at_lo = lo;
+                        cnt = 0;
+                    }
+                    ++cnt;
+                }
             }
+            if (cnt) atomicAdd(&t_cnt[SW::at(at_lo)], cnt);
             __syncthreads();
         }
 
@@ -643,16 +715,50 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
         }
 
         // ---------------- a9: fields on the beam particles (or query radii)
-        {
-            const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
+        if (mode == MODE_MARCH) {
+            // contiguous runs of the radius-sorted particles, as in a3
+            const int per = (m + T - 1) / T;
+            const int q1 = min(m, (tid + 1) * per);
+            int kr = 0;
+            for (int qb = tid * per; qb < q1; qb += kPartBatch) {
+              float xb[kPartBatch], qb_s[kPartBatch];  // loaded together, then evaluated
+#pragma unroll
+              for (int j = 0; j < kPartBatch; ++j) {
+                  xb[j] = qb + j < q1 ? W.br[b0 + qb + j] : 0.f;
+                  qb_s[j] = qb + j < q1 ? W.bQs[b0 + qb + j] : 0.f;
+              }
+#pragma unroll
+              for (int j = 0; j < kPartBatch; ++j) {
+                const int q = qb + j;
+                if (q >= q1) break;
+                const R x = xb[j];
+                R psi, dpr, dpz, bp, bb = 0.f;
+                if (x > 0.f) {
+                    kr = ring_rank_from<K>(sm.rh, n, kr, x, true);
+                    fast_fields_region<K>(sm, n, TK, kr, x, rmax, half_n, quarter_n, Wtot, Imax, c0, &dpr, &dpz,
+                                          &bp, &psi);
+                    bb = qb_s[j] * inv_2pi_dxi / x;
+                } else {
+                    psi = ff_to_f(ff_add(Ltot, c0));
+                    dpr = 0.f;
+                    dpz = -ff_to_f(Ttot);
+                    bp = 0.f;
+                }
+                const int64_t o = b0 + q;
+                W.out_ez[o] = -dpz;
+                W.out_wr[o] = -dpr;
+                W.out_bt[o] = bp + bb;
+                W.out_psi[o] = psi;
+              }
+            }
+        } else {
+            const int64_t nq = W.nq;
             for (int64_t q = tid; q < nq; q += T) {
-                R x = mode == MODE_MARCH ? W.br[b0 + q] : (R)W.rq[q];
+                R x = (R)W.rq[q];
                 R psi, dpr, dpz, bp, bb = 0.f;
                 if (x > 0.f) {
                     fast_fields_at<K>(sm, n, TK, x, rmax, half_n, quarter_n, Wtot, Imax, c0, &dpr, &dpz, &bp, &psi);
-                    if (mode == MODE_MARCH) {
-                        bb = W.bQs[b0 + q] * inv_2pi_dxi / x;
-                    } else if (m > 0) {
+                    if (m > 0) {
                         int l2 = lower_bound_dev(W.br + b0, m, x);
                         R Q = l2 < m ? W.bE[b0 + l2] : qtot;
                         bb = Q * inv_2pi_dxi / x;
@@ -663,18 +769,10 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                     dpz = -ff_to_f(Ttot);
                     bp = 0.f;
                 }
-                if (mode == MODE_MARCH) {
-                    int64_t o = b0 + q;
-                    W.out_ez[o] = -dpz;
-                    W.out_wr[o] = -dpr;
-                    W.out_bt[o] = bp + bb;
-                    W.out_psi[o] = psi;
-                } else {
-                    if (W.q_ez) W.q_ez[q] = -dpz;
-                    if (W.q_wr) W.q_wr[q] = -dpr;
-                    if (W.q_bt) W.q_bt[q] = bp + bb;
-                    if (W.q_psi) W.q_psi[q] = psi;
-                }
+                if (W.q_ez) W.q_ez[q] = -dpz;
+                if (W.q_wr) W.q_wr[q] = -dpr;
+                if (W.q_bt) W.q_bt[q] = bp + bb;
+                if (W.q_psi) W.q_psi[q] = psi;
             }
         }
         bad = __syncthreads_or(bad);
