@@ -370,6 +370,32 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_uniform(args):
+    """A batch of identical wakes (--uniform RINGS,SLICES,COPIES): one batched
+    march, timed with CUDA events; the small, fixed case the kernel profiles
+    are taken on.  Driver: n_b0 = 1, sigma_r = 0.5, sigma_z = 1, 20k particles;
+    uniform rings out to 6; d xi = 0.01."""
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    n, slices, copies = (int(v) for v in args.uniform.split(","))
+    drv = W.gaussian_beam(20_000, 1.0, 0.5, 1.0, 0.5, seed=5)
+    wk = W.Wake(f"uniform{n}", W.edges_uniform(n, 6.0), [drv], 0.01, slices)
+    gs = [wm.Wake.from_workload(wk, precision="mixed") for _ in range(copies)]
+    wm.wake_batch_run(gs)
+    torch.cuda.synchronize()
+    wm.wake_batch_reset(gs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    wm.wake_batch_run(gs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": "uniform", "rings": n, "slices": slices, "copies": copies,
+                      "launch": gs[0].launch_config(), "march_ms": ms, "us_per_slice": ms * 1e3 / slices,
+                      "ring_slices_per_s": n * slices * copies / (ms / 1e3)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,8 +414,11 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-step-us", type=float, default=4000.0)
+    ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.uniform:
+        run_uniform(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -87,7 +87,7 @@ typedef struct {
 
 typedef struct {
     double dxi;               /* slice thickness, > 0                            */
-    int32_t n_steps;          /* slices in the window, >= 1                      */
+    int32_t n_steps;          /* slices in the window, 1..12288                  */
     int32_t precision;        /* WAKE_FP64 or WAKE_MIXED                         */
     int32_t flags;            /* WAKE_DUMP_* bits                                */
     int32_t block_threads;    /* FP64: threads per wake (multiple of 32,

@@ -24,17 +24,29 @@ __global__ void fold_charge_kernel(double* qw, const double* w, double q, int64_
         qw[k] = q * w[k];
 }
 
+// Slice histogram.  Each block takes a contiguous chunk of particles and
+// counts them in shared memory (particles of a beam crowd into the same few
+// hundred slices, so global atomics per particle would serialise), then adds
+// its non-zero bins to the global counts.  n_steps <= kBinSmem.
 __global__ void bin_count_kernel(const double* __restrict__ xi, int64_t n, double dxi, int32_t n_steps,
                                  int32_t* __restrict__ slot, int32_t* __restrict__ cnt) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        double s = floor(__dadd_rn(__ddiv_rn(xi[k], dxi), 0.5));
+    extern __shared__ int32_t hist[];
+    for (int32_t b = threadIdx.x; b < n_steps; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = blockIdx.x * per, k1 = min(n, k0 + per);
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const double s = floor(__dadd_rn(__ddiv_rn(xi[k], dxi), 0.5));
         int32_t sl = -1;
         if (s >= 0.0 && s < (double)n_steps) {
             sl = (int32_t)s;
-            atomicAdd(&cnt[sl], 1);
+            atomicAdd(&hist[sl], 1);
         }
         slot[k] = sl;
     }
+    __syncthreads();
+    for (int32_t b = threadIdx.x; b < n_steps; b += blockDim.x)
+        if (hist[b]) atomicAdd(&cnt[b], hist[b]);
 }
 
 // single block: exclusive scan of cnt[0..n) into off[0..n], off[n] = total
@@ -63,14 +75,33 @@ __global__ void excl_scan_kernel(const int32_t* __restrict__ cnt, int32_t n, int
     }
 }
 
-__global__ void bin_scatter_kernel(const int32_t* __restrict__ slot, int64_t n, const int32_t* __restrict__ off,
-                                   int32_t* __restrict__ fill, int32_t* __restrict__ binned_idx) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        int32_t s = slot[k];
-        if (s >= 0) {
-            int32_t pos = off[s] + atomicAdd(&fill[s], 1);
-            binned_idx[pos] = (int32_t)k;
-        }
+// Particle indices into their slices.  Each block takes the same chunk as
+// in the histogram, ranks its particles within each slice in shared memory,
+// reserves one range per non-empty slice with a single global atomic, and
+// writes every index at its slice offset + range start + local rank.
+__global__ void bin_scatter_kernel(const int32_t* __restrict__ slot, int64_t n, int32_t n_steps,
+                                   const int32_t* __restrict__ off, int32_t* __restrict__ fill,
+                                   int32_t* __restrict__ binned_idx) {
+    extern __shared__ int32_t hist[];  // [n_steps] local counts, then range starts
+    for (int32_t b = threadIdx.x; b < n_steps; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = blockIdx.x * per, k1 = min(n, k0 + per);
+    int32_t rank[kBinPerThread];
+#pragma unroll
+    for (int j = 0; j < kBinPerThread; ++j) {
+        const int64_t k = k0 + threadIdx.x + (int64_t)j * blockDim.x;
+        const int32_t s = k < k1 ? slot[k] : -1;
+        rank[j] = s >= 0 ? atomicAdd(&hist[s], 1) : -1;
+    }
+    __syncthreads();
+    for (int32_t b = threadIdx.x; b < n_steps; b += blockDim.x)
+        if (hist[b]) hist[b] = off[b] + atomicAdd(&fill[b], hist[b]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kBinPerThread; ++j) {
+        const int64_t k = k0 + threadIdx.x + (int64_t)j * blockDim.x;
+        if (rank[j] >= 0) binned_idx[hist[slot[k]] + rank[j]] = (int32_t)k;
     }
 }
 
@@ -180,10 +211,18 @@ cudaError_t launch_fold_charge(double* qw, const double* w, double q, int64_t n,
     return cudaGetLastError();
 }
 
+// blocks of the binning kernels: chunks of kBinPerThread x 256 particles
+static int bin_grid(int64_t n) {
+    const int64_t chunk = (int64_t)kBinPerThread * 256;
+    int64_t g = (n + chunk - 1) / chunk;
+    return (int)(g < 1 ? 1 : g);
+}
+
 cudaError_t launch_bin_count(const double* xi, int64_t n, double dxi, int32_t n_steps, int32_t* slot,
                              int32_t* cnt, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    bin_count_kernel<<<grid_for(n, 256), 256, 0, st>>>(xi, n, dxi, n_steps, slot, cnt);
+    if (n_steps > kBinSmem) return cudaErrorInvalidValue;
+    bin_count_kernel<<<bin_grid(n), 256, (size_t)n_steps * sizeof(int32_t), st>>>(xi, n, dxi, n_steps, slot, cnt);
     return cudaGetLastError();
 }
 
@@ -192,10 +231,12 @@ cudaError_t launch_excl_scan(const int32_t* cnt, int32_t n, int32_t* off, int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, const int32_t* off, int32_t* fill,
+cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, int32_t n_steps, const int32_t* off, int32_t* fill,
                                int32_t* binned_idx, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    bin_scatter_kernel<<<grid_for(n, 256), 256, 0, st>>>(slot, n, off, fill, binned_idx);
+    if (n_steps > kBinSmem) return cudaErrorInvalidValue;
+    bin_scatter_kernel<<<bin_grid(n), 256, (size_t)n_steps * sizeof(int32_t), st>>>(slot, n, n_steps, off, fill,
+                                                                                      binned_idx);
     return cudaGetLastError();
 }
 
@@ -210,12 +251,18 @@ template <class R>
 cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
                               int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t* ctl,
                               cudaStream_t st) {
-    size_t sm = slice_sort_smem(m_pad);
-    cudaError_t e = cudaFuncSetAttribute(slice_sort_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int grid = n_steps < 152 * 4 ? n_steps : 152 * 4;
+    // the attribute allows the largest slice the library accepts; a launch
+    // asks only for its own m_pad (a power of two >= the wake's densest slice)
+    static cudaError_t attr = cudaFuncSetAttribute(slice_sort_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)slice_sort_smem(kSliceSortMaxPad));
+    if (attr != cudaSuccess) return attr;
+    if (m_pad > kSliceSortMaxPad) m_pad = kSliceSortMaxPad;
+    const size_t sm = slice_sort_smem(m_pad);
+    int threads = m_pad / 2;
+    threads = threads < 64 ? 64 : threads > 512 ? 512 : threads;
+    int grid = n_steps < 152 * 8 ? n_steps : 152 * 8;
     if (grid < 1) grid = 1;
-    slice_sort_kernel<R><<<grid, 512, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, ctl);
+    slice_sort_kernel<R><<<grid, threads, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, ctl);
     return cudaGetLastError();
 }
 

@@ -8,9 +8,15 @@ cudaError_t launch_fold_charge(double* qw, const double* w, double q, int64_t n,
 cudaError_t launch_bin_count(const double* xi, int64_t n, double dxi, int32_t n_steps, int32_t* slot,
                              int32_t* cnt, cudaStream_t st);
 cudaError_t launch_excl_scan(const int32_t* cnt, int32_t n, int32_t* off, int32_t* max_count, cudaStream_t st);
-cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, const int32_t* off, int32_t* fill,
+cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, int32_t n_steps, const int32_t* off, int32_t* fill,
                                int32_t* binned_idx, cudaStream_t st);
+// binning: particles per thread of a block's chunk, and the most slices a
+// window may have (the per-block histogram lives in shared memory)
+constexpr int kBinPerThread = 16;
+constexpr int32_t kBinSmem = 48 * 1024 / 4;
 size_t slice_sort_smem(int32_t m_pad);
+// the largest slice the per-slice shared-memory sort takes
+constexpr int32_t kSliceSortMaxPad = 8192;
 cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st);
 template <class R>
 cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,

@@ -82,6 +82,7 @@ struct wake_handle {
     int32_t fast_threads = 0;               // > 0: the on-chip march serves this wake
     int32_t fast_k = 8;                     // its rings per thread
     int32_t fast_cl = 1;                    // CTAs per wake (thread-block cluster if > 1)
+    int32_t slice_max = kMaxSliceParticles; // particles in the densest slice (host count)
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
 };
 
@@ -160,6 +161,19 @@ void free_all(wake_handle* h) {
 // Enqueues the a0/a1 preparation of a wake: control words, ring
 // initialisation, charge folding, nearest-slice binning and per-slice radial
 // sort of the (device-resident) beam, cleared outputs.  Asynchronous.
+// Particles in the densest slice [0, n_steps), counted on the host with the
+// kernels' nearest-slice rule (the same double division and addition).
+int32_t densest_slice(const wake_beam_desc* beams, int32_t n_beams, double dxi, int32_t n_steps) {
+    std::vector<int32_t> cnt((size_t)n_steps, 0);
+    int32_t mx = 0;
+    for (int32_t b = 0; b < n_beams; ++b)
+        for (int64_t k = 0; k < beams[b].n; ++k) {
+            const double s = std::floor(beams[b].xi[k] / dxi + 0.5);
+            if (s >= 0.0 && s < (double)n_steps) mx = std::max(mx, ++cnt[(size_t)s]);
+        }
+    return mx;
+}
+
 // New beam arrays for wake_reset: same species count and sizes as at init.
 wake_status check_new_beams(const wake_handle* h, const wake_beam_desc* beams, int32_t n_beams) {
     if (!beams) return WAKE_OK;
@@ -178,6 +192,7 @@ wake_status check_new_beams(const wake_handle* h, const wake_beam_desc* beams, i
 // Enqueues the host-to-device copies of checked new beam arrays on st.
 wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams, cudaStream_t st) {
     if (!beams) return WAKE_OK;
+    h->slice_max = densest_slice(beams, n_beams, h->dxi, h->n_steps);
     int64_t off = 0;
     for (int32_t b = 0; b < n_beams; ++b) {
         const size_t bytes = beams[b].n * sizeof(double);
@@ -215,10 +230,14 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st) {
         WK_CUDA(cudaMemsetAsync(h->d_fill, 0, (size_t)ns * sizeof(int32_t), st));
         WK_CUDA(launch_bin_count(h->d_xi, h->nb_total, h->dxi, ns, h->d_slot, h->d_cnt, st));
         WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, st));
-        WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, h->d_boff, h->d_fill, h->d_bidx, st));
+        WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, ns, h->d_boff, h->d_fill, h->d_bidx, st));
+        // sort size: a power of two >= the densest slice (a slice beyond
+        // kMaxSliceParticles is flagged by the kernel)
+        const int32_t m_pad = h->slice_max > kMaxSliceParticles ? kMaxSliceParticles
+                                                                 : next_pow2(std::max(h->slice_max, 64));
         WK_CUDA(launch_slice_sort<R>(h->d_boff, ns, h->d_r, h->d_qw, h->d_bidx, const_cast<R*>(D.br),
                                      const_cast<R*>(D.bE), const_cast<R*>(D.bQs), const_cast<R*>(D.bTot),
-                                     kMaxSliceParticles, h->d_ctl, st));
+                                     m_pad, h->d_ctl, st));
         for (int k = 0; k < 4; ++k)
             WK_CUDA(cudaMemsetAsync(h->d_out[k], 0, (size_t)h->nb_total * rb, st));
     }
@@ -804,7 +823,8 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     if (cfg->precision != WAKE_FP64 && cfg->precision != WAKE_MIXED)
         return fail(WAKE_EINVAL, "wake_init: unknown precision %d", cfg->precision);
     if (!(cfg->dxi > 0.0) || !std::isfinite(cfg->dxi)) return fail(WAKE_EINVAL, "wake_init: dxi must be > 0");
-    if (cfg->n_steps < 1) return fail(WAKE_EINVAL, "wake_init: n_steps must be >= 1");
+    if (cfg->n_steps < 1 || cfg->n_steps > kBinSmem)
+        return fail(WAKE_EINVAL, "wake_init: n_steps must be in [1, %d]", (int)kBinSmem);
     int32_t threads = cfg->block_threads ? cfg->block_threads : kDefaultThreads;
     if (threads < 64 || threads > 512 || threads % 32)
         return fail(WAKE_EINVAL, "wake_init: block_threads must be a multiple of 32 in [64, 512]");
@@ -854,6 +874,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->fast_threads = shape.threads;
     h->fast_k = shape.k;
     h->fast_cl = shape.cl;
+    h->slice_max = densest_slice(beams, n_beams, cfg->dxi, cfg->n_steps);
     wake_status s = h->prec == WAKE_FP64 ? init_impl<PrecF64>(h, cfg, plasma, beams, n_beams)
                                          : init_impl<PrecMixed>(h, cfg, plasma, beams, n_beams);
     if (s != WAKE_OK) {
