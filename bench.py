@@ -110,6 +110,15 @@ def _reduce_max_sum(tot_ms, ring_slices, device):
     return float(mx[0]), float(sm_[1])
 
 
+def _shape(n_rings, args):
+    """Launch shape of a wake: the library's automatic one, or with
+    --rings-per-cta R, clusters of ceil(n / R) CTAs of 4 rings per thread."""
+    if not args.rings_per_cta or n_rings <= 2048:
+        return {}
+    cl = -(-n_rings // args.rings_per_cta)
+    return {"rings_per_thread": 4, "cluster_ctas": cl} if cl <= 16 else {}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -121,7 +130,8 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
     wakes = _workload(args.n_wakes, rank)
-    gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream) for wk in wakes]
+    gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream, **_shape(wk.n_rings, args))
+          for wk in wakes]
     torch.cuda.synchronize()
     # one march launch per distinct (threads, rings per thread, blocks per wake)
     n_march_launches = len({g.launch_config() for g in gs})
@@ -192,14 +202,10 @@ def run_ours(args):
     if not args.skip_e2e:
         outs = [{k: torch.empty(g.n_beam, dtype=torch.float32).pin_memory() for k in ("ez", "wr")} for g in gs]
         d2h = sum(g.n_beam for g in gs) * 2 * 4
-        from paper_2603_16623_gb300.wake import _check, load
-        lib = load()
-
         def e2e_step():
             wm.wake_batch_reset(gs, pinned)
             wm.wake_batch_run(gs)
-            for g, o in zip(gs, outs):
-                _check(lib.wake_get_beam_fields(g.handle, o["ez"].data_ptr(), o["wr"].data_ptr(), None, None, 0))
+            wm.wake_batch_get_beam_fields(gs, [o["ez"] for o in outs], [o["wr"] for o in outs])
 
         e2e_step()
         torch.cuda.synchronize()
@@ -307,12 +313,15 @@ def serve_bench(args, wakes, pinned, stream, rank):
         reqs.append(serve.Request(rid=i, arrival=float(t), edges=wk.edges, beams=pinned[int(k)], dxi=wk.dxi,
                                   n_steps=wk.n_steps, out_ez=outs[int(k)][0], out_wr=outs[int(k)][1]))
     t0 = time.perf_counter()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_budget = args.serve_sm_fill * sms if args.serve_sm_fill > 0 else None
     srv = serve.WakeServer(int(args.serve_budget_gb * (1 << 30)), step_ns=int(args.serve_step_us * 1e3),
-                           stream=stream.cuda_stream, clock=lambda: time.perf_counter() - t0)
+                           stream=stream.cuda_stream, clock=lambda: time.perf_counter() - t0, sm_budget=sm_budget)
     stats = serve.run_stream(srv, reqs)
     torch.cuda.synchronize()
     out = stats.summary()
     out.update({"arrival_rate_per_s": args.serve_rate, "memory_budget_gb": args.serve_budget_gb,
+                "sm_budget": sm_budget,
                 "step_us": args.serve_step_us,
                 "requests_from": f"{len(wakes)} batched-workload wakes, drawn with seed 4",
                 "offered_ring_slices_per_s": float(sum(wakes[int(k)].n_rings * wakes[int(k)].n_steps
@@ -414,7 +423,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-step-us", type=float, default=4000.0)
+    ap.add_argument("--serve-sm-fill", type=float, default=1.5,
+                    help="admit while running wakes hold fewer than this many SMs' worth (x SM count); 0: no cap")
     ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
+    ap.add_argument("--rings-per-cta", type=int, default=0, help="cluster wakes: at most this many rings per CTA")
     args = ap.parse_args()
     if args.uniform:
         run_uniform(args)

@@ -130,7 +130,9 @@ wake_status wake_reset(wake_handle *h, const wake_beam_desc *beams, int32_t n_be
    preparations running concurrently on the library's auxiliary streams,
    ordered after the work already queued on the handles' (common) stream and
    joined back into it.  beams[i] (may be NULL, or beams itself NULL) gives
-   wake i new beam arrays with n_beams[i] species, under wake_reset's rules.
+   wake i new beam arrays with n_beams[i] species, under wake_reset's rules;
+   with beams given, the call waits once for the device between the slice
+   histogram and the per-slice sort (whose size is the densest slice).
    Errors: EINVAL (NULL handle, different streams, bad beams), ECUDA. */
 wake_status wake_batch_reset(int32_t n, wake_handle *const *handles, const wake_beam_desc *const *beams,
                              const int32_t *n_beams);
@@ -162,6 +164,13 @@ wake_status wake_fields_at(wake_handle *h, int64_t n, const double *r, void *ez,
    Errors: EINVAL, ECUDA. */
 wake_status wake_get_beam_fields(wake_handle *h, void *ez, void *wr, void *bt, void *psi,
                                  int32_t device_ptrs);
+
+/* wake_get_beam_fields of n wakes sharing one stream: E_z and W_r only
+   (ez[i], wr[i] may be NULL; ez or wr itself may be NULL), all copies
+   queued, then one synchronisation for host arrays.  Errors: EINVAL,
+   ENOMEM, ECUDA. */
+wake_status wake_batch_get_beam_fields(int32_t n, wake_handle *const *handles, void *const *ez, void *const *wr,
+                                       int32_t device_ptrs);
 
 /* Runs the rest of the window and returns E_z and W_r per beam particle in
    caller order (host arrays of "real", NULL = skip) and, if the handle was

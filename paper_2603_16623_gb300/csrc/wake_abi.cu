@@ -190,9 +190,10 @@ wake_status check_new_beams(const wake_handle* h, const wake_beam_desc* beams, i
 }
 
 // Enqueues the host-to-device copies of checked new beam arrays on st.
-wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams, cudaStream_t st) {
+wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams, cudaStream_t st,
+                         bool count_on_host = true) {
     if (!beams) return WAKE_OK;
-    h->slice_max = densest_slice(beams, n_beams, h->dxi, h->n_steps);
+    if (count_on_host) h->slice_max = densest_slice(beams, n_beams, h->dxi, h->n_steps);
     int64_t off = 0;
     for (int32_t b = 0; b < n_beams; ++b) {
         const size_t bytes = beams[b].n * sizeof(double);
@@ -208,7 +209,13 @@ wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_
 }
 
 template <class P>
-wake_status prepare_impl(wake_handle* h, cudaStream_t st) {
+wake_status prepare_sort(wake_handle* h, cudaStream_t st);
+
+// First part of the a0/a1 preparation (control words, rings, charge, slice
+// histogram and offsets, whose maximum lands in d_dmax); with split = false
+// also the second part (prepare_sort).
+template <class P>
+wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
     using R = typename P::R;
     WakeDev<P> D;
     std::memcpy(&D, h->desc_host.data(), sizeof(D));
@@ -230,6 +237,21 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st) {
         WK_CUDA(cudaMemsetAsync(h->d_fill, 0, (size_t)ns * sizeof(int32_t), st));
         WK_CUDA(launch_bin_count(h->d_xi, h->nb_total, h->dxi, ns, h->d_slot, h->d_cnt, st));
         WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, st));
+    }
+    if (!split) return prepare_sort<P>(h, st);
+    return WAKE_OK;
+}
+
+// Second part of the a1 preparation: scatter into slices and the per-slice
+// radial sort, sized by h->slice_max; cleared outputs and dumps.
+template <class P>
+wake_status prepare_sort(wake_handle* h, cudaStream_t st) {
+    using R = typename P::R;
+    WakeDev<P> D;
+    std::memcpy(&D, h->desc_host.data(), sizeof(D));
+    const int32_t n = h->n, ns = h->n_steps;
+    const size_t rb = h->real_bytes();
+    if (h->nb_total > 0) {
         WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, ns, h->d_boff, h->d_fill, h->d_bidx, st));
         // sort size: a power of two >= the densest slice (a slice beyond
         // kMaxSliceParticles is flagged by the kernel)
@@ -375,9 +397,10 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
 }
 
 // The on-chip march (mixed precision).  Automatic shape: one CTA of up to
-// 512 threads x 4 rings for wakes up to 2048 rings; beyond, a thread-block
-// cluster of ceil(n / 2048) such CTAs (up to 16, the largest cluster GB300
-// allows); beyond 32,768 rings, 8 rings per thread.  A caller (or the autotuner) may instead fix the rings per thread
+// 512 threads x 4 rings for wakes up to 2048 rings; up to 16,384 rings a
+// thread-block cluster of ceil(n / 1024) CTAs; up to 32,768 one of
+// ceil(n / 2048) CTAs (16 is the largest cluster GB300 allows); beyond, 8
+// rings per thread.  A caller (or the autotuner) may instead fix the rings per thread
 // (4 or 8) and the CTAs per wake; the threads per CTA then follow from n.
 constexpr int32_t kRingsPerCta = 4 * kFastMaxThreads;
 constexpr int32_t kMaxClusterCtas = 16;
@@ -397,10 +420,24 @@ wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want
     if (want_k != 0 && want_k != 4 && want_k != 8) return fail(WAKE_EINVAL, "wake_init: rings_per_thread must be 0, 4 or 8");
     if (want_cl < 0 || want_cl > kMaxClusterCtas)
         return fail(WAKE_EINVAL, "wake_init: cluster_ctas must be in [0, %d]", kMaxClusterCtas);
-    // automatic: 4 rings per thread while a cluster of at most 16 such CTAs
-    // holds the wake, else 8 (up to 16 x 512 x 8 = 65,536 rings)
-    f.k = want_k ? want_k : (n <= kMaxClusterCtas * kRingsPerCta ? 4 : 8);
-    f.cl = want_cl ? want_cl : (n + f.k * kFastMaxThreads - 1) / (f.k * kFastMaxThreads);
+    // automatic: one CTA up to 2048 rings; beyond, clusters of CTAs of at
+    // most 1024 rings (<= 256 threads x 4, two such CTAs fit an SM's
+    // registers: a shorter per-slice chain for the same SM time, measured on
+    // the batched workload), then of 2048 rings, then 8 rings per thread (up
+    // to 16 x 512 x 8 = 65,536 rings)
+    if (want_k || want_cl) {
+        f.k = want_k ? want_k : 4;
+        f.cl = want_cl ? want_cl : (n + f.k * kFastMaxThreads - 1) / (f.k * kFastMaxThreads);
+    } else if (n <= kRingsPerCta) {
+        f.k = 4;
+        f.cl = 1;
+    } else if (n <= kMaxClusterCtas * kRingsPerCta / 2) {
+        f.k = 4;
+        f.cl = (n + kRingsPerCta / 2 - 1) / (kRingsPerCta / 2);
+    } else {
+        f.k = n <= kMaxClusterCtas * kRingsPerCta ? 4 : 8;
+        f.cl = (n + f.k * kFastMaxThreads - 1) / (f.k * kFastMaxThreads);
+    }
     if (f.cl > kMaxClusterCtas) {
         if (want_k || want_cl)
             return fail(WAKE_EINVAL, "wake_init: %d rings need more than %d CTAs of %d x %d rings", n, kMaxClusterCtas,
@@ -539,35 +576,44 @@ wake_status fields_at_impl(wake_handle* h, int64_t n, const double* r, void* ez,
     return WAKE_OK;
 }
 
+// Enqueues the fields on the beam particles, in the caller's particle order,
+// into caller arrays (device, or host through a staging buffer from the
+// library's pool); no synchronisation.
 template <class R>
-wake_status beam_fields_impl(wake_handle* h, void* const outs_user[4], int32_t device_ptrs) {
+wake_status beam_fields_enqueue(wake_handle* h, void* const outs_user[4], int32_t device_ptrs) {
     const int64_t nb = h->nb_total;
     if (nb == 0) return WAKE_OK;
     R* tmp = nullptr;
     if (!device_ptrs) {
-        if (cudaMalloc(&tmp, nb * sizeof(R)) != cudaSuccess) {
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = wake_pool(&pool);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&tmp), nb * sizeof(R), pool, h->st);
+        if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(WAKE_ENOMEM, "beam output staging allocation failed");
         }
     }
-    wake_status st = WAKE_OK;
-    for (int k = 0; k < 4 && st == WAKE_OK; ++k) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
         if (!outs_user[k]) continue;
         R* dst = device_ptrs ? static_cast<R*>(outs_user[k]) : tmp;
-        cudaError_t e = cudaMemsetAsync(dst, 0, nb * sizeof(R), h->st);
+        e = cudaMemsetAsync(dst, 0, nb * sizeof(R), h->st);
         if (e == cudaSuccess)
             e = launch_scatter_out<R>(h->d_bidx, h->d_boff + h->n_steps, nb, static_cast<const R*>(h->d_out[k]),
                                       dst, h->st);
         if (e == cudaSuccess && !device_ptrs)
             e = cudaMemcpyAsync(outs_user[k], tmp, nb * sizeof(R), cudaMemcpyDeviceToHost, h->st);
-        if (e == cudaSuccess && !device_ptrs) e = cudaStreamSynchronize(h->st);
-        if (e != cudaSuccess) st = fail(WAKE_ECUDA, "wake_get_beam_fields: %s", cudaGetErrorString(e));
     }
-    if (tmp) {
-        cudaStreamSynchronize(h->st);
-        cudaFree(tmp);
-    }
-    return st;
+    if (tmp) cudaFreeAsync(tmp, h->st);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_get_beam_fields: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
+template <class R>
+wake_status beam_fields_impl(wake_handle* h, void* const outs_user[4], int32_t device_ptrs) {
+    WK_TRY(beam_fields_enqueue<R>(h, outs_user, device_ptrs));
+    if (!device_ptrs) WK_CUDA(cudaStreamSynchronize(h->st));
+    return WAKE_OK;
 }
 
 template <class P>
@@ -922,13 +968,34 @@ wake_status wake_batch_reset(int32_t n, wake_handle* const* handles, const wake_
         WK_CUDA(aux_stream(j, &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
     }
+    // with new beams the densest slice is read back from the device between
+    // the histogram and the sort (one synchronisation for the whole batch)
+    const bool split = beams != nullptr;
     for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
         wake_handle* h = handles[i];
         cudaStream_t as = nullptr;
         WK_CUDA(aux_stream(i % n_streams, &as));
-        if (beams && beams[i]) res = upload_beams(h, beams[i], n_beams[i], as);
+        if (beams && beams[i]) res = upload_beams(h, beams[i], n_beams[i], as, false);
         if (res == WAKE_OK)
-            res = h->prec == WAKE_FP64 ? prepare_impl<PrecF64>(h, as) : prepare_impl<PrecMixed>(h, as);
+            res = h->prec == WAKE_FP64 ? prepare_impl<PrecF64>(h, as, split) : prepare_impl<PrecMixed>(h, as, split);
+    }
+    if (split && res == WAKE_OK) {
+        std::vector<int32_t> dmax((size_t)n, 0);
+        for (int32_t j = 0; j < n_streams; ++j) {
+            cudaStream_t as = nullptr;
+            WK_CUDA(aux_stream(j, &as));
+            WK_CUDA(cudaStreamSynchronize(as));
+        }
+        for (int32_t i = 0; i < n; ++i)
+            if (handles[i]->nb_total > 0)
+                WK_CUDA(cudaMemcpy(&dmax[(size_t)i], handles[i]->d_dmax, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
+            wake_handle* h = handles[i];
+            if (h->nb_total > 0) h->slice_max = dmax[(size_t)i];
+            cudaStream_t as = nullptr;
+            WK_CUDA(aux_stream(i % n_streams, &as));
+            res = h->prec == WAKE_FP64 ? prepare_sort<PrecF64>(h, as) : prepare_sort<PrecMixed>(h, as);
+        }
     }
     for (int32_t j = 0; j < n_streams; ++j) {
         cudaStream_t as = nullptr;
@@ -979,6 +1046,27 @@ wake_status wake_get_beam_fields(wake_handle* h, void* ez, void* wr, void* bt, v
     void* outs[4] = {ez, wr, bt, psi};
     if (h->prec == WAKE_FP64) return beam_fields_impl<double>(h, outs, device_ptrs);
     return beam_fields_impl<float>(h, outs, device_ptrs);
+}
+
+wake_status wake_batch_get_beam_fields(int32_t n, wake_handle* const* handles, void* const* ez, void* const* wr,
+                                       int32_t device_ptrs) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_get_beam_fields: bad handle array");
+    for (int32_t i = 0; i < n; ++i) {
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_get_beam_fields: handle %d is NULL", i);
+        if (handles[i]->st != handles[0]->st)
+            return fail(WAKE_EINVAL, "wake_batch_get_beam_fields: handles must share a stream");
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        void* outs[4] = {ez ? ez[i] : nullptr, wr ? wr[i] : nullptr, nullptr, nullptr};
+        wake_status s = handles[i]->prec == WAKE_FP64 ? beam_fields_enqueue<double>(handles[i], outs, device_ptrs)
+                                                      : beam_fields_enqueue<float>(handles[i], outs, device_ptrs);
+        if (s != WAKE_OK) {
+            cudaStreamSynchronize(handles[0]->st);
+            return s;
+        }
+    }
+    if (n > 0 && !device_ptrs) WK_CUDA(cudaStreamSynchronize(handles[0]->st));
+    return WAKE_OK;
 }
 
 wake_status wake_run(wake_handle* h, void* beam_ez, void* beam_wr, void* ring_r) {

@@ -34,6 +34,13 @@ def estimate_device_bytes(n_rings: int, n_beam: int, n_steps: int) -> int:
     return 192 * n_rings + 72 * n_beam + 16 * (n_steps + 1) + (64 << 10)
 
 
+def sm_share(launch_config) -> float:
+    """SM-equivalents a wake holds while it runs: its CTAs, each taking
+    threads x 128 registers of an SM's 65,536."""
+    threads, _, ctas = launch_config
+    return ctas * min(1.0, threads / 512.0)
+
+
 @dataclass
 class Request:
     rid: int
@@ -49,6 +56,7 @@ class Request:
     finished: float = float("nan")
     status: int = -1
     slices_done: int = 0
+    sm_share: float = 0.0
 
     @property
     def n_rings(self) -> int:
@@ -88,8 +96,14 @@ class WakeServer:
     """Admits, steps and retires wakes; see the module docstring."""
 
     def __init__(self, memory_budget: int, step_ns: int = 4_000_000, stream=None,
-                 clock: Optional[Callable[[], float]] = None):
+                 clock: Optional[Callable[[], float]] = None, sm_budget: Optional[float] = None):
         self.budget = int(memory_budget)
+        # Admission also stops once the running wakes fill the SMs
+        # (sm_budget SM-equivalents): beyond that every wake would only run
+        # slower (they share the SMs), raising everyone's latency for no
+        # throughput.  None: memory alone decides.
+        self.sm_budget = sm_budget
+        self.sm_used = 0.0
         self.step_ns = int(step_ns)
         self.stream = stream
         self.clock = clock or time.perf_counter
@@ -108,23 +122,31 @@ class WakeServer:
             est = estimate_device_bytes(req.n_rings, req.n_beam, req.n_steps)
             if self.active and self.used + est > self.budget:
                 break
+            if self.active and self.sm_budget is not None and self.sm_used >= self.sm_budget:
+                break
             self.queue.popleft()
             w = wm.Wake(req.edges, req.beams, req.dxi, req.n_steps, precision="mixed",
                         flags=wm.WAKE_INIT_ASYNC, stream=self.stream)
             req.admitted = self.clock()
+            req.sm_share = sm_share(w.launch_config())
             self.used += est
+            self.sm_used += req.sm_share
             self.active.append((req, w, est))
         self.stats.max_active = max(self.stats.max_active, len(self.active))
         self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
 
     def step(self) -> List[Request]:
-        """One scheduling round: admit, advance, retire.  Returns the
-        requests that finished in this round."""
+        """One scheduling round: advance the running wakes, admit, retire.
+        Returns the requests that finished in this round."""
+        # the step is queued first, so that creating the newly admitted
+        # wakes (host-side checks and uploads) overlaps it on the device
+        stepped = [w for _, w, _ in self.active]
+        if stepped:
+            wm.wake_batch_step(stepped, 1 << 30, self.step_ns)
         self._admit()
         if not self.active:
             return []
         wakes = [w for _, w, _ in self.active]
-        wm.wake_batch_step(wakes, 1 << 30, self.step_ns)
         nxt, st = wm.wake_batch_progress(wakes)
         self.stats.steps += 1
         done, keep = [], []
@@ -144,6 +166,7 @@ class WakeServer:
             req.slices_done = min(n, req.n_steps)
             w.close()
             self.used -= est
+            self.sm_used -= req.sm_share
             self.stats.completed.append(req)
             out.append(req)
         return out

@@ -65,6 +65,7 @@ _SIGS = {
     "wake_batch_step": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.c_int64], C.c_int),
     "wake_batch_progress": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
     "wake_get_device_bytes": ([_vp, C.POINTER(C.c_int64)], C.c_int),
+    "wake_batch_get_beam_fields": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -332,6 +333,17 @@ def wake_batch_progress(wakes: List[Wake]):
     st = np.zeros(max(1, n), dtype=np.int32)
     _check(load().wake_batch_progress(n, arr, nxt.ctypes.data, st.ctypes.data))
     return nxt[:n], st[:n]
+
+
+def wake_batch_get_beam_fields(wakes: List[Wake], ez: Sequence, wr: Sequence):
+    """E_z and W_r of every wake's beam particles into host arrays (numpy or
+    pinned torch tensors; None to skip), one synchronisation."""
+    n = len(wakes)
+    ptr = lambda a: (a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data) if a is not None else None
+    arr = (_vp * max(1, n))(*[w.handle for w in wakes])
+    pez = (_vp * max(1, n))(*[ptr(a) for a in ez])
+    pwr = (_vp * max(1, n))(*[ptr(a) for a in wr])
+    _check(load().wake_batch_get_beam_fields(n, arr, pez, pwr, 0))
 
 
 def wake_batch_run(wakes: List[Wake]):
