@@ -6,3 +6,4 @@ imports it.
 """
 from .oracle import (OracleResult, build, ring_init, slice_fields, bp_shooting, bp_solve,  # noqa: F401
                      run, run_wake, lib_path)
+from . import beam_push  # noqa: F401
