@@ -224,6 +224,11 @@ def run_ours(args):
         e2e = {"value": rs_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_s * 1e3}
 
+    # ---- beam push (the step after a solve): Boris step of every beam particle
+    push = None
+    if not args.skip_push:
+        push = push_bench(args, gs, wakes, stream)
+
     # ---- serving: Poisson arrivals of batched-workload wakes, continuous batching
     serving = None
     if not args.skip_serve:
@@ -281,6 +286,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
             "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + n_march_launches),
             "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "serving": serving,
+            "beam_push": push,
             "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
             "wall_s": wall,
@@ -290,6 +296,40 @@ def run_ours(args):
         g.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+# algorithmic HBM bytes per beam particle of one push (one fused kernel):
+# read x, y, xi, u_x, u_y, u_z (48), its sorted position (4) and E_z, W_r,
+# B_theta there (12); write x, y, xi, r, u_x, u_y, u_z (56)
+PUSH_BYTES_PER_PARTICLE = 48 + 4 + 12 + 56
+
+
+def push_bench(args, gs, wakes, stream):
+    """wake_batch_push_beam over the whole batch after a solve, timed with
+    CUDA events; HBM-bound (one pass over the particle arrays)."""
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    n_part = 0
+    for g, wk in zip(gs, wakes):
+        b = np.concatenate([bm.r for bm in wk.beams])
+        n = b.shape[0]
+        g.set_beam_phase_space(b, np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, 2000.0))
+        n_part += n
+    wm.wake_batch_push_beam(gs, 0.1)  # warm-up
+    torch.cuda.synchronize()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        wm.wake_batch_push_beam(gs, 0.1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    gbs = PUSH_BYTES_PER_PARTICLE * n_part / (ms / 1e3) / 1e9
+    return {"particles": n_part, "ms_per_push": ms, "particles_per_s": n_part / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "bytes_per_particle": PUSH_BYTES_PER_PARTICLE, "peak_basis": "measured copy (MEASURED_PEAKS.json)"}}
 
 
 def serve_bench(args, wakes, pinned, stream, rank):
@@ -419,6 +459,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-push", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)

@@ -236,6 +236,40 @@ wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, vo
 wake_status wake_get_launch_config(wake_handle *h, int32_t *threads, int32_t *rings_per_thread,
                                    int32_t *blocks_per_wake);
 
+/* Beam push between wake solves (Sec. V: the beam moves over a time step in
+   the fields the wake gave at each particle; Boris method).  The beam needs
+   a full phase space for it: x, y, u_x, u_y, u_z (u = p/(m c)) per beam
+   particle in the concatenated order of wake_init, host double arrays of
+   the total particle count; the radius the wake bins by becomes |(x, y)|
+   and xi stays as given.  Beam species must be electrons or positrons
+   (q = -1 or +1, electron mass).  Synchronises the
+   handle's stream.  Errors: EINVAL (NULL arrays, non-finite values), ENOMEM,
+   ECUDA. */
+wake_status wake_set_beam_phase_space(wake_handle *h, const double *x, const double *y, const double *ux,
+                                      const double *uy, const double *uz);
+
+/* The beam's current x, y, xi, r (the radius the next wake_reset bins by),
+   u_x, u_y, u_z (host double arrays, any may be NULL).  Errors: EINVAL (no
+   phase space set and x, y or u asked for), ECUDA. */
+wake_status wake_get_beam_phase_space(wake_handle *h, double *x, double *y, double *xi, double *r, double *ux,
+                                      double *uy, double *uz);
+
+/* One time step dt (> 0, in 1/omega_p) of every beam particle in the fields
+   of the last march (particles outside the window see none): u is updated
+   by the Boris method with E = (E_r x/r, E_r y/r, E_z), E_r = W_r + B_theta,
+   B = (-B_theta y/r, B_theta x/r, 0), then x, y move by dt u/gamma and xi by
+   dt (1 - u_z/gamma).  The next wake_reset(h, NULL) bins the moved beam, and
+   a march then solves the wake it drives.  FP64 wakes push in FP64; mixed
+   wakes add FP32 increments (~1e-7 of themselves) to the FP64 phase space.
+   Asynchronous on the handle's stream.  Errors: EINVAL (dt <= 0, no phase
+   space, unsupported species), ENOMEM, ECUDA. */
+wake_status wake_push_beam(wake_handle *h, double dt);
+
+/* wake_push_beam of n wakes sharing one stream and one precision, as one
+   kernel launch on that stream.  Errors: as wake_push_beam, and EINVAL for
+   handles on different streams or of different precisions. */
+wake_status wake_batch_push_beam(int32_t n, wake_handle *const *handles, double dt);
+
 /* wake_fields_at without any allocation.  The paper has no counterpart:
    this entry exists for callers that cannot allocate while they run -- a
    host code that owns the device's memory through its own pool allocator,

@@ -112,7 +112,7 @@ __global__ void slice_sort_kernel(const int32_t* __restrict__ off, int32_t n_ste
                                   const double* __restrict__ r_in, const double* __restrict__ qw_in,
                                   int32_t* __restrict__ idx, R* __restrict__ br, R* __restrict__ bE,
                                   R* __restrict__ bQs, R* __restrict__ bTot, int32_t m_pad,
-                                  int32_t* __restrict__ ctl) {
+                                  int32_t* __restrict__ ctl, int32_t* __restrict__ inv) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* keys = reinterpret_cast<double*>(smem);
     double* pre = keys + m_pad;
@@ -173,6 +173,7 @@ __global__ void slice_sort_kernel(const int32_t* __restrict__ off, int32_t n_ste
             int32_t f = i;
             while (f > 0 && keys[f - 1] == keys[i]) --f;  // first of a tie group
             idx[b0 + i] = vals[i];
+            if (inv) inv[vals[i]] = b0 + i;  // caller index -> sorted position
             br[b0 + i] = (R)keys[i];
             bE[b0 + i] = (R)pre[i];
             bQs[b0 + i] = (R)pre[f];
@@ -250,7 +251,7 @@ cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st) {
 template <class R>
 cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
                               int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t* ctl,
-                              cudaStream_t st) {
+                              int32_t* inv, cudaStream_t st) {
     // the attribute allows the largest slice the library accepts; a launch
     // asks only for its own m_pad (a power of two >= the wake's densest slice)
     static cudaError_t attr = cudaFuncSetAttribute(slice_sort_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -262,7 +263,8 @@ cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double*
     threads = threads < 64 ? 64 : threads > 512 ? 512 : threads;
     int grid = n_steps < 152 * 8 ? n_steps : 152 * 8;
     if (grid < 1) grid = 1;
-    slice_sort_kernel<R><<<grid, threads, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, ctl);
+    slice_sort_kernel<R><<<grid, threads, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, ctl,
+                                                    inv);
     return cudaGetLastError();
 }
 
@@ -275,10 +277,11 @@ cudaError_t launch_scatter_out(const int32_t* idx, const int32_t* nbin, int64_t 
 }
 
 template cudaError_t launch_slice_sort<double>(const int32_t*, int32_t, const double*, const double*, int32_t*,
-                                               double*, double*, double*, double*, int32_t, int32_t*,
+                                               double*, double*, double*, double*, int32_t, int32_t*, int32_t*,
                                                cudaStream_t);
 template cudaError_t launch_slice_sort<float>(const int32_t*, int32_t, const double*, const double*, int32_t*,
-                                              float*, float*, float*, float*, int32_t, int32_t*, cudaStream_t);
+                                              float*, float*, float*, float*, int32_t, int32_t*, int32_t*,
+                                              cudaStream_t);
 template cudaError_t launch_scatter_out<double>(const int32_t*, const int32_t*, int64_t, const double*, double*,
                                                 cudaStream_t);
 template cudaError_t launch_scatter_out<float>(const int32_t*, const int32_t*, int64_t, const float*, float*,

@@ -21,7 +21,7 @@ cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st);
 template <class R>
 cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
                               int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t* ctl,
-                              cudaStream_t st);
+                              int32_t* inv, cudaStream_t st);  // inv (nullable): caller index -> sorted position
 template <class R>
 cudaError_t launch_scatter_out(const int32_t* idx, const int32_t* nbin, int64_t nb_max, const R* src, R* dst,
                                cudaStream_t st);

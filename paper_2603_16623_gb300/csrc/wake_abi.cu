@@ -20,6 +20,7 @@
 #include "../../include/wake.h"
 #include "beam.h"
 #include "march.h"
+#include "push.h"
 
 using namespace gbwake;
 
@@ -69,11 +70,13 @@ struct wake_handle {
     std::vector<int64_t> beam_n;            // particles per species
     std::vector<double> beam_q;             // charge sign per species
     double *d_edges = nullptr, *d_xi = nullptr, *d_r = nullptr, *d_w = nullptr, *d_qw = nullptr;
+    double* d_ps[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // beam x, y, u_x, u_y, u_z (push)
     int32_t *d_slot = nullptr, *d_cnt = nullptr, *d_fill = nullptr, *d_boff = nullptr, *d_dmax = nullptr;
     void* d_desc = nullptr;                 // device WakeDev<P>
     std::vector<unsigned char> desc_host;   // host copy of the descriptor
     int32_t* d_ctl = nullptr;
     int32_t* d_bidx = nullptr;
+    int32_t* d_inv = nullptr;               // caller particle -> sorted (binned) position, -1 outside
     void* d_out[4] = {nullptr, nullptr, nullptr, nullptr};
     void* d_dump[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void* d_rho[2] = {nullptr, nullptr};
@@ -257,9 +260,10 @@ wake_status prepare_sort(wake_handle* h, cudaStream_t st) {
         // kMaxSliceParticles is flagged by the kernel)
         const int32_t m_pad = h->slice_max > kMaxSliceParticles ? kMaxSliceParticles
                                                                  : next_pow2(std::max(h->slice_max, 64));
+        WK_CUDA(cudaMemsetAsync(h->d_inv, 0xff, (size_t)h->nb_total * sizeof(int32_t), st));
         WK_CUDA(launch_slice_sort<R>(h->d_boff, ns, h->d_r, h->d_qw, h->d_bidx, const_cast<R*>(D.br),
                                      const_cast<R*>(D.bE), const_cast<R*>(D.bQs), const_cast<R*>(D.bTot),
-                                     m_pad, h->d_ctl, st));
+                                     m_pad, h->d_ctl, h->d_inv, st));
         for (int k = 0; k < 4; ++k)
             WK_CUDA(cudaMemsetAsync(h->d_out[k], 0, (size_t)h->nb_total * rb, st));
     }
@@ -345,6 +349,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         WK_TRY(dalloc_t(h, (size_t)nb, &h->d_qw));
         WK_TRY(dalloc_t(h, (size_t)nb, &h->d_slot));
         WK_TRY(dalloc_t(h, (size_t)nb, &h->d_bidx));
+        WK_TRY(dalloc_t(h, (size_t)nb, &h->d_inv));
         WK_TRY(dalloc_t(h, (size_t)ns, &h->d_cnt));
         WK_TRY(dalloc_t(h, (size_t)ns, &h->d_fill));
         WK_TRY(dalloc_t(h, 1, &h->d_dmax));
@@ -848,6 +853,86 @@ wake_status fields_at_static_impl(wake_handle* h, int64_t n, const double* r, vo
 
 }  // namespace
 
+namespace {
+
+// One wake's push description: its particle arrays, the fields of the last
+// march in sorted order, the caller -> sorted map and its species.
+template <class R>
+PushWake<R> push_desc(const wake_handle* h) {
+    PushWake<R> d = {};
+    d.n = h->nb_total;
+    d.x = h->d_ps[0];
+    d.y = h->d_ps[1];
+    d.xi = h->d_xi;
+    d.r = h->d_r;
+    d.ux = h->d_ps[2];
+    d.uy = h->d_ps[3];
+    d.uz = h->d_ps[4];
+    d.ez = static_cast<const R*>(h->d_out[0]);
+    d.wr = static_cast<const R*>(h->d_out[1]);
+    d.bt = static_cast<const R*>(h->d_out[2]);
+    d.inv = h->d_inv;
+    return d;
+}
+
+// Enqueues the push of n wakes (one launch) on stream st: each wake cut
+// into particle ranges of push_item_size(total), the descriptors and ranges
+// travel through one pooled device buffer.
+template <class R>
+wake_status push_enqueue(wake_handle* const* hs, int32_t n, double dt, cudaStream_t st) {
+    std::vector<PushWake<R>> descs;
+    std::vector<const wake_handle*> owner;
+    int64_t total = 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (hs[i]->nb_total > 0) {
+            descs.push_back(push_desc<R>(hs[i]));
+            owner.push_back(hs[i]);
+            total += hs[i]->nb_total;
+        }
+    if (descs.empty()) return WAKE_OK;
+    const int64_t chunk = push_item_size(total);
+    std::vector<PushItem> items;
+    for (size_t w = 0; w < descs.size(); ++w) {
+        int64_t off = 0;
+        for (size_t b = 0; b < owner[w]->beam_n.size(); ++b) {
+            const int64_t end = off + owner[w]->beam_n[b];
+            for (int64_t k = off; k < end; k += chunk)
+                items.push_back(PushItem{(int32_t)w, 0, k, std::min(k + chunk, end), owner[w]->beam_q[b]});
+            off = end;
+        }
+    }
+    if (items.size() > (size_t)INT32_MAX) return fail(WAKE_EINVAL, "wake_push_beam: too many particles");
+    const size_t desc_bytes = (descs.size() * sizeof(PushWake<R>) + 15) / 16 * 16;
+    const size_t item_bytes = items.size() * sizeof(PushItem);
+    std::vector<unsigned char> host(desc_bytes + item_bytes);
+    std::memcpy(host.data(), descs.data(), descs.size() * sizeof(PushWake<R>));
+    std::memcpy(host.data() + desc_bytes, items.data(), item_bytes);
+    cudaMemPool_t pool = nullptr;
+    WK_CUDA(wake_pool(&pool));
+    void* buf = nullptr;
+    WK_CUDA(cudaMallocFromPoolAsync(&buf, host.size(), pool, st));
+    cudaError_t e = cudaMemcpyAsync(buf, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_beam_push<R>(static_cast<const PushWake<R>*>(buf),
+                                reinterpret_cast<const PushItem*>(static_cast<unsigned char*>(buf) + desc_bytes),
+                                (int32_t)items.size(), dt, st);
+    cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_push_beam: %s", cudaGetErrorString(e));
+    return WAKE_OK;
+}
+
+wake_status check_push(const wake_handle* h, double dt) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(WAKE_EINVAL, "wake_push_beam: dt must be > 0");
+    if (h->nb_total > 0 && !h->d_ps[0])
+        return fail(WAKE_EINVAL, "wake_push_beam: set the beam phase space first (wake_set_beam_phase_space)");
+    for (double q : h->beam_q)
+        if (q != 1.0 && q != -1.0)
+            return fail(WAKE_EINVAL, "wake_push_beam: beam species must be electrons or positrons (q = -1 or +1)");
+    return WAKE_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* wake_last_error(void) { return g_err.c_str(); }
@@ -1214,6 +1299,62 @@ wake_status wake_fields_at_static(wake_handle* h, int64_t n, const double* r, vo
     void* outs[4] = {ez, wr, bt, psi};
     if (h->prec == WAKE_FP64) return fields_at_static_impl<PrecF64>(h, n, r, outs, base);
     return fields_at_static_impl<PrecMixed>(h, n, r, outs, base);
+}
+
+wake_status wake_set_beam_phase_space(wake_handle* h, const double* x, const double* y, const double* ux,
+                                      const double* uy, const double* uz) {
+    WK_TRY(check_handle(h));
+    const int64_t nb = h->nb_total;
+    if (nb > 0 && (!x || !y || !ux || !uy || !uz))
+        return fail(WAKE_EINVAL, "wake_set_beam_phase_space: x, y, ux, uy, uz are required");
+    for (int64_t k = 0; k < nb; ++k)
+        if (!std::isfinite(x[k]) || !std::isfinite(y[k]) || !std::isfinite(ux[k]) || !std::isfinite(uy[k]) ||
+            !std::isfinite(uz[k]))
+            return fail(WAKE_EINVAL, "wake_set_beam_phase_space: particle %lld is not finite", (long long)k);
+    if (nb == 0) return WAKE_OK;
+    if (!h->d_ps[0])
+        for (int c = 0; c < 5; ++c) WK_TRY(dalloc_t(h, (size_t)nb, &h->d_ps[c]));
+    const double* src[5] = {x, y, ux, uy, uz};
+    for (int c = 0; c < 5; ++c)
+        WK_CUDA(cudaMemcpyAsync(h->d_ps[c], src[c], (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    WK_CUDA(launch_beam_radius(nb, h->d_ps[0], h->d_ps[1], h->d_r, h->st));
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    return WAKE_OK;
+}
+
+wake_status wake_get_beam_phase_space(wake_handle* h, double* x, double* y, double* xi, double* r, double* ux,
+                                      double* uy, double* uz) {
+    WK_TRY(check_handle(h));
+    const int64_t nb = h->nb_total;
+    if (nb == 0) return WAKE_OK;
+    if (!h->d_ps[0] && (x || y || ux || uy || uz))
+        return fail(WAKE_EINVAL, "wake_get_beam_phase_space: no phase space was set");
+    double* dst[7] = {x, y, xi, r, ux, uy, uz};
+    const double* src[7] = {h->d_ps[0], h->d_ps[1], h->d_xi, h->d_r, h->d_ps[2], h->d_ps[3], h->d_ps[4]};
+    for (int c = 0; c < 7; ++c)
+        if (dst[c]) WK_CUDA(cudaMemcpyAsync(dst[c], src[c], (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    return WAKE_OK;
+}
+
+wake_status wake_push_beam(wake_handle* h, double dt) {
+    WK_TRY(check_handle(h));
+    WK_TRY(check_push(h, dt));
+    if (h->prec == WAKE_FP64) return push_enqueue<double>(&h, 1, dt, h->st);
+    return push_enqueue<float>(&h, 1, dt, h->st);
+}
+
+wake_status wake_batch_push_beam(int32_t n, wake_handle* const* handles, double dt) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_push_beam: bad handle array");
+    if (n == 0) return WAKE_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_push_beam: handle %d is NULL", i);
+        if (handles[i]->st != handles[0]->st || handles[i]->prec != handles[0]->prec)
+            return fail(WAKE_EINVAL, "wake_batch_push_beam: handles must share stream and precision");
+        WK_TRY(check_push(handles[i], dt));
+    }
+    if (handles[0]->prec == WAKE_FP64) return push_enqueue<double>(handles, n, dt, handles[0]->st);
+    return push_enqueue<float>(handles, n, dt, handles[0]->st);
 }
 
 void wake_destroy(wake_handle* h) {

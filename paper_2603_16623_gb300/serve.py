@@ -29,9 +29,10 @@ from . import wake as wm
 
 def estimate_device_bytes(n_rings: int, n_beam: int, n_steps: int) -> int:
     """Upper bound of the device bytes a mixed-precision wake takes (the
-    arrays wake_init allocates: ~180 B per ring, ~68 B per beam particle,
-    16 B per slice, plus per-allocation rounding)."""
-    return 192 * n_rings + 72 * n_beam + 16 * (n_steps + 1) + (64 << 10)
+    arrays wake_init allocates: ~180 B per ring, ~72 B per beam particle,
+    16 B per slice, plus per-allocation rounding; a beam phase space for
+    the push adds 40 B per particle, not counted here)."""
+    return 192 * n_rings + 80 * n_beam + 16 * (n_steps + 1) + (64 << 10)
 
 
 def sm_share(launch_config) -> float:

@@ -66,6 +66,10 @@ _SIGS = {
     "wake_batch_progress": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
     "wake_get_device_bytes": ([_vp, C.POINTER(C.c_int64)], C.c_int),
     "wake_batch_get_beam_fields": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
+    "wake_set_beam_phase_space": ([_vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "wake_get_beam_phase_space": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "wake_push_beam": ([_vp, C.c_double], C.c_int),
+    "wake_batch_push_beam": ([C.c_int32, C.POINTER(_vp), C.c_double], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -255,6 +259,24 @@ class Wake:
                                           fr.ctypes.data if fr is not None else None,
                                           fu.ctypes.data if fu is not None else None))
 
+    def set_beam_phase_space(self, x, y, ux, uy, uz):
+        """Full phase space of the beam particles (concatenated order) for
+        push_beam; the binning radius becomes |(x, y)|."""
+        arrs = [_f64(a) for a in (x, y, ux, uy, uz)]
+        _check(load().wake_set_beam_phase_space(self.handle, *[a.ctypes.data for a in arrs]))
+
+    def beam_phase_space(self) -> Dict[str, np.ndarray]:
+        """x, y, xi, r, ux, uy, uz of the beam particles (float64)."""
+        keys = ("x", "y", "xi", "r", "ux", "uy", "uz")
+        out = {k: np.zeros(self.n_beam) for k in keys}
+        _check(load().wake_get_beam_phase_space(self.handle, *[out[k].ctypes.data for k in keys]))
+        return out
+
+    def push_beam(self, dt: float):
+        """One Boris step dt of the beam in the fields of the last march
+        (asynchronous); reset() then bins the moved beam."""
+        _check(load().wake_push_beam(self.handle, float(dt)))
+
     def device_bytes(self) -> int:
         b = C.c_int64()
         _check(load().wake_get_device_bytes(self.handle, C.byref(b)))
@@ -344,6 +366,12 @@ def wake_batch_get_beam_fields(wakes: List[Wake], ez: Sequence, wr: Sequence):
     pez = (_vp * max(1, n))(*[ptr(a) for a in ez])
     pwr = (_vp * max(1, n))(*[ptr(a) for a in wr])
     _check(load().wake_batch_get_beam_fields(n, arr, pez, pwr, 0))
+
+
+def wake_batch_push_beam(wakes: List[Wake], dt: float):
+    """push_beam of many wakes at once (asynchronous)."""
+    arr = (_vp * max(1, len(wakes)))(*[w.handle for w in wakes])
+    _check(load().wake_batch_push_beam(len(wakes), arr, float(dt)))
 
 
 def wake_batch_run(wakes: List[Wake]):
