@@ -10,7 +10,7 @@ import ctypes as C
 import os
 import subprocess
 from dataclasses import dataclass
-from typing import Dict, Optional, Sequence
+from typing import Dict, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -77,6 +77,9 @@ def _lib():
         lib = C.CDLL(build())
         lib.orc_run.argtypes = [C.POINTER(_Problem), C.c_int32, C.POINTER(_Outputs)]
         lib.orc_run.restype = C.c_int
+        lib.orc_run_ions.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, C.c_int32,
+                                     C.POINTER(_Outputs)]
+        lib.orc_run_ions.restype = C.c_int
         lib.orc_slice_fields.argtypes = [C.c_int32, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
                                          C.c_int64, _dp, _dp, C.c_double, C.POINTER(_SliceOut)]
         lib.orc_slice_fields.restype = C.c_int
@@ -182,18 +185,21 @@ class OracleResult:
 
 def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: float = 1.0,
         max_slices: int = 0, beam_fields: Sequence[str] = ("ez", "wr", "bt", "psi"),
-        ring_dumps: Sequence[str] = ()) -> OracleResult:
+        ring_dumps: Sequence[str] = (), ions: Optional[Tuple[float, float]] = None) -> OracleResult:
     """March the whole window (or its first max_slices slices).
 
     beam_fields: subset of ez, wr, bt, psi (per particle, caller order).
     ring_dumps: subset of r, ur, psi, dpsidr, dpsidz, bp, bb, psibar, gamma, uz,
     frprev, fuprev
-    ([slices, rings] by ring id, values at the start of each slice)."""
+    ([slices, rings] by ring id, values at the start of each slice).
+    ions: (Z, M) for mobile ions as a second ring species (orc_run_ions);
+    ring dumps and final state then have 2 N columns, ions after electrons."""
     edges = _f64(edges)
     bxi, br, bqw = _f64(beam_xi), _f64(beam_r), _f64(beam_qw)
-    n = edges.shape[0] - 1
+    n_e = edges.shape[0] - 1
+    n = n_e if ions is None else 2 * n_e
     nb = bxi.shape[0]
-    prob = _Problem(n, _ptr(edges), density, nb, _ptr(bxi), _ptr(br), _ptr(bqw), dxi, n_steps)
+    prob = _Problem(n_e, _ptr(edges), density, nb, _ptr(bxi), _ptr(br), _ptr(bqw), dxi, n_steps)
     out = _Outputs()
     beam = {}
     for k in beam_fields:
@@ -207,7 +213,10 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     final_r = np.empty(n)
     final_ur = np.empty(n)
     out.final_r, out.final_ur = _ptr(final_r), _ptr(final_ur)
-    rc = _lib().orc_run(C.byref(prob), max_slices, C.byref(out))
+    if ions is None:
+        rc = _lib().orc_run(C.byref(prob), max_slices, C.byref(out))
+    else:
+        rc = _lib().orc_run_ions(C.byref(prob), float(ions[0]), float(ions[1]), max_slices, C.byref(out))
     if rc:
         raise RuntimeError(f"orc_run failed ({rc})")
     return OracleResult(out.status, out.fail_slice, out.slices_run, beam, rings, final_r, final_ur)
@@ -222,4 +231,5 @@ def run_wake(wake, **kw) -> OracleResult:
         qw = np.concatenate([b.q * b.w for b in wake.beams])
     else:
         xi = r = qw = np.zeros(0)
+    kw.setdefault("ions", getattr(wake, "ions", None))
     return run(wake.edges, xi, r, qw, wake.dxi, wake.n_steps, density=wake.density, **kw)

@@ -735,3 +735,428 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
     ws_free(&s);
     return rc;
 }
+
+/* ====================================================================== */
+/* Mobile ions: two ring species (Sec. II, "key algorithmic adjustments")   */
+/* ====================================================================== */
+/*
+ * Electrons (q = -1, m = 1) and ions (q = +Z, m = M electron masses) are
+ * both rings, initialised on the same cell edges from the same density
+ * profile (Eq. macroparticle_weight), the ions with density n/Z so that the
+ * plasma is neutral.  With the signed charge weight c_j = -q_j w_j
+ * (electrons +w_j, ions -w_j for Z w^ion = w^e) the sums of Sec. II are, per
+ * species,
+ *   psi(rho)      = sum_j c_j ln max(rho, rho_j)                 (Eq. psi)
+ *   d_rho psi     = (1/rho) sum_{rho_j < rho} c_j                (Eq. dpsi_dr)
+ *   d_zeta psi    = -sum_{rho_j >= rho} c_j u_j / (rho_j psibar_j)
+ *                   (Eq. dpsi_dzeta; the sign reading of zeta_derivative())
+ *   psibar_j      = 1 - (q_j/m_j) psi_j                           (Eq. cold_plasma_constant)
+ * Each species is solved on its own rings (with the self weight at its own
+ * ring), and its fields reach the rings of the other species by linear
+ * interpolation between its own ring values: at a radius x, j = the last ring
+ * of the species below x, F(x) = F_j + (F_{j+1} - F_j)(x - rho_j)/(rho_{j+1} -
+ * rho_j).  Below the species' first ring the interpolation runs from the
+ * axis value (d_rho psi = 0, B = 0); between its last ring and the plasma's
+ * initial outer edge rho_max = edges[N] it runs to the exact value at
+ * rho_max (all of the species' charge inside); beyond both the species'
+ * field is smooth and is taken exactly.  For an unperturbed uniform species
+ * this reproduces the continuous column: its d_rho psi is linear in rho.  B_theta^(p) comes from the electrons only
+ * (Eqs. b_coeffs_1..3 over electron rings with the total fields); the ions
+ * see it interpolated.  Beam particles see the exact sums of both species.
+ * Ions move by Eqs. plasma_particle_motion_1,2 with q/m = Z/M: in xi = -zeta,
+ *   d rho / d xi = u / psibar,  d u / d xi = -(q/m) (gamma d_rho psi / psibar - B_theta).
+ */
+
+typedef struct {
+    int32_t n;
+    double qm;                     /* q / m */
+    double edge;                   /* the plasma's initial outer edge rho_max */
+    double *r, *u, *c, *ch;        /* sorted state, charge weight, self weight */
+    double *S, *L, *T;             /* exclusive prefix sums [n+1] */
+    double Stot, Ltot, Ttot;
+    double *psi_o, *dpr_o, *dpz_o; /* own-species fields at own rings */
+    double *psi, *dpr, *dpz;       /* totals at own rings */
+    double *psib, *gam, *uz, *t, *bb, *bp;
+    int32_t *order, *tmp;
+} species_ws;
+
+static int sp_alloc(species_ws *s, int32_t n, double qm, double edge)
+{
+    memset(s, 0, sizeof(*s));
+    s->n = n;
+    s->qm = qm;
+    s->edge = edge;
+    size_t m = (size_t)n + 1;
+    double *blk = (double *)calloc(m * 20, sizeof(double));
+    s->order = (int32_t *)malloc(m * sizeof(int32_t));
+    s->tmp = (int32_t *)malloc(m * sizeof(int32_t));
+    if (!blk || !s->order || !s->tmp) {
+        free(blk);
+        free(s->order);
+        free(s->tmp);
+        return ORC_ENOMEM;
+    }
+    double **f[] = {&s->r, &s->u, &s->c, &s->ch, &s->S, &s->L, &s->T, &s->psi_o, &s->dpr_o,
+                    &s->dpz_o, &s->psi, &s->dpr, &s->dpz, &s->psib, &s->gam, &s->uz, &s->t,
+                    &s->bb, &s->bp};
+    for (size_t k = 0; k < sizeof(f) / sizeof(f[0]); ++k)
+        *f[k] = blk + k * m;
+    for (int32_t j = 0; j < n; ++j)
+        s->order[j] = j;
+    return ORC_OK;
+}
+
+static void sp_free(species_ws *s)
+{
+    free(s->r);
+    free(s->order);
+    free(s->tmp);
+    memset(s, 0, sizeof(*s));
+}
+
+/* Sort the species (stable w.r.t. its previous order), gather the beam
+   source and its own psi, d_rho psi at its rings (self weight in d_rho psi). */
+static void sp_own_potential(species_ws *s, const double *rho_id, const double *ur_id,
+                             const double *c_id, const double *ch_id, const beam_slice *bs, double dxi)
+{
+    int32_t n = s->n;
+    stable_sort_ids(n, s->order, rho_id, s->tmp);
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t id = s->order[i];
+        s->r[i] = rho_id[id];
+        s->u[i] = ur_id[id];
+        s->c[i] = c_id[id];
+        s->ch[i] = ch_id[id];
+        s->bb[i] = beam_field(bs, s->r[i], dxi);
+    }
+    double aS = 0.0, aL = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        s->S[i] = aS;
+        s->L[i] = aL;
+        aS += s->c[i];
+        aL += s->c[i] * log(s->r[i]);
+    }
+    s->S[n] = aS;
+    s->L[n] = aL;
+    s->Stot = aS;
+    s->Ltot = aL;
+    for (int32_t i = 0; i < n; ++i) {
+        double r = s->r[i];
+        s->psi_o[i] = (s->Ltot - s->L[i]) + s->S[i] * log(r);
+        s->dpr_o[i] = (s->S[i] + s->ch[i]) / r;
+    }
+}
+
+/* The species' own d_zeta psi at its rings (needs psibar, so the totals of
+   psi first): T prefix of t = c u / (rho psibar), self weight on the ring's
+   own term. */
+static void sp_own_dzeta(species_ws *s)
+{
+    int32_t n = s->n;
+    double aT = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        s->T[i] = aT;
+        aT += s->t[i];
+    }
+    s->T[n] = aT;
+    s->Ttot = aT;
+    for (int32_t i = 0; i < n; ++i) {
+        double above = s->Ttot - s->T[i + 1];
+        s->dpz_o[i] = -(above + (1.0 - s->ch[i] / s->c[i]) * s->t[i]);
+    }
+}
+
+/* The species' field outside all its rings at radius x > 0 (which = 0, 1,
+   2 for psi, d_rho psi, d_zeta psi; 3 for B^(p), whose outermost region has
+   a_N = 0 and b_N = bN). */
+static double sp_outside(const species_ws *s, int which, double bN, double x)
+{
+    if (which == 0) return s->Stot * log(x);
+    if (which == 1) return s->Stot / x;
+    if (which == 2) return 0.0;
+    return bN / x;
+}
+
+/* Linear interpolation of a species' ring values F[0..n) (radius order r)
+   at radius x (the multi-species gather of Sec. II).  F0: the value on the
+   axis; the node beyond the last ring is rho_max with the outside value. */
+static double sp_interp(const species_ws *s, const double *F, double F0, int which, double bN,
+                        double x)
+{
+    int32_t n = s->n;
+    int64_t k = lower_bound(s->r, n, x);   /* rings strictly below x */
+    if (k >= n) {
+        double rl = s->r[n - 1];
+        if (x >= s->edge || !(s->edge > rl))
+            return sp_outside(s, which, bN, x);
+        double Fe = sp_outside(s, which, bN, s->edge);
+        return F[n - 1] + (Fe - F[n - 1]) * (x - rl) / (s->edge - rl);
+    }
+    double rl = k > 0 ? s->r[k - 1] : 0.0;
+    double Fl = k > 0 ? F[k - 1] : F0;
+    double rh = s->r[k], Fh = F[k];
+    if (!(rh > rl))
+        return Fh;
+    return Fl + (Fh - Fl) * (x - rl) / (rh - rl);
+}
+
+/* psi, d_rho psi, d_zeta psi of one species alone at an off-ring radius x
+   (exact sums, no self weight): what a beam particle sees of it. */
+static void sp_exact_at(const species_ws *s, double x, double *psi, double *dpr, double *dpz)
+{
+    if (!(x > 0.0)) {
+        *psi = s->Ltot;
+        *dpr = 0.0;
+        *dpz = -s->Ttot;
+        return;
+    }
+    int64_t k = lower_bound(s->r, s->n, x);
+    *psi = (s->Ltot - s->L[k]) + s->S[k] * log(x);
+    *dpr = s->S[k] / x;
+    *dpz = -(s->Ttot - s->T[k]);
+}
+
+int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_slices,
+                 orc_outputs *out)
+{
+    if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
+        !(ion_z > 0.0) || !(ion_m > 0.0) ||
+        (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
+        return ORC_EINVAL;
+    for (int32_t j = 0; j < p->n_rings; ++j)
+        if (!(p->edges[j + 1] > p->edges[j]))
+            return ORC_EINVAL;
+    if (p->edges[0] != 0.0)
+        return ORC_EINVAL;
+    const int32_t n = p->n_rings, ns = p->n_steps, n2 = 2 * n;
+    const int32_t nrun = (max_slices > 0 && max_slices < ns) ? max_slices : ns;
+    const double dxi = p->dxi;
+    out->status = ORC_OK;
+    out->fail_slice = -1;
+    out->slices_run = 0;
+
+    /* state by ring id: electrons 0..n-1, ions n..2n-1 */
+    double *st = (double *)calloc((size_t)n2 * 6, sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)ns + 2, sizeof(int64_t));
+    bpart *parts = (bpart *)malloc((size_t)(p->n_beam + 1) * sizeof(bpart));
+    double *ab = (double *)malloc(((size_t)n + 1) * 5 * sizeof(double));
+    species_ws sp[2];
+    int rc = sp_alloc(&sp[0], n, -1.0, p->edges[n]);
+    if (!rc) {
+        rc = sp_alloc(&sp[1], n, ion_z / ion_m, p->edges[n]);
+        if (rc) sp_free(&sp[0]);
+    }
+    if (!st || !cnt || !parts || !ab || rc) {
+        free(st); free(cnt); free(parts); free(ab);
+        if (!rc) { sp_free(&sp[0]); sp_free(&sp[1]); }
+        return ORC_ENOMEM;
+    }
+    double *rho = st, *ur = st + n2, *cw = st + 2 * n2, *ch = st + 3 * n2;
+    double *fr_prev = st + 4 * n2, *fu_prev = st + 5 * n2;
+    double *A = ab, *B = ab + (n + 1), *Cc = ab + 2 * (n + 1), *ak = ab + 3 * (n + 1),
+           *bk = ab + 4 * (n + 1);
+    double *w0 = (double *)malloc((size_t)n * 2 * sizeof(double));
+    if (!w0) {
+        free(st); free(cnt); free(parts); free(ab);
+        sp_free(&sp[0]); sp_free(&sp[1]);
+        return ORC_ENOMEM;
+    }
+    orc_ring_init(n, p->edges, p->density, rho, NULL, w0, w0 + n);
+    for (int32_t j = 0; j < n; ++j) {
+        rho[n + j] = rho[j];
+        cw[j] = w0[j];          /* electrons: c = -q w = +w */
+        ch[j] = w0[n + j];
+        cw[n + j] = -w0[j];     /* ions: w^ion = w / Z, c = -Z w^ion */
+        ch[n + j] = -w0[n + j];
+    }
+    free(w0);
+
+    /* nearest-slice binning of the beam, as orc_run */
+    for (int64_t k = 0; k < p->n_beam; ++k) {
+        int64_t sl = nearest_slice(p->beam_xi[k], dxi);
+        if (sl >= 0 && sl < ns)
+            cnt[sl + 1]++;
+    }
+    for (int32_t sl = 0; sl < ns; ++sl)
+        cnt[sl + 1] += cnt[sl];
+    {
+        int64_t *fill = (int64_t *)malloc(((size_t)ns + 1) * sizeof(int64_t));
+        if (!fill) {
+            rc = ORC_ENOMEM;
+        } else {
+            memcpy(fill, cnt, ((size_t)ns + 1) * sizeof(int64_t));
+            for (int64_t k = 0; k < p->n_beam; ++k) {
+                int64_t sl = nearest_slice(p->beam_xi[k], dxi);
+                if (sl >= 0 && sl < ns) {
+                    bpart *bp = &parts[fill[sl]++];
+                    bp->r = p->beam_r[k];
+                    bp->qw = p->beam_qw[k];
+                    bp->idx = k;
+                }
+            }
+            free(fill);
+        }
+    }
+    for (int64_t k = 0; k < p->n_beam; ++k) {
+        if (out->ez) out->ez[k] = 0.0;
+        if (out->wr) out->wr[k] = 0.0;
+        if (out->bt) out->bt[k] = 0.0;
+        if (out->psi) out->psi[k] = 0.0;
+    }
+
+    int have_prev = 0;
+    for (int32_t sl = 0; sl < nrun && !rc; ++sl) {
+        beam_slice bs = {0, NULL, NULL, NULL};
+        rc = beam_slice_build(&bs, cnt[sl + 1] - cnt[sl], parts + cnt[sl]);
+        if (rc)
+            break;
+        species_ws *e = &sp[0], *io = &sp[1];
+        /* 1. each species: sort, beam source, own psi and d_rho psi */
+        sp_own_potential(e, rho, ur, cw, ch, &bs, dxi);
+        sp_own_potential(io, rho + n, ur + n, cw + n, ch + n, &bs, dxi);
+        /* 2. totals of psi, d_rho psi at every ring (own + the other species
+              interpolated), then psibar, gamma, u_z, t */
+        for (int s = 0; s < 2; ++s) {
+            species_ws *me = &sp[s], *ot = &sp[1 - s];
+            for (int32_t i = 0; i < n; ++i) {
+                double x = me->r[i];
+                me->psi[i] = me->psi_o[i] + sp_interp(ot, ot->psi_o, ot->Ltot, 0, 0.0, x);
+                me->dpr[i] = me->dpr_o[i] + sp_interp(ot, ot->dpr_o, 0.0, 1, 0.0, x);
+                double pb = 1.0 - me->qm * me->psi[i];
+                double u = me->u[i];
+                me->psib[i] = pb;
+                me->gam[i] = (1.0 + u * u + pb * pb) / (2.0 * pb);
+                me->uz[i] = (1.0 + u * u - pb * pb) / (2.0 * pb);
+                me->t[i] = me->c[i] * u / (x * pb);
+            }
+        }
+        /* 3. d_zeta psi: own, then the totals */
+        sp_own_dzeta(e);
+        sp_own_dzeta(io);
+        for (int s = 0; s < 2; ++s) {
+            species_ws *me = &sp[s], *ot = &sp[1 - s];
+            for (int32_t i = 0; i < n; ++i)
+                me->dpz[i] = me->dpz_o[i] + sp_interp(ot, ot->dpz_o, -ot->Ttot, 2, 0.0, me->r[i]);
+        }
+        /* 4. B_theta^(p) from the electrons (Eqs. b_coeffs_1..3, q = -1, m = 1,
+              with the total fields at the electron rings), Eq. ai_bi */
+        for (int32_t i = 0; i < n; ++i) {
+            double r = e->r[i], u = e->u[i], w = e->c[i], pb = e->psib[i];
+            double g = e->gam[i], dpr = e->dpr[i], dpz = e->dpz[i];
+            double wr = w / r;
+            A[i] = wr / pb;
+            B[i] = -wr * g * dpr / (pb * pb) + wr * e->bb[i] / pb + (w / (r * r)) * u * u / (pb * pb) +
+                   wr * u * u * dpr / (pb * pb * pb) - wr * u * dpz / (pb * pb);
+            Cc[i] = -wr * (g / pb - 1.0 - u * u / (pb * pb));
+        }
+        rc = orc_bp_solve(n, e->r, A, B, Cc, ak, bk);
+        if (rc) {
+            beam_slice_free(&bs);
+            break;
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            double r = e->r[i];
+            e->bp[i] = 0.5 * ((ak[i] + ak[i + 1]) * r + (bk[i] + bk[i + 1]) / r);
+        }
+        /* the ions see the electrons' B^(p) interpolated */
+        for (int32_t i = 0; i < n; ++i)
+            io->bp[i] = sp_interp(e, e->bp, 0.0, 3, bk[n], io->r[i]);
+        /* ring dumps (ids: electrons 0..n-1, ions n..2n-1) */
+        size_t row = (size_t)sl * (size_t)n2;
+        for (int s = 0; s < 2; ++s) {
+            species_ws *me = &sp[s];
+            for (int32_t i = 0; i < n; ++i) {
+                int32_t id = me->order[i] + s * n;
+                if (out->ring_r) out->ring_r[row + id] = me->r[i];
+                if (out->ring_ur) out->ring_ur[row + id] = me->u[i];
+                if (out->ring_psi) out->ring_psi[row + id] = me->psi[i];
+                if (out->ring_dpsidr) out->ring_dpsidr[row + id] = me->dpr[i];
+                if (out->ring_dpsidz) out->ring_dpsidz[row + id] = me->dpz[i];
+                if (out->ring_bp) out->ring_bp[row + id] = me->bp[i];
+                if (out->ring_bb) out->ring_bb[row + id] = me->bb[i];
+                if (out->ring_psibar) out->ring_psibar[row + id] = me->psib[i];
+                if (out->ring_gamma) out->ring_gamma[row + id] = me->gam[i];
+                if (out->ring_uz) out->ring_uz[row + id] = me->uz[i];
+                if (out->ring_frprev) out->ring_frprev[row + id] = have_prev ? fr_prev[id] : 0.0;
+                if (out->ring_fuprev) out->ring_fuprev[row + id] = have_prev ? fu_prev[id] : 0.0;
+            }
+        }
+        /* 5. beam particles: exact sums of both species, electron B^(p) */
+        for (int64_t q = 0; q < bs.m; ++q) {
+            double x = bs.r[q], psi = 0.0, dpr = 0.0, dpz = 0.0, bpv = 0.0;
+            for (int s = 0; s < 2; ++s) {
+                double a1, a2, a3;
+                sp_exact_at(&sp[s], x, &a1, &a2, &a3);
+                psi += a1;
+                dpr += a2;
+                dpz += a3;
+            }
+            if (x > 0.0) {
+                int64_t k = lower_bound(e->r, n, x);
+                bpv = ak[k] * x + bk[k] / x;
+            }
+            double bbv = beam_field(&bs, x, dxi);
+            int64_t k = bs.idx[q];
+            if (out->ez) out->ez[k] = -dpz;
+            if (out->wr) out->wr[k] = -dpr;
+            if (out->bt) out->bt[k] = bpv + bbv;
+            if (out->psi) out->psi[k] = psi;
+        }
+        beam_slice_free(&bs);
+        out->slices_run = sl + 1;
+        /* guard (c11) over both species */
+        int ok = 1;
+        for (int s = 0; s < 2 && ok; ++s)
+            for (int32_t i = 0; i < n; ++i) {
+                species_ws *me = &sp[s];
+                if (!(me->psib[i] > 0.0) || !isfinite(me->psi[i]) || !isfinite(me->dpr[i]) ||
+                    !isfinite(me->dpz[i]) || !isfinite(me->bp[i]) || !isfinite(me->bb[i]) ||
+                    !isfinite(me->gam[i])) {
+                    ok = 0;
+                    break;
+                }
+            }
+        if (!ok) {
+            out->status = ORC_ENONFINITE;
+            out->fail_slice = sl;
+            break;
+        }
+        /* 6. push both species (AB2, Euler start, axis reflection) */
+        for (int s = 0; s < 2; ++s) {
+            species_ws *me = &sp[s];
+            for (int32_t i = 0; i < n; ++i) {
+                int32_t id = me->order[i] + s * n;
+                double pb = me->psib[i];
+                double fr = me->u[i] / pb;
+                double fu = -me->qm * (me->gam[i] * me->dpr[i] / pb - (me->bp[i] + me->bb[i]));
+                if (have_prev) {
+                    rho[id] = me->r[i] + dxi * (1.5 * fr - 0.5 * fr_prev[id]);
+                    ur[id] = me->u[i] + dxi * (1.5 * fu - 0.5 * fu_prev[id]);
+                } else {
+                    rho[id] = me->r[i] + dxi * fr;
+                    ur[id] = me->u[i] + dxi * fu;
+                }
+                fr_prev[id] = fr;
+                fu_prev[id] = fu;
+                if (rho[id] < 0.0) {
+                    rho[id] = -rho[id];
+                    ur[id] = -ur[id];
+                    fr_prev[id] = -fr_prev[id];
+                    fu_prev[id] = -fu_prev[id];
+                }
+            }
+        }
+        have_prev = 1;
+    }
+    if (out->final_r)
+        memcpy(out->final_r, rho, (size_t)n2 * sizeof(double));
+    if (out->final_ur)
+        memcpy(out->final_ur, ur, (size_t)n2 * sizeof(double));
+    free(st);
+    free(cnt);
+    free(parts);
+    free(ab);
+    sp_free(&sp[0]);
+    sp_free(&sp[1]);
+    return rc;
+}

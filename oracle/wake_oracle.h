@@ -88,6 +88,14 @@ int orc_bp_solve(int32_t n, const double *rho, const double *A, const double *B,
 /* Whole window (or its first max_slices slices when max_slices > 0). */
 int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out);
 
+/* The same with mobile ions of charge Z > 0 and mass M > 0 (electron
+   masses) as a second ring species on the same edges, in place of the
+   immobile column (Sec. II, multiple plasma species): ring outputs are
+   [n_steps][2 N] and final_r, final_ur [2 N], electrons by id 0..N-1, ions
+   N..2N-1. */
+int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_slices,
+                 orc_outputs *out);
+
 #ifdef __cplusplus
 }
 #endif

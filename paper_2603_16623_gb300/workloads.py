@@ -22,7 +22,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import List
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -50,6 +50,9 @@ class Wake:
     dxi: float
     n_steps: int
     density: float = 1.0
+    # mobile ions (charge Z, mass M in electron masses) as a second ring
+    # species on the same edges; None: an immobile ion column
+    ions: Optional[Tuple[float, float]] = None
 
     @property
     def n_rings(self) -> int:
