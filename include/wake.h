@@ -66,12 +66,27 @@ enum {
 
 /* Plasma column (Sec. II, ring macroparticles): ring j fills the cell
    [r_edges[j], r_edges[j+1]); it starts at the cell centre with u_r = 0 and
-   weight density * centre * width (Eq. macroparticle_weight). */
+   weight density * centre * width (Eq. macroparticle_weight).
+
+   Mobile ions (Sec. II, multiple plasma species): with ion_charge Z > 0 the
+   ions are a second ring species of charge Z and mass ion_mass M (electron
+   masses) on the same cells, of density density / Z (neutral), instead of
+   the immobile column.  Each species' psi, d_rho psi and d_zeta psi are
+   solved on its own rings and reach the other species' rings by linear
+   interpolation between its ring values; B_theta^(p) comes from the
+   electrons only; ions move with q/m = Z/M.  A wake then has 2 n_rings
+   rings: ids 0..n_rings-1 electrons, n_rings..2 n_rings-1 ions, in every
+   per-ring array of this interface (ring state, dumps).  n_rings <= 4096,
+   the one-CTA march (rings_per_thread and cluster_ctas must be 0). */
 typedef struct {
-    int32_t n_rings;          /* 1 <= n_rings <= wake_max_rings()                */
+    int32_t n_rings;          /* 1 <= n_rings <= wake_max_rings() (4096 with
+                                 mobile ions)                                   */
     const double *r_edges;    /* host, n_rings+1 values, r_edges[0] = 0,
                                  strictly increasing                            */
-    double density;           /* uniform plasma (= ion column) density, > 0     */
+    double density;           /* uniform electron density (= ion column
+                                 charge density), > 0                           */
+    double ion_charge;        /* 0: immobile ion column; > 0: mobile ions, Z   */
+    double ion_mass;          /* mobile ions: M in electron masses, > 0         */
 } wake_plasma_desc;
 
 /* A beam species (ultra-relativistic, frozen during a wake solve, Sec. II).

@@ -13,14 +13,18 @@ __device__ __forceinline__ float2 split_ff(double v) {
     return make_float2(h, (float)(v - (double)h));
 }
 
+// With mobile ions (n_total = 2 n), ring n + j is the ion ring of cell j,
+// with the signed charge weight -w (ions of density n / Z, charge Z).
 template <class R>
-__global__ void ring_init_kernel(const double* __restrict__ edges, int32_t n, double density, R* w, R* wh,
-                                 R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab) {
-    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        double d = edges[j + 1] - edges[j];
-        double c = 0.5 * (edges[j] + edges[j + 1]);
-        double wj = density * c * d;
-        double whj = density * (0.5 * c * d - 0.125 * d * d);
+__global__ void ring_init_kernel(const double* __restrict__ edges, int32_t n, int32_t n_total, double density, R* w,
+                                 R* wh, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_total; j += gridDim.x * blockDim.x) {
+        const int32_t cell = j < n ? j : j - n;
+        const double sign = j < n ? 1.0 : -1.0;
+        double d = edges[cell + 1] - edges[cell];
+        double c = 0.5 * (edges[cell] + edges[cell + 1]);
+        double wj = sign * density * c * d;
+        double whj = sign * density * (0.5 * c * d - 0.125 * d * d);
         w[j] = (R)wj;
         wh[j] = (R)whj;
         rho[j] = (R)c;
@@ -204,10 +208,22 @@ cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* ou
 }
 
 template <class R>
-cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
-                             R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st) {
-    int grid = (n + 255) / 256;
-    ring_init_kernel<R><<<grid, 256, 0, st>>>(edges, n, density, w, wh, rho, rho_lo, ur, frho, fur, rid, ctab);
+cudaError_t launch_ring_init(const double* edges, int32_t n, int32_t n_total, double density, R* w, R* wh, R* rho,
+                             R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st) {
+    int grid = (n_total + 255) / 256;
+    ring_init_kernel<R><<<grid, 256, 0, st>>>(edges, n, n_total, density, w, wh, rho, rho_lo, ur, frho, fur, rid,
+                                              ctab);
+    return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_march_ions(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                              int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
+                              cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(march_ions_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    march_ions_kernel<P><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, mb_cap);
     return cudaGetLastError();
 }
 
@@ -222,10 +238,14 @@ template cudaError_t launch_march<PrecF64>(const WakeDev<PrecF64>*, const int32_
                                            int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_march<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t, int32_t,
                                              int32_t, size_t, int32_t, cudaStream_t);
-template cudaError_t launch_ring_init<double>(const double*, int32_t, double, double*, double*, double*, double*,
-                                              double*, double*, double*, int32_t*, float4*, cudaStream_t);
-template cudaError_t launch_ring_init<float>(const double*, int32_t, double, float*, float*, float*, float*, float*,
-                                             float*, float*, int32_t*, float4*, cudaStream_t);
+template cudaError_t launch_ring_init<double>(const double*, int32_t, int32_t, double, double*, double*, double*,
+                                              double*, double*, double*, double*, int32_t*, float4*, cudaStream_t);
+template cudaError_t launch_ring_init<float>(const double*, int32_t, int32_t, double, float*, float*, float*, float*,
+                                             float*, float*, float*, int32_t*, float4*, cudaStream_t);
+template cudaError_t launch_march_ions<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
+                                                int32_t, size_t, int32_t, cudaStream_t);
+template cudaError_t launch_march_ions<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t,
+                                                  int32_t, int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_gather_by_id<double>(const int32_t*, const double*, double*, int32_t, cudaStream_t);
 template cudaError_t launch_gather_by_id<float>(const int32_t*, const float*, float*, int32_t, cudaStream_t);
 

@@ -65,6 +65,13 @@ struct WakeDev {
     // > 0: a march launch stops at the first slice boundary this many ns
     // after its start (on-chip kernels; batched steps of a serving loop)
     int64_t budget_ns;
+    // mobile ions (march_ions.cuh): n_ion > 0 rings per species, n = 2 n_ion,
+    // electrons at ids [0, n_ion), ions at [n_ion, n); w, wh are the signed
+    // charge weights -q w; ion_qm = Z / M; own-species fields per ring
+    int32_t n_ion, pad1;
+    double ion_qm;
+    A *psio, *dpro;
+    R* dpzo;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {

@@ -6,6 +6,7 @@
 #include "march.cuh"
 #include "march_cluster.cuh"
 #include "march_fast.cuh"
+#include "march_ions.cuh"
 
 namespace gbwake {
 template <class P>
@@ -23,9 +24,15 @@ cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_
                                  cudaStream_t st);
 // gathers (next slice, status) of n wakes' control words into out[2n]
 cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* out, cudaStream_t st);
+// n cells; n_total = n (electrons) or 2 n (electrons, then mobile ions)
 template <class R>
-cudaError_t launch_ring_init(const double* edges, int32_t n, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
-                             R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st);
+cudaError_t launch_ring_init(const double* edges, int32_t n, int32_t n_total, double density, R* w, R* wh, R* rho,
+                             R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st);
+// the march of wakes with mobile ions (march_ions.cuh), one block per wake
+template <class P>
+cudaError_t launch_march_ions(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                              int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
+                              cudaStream_t st);
 template <class R>
 cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_t n, cudaStream_t st);
 template <class R>

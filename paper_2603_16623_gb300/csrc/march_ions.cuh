@@ -1,0 +1,591 @@
+// march_ions.cuh -- the per-slice march of a wake with mobile ions.
+//
+// Electrons (q = -1, m = 1) and ions (q = +Z, m = M) are both ring species
+// on the same cells (Sec. II, multiple plasma species): ring ids 0..N-1 are
+// electrons, N..2N-1 ions, and the sorted arrays hold the electrons at
+// positions [0, N) and the ions at [N, 2N), each segment in radius order.
+// Each ring carries its signed charge weight c = -q w (electrons +w, ions -w
+// for neutrality), so that per species
+//   psi = sum c ln max(rho, rho_j),  d_rho psi = (1/rho) sum_{rho_j<rho} c_j,
+//   d_zeta psi = -sum_{rho_j>=rho} c_j u_j / (rho_j psibar_j),
+// psibar = 1 - (q/m) psi.  One block owns one wake; per slice:
+//   a2 sort each segment (stable w.r.t. the previous order)
+//   a3 B^(b) at all rings
+//   a4 per species: block scan of (c, c ln rho) -> its own psi, d_rho psi
+//      at its rings (self weight in d_rho psi)
+//   a5 totals at every ring: own + the other species' ring values linearly
+//      interpolated at the ring's radius; psibar, gamma, t
+//   a6 per species: block scan of t -> its own d_zeta psi; totals likewise
+//   a7 A, B, C over the electron rings (B_theta^(p) from electrons only)
+//   a8 B^(p) of the electrons (the two-sided solve of march.cuh); the ions
+//      see it interpolated
+//   a9 fields on beam particles (or query radii): exact sums of both species
+//   a10 AB2 push of both species with their q/m, axis reflection
+// Mixed precision keeps each ring radius as a float-float pair (rho, rho_lo)
+// through the AB2 push and takes ln rho as ln rho0 + log1p((rho - rho0) /
+// rho0) with ln rho0 float-float from the per-ring table: plain FP32 radii
+// would accumulate the push's rounding over the window, which near the axis
+// is a sizeable fraction of rho.
+// Interpolation of a species' ring values F at radius x: between the last
+// ring below x and the next; from the axis value below its first ring; to
+// the exact outside value at the plasma's initial edge rho_max beyond its
+// last ring; exact outside values beyond both.
+#pragma once
+
+#include "march.cuh"
+
+namespace gbwake {
+
+// ln rho of ring `id` at radius (r, r_lo) in the accumulator type
+__device__ __forceinline__ double ring_log(const float4*, int, double r, double) { return log(r); }
+__device__ __forceinline__ ff ring_log(const float4* ctab, int id, float r, float r_lo) {
+    const float4 c = ctab[3 * id];  // {rho0 (hi, lo), ln rho0 (hi, lo)}
+    const ff r0 = {c.x, c.y};
+    const float dl = ff_to_f(ff_acc(ff{r, r_lo}, ff_neg(r0)));
+    return ff_add_f(ff{c.z, c.w}, log1pf(dl / c.x));
+}
+// ln X of an arbitrary radius X (accumulator type), relative to the plasma
+// edge whose logarithm ln_e is known to the accumulator's precision
+__device__ __forceinline__ double acc_log(double X, double, double, double) { return log(X); }
+__device__ __forceinline__ ff acc_log(ff X, ff Xe, ff ln_e, float edge) {
+    return ff_add_f(ln_e, log1pf(ff_to_f(ff_acc(X, ff_neg(Xe))) / edge));
+}
+__device__ __forceinline__ double acc_mul_a(double a, double b) { return a * b; }
+__device__ __forceinline__ ff acc_mul_a(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ double acc_div(double a, double b) { return a / b; }
+__device__ __forceinline__ ff acc_div(ff a, ff b) {
+    const float q1 = a.hi / b.hi;
+    const ff rem = ff_acc(a, ff_neg(ff_mul_f(b, q1)));
+    return ff_fast_two_sum(q1, rem.hi / b.hi);
+}
+// ring radius at sorted position p in the accumulator type
+__device__ __forceinline__ double ring_radius(const double* hi, const double*, int p) { return hi[p]; }
+__device__ __forceinline__ ff ring_radius(const float* hi, const float* lo, int p) { return ff{hi[p], lo[p]}; }
+
+// rho + d in the state's arithmetic: FP64, or float-float (hi in r, lo in r_lo)
+__device__ __forceinline__ void radius_add(double& r, double&, double d) { r += d; }
+__device__ __forceinline__ void radius_add(float& r, float& r_lo, float d) {
+    const ff s = ff_add_f(ff{r, r_lo}, d);
+    r = s.hi;
+    r_lo = s.lo;
+}
+
+// Where radius X (hi part xh) falls among a species' n rings (hi radii rh,
+// lo parts rl, increasing): case 0 between its rings k-1 and k (k = 0: the
+// axis and ring 0), case 1 between its last ring and the plasma edge Xe,
+// case 2 outside both (exact outside values); wgt the linear weight of the
+// upper node, from radius differences taken in the accumulator type.
+template <class A, class R>
+struct Locate {
+    int where, k;
+    R wgt;   // the weight rounded to R
+    A wgtA;  // the weight in the accumulator type
+};
+template <class A, class R>
+__device__ __forceinline__ Locate<A, R> locate(const R* rh, const R* rl, int n, R edge, A Xe, A X, R xh) {
+    Locate<A, R> L;
+    L.k = lower_bound_dev(rh, n, xh);  // rings strictly below X
+    A Xl, Xu;
+    if (L.k >= n) {
+        if (!(xh < edge) || !(edge > rh[n - 1])) {
+            L.where = 2;
+            L.wgt = 0;
+            L.wgtA = acc_zero(A());
+            return L;
+        }
+        L.where = 1;
+        Xl = ring_radius(rh, rl, n - 1);
+        Xu = Xe;
+    } else {
+        L.where = 0;
+        Xl = L.k > 0 ? ring_radius(rh, rl, L.k - 1) : acc_zero(A());
+        Xu = ring_radius(rh, rl, L.k);
+    }
+    const A den = acc_sub(Xu, Xl);
+    L.wgtA = acc_to_r(den) > (R)0 ? acc_div(acc_sub(X, Xl), den) : acc_from_d(1.0, A());
+    L.wgt = acc_to_r(L.wgtA);
+    return L;
+}
+// F at the located radius from the species' ring values F (lower node F0 on
+// the axis, upper node Fe at the edge), in the accumulator type
+template <class A, class R>
+__device__ __forceinline__ A gather_acc(const Locate<A, R>& L, const A* F, int n, A F0, A Fe) {
+    A lo, up;
+    if (L.where == 1) {
+        lo = F[n - 1];
+        up = Fe;
+    } else {
+        lo = L.k > 0 ? F[L.k - 1] : F0;
+        up = F[L.k];
+    }
+    return acc_add(lo, acc_mul_a(acc_sub(up, lo), L.wgtA));
+}
+template <class A, class R>
+__device__ __forceinline__ R gather_r(const Locate<A, R>& L, const R* F, int n, R F0, R Fe) {
+    R lo, up;
+    if (L.where == 1) {
+        lo = F[n - 1];
+        up = Fe;
+    } else {
+        lo = L.k > 0 ? F[L.k - 1] : F0;
+        up = F[L.k];
+    }
+    return lo + (up - lo) * L.wgt;
+}
+
+template <class P>
+__global__ void __launch_bounds__(512)
+march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ order, int32_t max_slices,
+                  int32_t mode, int32_t mb_cap) {
+    using R = typename P::R;
+    using A = typename P::A;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_ctl[CTL_N];
+
+    const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
+    const int T = blockDim.x;
+    const int tid = threadIdx.x;
+    const int n = W.n;           // all rings
+    const int N = W.n_ion;       // rings per species
+    const int K = (N + T - 1) / T;
+    const int q0 = min(N, tid * K);
+    const int q1 = min(N, q0 + K);
+    const R qm[2] = {(R)-1, (R)W.ion_qm};
+
+    unsigned char* sscan = smem;
+    R* keys = reinterpret_cast<R*>(smem + kScanBytes);
+    int32_t* vals = reinterpret_cast<int32_t*>(keys + W.n_pad);
+    R* sR = keys;      // sorted ring radii, both segments (after the sort)
+    R* sB = keys + n;  // staged beam radii of the slice
+
+    if (tid < CTL_N) s_ctl[tid] = W.ctl[tid];
+    __syncthreads();
+    if (s_ctl[CTL_STATUS] != 0) return;
+    int slice = s_ctl[CTL_NEXT];
+    int buf = s_ctl[CTL_BUF];
+    int has_prev = s_ctl[CTL_PREV];
+    int status = 0, fail = -1;
+    const int s_end = mode == MODE_MARCH ? min(W.n_steps, slice + max_slices) : slice + 1;
+
+    const R edge = (R)W.rho_max;
+    const A Xe = acc_from_d(W.rho_max, A());          // the plasma edge, accumulator precision
+    const A ln_e = acc_from_d(log(W.rho_max), A());
+    const A inv_e = acc_from_d(1.0 / W.rho_max, A());
+    const R dxi = (R)W.dxi;
+    const R inv_2pi_dxi = (R)(1.0 / (6.283185307179586476925286766559 * W.dxi));
+    const A zeroA = acc_zero(A());
+
+    for (; slice < s_end; ++slice) {
+        // ---------------- a2: sort each segment by radius (stable)
+        {
+            R* rho = W.rho[buf];
+            bool ok = true;
+            for (int s = 0; s < 2; ++s)
+                for (int q = q0; q < q1; ++q)
+                    if (q + 1 < N && rho[s * N + q + 1] < rho[s * N + q]) ok = false;
+            if (!__syncthreads_and(ok)) {
+                const int nb = buf ^ 1;
+                for (int s = 0; s < 2; ++s) {
+                    const int base = s * N;
+                    for (int i = tid; i < W.n_pad; i += T) {
+                        keys[i] = i < N ? rho[base + i] : (R)INFINITY;
+                        vals[i] = i;
+                    }
+                    __syncthreads();
+                    for (int k = 2; k <= W.n_pad; k <<= 1) {
+                        for (int j = k >> 1; j > 0; j >>= 1) {
+                            for (int i = tid; i < W.n_pad; i += T) {
+                                int ixj = i ^ j;
+                                if (ixj > i) {
+                                    R ki = keys[i], kj = keys[ixj];
+                                    int vi = vals[i], vj = vals[ixj];
+                                    bool gt = (ki > kj) || (ki == kj && vi > vj);
+                                    if (gt == ((i & k) == 0)) {
+                                        keys[i] = kj; keys[ixj] = ki;
+                                        vals[i] = vj; vals[ixj] = vi;
+                                    }
+                                }
+                            }
+                            __syncthreads();
+                        }
+                    }
+                    for (int i = tid; i < N; i += T) {
+                        const int src = base + vals[i], dst = base + i;
+                        W.rho[nb][dst] = W.rho[buf][src];
+                        W.ur[nb][dst] = W.ur[buf][src];
+                        W.frho[nb][dst] = W.frho[buf][src];
+                        W.fur[nb][dst] = W.fur[buf][src];
+                        W.rid[nb][dst] = W.rid[buf][src];
+                        keys[i] = W.rho_lo[src];  // the sort keys are no longer needed
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < N; i += T) W.rho_lo[base + i] = keys[i];
+                    __syncthreads();
+                }
+                buf = nb;
+            }
+        }
+        R* rho = W.rho[buf];
+        R* ur = W.ur[buf];
+        R* frho = W.frho[buf];
+        R* fur = W.fur[buf];
+        const int32_t* rid = W.rid[buf];
+
+        // ---------------- stage ring radii and this slice's beam radii
+        const bool have_beam = W.nb > 0 && slice < W.n_steps;
+        int b0 = 0, m = 0;
+        R qtot = 0;
+        if (have_beam) {
+            b0 = W.boff[slice];
+            m = W.boff[slice + 1] - b0;
+            qtot = W.bTot[slice];
+        }
+        const bool staged = m <= mb_cap;
+        for (int p = tid; p < n; p += T) sR[p] = rho[p];
+        if (staged)
+            for (int q = tid; q < m; q += T) sB[q] = W.br[b0 + q];
+        __syncthreads();
+        const R* beamR = staged ? sB : (W.br + b0);
+
+        // ---------------- a3 + a4: beam field at rings; per species own psi, d_rho psi
+        A Stot[2], Ltot[2];
+        for (int s = 0; s < 2; ++s) {
+            const int base = s * N, rb = s * (N + 1);
+            Pair<A> loc = {zeroA, zeroA};
+            for (int q = q0; q < q1; ++q) {
+                const int p = base + q;
+                R r = sR[p];
+                const int id = rid[p];
+                R c = W.w[id];
+                R bbv = 0;
+                if (m > 0 && r > (R)0) {
+                    int lb = lower_bound_dev(beamR, m, r);
+                    R Q = lb < m ? W.bE[b0 + lb] : qtot;
+                    bbv = Q * inv_2pi_dxi / r;
+                }
+                W.bb[p] = bbv;
+                loc.x = acc_add_r(loc.x, c);
+                loc.y = acc_add(loc.y, acc_mul_r(ring_log(W.ctab, id, r, W.rho_lo[p]), c));
+            }
+            Pair<A> tot;
+            Pair<A> ex = block_excl_scan<false>(loc, OpAddPair(), Pair<A>{zeroA, zeroA},
+                                                reinterpret_cast<Pair<A>*>(sscan), tot);
+            Stot[s] = tot.x;
+            Ltot[s] = tot.y;
+            A S = ex.x, L = ex.y;
+            for (int q = q0; q < q1; ++q) {
+                const int p = base + q;
+                R r = sR[p];
+                int id = rid[p];
+                R c = W.w[id], ch = W.wh[id];
+                const A lnr = ring_log(W.ctab, id, r, W.rho_lo[p]);
+                A Lsuf = acc_sub(tot.y, L);
+                W.regS[rb + q] = S;
+                W.regL[rb + q] = Lsuf;
+                // own fields kept in the accumulator type: the two species'
+                // values are large and cancel to the small total
+                W.psio[p] = acc_add(Lsuf, acc_mul_a(S, lnr));
+                W.dpro[p] = acc_div(acc_add_r(S, ch), ring_radius(sR, W.rho_lo, p));
+                S = acc_add_r(S, c);
+                L = acc_add(L, acc_mul_r(lnr, c));
+            }
+            if (tid == 0) {
+                W.regS[rb + N] = tot.x;
+                W.regL[rb + N] = zeroA;
+                W.regT[rb + N] = (R)0;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- a5: totals of psi, d_rho psi; psibar, gamma, t
+        for (int s = 0; s < 2; ++s) {
+            const int base = s * N, ob = (1 - s) * N;
+            const A oS = Stot[1 - s];
+            const A psi_e = acc_mul_a(oS, ln_e), dpr_e = acc_mul_a(oS, inv_e);  // the other species at the edge
+            for (int q = q0; q < q1; ++q) {
+                const int p = base + q;
+                R r = sR[p], u = ur[p];
+                R c = W.w[rid[p]];
+                const A X = ring_radius(sR, W.rho_lo, p);
+                const auto Lc = locate(sR + ob, W.rho_lo + ob, N, edge, Xe, X, r);
+                A psiA, dprA;
+                if (Lc.where == 2) {
+                    psiA = acc_mul_a(oS, acc_log(X, Xe, ln_e, edge));
+                    dprA = acc_div(oS, X);
+                } else {
+                    psiA = gather_acc(Lc, W.psio + ob, N, Ltot[1 - s], psi_e);
+                    dprA = gather_acc(Lc, W.dpro + ob, N, zeroA, dpr_e);
+                }
+                R psi = acc_to_r(acc_add(W.psio[p], psiA));
+                R dprv = acc_to_r(acc_add(W.dpro[p], dprA));
+                R pb = (R)1 - qm[s] * psi;
+                W.psib[p] = pb;
+                W.gam[p] = ((R)1 + u * u + pb * pb) / ((R)2 * pb);
+                W.dpr[p] = dprv;
+                W.tt[p] = c * u / (r * pb);
+                if (mode == MODE_MARCH && W.dump_psi) {
+                    size_t row = (size_t)slice * n + rid[p];
+                    W.dump_psi[row] = psi;
+                    W.dump_dpr[row] = dprv;
+                }
+            }
+        }
+
+        // ---------------- a6: per species own d_zeta psi, then the totals
+        A Ttot[2];
+        for (int s = 0; s < 2; ++s) {
+            const int base = s * N, rb = s * (N + 1);
+            A tl = zeroA;
+            for (int q = q0; q < q1; ++q) tl = acc_add_r(tl, W.tt[base + q]);
+            A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot[s]);
+            A Tacc = Tex;
+            for (int q = q0; q < q1; ++q) {
+                const int p = base + q;
+                int id = rid[p];
+                R c = W.w[id], ch = W.wh[id];
+                R t = W.tt[p];
+                W.regT[rb + q] = acc_to_r(acc_sub(Ttot[s], Tacc));
+                Tacc = acc_add_r(Tacc, t);
+                R above = acc_to_r(acc_sub(Ttot[s], Tacc));
+                W.dpzo[p] = -(above + ((R)1 - ch / c) * t);
+            }
+        }
+        __syncthreads();
+        for (int s = 0; s < 2; ++s) {
+            const int base = s * N, ob = (1 - s) * N;
+            const R oT = acc_to_r(Ttot[1 - s]);
+            for (int q = q0; q < q1; ++q) {
+                const int p = base + q;
+                const auto Lc = locate(sR + ob, W.rho_lo + ob, N, edge, Xe, ring_radius(sR, W.rho_lo, p), sR[p]);
+                // no ring of the other species above: no d_zeta psi from it
+                R dpz = W.dpzo[p] + (Lc.where == 2 ? (R)0 : gather_r(Lc, W.dpzo + ob, N, -oT, (R)0));
+                W.tt[p] = dpz;  // t no longer needed: keep d_zeta psi
+                if (mode == MODE_MARCH && W.dump_dpz) W.dump_dpz[(size_t)slice * n + rid[p]] = dpz;
+            }
+        }
+
+        // ---------------- a7: A, B, C over the electron rings
+        for (int q = q0; q < q1; ++q) {
+            const int p = q;
+            R r = sR[p], u = ur[p];
+            R w = W.w[rid[p]];
+            R pb = W.psib[p], g = W.gam[p], dprv = W.dpr[p], dpz = W.tt[p], bbv = W.bb[p];
+            R wr = w / r, pb2 = pb * pb;
+            W.cA[p] = wr / pb;
+            W.cB[p] = -wr * g * dprv / pb2 + wr * bbv / pb + (w / (r * r)) * u * u / pb2 +
+                      wr * u * u * dprv / (pb2 * pb) - wr * u * dpz / pb2;
+            W.cC[p] = -wr * (g / pb - (R)1 - u * u / pb2);
+        }
+
+        // ---------------- a8: B_theta^(p) of the electrons (regions 0..N)
+        {
+            const Mat2<R> I2 = {1, 0, 0, 1};
+            Mat2<R> Mf = I2, Mb = I2;
+            for (int p = q0; p < q1; ++p) {
+                R r = sR[p], hA = (R)0.5 * W.cA[p];
+                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
+                Mf = OpMatLeft()(Mf, M);
+            }
+            for (int p = q1 - 1; p >= q0; --p) {
+                R r = sR[p], hA = (R)0.5 * W.cA[p];
+                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
+                Mb = OpMatLeft()(Mb, Mi);
+            }
+            Mat2<R> tf, tb;
+            Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
+            Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
+            if (tid == 0) {
+                W.Ra[0] = 1;
+                W.Rb[0] = 0;
+                W.Da[N] = 0;
+                W.Db[N] = 1;
+            }
+            for (int p = q0; p < q1; ++p) {
+                R r = sR[p], hA = (R)0.5 * W.cA[p];
+                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
+                Yf = OpMatLeft()(Yf, M);
+                W.Ra[p + 1] = Yf.m00;
+                W.Rb[p + 1] = Yf.m10;
+            }
+            A gl = zeroA, dl = zeroA;
+            for (int p = q1 - 1; p >= q0; --p) {
+                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
+                R hA = (R)0.5 * Ac;
+                R d0 = Yb.m01, d1 = Yb.m11;
+                R g0 = W.Ra[p + 1], g1 = W.Rb[p + 1];
+                R s0 = (R)0.25 * ((R)2 * Bc + Ac * Cc);
+                R s1 = (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r);
+                R wr = g0 * d1 - g1 * d0;
+                R gp = (s0 * d1 - s1 * d0) / wr;
+                R dp = (g0 * s1 - g1 * s0) / wr;
+                W.cB[p] = gp;
+                W.cC[p] = dp;
+                gl = acc_add_r(gl, gp);
+                dl = acc_add_r(dl, dp);
+                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
+                Yb = OpMatLeft()(Yb, Mi);
+                W.Da[p] = Yb.m01;
+                W.Db[p] = Yb.m11;
+            }
+            A g_tot, d_tot;
+            Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
+            A Gsuf = gd.y;
+            for (int p = q1 - 1; p >= q0; --p) {
+                Gsuf = acc_add_r(Gsuf, W.cB[p]);
+                R G = acc_to_r(Gsuf);
+                W.ak[p] = -G * W.Ra[p];
+                W.bk[p] = -G * W.Rb[p];
+            }
+            A Hex = gd.x;
+            for (int p = q0; p < q1; ++p) {
+                R H = acc_to_r(Hex);
+                W.ak[p] += H * W.Da[p];
+                W.bk[p] += H * W.Db[p];
+                Hex = acc_add_r(Hex, W.cC[p]);
+            }
+            if (tid == 0) {
+                R H = acc_to_r(d_tot);
+                W.ak[N] = H * W.Da[N];
+                W.bk[N] = H * W.Db[N];
+            }
+        }
+        __syncthreads();
+        // B^(p) at the electron rings, then interpolated at the ion rings
+        for (int p = q0; p < q1; ++p) {
+            R r = sR[p];
+            W.cA[p] = (R)0.5 * ((W.ak[p] + W.ak[p + 1]) * r + (W.bk[p] + W.bk[p + 1]) / r);
+        }
+        __syncthreads();
+        {
+            const R bN = W.bk[N];
+            for (int q = q0; q < q1; ++q) {
+                const int p = N + q;
+                const R x = sR[p];
+                const auto Lc = locate(sR, W.rho_lo, N, edge, Xe, ring_radius(sR, W.rho_lo, p), x);
+                W.cA[p] = Lc.where == 2 ? bN / x : gather_r(Lc, W.cA, N, (R)0, bN / edge);
+            }
+        }
+
+        // ---------------- guard, dumps
+        bool bad = false;
+        for (int s = 0; s < 2; ++s)
+            for (int q = q0; q < q1; ++q) {
+                const int p = s * N + q;
+                R r = sR[p];
+                R bpv = W.cA[p];
+                R pb = W.psib[p];
+                if (!(pb > (R)0) || !real_finite(pb) || !real_finite(W.dpr[p]) || !real_finite(W.tt[p]) ||
+                    !real_finite(bpv) || !real_finite(W.bb[p]) || !real_finite(W.gam[p]))
+                    bad = true;
+                if (mode == MODE_MARCH) {
+                    size_t row = (size_t)slice * n + rid[p];
+                    if (W.dump_r) W.dump_r[row] = r;
+                    if (W.dump_ur) {
+                        W.dump_ur[row] = ur[p];
+                        W.dump_bp[row] = bpv;
+                        W.dump_bb[row] = W.bb[p];
+                    }
+                }
+            }
+        bad = __syncthreads_or(bad);
+
+        // ---------------- a9: fields on beam particles (or query radii)
+        {
+            const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
+            for (int64_t q = tid; q < nq; q += T) {
+                R x;
+                if (mode == MODE_MARCH) x = staged ? beamR[q] : W.br[b0 + q];
+                else x = (R)W.rq[q];
+                R psi = 0, dprv = 0, dpz = 0, bpv = 0, bbv = 0;
+                if (x > (R)0) {
+                    // the species' enclosed charges and log sums cancel: add
+                    // them in the accumulator type before rounding
+                    A Ssum = zeroA, Lsum = zeroA;
+                    for (int s = 0; s < 2; ++s) {
+                        const int rb = s * (N + 1);
+                        int k = lower_bound_dev(sR + s * N, N, x);
+                        Ssum = acc_add(Ssum, W.regS[rb + k]);
+                        Lsum = acc_add(Lsum, W.regL[rb + k]);
+                        dpz -= W.regT[rb + k];
+                        if (s == 0) bpv = W.ak[k] * x + W.bk[k] / x;
+                    }
+                    psi = acc_to_r(acc_add(Lsum, acc_mul_r(Ssum, real_log(x))));
+                    dprv = acc_to_r(Ssum) / x;
+                    if (mode == MODE_MARCH) {
+                        bbv = W.bQs[b0 + q] * inv_2pi_dxi / x;
+                    } else if (m > 0) {
+                        int lb = lower_bound_dev(beamR, m, x);
+                        R Q = lb < m ? W.bE[b0 + lb] : qtot;
+                        bbv = Q * inv_2pi_dxi / x;
+                    }
+                } else {
+                    psi = acc_to_r(acc_add(W.regL[0], W.regL[N + 1]));
+                    dpz = -(W.regT[0] + W.regT[N + 1]);
+                }
+                if (mode == MODE_MARCH) {
+                    int64_t o = b0 + q;
+                    W.out_ez[o] = -dpz;
+                    W.out_wr[o] = -dprv;
+                    W.out_bt[o] = bpv + bbv;
+                    W.out_psi[o] = psi;
+                } else {
+                    if (W.q_ez) W.q_ez[q] = -dpz;
+                    if (W.q_wr) W.q_wr[q] = -dprv;
+                    if (W.q_bt) W.q_bt[q] = bpv + bbv;
+                    if (W.q_psi) W.q_psi[q] = psi;
+                }
+            }
+        }
+        if (mode != MODE_MARCH) break;
+        if (bad) {
+            status = 4;
+            fail = slice;
+            ++slice;
+            break;
+        }
+
+        // ---------------- a10: AB2 push of both species
+        for (int s = 0; s < 2; ++s)
+            for (int q = q0; q < q1; ++q) {
+                const int p = s * N + q;
+                R r = sR[p], u = ur[p];
+                R pb = W.psib[p];
+                R fr = u / pb;
+                R fu = -qm[s] * (W.gam[p] * W.dpr[p] / pb - (W.cA[p] + W.bb[p]));
+                R rn = r, rlo = W.rho_lo[p], un;
+                if (has_prev) {
+                    radius_add(rn, rlo, dxi * ((R)1.5 * fr - (R)0.5 * frho[p]));
+                    un = u + dxi * ((R)1.5 * fu - (R)0.5 * fur[p]);
+                } else {
+                    radius_add(rn, rlo, dxi * fr);
+                    un = u + dxi * fu;
+                }
+                if (rn < (R)0) {  // through the axis: the ring reappears at -rho
+                    rn = -rn;
+                    rlo = -rlo;
+                    un = -un;
+                    fr = -fr;
+                    fu = -fu;
+                }
+                rho[p] = rn;
+                W.rho_lo[p] = rlo;
+                ur[p] = un;
+                frho[p] = fr;
+                fur[p] = fu;
+            }
+        has_prev = 1;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
+        W.ctl[CTL_BUF] = buf;
+        W.ctl[CTL_PREV] = has_prev;
+        if (status) {
+            W.ctl[CTL_STATUS] = status;
+            W.ctl[CTL_FAIL] = fail;
+        }
+    }
+}
+
+}  // namespace gbwake

@@ -47,6 +47,7 @@ wake_status fail(wake_status st, const char* fmt, ...) {
     } while (0)
 
 constexpr int32_t kMaxRings = 8192;           // FP64 path (one CTA per wake, sort in shared memory)
+constexpr int32_t kMaxIonCells = 4096;        // mobile ions: rings per species (2 x 4096 rings per wake)
 constexpr int32_t kMaxRingsMixed = 65536;     // mixed path: a 16-CTA cluster of 512 threads x 8 rings
 constexpr int32_t kMaxSliceParticles = 8192;
 constexpr int32_t kDefaultThreads = 256;
@@ -62,6 +63,8 @@ int32_t next_pow2(int32_t v) {
 struct wake_handle {
     int32_t prec = WAKE_FP64;
     int32_t n = 0, n_steps = 0, n_pad = 0, threads = kDefaultThreads, flags = 0;
+    int32_t n_ion = 0;                      // > 0: mobile ions, rings per species (n = 2 n_ion)
+    double ion_qm = 0;                      // their Z / M
     double dxi = 0, density = 1, rho_max = 0;
     cudaStream_t st = nullptr;
     int64_t nb_total = 0;  // beam particles given by the caller
@@ -224,7 +227,8 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
     std::memcpy(&D, h->desc_host.data(), sizeof(D));
     const int32_t n = h->n, ns = h->n_steps;
     WK_CUDA(launch_reset_ctl(h->d_ctl, st));
-    WK_CUDA(launch_ring_init<R>(h->d_edges, n, h->density, const_cast<R*>(D.w), const_cast<R*>(D.wh), D.rho[0],
+    WK_CUDA(launch_ring_init<R>(h->d_edges, h->n_ion ? h->n_ion : n, n, h->density, const_cast<R*>(D.w),
+                                const_cast<R*>(D.wh), D.rho[0],
                                 D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], const_cast<float4*>(D.ctab),
                                 st));
     const size_t rb = h->real_bytes();
@@ -288,10 +292,13 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     D.dxi = h->dxi;
     D.density = h->density;
     D.rho_max = h->rho_max;
+    D.n_ion = h->n_ion;
+    D.ion_qm = h->ion_qm;
 
     // plasma column and ring state
-    WK_TRY(dalloc_t(h, (size_t)n + 1, &h->d_edges));
-    WK_CUDA(cudaMemcpyAsync(h->d_edges, plasma->r_edges, ((size_t)n + 1) * sizeof(double),
+    const int32_t n_cells = h->n_ion ? h->n_ion : n;
+    WK_TRY(dalloc_t(h, (size_t)n_cells + 1, &h->d_edges));
+    WK_CUDA(cudaMemcpyAsync(h->d_edges, plasma->r_edges, ((size_t)n_cells + 1) * sizeof(double),
                             cudaMemcpyHostToDevice, h->st));
     R *w, *wh;
     WK_TRY(dalloc_t(h, n, &w));
@@ -309,17 +316,23 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         h->d_rid[b] = D.rid[b];
     }
     WK_TRY(dalloc_t(h, n, &D.rho_lo));
-    if (h->fast_threads > 0) {
+    if (h->fast_threads > 0 || (h->n_ion > 0 && h->prec == WAKE_MIXED)) {
         float4* ct;
         WK_TRY(dalloc_t(h, (size_t)3 * n, &ct));
         D.ctab = ct;
     }
     R** scratch[] = {&D.bb, &D.psib, &D.gam, &D.dpr, &D.tt, &D.cA, &D.cB, &D.cC};
     for (R** sp : scratch) WK_TRY(dalloc_t(h, n, sp));
-    WK_TRY(dalloc_t(h, (size_t)n + 1, &D.regS));
-    WK_TRY(dalloc_t(h, (size_t)n + 1, &D.regL));
+    if (h->n_ion) {
+        WK_TRY(dalloc_t(h, n, &D.psio));
+        WK_TRY(dalloc_t(h, n, &D.dpro));
+        WK_TRY(dalloc_t(h, n, &D.dpzo));
+    }
+    // regions: n + 1 (one species), or n_ion + 1 per species
+    WK_TRY(dalloc_t(h, (size_t)n + 2, &D.regS));
+    WK_TRY(dalloc_t(h, (size_t)n + 2, &D.regL));
     R** regions[] = {&D.regT, &D.ak, &D.bk, &D.Ra, &D.Rb, &D.Da, &D.Db};
-    for (R** sp : regions) WK_TRY(dalloc_t(h, (size_t)n + 1, sp));
+    for (R** sp : regions) WK_TRY(dalloc_t(h, (size_t)n + 2, sp));
     WK_TRY(dalloc_t(h, CTL_N, &D.ctl));
     h->d_ctl = D.ctl;
 
@@ -507,6 +520,10 @@ wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_sli
     }
     int32_t mb_cap = 0;
     size_t smem = march_smem(h->n, h->n_pad, h->real_bytes(), kMaxSliceParticles, &mb_cap);
+    if (h->n_ion) {
+        WK_CUDA(launch_march_ions<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
+        return WAKE_OK;
+    }
     WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
     return WAKE_OK;
 }
@@ -661,8 +678,12 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     }
     int32_t mb_cap = 0;
     size_t smem = march_smem(n_max, pad_max, hs[0]->real_bytes(), kMaxSliceParticles, &mb_cap);
-    e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH, hs[0]->threads,
-                        smem, mb_cap, st);
+    if (hs[0]->n_ion)
+        e = launch_march_ions<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
+                                 hs[0]->threads, smem, mb_cap, st);
+    else
+        e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
+                            hs[0]->threads, smem, mb_cap, st);
     cudaFreeAsync(d_buf, st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
     return WAKE_OK;
@@ -678,6 +699,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
     for (int32_t i = 0; i < n; ++i) {
         int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
+        if (hs[i]->n_ion) key = -1;  // the two-species kernel
         auto it = std::find(keys.begin(), keys.end(), key);
         if (it == keys.end()) {
             keys.push_back(key);
@@ -959,9 +981,17 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     int32_t threads = cfg->block_threads ? cfg->block_threads : kDefaultThreads;
     if (threads < 64 || threads > 512 || threads % 32)
         return fail(WAKE_EINVAL, "wake_init: block_threads must be a multiple of 32 in [64, 512]");
-    const int32_t n = plasma->n_rings;
-    const int32_t max_rings = wake_max_rings(cfg->precision);
-    if (n < 1 || n > max_rings) return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]", max_rings);
+    const int32_t n_cells = plasma->n_rings;
+    const bool ions = plasma->ion_charge != 0.0;
+    if (ions && (!(plasma->ion_charge > 0.0) || !(plasma->ion_mass > 0.0) || !std::isfinite(plasma->ion_charge) ||
+                 !std::isfinite(plasma->ion_mass)))
+        return fail(WAKE_EINVAL, "wake_init: mobile ions need ion_charge > 0 and ion_mass > 0");
+    if (ions && (cfg->rings_per_thread || cfg->cluster_ctas))
+        return fail(WAKE_EINVAL, "wake_init: rings_per_thread and cluster_ctas do not apply with mobile ions");
+    const int32_t max_rings = ions ? kMaxIonCells : wake_max_rings(cfg->precision);
+    if (n_cells < 1 || n_cells > max_rings)
+        return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]%s", max_rings, ions ? " with mobile ions" : "");
+    const int32_t n = n_cells;
     if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");
     if (!(plasma->density > 0.0) || !std::isfinite(plasma->density))
         return fail(WAKE_EINVAL, "wake_init: density must be > 0");
@@ -985,9 +1015,11 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
 
     wake_handle* h = new wake_handle();
     h->prec = cfg->precision;
-    h->n = n;
+    h->n = ions ? 2 * n : n;
+    h->n_ion = ions ? n : 0;
+    h->ion_qm = ions ? plasma->ion_charge / plasma->ion_mass : 0.0;
     h->n_steps = cfg->n_steps;
-    h->n_pad = next_pow2(std::max(n, 2));
+    h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;
     h->flags = cfg->flags;
     h->dxi = cfg->dxi;
@@ -996,7 +1028,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->st = static_cast<cudaStream_t>(cuda_stream);
     FastShape shape;
     {
-        wake_status fs = fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
+        wake_status fs = ions ? WAKE_OK : fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
         if (fs != WAKE_OK) {
             delete h;
             return fs;

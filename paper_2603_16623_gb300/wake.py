@@ -38,7 +38,8 @@ _dp = C.POINTER(C.c_double)
 
 
 class wake_plasma_desc(C.Structure):
-    _fields_ = [("n_rings", C.c_int32), ("r_edges", _dp), ("density", C.c_double)]
+    _fields_ = [("n_rings", C.c_int32), ("r_edges", _dp), ("density", C.c_double), ("ion_charge", C.c_double),
+                ("ion_mass", C.c_double)]
 
 
 class wake_beam_desc(C.Structure):
@@ -137,12 +138,17 @@ class Wake:
 
     def __init__(self, edges, beams: Sequence = (), dxi: float = 0.01, n_steps: int = 1000,
                  precision: str = "mixed", density: float = 1.0, flags: int = 0,
-                 block_threads: int = 0, stream=None, rings_per_thread: int = 0, cluster_ctas: int = 0):
+                 block_threads: int = 0, stream=None, rings_per_thread: int = 0, cluster_ctas: int = 0,
+                 ions=None):
+        """ions: None (immobile ion column) or (Z, M) for mobile ions; the
+        wake then has 2 x cells rings (electrons, then ions) in every
+        per-ring array."""
         lib = load()
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32
         self.edges = _f64(edges)
-        self.n_rings = self.edges.shape[0] - 1
+        self.n_cells = self.edges.shape[0] - 1
+        self.n_rings = self.n_cells if ions is None else 2 * self.n_cells
         self.n_steps = int(n_steps)
         self._keep = [self.edges]
         # beams: numpy arrays, or pinned float64 torch CPU tensors (uploaded
@@ -153,7 +159,8 @@ class Wake:
         self.n_beam = int(sum(d.n for d in descs[:len(beams)]))
         cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads),
                           int(rings_per_thread), int(cluster_ctas))
-        plasma = wake_plasma_desc(self.n_rings, _dptr(self.edges), float(density))
+        z, m = (0.0, 0.0) if ions is None else (float(ions[0]), float(ions[1]))
+        plasma = wake_plasma_desc(self.n_cells, _dptr(self.edges), float(density), z, m)
         if stream is None:
             stream = _default_stream()
         self.stream = stream
@@ -164,6 +171,7 @@ class Wake:
 
     @classmethod
     def from_workload(cls, wake, **kw) -> "Wake":
+        kw.setdefault("ions", getattr(wake, "ions", None))
         return cls(wake.edges, wake.beams, wake.dxi, wake.n_steps, density=wake.density, **kw)
 
     def close(self):

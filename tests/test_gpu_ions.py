@@ -1,0 +1,191 @@
+"""GPU parity of wakes with mobile ions (the two-species march of
+march_ions.cuh) against the oracle's two-species march (orc_run_ions):
+electrons and ions as ring species on the same cells, each solved on its own
+rings and gathered into the other by linear interpolation, B_theta^(p) from
+the electrons, ions moving with q/m = Z/M (Sec. II, multiple plasma
+species).
+
+Tolerances as for electron-only wakes: 1e-10 norm-wise for FP64, 1e-5 for
+the mixed path on ring radii and on E_z, W_r at beam particles whose place
+among the rings (of either species) is unambiguous at the run's precision.
+Strong wakes are checked slice by slice through the checkpoint API (the
+oracle's state at slice n, one GPU slice, compared with the oracle's slice
+n and state n + 1)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_16623_gb300 import workloads as W
+from test_gpu_parity import FP64_TOL, MIXED_FIELD_TOL, MIXED_TOL, nerr, unambiguous
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2603_16623_gb300 import wake
+    wake.load()
+    yield
+
+
+def ion_wake(n=300, steps=500, nb0=1.5, ions=(1.0, 100.0), seed=61, edges=None):
+    drv = W.gaussian_beam(40_000, nb0, 0.3, 0.6, 1.8, seed=seed)
+    e = W.edges_uniform(n, 5.0) if edges is None else edges
+    return W.Wake(f"ions{seed}", e, [drv], 0.01, steps, ions=ions)
+
+
+def gpu_run(wk, precision, threads=0, dumps=True):
+    from paper_2603_16623_gb300 import wake as wm
+    g = wm.Wake.from_workload(wk, precision=precision, block_threads=threads,
+                              flags=wm.WAKE_DUMP_RING_FIELDS if dumps else 0)
+    assert g.n_rings == 2 * wk.n_rings
+    st, _, _, _ = g.run()
+    out = {"status": st, "progress": g.progress(), "beam": g.beam_fields(), "final": g.ring_state()}
+    if dumps:
+        out["rings"] = g.ring_dumps()
+    g.close()
+    return out
+
+
+def oracle_run(wk, dumps=True):
+    keys = ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb") if dumps else ()
+    return oracle.run_wake(wk, ring_dumps=keys)
+
+
+@pytest.mark.parametrize("threads", [64, 256])
+def test_fp64_ion_wake_matches_oracle(threads):
+    wk = ion_wake()
+    ref = oracle_run(wk)
+    assert ref.status == 0
+    # the ions have moved measurably
+    n = wk.n_rings
+    assert np.max(np.abs(ref.final_r[n:] - ref.rings["r"][0][n:])) > 1e-4
+    got = gpu_run(wk, "fp64", threads)
+    assert got["status"] == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_fp64_light_multiply_charged_ions_on_refined_cells():
+    """Z = 2, M = 25 (q/m = 0.08) on refined cells with a ragged ring count."""
+    wk = ion_wake(steps=400, nb0=3.0, ions=(2.0, 25.0), seed=62, edges=W.edges_refined(150, 1.0, 133, 5.0))
+    ref = oracle_run(wk)
+    assert ref.status == 0
+    got = gpu_run(wk, "fp64", 128)
+    assert got["status"] == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_mixed_ion_wake_within_tolerance():
+    wk = ion_wake(n=500, steps=600, seed=63)
+    ref = oracle_run(wk)
+    got = gpu_run(wk, "mixed", 256)
+    assert got["status"] == ref.status == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    ok = unambiguous(wk, ref.rings["r"], got["rings"]["r"])
+    assert ok.mean() > 0.95
+    for k in ("ez", "wr"):
+        assert nerr(got["beam"][k][ok], ref.beam[k][ok]) < MIXED_TOL, k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_one_step_parity_on_a_strong_ion_wake(precision):
+    """A dense narrow driver with light ions: rings cross and the ions
+    collapse onto the axis; every 50th slice is solved once on the GPU from
+    the oracle's state."""
+    from paper_2603_16623_gb300 import wake as wm
+    drv = W.gaussian_beam(60_000, 12.0, 0.15, 0.5, 2.0, seed=64)
+    wk = W.Wake("strong_ions", W.edges_uniform(400, 4.0), [drv], 0.01, 700, ions=(1.0, 20.0))
+    ref = oracle.run_wake(wk, ring_dumps=("r", "ur", "frprev", "fuprev", "psi", "dpsidr", "dpsidz", "bp", "bb"))
+    R = ref.rings
+    n2 = 2 * wk.n_rings
+    bad = []
+    for n in range(0, ref.slices_run - 1, 50):
+        g = wm.Wake.from_workload(wk, precision=precision, flags=wm.WAKE_DUMP_RING_FIELDS)
+        g.set_ring_state(n, R["r"][n], R["ur"][n], R["frprev"][n], R["fuprev"][n])
+        g.step_slices(1)
+        assert g.progress()[:2] == (n + 1, 0)
+        d = g.ring_dumps()
+        rho, ur = g.ring_state()
+        keep = np.ones(n2, dtype=bool)
+        if precision == "mixed":
+            # rings of one species tied in float may sort either way
+            for s in (0, 1):
+                idx = np.arange(s * wk.n_rings, (s + 1) * wk.n_rings)
+                order = idx[np.argsort(R["r"][n][idx], kind="stable")]
+                rs = R["r"][n][order]
+                close = np.diff(rs) <= 5e-7 * rs[1:]
+                keep[order[1:][close]] = False
+                keep[order[:-1][close]] = False
+            assert keep.mean() > 0.99
+        e = {k: nerr(d[k][n][keep], R[k][n][keep]) for k in ("psi", "dpsidr", "dpsidz", "bp", "bb")}
+        e["r"] = nerr(rho[keep], R["r"][n + 1][keep])
+        e["ur"] = nerr(ur[keep], R["ur"][n + 1][keep])
+        g.close()
+        for k, v in e.items():
+            tol = FP64_TOL if precision == "fp64" else MIXED_FIELD_TOL.get(k, MIXED_TOL)
+            if k == "ur":
+                tol = max(tol, 1e-14)
+            if not v < tol:
+                bad.append((n, k, v))
+    assert not bad, bad
+
+
+def test_ion_wakes_batched_equal_alone():
+    from paper_2603_16623_gb300 import wake as wm
+    wakes = [ion_wake(n=200, steps=300, seed=65), ion_wake(n=333, steps=250, ions=(1.0, 400.0), seed=66),
+             W.Wake("plain", W.edges_uniform(250, 5.0), [W.gaussian_beam(20_000, 1.0, 0.3, 0.6, 1.8, seed=67)],
+                    0.01, 280)]
+    alone = []
+    for wk in wakes:
+        g = wm.Wake.from_workload(wk, precision="mixed")
+        g.run()
+        alone.append((g.ring_state(), g.beam_fields(("ez", "wr"))))
+        g.close()
+    gs = [wm.Wake.from_workload(wk, precision="mixed") for wk in wakes]
+    wm.wake_batch_run(gs)
+    for g, (st, bf) in zip(gs, alone):
+        r, u = g.ring_state()
+        assert np.array_equal(r, st[0]) and np.array_equal(u, st[1])
+        f = g.beam_fields(("ez", "wr"))
+        assert np.array_equal(f["ez"], bf["ez"]) and np.array_equal(f["wr"], bf["wr"])
+        g.close()
+
+
+def test_ion_wake_checkpoint_round_trip_resumes_bitwise():
+    from paper_2603_16623_gb300 import wake as wm
+    wk = ion_wake(n=180, steps=300, seed=68)
+    for precision in ("fp64", "mixed"):
+        a = wm.Wake.from_workload(wk, precision=precision)
+        a.step_slices(110)
+        rho, ur, fr, fu = a.ring_state(history=True)
+        assert rho.shape == (2 * wk.n_rings,)
+        a.step_slices(1000)
+        b = wm.Wake.from_workload(wk, precision=precision)
+        b.set_ring_state(110, rho, ur, fr, fu)
+        b.step_slices(1000)
+        ra, rb = a.ring_state(), b.ring_state()
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1]), precision
+        a.close()
+        b.close()
+
+
+def test_ion_wake_rejects_bad_arguments():
+    from paper_2603_16623_gb300 import wake as wm
+    wk = ion_wake(n=50, steps=20)
+    for ions in ((-1.0, 10.0), (1.0, 0.0), (1.0, float("nan"))):
+        with pytest.raises(wm.WakeError):
+            wm.Wake.from_workload(wk, precision="mixed", ions=ions)
+    with pytest.raises(wm.WakeError):
+        wm.Wake.from_workload(wk, precision="mixed", rings_per_thread=4)
+    big = W.Wake("big", W.edges_uniform(4097, 5.0), [], 0.01, 10, ions=(1.0, 100.0))
+    with pytest.raises(wm.WakeError):
+        wm.Wake.from_workload(big, precision="mixed")
