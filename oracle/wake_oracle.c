@@ -586,7 +586,7 @@ static int64_t nearest_slice(double xi, double dxi)
 int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
 {
     if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
-        (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
+        p->cell_density || (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
         return ORC_EINVAL;
     for (int32_t j = 0; j < p->n_rings; ++j)
         if (!(p->edges[j + 1] > p->edges[j]))
@@ -923,6 +923,10 @@ int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_s
         !(ion_z > 0.0) || !(ion_m > 0.0) ||
         (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
         return ORC_EINVAL;
+    if (p->cell_density)
+        for (int32_t j = 0; j < p->n_rings; ++j)
+            if (!(p->cell_density[j] > 0.0))
+                return ORC_EINVAL;
     for (int32_t j = 0; j < p->n_rings; ++j)
         if (!(p->edges[j + 1] > p->edges[j]))
             return ORC_EINVAL;
@@ -943,7 +947,7 @@ int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_s
     species_ws sp[2];
     int rc = sp_alloc(&sp[0], n, -1.0, p->edges[n]);
     if (!rc) {
-        rc = sp_alloc(&sp[1], n, ion_z / ion_m, p->edges[n]);
+        rc = sp_alloc(&sp[1], n, isinf(ion_m) ? 0.0 : ion_z / ion_m, p->edges[n]);
         if (rc) sp_free(&sp[0]);
     }
     if (!st || !cnt || !parts || !ab || rc) {
@@ -961,7 +965,12 @@ int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_s
         sp_free(&sp[0]); sp_free(&sp[1]);
         return ORC_ENOMEM;
     }
-    orc_ring_init(n, p->edges, p->density, rho, NULL, w0, w0 + n);
+    /* Eq. macroparticle_weight with the cell's own density (uniform within
+       the cell), and the self weight of the cell below the ring */
+    for (int32_t j = 0; j < n; ++j) {
+        double dens_j = p->cell_density ? p->cell_density[j] : p->density;
+        orc_ring_init(1, p->edges + j, dens_j, rho + j, NULL, w0 + j, w0 + n + j);
+    }
     for (int32_t j = 0; j < n; ++j) {
         rho[n + j] = rho[j];
         cw[j] = w0[j];          /* electrons: c = -q w = +w */

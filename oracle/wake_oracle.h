@@ -31,6 +31,10 @@ typedef struct {
     const double *beam_qw;    /* [n_beam] charge sign x weight */
     double dxi;               /* step in xi (> 0) */
     int32_t n_steps;          /* slices in the window */
+    /* radial density profile: density of each cell [n_rings] (> 0), uniform
+       within a cell; NULL = `density` everywhere.  orc_run_ions only (the
+       ion rings carry the profile; orc_run's column is uniform). */
+    const double *cell_density;
 } orc_problem;
 
 typedef struct {
@@ -89,10 +93,11 @@ int orc_bp_solve(int32_t n, const double *rho, const double *A, const double *B,
 int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out);
 
 /* The same with mobile ions of charge Z > 0 and mass M > 0 (electron
-   masses) as a second ring species on the same edges, in place of the
-   immobile column (Sec. II, multiple plasma species): ring outputs are
-   [n_steps][2 N] and final_r, final_ur [2 N], electrons by id 0..N-1, ions
-   N..2N-1. */
+   masses; M = +inf: ions that never move) as a second ring species on the
+   same edges, in place of the immobile column (Sec. II, multiple plasma
+   species): ring outputs are [n_steps][2 N] and final_r, final_ur [2 N],
+   electrons by id 0..N-1, ions N..2N-1.  Both species follow the density
+   profile (p->cell_density, ions at 1/Z of it). */
 int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_slices,
                  orc_outputs *out);
 

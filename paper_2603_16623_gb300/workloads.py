@@ -50,9 +50,13 @@ class Wake:
     dxi: float
     n_steps: int
     density: float = 1.0
-    # mobile ions (charge Z, mass M in electron masses) as a second ring
-    # species on the same edges; None: an immobile ion column
+    # mobile ions (charge Z, mass M in electron masses; M = inf: ion rings
+    # that never move) as a second ring species on the same edges; None: an
+    # immobile ion column
     ions: Optional[Tuple[float, float]] = None
+    # radial density profile: density per cell (uniform within a cell), in
+    # place of the uniform `density`; needs ion rings (`ions`)
+    cell_density: Optional[np.ndarray] = None
 
     @property
     def n_rings(self) -> int:
@@ -70,6 +74,13 @@ class Wake:
 # ----------------------------------------------------------------------------
 # ring-cell edges
 # ----------------------------------------------------------------------------
+def parabolic_profile(edges: np.ndarray, n0: float = 1.0, w0: float = 2.0) -> np.ndarray:
+    """Density per cell of the parabolic channel n0 (1 + 4 r^2 / w0^4) (the
+    paper's guiding profile with k_p = 1), sampled at the cell centres."""
+    c = 0.5 * (edges[1:] + edges[:-1])
+    return n0 * (1.0 + 4.0 * c * c / w0 ** 4)
+
+
 def edges_uniform(n_rings: int, r_max: float) -> np.ndarray:
     return np.linspace(0.0, r_max, n_rings + 1, dtype=np.float64)
 

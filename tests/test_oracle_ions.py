@@ -120,3 +120,56 @@ def test_dense_electron_beam_pulls_ions_inward():
     assert inside.sum() > 5
     assert np.all(ur_ions[inside] < 0.0)
     assert np.all(res.final_r[n:][inside] < r0[inside])
+
+
+# --------------------------------------------------------------------------
+# radial density profiles (Sec. II: arbitrary profiles, carried by the rings
+# of both species; ion rings of infinite mass stand still)
+# --------------------------------------------------------------------------
+def test_unperturbed_profiled_plasma_has_no_field():
+    e = W.edges_refined(50, 1.0, 70, 6.0)
+    prof = W.parabolic_profile(e, 1.0, 3.0)
+    for ions in ((1.0, float("inf")), (1.0, 1836.0)):
+        res = oracle.run(e, [], [], [], 0.05, 40, ions=ions, cell_density=prof,
+                         ring_dumps=("r", "psi", "dpsidr", "dpsidz", "bp"))
+        assert res.status == 0
+        for k in ("psi", "dpsidr", "dpsidz", "bp"):
+            assert np.max(np.abs(res.rings[k])) == 0.0, k
+        assert np.array_equal(res.final_r, res.rings["r"][0])
+
+
+def test_uniform_profile_equals_the_scalar_density():
+    drv = _drv(1.0)
+    e = W.edges_uniform(120, 4.0)
+    a = oracle.run_wake(W.Wake("a", e, [drv], 0.01, 300, density=2.5, ions=(1.0, 100.0)), ring_dumps=("r",))
+    b = oracle.run_wake(W.Wake("b", e, [drv], 0.01, 300, density=1.0, ions=(1.0, 100.0),
+                               cell_density=np.full(120, 2.5)), ring_dumps=("r",))
+    assert np.array_equal(a.rings["r"], b.rings["r"]) and np.array_equal(a.beam["ez"], b.beam["ez"])
+
+
+def test_rings_oscillate_at_the_local_plasma_frequency():
+    """A weak, wide, short driver kicks the rings of a parabolic channel
+    n = 1 + r^2/16 (static ion rings); afterwards each ring oscillates at
+    the local plasma frequency sqrt(n(rho)) (its displacement delta moves
+    the enclosed ion charge by n rho delta: E_r = n delta)."""
+    n = 200
+    e = W.edges_uniform(n, 8.0)
+    c = 0.5 * (e[1:] + e[:-1])
+    prof = 1.0 + 4.0 * c * c / 64.0
+    drv = W.gaussian_beam(40_000, 0.002, 6.0, 0.3, 1.0, seed=5)
+    res = oracle.run_wake(W.Wake("osc", e, [drv], 0.01, 3000, ions=(1.0, float("inf")), cell_density=prof),
+                          ring_dumps=("r",), beam_fields=())
+    assert res.status == 0
+    r = res.rings["r"]
+    omegas, local = [], []
+    for j in range(10, n - 10, 30):
+        d = r[300:, j] - r[0, j]
+        d = d - d.mean()
+        f = np.abs(np.fft.rfft(d * np.hanning(d.shape[0])))
+        k = int(np.argmax(f[1:])) + 1
+        kk = k + 0.5 * (f[k - 1] - f[k + 1]) / (f[k - 1] - 2 * f[k] + f[k + 1])
+        omegas.append(2 * np.pi * kk / (d.shape[0] * 0.01))
+        local.append(np.sqrt(prof[j]))
+    omegas, local = np.array(omegas), np.array(local)
+    assert np.all(np.abs(omegas / local - 1.0) < 0.05), (omegas, local)
+    assert np.all(np.diff(omegas) > 0)
