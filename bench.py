@@ -43,6 +43,12 @@ UNIT = "ring-slices/s"
 # gamma/t 21, d_zeta psi 6, A/B/C 27, B_theta^(p) recursion and value 44,
 # AB2 push 13
 FLOPS_PER_RING_SLICE = 117
+# the same count for the two-species march with mobile ions (orc_run_ions):
+# per ring of either species beam field 2, prefix sums 4, own psi/d_rho psi
+# 5, their gather from the other species and the totals 11, psibar/gamma/t
+# 11, d_zeta psi (prefix, own, gather, total) 13, AB2 push 13; per electron
+# ring A/B/C 27 and B^(p) 44; per ion ring the B^(p) gather 6
+FLOPS_PER_RING_SLICE_IONS = (130 + 65) / 2
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
 SMS, FP32_LANES = 152, 128
 
@@ -229,6 +235,11 @@ def run_ours(args):
     if not args.skip_push:
         push = push_bench(args, gs, wakes, stream)
 
+    # ---- mobile ions: the two-species march on batched wakes
+    ions = None
+    if not args.skip_ions:
+        ions = ions_bench(args, wakes, stream)
+
     # ---- serving: Poisson arrivals of batched-workload wakes, continuous batching
     serving = None
     if not args.skip_serve:
@@ -287,6 +298,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + n_march_launches),
             "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "serving": serving,
             "beam_push": push,
+            "mobile_ions": _ions_roofline(ions, peak_tflops, sm_mhz),
             "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
             "wall_s": wall,
@@ -330,6 +342,60 @@ def push_bench(args, gs, wakes, stream):
     return {"particles": n_part, "ms_per_push": ms, "particles_per_s": n_part / (ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "bytes_per_particle": PUSH_BYTES_PER_PARTICLE, "peak_basis": "measured copy (MEASURED_PEAKS.json)"}}
+
+
+def ions_bench(args, wakes, stream):
+    """A batch of the workload's wakes of <= 4096 rings with mobile hydrogen
+    ions (Z = 1, M = 1836) in place of the ion column: batched reset + march,
+    CUDA-event timed; ring-slices count both species."""
+    import dataclasses
+    sel = [dataclasses.replace(wk, ions=(1.0, 1836.0)) for wk in wakes if wk.n_rings <= 4096][: args.ion_wakes]
+    res = _ions_batch(sel, stream)
+    res["ions"] = "Z = 1, M = 1836 (hydrogen), same cells as the electrons"
+    # a radial profile changes only the ring weights: the parabolic channel
+    # n = 1 + 4 r^2 / w0^4 (w0 = 3) with static ion rings
+    prof = [dataclasses.replace(wk, ions=(1.0, float("inf")), cell_density=W.parabolic_profile(wk.edges, 1.0, 3.0))
+            for wk in sel]
+    res["parabolic_static_ions"] = _ions_batch(prof, stream)
+    return res
+
+
+def _ions_batch(sel, stream):
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream) for wk in sel]
+    wm.wake_batch_reset(gs)
+    wm.wake_batch_run(gs)  # warm-up
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    wm.wake_batch_reset(gs)
+    ev[1].record(stream)
+    wm.wake_batch_run(gs)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    ring_slices, stopped = 0, 0
+    for g, wk in zip(gs, sel):
+        nxt, st, _ = g.progress()
+        ring_slices += 2 * wk.n_rings * nxt
+        stopped += int(st != 0)
+        g.close()
+    march_ms = ev[1].elapsed_time(ev[2])
+    step_ms = ev[0].elapsed_time(ev[2])
+    return {"wakes": len(sel), "rings_per_species": [min(wk.n_rings for wk in sel), max(wk.n_rings for wk in sel)],
+            "ring_slices": ring_slices, "wakes_stopped_by_breakdown": stopped,
+            "ms_per_step": step_ms, "march_ms": march_ms, "value": ring_slices / (step_ms / 1e3), "unit": UNIT}
+
+
+def _ions_roofline(ions, peak_tflops, sm_mhz):
+    if ions is None:
+        return None
+    achieved = FLOPS_PER_RING_SLICE_IONS * ions["ring_slices"] / (ions["march_ms"] / 1e3) / 1e12
+    ions["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                        "frac": achieved / peak_tflops, "traffic": None, "kernel": "march_ions_kernel<PrecMixed>",
+                        "flops_per_ring_slice": FLOPS_PER_RING_SLICE_IONS,
+                        "peak_basis": f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
+    return ions
 
 
 def serve_bench(args, wakes, pinned, stream, rank):
@@ -460,6 +526,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-push", action="store_true")
+    ap.add_argument("--skip-ions", action="store_true")
+    ap.add_argument("--ion-wakes", type=int, default=152)
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)

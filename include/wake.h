@@ -77,7 +77,13 @@ enum {
    electrons only; ions move with q/m = Z/M.  A wake then has 2 n_rings
    rings: ids 0..n_rings-1 electrons, n_rings..2 n_rings-1 ions, in every
    per-ring array of this interface (ring state, dumps).  n_rings <= 4096,
-   the one-CTA march (rings_per_thread and cluster_ctas must be 0). */
+   the one-CTA march (rings_per_thread and cluster_ctas must be 0).
+   ion_mass = +inf gives ion rings that never move.
+
+   Radial density profile (Sec. II, arbitrary profiles): cell_density (host,
+   n_rings values > 0, uniform within each cell; NULL = `density`
+   everywhere) sets both species' ring weights; it needs ion rings
+   (ion_charge > 0), which carry the profile of the background. */
 typedef struct {
     int32_t n_rings;          /* 1 <= n_rings <= wake_max_rings() (4096 with
                                  mobile ions)                                   */
@@ -86,7 +92,8 @@ typedef struct {
     double density;           /* uniform electron density (= ion column
                                  charge density), > 0                           */
     double ion_charge;        /* 0: immobile ion column; > 0: mobile ions, Z   */
-    double ion_mass;          /* mobile ions: M in electron masses, > 0         */
+    double ion_mass;          /* mobile ions: M in electron masses, > 0 or +inf */
+    const double *cell_density; /* NULL, or n_rings cell densities (ion rings) */
 } wake_plasma_desc;
 
 /* A beam species (ultra-relativistic, frozen during a wake solve, Sec. II).
@@ -105,8 +112,9 @@ typedef struct {
     int32_t n_steps;          /* slices in the window, 1..12288                  */
     int32_t precision;        /* WAKE_FP64 or WAKE_MIXED                         */
     int32_t flags;            /* WAKE_DUMP_* bits                                */
-    int32_t block_threads;    /* FP64: threads per wake (multiple of 32,
-                                 64..512); 0 = library default                  */
+    int32_t block_threads;    /* FP64 and mobile ions: threads per wake
+                                 (multiple of 32, 64..512); 0 = library
+                                 default (256; 512 with mobile ions)           */
     int32_t rings_per_thread; /* MIXED: 4 or 8 rings per thread; 0 = automatic  */
     int32_t cluster_ctas;     /* MIXED: CTAs per wake, 1..16 (> 1: a thread-
                                  block cluster); 0 = automatic.  The threads
@@ -194,10 +202,12 @@ wake_status wake_batch_get_beam_fields(int32_t n, wake_handle *const *handles, v
    Returns ENONFINITE if the wake stopped early (outputs still written). */
 wake_status wake_run(wake_handle *h, void *beam_ez, void *beam_wr, void *ring_r);
 
-/* Runs the rest of the window of n handles in ONE persistent launch (one
-   thread block walks one wake; blocks take wakes largest-first).  All
-   handles must share precision, stream and block_threads.  Returns OK when
-   the launch was enqueued; per-wake outcome via wake_get_progress. */
+/* Runs the rest of the window of n handles: one launch per kernel
+   configuration (launch shape, block size, mobile ions or not), run
+   concurrently (one thread block, or cluster, walks one wake; blocks take
+   wakes largest-first).  All handles must share precision and stream.
+   Returns OK when the launches were enqueued; per-wake outcome via
+   wake_get_progress. */
 wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
 
 /* Advances every wake by up to max_slices slices (fewer at the end of a
@@ -206,8 +216,8 @@ wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
    boundary at least that long after its start (it always does one slice):
    the step of a continuous-batching loop, whose wakes of different sizes
    then finish a step together.  Asynchronous on the handles' stream.
-   Errors: EINVAL (NULL handle, mixed precision/stream/block_threads,
-   negative limits), ECUDA. */
+   Errors: EINVAL (NULL handle, mixed precision or stream, negative
+   limits), ECUDA. */
 wake_status wake_batch_step(int32_t n, wake_handle *const *handles, int32_t max_slices,
                             int64_t time_budget_ns);
 

@@ -15,16 +15,20 @@ __device__ __forceinline__ float2 split_ff(double v) {
 
 // With mobile ions (n_total = 2 n), ring n + j is the ion ring of cell j,
 // with the signed charge weight -w (ions of density n / Z, charge Z).
+// A radial density profile gives each cell its own density (cell_density,
+// else the uniform density).
 template <class R>
-__global__ void ring_init_kernel(const double* __restrict__ edges, int32_t n, int32_t n_total, double density, R* w,
-                                 R* wh, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab) {
+__global__ void ring_init_kernel(const double* __restrict__ edges, const double* __restrict__ cell_density,
+                                 int32_t n, int32_t n_total, double density, R* w, R* wh, R* rho, R* rho_lo, R* ur,
+                                 R* frho, R* fur, int32_t* rid, float4* ctab) {
     for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_total; j += gridDim.x * blockDim.x) {
         const int32_t cell = j < n ? j : j - n;
         const double sign = j < n ? 1.0 : -1.0;
+        const double dens = cell_density ? cell_density[cell] : density;
         double d = edges[cell + 1] - edges[cell];
         double c = 0.5 * (edges[cell] + edges[cell + 1]);
-        double wj = sign * density * c * d;
-        double whj = sign * density * (0.5 * c * d - 0.125 * d * d);
+        double wj = sign * dens * c * d;
+        double whj = sign * dens * (0.5 * c * d - 0.125 * d * d);
         w[j] = (R)wj;
         wh[j] = (R)whj;
         rho[j] = (R)c;
@@ -208,11 +212,12 @@ cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* ou
 }
 
 template <class R>
-cudaError_t launch_ring_init(const double* edges, int32_t n, int32_t n_total, double density, R* w, R* wh, R* rho,
-                             R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st) {
+cudaError_t launch_ring_init(const double* edges, const double* cell_density, int32_t n, int32_t n_total,
+                             double density, R* w, R* wh, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid,
+                             float4* ctab, cudaStream_t st) {
     int grid = (n_total + 255) / 256;
-    ring_init_kernel<R><<<grid, 256, 0, st>>>(edges, n, n_total, density, w, wh, rho, rho_lo, ur, frho, fur, rid,
-                                              ctab);
+    ring_init_kernel<R><<<grid, 256, 0, st>>>(edges, cell_density, n, n_total, density, w, wh, rho, rho_lo, ur,
+                                              frho, fur, rid, ctab);
     return cudaGetLastError();
 }
 
@@ -238,10 +243,12 @@ template cudaError_t launch_march<PrecF64>(const WakeDev<PrecF64>*, const int32_
                                            int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_march<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t, int32_t,
                                              int32_t, size_t, int32_t, cudaStream_t);
-template cudaError_t launch_ring_init<double>(const double*, int32_t, int32_t, double, double*, double*, double*,
-                                              double*, double*, double*, double*, int32_t*, float4*, cudaStream_t);
-template cudaError_t launch_ring_init<float>(const double*, int32_t, int32_t, double, float*, float*, float*, float*,
-                                             float*, float*, float*, int32_t*, float4*, cudaStream_t);
+template cudaError_t launch_ring_init<double>(const double*, const double*, int32_t, int32_t, double, double*,
+                                              double*, double*, double*, double*, double*, double*, int32_t*,
+                                              float4*, cudaStream_t);
+template cudaError_t launch_ring_init<float>(const double*, const double*, int32_t, int32_t, double, float*, float*,
+                                             float*, float*, float*, float*, float*, int32_t*, float4*,
+                                             cudaStream_t);
 template cudaError_t launch_march_ions<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
                                                 int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_march_ions<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t,

@@ -25,9 +25,11 @@ cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_
 // gathers (next slice, status) of n wakes' control words into out[2n]
 cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* out, cudaStream_t st);
 // n cells; n_total = n (electrons) or 2 n (electrons, then mobile ions)
+// (cell_density: NULL, or n cell densities)
 template <class R>
-cudaError_t launch_ring_init(const double* edges, int32_t n, int32_t n_total, double density, R* w, R* wh, R* rho,
-                             R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid, float4* ctab, cudaStream_t st);
+cudaError_t launch_ring_init(const double* edges, const double* cell_density, int32_t n, int32_t n_total,
+                             double density, R* w, R* wh, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid,
+                             float4* ctab, cudaStream_t st);
 // the march of wakes with mobile ions (march_ions.cuh), one block per wake
 template <class P>
 cudaError_t launch_march_ions(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,

@@ -72,6 +72,7 @@ struct wake_handle {
     size_t alloc_bytes = 0;                 // device bytes held (wake_get_device_bytes)
     std::vector<int64_t> beam_n;            // particles per species
     std::vector<double> beam_q;             // charge sign per species
+    double* d_density = nullptr;            // cell densities (radial profile), or NULL
     double *d_edges = nullptr, *d_xi = nullptr, *d_r = nullptr, *d_w = nullptr, *d_qw = nullptr;
     double* d_ps[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // beam x, y, u_x, u_y, u_z (push)
     int32_t *d_slot = nullptr, *d_cnt = nullptr, *d_fill = nullptr, *d_boff = nullptr, *d_dmax = nullptr;
@@ -227,7 +228,7 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
     std::memcpy(&D, h->desc_host.data(), sizeof(D));
     const int32_t n = h->n, ns = h->n_steps;
     WK_CUDA(launch_reset_ctl(h->d_ctl, st));
-    WK_CUDA(launch_ring_init<R>(h->d_edges, h->n_ion ? h->n_ion : n, n, h->density, const_cast<R*>(D.w),
+    WK_CUDA(launch_ring_init<R>(h->d_edges, h->d_density, h->n_ion ? h->n_ion : n, n, h->density, const_cast<R*>(D.w),
                                 const_cast<R*>(D.wh), D.rho[0],
                                 D.rho_lo, D.ur[0], D.frho[0], D.fur[0], D.rid[0], const_cast<float4*>(D.ctab),
                                 st));
@@ -300,6 +301,11 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     WK_TRY(dalloc_t(h, (size_t)n_cells + 1, &h->d_edges));
     WK_CUDA(cudaMemcpyAsync(h->d_edges, plasma->r_edges, ((size_t)n_cells + 1) * sizeof(double),
                             cudaMemcpyHostToDevice, h->st));
+    if (plasma->cell_density) {
+        WK_TRY(dalloc_t(h, (size_t)n_cells, &h->d_density));
+        WK_CUDA(cudaMemcpyAsync(h->d_density, plasma->cell_density, (size_t)n_cells * sizeof(double),
+                                cudaMemcpyHostToDevice, h->st));
+    }
     R *w, *wh;
     WK_TRY(dalloc_t(h, n, &w));
     WK_TRY(dalloc_t(h, n, &wh));
@@ -699,7 +705,8 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
     for (int32_t i = 0; i < n; ++i) {
         int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
-        if (hs[i]->n_ion) key = -1;  // the two-species kernel
+        // the one-CTA kernels (plain and two-species) by their block size
+        if (!hs[i]->fast_threads) key = (hs[i]->n_ion ? -1 : -2) - 1024 * hs[i]->threads;
         auto it = std::find(keys.begin(), keys.end(), key);
         if (it == keys.end()) {
             keys.push_back(key);
@@ -984,14 +991,17 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     const int32_t n_cells = plasma->n_rings;
     const bool ions = plasma->ion_charge != 0.0;
     if (ions && (!(plasma->ion_charge > 0.0) || !(plasma->ion_mass > 0.0) || !std::isfinite(plasma->ion_charge) ||
-                 !std::isfinite(plasma->ion_mass)))
-        return fail(WAKE_EINVAL, "wake_init: mobile ions need ion_charge > 0 and ion_mass > 0");
+                 std::isnan(plasma->ion_mass)))
+        return fail(WAKE_EINVAL, "wake_init: mobile ions need ion_charge > 0 and ion_mass > 0 (or +inf)");
+    if (plasma->cell_density && !ions)
+        return fail(WAKE_EINVAL, "wake_init: a density profile needs ion rings (ion_charge > 0)");
     if (ions && (cfg->rings_per_thread || cfg->cluster_ctas))
         return fail(WAKE_EINVAL, "wake_init: rings_per_thread and cluster_ctas do not apply with mobile ions");
     const int32_t max_rings = ions ? kMaxIonCells : wake_max_rings(cfg->precision);
     if (n_cells < 1 || n_cells > max_rings)
         return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]%s", max_rings, ions ? " with mobile ions" : "");
     const int32_t n = n_cells;
+    if (ions && !cfg->block_threads) threads = 512;  // the two-species march: one CTA of 512 threads per wake
     if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");
     if (!(plasma->density > 0.0) || !std::isfinite(plasma->density))
         return fail(WAKE_EINVAL, "wake_init: density must be > 0");
@@ -999,6 +1009,10 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     for (int32_t j = 0; j < n; ++j)
         if (!(plasma->r_edges[j + 1] > plasma->r_edges[j]) || !std::isfinite(plasma->r_edges[j + 1]))
             return fail(WAKE_EINVAL, "wake_init: r_edges must be finite and strictly increasing (index %d)", j + 1);
+    if (plasma->cell_density)
+        for (int32_t j = 0; j < n; ++j)
+            if (!(plasma->cell_density[j] > 0.0) || !std::isfinite(plasma->cell_density[j]))
+                return fail(WAKE_EINVAL, "wake_init: cell_density[%d] must be finite and > 0", j);
     if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(WAKE_EINVAL, "wake_init: bad beams");
     int64_t nb = 0;
     for (int32_t b = 0; b < n_beams; ++b) {
@@ -1017,7 +1031,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->prec = cfg->precision;
     h->n = ions ? 2 * n : n;
     h->n_ion = ions ? n : 0;
-    h->ion_qm = ions ? plasma->ion_charge / plasma->ion_mass : 0.0;
+    h->ion_qm = ions && std::isfinite(plasma->ion_mass) ? plasma->ion_charge / plasma->ion_mass : 0.0;
     h->n_steps = cfg->n_steps;
     h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;
@@ -1205,9 +1219,8 @@ wake_status wake_batch_step(int32_t n, wake_handle* const* handles, int32_t max_
     if (n == 0 || max_slices == 0) return WAKE_OK;
     for (int32_t i = 0; i < n; ++i) {
         if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_step: handle %d is NULL", i);
-        if (handles[i]->prec != handles[0]->prec || handles[i]->st != handles[0]->st ||
-            handles[i]->threads != handles[0]->threads)
-            return fail(WAKE_EINVAL, "wake_batch_step: handles must share precision, stream and block_threads");
+        if (handles[i]->prec != handles[0]->prec || handles[i]->st != handles[0]->st)
+            return fail(WAKE_EINVAL, "wake_batch_step: handles must share precision and stream");
     }
     if (handles[0]->prec == WAKE_FP64) return batch_impl<PrecF64>(n, handles, max_slices, time_budget_ns);
     return batch_impl<PrecMixed>(n, handles, max_slices, time_budget_ns);

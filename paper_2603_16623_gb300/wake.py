@@ -39,7 +39,7 @@ _dp = C.POINTER(C.c_double)
 
 class wake_plasma_desc(C.Structure):
     _fields_ = [("n_rings", C.c_int32), ("r_edges", _dp), ("density", C.c_double), ("ion_charge", C.c_double),
-                ("ion_mass", C.c_double)]
+                ("ion_mass", C.c_double), ("cell_density", _dp)]
 
 
 class wake_beam_desc(C.Structure):
@@ -139,10 +139,11 @@ class Wake:
     def __init__(self, edges, beams: Sequence = (), dxi: float = 0.01, n_steps: int = 1000,
                  precision: str = "mixed", density: float = 1.0, flags: int = 0,
                  block_threads: int = 0, stream=None, rings_per_thread: int = 0, cluster_ctas: int = 0,
-                 ions=None):
-        """ions: None (immobile ion column) or (Z, M) for mobile ions; the
-        wake then has 2 x cells rings (electrons, then ions) in every
-        per-ring array."""
+                 ions=None, cell_density=None):
+        """ions: None (immobile ion column) or (Z, M) for mobile ions (M =
+        inf: ion rings that never move); the wake then has 2 x cells rings
+        (electrons, then ions) in every per-ring array.  cell_density: a
+        radial density profile, one value per cell (needs ions)."""
         lib = load()
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32
@@ -160,7 +161,10 @@ class Wake:
         cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads),
                           int(rings_per_thread), int(cluster_ctas))
         z, m = (0.0, 0.0) if ions is None else (float(ions[0]), float(ions[1]))
-        plasma = wake_plasma_desc(self.n_cells, _dptr(self.edges), float(density), z, m)
+        prof = None if cell_density is None else _f64(cell_density)
+        self._keep.append(prof)
+        plasma = wake_plasma_desc(self.n_cells, _dptr(self.edges), float(density), z, m,
+                                  _dptr(prof) if prof is not None else None)
         if stream is None:
             stream = _default_stream()
         self.stream = stream
@@ -172,6 +176,7 @@ class Wake:
     @classmethod
     def from_workload(cls, wake, **kw) -> "Wake":
         kw.setdefault("ions", getattr(wake, "ions", None))
+        kw.setdefault("cell_density", getattr(wake, "cell_density", None))
         return cls(wake.edges, wake.beams, wake.dxi, wake.n_steps, density=wake.density, **kw)
 
     def close(self):

@@ -189,3 +189,50 @@ def test_ion_wake_rejects_bad_arguments():
     big = W.Wake("big", W.edges_uniform(4097, 5.0), [], 0.01, 10, ions=(1.0, 100.0))
     with pytest.raises(wm.WakeError):
         wm.Wake.from_workload(big, precision="mixed")
+
+
+# ---------------------------------------------------------------------------
+# radial density profiles (carried by both ring species)
+# ---------------------------------------------------------------------------
+def profile_wake(ions, n=300, steps=450, seed=70, nb0=1.5):
+    e = W.edges_refined(120, 1.5, n - 120, 6.0)
+    drv = W.gaussian_beam(40_000, nb0, 0.3, 0.6, 1.8, seed=seed)
+    return W.Wake(f"profile{seed}", e, [drv], 0.01, steps, ions=ions, cell_density=W.parabolic_profile(e, 1.0, 3.0))
+
+
+def test_fp64_parabolic_channel_with_static_ion_rings_matches_oracle():
+    wk = profile_wake((1.0, float("inf")))
+    ref = oracle_run(wk)
+    assert ref.status == 0
+    n = wk.n_rings
+    assert np.array_equal(ref.final_r[n:], ref.rings["r"][0][n:])  # the ions stand still
+    got = gpu_run(wk, "fp64", 256)
+    assert got["status"] == 0
+    assert np.array_equal(got["final"][0][n:], ref.final_r[n:])
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_mixed_parabolic_channel_with_mobile_ions_within_tolerance():
+    wk = profile_wake((1.0, 200.0), seed=71)
+    ref = oracle_run(wk)
+    got = gpu_run(wk, "mixed", 256)
+    assert got["status"] == ref.status == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    ok = unambiguous(wk, ref.rings["r"], got["rings"]["r"])
+    assert ok.mean() > 0.95
+    for k in ("ez", "wr"):
+        assert nerr(got["beam"][k][ok], ref.beam[k][ok]) < MIXED_TOL, k
+
+
+def test_profile_rejects_bad_use():
+    from paper_2603_16623_gb300 import wake as wm
+    wk = profile_wake((1.0, 100.0), n=160, steps=20)
+    with pytest.raises(wm.WakeError):  # a profile needs ion rings
+        wm.Wake.from_workload(wk, precision="mixed", ions=None)
+    bad = np.array(wk.cell_density)
+    bad[7] = -1.0
+    with pytest.raises(wm.WakeError):
+        wm.Wake.from_workload(wk, precision="mixed", cell_density=bad)
