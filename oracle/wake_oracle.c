@@ -380,10 +380,13 @@ static double zeta_derivative(double suffix_above, double t_self, double w_self,
 
 /* All ring fields of one slice (Sec. III order: sources, psi and its
    derivatives, u_z and gamma, B_theta^(p)).  order[] holds the previous
-   radius order on entry and the new one on exit. */
+   radius order on entry and the new one on exit.  The beam source is
+   w1 x (the field of slice bs) + w2 x (that of bs2, if given): the RK4
+   stages between two slices take the mean of both. */
 static int slice_core(slice_ws *s, int32_t *order, const double *rho_id,
                       const double *ur_id, const double *w_id, const double *wh_id,
-                      double dens, double rho_max, const beam_slice *bs, double dxi)
+                      double dens, double rho_max, const beam_slice *bs, const beam_slice *bs2,
+                      double w1, double w2, double dxi)
 {
     int32_t n = s->n;
     /* sort by radius, stable w.r.t. the previous order */
@@ -396,8 +399,11 @@ static int slice_core(slice_ws *s, int32_t *order, const double *rho_id,
         s->wh[i] = wh_id[id];
     }
     /* gather the beam source at the rings */
-    for (int32_t i = 0; i < n; ++i)
-        s->bb[i] = beam_field(bs, s->r[i], dxi);
+    for (int32_t i = 0; i < n; ++i) {
+        s->bb[i] = w1 * beam_field(bs, s->r[i], dxi);
+        if (bs2)
+            s->bb[i] += w2 * beam_field(bs2, s->r[i], dxi);
+    }
     /* radial prefix sums of charge and of charge x ln rho (Eqs. dpsi_dr, psi) */
     double accS = 0.0, accL = 0.0;
     for (int32_t i = 0; i < n; ++i) {
@@ -529,7 +535,7 @@ int orc_slice_fields(int32_t n, const double *rho, const double *ur,
     if (!rc) {
         for (int32_t i = 0; i < n; ++i)
             order[i] = i;
-        rc = slice_core(&s, order, rho, ur, w, what, density, rho_max, &bs, dxi);
+        rc = slice_core(&s, order, rho, ur, w, what, density, rho_max, &bs, NULL, 1.0, 0.0, dxi);
     }
     if (!rc) {
         for (int32_t i = 0; i < n; ++i) {
@@ -586,7 +592,8 @@ static int64_t nearest_slice(double xi, double dxi)
 int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
 {
     if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
-        p->cell_density || (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
+        p->cell_density || (p->integrator != ORC_AB2 && p->integrator != ORC_RK4) ||
+        (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
         return ORC_EINVAL;
     for (int32_t j = 0; j < p->n_rings; ++j)
         if (!(p->edges[j + 1] > p->edges[j]))
@@ -600,20 +607,26 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
     out->fail_slice = -1;
     out->slices_run = 0;
 
-    /* state by ring id */
+    /* state by ring id; RK4 scratch: stage state, derivatives, stage order */
     double *st = (double *)calloc((size_t)n * 6, sizeof(double));
-    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    double *rk = (double *)calloc((size_t)n * 7, sizeof(double));
+    int32_t *order = (int32_t *)malloc((size_t)n * 2 * sizeof(int32_t));
     int64_t *cnt = (int64_t *)calloc((size_t)ns + 2, sizeof(int64_t));
     bpart *parts = (bpart *)malloc((size_t)(p->n_beam + 1) * sizeof(bpart));
     slice_ws s;
     int rc = ws_alloc(&s, n);
-    if (!st || !order || !cnt || !parts || rc) {
-        free(st); free(order); free(cnt); free(parts);
+    if (!st || !rk || !order || !cnt || !parts || rc) {
+        free(st); free(rk); free(order); free(cnt); free(parts);
         if (!rc) ws_free(&s);
         return ORC_ENOMEM;
     }
     double *rho = st, *ur = st + n, *w = st + 2 * n, *wh = st + 3 * n;
     double *fr_prev = st + 4 * n, *fu_prev = st + 5 * n;
+    /* RK4: stage state (rs, us, mirror sign sg), the last stage's
+       derivatives (ksr, ksu) and the weighted sums k1 + 2 k2 + 2 k3 + k4 */
+    double *rs = rk, *us = rk + n, *sg = rk + 2 * n, *ksr = rk + 3 * n, *ksu = rk + 4 * n;
+    double *sum_r = rk + 5 * n, *sum_u = rk + 6 * n;
+    int32_t *ord_s = order + n;
     orc_ring_init(n, p->edges, dens, rho, NULL, w, wh);
     for (int32_t j = 0; j < n; ++j)
         order[j] = j;
@@ -658,7 +671,7 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
         rc = beam_slice_build(&bs, cnt[sl + 1] - cnt[sl], parts + cnt[sl]);
         if (rc)
             break;
-        rc = slice_core(&s, order, rho, ur, w, wh, dens, rho_max, &bs, dxi);
+        rc = slice_core(&s, order, rho, ur, w, wh, dens, rho_max, &bs, NULL, 1.0, 0.0, dxi);
         if (rc) {
             beam_slice_free(&bs);
             break;
@@ -689,13 +702,86 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
             if (out->bt) out->bt[k] = bpv + bbv;
             if (out->psi) out->psi[k] = psi;
         }
-        beam_slice_free(&bs);
         out->slices_run = sl + 1;
         if (!ring_fields_ok(&s)) {
+            beam_slice_free(&bs);
             out->status = ORC_ENONFINITE;
             out->fail_slice = sl;
             break;
         }
+        if (p->integrator == ORC_RK4) {
+            /* classical RK4 over the slice (the integrator of Sec. II's
+               reference model): k1 at (xi_n, y_n) from the fields above,
+               k2, k3 at xi_n + dxi/2 with the mean of slices n and n+1 as
+               the beam source, k4 at xi_n + dxi with slice n+1's.  A stage
+               state below the axis is evaluated mirrored (rho, u -> -rho,
+               -u) and its derivative mirrored back: the ring equations are
+               odd in (rho, u).  Each stage sorts from the slice's order. */
+            beam_slice bsn = {0, NULL, NULL, NULL};
+            rc = sl + 1 < ns ? beam_slice_build(&bsn, cnt[sl + 2] - cnt[sl + 1], parts + cnt[sl + 1])
+                             : beam_slice_build(&bsn, 0, parts);
+            if (rc) {
+                beam_slice_free(&bs);
+                break;
+            }
+            for (int32_t i = 0; i < n; ++i) {
+                int32_t id = order[i];
+                double pb = s.psib[i];
+                ksr[id] = s.u[i] / pb;
+                ksu[id] = s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]);
+                sum_r[id] = ksr[id];
+                sum_u[id] = ksu[id];
+            }
+            static const double cs[3] = {0.5, 0.5, 1.0}, ws[3] = {2.0, 2.0, 1.0};
+            int bad = 0;
+            for (int stg = 0; stg < 3 && !bad; ++stg) {
+                for (int32_t id = 0; id < n; ++id) {
+                    double r = rho[id] + cs[stg] * dxi * ksr[id];
+                    double u = ur[id] + cs[stg] * dxi * ksu[id];
+                    sg[id] = r < 0.0 ? -1.0 : 1.0;
+                    rs[id] = sg[id] * r;
+                    us[id] = sg[id] * u;
+                }
+                memcpy(ord_s, order, (size_t)n * sizeof(int32_t));
+                if (stg < 2)
+                    rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bs, &bsn, 0.5, 0.5, dxi);
+                else
+                    rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bsn, NULL, 1.0, 0.0, dxi);
+                if (rc)
+                    break;
+                if (!ring_fields_ok(&s)) {
+                    bad = 1;
+                    break;
+                }
+                for (int32_t i = 0; i < n; ++i) {
+                    int32_t id = ord_s[i];
+                    double pb = s.psib[i];
+                    ksr[id] = sg[id] * (s.u[i] / pb);
+                    ksu[id] = sg[id] * (s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]));
+                    sum_r[id] += ws[stg] * ksr[id];
+                    sum_u[id] += ws[stg] * ksu[id];
+                }
+            }
+            beam_slice_free(&bsn);
+            beam_slice_free(&bs);
+            if (rc)
+                break;
+            if (bad) {
+                out->status = ORC_ENONFINITE;
+                out->fail_slice = sl;
+                break;
+            }
+            for (int32_t id = 0; id < n; ++id) {
+                rho[id] += dxi / 6.0 * sum_r[id];
+                ur[id] += dxi / 6.0 * sum_u[id];
+                if (rho[id] < 0.0) {
+                    rho[id] = -rho[id];
+                    ur[id] = -ur[id];
+                }
+            }
+            continue;
+        }
+        beam_slice_free(&bs);
         /* evolve rho, u_r to the next slice (Eqs. plasma_particle_motion_1,2
            with xi = -zeta; second-order Adams-Bashforth, Sec. III; forward
            Euler on the first step) */
@@ -729,6 +815,7 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
     if (out->final_ur)
         memcpy(out->final_ur, ur, (size_t)n * sizeof(double));
     free(st);
+    free(rk);
     free(order);
     free(cnt);
     free(parts);

@@ -20,6 +20,7 @@ extern "C" {
 #endif
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 4 };
+enum { ORC_AB2 = 0, ORC_RK4 = 1 };
 
 typedef struct {
     int32_t n_rings;          /* N >= 1 */
@@ -35,6 +36,9 @@ typedef struct {
        within a cell; NULL = `density` everywhere.  orc_run_ions only (the
        ion rings carry the profile; orc_run's column is uniform). */
     const double *cell_density;
+    /* ring integrator of orc_run: ORC_AB2 (Sec. III) or ORC_RK4 (the
+       Runge-Kutta alternative Sec. II names) */
+    int32_t integrator;
 } orc_problem;
 
 typedef struct {

@@ -57,6 +57,8 @@ class Wake:
     # radial density profile: density per cell (uniform within a cell), in
     # place of the uniform `density`; needs ion rings (`ions`)
     cell_density: Optional[np.ndarray] = None
+    # ring integrator: "ab2" (Sec. III) or "rk4"
+    integrator: str = "ab2"
 
     @property
     def n_rings(self) -> int:
