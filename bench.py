@@ -49,6 +49,11 @@ FLOPS_PER_RING_SLICE = 117
 # 11, d_zeta psi (prefix, own, gather, total) 13, AB2 push 13; per electron
 # ring A/B/C 27 and B^(p) 44; per ion ring the B^(p) gather 6
 FLOPS_PER_RING_SLICE_IONS = (130 + 65) / 2
+# and for the RK4 integrator (orc_run with integrator rk4): four field
+# evaluations of a3-a8 and B^(p) at the rings (104 each, +2 for the second
+# source at the two half steps), the derivatives (5 per stage), three stage
+# states (4 each), the weighted sums (4 per later stage) and the update (4)
+FLOPS_PER_RING_SLICE_RK4 = 4 * 104 + 2 * 2 + 4 * 5 + 3 * 4 + 3 * 4 + 4
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
 SMS, FP32_LANES = 152, 128
 
@@ -240,6 +245,11 @@ def run_ours(args):
     if not args.skip_ions:
         ions = ions_bench(args, wakes, stream)
 
+    # ---- the RK4 ring integrator on batched wakes
+    rk4 = None
+    if not args.skip_rk4:
+        rk4 = rk4_bench(args, wakes, stream)
+
     # ---- serving: Poisson arrivals of batched-workload wakes, continuous batching
     serving = None
     if not args.skip_serve:
@@ -299,6 +309,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "serving": serving,
             "beam_push": push,
             "mobile_ions": _ions_roofline(ions, peak_tflops, sm_mhz),
+            "rk4": _alu_roofline(rk4, peak_tflops, sm_mhz, FLOPS_PER_RING_SLICE_RK4, "march_rk4_kernel<PrecMixed>", 1),
             "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
             "wall_s": wall,
@@ -360,7 +371,28 @@ def ions_bench(args, wakes, stream):
     return res
 
 
-def _ions_batch(sel, stream):
+def rk4_bench(args, wakes, stream):
+    """The batched workload's wakes of <= 8192 rings with the RK4 ring
+    integrator (one CTA of 512 threads per wake): batched reset + march,
+    CUDA-event timed."""
+    import dataclasses
+    sel = [dataclasses.replace(wk, integrator="rk4") for wk in wakes if wk.n_rings <= 8192][: args.rk4_wakes]
+    res = _ions_batch(sel, stream, species=1)
+    res["integrator"] = "classical RK4 per slice (four field evaluations), electrons over the ion column"
+    return res
+
+
+def _alu_roofline(res, peak_tflops, sm_mhz, flops, kernel, species):
+    if res is None:
+        return None
+    achieved = flops * res["ring_slices"] / (res["march_ms"] / 1e3) / 1e12
+    res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                       "frac": achieved / peak_tflops, "traffic": None, "kernel": kernel, "flops_per_ring_slice": flops,
+                       "peak_basis": f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
+    return res
+
+
+def _ions_batch(sel, stream, species=2):
     import torch
     from paper_2603_16623_gb300 import wake as wm
     gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream) for wk in sel]
@@ -377,12 +409,12 @@ def _ions_batch(sel, stream):
     ring_slices, stopped = 0, 0
     for g, wk in zip(gs, sel):
         nxt, st, _ = g.progress()
-        ring_slices += 2 * wk.n_rings * nxt
+        ring_slices += species * wk.n_rings * nxt
         stopped += int(st != 0)
         g.close()
     march_ms = ev[1].elapsed_time(ev[2])
     step_ms = ev[0].elapsed_time(ev[2])
-    return {"wakes": len(sel), "rings_per_species": [min(wk.n_rings for wk in sel), max(wk.n_rings for wk in sel)],
+    return {"wakes": len(sel), "cells": [min(wk.n_rings for wk in sel), max(wk.n_rings for wk in sel)],
             "ring_slices": ring_slices, "wakes_stopped_by_breakdown": stopped,
             "ms_per_step": step_ms, "march_ms": march_ms, "value": ring_slices / (step_ms / 1e3), "unit": UNIT}
 
@@ -528,6 +560,8 @@ def main():
     ap.add_argument("--skip-push", action="store_true")
     ap.add_argument("--skip-ions", action="store_true")
     ap.add_argument("--ion-wakes", type=int, default=152)
+    ap.add_argument("--skip-rk4", action="store_true")
+    ap.add_argument("--rk4-wakes", type=int, default=152)
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)

@@ -53,6 +53,16 @@ enum {
 
 enum { WAKE_FP64 = 0, WAKE_MIXED = 1 };
 
+/* ring integrators (wake_config.integrator) */
+enum {
+    WAKE_AB2 = 0,  /* second-order Adams-Bashforth, forward Euler start (Sec. III) */
+    WAKE_RK4 = 1   /* classical fourth-order Runge-Kutta, the alternative Sec. II
+                      names: four field evaluations per slice, the beam source at
+                      the half step the mean of the two slices; a stage state
+                      below the axis is evaluated mirrored.  Electron-only wakes
+                      (no mobile ions), on the one-CTA march. */
+};
+
 /* flags of wake_config */
 enum {
     WAKE_DUMP_RING_R = 1,      /* keep ring radii at the start of every slice  */
@@ -112,9 +122,9 @@ typedef struct {
     int32_t n_steps;          /* slices in the window, 1..12288                  */
     int32_t precision;        /* WAKE_FP64 or WAKE_MIXED                         */
     int32_t flags;            /* WAKE_DUMP_* bits                                */
-    int32_t block_threads;    /* FP64 and mobile ions: threads per wake
+    int32_t block_threads;    /* FP64, mobile ions, RK4: threads per wake
                                  (multiple of 32, 64..512); 0 = library
-                                 default (256; 512 with mobile ions)           */
+                                 default (256; 512 with mobile ions or RK4)    */
     int32_t rings_per_thread; /* MIXED: 4 or 8 rings per thread; 0 = automatic  */
     int32_t cluster_ctas;     /* MIXED: CTAs per wake, 1..16 (> 1: a thread-
                                  block cluster); 0 = automatic.  The threads
@@ -122,6 +132,7 @@ typedef struct {
                                  cluster_ctas)) rounded up to a multiple of 32,
                                  at most 512, and no CTA may be left empty.
                                  Both must be 0 for WAKE_FP64.                  */
+    int32_t integrator;       /* WAKE_AB2 (0) or WAKE_RK4                        */
 } wake_config;
 
 typedef struct wake_handle wake_handle;

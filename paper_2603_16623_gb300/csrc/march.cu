@@ -249,6 +249,21 @@ template cudaError_t launch_ring_init<double>(const double*, const double*, int3
 template cudaError_t launch_ring_init<float>(const double*, const double*, int32_t, int32_t, double, float*, float*,
                                              float*, float*, float*, float*, float*, int32_t*, float4*,
                                              cudaStream_t);
+template <class P>
+cudaError_t launch_march_rk4(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                             int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
+                             cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(march_rk4_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    march_rk4_kernel<P><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, mb_cap);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_march_rk4<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
+                                               int32_t, size_t, int32_t, cudaStream_t);
+template cudaError_t launch_march_rk4<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t,
+                                                 int32_t, int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_march_ions<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
                                                 int32_t, size_t, int32_t, cudaStream_t);
 template cudaError_t launch_march_ions<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t,

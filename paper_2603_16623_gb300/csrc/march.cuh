@@ -72,6 +72,10 @@ struct WakeDev {
     double ion_qm;
     A *psio, *dpro;
     R* dpzo;
+    // RK4 (march_rk4.cuh): stage state (radius hi/lo, u, mirror sign), the
+    // last stage's derivatives, the stage's radius order
+    R *rk_r, *rk_rlo, *rk_u, *rk_sg, *rk_kr, *rk_ku;
+    int32_t* rk_perm;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {

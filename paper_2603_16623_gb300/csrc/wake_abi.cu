@@ -64,6 +64,7 @@ struct wake_handle {
     int32_t prec = WAKE_FP64;
     int32_t n = 0, n_steps = 0, n_pad = 0, threads = kDefaultThreads, flags = 0;
     int32_t n_ion = 0;                      // > 0: mobile ions, rings per species (n = 2 n_ion)
+    int32_t rk4 = 0;                        // the RK4 integrator (march_rk4.cuh)
     double ion_qm = 0;                      // their Z / M
     double dxi = 0, density = 1, rho_max = 0;
     cudaStream_t st = nullptr;
@@ -322,13 +323,18 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         h->d_rid[b] = D.rid[b];
     }
     WK_TRY(dalloc_t(h, n, &D.rho_lo));
-    if (h->fast_threads > 0 || (h->n_ion > 0 && h->prec == WAKE_MIXED)) {
+    if (h->fast_threads > 0 || ((h->n_ion > 0 || h->rk4) && h->prec == WAKE_MIXED)) {
         float4* ct;
         WK_TRY(dalloc_t(h, (size_t)3 * n, &ct));
         D.ctab = ct;
     }
     R** scratch[] = {&D.bb, &D.psib, &D.gam, &D.dpr, &D.tt, &D.cA, &D.cB, &D.cC};
     for (R** sp : scratch) WK_TRY(dalloc_t(h, n, sp));
+    if (h->rk4) {
+        R** rk[] = {&D.rk_r, &D.rk_rlo, &D.rk_u, &D.rk_sg, &D.rk_kr, &D.rk_ku};
+        for (R** sp : rk) WK_TRY(dalloc_t(h, n, sp));
+        WK_TRY(dalloc_t(h, n, &D.rk_perm));
+    }
     if (h->n_ion) {
         WK_TRY(dalloc_t(h, n, &D.psio));
         WK_TRY(dalloc_t(h, n, &D.dpro));
@@ -530,6 +536,10 @@ wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_sli
         WK_CUDA(launch_march_ions<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
         return WAKE_OK;
     }
+    if (h->rk4) {
+        WK_CUDA(launch_march_rk4<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
+        return WAKE_OK;
+    }
     WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
     return WAKE_OK;
 }
@@ -687,6 +697,9 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     if (hs[0]->n_ion)
         e = launch_march_ions<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
                                  hs[0]->threads, smem, mb_cap, st);
+    else if (hs[0]->rk4)
+        e = launch_march_rk4<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
+                                hs[0]->threads, smem, mb_cap, st);
     else
         e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
                             hs[0]->threads, smem, mb_cap, st);
@@ -706,7 +719,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
         int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
         // the one-CTA kernels (plain and two-species) by their block size
-        if (!hs[i]->fast_threads) key = (hs[i]->n_ion ? -1 : -2) - 1024 * hs[i]->threads;
+        if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * hs[i]->threads);
         auto it = std::find(keys.begin(), keys.end(), key);
         if (it == keys.end()) {
             keys.push_back(key);
@@ -1001,7 +1014,14 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     if (n_cells < 1 || n_cells > max_rings)
         return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]%s", max_rings, ions ? " with mobile ions" : "");
     const int32_t n = n_cells;
-    if (ions && !cfg->block_threads) threads = 512;  // the two-species march: one CTA of 512 threads per wake
+    if (cfg->integrator != WAKE_AB2 && cfg->integrator != WAKE_RK4)
+        return fail(WAKE_EINVAL, "wake_init: unknown integrator %d", cfg->integrator);
+    const bool rk4 = cfg->integrator == WAKE_RK4;
+    if (rk4 && (ions || cfg->rings_per_thread || cfg->cluster_ctas))
+        return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the one-CTA march (no mobile ions, "
+                                 "rings_per_thread and cluster_ctas 0)");
+    // the two-species and RK4 marches: one CTA of 512 threads per wake
+    if ((ions || rk4) && !cfg->block_threads) threads = 512;
     if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");
     if (!(plasma->density > 0.0) || !std::isfinite(plasma->density))
         return fail(WAKE_EINVAL, "wake_init: density must be > 0");
@@ -1032,6 +1052,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->n = ions ? 2 * n : n;
     h->n_ion = ions ? n : 0;
     h->ion_qm = ions && std::isfinite(plasma->ion_mass) ? plasma->ion_charge / plasma->ion_mass : 0.0;
+    h->rk4 = rk4 ? 1 : 0;
     h->n_steps = cfg->n_steps;
     h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;
@@ -1042,7 +1063,8 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->st = static_cast<cudaStream_t>(cuda_stream);
     FastShape shape;
     {
-        wake_status fs = ions ? WAKE_OK : fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
+        wake_status fs = (ions || rk4) ? WAKE_OK
+                                       : fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
         if (fs != WAKE_OK) {
             delete h;
             return fs;
