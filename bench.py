@@ -521,12 +521,15 @@ def run_uniform(args):
     """A batch of identical wakes (--uniform RINGS,SLICES,COPIES): one batched
     march, timed with CUDA events; the small, fixed case the kernel profiles
     are taken on.  Driver: n_b0 = 1, sigma_r = 0.5, sigma_z = 1, 20k particles;
-    uniform rings out to 6; d xi = 0.01."""
+    uniform rings out to 6; d xi = 0.01.  --uniform-kind: the AB2 march
+    ("ab2"), mobile hydrogen ions ("ions", RINGS per species) or RK4."""
     import torch
     from paper_2603_16623_gb300 import wake as wm
     n, slices, copies = (int(v) for v in args.uniform.split(","))
     drv = W.gaussian_beam(20_000, 1.0, 0.5, 1.0, 0.5, seed=5)
-    wk = W.Wake(f"uniform{n}", W.edges_uniform(n, 6.0), [drv], 0.01, slices)
+    kind = {"ab2": {}, "ions": {"ions": (1.0, 1836.0)}, "rk4": {"integrator": "rk4"}}[args.uniform_kind]
+    wk = W.Wake(f"uniform{n}", W.edges_uniform(n, 6.0), [drv], 0.01, slices, **kind)
+    n = n * (2 if args.uniform_kind == "ions" else 1)
     gs = [wm.Wake.from_workload(wk, precision="mixed") for _ in range(copies)]
     wm.wake_batch_run(gs)
     torch.cuda.synchronize()
@@ -538,7 +541,7 @@ def run_uniform(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    print(json.dumps({"case": "uniform", "rings": n, "slices": slices, "copies": copies,
+    print(json.dumps({"case": "uniform", "kind": args.uniform_kind, "rings": n, "slices": slices, "copies": copies,
                       "launch": gs[0].launch_config(), "march_ms": ms, "us_per_slice": ms * 1e3 / slices,
                       "ring_slices_per_s": n * slices * copies / (ms / 1e3)}))
 
@@ -569,6 +572,7 @@ def main():
     ap.add_argument("--serve-sm-fill", type=float, default=1.5,
                     help="admit while running wakes hold fewer than this many SMs' worth (x SM count); 0: no cap")
     ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
+    ap.add_argument("--uniform-kind", default="ab2", choices=["ab2", "ions", "rk4"])
     ap.add_argument("--rings-per-cta", type=int, default=0, help="cluster wakes: at most this many rings per CTA")
     args = ap.parse_args()
     if args.uniform:
