@@ -26,7 +26,8 @@ _ip = C.POINTER(C.c_int32)
 class _Problem(C.Structure):
     _fields_ = [("n_rings", C.c_int32), ("edges", _dp), ("density", C.c_double),
                 ("n_beam", C.c_int64), ("beam_xi", _dp), ("beam_r", _dp), ("beam_qw", _dp),
-                ("dxi", C.c_double), ("n_steps", C.c_int32), ("cell_density", _dp), ("integrator", C.c_int32)]
+                ("dxi", C.c_double), ("n_steps", C.c_int32), ("cell_density", _dp), ("integrator", C.c_int32),
+                ("grid_nr", C.c_int32), ("beam_species", _ip), ("n_species", C.c_int32)]
 
 
 _RING_DUMPS = ["ring_r", "ring_ur", "ring_psi", "ring_dpsidr", "ring_dpsidz", "ring_bp",
@@ -186,7 +187,7 @@ class OracleResult:
 def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: float = 1.0,
         max_slices: int = 0, beam_fields: Sequence[str] = ("ez", "wr", "bt", "psi"),
         ring_dumps: Sequence[str] = (), ions: Optional[Tuple[float, float]] = None,
-        cell_density=None, integrator: str = "ab2") -> OracleResult:
+        cell_density=None, integrator: str = "ab2", grid_nr: int = 0, beam_species=None) -> OracleResult:
     """March the whole window (or its first max_slices slices).
 
     beam_fields: subset of ez, wr, bt, psi (per particle, caller order).
@@ -197,15 +198,20 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     M = inf: ion rings that never move); ring dumps and final state then have
     2 N columns, ions after electrons.  cell_density: the density of each
     cell (a radial profile), with ions only.  integrator: "ab2" or "rk4"
-    (electron-only march)."""
+    (electron-only march).  grid_nr > 0: beam fields through adaptive beam
+    grids of grid_nr radial cells per species (beam_species: each
+    particle's species index; None: one species)."""
     edges = _f64(edges)
     bxi, br, bqw = _f64(beam_xi), _f64(beam_r), _f64(beam_qw)
     n_e = edges.shape[0] - 1
     n = n_e if ions is None else 2 * n_e
     nb = bxi.shape[0]
     cd = None if cell_density is None else _f64(cell_density)
+    sp = None if beam_species is None else np.ascontiguousarray(beam_species, dtype=np.int32)
+    n_sp = 1 if sp is None or sp.shape[0] == 0 else int(sp.max()) + 1
     prob = _Problem(n_e, _ptr(edges), density, nb, _ptr(bxi), _ptr(br), _ptr(bqw), dxi, n_steps, _ptr(cd),
-                    {"ab2": 0, "rk4": 1}[integrator])
+                    {"ab2": 0, "rk4": 1}[integrator], int(grid_nr),
+                    None if sp is None else sp.ctypes.data_as(_ip), n_sp)
     out = _Outputs()
     beam = {}
     for k in beam_fields:
@@ -240,4 +246,8 @@ def run_wake(wake, **kw) -> OracleResult:
     kw.setdefault("ions", getattr(wake, "ions", None))
     kw.setdefault("cell_density", getattr(wake, "cell_density", None))
     kw.setdefault("integrator", getattr(wake, "integrator", "ab2"))
+    kw.setdefault("grid_nr", getattr(wake, "grid_nr", 0))
+    if wake.beams:
+        kw.setdefault("beam_species", np.concatenate([np.full(b.n, i, dtype=np.int32)
+                                                      for i, b in enumerate(wake.beams)]))
     return run(wake.edges, xi, r, qw, wake.dxi, wake.n_steps, density=wake.density, **kw)

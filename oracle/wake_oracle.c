@@ -378,15 +378,59 @@ static double zeta_derivative(double suffix_above, double t_self, double w_self,
     return -(suffix_above + (1.0 - wh_self / w_self) * t_self);
 }
 
+/* The adaptive beam grids of one slice (Sec. IV): species b has nr radial
+   cells of width R[b] / nr; B[b (nr + 1) + j] is its B^(b) at node r_j =
+   j R[b] / nr: the slice's charge of species b strictly inside r_j over
+   2 pi dxi r_j (0 on the axis). */
+typedef struct {
+    int32_t nsp, nr;
+    const double *R;
+    double *B;
+} ag_slice;
+
+/* Node index j with r_j <= x < r_{j+1} for x >= 0 (nodes j dr, the
+   comparison as written: j dr <= x), clamped to [0, nr - 1]. */
+static int32_t ag_cell(double x, double dr, int32_t nr)
+{
+    int32_t j = (int32_t)floor(x / dr);
+    if (j > nr - 1) j = nr - 1;
+    if (j < 0) j = 0;
+    while (j > 0 && (double)j * dr > x) --j;
+    while (j < nr - 1 && (double)(j + 1) * dr <= x) ++j;
+    return j;
+}
+
+/* B^(b) of species b at radius rho from its grid: linear between the nodes
+   inside the grid, B_N r_N / rho beyond it (Sec. IV). */
+static double ag_species_field(const ag_slice *g, int32_t b, double rho)
+{
+    const double *B = g->B + (size_t)b * (g->nr + 1);
+    double R = g->R[b], dr = R / g->nr;
+    if (rho >= R)
+        return B[g->nr] * R / rho;
+    int32_t j = ag_cell(rho, dr, g->nr);
+    double t = (rho - (double)j * dr) / dr;
+    return (1.0 - t) * B[j] + t * B[j + 1];
+}
+
+static double ag_field(const ag_slice *g, double rho)
+{
+    double v = 0.0;
+    for (int32_t b = 0; b < g->nsp; ++b)
+        v += ag_species_field(g, b, rho);
+    return v;
+}
+
 /* All ring fields of one slice (Sec. III order: sources, psi and its
    derivatives, u_z and gamma, B_theta^(p)).  order[] holds the previous
    radius order on entry and the new one on exit.  The beam source is
    w1 x (the field of slice bs) + w2 x (that of bs2, if given): the RK4
-   stages between two slices take the mean of both. */
+   stages between two slices take the mean of both; with beam grids (ag)
+   the grids' field instead. */
 static int slice_core(slice_ws *s, int32_t *order, const double *rho_id,
                       const double *ur_id, const double *w_id, const double *wh_id,
                       double dens, double rho_max, const beam_slice *bs, const beam_slice *bs2,
-                      double w1, double w2, double dxi)
+                      double w1, double w2, const ag_slice *ag, double dxi)
 {
     int32_t n = s->n;
     /* sort by radius, stable w.r.t. the previous order */
@@ -400,6 +444,10 @@ static int slice_core(slice_ws *s, int32_t *order, const double *rho_id,
     }
     /* gather the beam source at the rings */
     for (int32_t i = 0; i < n; ++i) {
+        if (ag) {
+            s->bb[i] = ag_field(ag, s->r[i]);
+            continue;
+        }
         s->bb[i] = w1 * beam_field(bs, s->r[i], dxi);
         if (bs2)
             s->bb[i] += w2 * beam_field(bs2, s->r[i], dxi);
@@ -535,7 +583,7 @@ int orc_slice_fields(int32_t n, const double *rho, const double *ur,
     if (!rc) {
         for (int32_t i = 0; i < n; ++i)
             order[i] = i;
-        rc = slice_core(&s, order, rho, ur, w, what, density, rho_max, &bs, NULL, 1.0, 0.0, dxi);
+        rc = slice_core(&s, order, rho, ur, w, what, density, rho_max, &bs, NULL, 1.0, 0.0, NULL, dxi);
     }
     if (!rc) {
         for (int32_t i = 0; i < n; ++i) {
@@ -593,8 +641,13 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
 {
     if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
         p->cell_density || (p->integrator != ORC_AB2 && p->integrator != ORC_RK4) ||
+        p->grid_nr < 0 || (p->grid_nr > 0 && (p->integrator != ORC_AB2 || p->n_species < 1)) ||
         (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
         return ORC_EINVAL;
+    if (p->grid_nr > 0 && p->beam_species)
+        for (int64_t k = 0; k < p->n_beam; ++k)
+            if (p->beam_species[k] < 0 || p->beam_species[k] >= p->n_species)
+                return ORC_EINVAL;
     for (int32_t j = 0; j < p->n_rings; ++j)
         if (!(p->edges[j + 1] > p->edges[j]))
             return ORC_EINVAL;
@@ -665,13 +718,56 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
         if (out->psi) out->psi[k] = 0.0;
     }
 
+    /* the adaptive beam grids (Sec. IV): per species nr cells out to (1 +
+       1/nr) x its largest radius, so that every particle lies strictly
+       inside; node fields [species][nr + 1][psi, dpr, dpz, bt] */
+    const int32_t nr = p->grid_nr, nsp = nr > 0 ? p->n_species : 0;
+    double *agR = NULL, *agB = NULL, *agF = NULL;
+    ag_slice ag = {nsp, nr, NULL, NULL};
+    if (nr > 0 && !rc) {
+        agR = (double *)calloc((size_t)nsp, sizeof(double));
+        agB = (double *)calloc((size_t)nsp * (nr + 1), sizeof(double));
+        agF = (double *)calloc((size_t)nsp * (nr + 1) * 4, sizeof(double));
+        if (!agR || !agB || !agF) {
+            rc = ORC_ENOMEM;
+        } else {
+            for (int64_t k = 0; k < p->n_beam; ++k) {
+                int32_t b = p->beam_species ? p->beam_species[k] : 0;
+                if (p->beam_r[k] > agR[b]) agR[b] = p->beam_r[k];
+            }
+            for (int32_t b = 0; b < nsp; ++b)
+                agR[b] = (agR[b] > 1e-12 ? agR[b] : 1e-12) * (1.0 + 1.0 / nr);
+            ag.R = agR;
+            ag.B = agB;
+        }
+    }
+
     int have_prev = 0;
     for (int32_t sl = 0; sl < nrun && !rc; ++sl) {
         beam_slice bs = {0, NULL, NULL, NULL};
         rc = beam_slice_build(&bs, cnt[sl + 1] - cnt[sl], parts + cnt[sl]);
         if (rc)
             break;
-        rc = slice_core(&s, order, rho, ur, w, wh, dens, rho_max, &bs, NULL, 1.0, 0.0, dxi);
+        if (nr > 0) {
+            /* B^(b) at the grid nodes: each particle's charge reaches the
+               nodes strictly above it */
+            memset(agB, 0, (size_t)nsp * (nr + 1) * sizeof(double));
+            for (int64_t q = 0; q < bs.m; ++q) {
+                int32_t b = p->beam_species ? p->beam_species[bs.idx[q]] : 0;
+                double dr = agR[b] / nr;
+                int32_t j = ag_cell(bs.r[q], dr, nr) + 1;  /* the first node above the particle */
+                agB[(size_t)b * (nr + 1) + j] += p->beam_qw[bs.idx[q]];
+            }
+            for (int32_t b = 0; b < nsp; ++b) {
+                double *B = agB + (size_t)b * (nr + 1), acc = 0.0, dr = agR[b] / nr;
+                B[0] = 0.0;
+                for (int32_t j = 1; j <= nr; ++j) {
+                    acc += B[j];
+                    B[j] = acc / (ORC_2PI * dxi * ((double)j * dr));
+                }
+            }
+        }
+        rc = slice_core(&s, order, rho, ur, w, wh, dens, rho_max, &bs, NULL, 1.0, 0.0, nr > 0 ? &ag : NULL, dxi);
         if (rc) {
             beam_slice_free(&bs);
             break;
@@ -692,11 +788,40 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
             if (out->ring_frprev) out->ring_frprev[row + id] = have_prev ? fr_prev[id] : 0.0;
             if (out->ring_fuprev) out->ring_fuprev[row + id] = have_prev ? fu_prev[id] : 0.0;
         }
-        /* fields on the beam particles of this slice */
+        /* fields on the beam particles of this slice: directly (a9), or from
+           the grid nodes (the plasma fields evaluated there, B^(b) of all
+           grids) by linear interpolation in r */
+        if (nr > 0) {
+            for (int32_t b = 0; b < nsp; ++b) {
+                double dr = agR[b] / nr;
+                for (int32_t j = 0; j <= nr; ++j) {
+                    double x = (double)j * dr, psi, dpr, dpz, bpv, bbv;
+                    fields_at(&s, &bs, dens, rho_max, dxi, x, &psi, &dpr, &dpz, &bpv, &bbv);
+                    double *F = agF + ((size_t)b * (nr + 1) + j) * 4;
+                    F[0] = psi;
+                    F[1] = dpr;
+                    F[2] = dpz;
+                    F[3] = bpv + (j > 0 ? ag_field(&ag, x) : 0.0);
+                }
+            }
+        }
         for (int64_t q = 0; q < bs.m; ++q) {
             double psi, dpr, dpz, bpv, bbv;
-            fields_at(&s, &bs, dens, rho_max, dxi, bs.r[q], &psi, &dpr, &dpz, &bpv, &bbv);
             int64_t k = bs.idx[q];
+            if (nr > 0) {
+                int32_t b = p->beam_species ? p->beam_species[k] : 0;
+                double dr = agR[b] / nr, x = bs.r[q];
+                int32_t j = ag_cell(x, dr, nr);
+                double t = (x - (double)j * dr) / dr;
+                const double *F0 = agF + ((size_t)b * (nr + 1) + j) * 4, *F1 = F0 + 4;
+                psi = (1.0 - t) * F0[0] + t * F1[0];
+                dpr = (1.0 - t) * F0[1] + t * F1[1];
+                dpz = (1.0 - t) * F0[2] + t * F1[2];
+                bpv = (1.0 - t) * F0[3] + t * F1[3];
+                bbv = 0.0;
+            } else {
+                fields_at(&s, &bs, dens, rho_max, dxi, bs.r[q], &psi, &dpr, &dpz, &bpv, &bbv);
+            }
             if (out->ez) out->ez[k] = -dpz;
             if (out->wr) out->wr[k] = -dpr;
             if (out->bt) out->bt[k] = bpv + bbv;
@@ -744,9 +869,9 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
                 }
                 memcpy(ord_s, order, (size_t)n * sizeof(int32_t));
                 if (stg < 2)
-                    rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bs, &bsn, 0.5, 0.5, dxi);
+                    rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bs, &bsn, 0.5, 0.5, NULL, dxi);
                 else
-                    rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bsn, NULL, 1.0, 0.0, dxi);
+                    rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bsn, NULL, 1.0, 0.0, NULL, dxi);
                 if (rc)
                     break;
                 if (!ring_fields_ok(&s)) {
@@ -814,6 +939,9 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
         memcpy(out->final_r, rho, (size_t)n * sizeof(double));
     if (out->final_ur)
         memcpy(out->final_ur, ur, (size_t)n * sizeof(double));
+    free(agR);
+    free(agB);
+    free(agF);
     free(st);
     free(rk);
     free(order);

@@ -39,6 +39,13 @@ typedef struct {
     /* ring integrator of orc_run: ORC_AB2 (Sec. III) or ORC_RK4 (the
        Runge-Kutta alternative Sec. II names) */
     int32_t integrator;
+    /* beam-plasma coupling through adaptive beam grids (Sec. IV; orc_run
+       with ORC_AB2): grid_nr > 0 radial cells per beam species, whose
+       extent covers all its particles; 0 = gridless (a9).  beam_species
+       [n_beam] gives each particle's species (NULL: all 0), n_species. */
+    int32_t grid_nr;
+    const int32_t *beam_species;
+    int32_t n_species;
 } orc_problem;
 
 typedef struct {

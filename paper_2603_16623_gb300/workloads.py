@@ -59,6 +59,9 @@ class Wake:
     cell_density: Optional[np.ndarray] = None
     # ring integrator: "ab2" (Sec. III) or "rk4"
     integrator: str = "ab2"
+    # beam-plasma coupling: 0 = gridless (fields at each beam particle);
+    # > 0 = adaptive beam grids of this many radial cells per beam (Sec. IV)
+    grid_nr: int = 0
 
     @property
     def n_rings(self) -> int:
