@@ -250,6 +250,11 @@ def run_ours(args):
     if not args.skip_rk4:
         rk4 = rk4_bench(args, wakes, stream)
 
+    # ---- adaptive beam grids against the gridless coupling (FP64)
+    grid = None
+    if not args.skip_grid:
+        grid = grid_bench(args, wakes, stream)
+
     # ---- serving: Poisson arrivals of batched-workload wakes, continuous batching
     serving = None
     if not args.skip_serve:
@@ -310,6 +315,7 @@ def run_ours(args):
             "beam_push": push,
             "mobile_ions": _ions_roofline(ions, peak_tflops, sm_mhz),
             "rk4": _alu_roofline(rk4, peak_tflops, sm_mhz, FLOPS_PER_RING_SLICE_RK4, "march_rk4_kernel<PrecMixed>", 1),
+            "beam_grid": grid,
             "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
             "wall_s": wall,
@@ -380,6 +386,38 @@ def rk4_bench(args, wakes, stream):
     res = _ions_batch(sel, stream, species=1)
     res["integrator"] = "classical RK4 per slice (four field evaluations), electrons over the ion column"
     return res
+
+
+def grid_bench(args, wakes, stream):
+    """The paper's grid coupling (adaptive beam grids of 32 radial cells per
+    beam) against the gridless one, both FP64 on the one-CTA march, on the
+    same batched wakes of <= 8192 rings over a bounded window (their first
+    args.grid_slices slices): batched reset + step, CUDA-event timed."""
+    import dataclasses
+
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    sel = [wk for wk in wakes if wk.n_rings <= 8192][: args.grid_wakes]
+    out = {"wakes": len(sel), "slices": args.grid_slices, "precision": "fp64", "grid_nr": 32}
+    for name, nr in (("gridless", 0), ("grid", 32)):
+        gs = [wm.Wake.from_workload(dataclasses.replace(wk, grid_nr=nr), precision="fp64", stream=stream.cuda_stream)
+              for wk in sel]
+        wm.wake_batch_reset(gs)
+        wm.wake_batch_step(gs, args.grid_slices)  # warm-up
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        wm.wake_batch_reset(gs)
+        wm.wake_batch_step(gs, args.grid_slices)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        rs = sum(wk.n_rings * g.progress()[0] for g, wk in zip(gs, sel))
+        ms = ev[0].elapsed_time(ev[1])
+        out[name] = {"ring_slices": rs, "ms_per_step": ms, "value": rs / (ms / 1e3), "unit": UNIT}
+        for g in gs:
+            g.close()
+    out["grid_over_gridless_time"] = out["grid"]["ms_per_step"] / out["gridless"]["ms_per_step"]
+    return out
 
 
 def _alu_roofline(res, peak_tflops, sm_mhz, flops, kernel, species):
@@ -564,6 +602,9 @@ def main():
     ap.add_argument("--skip-ions", action="store_true")
     ap.add_argument("--ion-wakes", type=int, default=152)
     ap.add_argument("--skip-rk4", action="store_true")
+    ap.add_argument("--skip-grid", action="store_true")
+    ap.add_argument("--grid-wakes", type=int, default=64)
+    ap.add_argument("--grid-slices", type=int, default=300)
     ap.add_argument("--rk4-wakes", type=int, default=152)
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=500.0)

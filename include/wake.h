@@ -133,6 +133,15 @@ typedef struct {
                                  at most 512, and no CTA may be left empty.
                                  Both must be 0 for WAKE_FP64.                  */
     int32_t integrator;       /* WAKE_AB2 (0) or WAKE_RK4                        */
+    int32_t grid_nr;          /* 0: gridless beam coupling (fields at each beam
+                                 particle); 1..1024: adaptive beam grids
+                                 (Sec. IV): per beam species grid_nr radial
+                                 cells out to (1 + 1/grid_nr) x its largest
+                                 radius, one node line per slice; B^(b) at
+                                 the rings from the grids (B_N r_N / rho
+                                 beyond), beam-particle fields interpolated
+                                 from the nodes.  WAKE_FP64, WAKE_AB2, no
+                                 mobile ions, at most 8 beam species.         */
 } wake_config;
 
 typedef struct wake_handle wake_handle;

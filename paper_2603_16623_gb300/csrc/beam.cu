@@ -287,4 +287,23 @@ template cudaError_t launch_scatter_out<double>(const int32_t*, const int32_t*, 
 template cudaError_t launch_scatter_out<float>(const int32_t*, const int32_t*, int64_t, const float*, float*,
                                                cudaStream_t);
 
+// radii are >= 0, so their bit patterns order as the values do
+__global__ void species_rmax_kernel(const double* __restrict__ r, SpeciesRanges sp, double* rmax) {
+    const int64_t nb = sp.begin[sp.n];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        while (s + 1 < sp.n && k >= sp.begin[s + 1]) ++s;
+        atomicMax(reinterpret_cast<unsigned long long*>(rmax + s), (unsigned long long)__double_as_longlong(r[k]));
+    }
+}
+
+cudaError_t launch_species_rmax(const double* r, SpeciesRanges sp, double* rmax, cudaStream_t st) {
+    const int64_t nb = sp.begin[sp.n];
+    if (nb <= 0) return cudaSuccess;
+    int64_t g = (nb + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    species_rmax_kernel<<<(int)g, 256, 0, st>>>(r, sp, rmax);
+    return cudaGetLastError();
+}
+
 }  // namespace gbwake

@@ -25,4 +25,11 @@ cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double*
 template <class R>
 cudaError_t launch_scatter_out(const int32_t* idx, const int32_t* nbin, int64_t nb_max, const R* src, R* dst,
                                cudaStream_t st);
+// largest radius of each beam species (caller order, species s = particles
+// [begin[s], begin[s+1])) into rmax[s], which the caller has zeroed
+struct SpeciesRanges {
+    int32_t n;
+    int64_t begin[9];
+};
+cudaError_t launch_species_rmax(const double* r, SpeciesRanges sp, double* rmax, cudaStream_t st);
 }  // namespace gbwake

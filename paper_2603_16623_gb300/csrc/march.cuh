@@ -27,6 +27,7 @@ enum { CTL_NEXT = 0, CTL_STATUS = 1, CTL_FAIL = 2, CTL_BUF = 3, CTL_PREV = 4, CT
 enum { MODE_MARCH = 0, MODE_QUERY = 1 };
 
 constexpr int kScanBytes = 33 * 64;  // block-scan scratch (33 values of <= 64 B)
+constexpr int kMaxGridSpecies = 8;   // beam species with adaptive grids
 
 template <class P>
 struct WakeDev {
@@ -76,6 +77,18 @@ struct WakeDev {
     // last stage's derivatives, the stage's radius order
     R *rk_r, *rk_rlo, *rk_u, *rk_sg, *rk_kr, *rk_ku;
     int32_t* rk_perm;
+    // adaptive beam grids (Sec. IV; FP64): grid_nr > 0 radial cells per
+    // beam species out to (1 + 1/grid_nr) x the species' largest radius
+    // (ag_rmax, from the preparation); species of caller particle k: the
+    // last s with sp_begin[s] <= k; bidx: binned -> caller index; qw: the
+    // caller's charge x weight; agB: B^(b) at the nodes [species][nr + 1];
+    // agF: the node fields [species][nr + 1][psi, d_rho psi, d_zeta psi, B]
+    int32_t grid_nr, n_species;
+    int64_t sp_begin[kMaxGridSpecies + 1];
+    const int32_t* bidx;
+    const double* qw;
+    const double* ag_rmax;
+    R *agB, *agF;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -94,6 +107,47 @@ template <class A, class R>
 __device__ __forceinline__ A ion_psi(R x, R rmax, R quarter_n, A Imax, A c0) {
     if (x <= rmax) return acc_sub(c0, acc_mul_r(acc_sq(x), quarter_n));
     return acc_mul_r(Imax, -real_log(x));
+}
+
+// Node index j with j dr <= x < (j + 1) dr for x >= 0, clamped to [0, nr - 1]
+// (the comparison as written, so that the two sides agree at the nodes).
+__device__ __forceinline__ int ag_cell(double x, double dr, int nr) {
+    int j = (int)floor(x / dr);
+    if (j > nr - 1) j = nr - 1;
+    if (j < 0) j = 0;
+    while (j > 0 && (double)j * dr > x) --j;
+    while (j < nr - 1 && (double)(j + 1) * dr <= x) ++j;
+    return j;
+}
+template <class P>
+__device__ __forceinline__ int ag_species(const WakeDev<P>& W, int64_t k) {
+    int s = 0;
+    while (s + 1 < W.n_species && k >= W.sp_begin[s + 1]) ++s;
+    return s;
+}
+// the grid extent of species b: (1 + 1/nr) x its largest radius (at least
+// 1e-12, for a beam on the axis)
+template <class P>
+__device__ __forceinline__ double ag_extent(const WakeDev<P>& W, int b) {
+    return fmax(W.ag_rmax[b], 1e-12) * (1.0 + 1.0 / W.grid_nr);
+}
+// B^(b) of species b at rho from its grid: linear between nodes inside,
+// B_N r_N / rho beyond (Sec. IV)
+template <class P>
+__device__ __forceinline__ double ag_species_field(const WakeDev<P>& W, int b, double rho) {
+    const int nr = W.grid_nr;
+    const double R = ag_extent(W, b), dr = R / nr;
+    const typename P::R* B = W.agB + (size_t)b * (nr + 1);
+    if (rho >= R) return (double)B[nr] * R / rho;
+    const int j = ag_cell(rho, dr, nr);
+    const double t = (rho - (double)j * dr) / dr;
+    return (1.0 - t) * (double)B[j] + t * (double)B[j + 1];
+}
+template <class P>
+__device__ __forceinline__ double ag_field(const WakeDev<P>& W, double rho) {
+    double v = 0.0;
+    for (int b = 0; b < W.n_species; ++b) v += ag_species_field(W, b, rho);
+    return v;
 }
 
 __device__ __forceinline__ double acc_add_prod(double a, double x, double y) { return a + x * y; }
@@ -203,6 +257,33 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         __syncthreads();
         const R* beamR = staged ? sB : (W.br + b0);
 
+        // ---------------- adaptive grids: B^(b) at the nodes of this slice
+        const int nr = W.grid_nr;
+        if (nr > 0) {
+            const int nn = W.n_species * (nr + 1);
+            for (int i = tid; i < nn; i += T) W.agB[i] = 0;
+            __syncthreads();
+            for (int q = tid; q < m; q += T) {  // each particle's charge reaches the nodes above it
+                const int64_t k = W.bidx[b0 + q];
+                const int b = ag_species(W, k);
+                const double dr = ag_extent(W, b) / nr;
+                const int j = ag_cell((double)W.br[b0 + q], dr, nr) + 1;
+                atomicAdd(W.agB + (size_t)b * (nr + 1) + j, (R)W.qw[k]);
+            }
+            __syncthreads();
+            if (tid < W.n_species) {
+                R* B = W.agB + (size_t)tid * (nr + 1);
+                const double dr = ag_extent(W, tid) / nr;
+                double acc = 0.0;
+                B[0] = 0;
+                for (int j = 1; j <= nr; ++j) {
+                    acc += (double)B[j];
+                    B[j] = (R)(acc / (6.283185307179586476925286766559 * W.dxi * ((double)j * dr)));
+                }
+            }
+            __syncthreads();
+        }
+
         // ---------------- a3 + a4: beam field at rings, local sums
         Pair<A> loc = {zeroA, zeroA};
         for (int p = p0; p < p1; ++p) {
@@ -210,7 +291,9 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
             int id = rid[p];
             R w = W.w[id];
             R bbv = 0;
-            if (m > 0 && r > (R)0) {
+            if (nr > 0) {
+                bbv = (R)ag_field(W, (double)r);
+            } else if (m > 0 && r > (R)0) {
                 int lb = lower_bound_dev(beamR, m, r);
                 R Q = lb < m ? W.bE[b0 + lb] : qtot;
                 bbv = Q * inv_2pi_dxi / r;
@@ -395,8 +478,54 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         }
         bad = __syncthreads_or(bad);
 
+        // ---------------- adaptive grids: the plasma fields at the nodes
+        if (nr > 0 && mode == MODE_MARCH) {
+            const int nn = W.n_species * (nr + 1);
+            for (int i = tid; i < nn; i += T) {
+                const int b = i / (nr + 1), j = i - b * (nr + 1);
+                const double dr = ag_extent(W, b) / nr;
+                const R x = (R)((double)j * dr);
+                R psi, dprv, dpz, bpv;
+                if (x > (R)0) {
+                    int k = lower_bound_dev(sR, n, x);
+                    A Sk = W.regS[k];
+                    psi = acc_to_r(acc_add(acc_add(W.regL[k], acc_mul_r(Sk, real_log(x))),
+                                           ion_psi(x, rmax, quarter_n, Imax, c0)));
+                    dprv = acc_to_r(acc_sub(Sk, ion_enclosed(x, rmax, half_n, Imax))) / x;
+                    dpz = -W.regT[k];
+                    bpv = W.ak[k] * x + W.bk[k] / x + (R)ag_field(W, (double)x);
+                } else {
+                    psi = acc_to_r(acc_add(W.regL[0], ion_psi((R)0, rmax, quarter_n, Imax, c0)));
+                    dprv = 0;
+                    dpz = -W.regT[0];
+                    bpv = 0;
+                }
+                R* F = W.agF + (size_t)i * 4;
+                F[0] = psi;
+                F[1] = dprv;
+                F[2] = dpz;
+                F[3] = bpv;
+            }
+            __syncthreads();
+            for (int q = tid; q < m; q += T) {
+                const int64_t kc = W.bidx[b0 + q];
+                const int b = ag_species(W, kc);
+                const double dr = ag_extent(W, b) / nr;
+                const double x = (double)W.br[b0 + q];
+                const int j = ag_cell(x, dr, nr);
+                const R t = (R)((x - (double)j * dr) / dr);
+                const R* F0 = W.agF + ((size_t)b * (nr + 1) + j) * 4;
+                const R* F1 = F0 + 4;
+                const int64_t o = b0 + q;
+                W.out_ez[o] = -(((R)1 - t) * F0[2] + t * F1[2]);
+                W.out_wr[o] = -(((R)1 - t) * F0[1] + t * F1[1]);
+                W.out_bt[o] = ((R)1 - t) * F0[3] + t * F1[3];
+                W.out_psi[o] = ((R)1 - t) * F0[0] + t * F1[0];
+            }
+        }
+
         // ---------------- a9: fields on beam particles (or query radii)
-        {
+        if (!(nr > 0 && mode == MODE_MARCH)) {
             const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
             for (int64_t q = tid; q < nq; q += T) {
                 R x;

@@ -65,6 +65,8 @@ struct wake_handle {
     int32_t n = 0, n_steps = 0, n_pad = 0, threads = kDefaultThreads, flags = 0;
     int32_t n_ion = 0;                      // > 0: mobile ions, rings per species (n = 2 n_ion)
     int32_t rk4 = 0;                        // the RK4 integrator (march_rk4.cuh)
+    int32_t grid_nr = 0;                    // > 0: adaptive beam grids (march.cuh)
+    double* d_ag_rmax = nullptr;            // largest radius per beam species (grids)
     double ion_qm = 0;                      // their Z / M
     double dxi = 0, density = 1, rho_max = 0;
     cudaStream_t st = nullptr;
@@ -245,6 +247,13 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
         WK_CUDA(cudaMemsetAsync(h->d_cnt, 0, (size_t)ns * sizeof(int32_t), st));
         WK_CUDA(cudaMemsetAsync(h->d_fill, 0, (size_t)ns * sizeof(int32_t), st));
         WK_CUDA(launch_bin_count(h->d_xi, h->nb_total, h->dxi, ns, h->d_slot, h->d_cnt, st));
+        if (h->grid_nr > 0) {  // the grids' extents from the beam as it is now
+            SpeciesRanges sp = {};
+            sp.n = (int32_t)h->beam_n.size();
+            for (int32_t b = 0; b < sp.n; ++b) sp.begin[b + 1] = sp.begin[b] + h->beam_n[b];
+            WK_CUDA(cudaMemsetAsync(h->d_ag_rmax, 0, (size_t)sp.n * sizeof(double), st));
+            WK_CUDA(launch_species_rmax(h->d_r, sp, h->d_ag_rmax, st));
+        }
         WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, st));
     }
     if (!split) return prepare_sort<P>(h, st);
@@ -393,6 +402,23 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         R* o;
         WK_TRY(dalloc_t(h, (size_t)nb, &o));
         h->d_out[k] = o;
+    }
+    if (h->grid_nr > 0) {
+        D.grid_nr = h->grid_nr;
+        D.n_species = (int32_t)h->beam_n.size();
+        int64_t off = 0;
+        for (int32_t b = 0; b < D.n_species; ++b) {
+            D.sp_begin[b] = off;
+            off += h->beam_n[b];
+        }
+        D.sp_begin[D.n_species] = off;
+        if (D.n_species == 0) D.n_species = 1;  // no beam: one empty grid
+        D.bidx = h->d_bidx;
+        D.qw = h->d_qw;
+        WK_TRY(dalloc_t(h, (size_t)D.n_species, &h->d_ag_rmax));
+        D.ag_rmax = h->d_ag_rmax;
+        WK_TRY(dalloc_t(h, (size_t)D.n_species * (h->grid_nr + 1), &D.agB));
+        WK_TRY(dalloc_t(h, (size_t)D.n_species * (h->grid_nr + 1) * 4, &D.agF));
     }
     D.out_ez = (R*)h->d_out[0];
     D.out_wr = (R*)h->d_out[1];
@@ -719,7 +745,8 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
         int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
         // the one-CTA kernels (plain and two-species) by their block size
-        if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * hs[i]->threads);
+        if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * (hs[i]->grid_nr > 0) +
+                                          8 * hs[i]->threads);
         auto it = std::find(keys.begin(), keys.end(), key);
         if (it == keys.end()) {
             keys.push_back(key);
@@ -1020,6 +1047,10 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     if (rk4 && (ions || cfg->rings_per_thread || cfg->cluster_ctas))
         return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the one-CTA march (no mobile ions, "
                                  "rings_per_thread and cluster_ctas 0)");
+    if (cfg->grid_nr < 0 || cfg->grid_nr > 1024) return fail(WAKE_EINVAL, "wake_init: grid_nr must be in [0, 1024]");
+    if (cfg->grid_nr > 0 && (cfg->precision != WAKE_FP64 || rk4 || ions || n_beams > kMaxGridSpecies))
+        return fail(WAKE_EINVAL, "wake_init: beam grids run WAKE_FP64, WAKE_AB2, without mobile ions, with at most "
+                                 "%d beam species", kMaxGridSpecies);
     // the two-species and RK4 marches: one CTA of 512 threads per wake
     if ((ions || rk4) && !cfg->block_threads) threads = 512;
     if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");
@@ -1053,6 +1084,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->n_ion = ions ? n : 0;
     h->ion_qm = ions && std::isfinite(plasma->ion_mass) ? plasma->ion_charge / plasma->ion_mass : 0.0;
     h->rk4 = rk4 ? 1 : 0;
+    h->grid_nr = cfg->grid_nr;
     h->n_steps = cfg->n_steps;
     h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;
@@ -1063,7 +1095,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->st = static_cast<cudaStream_t>(cuda_stream);
     FastShape shape;
     {
-        wake_status fs = (ions || rk4) ? WAKE_OK
+        wake_status fs = (ions || rk4 || cfg->grid_nr > 0) ? WAKE_OK
                                        : fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
         if (fs != WAKE_OK) {
             delete h;

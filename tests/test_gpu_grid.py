@@ -1,0 +1,98 @@
+"""GPU parity of the adaptive beam grids (Sec. IV; the grid path of
+march.cuh) against the oracle's grid march (orc_run with grid_nr > 0):
+per beam species grid_nr radial cells covering its particles, one node line
+per slice, B^(b) at the rings from the grids, beam-particle fields
+interpolated from the nodes.  FP64, 1e-10 norm-wise.  The node charges are
+summed with atomics on the GPU (order-dependent rounding), so batched and
+alone runs agree to rounding, not bitwise."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_16623_gb300 import workloads as W
+from test_gpu_parity import FP64_TOL, nerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2603_16623_gb300 import wake
+    wake.load()
+    yield
+
+
+def grid_wake(grid_nr=32, n=300, steps=400, seed=91, two_beams=False):
+    drv = W.gaussian_beam(30_000, 0.8, 0.35, 0.6, 1.8, seed=seed)
+    beams = [drv]
+    if two_beams:
+        beams.append(W.gaussian_beam(8_000, 0.3, 0.12, 0.2, 3.2, seed=seed + 1))
+    return W.Wake(f"grid{seed}", W.edges_uniform(n, 5.0), beams, 0.01, steps, grid_nr=grid_nr)
+
+
+def gpu_run(wk, threads=0):
+    from paper_2603_16623_gb300 import wake as wm
+    g = wm.Wake.from_workload(wk, precision="fp64", block_threads=threads, flags=wm.WAKE_DUMP_RING_FIELDS)
+    st, _, _, _ = g.run()
+    out = {"status": st, "beam": g.beam_fields(), "rings": g.ring_dumps(), "final": g.ring_state()}
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("grid_nr,threads", [(32, 256), (7, 64)])
+def test_fp64_grid_wake_matches_oracle(grid_nr, threads):
+    wk = grid_wake(grid_nr)
+    ref = oracle.run_wake(wk, ring_dumps=("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"))
+    assert ref.status == 0
+    got = gpu_run(wk, threads)
+    assert got["status"] == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_fp64_driver_and_witness_grids_match_oracle():
+    """Two species with grids of different extents (the witness narrower)."""
+    wk = grid_wake(24, steps=420, seed=93, two_beams=True)
+    ref = oracle.run_wake(wk, ring_dumps=("r", "bb"))
+    assert ref.status == 0
+    got = gpu_run(wk, 128)
+    assert got["status"] == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < FP64_TOL
+    assert nerr(got["rings"]["bb"], ref.rings["bb"]) < FP64_TOL
+    for k in ("ez", "wr", "bt"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_grid_wakes_batched_match_alone():
+    from paper_2603_16623_gb300 import wake as wm
+    wakes = [grid_wake(16, n=200, steps=250, seed=95), grid_wake(40, n=260, steps=300, seed=96, two_beams=True)]
+    alone = []
+    for wk in wakes:
+        g = wm.Wake.from_workload(wk, precision="fp64")
+        g.run()
+        alone.append((g.ring_state(), g.beam_fields(("ez", "wr"))))
+        g.close()
+    gs = [wm.Wake.from_workload(wk, precision="fp64") for wk in wakes]
+    wm.wake_batch_run(gs)
+    for g, (st, bf) in zip(gs, alone):
+        r, _ = g.ring_state()
+        assert nerr(r, st[0]) < 1e-12
+        f = g.beam_fields(("ez", "wr"))
+        assert nerr(f["ez"], bf["ez"]) < 1e-12 and nerr(f["wr"], bf["wr"]) < 1e-12
+        g.close()
+
+
+def test_grid_rejects_bad_use():
+    from paper_2603_16623_gb300 import wake as wm
+    wk = grid_wake(8, n=50, steps=20)
+    with pytest.raises(wm.WakeError):
+        wm.Wake.from_workload(wk, precision="mixed")
+    with pytest.raises(wm.WakeError):
+        wm.Wake.from_workload(wk, precision="fp64", grid_nr=2000)
+    with pytest.raises(wm.WakeError):
+        wm.Wake.from_workload(wk, precision="fp64", integrator="rk4")
