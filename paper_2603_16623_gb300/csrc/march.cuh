@@ -153,6 +153,120 @@ __device__ __forceinline__ double ag_field(const WakeDev<P>& W, double rho) {
 __device__ __forceinline__ double acc_add_prod(double a, double x, double y) { return a + x * y; }
 __device__ __forceinline__ ff acc_add_prod(ff a, float x, float y) { return ff_add(a, ff_two_prod(x, y)); }
 
+// a8: the region coefficients a_k, b_k of B_theta^(p) = a_k rho + b_k / rho
+// (Eq. ai_bi with b_0 = 0, a_n = 0) for the rings at sorted positions
+// [0, n) (radii sR, coefficients W.cA, W.cB, W.cC; this thread's positions
+// [p0, p1)), in W.ak, W.bk [0..n].  W.cB, W.cC are overwritten with the ring
+// sources gamma_p, delta_p.  Ends without a barrier after the last writes.
+template <class P>
+__device__ void bp_region_solve(const WakeDev<P>& W, const typename P::R* sR, int n, int p0, int p1,
+                                unsigned char* sscan) {
+    using R = typename P::R;
+    using A = typename P::A;
+    const int tid = threadIdx.x;
+    const A zeroA = acc_zero(A());
+    // regular solution R_k (R_0 = (1,0)) forward, decaying solution D_k
+    // (D_n = (0,1)) backward, then x_k = -G_k R_k + H_k D_k with the
+    // ring sources c_p = gamma_p R_{p+1} + delta_p D_{p+1},
+    // G_k = sum_{p>=k} gamma_p, H_k = sum_{p<k} delta_p.
+    const Mat2<R> I2 = {1, 0, 0, 1};
+    Mat2<R> Mf = I2, Mb = I2;
+    for (int p = p0; p < p1; ++p) {
+        R r = sR[p], hA = (R)0.5 * W.cA[p];
+        Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
+        Mf = OpMatLeft()(Mf, M);
+    }
+    for (int p = p1 - 1; p >= p0; --p) {
+        R r = sR[p], hA = (R)0.5 * W.cA[p];
+        Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};  // inverse (det 1)
+        Mb = OpMatLeft()(Mb, Mi);
+    }
+    Mat2<R> tf, tb;
+    Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
+    Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
+    if (tid == 0) {
+        W.Ra[0] = 1;
+        W.Rb[0] = 0;
+        W.Da[n] = 0;
+        W.Db[n] = 1;
+    }
+    for (int p = p0; p < p1; ++p) {
+        R r = sR[p], hA = (R)0.5 * W.cA[p];
+        Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
+        Yf = OpMatLeft()(Yf, M);
+        W.Ra[p + 1] = Yf.m00;
+        W.Rb[p + 1] = Yf.m10;
+    }
+    A gl = zeroA, dl = zeroA;
+    for (int p = p1 - 1; p >= p0; --p) {
+        R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
+        R hA = (R)0.5 * Ac;
+        R d0 = Yb.m01, d1 = Yb.m11;        // D_{p+1}
+        R q0 = W.Ra[p + 1], q1 = W.Rb[p + 1];  // R_{p+1}
+        R s0 = (R)0.25 * ((R)2 * Bc + Ac * Cc);
+        R s1 = (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r);
+        R wr = q0 * d1 - q1 * d0;
+        R gp = (s0 * d1 - s1 * d0) / wr;
+        R dp = (q0 * s1 - q1 * s0) / wr;
+        W.cB[p] = gp;  // reuse: gamma_p
+        W.cC[p] = dp;  // reuse: delta_p
+        gl = acc_add_r(gl, gp);
+        dl = acc_add_r(dl, dp);
+        Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
+        Yb = OpMatLeft()(Yb, Mi);
+        W.Da[p] = Yb.m01;
+        W.Db[p] = Yb.m11;
+    }
+    // G_k = sum_{p >= k} gamma_p as a true suffix sum (a total minus a
+    // prefix would cancel where G_k is small and R_k ~ e^rho is large)
+    A g_tot, d_tot;
+    Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
+    // the scan's barriers order the R/D writes above before these reads
+    A Gsuf = gd.y;  // sum of gamma over rings >= p1
+    for (int p = p1 - 1; p >= p0; --p) {
+        Gsuf = acc_add_r(Gsuf, W.cB[p]);  // sum over rings >= p
+        R G = acc_to_r(Gsuf);
+        W.ak[p] = -G * W.Ra[p];
+        W.bk[p] = -G * W.Rb[p];
+    }
+    A Hex = gd.x;   // sum of delta over rings < p
+    for (int p = p0; p < p1; ++p) {
+        R H = acc_to_r(Hex);
+        W.ak[p] += H * W.Da[p];
+        W.bk[p] += H * W.Db[p];
+        Hex = acc_add_r(Hex, W.cC[p]);
+    }
+    if (tid == 0) {
+        R H = acc_to_r(d_tot);
+        W.ak[n] = H * W.Da[n];
+        W.bk[n] = H * W.Db[n];
+    }
+}
+
+// Bitonic sort of keys[0..n_pad) ascending, ties by vals ascending (the
+// caller pads with +inf keys); every thread of the block takes part.
+template <class R>
+__device__ void block_bitonic_sort(R* keys, int32_t* vals, int n_pad) {
+    const int T = blockDim.x, tid = threadIdx.x;
+    for (int k = 2; k <= n_pad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < n_pad; i += T) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    R ki = keys[i], kj = keys[ixj];
+                    int vi = vals[i], vj = vals[ixj];
+                    bool gt = (ki > kj) || (ki == kj && vi > vj);
+                    if (gt == ((i & k) == 0)) {
+                        keys[i] = kj; keys[ixj] = ki;
+                        vals[i] = vj; vals[ixj] = vi;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <class P>
 __global__ void __launch_bounds__(512)
 march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ order,
@@ -206,23 +320,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 vals[i] = i;
             }
             __syncthreads();
-            for (int k = 2; k <= W.n_pad; k <<= 1) {
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < W.n_pad; i += T) {
-                        int ixj = i ^ j;
-                        if (ixj > i) {
-                            R ki = keys[i], kj = keys[ixj];
-                            int vi = vals[i], vj = vals[ixj];
-                            bool gt = (ki > kj) || (ki == kj && vi > vj);
-                            if (gt == ((i & k) == 0)) {
-                                keys[i] = kj; keys[ixj] = ki;
-                                vals[i] = vj; vals[ixj] = vi;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
+            block_bitonic_sort(keys, vals, W.n_pad);
             const int nb = buf ^ 1;
             for (int p = tid; p < n; p += T) {
                 int src = vals[p];
@@ -375,84 +473,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         }
 
         // ---------------- a8: B_theta^(p) region coefficients a_k, b_k
-        {
-            // regular solution R_k (R_0 = (1,0)) forward, decaying solution D_k
-            // (D_n = (0,1)) backward, then x_k = -G_k R_k + H_k D_k with the
-            // ring sources c_p = gamma_p R_{p+1} + delta_p D_{p+1},
-            // G_k = sum_{p>=k} gamma_p, H_k = sum_{p<k} delta_p.
-            const Mat2<R> I2 = {1, 0, 0, 1};
-            Mat2<R> Mf = I2, Mb = I2;
-            for (int p = p0; p < p1; ++p) {
-                R r = sR[p], hA = (R)0.5 * W.cA[p];
-                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
-                Mf = OpMatLeft()(Mf, M);
-            }
-            for (int p = p1 - 1; p >= p0; --p) {
-                R r = sR[p], hA = (R)0.5 * W.cA[p];
-                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};  // inverse (det 1)
-                Mb = OpMatLeft()(Mb, Mi);
-            }
-            Mat2<R> tf, tb;
-            Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
-            Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
-            if (tid == 0) {
-                W.Ra[0] = 1;
-                W.Rb[0] = 0;
-                W.Da[n] = 0;
-                W.Db[n] = 1;
-            }
-            for (int p = p0; p < p1; ++p) {
-                R r = sR[p], hA = (R)0.5 * W.cA[p];
-                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
-                Yf = OpMatLeft()(Yf, M);
-                W.Ra[p + 1] = Yf.m00;
-                W.Rb[p + 1] = Yf.m10;
-            }
-            A gl = zeroA, dl = zeroA;
-            for (int p = p1 - 1; p >= p0; --p) {
-                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
-                R hA = (R)0.5 * Ac;
-                R d0 = Yb.m01, d1 = Yb.m11;        // D_{p+1}
-                R q0 = W.Ra[p + 1], q1 = W.Rb[p + 1];  // R_{p+1}
-                R s0 = (R)0.25 * ((R)2 * Bc + Ac * Cc);
-                R s1 = (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r);
-                R wr = q0 * d1 - q1 * d0;
-                R gp = (s0 * d1 - s1 * d0) / wr;
-                R dp = (q0 * s1 - q1 * s0) / wr;
-                W.cB[p] = gp;  // reuse: gamma_p
-                W.cC[p] = dp;  // reuse: delta_p
-                gl = acc_add_r(gl, gp);
-                dl = acc_add_r(dl, dp);
-                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
-                Yb = OpMatLeft()(Yb, Mi);
-                W.Da[p] = Yb.m01;
-                W.Db[p] = Yb.m11;
-            }
-            // G_k = sum_{p >= k} gamma_p as a true suffix sum (a total minus a
-            // prefix would cancel where G_k is small and R_k ~ e^rho is large)
-            A g_tot, d_tot;
-            Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
-            // the scan's barriers order the R/D writes above before these reads
-            A Gsuf = gd.y;  // sum of gamma over rings >= p1
-            for (int p = p1 - 1; p >= p0; --p) {
-                Gsuf = acc_add_r(Gsuf, W.cB[p]);  // sum over rings >= p
-                R G = acc_to_r(Gsuf);
-                W.ak[p] = -G * W.Ra[p];
-                W.bk[p] = -G * W.Rb[p];
-            }
-            A Hex = gd.x;   // sum of delta over rings < p
-            for (int p = p0; p < p1; ++p) {
-                R H = acc_to_r(Hex);
-                W.ak[p] += H * W.Da[p];
-                W.bk[p] += H * W.Db[p];
-                Hex = acc_add_r(Hex, W.cC[p]);
-            }
-            if (tid == 0) {
-                R H = acc_to_r(d_tot);
-                W.ak[n] = H * W.Da[n];
-                W.bk[n] = H * W.Db[n];
-            }
-        }
+        bp_region_solve(W, sR, n, p0, p1, sscan);
         __syncthreads();
 
         // ---------------- B^(p) at the rings, guard, dumps

@@ -192,23 +192,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                         vals[i] = i;
                     }
                     __syncthreads();
-                    for (int k = 2; k <= W.n_pad; k <<= 1) {
-                        for (int j = k >> 1; j > 0; j >>= 1) {
-                            for (int i = tid; i < W.n_pad; i += T) {
-                                int ixj = i ^ j;
-                                if (ixj > i) {
-                                    R ki = keys[i], kj = keys[ixj];
-                                    int vi = vals[i], vj = vals[ixj];
-                                    bool gt = (ki > kj) || (ki == kj && vi > vj);
-                                    if (gt == ((i & k) == 0)) {
-                                        keys[i] = kj; keys[ixj] = ki;
-                                        vals[i] = vj; vals[ixj] = vi;
-                                    }
-                                }
-                            }
-                            __syncthreads();
-                        }
-                    }
+                    block_bitonic_sort(keys, vals, W.n_pad);
                     for (int i = tid; i < N; i += T) {
                         const int src = base + vals[i], dst = base + i;
                         W.rho[nb][dst] = W.rho[buf][src];
@@ -378,77 +362,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         }
 
         // ---------------- a8: B_theta^(p) of the electrons (regions 0..N)
-        {
-            const Mat2<R> I2 = {1, 0, 0, 1};
-            Mat2<R> Mf = I2, Mb = I2;
-            for (int p = q0; p < q1; ++p) {
-                R r = sR[p], hA = (R)0.5 * W.cA[p];
-                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
-                Mf = OpMatLeft()(Mf, M);
-            }
-            for (int p = q1 - 1; p >= q0; --p) {
-                R r = sR[p], hA = (R)0.5 * W.cA[p];
-                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
-                Mb = OpMatLeft()(Mb, Mi);
-            }
-            Mat2<R> tf, tb;
-            Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
-            Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
-            if (tid == 0) {
-                W.Ra[0] = 1;
-                W.Rb[0] = 0;
-                W.Da[N] = 0;
-                W.Db[N] = 1;
-            }
-            for (int p = q0; p < q1; ++p) {
-                R r = sR[p], hA = (R)0.5 * W.cA[p];
-                Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
-                Yf = OpMatLeft()(Yf, M);
-                W.Ra[p + 1] = Yf.m00;
-                W.Rb[p + 1] = Yf.m10;
-            }
-            A gl = zeroA, dl = zeroA;
-            for (int p = q1 - 1; p >= q0; --p) {
-                R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
-                R hA = (R)0.5 * Ac;
-                R d0 = Yb.m01, d1 = Yb.m11;
-                R g0 = W.Ra[p + 1], g1 = W.Rb[p + 1];
-                R s0 = (R)0.25 * ((R)2 * Bc + Ac * Cc);
-                R s1 = (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r);
-                R wr = g0 * d1 - g1 * d0;
-                R gp = (s0 * d1 - s1 * d0) / wr;
-                R dp = (g0 * s1 - g1 * s0) / wr;
-                W.cB[p] = gp;
-                W.cC[p] = dp;
-                gl = acc_add_r(gl, gp);
-                dl = acc_add_r(dl, dp);
-                Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
-                Yb = OpMatLeft()(Yb, Mi);
-                W.Da[p] = Yb.m01;
-                W.Db[p] = Yb.m11;
-            }
-            A g_tot, d_tot;
-            Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
-            A Gsuf = gd.y;
-            for (int p = q1 - 1; p >= q0; --p) {
-                Gsuf = acc_add_r(Gsuf, W.cB[p]);
-                R G = acc_to_r(Gsuf);
-                W.ak[p] = -G * W.Ra[p];
-                W.bk[p] = -G * W.Rb[p];
-            }
-            A Hex = gd.x;
-            for (int p = q0; p < q1; ++p) {
-                R H = acc_to_r(Hex);
-                W.ak[p] += H * W.Da[p];
-                W.bk[p] += H * W.Db[p];
-                Hex = acc_add_r(Hex, W.cC[p]);
-            }
-            if (tid == 0) {
-                R H = acc_to_r(d_tot);
-                W.ak[N] = H * W.Da[N];
-                W.bk[N] = H * W.Db[N];
-            }
-        }
+        bp_region_solve(W, sR, N, q0, q1, sscan);
         __syncthreads();
         // B^(p) at the electron rings, then interpolated at the ion rings
         for (int p = q0; p < q1; ++p) {

@@ -180,77 +180,7 @@ __device__ bool rk_stage(const WakeDev<P>& W, unsigned char* sscan, const typena
     }
 
     // a8: B_theta^(p) (the two-sided solve of march.cuh)
-    {
-        const Mat2<R> I2 = {1, 0, 0, 1};
-        Mat2<R> Mf = I2, Mb = I2;
-        for (int p = p0; p < p1; ++p) {
-            R r = sR[p], hA = (R)0.5 * W.cA[p];
-            Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
-            Mf = OpMatLeft()(Mf, M);
-        }
-        for (int p = p1 - 1; p >= p0; --p) {
-            R r = sR[p], hA = (R)0.5 * W.cA[p];
-            Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
-            Mb = OpMatLeft()(Mb, Mi);
-        }
-        Mat2<R> tf, tb;
-        Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
-        Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
-        if (tid == 0) {
-            W.Ra[0] = 1;
-            W.Rb[0] = 0;
-            W.Da[n] = 0;
-            W.Db[n] = 1;
-        }
-        for (int p = p0; p < p1; ++p) {
-            R r = sR[p], hA = (R)0.5 * W.cA[p];
-            Mat2<R> M = {(R)1 + hA * r, hA / r, -hA * r * r * r, (R)1 - hA * r};
-            Yf = OpMatLeft()(Yf, M);
-            W.Ra[p + 1] = Yf.m00;
-            W.Rb[p + 1] = Yf.m10;
-        }
-        A gl = zeroA, dl = zeroA;
-        for (int p = p1 - 1; p >= p0; --p) {
-            R r = sR[p], Ac = W.cA[p], Bc = W.cB[p], Cc = W.cC[p];
-            R hA = (R)0.5 * Ac;
-            R d0 = Yb.m01, d1 = Yb.m11;
-            R g0 = W.Ra[p + 1], g1 = W.Rb[p + 1];
-            R s0 = (R)0.25 * ((R)2 * Bc + Ac * Cc);
-            R s1 = (R)0.25 * r * ((R)4 * Cc - (R)2 * Bc * r - Ac * Cc * r);
-            R wr = g0 * d1 - g1 * d0;
-            R gp = (s0 * d1 - s1 * d0) / wr;
-            R dp = (g0 * s1 - g1 * s0) / wr;
-            W.cB[p] = gp;
-            W.cC[p] = dp;
-            gl = acc_add_r(gl, gp);
-            dl = acc_add_r(dl, dp);
-            Mat2<R> Mi = {(R)1 - hA * r, -hA / r, hA * r * r * r, (R)1 + hA * r};
-            Yb = OpMatLeft()(Yb, Mi);
-            W.Da[p] = Yb.m01;
-            W.Db[p] = Yb.m11;
-        }
-        A g_tot, d_tot;
-        Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
-        A Gsuf = gd.y;
-        for (int p = p1 - 1; p >= p0; --p) {
-            Gsuf = acc_add_r(Gsuf, W.cB[p]);
-            R G = acc_to_r(Gsuf);
-            W.ak[p] = -G * W.Ra[p];
-            W.bk[p] = -G * W.Rb[p];
-        }
-        A Hex = gd.x;
-        for (int p = p0; p < p1; ++p) {
-            R H = acc_to_r(Hex);
-            W.ak[p] += H * W.Da[p];
-            W.bk[p] += H * W.Db[p];
-            Hex = acc_add_r(Hex, W.cC[p]);
-        }
-        if (tid == 0) {
-            R H = acc_to_r(d_tot);
-            W.ak[n] = H * W.Da[n];
-            W.bk[n] = H * W.Db[n];
-        }
-    }
+    bp_region_solve(W, sR, n, p0, p1, sscan);
     __syncthreads();
 
     // B^(p) at the rings, guard, dumps, derivatives
@@ -322,29 +252,6 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
     const R dxi = (R)W.dxi;
     const R inv_2pi_dxi = (R)(1.0 / (6.283185307179586476925286766559 * W.dxi));
 
-    // bitonic sort of keys[0..n) (padded to n_pad) with vals the positions;
-    // equal keys keep their position order
-    auto block_sort = [&](int n_keys) {
-        for (int k = 2; k <= W.n_pad; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < W.n_pad; i += T) {
-                    int ixj = i ^ j;
-                    if (ixj > i) {
-                        R ki = keys[i], kj = keys[ixj];
-                        int vi = vals[i], vj = vals[ixj];
-                        bool gt = (ki > kj) || (ki == kj && vi > vj);
-                        if (gt == ((i & k) == 0)) {
-                            keys[i] = kj; keys[ixj] = ki;
-                            vals[i] = vj; vals[ixj] = vi;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        (void)n_keys;
-    };
-
     for (; slice < s_end; ++slice) {
         // ---------------- a2: sort the state by radius (stable)
         {
@@ -358,7 +265,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
                     vals[i] = i;
                 }
                 __syncthreads();
-                block_sort(n);
+                block_bitonic_sort(keys, vals, W.n_pad);
                 const int nb = buf ^ 1;
                 for (int p = tid; p < n; p += T) {
                     int src = vals[p];
@@ -487,7 +394,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
                     vals[i] = i;
                 }
                 __syncthreads();
-                block_sort(n);
+                block_bitonic_sort(keys, vals, W.n_pad);
                 for (int i = tid; i < n; i += T) W.rk_perm[i] = vals[i];
                 perm = W.rk_perm;
                 __syncthreads();
