@@ -6,10 +6,16 @@
  * benchmark's CPU-baseline/reference legs may load it; the product library
  * never links or calls it, and it shares no code with the CUDA sources.
  *
- * Model: Sec. II of the paper (gridless quasistatic model), electrons only
- * (q = -1, m = 1) over an immobile uniform ion column of density n filling
- * rho <= rho_max = edges[N] (the Baxevanis-Stupakov limit named at the end of
- * Sec. II), no laser.  xi = -zeta; one step advances xi by dxi.
+ * Model: Sec. II of the paper (gridless quasistatic model), no laser; xi =
+ * -zeta, one step advances xi by dxi.
+ *   orc_run: electrons (q = -1, m = 1) over an immobile uniform ion column of
+ *     density n filling rho <= rho_max = edges[N] (the Baxevanis-Stupakov
+ *     limit named at the end of Sec. II); the ring integrator AB2 (Sec. III)
+ *     or RK4; the beam fields gridless (a9) or through adaptive beam grids
+ *     (Sec. IV, AB2 only).
+ *   orc_run_ions: electrons and mobile ions as two ring species (Sec. II,
+ *     multiple plasma species), with an optional radial density profile.
+ * The beam push between solves is oracle/beam_push.py.
  */
 #ifndef WAKE_ORACLE_H
 #define WAKE_ORACLE_H
