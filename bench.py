@@ -356,7 +356,20 @@ def push_bench(args, gs, wakes, stream):
     ms = e0.elapsed_time(e1) / reps
     peak = _peaks().get("hbm_gbs", 6800.0)
     gbs = PUSH_BYTES_PER_PARTICLE * n_part / (ms / 1e3) / 1e9
+    # one coupled stage step (Sec. V): bin the pushed beams again (the
+    # densest slice read back from the device), solve every wake, push
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    wm.wake_batch_reset(gs)
+    wm.wake_batch_run(gs)
+    wm.wake_batch_push_beam(gs, 0.1)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    stage_ms = s0.elapsed_time(s1)
+    stage_rs = sum(wk.n_rings * g.progress()[0] for g, wk in zip(gs, wakes))
     return {"particles": n_part, "ms_per_push": ms, "particles_per_s": n_part / (ms / 1e3),
+            "stage_step": {"ms": stage_ms, "ring_slices_per_s": stage_rs / (stage_ms / 1e3),
+                           "steps": "batched reset of the pushed beams + march + push"},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "bytes_per_particle": PUSH_BYTES_PER_PARTICLE, "peak_basis": "measured copy (MEASURED_PEAKS.json)"}}
 

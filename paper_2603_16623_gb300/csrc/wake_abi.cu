@@ -93,6 +93,8 @@ struct wake_handle {
     int32_t fast_k = 8;                     // its rings per thread
     int32_t fast_cl = 1;                    // CTAs per wake (thread-block cluster if > 1)
     int32_t slice_max = kMaxSliceParticles; // particles in the densest slice (host count)
+    bool recount = false;                   // the beam moved on the device (push): the next
+                                            // preparation reads the densest slice back
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
 };
 
@@ -987,6 +989,9 @@ wake_status push_enqueue(wake_handle* const* hs, int32_t n, double dt, cudaStrea
                                 (int32_t)items.size(), dt, st);
     cudaFreeAsync(buf, st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_push_beam: %s", cudaGetErrorString(e));
+    // particles may have changed slices: the next binning sizes its sort
+    // from the device's count, not the one taken before the push
+    for (int32_t i = 0; i < n; ++i) hs[i]->recount = true;
     return WAKE_OK;
 }
 
@@ -1123,6 +1128,21 @@ wake_status wake_reset(wake_handle* h, const wake_beam_desc* beams, int32_t n_be
     WK_TRY(check_handle(h));
     WK_TRY(check_new_beams(h, beams, n_beams));
     WK_TRY(upload_beams(h, beams, n_beams, h->st));
+    if (h->recount && !beams) {
+        // the pushed beam: histogram, then the densest slice from the device
+        if (h->prec == WAKE_FP64) WK_TRY(prepare_impl<PrecF64>(h, h->st, true));
+        else WK_TRY(prepare_impl<PrecMixed>(h, h->st, true));
+        if (h->nb_total > 0) {
+            int32_t dmax = 0;
+            WK_CUDA(cudaMemcpyAsync(&dmax, h->d_dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+            WK_CUDA(cudaStreamSynchronize(h->st));
+            h->slice_max = dmax;
+        }
+        h->recount = false;
+        if (h->prec == WAKE_FP64) return prepare_sort<PrecF64>(h, h->st);
+        return prepare_sort<PrecMixed>(h, h->st);
+    }
+    h->recount = false;
     if (h->prec == WAKE_FP64) return prepare_impl<PrecF64>(h, h->st);
     return prepare_impl<PrecMixed>(h, h->st);
 }
@@ -1153,9 +1173,11 @@ wake_status wake_batch_reset(int32_t n, wake_handle* const* handles, const wake_
         WK_CUDA(aux_stream(j, &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
     }
-    // with new beams the densest slice is read back from the device between
-    // the histogram and the sort (one synchronisation for the whole batch)
-    const bool split = beams != nullptr;
+    // with new beams, or beams moved by a push, the densest slice is read back
+    // from the device between the histogram and the sort (one
+    // synchronisation for the whole batch)
+    bool split = beams != nullptr;
+    for (int32_t i = 0; i < n; ++i) split = split || handles[i]->recount;
     for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
         wake_handle* h = handles[i];
         cudaStream_t as = nullptr;
@@ -1177,6 +1199,7 @@ wake_status wake_batch_reset(int32_t n, wake_handle* const* handles, const wake_
         for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
             wake_handle* h = handles[i];
             if (h->nb_total > 0) h->slice_max = dmax[(size_t)i];
+            h->recount = false;
             cudaStream_t as = nullptr;
             WK_CUDA(aux_stream(i % n_streams, &as));
             res = h->prec == WAKE_FP64 ? prepare_sort<PrecF64>(h, as) : prepare_sort<PrecMixed>(h, as);

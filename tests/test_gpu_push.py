@@ -160,3 +160,53 @@ def test_two_species_and_batched_push_match_oracle():
         for k in ("x", "y", "xi", "ux", "uy", "uz"):
             assert nerr(got[k] - ps0[k], ref[k] - ps0[k]) < 2e-6, (wk.name, k)
         g.close()
+
+
+def _crowding_beam():
+    """Three groups of 1000 particles in slices 18, 19, 20 whose axial
+    velocities would slip them all into slice 30 in one push of dt = 0.2
+    (where 100 fast particles sit) without fields: the densest slice grows
+    from 1000 particles to over 2000."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    xi, uz = [], []
+    for xi0, vz in ((0.20, 0.5), (0.19, 0.45), (0.18, 0.4)):
+        xi.append(np.full(1000, xi0))
+        uz.append(np.full(1000, vz / np.sqrt(1 - vz * vz)))
+    xi.append(np.full(100, 0.30))
+    uz.append(np.full(100, 2000.0))
+    xi, uz = np.concatenate(xi), np.concatenate(uz)
+    r = 0.3 * np.sqrt(-2 * np.log(1 - rng.random(xi.shape[0])))
+    beam = W.Beam(xi, r, np.full(xi.shape[0], 2e-4), -1.0)
+    return W.Wake("crowd", W.edges_uniform(150, 4.0), [beam], 0.01, 60), uz
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_a_push_that_crowds_a_slice_is_binned_again(batched):
+    from paper_2603_16623_gb300 import wake as wm
+    wk, uz = _crowding_beam()
+    n = wk.n_beam
+    g = wm.Wake.from_workload(wk, precision="fp64")
+    st, _, _, _ = g.run()
+    assert st == 0
+    g.set_beam_phase_space(wk.beams[0].r, np.zeros(n), np.zeros(n), np.zeros(n), uz)
+    if batched:
+        wm.wake_batch_push_beam([g], 0.2)
+        wm.wake_batch_reset([g])
+        wm.wake_batch_run([g])
+        st = g.progress()[1]
+    else:
+        g.push_beam(0.2)
+        g.reset()
+        st, _, _, _ = g.run()
+    assert st == 0
+    ps = g.beam_phase_space()
+    sl = np.floor(ps["xi"] / wk.dxi + 0.5).astype(int)
+    # the fields spread the slow groups over a few slices; the densest now
+    # holds more than the 1024 that a sort sized from before the push takes
+    assert np.bincount(sl).max() > 1024
+    ref = oracle.run_wake(W.Wake(wk.name, wk.edges, [W.Beam(ps["xi"], ps["r"], wk.beams[0].w, -1.0)], wk.dxi,
+                                 wk.n_steps))
+    got = g.beam_fields(("ez", "wr"))
+    for k in ("ez", "wr"):
+        assert nerr(got[k], ref.beam[k]) < 1e-10, k
+    g.close()
