@@ -260,7 +260,7 @@ def run_ours(args):
     if not args.skip_serve:
         serving = serve_bench(args, wakes, pinned, stream, rank)
 
-    # ---- plain FP64 one-wake-per-launch on a bounded sample (the spec denominator)
+    # ---- plain FP64 one-wake-per-launch on a bounded sample (the plain GPU baseline)
     plain = None
     if not args.skip_plain and rank == 0:
         sample = wakes[: args.plain_wakes]
