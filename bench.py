@@ -148,14 +148,21 @@ def run_ours(args):
     n_march_launches = len({g.launch_config() for g in gs})
 
     def step(ev=None):
+        # a0/a1 preparation and the march of every wake, pipelined: each
+        # launch shape's march starts once its own wakes are prepared
         if ev is not None:
             ev[0].record(stream)
-        wm.wake_batch_reset(gs)
+        wm.wake_batch_reset_run(gs)
         if ev is not None:
             ev[1].record(stream)
+
+    def phase_step(ev):
+        # the two phases one after the other (for their times)
+        ev[0].record(stream)
+        wm.wake_batch_reset(gs)
+        ev[1].record(stream)
         wm.wake_batch_run(gs)
-        if ev is not None:
-            ev[2].record(stream)
+        ev[2].record(stream)
 
     for _ in range(args.warmup):
         step()
@@ -168,7 +175,7 @@ def run_ours(args):
         ring_slices += wk.n_rings * nxt
         stopped += int(st != 0)
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{os.getpid()}.csv")
     proc, fh = _clock_sampler(clk_path) if rank == 0 else (None, None)
     if ws > 1:
@@ -185,9 +192,12 @@ def run_ours(args):
         proc.terminate()
         proc.wait()
         fh.close()
-    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
-    march_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    phase_step(pev)
+    torch.cuda.synchronize()
+    march_ms = [pev[1].elapsed_time(pev[2])]
+    prep_ms = [pev[0].elapsed_time(pev[1])]
     tot_ms = sum(step_ms)
     if ws > 1:
         tot_ms_max, rs_all = _reduce_max_sum(tot_ms, ring_slices, "cuda")
@@ -317,7 +327,8 @@ def run_ours(args):
             "rk4": _alu_roofline(rk4, peak_tflops, sm_mhz, FLOPS_PER_RING_SLICE_RK4, "march_rk4_kernel<PrecMixed>", 1),
             "beam_grid": grid,
             "clocks": clocks,
-            "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms},
+            "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms,
+                          "note": "one untimed step with the two phases in sequence; the timed steps pipeline them"},
             "wall_s": wall,
         }
         print(json.dumps(line))

@@ -230,6 +230,13 @@ wake_status wake_run(wake_handle *h, void *beam_ez, void *beam_wr, void *ring_r)
    wake_get_progress. */
 wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
 
+/* wake_batch_reset(n, handles, NULL, NULL) followed by wake_batch_run, as
+   one pipelined submission: each kernel configuration's march starts as soon
+   as its own wakes are prepared (the costliest configurations' wakes are
+   prepared first), so the preparation of the others overlaps it.  The same
+   results as the two calls.  Errors: as wake_batch_run. */
+wake_status wake_batch_reset_run(int32_t n, wake_handle *const *handles);
+
 /* Advances every wake by up to max_slices slices (fewer at the end of a
    window or after a stop), in the launches of wake_batch_run.  With
    time_budget_ns > 0 each wake's launch also stops at the first slice

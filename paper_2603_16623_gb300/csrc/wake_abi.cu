@@ -736,17 +736,16 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     return WAKE_OK;
 }
 
-template <class P>
-wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, int64_t budget_ns) {
-    cudaStream_t st = hs[0]->st;
-    // one bucket per kernel configuration, each on its own stream, ordered
-    // after the work already queued on the handles' stream and joined back
+// The handles grouped by kernel configuration (one march launch each),
+// the bucket with the longest critical path (slices x rings per CTA of its
+// longest wake) first.
+std::vector<std::vector<wake_handle*>> bucket_handles(int32_t n, wake_handle* const* hs) {
     std::vector<int32_t> keys;
     std::vector<std::vector<wake_handle*>> buckets;
     for (int32_t i = 0; i < n; ++i) {
         int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
-        // the one-CTA kernels (plain and two-species) by their block size
+        // the one-CTA kernels (plain, two-species, RK4, grids) by their block size
         if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * (hs[i]->grid_nr > 0) +
                                           8 * hs[i]->threads);
         auto it = std::find(keys.begin(), keys.end(), key);
@@ -757,9 +756,6 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
         }
         buckets[it - keys.begin()].push_back(hs[i]);
     }
-    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st, max_slices, budget_ns);
-    // longest critical path first: slices x rings per CTA of the bucket's
-    // longest wake
     std::vector<double> cost(buckets.size(), 0.0);
     for (size_t b = 0; b < buckets.size(); ++b)
         for (const wake_handle* h : buckets[b]) {
@@ -768,17 +764,28 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
         }
     std::vector<size_t> border(buckets.size());
     for (size_t b = 0; b < border.size(); ++b) border[b] = b;
-    std::stable_sort(border.begin(), border.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(border.begin(), border.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<std::vector<wake_handle*>> out;
+    for (size_t b : border) out.push_back(std::move(buckets[b]));
+    return out;
+}
+
+template <class P>
+wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, int64_t budget_ns) {
+    cudaStream_t st = hs[0]->st;
+    // one bucket per kernel configuration, each on its own stream, ordered
+    // after the work already queued on the handles' stream and joined back
+    std::vector<std::vector<wake_handle*>> buckets = bucket_handles(n, hs);
+    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st, max_slices, budget_ns);
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
     wake_status res = WAKE_OK;
-    for (size_t i = 0; i < border.size(); ++i) {
-        const size_t b = border[i];
+    for (size_t i = 0; i < buckets.size(); ++i) {
         cudaStream_t as = nullptr;
         WK_CUDA(aux_stream((int)(i % kAuxStreams), &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
-        wake_status r = batch_bucket<P>(buckets[b], buckets[b][0]->fast_threads, as, max_slices, budget_ns);
+        wake_status r = batch_bucket<P>(buckets[i], buckets[i][0]->fast_threads, as, max_slices, budget_ns);
         if (r != WAKE_OK) res = r;
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -787,6 +794,76 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
         cudaEventDestroy(done);
     }
     cudaEventDestroy(start);
+    return res;
+}
+
+// The a0/a1 preparation and the whole-window march of n wakes, pipelined:
+// the preparations run on half of the auxiliary streams, the costliest
+// buckets' wakes first, and each bucket's march waits only for its own
+// wakes' preparations (on the other half), so that the heavy marches start
+// while the light wakes are still being prepared.  Everything is ordered
+// after the work queued on the handles' stream and joined back into it.
+template <class P>
+wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs) {
+    cudaStream_t st = hs[0]->st;
+    std::vector<std::vector<wake_handle*>> buckets = bucket_handles(n, hs);
+    constexpr int kPrepStreams = kAuxStreams / 2;
+    cudaEvent_t start;
+    WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    WK_CUDA(cudaEventRecord(start, st));
+    for (int j = 0; j < kPrepStreams; ++j) {
+        cudaStream_t ps = nullptr;
+        WK_CUDA(aux_stream(kAuxStreams - 1 - j, &ps));
+        WK_CUDA(cudaStreamWaitEvent(ps, start, 0));
+    }
+    std::vector<cudaEvent_t> events;
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        cudaEventDestroy(start);
+    };
+    wake_status res = WAKE_OK;
+    int next_prep = 0;
+    for (size_t i = 0; i < buckets.size() && res == WAKE_OK; ++i) {
+        cudaStream_t ms = nullptr;
+        if (aux_stream((int)(i % kPrepStreams), &ms) != cudaSuccess) {
+            res = fail(WAKE_ECUDA, "wake_batch_reset_run: no stream");
+            break;
+        }
+        cudaStreamWaitEvent(ms, start, 0);
+        for (wake_handle* h : buckets[i]) {
+            cudaStream_t ps = nullptr;
+            aux_stream(kAuxStreams - 1 - (next_prep++ % kPrepStreams), &ps);
+            res = prepare_impl<P>(h, ps);
+            if (res != WAKE_OK) break;
+            h->recount = false;
+            cudaEvent_t ready;
+            if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+                res = fail(WAKE_ECUDA, "wake_batch_reset_run: event creation failed");
+                break;
+            }
+            events.push_back(ready);
+            cudaEventRecord(ready, ps);
+            cudaStreamWaitEvent(ms, ready, 0);
+        }
+        if (res != WAKE_OK) break;
+        res = batch_bucket<P>(buckets[i], buckets[i][0]->fast_threads, ms, 1 << 30, 0);
+        cudaEvent_t done;
+        WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        events.push_back(done);
+        WK_CUDA(cudaEventRecord(done, ms));
+        WK_CUDA(cudaStreamWaitEvent(st, done, 0));
+    }
+    // the preparation streams join back too (also after an error)
+    for (int j = 0; j < kPrepStreams; ++j) {
+        cudaStream_t ps = nullptr;
+        if (aux_stream(kAuxStreams - 1 - j, &ps) != cudaSuccess) continue;
+        cudaEvent_t done;
+        if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) continue;
+        events.push_back(done);
+        cudaEventRecord(done, ps);
+        cudaStreamWaitEvent(st, done, 0);
+    }
+    cleanup();
     return res;
 }
 
@@ -1305,6 +1382,26 @@ wake_status wake_batch_step(int32_t n, wake_handle* const* handles, int32_t max_
 
 wake_status wake_batch_run(int32_t n, wake_handle* const* handles) {
     return wake_batch_step(n, handles, 1 << 30, 0);
+}
+
+wake_status wake_batch_reset_run(int32_t n, wake_handle* const* handles) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_reset_run: bad handle array");
+    if (n == 0) return WAKE_OK;
+    bool recount = false;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_reset_run: handle %d is NULL", i);
+        if (handles[i]->prec != handles[0]->prec || handles[i]->st != handles[0]->st)
+            return fail(WAKE_EINVAL, "wake_batch_reset_run: handles must share precision and stream");
+        recount = recount || handles[i]->recount;
+    }
+    // a pushed beam needs its densest slice read back between histogram and
+    // sort: the two calls in sequence
+    if (recount) {
+        WK_TRY(wake_batch_reset(n, handles, nullptr, nullptr));
+        return wake_batch_run(n, handles);
+    }
+    if (handles[0]->prec == WAKE_FP64) return batch_reset_run_impl<PrecF64>(n, handles);
+    return batch_reset_run_impl<PrecMixed>(n, handles);
 }
 
 wake_status wake_batch_progress(int32_t n, wake_handle* const* handles, int32_t* next_slice, int32_t* status) {

@@ -71,6 +71,7 @@ _SIGS = {
     "wake_get_beam_phase_space": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_push_beam": ([_vp, C.c_double], C.c_int),
     "wake_batch_push_beam": ([C.c_int32, C.POINTER(_vp), C.c_double], C.c_int),
+    "wake_batch_reset_run": ([C.c_int32, C.POINTER(_vp)], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -395,6 +396,14 @@ def wake_batch_run(wakes: List[Wake]):
     """All wakes' remaining slices in one persistent launch."""
     arr = (_vp * len(wakes))(*[w.handle for w in wakes])
     _check(load().wake_batch_run(len(wakes), arr))
+
+
+def wake_batch_reset_run(wakes: List[Wake]):
+    """wake_batch_reset (device-resident beams) + wake_batch_run as one
+    pipelined submission: each launch shape's march starts once its own
+    wakes are prepared."""
+    arr = (_vp * len(wakes))(*[w.handle for w in wakes])
+    _check(load().wake_batch_reset_run(len(wakes), arr))
 
 
 def wake_max_rings(precision: str = "mixed") -> int:

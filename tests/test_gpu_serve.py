@@ -104,3 +104,29 @@ def test_device_bytes_estimate_bounds_the_allocation():
         est = serve.estimate_device_bytes(wk.n_rings, wk.n_beam, wk.n_steps)
         assert 0 < got <= est, (wk.name, got, est)
         g.close()
+
+
+def test_pipelined_reset_run_equals_reset_then_run():
+    """wake_batch_reset_run gives bitwise the results of wake_batch_reset +
+    wake_batch_run, on a batch that mixes one-CTA and cluster wakes, a
+    mobile-ion wake and an RK4 wake, run twice in a row."""
+    from paper_2603_16623_gb300 import wake as wm
+    wakes = _mix()[:6]
+    drv = W.gaussian_beam(9_000, 1.0, 0.3, 0.5, 1.6, seed=731)
+    wakes.append(W.Wake("ions", W.edges_uniform(300, 5.0), [drv], 0.01, 260, ions=(1.0, 100.0)))
+    wakes.append(W.Wake("rk4", W.edges_uniform(280, 5.0), [drv], 0.01, 240, integrator="rk4"))
+    a = [wm.Wake.from_workload(wk, precision="mixed") for wk in wakes]
+    b = [wm.Wake.from_workload(wk, precision="mixed") for wk in wakes]
+    for _ in range(2):
+        wm.wake_batch_reset(a)
+        wm.wake_batch_run(a)
+        wm.wake_batch_reset_run(b)
+        na, sa = wm.wake_batch_progress(a)
+        nb, sb = wm.wake_batch_progress(b)
+        assert list(na) == list(nb) and list(sa) == list(sb)
+        for ga, gb in zip(a, b):
+            fa, fb = ga.beam_fields(("ez", "wr")), gb.beam_fields(("ez", "wr"))
+            assert np.array_equal(fa["ez"], fb["ez"]) and np.array_equal(fa["wr"], fb["wr"])
+            assert np.array_equal(ga.ring_state()[0], gb.ring_state()[0])
+    for g in a + b:
+        g.close()
