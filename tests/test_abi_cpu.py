@@ -70,3 +70,41 @@ def test_launch_shape_is_validated_on_the_host(precision, n, k, cl, why):
     assert st == wm.WAKE_EINVAL
     assert not h.value
     assert why in lib.wake_last_error().decode()
+
+
+@pytest.mark.parametrize("case,why", [
+    ({"ion_charge": -1.0, "ion_mass": 10.0}, "ion_charge > 0"),
+    ({"ion_charge": 1.0, "ion_mass": 0.0}, "ion_charge > 0"),
+    ({"ion_charge": 1.0, "ion_mass": float("nan")}, "ion_charge > 0"),
+    ({"ion_charge": 1.0, "ion_mass": 100.0, "k": 4}, "do not apply with mobile ions"),
+    ({"ion_charge": 1.0, "ion_mass": 100.0, "n": 4097}, "with mobile ions"),
+    ({"profile": 1.0}, "needs ion rings"),
+    ({"ion_charge": 1.0, "ion_mass": 100.0, "profile": -1.0}, "cell_density[7]"),
+    ({"integrator": 7}, "unknown integrator"),
+    ({"integrator": 1, "ion_charge": 1.0, "ion_mass": 100.0}, "RK4 runs electron-only"),
+    ({"integrator": 1, "cl": 2}, "RK4 runs electron-only"),
+    ({"grid_nr": 2000, "precision": "fp64"}, "grid_nr must be"),
+    ({"grid_nr": 16}, "beam grids run WAKE_FP64"),
+    ({"grid_nr": 16, "precision": "fp64", "integrator": 1}, "beam grids run WAKE_FP64"),
+])
+def test_model_options_are_validated_on_the_host(case, why):
+    """Mobile ions, density profiles, the RK4 integrator and beam grids: bad
+    combinations fail in wake_init with EINVAL before any device work."""
+    from paper_2603_16623_gb300 import wake as wm
+    lib = wm.load()
+    n = case.get("n", 100)
+    edges = np.linspace(0.0, 5.0, n + 1)
+    prof = None
+    if "profile" in case:
+        prof = np.full(n, 1.0)
+        prof[7] = case["profile"]
+    cfg = wm.wake_config(0.01, 10, wm.PRECISION[case.get("precision", "mixed")], 0, 0, case.get("k", 0),
+                         case.get("cl", 0), case.get("integrator", 0), case.get("grid_nr", 0))
+    dp = ctypes.POINTER(ctypes.c_double)
+    plasma = wm.wake_plasma_desc(n, edges.ctypes.data_as(dp), 1.0, case.get("ion_charge", 0.0),
+                                 case.get("ion_mass", 0.0), prof.ctypes.data_as(dp) if prof is not None else None)
+    h = ctypes.c_void_p()
+    st = lib.wake_init(ctypes.byref(cfg), ctypes.byref(plasma), None, 0, None, ctypes.byref(h))
+    assert st == wm.WAKE_EINVAL
+    assert not h.value
+    assert why in lib.wake_last_error().decode()
