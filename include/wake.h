@@ -283,8 +283,11 @@ wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, vo
                                 void *dpsidz, void *bp, void *bb);
 
 /* How the march kernels serve this wake: threads per block, rings per
-   thread, and thread blocks per wake (> 1: a thread-block cluster).  For
-   batched launches, wakes with equal triples share one launch. */
+   thread (on the one-CTA marches: ceil(rings / threads), both species
+   counted with mobile ions), and thread blocks per wake (> 1: a thread-
+   block cluster).  For batched launches, wakes of the same march (on-chip,
+   plain, two-species, RK4, beam grids) with equal triples share one
+   launch. */
 wake_status wake_get_launch_config(wake_handle *h, int32_t *threads, int32_t *rings_per_thread,
                                    int32_t *blocks_per_wake);
 
