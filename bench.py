@@ -414,17 +414,20 @@ def rk4_bench(args, wakes, stream):
 
 def grid_bench(args, wakes, stream):
     """The paper's grid coupling (adaptive beam grids of 32 radial cells per
-    beam) against the gridless one, both FP64 on the one-CTA march, on the
-    same batched wakes of <= 8192 rings over a bounded window (their first
-    args.grid_slices slices): batched reset + step, CUDA-event timed."""
+    beam) against the gridless one on the same batched wakes of <= 8192
+    rings over a bounded window (their first args.grid_slices slices):
+    FP64 (both on the one-CTA march) and mixed (grids on the one-CTA march,
+    gridless on the on-chip one); batched reset + step, CUDA-event timed."""
     import dataclasses
 
     import torch
     from paper_2603_16623_gb300 import wake as wm
     sel = [wk for wk in wakes if wk.n_rings <= 8192][: args.grid_wakes]
-    out = {"wakes": len(sel), "slices": args.grid_slices, "precision": "fp64", "grid_nr": 32}
-    for name, nr in (("gridless", 0), ("grid", 32)):
-        gs = [wm.Wake.from_workload(dataclasses.replace(wk, grid_nr=nr), precision="fp64", stream=stream.cuda_stream)
+    out = {"wakes": len(sel), "slices": args.grid_slices, "grid_nr": 32,
+           "note": "fp64: both on the one-CTA march; mixed: grids on the one-CTA march, gridless on the on-chip one"}
+    for name, nr, prec in (("gridless", 0, "fp64"), ("grid", 32, "fp64"), ("mixed_gridless", 0, "mixed"),
+                           ("mixed_grid", 32, "mixed")):
+        gs = [wm.Wake.from_workload(dataclasses.replace(wk, grid_nr=nr), precision=prec, stream=stream.cuda_stream)
               for wk in sel]
         wm.wake_batch_reset(gs)
         wm.wake_batch_step(gs, args.grid_slices)  # warm-up
@@ -441,6 +444,7 @@ def grid_bench(args, wakes, stream):
         for g in gs:
             g.close()
     out["grid_over_gridless_time"] = out["grid"]["ms_per_step"] / out["gridless"]["ms_per_step"]
+    out["mixed_grid_over_gridless_time"] = out["mixed_grid"]["ms_per_step"] / out["mixed_gridless"]["ms_per_step"]
     return out
 
 

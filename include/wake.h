@@ -140,8 +140,8 @@ typedef struct {
                                  radius, one node line per slice; B^(b) at
                                  the rings from the grids (B_N r_N / rho
                                  beyond), beam-particle fields interpolated
-                                 from the nodes.  WAKE_FP64, WAKE_AB2, no
-                                 mobile ions, at most 8 beam species.         */
+                                 from the nodes.  WAKE_AB2, no mobile ions,
+                                 at most 8 beam species; both precisions. */
 } wake_config;
 
 typedef struct wake_handle wake_handle;

@@ -87,6 +87,7 @@ struct WakeDev {
     int64_t sp_begin[kMaxGridSpecies + 1];
     const int32_t* bidx;
     const double* qw;
+    const double* rc;  // the caller's beam radii (FP64)
     const double* ag_rmax;
     R *agB, *agF;
 };
@@ -148,6 +149,65 @@ __device__ __forceinline__ double ag_field(const WakeDev<P>& W, double rho) {
     double v = 0.0;
     for (int b = 0; b < W.n_species; ++b) v += ag_species_field(W, b, rho);
     return v;
+}
+
+// ---------------------------------------------------------------------------
+// precision helpers of the one-CTA marches: in FP64 they are the plain
+// operations; the mixed path keeps ring radii float-float (hi in rho, lo in
+// rho_lo), takes ln rho as ln rho0 + log1p((rho - rho0) / rho0) and the
+// weights float-float from the per-ring table ctab
+// ---------------------------------------------------------------------------
+// ln rho of ring `id` at radius (r, r_lo) in the accumulator type
+__device__ __forceinline__ double ring_log(const float4*, int, double r, double) { return log(r); }
+__device__ __forceinline__ ff ring_log(const float4* ctab, int id, float r, float r_lo) {
+    const float4 c = ctab[3 * id];  // {rho0 (hi, lo), ln rho0 (hi, lo)}
+    const ff r0 = {c.x, c.y};
+    const float dl = ff_to_f(ff_acc(ff{r, r_lo}, ff_neg(r0)));
+    return ff_add_f(ff{c.z, c.w}, log1pf(dl / c.x));
+}
+// ln X of an arbitrary radius X (accumulator type), relative to the plasma
+// edge whose logarithm ln_e is known to the accumulator's precision
+__device__ __forceinline__ double acc_log(double X, double, double, double) { return log(X); }
+__device__ __forceinline__ ff acc_log(ff X, ff Xe, ff ln_e, float edge) {
+    return ff_add_f(ln_e, log1pf(ff_to_f(ff_acc(X, ff_neg(Xe))) / edge));
+}
+__device__ __forceinline__ double acc_mul_a(double a, double b) { return a * b; }
+__device__ __forceinline__ ff acc_mul_a(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ double acc_div(double a, double b) { return a / b; }
+__device__ __forceinline__ ff acc_div(ff a, ff b) {
+    const float q1 = a.hi / b.hi;
+    const ff rem = ff_acc(a, ff_neg(ff_mul_f(b, q1)));
+    return ff_fast_two_sum(q1, rem.hi / b.hi);
+}
+// ring radius at sorted position p in the accumulator type
+__device__ __forceinline__ double ring_radius(const double* hi, const double*, int p) { return hi[p]; }
+__device__ __forceinline__ ff ring_radius(const float* hi, const float* lo, int p) { return ff{hi[p], lo[p]}; }
+
+// rho + d in the state's arithmetic: FP64, or float-float (hi in r, lo in r_lo)
+__device__ __forceinline__ void radius_add(double& r, double&, double d) { r += d; }
+__device__ __forceinline__ void radius_add(float& r, float& r_lo, float d) {
+    const ff s = ff_add_f(ff{r, r_lo}, d);
+    r = s.hi;
+    r_lo = s.lo;
+}
+
+// a radius (hi, lo) in the accumulator type
+__device__ __forceinline__ double make_radius(double hi, double) { return hi; }
+__device__ __forceinline__ ff make_radius(float hi, float lo) { return ff{hi, lo}; }
+
+// ring id's weight and self weight in the accumulator type: the mixed path
+// takes them float-float from the per-ring table ({w, what} = ctab[3 id + 1]),
+// since their sum meets the exact ion column and FP32-rounded weights would
+// leave ~1e-7 of the enclosed charge
+__device__ __forceinline__ void ring_weights(const float4*, const double* w, const double* wh, int id, double& wa,
+                                             double& wha) {
+    wa = w[id];
+    wha = wh[id];
+}
+__device__ __forceinline__ void ring_weights(const float4* ctab, const float*, const float*, int id, ff& wa, ff& wha) {
+    const float4 c = ctab[3 * id + 1];
+    wa = ff{c.x, c.y};
+    wha = ff{c.z, c.w};
 }
 
 __device__ __forceinline__ double acc_add_prod(double a, double x, double y) { return a + x * y; }
@@ -329,7 +389,10 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 W.frho[nb][p] = W.frho[buf][src];
                 W.fur[nb][p] = W.fur[buf][src];
                 W.rid[nb][p] = W.rid[buf][src];
+                keys[p] = W.rho_lo[src];  // the sort keys are no longer needed
             }
+            __syncthreads();
+            for (int p = tid; p < n; p += T) W.rho_lo[p] = keys[p];
             buf = nb;
             rho = W.rho[buf];
             __syncthreads();
@@ -365,7 +428,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 const int64_t k = W.bidx[b0 + q];
                 const int b = ag_species(W, k);
                 const double dr = ag_extent(W, b) / nr;
-                const int j = ag_cell((double)W.br[b0 + q], dr, nr) + 1;
+                const int j = ag_cell(W.rc[k], dr, nr) + 1;
                 atomicAdd(W.agB + (size_t)b * (nr + 1) + j, (R)W.qw[k]);
             }
             __syncthreads();
@@ -387,7 +450,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         for (int p = p0; p < p1; ++p) {
             R r = sR[p];
             int id = rid[p];
-            R w = W.w[id];
+            A wa, wha;
+            ring_weights(W.ctab, W.w, W.wh, id, wa, wha);
             R bbv = 0;
             if (nr > 0) {
                 bbv = (R)ag_field(W, (double)r);
@@ -397,8 +461,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 bbv = Q * inv_2pi_dxi / r;
             }
             W.bb[p] = bbv;
-            loc.x = acc_add_r(loc.x, w);
-            loc.y = acc_add_prod(loc.y, w, real_log(r));
+            loc.x = acc_add(loc.x, wa);
+            loc.y = acc_add(loc.y, acc_mul_a(ring_log(W.ctab, id, r, W.rho_lo[p]), wa));
         }
         Pair<A> tot;
         Pair<A> ex = block_excl_scan<false>(loc, OpAddPair(), Pair<A>{zeroA, zeroA},
@@ -412,15 +476,22 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
             R r = sR[p];
             R u = ur[p];
             int id = rid[p];
-            R w = W.w[id], wh = W.wh[id];
-            R lnr = real_log(r);
+            R w = W.w[id];
+            A wa, wha;
+            ring_weights(W.ctab, W.w, W.wh, id, wa, wha);
+            const A X = make_radius(r, W.rho_lo[p]);
+            const A lnr = ring_log(W.ctab, id, r, W.rho_lo[p]);
             A Lsuf = acc_sub(Ltot, L);
             W.regS[p] = S;
             W.regL[p] = Lsuf;
-            A psiA = acc_add(acc_add(Lsuf, acc_mul_r(S, lnr)), ion_psi(r, rmax, quarter_n, Imax, c0));
+            // the ion column's terms from the radius in the accumulator type:
+            // psi and d_rho psi are differences of terms ~n rho_max^2
+            const A r2 = acc_mul_a(X, X);
+            const A Ir = r < rmax ? acc_mul_r(r2, half_n) : Imax;
+            const A psion = r <= rmax ? acc_sub(c0, acc_mul_r(r2, quarter_n)) : acc_sub(zeroA, acc_mul_a(Imax, lnr));
+            A psiA = acc_add(acc_add(Lsuf, acc_mul_a(S, lnr)), psion);
             R psi = acc_to_r(psiA);
-            A encl = acc_sub(acc_add_r(S, wh), ion_enclosed(r, rmax, half_n, Imax));
-            R dprv = acc_to_r(encl) / r;
+            R dprv = acc_to_r(acc_div(acc_sub(acc_add(S, wha), Ir), X));
             R pb = (R)1 + psi;
             R g = ((R)1 + u * u + pb * pb) / ((R)2 * pb);
             R t = w * u / (r * pb);
@@ -433,8 +504,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 W.dump_psi[row] = psi;
                 W.dump_dpr[row] = dprv;
             }
-            S = acc_add_r(S, w);
-            L = acc_add_prod(L, w, lnr);
+            S = acc_add(S, wa);
+            L = acc_add(L, acc_mul_a(lnr, wa));
             tl = acc_add_r(tl, t);
         }
         if (tid == 0) {
@@ -532,7 +603,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 const int64_t kc = W.bidx[b0 + q];
                 const int b = ag_species(W, kc);
                 const double dr = ag_extent(W, b) / nr;
-                const double x = (double)W.br[b0 + q];
+                const double x = W.rc[kc];  // the caller's FP64 radius: node membership as the oracle's
                 const int j = ag_cell(x, dr, nr);
                 const R t = (R)((x - (double)j * dr) / dr);
                 const R* F0 = W.agF + ((size_t)b * (nr + 1) + j) * 4;
@@ -606,21 +677,23 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
             R pb = W.psib[p];
             R fr = u / pb;
             R fu = W.gam[p] * W.dpr[p] / pb - (W.cA[p] + W.bb[p]);
-            R rn, un;
+            R rn = r, rlo = W.rho_lo[p], un;
             if (has_prev) {
-                rn = r + dxi * ((R)1.5 * fr - (R)0.5 * frho[p]);
+                radius_add(rn, rlo, dxi * ((R)1.5 * fr - (R)0.5 * frho[p]));
                 un = u + dxi * ((R)1.5 * fu - (R)0.5 * fur[p]);
             } else {
-                rn = r + dxi * fr;
+                radius_add(rn, rlo, dxi * fr);
                 un = u + dxi * fu;
             }
             if (rn < (R)0) {
                 rn = -rn;
+                rlo = -rlo;
                 un = -un;
                 fr = -fr;
                 fu = -fu;
             }
             rho[p] = rn;
+            W.rho_lo[p] = rlo;
             ur[p] = un;
             frho[p] = fr;
             fur[p] = fu;

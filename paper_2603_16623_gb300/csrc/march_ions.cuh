@@ -36,40 +36,6 @@
 
 namespace gbwake {
 
-// ln rho of ring `id` at radius (r, r_lo) in the accumulator type
-__device__ __forceinline__ double ring_log(const float4*, int, double r, double) { return log(r); }
-__device__ __forceinline__ ff ring_log(const float4* ctab, int id, float r, float r_lo) {
-    const float4 c = ctab[3 * id];  // {rho0 (hi, lo), ln rho0 (hi, lo)}
-    const ff r0 = {c.x, c.y};
-    const float dl = ff_to_f(ff_acc(ff{r, r_lo}, ff_neg(r0)));
-    return ff_add_f(ff{c.z, c.w}, log1pf(dl / c.x));
-}
-// ln X of an arbitrary radius X (accumulator type), relative to the plasma
-// edge whose logarithm ln_e is known to the accumulator's precision
-__device__ __forceinline__ double acc_log(double X, double, double, double) { return log(X); }
-__device__ __forceinline__ ff acc_log(ff X, ff Xe, ff ln_e, float edge) {
-    return ff_add_f(ln_e, log1pf(ff_to_f(ff_acc(X, ff_neg(Xe))) / edge));
-}
-__device__ __forceinline__ double acc_mul_a(double a, double b) { return a * b; }
-__device__ __forceinline__ ff acc_mul_a(ff a, ff b) { return ff_mul(a, b); }
-__device__ __forceinline__ double acc_div(double a, double b) { return a / b; }
-__device__ __forceinline__ ff acc_div(ff a, ff b) {
-    const float q1 = a.hi / b.hi;
-    const ff rem = ff_acc(a, ff_neg(ff_mul_f(b, q1)));
-    return ff_fast_two_sum(q1, rem.hi / b.hi);
-}
-// ring radius at sorted position p in the accumulator type
-__device__ __forceinline__ double ring_radius(const double* hi, const double*, int p) { return hi[p]; }
-__device__ __forceinline__ ff ring_radius(const float* hi, const float* lo, int p) { return ff{hi[p], lo[p]}; }
-
-// rho + d in the state's arithmetic: FP64, or float-float (hi in r, lo in r_lo)
-__device__ __forceinline__ void radius_add(double& r, double&, double d) { r += d; }
-__device__ __forceinline__ void radius_add(float& r, float& r_lo, float d) {
-    const ff s = ff_add_f(ff{r, r_lo}, d);
-    r = s.hi;
-    r_lo = s.lo;
-}
-
 // Where radius X (hi part xh) falls among a species' n rings (hi radii rh,
 // lo parts rl, increasing): case 0 between its rings k-1 and k (k = 0: the
 // axis and ring 0), case 1 between its last ring and the plasma edge Xe,

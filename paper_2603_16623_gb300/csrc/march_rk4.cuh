@@ -25,25 +25,6 @@
 
 namespace gbwake {
 
-// a radius (hi, lo) in the accumulator type
-__device__ __forceinline__ double make_radius(double hi, double) { return hi; }
-__device__ __forceinline__ ff make_radius(float hi, float lo) { return ff{hi, lo}; }
-
-// ring id's weight and self weight in the accumulator type: the mixed path
-// takes them float-float from the per-ring table ({w, what} = ctab[3 id + 1]),
-// since their sum meets the exact ion column and FP32-rounded weights would
-// leave ~1e-7 of the enclosed charge
-__device__ __forceinline__ void ring_weights(const float4*, const double* w, const double* wh, int id, double& wa,
-                                             double& wha) {
-    wa = w[id];
-    wha = wh[id];
-}
-__device__ __forceinline__ void ring_weights(const float4* ctab, const float*, const float*, int id, ff& wa, ff& wha) {
-    const float4 c = ctab[3 * id + 1];
-    wa = ff{c.x, c.y};
-    wha = ff{c.z, c.w};
-}
-
 // the beam source of a stage: w1 x (slice a) + w2 x (slice b, if m2 > 0)
 template <class R>
 struct RkSource {

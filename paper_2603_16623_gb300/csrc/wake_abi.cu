@@ -334,7 +334,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         h->d_rid[b] = D.rid[b];
     }
     WK_TRY(dalloc_t(h, n, &D.rho_lo));
-    if (h->fast_threads > 0 || ((h->n_ion > 0 || h->rk4) && h->prec == WAKE_MIXED)) {
+    if (h->prec == WAKE_MIXED) {  // every mixed march takes its constants from the table
         float4* ct;
         WK_TRY(dalloc_t(h, (size_t)3 * n, &ct));
         D.ctab = ct;
@@ -417,6 +417,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
         if (D.n_species == 0) D.n_species = 1;  // no beam: one empty grid
         D.bidx = h->d_bidx;
         D.qw = h->d_qw;
+        D.rc = h->d_r;
         WK_TRY(dalloc_t(h, (size_t)D.n_species, &h->d_ag_rmax));
         D.ag_rmax = h->d_ag_rmax;
         WK_TRY(dalloc_t(h, (size_t)D.n_species * (h->grid_nr + 1), &D.agB));
@@ -1130,9 +1131,9 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
         return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the one-CTA march (no mobile ions, "
                                  "rings_per_thread and cluster_ctas 0)");
     if (cfg->grid_nr < 0 || cfg->grid_nr > 1024) return fail(WAKE_EINVAL, "wake_init: grid_nr must be in [0, 1024]");
-    if (cfg->grid_nr > 0 && (cfg->precision != WAKE_FP64 || rk4 || ions || n_beams > kMaxGridSpecies))
-        return fail(WAKE_EINVAL, "wake_init: beam grids run WAKE_FP64, WAKE_AB2, without mobile ions, with at most "
-                                 "%d beam species", kMaxGridSpecies);
+    if (cfg->grid_nr > 0 && (rk4 || ions || n_beams > kMaxGridSpecies))
+        return fail(WAKE_EINVAL, "wake_init: beam grids run WAKE_AB2, without mobile ions, with at most %d beam "
+                                 "species", kMaxGridSpecies);
     // the two-species and RK4 marches: one CTA of 512 threads per wake
     if ((ions || rk4) && !cfg->block_threads) threads = 512;
     if (!plasma->r_edges) return fail(WAKE_EINVAL, "wake_init: r_edges is NULL");

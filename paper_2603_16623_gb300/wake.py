@@ -146,7 +146,7 @@ class Wake:
         (electrons, then ions) in every per-ring array.  cell_density: a
         radial density profile, one value per cell (needs ions).  integrator:
         "ab2" or "rk4".  grid_nr > 0: beam fields through adaptive beam
-        grids of grid_nr radial cells per beam (FP64)."""
+        grids of grid_nr radial cells per beam."""
         lib = load()
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32

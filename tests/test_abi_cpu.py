@@ -84,8 +84,8 @@ def test_launch_shape_is_validated_on_the_host(precision, n, k, cl, why):
     ({"integrator": 1, "ion_charge": 1.0, "ion_mass": 100.0}, "RK4 runs electron-only"),
     ({"integrator": 1, "cl": 2}, "RK4 runs electron-only"),
     ({"grid_nr": 2000, "precision": "fp64"}, "grid_nr must be"),
-    ({"grid_nr": 16}, "beam grids run WAKE_FP64"),
-    ({"grid_nr": 16, "precision": "fp64", "integrator": 1}, "beam grids run WAKE_FP64"),
+    ({"grid_nr": 16, "ion_charge": 1.0, "ion_mass": 100.0}, "beam grids run WAKE_AB2"),
+    ({"grid_nr": 16, "precision": "fp64", "integrator": 1}, "beam grids run WAKE_AB2"),
 ])
 def test_model_options_are_validated_on_the_host(case, why):
     """Mobile ions, density profiles, the RK4 integrator and beam grids: bad

@@ -2,7 +2,7 @@
 march.cuh) against the oracle's grid march (orc_run with grid_nr > 0):
 per beam species grid_nr radial cells covering its particles, one node line
 per slice, B^(b) at the rings from the grids, beam-particle fields
-interpolated from the nodes.  FP64, 1e-10 norm-wise.  The node charges are
+interpolated from the nodes.  FP64 1e-10 and mixed 1e-5 norm-wise.  The node charges are
 summed with atomics on the GPU (order-dependent rounding), so batched and
 alone runs agree to rounding, not bitwise."""
 import numpy as np
@@ -87,11 +87,28 @@ def test_grid_wakes_batched_match_alone():
         g.close()
 
 
+def test_mixed_grid_wake_within_tolerance():
+    """The mixed one-CTA march (float-float radii and weights, ln rho from
+    the table) with grids, against the oracle at the mixed path's 1e-5; the
+    grids decide node membership from the caller's FP64 radii."""
+    from paper_2603_16623_gb300 import wake as wm
+    wk = grid_wake(32, n=400, steps=500, seed=97, two_beams=True)
+    ref = oracle.run_wake(wk, ring_dumps=("r",))
+    g = wm.Wake.from_workload(wk, precision="mixed", flags=wm.WAKE_DUMP_RING_R)
+    st, _, _, rr = g.run(ring_r=True)
+    assert st == ref.status == 0
+    assert nerr(rr, ref.rings["r"]) < 1e-5
+    f = g.beam_fields(("ez", "wr", "bt"))
+    for k in ("ez", "wr", "bt"):
+        assert nerr(f[k], ref.beam[k]) < 1e-5, k
+    g.close()
+
+
 def test_grid_rejects_bad_use():
     from paper_2603_16623_gb300 import wake as wm
     wk = grid_wake(8, n=50, steps=20)
     with pytest.raises(wm.WakeError):
-        wm.Wake.from_workload(wk, precision="mixed")
+        wm.Wake.from_workload(wk, precision="mixed", ions=(1.0, 100.0))
     with pytest.raises(wm.WakeError):
         wm.Wake.from_workload(wk, precision="fp64", grid_nr=2000)
     with pytest.raises(wm.WakeError):
