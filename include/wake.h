@@ -194,6 +194,9 @@ wake_status wake_step_slices(wake_handle *h, int32_t n_slices);
    solve) at n arbitrary radii r (Eqs. b_theta_plasma..dpsi_dzeta sampled off
    the rings): ez = E_z = -d_zeta psi, wr = E_r - B_theta = -d_rho psi,
    bt = B_theta^(p) + B_theta^(b), psi.  The ring state is not advanced.
+   The fields are the gridless sums at r also for wakes with beam grids
+   (the plasma answering the grids' B^(b), the beam's own B^(b) at r from
+   its particles); with mobile ions, the sums of both species.
    r and the outputs are host arrays (device_ptrs = 0) or device arrays
    (device_ptrs = 1); outputs are "real"; any output may be NULL.
    Errors: EINVAL (n < 0, window finished), ECUDA. */
