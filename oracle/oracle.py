@@ -27,7 +27,8 @@ class _Problem(C.Structure):
     _fields_ = [("n_rings", C.c_int32), ("edges", _dp), ("density", C.c_double),
                 ("n_beam", C.c_int64), ("beam_xi", _dp), ("beam_r", _dp), ("beam_qw", _dp),
                 ("dxi", C.c_double), ("n_steps", C.c_int32), ("cell_density", _dp), ("integrator", C.c_int32),
-                ("grid_nr", C.c_int32), ("beam_species", _ip), ("n_species", C.c_int32)]
+                ("grid_nr", C.c_int32), ("beam_species", _ip), ("n_species", C.c_int32),
+                ("grid_rmax", C.c_double)]
 
 
 _RING_DUMPS = ["ring_r", "ring_ur", "ring_psi", "ring_dpsidr", "ring_dpsidz", "ring_bp",
@@ -187,7 +188,8 @@ class OracleResult:
 def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: float = 1.0,
         max_slices: int = 0, beam_fields: Sequence[str] = ("ez", "wr", "bt", "psi"),
         ring_dumps: Sequence[str] = (), ions: Optional[Tuple[float, float]] = None,
-        cell_density=None, integrator: str = "ab2", grid_nr: int = 0, beam_species=None) -> OracleResult:
+        cell_density=None, integrator: str = "ab2", grid_nr: int = 0, beam_species=None,
+        grid_rmax: float = 0.0) -> OracleResult:
     """March the whole window (or its first max_slices slices).
 
     beam_fields: subset of ez, wr, bt, psi (per particle, caller order).
@@ -200,7 +202,8 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     cell (a radial profile), with ions only.  integrator: "ab2" or "rk4"
     (electron-only march).  grid_nr > 0: beam fields through adaptive beam
     grids of grid_nr radial cells per species (beam_species: each
-    particle's species index; None: one species)."""
+    particle's species index; None: one species); grid_rmax > 0: grids of
+    that fixed extent (the regular intermediate grid)."""
     edges = _f64(edges)
     bxi, br, bqw = _f64(beam_xi), _f64(beam_r), _f64(beam_qw)
     n_e = edges.shape[0] - 1
@@ -211,7 +214,7 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     n_sp = 1 if sp is None or sp.shape[0] == 0 else int(sp.max()) + 1
     prob = _Problem(n_e, _ptr(edges), density, nb, _ptr(bxi), _ptr(br), _ptr(bqw), dxi, n_steps, _ptr(cd),
                     {"ab2": 0, "rk4": 1}[integrator], int(grid_nr),
-                    None if sp is None else sp.ctypes.data_as(_ip), n_sp)
+                    None if sp is None else sp.ctypes.data_as(_ip), n_sp, float(grid_rmax))
     out = _Outputs()
     beam = {}
     for k in beam_fields:
@@ -247,6 +250,7 @@ def run_wake(wake, **kw) -> OracleResult:
     kw.setdefault("cell_density", getattr(wake, "cell_density", None))
     kw.setdefault("integrator", getattr(wake, "integrator", "ab2"))
     kw.setdefault("grid_nr", getattr(wake, "grid_nr", 0))
+    kw.setdefault("grid_rmax", getattr(wake, "grid_rmax", 0.0))
     if wake.beams:
         kw.setdefault("beam_species", np.concatenate([np.full(b.n, i, dtype=np.int32)
                                                       for i, b in enumerate(wake.beams)]))

@@ -735,8 +735,17 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
                 int32_t b = p->beam_species ? p->beam_species[k] : 0;
                 if (p->beam_r[k] > agR[b]) agR[b] = p->beam_r[k];
             }
-            for (int32_t b = 0; b < nsp; ++b)
-                agR[b] = (agR[b] > 1e-12 ? agR[b] : 1e-12) * (1.0 + 1.0 / nr);
+            for (int32_t b = 0; b < nsp; ++b) {
+                if (p->grid_rmax > 0.0) {
+                    /* the regular intermediate grid: a fixed extent that every
+                       particle must lie below */
+                    if (!(agR[b] < p->grid_rmax))
+                        rc = ORC_EINVAL;
+                    agR[b] = p->grid_rmax;
+                } else {
+                    agR[b] = (agR[b] > 1e-12 ? agR[b] : 1e-12) * (1.0 + 1.0 / nr);
+                }
+            }
             ag.R = agR;
             ag.B = agB;
         }

@@ -52,6 +52,10 @@ typedef struct {
     int32_t grid_nr;
     const int32_t *beam_species;
     int32_t n_species;
+    /* grid_rmax > 0: every species' grid spans [0, grid_rmax] (the regular
+       intermediate grid); every beam particle must lie below it (else
+       ORC_EINVAL).  0: the adaptive extent. */
+    double grid_rmax;
 } orc_problem;
 
 typedef struct {

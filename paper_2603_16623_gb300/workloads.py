@@ -62,6 +62,9 @@ class Wake:
     # beam-plasma coupling: 0 = gridless (fields at each beam particle);
     # > 0 = adaptive beam grids of this many radial cells per beam (Sec. IV)
     grid_nr: int = 0
+    # > 0: the grids' fixed extent (a regular intermediate grid over [0,
+    # grid_rmax] that every beam particle lies in); 0: adaptive
+    grid_rmax: float = 0.0
 
     @property
     def n_rings(self) -> int:

@@ -9,6 +9,7 @@ two rings d_rho psi runs a sawtooth of amplitude ~n d_rho / 2 (the rings'
 discreteness), which the grid averages out, so W_r is not compared; E_z is
 smooth and converges at second order in the grid spacing."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2603_16623_gb300 import workloads as W
@@ -59,3 +60,35 @@ def test_a_beam_split_into_two_identical_species_gives_the_same_fields():
         den = np.max(np.abs(one.beam[k]))
         assert np.max(np.abs(f2[:n] - one.beam[k])) < 1e-12 * den, k
     assert np.max(np.abs(two.rings["r"] - one.rings["r"])) < 1e-12
+
+
+def test_regular_grid_of_the_adaptive_extent_equals_the_adaptive_grid():
+    """A fixed extent equal to the adaptive one (one species) gives the same
+    wake bitwise: the extent is the only difference between the two."""
+    drv = W.gaussian_beam(8_000, 1.0, 0.3, 0.5, 1.5, seed=13)
+    e = W.edges_uniform(300, 5.0)
+    ada = oracle.run_wake(W.Wake("a", e, [drv], 0.01, 300, grid_nr=20), ring_dumps=("r",))
+    R = float(np.max(drv.r) * (1 + 1 / 20))
+    reg = oracle.run_wake(W.Wake("r", e, [drv], 0.01, 300, grid_nr=20, grid_rmax=R), ring_dumps=("r",))
+    assert np.array_equal(ada.rings["r"], reg.rings["r"]) and np.array_equal(ada.beam["ez"], reg.beam["ez"])
+
+
+def test_regular_grid_ez_converges_at_second_order():
+    """The regular intermediate grid over [0, 3] (the beam within it)."""
+    ref = oracle.run_wake(_linear_case(0), beam_fields=("ez",))
+    errs = []
+    for nr in (8, 16, 32):
+        wk = _linear_case(nr)
+        g = oracle.run_wake(W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, wk.n_steps, grid_nr=nr, grid_rmax=3.0),
+                            beam_fields=("ez",))
+        assert g.status == 0
+        errs.append(np.max(np.abs(g.beam["ez"] - ref.beam["ez"])) / np.max(np.abs(ref.beam["ez"])))
+    q = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(3.5 < x < 4.5 for x in q), (errs, q)
+
+
+def test_regular_grid_refuses_a_beam_beyond_it():
+    drv = W.gaussian_beam(2_000, 1.0, 0.5, 0.5, 0.6, seed=14)
+    wk = W.Wake("out", W.edges_uniform(100, 5.0), [drv], 0.01, 100, grid_nr=8, grid_rmax=0.5)
+    with pytest.raises(RuntimeError):
+        oracle.run_wake(wk)
