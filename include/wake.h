@@ -142,6 +142,13 @@ typedef struct {
                                  beyond), beam-particle fields interpolated
                                  from the nodes.  WAKE_AB2, no mobile ions,
                                  at most 8 beam species; both precisions. */
+    double grid_rmax;         /* with grid_nr > 0: 0 = adaptive extents; > 0 =
+                                 every grid spans [0, grid_rmax] (the regular
+                                 intermediate grid).  Every beam particle must
+                                 lie below it: EINVAL at wake_init and
+                                 wake_reset with new beams; a push that moves
+                                 one beyond makes the next preparation stop
+                                 the wake with status EINVAL. */
 } wake_config;
 
 typedef struct wake_handle wake_handle;

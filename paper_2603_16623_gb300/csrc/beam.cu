@@ -306,4 +306,19 @@ cudaError_t launch_species_rmax(const double* r, SpeciesRanges sp, double* rmax,
     return cudaGetLastError();
 }
 
+__global__ void grid_extent_check_kernel(const double* rmax, int32_t n_species, double grid_rmax, int32_t* ctl) {
+    for (int b = 0; b < n_species; ++b)
+        if (!(rmax[b] < grid_rmax)) {
+            ctl[1] = 1;   // status EINVAL
+            ctl[2] = -1;  // no slice ran
+            return;
+        }
+}
+
+cudaError_t launch_grid_extent_check(const double* rmax, int32_t n_species, double grid_rmax, int32_t* ctl,
+                                     cudaStream_t st) {
+    grid_extent_check_kernel<<<1, 1, 0, st>>>(rmax, n_species, grid_rmax, ctl);
+    return cudaGetLastError();
+}
+
 }  // namespace gbwake

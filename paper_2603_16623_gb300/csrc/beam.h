@@ -32,4 +32,8 @@ struct SpeciesRanges {
     int64_t begin[9];
 };
 cudaError_t launch_species_rmax(const double* r, SpeciesRanges sp, double* rmax, cudaStream_t st);
+// a fixed grid extent that some species' largest radius reaches: the wake
+// stops (ctl status EINVAL, failing slice -1)
+cudaError_t launch_grid_extent_check(const double* rmax, int32_t n_species, double grid_rmax, int32_t* ctl,
+                                     cudaStream_t st);
 }  // namespace gbwake

@@ -84,6 +84,7 @@ struct WakeDev {
     // caller's charge x weight; agB: B^(b) at the nodes [species][nr + 1];
     // agF: the node fields [species][nr + 1][psi, d_rho psi, d_zeta psi, B]
     int32_t grid_nr, n_species;
+    double grid_rmax;  // > 0: every grid's fixed extent
     int64_t sp_begin[kMaxGridSpecies + 1];
     const int32_t* bidx;
     const double* qw;
@@ -130,6 +131,7 @@ __device__ __forceinline__ int ag_species(const WakeDev<P>& W, int64_t k) {
 // 1e-12, for a beam on the axis)
 template <class P>
 __device__ __forceinline__ double ag_extent(const WakeDev<P>& W, int b) {
+    if (W.grid_rmax > 0.0) return W.grid_rmax;  // the regular intermediate grid
     return fmax(W.ag_rmax[b], 1e-12) * (1.0 + 1.0 / W.grid_nr);
 }
 // B^(b) of species b at rho from its grid: linear between nodes inside,

@@ -66,6 +66,7 @@ struct wake_handle {
     int32_t n_ion = 0;                      // > 0: mobile ions, rings per species (n = 2 n_ion)
     int32_t rk4 = 0;                        // the RK4 integrator (march_rk4.cuh)
     int32_t grid_nr = 0;                    // > 0: adaptive beam grids (march.cuh)
+    double grid_rmax = 0;                   // > 0: the grids' fixed extent
     double* d_ag_rmax = nullptr;            // largest radius per beam species (grids)
     double ion_qm = 0;                      // their Z / M
     double dxi = 0, density = 1, rho_max = 0;
@@ -186,9 +187,16 @@ int32_t densest_slice(const wake_beam_desc* beams, int32_t n_beams, double dxi, 
     return mx;
 }
 
-// New beam arrays for wake_reset: same species count and sizes as at init.
+// New beam arrays for wake_reset: same species count and sizes as at init,
+// inside a fixed grid extent.
 wake_status check_new_beams(const wake_handle* h, const wake_beam_desc* beams, int32_t n_beams) {
     if (!beams) return WAKE_OK;
+    if (h->grid_rmax > 0.0)
+        for (int32_t b = 0; b < n_beams; ++b)
+            for (int64_t k = 0; k < beams[b].n && beams[b].r; ++k)
+                if (!(beams[b].r[k] < h->grid_rmax))
+                    return fail(WAKE_EINVAL, "wake_reset: beam %d particle %lld lies beyond grid_rmax", b,
+                                (long long)k);
     if (n_beams != (int32_t)h->beam_n.size())
         return fail(WAKE_EINVAL, "wake_reset: %d species given, %zu at init", n_beams, h->beam_n.size());
     for (int32_t b = 0; b < n_beams; ++b) {
@@ -255,6 +263,7 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
             for (int32_t b = 0; b < sp.n; ++b) sp.begin[b + 1] = sp.begin[b] + h->beam_n[b];
             WK_CUDA(cudaMemsetAsync(h->d_ag_rmax, 0, (size_t)sp.n * sizeof(double), st));
             WK_CUDA(launch_species_rmax(h->d_r, sp, h->d_ag_rmax, st));
+            if (h->grid_rmax > 0.0) WK_CUDA(launch_grid_extent_check(h->d_ag_rmax, sp.n, h->grid_rmax, h->d_ctl, st));
         }
         WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, st));
     }
@@ -407,6 +416,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     }
     if (h->grid_nr > 0) {
         D.grid_nr = h->grid_nr;
+        D.grid_rmax = h->grid_rmax;
         D.n_species = (int32_t)h->beam_n.size();
         int64_t off = 0;
         for (int32_t b = 0; b < D.n_species; ++b) {
@@ -1131,6 +1141,14 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
         return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the one-CTA march (no mobile ions, "
                                  "rings_per_thread and cluster_ctas 0)");
     if (cfg->grid_nr < 0 || cfg->grid_nr > 1024) return fail(WAKE_EINVAL, "wake_init: grid_nr must be in [0, 1024]");
+    if (!(cfg->grid_rmax >= 0.0) || !std::isfinite(cfg->grid_rmax) || (cfg->grid_rmax > 0.0 && cfg->grid_nr == 0))
+        return fail(WAKE_EINVAL, "wake_init: grid_rmax must be finite, >= 0, and set only with grid_nr > 0");
+    if (cfg->grid_rmax > 0.0)
+        for (int32_t b = 0; b < n_beams; ++b)
+            for (int64_t k = 0; k < beams[b].n; ++k)
+                if (!(beams[b].r[k] < cfg->grid_rmax))
+                    return fail(WAKE_EINVAL, "wake_init: beam %d particle %lld lies beyond grid_rmax", b,
+                                (long long)k);
     if (cfg->grid_nr > 0 && (rk4 || ions || n_beams > kMaxGridSpecies))
         return fail(WAKE_EINVAL, "wake_init: beam grids run WAKE_AB2, without mobile ions, with at most %d beam "
                                  "species", kMaxGridSpecies);
@@ -1168,6 +1186,7 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->ion_qm = ions && std::isfinite(plasma->ion_mass) ? plasma->ion_charge / plasma->ion_mass : 0.0;
     h->rk4 = rk4 ? 1 : 0;
     h->grid_nr = cfg->grid_nr;
+    h->grid_rmax = cfg->grid_rmax;
     h->n_steps = cfg->n_steps;
     h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;

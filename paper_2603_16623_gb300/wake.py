@@ -49,7 +49,8 @@ class wake_beam_desc(C.Structure):
 class wake_config(C.Structure):
     _fields_ = [("dxi", C.c_double), ("n_steps", C.c_int32), ("precision", C.c_int32),
                 ("flags", C.c_int32), ("block_threads", C.c_int32), ("rings_per_thread", C.c_int32),
-                ("cluster_ctas", C.c_int32), ("integrator", C.c_int32), ("grid_nr", C.c_int32)]
+                ("cluster_ctas", C.c_int32), ("integrator", C.c_int32), ("grid_nr", C.c_int32),
+                ("grid_rmax", C.c_double)]
 
 
 _vp = C.c_void_p
@@ -140,13 +141,15 @@ class Wake:
     def __init__(self, edges, beams: Sequence = (), dxi: float = 0.01, n_steps: int = 1000,
                  precision: str = "mixed", density: float = 1.0, flags: int = 0,
                  block_threads: int = 0, stream=None, rings_per_thread: int = 0, cluster_ctas: int = 0,
-                 ions=None, cell_density=None, integrator: str = "ab2", grid_nr: int = 0):
+                 ions=None, cell_density=None, integrator: str = "ab2", grid_nr: int = 0,
+                 grid_rmax: float = 0.0):
         """ions: None (immobile ion column) or (Z, M) for mobile ions (M =
         inf: ion rings that never move); the wake then has 2 x cells rings
         (electrons, then ions) in every per-ring array.  cell_density: a
         radial density profile, one value per cell (needs ions).  integrator:
         "ab2" or "rk4".  grid_nr > 0: beam fields through adaptive beam
-        grids of grid_nr radial cells per beam."""
+        grids of grid_nr radial cells per beam; grid_rmax > 0 fixes their
+        extent (the regular intermediate grid)."""
         lib = load()
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32
@@ -162,7 +165,8 @@ class Wake:
         self._keep += keep
         self.n_beam = int(sum(d.n for d in descs[:len(beams)]))
         cfg = wake_config(float(dxi), self.n_steps, PRECISION[precision], int(flags), int(block_threads),
-                          int(rings_per_thread), int(cluster_ctas), {"ab2": 0, "rk4": 1}[integrator], int(grid_nr))
+                          int(rings_per_thread), int(cluster_ctas), {"ab2": 0, "rk4": 1}[integrator], int(grid_nr),
+                          float(grid_rmax))
         z, m = (0.0, 0.0) if ions is None else (float(ions[0]), float(ions[1]))
         prof = None if cell_density is None else _f64(cell_density)
         self._keep.append(prof)
@@ -182,6 +186,7 @@ class Wake:
         kw.setdefault("cell_density", getattr(wake, "cell_density", None))
         kw.setdefault("integrator", getattr(wake, "integrator", "ab2"))
         kw.setdefault("grid_nr", getattr(wake, "grid_nr", 0))
+        kw.setdefault("grid_rmax", getattr(wake, "grid_rmax", 0.0))
         return cls(wake.edges, wake.beams, wake.dxi, wake.n_steps, density=wake.density, **kw)
 
     def close(self):

@@ -86,6 +86,8 @@ def test_launch_shape_is_validated_on_the_host(precision, n, k, cl, why):
     ({"grid_nr": 2000, "precision": "fp64"}, "grid_nr must be"),
     ({"grid_nr": 16, "ion_charge": 1.0, "ion_mass": 100.0}, "beam grids run WAKE_AB2"),
     ({"grid_nr": 16, "precision": "fp64", "integrator": 1}, "beam grids run WAKE_AB2"),
+    ({"grid_rmax": 2.0}, "grid_rmax must be"),
+    ({"grid_nr": 16, "grid_rmax": -1.0}, "grid_rmax must be"),
 ])
 def test_model_options_are_validated_on_the_host(case, why):
     """Mobile ions, density profiles, the RK4 integrator and beam grids: bad
@@ -99,7 +101,8 @@ def test_model_options_are_validated_on_the_host(case, why):
         prof = np.full(n, 1.0)
         prof[7] = case["profile"]
     cfg = wm.wake_config(0.01, 10, wm.PRECISION[case.get("precision", "mixed")], 0, 0, case.get("k", 0),
-                         case.get("cl", 0), case.get("integrator", 0), case.get("grid_nr", 0))
+                         case.get("cl", 0), case.get("integrator", 0), case.get("grid_nr", 0),
+                         case.get("grid_rmax", 0.0))
     dp = ctypes.POINTER(ctypes.c_double)
     plasma = wm.wake_plasma_desc(n, edges.ctypes.data_as(dp), 1.0, case.get("ion_charge", 0.0),
                                  case.get("ion_mass", 0.0), prof.ctypes.data_as(dp) if prof is not None else None)
@@ -108,3 +111,19 @@ def test_model_options_are_validated_on_the_host(case, why):
     assert st == wm.WAKE_EINVAL
     assert not h.value
     assert why in lib.wake_last_error().decode()
+
+
+def test_a_beam_beyond_a_fixed_grid_is_refused_on_the_host():
+    from paper_2603_16623_gb300 import wake as wm
+    lib = wm.load()
+    n = 50
+    edges = np.linspace(0.0, 5.0, n + 1)
+    xi, r, w = np.array([0.1, 0.2]), np.array([0.3, 2.5]), np.array([1e-3, 1e-3])
+    dp = ctypes.POINTER(ctypes.c_double)
+    beam = wm.wake_beam_desc(2, xi.ctypes.data_as(dp), r.ctypes.data_as(dp), w.ctypes.data_as(dp), -1.0)
+    cfg = wm.wake_config(0.01, 10, wm.PRECISION["fp64"], 0, 0, 0, 0, 0, 8, 2.0)
+    plasma = wm.wake_plasma_desc(n, edges.ctypes.data_as(dp), 1.0)
+    h = ctypes.c_void_p()
+    st = lib.wake_init(ctypes.byref(cfg), ctypes.byref(plasma), ctypes.byref(beam), 1, None, ctypes.byref(h))
+    assert st == wm.WAKE_EINVAL and not h.value
+    assert "beyond grid_rmax" in lib.wake_last_error().decode()

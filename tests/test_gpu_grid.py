@@ -113,3 +113,41 @@ def test_grid_rejects_bad_use():
         wm.Wake.from_workload(wk, precision="fp64", grid_nr=2000)
     with pytest.raises(wm.WakeError):
         wm.Wake.from_workload(wk, precision="fp64", integrator="rk4")
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", 1e-5)])
+def test_regular_intermediate_grid_matches_oracle(precision, tol):
+    """A fixed grid extent of 2.5 for both beams (the regular grid)."""
+    from paper_2603_16623_gb300 import wake as wm
+    wk = grid_wake(48, n=300, steps=400, seed=98, two_beams=True)
+    wk = W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, wk.n_steps, grid_nr=48, grid_rmax=2.5)
+    ref = oracle.run_wake(wk, ring_dumps=("r",))
+    assert ref.status == 0
+    g = wm.Wake.from_workload(wk, precision=precision, flags=wm.WAKE_DUMP_RING_R)
+    st, _, _, rr = g.run(ring_r=True)
+    assert st == 0
+    assert nerr(rr, ref.rings["r"]) < tol
+    f = g.beam_fields(("ez", "wr", "bt"))
+    for k in ("ez", "wr", "bt"):
+        assert nerr(f[k], ref.beam[k]) < tol, k
+    g.close()
+
+
+def test_a_particle_moved_beyond_a_fixed_grid_stops_the_wake():
+    """Moving a particle beyond the fixed extent (here by giving it a phase
+    space there) stops the next solve with status EINVAL before any slice."""
+    from paper_2603_16623_gb300 import wake as wm
+    wk = grid_wake(16, n=100, steps=50, seed=99)
+    wk = W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, wk.n_steps, grid_nr=16, grid_rmax=3.0)
+    g = wm.Wake.from_workload(wk, precision="fp64")
+    st, _, _, _ = g.run()
+    assert st == 0
+    b = wk.beams[0]
+    x = b.r.copy()
+    x[5] = 3.5
+    g.set_beam_phase_space(x, np.zeros(b.n), np.zeros(b.n), np.zeros(b.n), np.full(b.n, 100.0))
+    g.reset()
+    g.step_slices(10)
+    nxt, status, fail = g.progress()
+    assert status == wm.WAKE_EINVAL and nxt == 0
+    g.close()
