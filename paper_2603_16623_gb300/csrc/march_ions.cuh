@@ -107,6 +107,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
     using A = typename P::A;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
+    __shared__ int s_stop;
 
     const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
     const int T = blockDim.x;
@@ -141,7 +142,15 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
     const R inv_2pi_dxi = (R)(1.0 / (6.283185307179586476925286766559 * W.dxi));
     const A zeroA = acc_zero(A());
 
+    const int slice0 = slice;
+    uint64_t t_start = 0;
     for (; slice < s_end; ++slice) {
+        // time budget (thread 0 decides, read after the order check's barrier)
+        if (W.budget_ns > 0 && tid == 0) {
+            const uint64_t now = global_ns();
+            if (slice == slice0) t_start = now;
+            s_stop = slice > slice0 && now - t_start >= (uint64_t)W.budget_ns;
+        }
         // ---------------- a2: sort each segment by radius (stable)
         {
             R* rho = W.rho[buf];
@@ -149,7 +158,9 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             for (int s = 0; s < 2; ++s)
                 for (int q = q0; q < q1; ++q)
                     if (q + 1 < N && rho[s * N + q + 1] < rho[s * N + q]) ok = false;
-            if (!__syncthreads_and(ok)) {
+            const bool in_order = __syncthreads_and(ok);
+            if (W.budget_ns > 0 && s_stop) break;
+            if (!in_order) {
                 const int nb = buf ^ 1;
                 for (int s = 0; s < 2; ++s) {
                     const int base = s * N;

@@ -208,6 +208,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
     using A = typename P::A;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
+    __shared__ int s_stop;
 
     const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
     const int T = blockDim.x;
@@ -233,14 +234,24 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
     const R dxi = (R)W.dxi;
     const R inv_2pi_dxi = (R)(1.0 / (6.283185307179586476925286766559 * W.dxi));
 
+    const int slice0 = slice;
+    uint64_t t_start = 0;
     for (; slice < s_end; ++slice) {
+        // time budget (thread 0 decides, read after the order check's barrier)
+        if (W.budget_ns > 0 && tid == 0) {
+            const uint64_t now = global_ns();
+            if (slice == slice0) t_start = now;
+            s_stop = slice > slice0 && now - t_start >= (uint64_t)W.budget_ns;
+        }
         // ---------------- a2: sort the state by radius (stable)
         {
             R* rho = W.rho[buf];
             bool ok = true;
             for (int p = p0; p < p1; ++p)
                 if (p + 1 < n && rho[p + 1] < rho[p]) ok = false;
-            if (!__syncthreads_and(ok)) {
+            const bool in_order = __syncthreads_and(ok);
+            if (W.budget_ns > 0 && s_stop) break;
+            if (!in_order) {
                 for (int i = tid; i < W.n_pad; i += T) {
                     keys[i] = i < n ? rho[i] : (R)INFINITY;
                     vals[i] = i;

@@ -130,3 +130,34 @@ def test_pipelined_reset_run_equals_reset_then_run():
             assert np.array_equal(ga.ring_state()[0], gb.ring_state()[0])
     for g in a + b:
         g.close()
+
+
+def test_time_budget_on_the_one_cta_marches():
+    """The budgeted batch step also stops the two-species, RK4 and grid
+    marches at a slice boundary; run on to the end, they give what they give
+    alone (bitwise; the grid's node charges are summed with atomics: to
+    float rounding)."""
+    from paper_2603_16623_gb300 import wake as wm
+    drv = W.gaussian_beam(9_000, 1.0, 0.3, 0.5, 1.6, seed=741)
+    wakes = [W.Wake("ions", W.edges_uniform(600, 5.0), [drv], 0.01, 400, ions=(1.0, 100.0)),
+             W.Wake("rk4", W.edges_uniform(600, 5.0), [drv], 0.01, 400, integrator="rk4"),
+             W.Wake("grid", W.edges_uniform(600, 5.0), [drv], 0.01, 400, grid_nr=32)]
+    alone = []
+    for wk in wakes:
+        g = wm.Wake.from_workload(wk, precision="mixed")
+        g.run()
+        alone.append((g.ring_state()[0], g.beam_fields(("ez",))["ez"]))
+        g.close()
+    gs = [wm.Wake.from_workload(wk, precision="mixed") for wk in wakes]
+    wm.wake_batch_step(gs, 1 << 30, 50_000)
+    nxt, st = wm.wake_batch_progress(gs)
+    assert not st.any()
+    assert all(0 < k < wk.n_steps for k, wk in zip(nxt, wakes)), list(nxt)
+    wm.wake_batch_step(gs, 1 << 30)
+    for g, wk, (r, ez) in zip(gs, wakes, alone):
+        assert g.progress()[:2] == (wk.n_steps, 0)
+        if wk.name == "grid":
+            assert np.max(np.abs(g.beam_fields(("ez",))["ez"] - ez)) <= 1e-5 * np.max(np.abs(ez))
+        else:
+            assert np.array_equal(g.ring_state()[0], r) and np.array_equal(g.beam_fields(("ez",))["ez"], ez)
+        g.close()
