@@ -170,10 +170,13 @@ def run_ours(args):
     # work actually done per step (wakes may stop at a model breakdown)
     ring_slices = 0
     stopped = 0
+    nexts = []
     for g, wk in zip(gs, wakes):
         nxt, st, fl = g.progress()
         ring_slices += wk.n_rings * nxt
         stopped += int(st != 0)
+        nexts.append(nxt)
+    evals = beam_evaluations(wakes, nexts)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{os.getpid()}.csv")
@@ -205,6 +208,10 @@ def run_ours(args):
         tot_ms_max = tot_ms
         rs_all = float(ring_slices)
     value = rs_all * args.steps / (tot_ms_max / 1e3)
+    if ws > 1:
+        _, evals_all = _reduce_max_sum(tot_ms, evals, "cuda")
+    else:
+        evals_all = float(evals)
 
     # pinned host copies of the beams (end-to-end and serving runs)
     pinned = []
@@ -294,10 +301,17 @@ def run_ours(args):
         for h in hs:
             h.close()
 
+    # ---- the single-wake workloads (linear, blowout, large) alone on the GPU
+    singles = None
+    if not args.skip_singles and rank == 0:
+        singles = single_wakes_bench(args, stream)
+
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
     if not args.skip_cpu and rank == 0 and ws == 1:
         cpu = cpu_sample(args.cpu_seconds)
+        # and single-threaded on the single-wake workloads
+        cpu["single_wakes"] = oracle_single_wakes(args.large_oracle_slices)
         # and on every host core (independent wakes in spawned processes)
         pool = OraclePool(_host_cores())
         cpu["all_cores"] = pool.sample(args.cpu_seconds / 2)
@@ -324,12 +338,16 @@ def run_ours(args):
                        "launches": sorted({g.launch_config() for g in gs}),
                        "ring_slices_per_step": ring_slices, "wakes_stopped_by_breakdown": stopped,
                        "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
+            "beam_evaluations": {"value": evals_all * args.steps / (tot_ms_max / 1e3),
+                                 "unit": "beam-particle field evaluations/s", "per_step": evals_all,
+                                 "note": "step a9: each beam particle binned into a slice its wake marched"},
             "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + n_march_launches),
             "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "serving": serving,
             "beam_push": push,
             "mobile_ions": _ions_roofline(ions, peak_tflops, sm_mhz),
             "rk4": _alu_roofline(rk4, peak_tflops, sm_mhz, FLOPS_PER_RING_SLICE_RK4, "march_rk4_kernel<PrecMixed>", 1),
             "beam_grid": grid,
+            "single_wakes": singles,
             "clocks": clocks,
             "phases_ms": {"prepare_a0_a1": sum(prep_ms) / len(prep_ms), "march": march_avg_ms,
                           "note": "one untimed step with the two phases in sequence; the timed steps pipeline them"},
@@ -537,6 +555,74 @@ def serve_bench(args, wakes, pinned, stream, rank):
     return out
 
 
+def beam_evaluations(wakes, nexts):
+    """Beam particles whose fields one solve evaluates (step a9): those
+    binned into a slice their wake marched, 0 <= floor(xi / dxi + 1/2) <
+    the wake's next slice."""
+    n = 0
+    for wk, nxt in zip(wakes, nexts):
+        for b in wk.beams:
+            s = np.floor(np.asarray(b.xi) / wk.dxi + 0.5)
+            n += int(np.count_nonzero((s >= 0) & (s < nxt)))
+    return n
+
+
+def _single_workloads(large_slices=None):
+    """The three single-wake workloads: linear (200 rings, 1000 slices),
+    blowout (2000 refined rings, 250k particles, 4000 slices) and large
+    (65,536 log-spaced rings, 4M particles, 8000 slices, or its first
+    large_slices)."""
+    lg = W.large_wake() if large_slices is None else W.large_wake(n_steps=large_slices)
+    return [W.linear_wake(), W.blowout_wake(), lg]
+
+
+def single_wakes_bench(args, stream):
+    """Each single-wake workload alone on the GPU, one wake per launch: the
+    mixed path over the whole window, and the plain FP64 path (at most 8192
+    rings: the large wake has no FP64 line), CUDA-event timed after one
+    untimed solve."""
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    out = {}
+    for wk in _single_workloads():
+        row = {"rings": wk.n_rings, "slices": wk.n_steps, "beam_particles": wk.n_beam}
+        for prec in ("mixed", "fp64"):
+            if wk.n_rings > wm.wake_max_rings(prec):
+                row[prec] = None
+                continue
+            g = wm.Wake.from_workload(wk, precision=prec, stream=stream.cuda_stream)
+            g.step_slices(wk.n_steps)  # warm-up solve
+            torch.cuda.synchronize()
+            g.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step_slices(wk.n_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            nxt, st, _ = g.progress()
+            row[prec] = {"ms": ms, "slices_run": nxt, "status": st, "launch": list(g.launch_config()),
+                         "value": wk.n_rings * nxt / (ms / 1e3), "unit": UNIT}
+            g.close()
+        out[wk.name] = row
+    return out
+
+
+def oracle_single_wakes(large_slices: int):
+    """The FP64 oracle, as it stands, on one host core on each single-wake
+    workload: the whole window of the linear and blowout wakes, the first
+    large_slices slices of the large one (its beam binning included)."""
+    import oracle
+    out = {}
+    for wk in _single_workloads(large_slices):
+        t0 = time.perf_counter()
+        res = oracle.run_wake(wk, beam_fields=())
+        dt = time.perf_counter() - t0
+        out[wk.name] = {"rings": wk.n_rings, "slices_run": res.slices_run, "s": dt, "cores": 1,
+                        "value": wk.n_rings * res.slices_run / dt, "unit": UNIT}
+    return out
+
+
 def cpu_sample(seconds: float):
     """The FP64 oracle, as it stands, on the first slices of the batched
     wakes until about `seconds` of single-core CPU time."""
@@ -689,6 +775,8 @@ def main():
     ap.add_argument("--ion-wakes", type=int, default=152)
     ap.add_argument("--skip-rk4", action="store_true")
     ap.add_argument("--skip-grid", action="store_true")
+    ap.add_argument("--skip-singles", action="store_true")
+    ap.add_argument("--large-oracle-slices", type=int, default=300)
     ap.add_argument("--grid-wakes", type=int, default=64)
     ap.add_argument("--grid-slices", type=int, default=300)
     ap.add_argument("--rk4-wakes", type=int, default=152)

@@ -42,3 +42,20 @@ def test_two_ranks_shard_wakes_and_reduce_max_time():
     assert n0 == ["batched[0]", "batched[1]", "batched[2]"]
     assert t0 == t1 == 15.0
     assert s0 == s1 == 3000.0
+
+
+def test_beam_evaluations_count_the_particles_of_marched_slices():
+    """Step a9 evaluates each beam particle binned into a slice its wake
+    marched: floor(xi / dxi + 1/2) in [0, next slice)."""
+    import numpy as np
+
+    import bench
+    from paper_2603_16623_gb300 import workloads as W
+    xi = np.array([-0.006, -0.004, 0.0, 0.0049, 0.005, 0.0151, 0.02, 0.5])
+    beam = W.Beam(xi, np.full(xi.shape, 0.3), np.full(xi.shape, 1e-3), -1.0)
+    wk = W.Wake("evals", W.edges_uniform(10, 2.0), [beam, beam], 0.01, 3)
+    # slices: -1, 0, 0, 0, 1, 2, 2, 50 (two beams of each)
+    assert bench.beam_evaluations([wk], [0]) == 0
+    assert bench.beam_evaluations([wk], [1]) == 2 * 3
+    assert bench.beam_evaluations([wk], [3]) == 2 * 6
+    assert bench.beam_evaluations([wk, wk], [3, 2]) == 2 * 6 + 2 * 4
