@@ -19,6 +19,7 @@ workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -141,7 +142,25 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
     wakes = _workload(args.n_wakes, rank)
-    gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream, **_shape(wk.n_rings, args))
+    tuning = None
+    if args.autotune:
+        # launch shapes timed on this GPU: on this batch's own step time
+        # (batch), or per size class on synthetic probe wakes (probe)
+        from paper_2603_16623_gb300 import autotune
+        t_tune = time.perf_counter()
+        sizes = [int(v) for v in args.autotune_sizes.split(",")]
+        if args.autotune == "batch":
+            table = autotune.tune_batch(wakes, sizes)
+        else:
+            table = autotune.tune(sizes, "mixed", slices=200, fill=args.autotune_fill)
+        tuning = {"mode": args.autotune, "entries": [dataclasses.asdict(e) for e in table.entries],
+                  "tuning_s": time.perf_counter() - t_tune}
+        if args.autotune == "probe":
+            tuning["fill"] = args.autotune_fill
+        shape = lambda n: table.shape_for(n)  # noqa: E731
+    else:
+        shape = lambda n: _shape(n, args)  # noqa: E731
+    gs = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream, **shape(wk.n_rings))
           for wk in wakes]
     torch.cuda.synchronize()
     # one march launch per distinct (threads, rings per thread, blocks per wake)
@@ -336,6 +355,8 @@ def run_ours(args):
                                    "rings, 1000-6000 slices of 0.01, 50k-500k beam particles",
                        "n_wakes": args.n_wakes, "precision": "mixed",
                        "launches": sorted({g.launch_config() for g in gs}),
+                       "launch_shapes": "autotuned" if tuning else "automatic",
+                       "autotune": tuning,
                        "ring_slices_per_step": ring_slices, "wakes_stopped_by_breakdown": stopped,
                        "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
             "beam_evaluations": {"value": evals_all * args.steps / (tot_ms_max / 1e3),
@@ -411,7 +432,6 @@ def ions_bench(args, wakes, stream):
     """A batch of the workload's wakes of <= 4096 rings with mobile hydrogen
     ions (Z = 1, M = 1836) in place of the ion column: batched reset + march,
     CUDA-event timed; ring-slices count both species."""
-    import dataclasses
     sel = [dataclasses.replace(wk, ions=(1.0, 1836.0)) for wk in wakes if wk.n_rings <= 4096][: args.ion_wakes]
     res = _ions_batch(sel, stream)
     res["ions"] = "Z = 1, M = 1836 (hydrogen), same cells as the electrons"
@@ -427,7 +447,6 @@ def rk4_bench(args, wakes, stream):
     """The batched workload's wakes of <= 8192 rings with the RK4 ring
     integrator (one CTA of 512 threads per wake): batched reset + march,
     CUDA-event timed."""
-    import dataclasses
     sel = [dataclasses.replace(wk, integrator="rk4") for wk in wakes if wk.n_rings <= 8192][: args.rk4_wakes]
     res = _ions_batch(sel, stream, species=1)
     res["integrator"] = "classical RK4 per slice (four field evaluations), electrons over the ion column"
@@ -440,8 +459,6 @@ def grid_bench(args, wakes, stream):
     rings over a bounded window (their first args.grid_slices slices):
     FP64 (both on the one-CTA march) and mixed (grids on the one-CTA march,
     gridless on the on-chip one); batched reset + step, CUDA-event timed."""
-    import dataclasses
-
     import torch
     from paper_2603_16623_gb300 import wake as wm
     sel = [wk for wk in wakes if wk.n_rings <= 8192][: args.grid_wakes]
@@ -789,6 +806,14 @@ def main():
     ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
     ap.add_argument("--uniform-kind", default="ab2", choices=["ab2", "ions", "rk4"])
     ap.add_argument("--rings-per-cta", type=int, default=0, help="cluster wakes: at most this many rings per CTA")
+    ap.add_argument("--autotune", default=None, choices=["batch", "probe"],
+                    help="launch shapes of the batched wakes from a tuning run on this GPU: on the batch's own "
+                         "step time (autotune.tune_batch) or per size class on probe wakes (autotune.tune)")
+    ap.add_argument("--autotune-sizes", default="512,1024,2048,3072,4096,6144,8192",
+                    help="ring counts of the tuned size classes")
+    ap.add_argument("--autotune-fill", type=float, default=2.0,
+                    help="probe tuning: CTAs in flight while a shape is timed, in SMs (2: throughput of a "
+                         "full GPU; small: one wake alone, its latency)")
     args = ap.parse_args()
     if args.uniform:
         run_uniform(args)

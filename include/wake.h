@@ -366,6 +366,22 @@ const char *wake_last_error(void);
 int32_t wake_max_rings(int32_t precision);          /* rings per wake supported */
 int64_t wake_max_slice_particles(int32_t precision); /* beam particles per slice */
 
+/* The launch shape wake_init gives the on-chip march (mixed precision,
+   electrons over the ion column, no beam grids) for a wake of n_rings rings
+   and the config's rings_per_thread and cluster_ctas (both 0: the automatic
+   shape), computed on the host: no device, no handle, nothing allocated.
+   Outputs (each may be NULL): threads per CTA, rings per thread and CTAs
+   per wake (> 1: a thread-block cluster); all three 0 when the wake runs on
+   a one-CTA march instead (FP64, or the automatic shape beyond the on-chip
+   march's 65,536 rings).  The launch-shape autotuner enumerates its
+   candidates with it.  Errors: EINVAL for a precision other than WAKE_FP64
+   or WAKE_MIXED, n_rings outside [1, wake_max_rings(precision)], or the
+   shape wake_init would refuse (rings_per_thread not 0, 4 or 8;
+   cluster_ctas outside [0, 16]; more than 512 threads per CTA; an empty
+   last CTA; either field set with FP64). */
+wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t rings_per_thread, int32_t cluster_ctas,
+                              int32_t *threads, int32_t *rings_per_thread_out, int32_t *blocks_per_wake);
+
 #ifdef __cplusplus
 }
 #endif

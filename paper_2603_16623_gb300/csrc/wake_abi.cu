@@ -1108,6 +1108,19 @@ int64_t wake_max_slice_particles(int32_t precision) {
     return kMaxSliceParticles;
 }
 
+wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t rings_per_thread, int32_t cluster_ctas,
+                              int32_t* threads, int32_t* rings_per_thread_out, int32_t* blocks_per_wake) {
+    if (precision != WAKE_FP64 && precision != WAKE_MIXED) return fail(WAKE_EINVAL, "wake_launch_shape: bad precision");
+    if (n_rings < 1 || n_rings > wake_max_rings(precision))
+        return fail(WAKE_EINVAL, "wake_launch_shape: n_rings must be in [1, %d]", wake_max_rings(precision));
+    FastShape f;
+    WK_TRY(fast_shape_for(precision, n_rings, rings_per_thread, cluster_ctas, &f));
+    if (threads) *threads = f.threads;
+    if (rings_per_thread_out) *rings_per_thread_out = f.threads ? f.k : 0;
+    if (blocks_per_wake) *blocks_per_wake = f.threads ? f.cl : 0;
+    return WAKE_OK;
+}
+
 wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, const wake_beam_desc* beams,
                       int32_t n_beams, void* cuda_stream, wake_handle** out) {
     if (!out) return fail(WAKE_EINVAL, "wake_init: out is NULL");

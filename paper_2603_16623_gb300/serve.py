@@ -97,8 +97,12 @@ class WakeServer:
     """Admits, steps and retires wakes; see the module docstring."""
 
     def __init__(self, memory_budget: int, step_ns: int = 4_000_000, stream=None,
-                 clock: Optional[Callable[[], float]] = None, sm_budget: Optional[float] = None):
+                 clock: Optional[Callable[[], float]] = None, sm_budget: Optional[float] = None,
+                 tuning=None):
         self.budget = int(memory_budget)
+        # launch shapes from an autotune.TuningTable (None: the library's
+        # automatic shapes)
+        self.tuning = tuning
         # Admission also stops once the running wakes fill the SMs
         # (sm_budget SM-equivalents): beyond that every wake would only run
         # slower (they share the SMs), raising everyone's latency for no
@@ -126,8 +130,9 @@ class WakeServer:
             if self.active and self.sm_budget is not None and self.sm_used >= self.sm_budget:
                 break
             self.queue.popleft()
+            shape = self.tuning.shape_for(req.n_rings, "mixed") if self.tuning is not None else {}
             w = wm.Wake(req.edges, req.beams, req.dxi, req.n_steps, precision="mixed",
-                        flags=wm.WAKE_INIT_ASYNC, stream=self.stream)
+                        flags=wm.WAKE_INIT_ASYNC, stream=self.stream, **shape)
             req.admitted = self.clock()
             req.sm_share = sm_share(w.launch_config())
             self.used += est

@@ -82,6 +82,8 @@ _SIGS = {
     "wake_destroy": ([_vp], None),
     "wake_last_error": ([], C.c_char_p),
     "wake_max_rings": ([C.c_int32], C.c_int32),
+    "wake_launch_shape": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                           C.POINTER(C.c_int32)], C.c_int),
     "wake_max_slice_particles": ([C.c_int32], C.c_int64),
 }
 
@@ -413,6 +415,17 @@ def wake_batch_reset_run(wakes: List[Wake]):
 
 def wake_max_rings(precision: str = "mixed") -> int:
     return int(load().wake_max_rings(PRECISION[precision]))
+
+
+def wake_launch_shape(n_rings: int, rings_per_thread: int = 0, cluster_ctas: int = 0, precision: str = "mixed"):
+    """(threads per CTA, rings per thread, CTAs per wake) that wake_init
+    gives the on-chip march for these fields, computed on the host; (0, 0,
+    0) when the wake runs on a one-CTA march.  WakeError for a shape
+    wake_init would refuse."""
+    t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().wake_launch_shape(PRECISION[precision], int(n_rings), int(rings_per_thread), int(cluster_ctas),
+                                    C.byref(t), C.byref(k), C.byref(c)))
+    return t.value, k.value, c.value
 
 
 def wake_max_slice_particles(precision: str = "mixed") -> int:
