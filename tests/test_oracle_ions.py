@@ -7,7 +7,8 @@ from a limit, not from the oracle's own formulas:
 - an unperturbed two-species plasma has no field anywhere and stays put;
 - infinitely heavy ions reproduce the immobile ion column, converging at
   second order in the ring spacing (linear interpolation of the uniform
-  column's linear d_rho psi is exact; its quadratic psi is not);
+  column's linear d_rho psi is exact; its quadratic psi is not), and so do
+  the fields on the beam particles and the B^(p) at the ion rings;
 - the Lorentz force integrated along the ion trajectories gives the
   algebraic u_z of the ions' own cold-plasma constant (q/m = Z/M);
 - the model depends on Z and M only through Z/M (neutrality fixes the ion
@@ -50,6 +51,51 @@ def test_heavy_ions_converge_to_the_immobile_column_at_second_order():
     ratios = [a / b for a, b in zip(errs, errs[1:])]
     assert all(q > 3.5 for q in ratios), (errs, ratios)
     assert errs[-1] < 5e-5
+
+
+@pytest.mark.parametrize("q,r_max", [(-1.0, 5.0), (+1.0, 2.0)])
+def test_heavy_ions_give_the_column_fields_on_beam_particles_and_ion_rings(q, r_max):
+    """With infinitely heavy ions, what the beam particles see (the exact
+    sums of both species) and the B^(p) the ion rings see (the electrons'
+    field interpolated) converge to the immobile column's, the latter taken
+    from the column's own slice solve at the ion radii: psi on the beam at
+    second order in the ring spacing, the rest at first (a particle or an
+    ion ring between rings sees a staircase of enclosed charge and B^(p)
+    jumps across each electron ring).  Errors relative to the column's
+    largest value, over three halvings of the spacing (first order: 8x).
+    A positron driver in a narrow column draws the outermost electrons in,
+    so that the outermost ion rings take B^(p) from beyond the last
+    electron ring."""
+    drv = W.gaussian_beam(20_000, 0.5, 0.4, 0.6, 1.6, seed=3, q=q)
+    dxi, steps = 0.02, 200
+    sl = np.floor(drv.xi / dxi + 0.5)
+    errs = {k: [] for k in ("ion_bp", "ez", "bt", "wr", "psi")}
+    for n in (50, 100, 200, 400):
+        edges = W.edges_uniform(n, r_max)
+        mob = oracle.run_wake(W.Wake("m", edges, [drv], dxi, steps, ions=(1.0, 1e12)), ring_dumps=("r", "bp"),
+                              beam_fields=("ez", "wr", "bt", "psi"))
+        col = oracle.run_wake(W.Wake("c", edges, [drv], dxi, steps), ring_dumps=("r", "ur"),
+                              beam_fields=("ez", "wr", "bt", "psi"))
+        assert mob.status == col.status == 0
+        _, _, w, wh = oracle.ring_init(edges)
+        e = scale = 0.0
+        for s in range(10, steps, 20):
+            m = sl == s
+            sf = oracle.slice_fields(col.rings["r"][s], col.rings["ur"][s], w, wh, 1.0, r_max, drv.r[m],
+                                     drv.q * drv.w[m], dxi, rq=mob.rings["r"][s, n:])
+            e = max(e, np.max(np.abs(mob.rings["bp"][s, n:] - sf["q_bp"])))
+            scale = max(scale, np.max(np.abs(sf["q_bp"])))
+        errs["ion_bp"].append(e / scale)
+        if q > 0:
+            beyond = np.max(mob.rings["r"][:, n:], axis=1) > np.max(mob.rings["r"][:, :n], axis=1)
+            assert beyond.sum() > steps // 2
+        for k in ("ez", "bt", "wr", "psi"):
+            errs[k].append(np.max(np.abs(mob.beam[k] - col.beam[k])) / np.max(np.abs(col.beam[k])))
+    gain = {k: v[0] / v[-1] for k, v in errs.items()}
+    assert gain["psi"] > 40 and errs["psi"][-1] < 1e-3, errs
+    for k, (g, last) in {"ion_bp": (5, 0.02), "ez": (5, 0.01), "bt": (5, 0.01), "wr": (4, 0.2)}.items():
+        assert gain[k] > g and errs[k][-1] < last, (k, errs[k])
+        assert all(a > b for a, b in zip(errs[k], errs[k][1:])), (k, errs[k])
 
 
 def _lorentz_residual(n, dxi, M):
