@@ -130,3 +130,28 @@ def test_cartesian_fields_are_radial_and_azimuthal():
     assert np.allclose(E[2], ez) and np.allclose(B[2], 0.0)
     E0, B0 = bp.cartesian_fields([0.0], [0.0], [1.5], [2.0], [3.0])
     assert np.allclose(E0[:, 0], [0, 0, 1.5]) and np.allclose(B0[:, 0], 0.0)
+
+
+def test_rotation_between_the_half_kicks_uses_the_half_kicked_gamma():
+    """With E and B together the Boris step is kick - rotate - kick: the
+    momentum after the first half kick, u- = u + hE, and the one before
+    the second, u+ = u_new - hE, have the same norm and the same component
+    along B, and the part across B turns by 2 atan(|h B| / gamma(u-))
+    (the rotation is taken at the half-kicked momentum's gamma)."""
+    rng = _rng(7)
+    n = 40
+    u = rng.normal(size=(3, n)) * 2.0
+    E = rng.normal(size=(3, n))
+    B = rng.normal(size=(3, n)) * 1.5
+    h = 0.09
+    un = bp.boris_step(u, E, B, h)
+    um, up = u + h * E, un - h * E
+    assert np.allclose(np.linalg.norm(up, axis=0), np.linalg.norm(um, axis=0), rtol=1e-14)
+    b = B / np.linalg.norm(B, axis=0)
+    assert np.allclose(np.sum(up * b, axis=0), np.sum(um * b, axis=0), rtol=0, atol=1e-13)
+    pm = um - np.sum(um * b, axis=0) * b
+    pp = up - np.sum(up * b, axis=0) * b
+    cosang = np.sum(pm * pp, axis=0) / (np.linalg.norm(pm, axis=0) * np.linalg.norm(pp, axis=0))
+    gm = np.sqrt(1 + np.sum(um * um, axis=0))
+    expect = 2 * np.arctan(h * np.linalg.norm(B, axis=0) / gm)
+    assert np.allclose(np.arccos(np.clip(cosang, -1, 1)), expect, rtol=0, atol=1e-7)
