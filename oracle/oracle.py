@@ -3,6 +3,10 @@
 TEST INFRASTRUCTURE ONLY.  The oracle is plain sequential FP64 C that follows
 Sec. II-III and App. A of the paper step by step; this module only marshals
 numpy arrays in and out of it and builds it with gcc on first use.
+
+The environment variable ORACLE_LIB, when set, names another build of the
+same source to load instead (the planted-mistake tests load altered copies
+through it).
 """
 from __future__ import annotations
 
@@ -56,6 +60,9 @@ def lib_path() -> str:
     return _LIB
 
 
+GCC_FLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into oracle/_build/liboracle.so."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -64,8 +71,7 @@ def build(force: bool = False) -> str:
                                              os.path.getmtime(os.path.join(_HERE, "wake_oracle.h"))))
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -76,7 +82,7 @@ _lib_handle = None
 def _lib():
     global _lib_handle
     if _lib_handle is None:
-        lib = C.CDLL(build())
+        lib = C.CDLL(os.environ.get("ORACLE_LIB") or build())
         lib.orc_run.argtypes = [C.POINTER(_Problem), C.c_int32, C.POINTER(_Outputs)]
         lib.orc_run.restype = C.c_int
         lib.orc_run_ions.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, C.c_int32,
