@@ -21,7 +21,7 @@ setups, with the shapes of Sec. IV-V):
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import List, Optional, Tuple
 
 import numpy as np

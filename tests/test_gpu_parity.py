@@ -14,7 +14,6 @@ ring state at slice n (with its AB2 history) is loaded through the checkpoint
 API, one slice is solved on the GPU, and the slice's fields and the next
 state are compared with the oracle's.
 """
-import math
 
 import numpy as np
 import pytest

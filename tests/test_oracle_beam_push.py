@@ -8,7 +8,6 @@ drift of xi, and the Cartesian form of the axisymmetric fields."""
 import math
 
 import numpy as np
-import pytest
 
 from oracle import beam_push as bp
 
