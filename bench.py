@@ -236,12 +236,8 @@ def run_ours(args):
     h2d = 0
     if not (args.skip_e2e and args.skip_serve):
         for wk in wakes:
-            bl = []
-            for b in wk.beams:
-                t = [torch.from_numpy(a).pin_memory() for a in (b.xi, b.r, b.w)]
-                bl.append(type("B", (), {"xi": t[0], "r": t[1], "w": t[2], "q": b.q}))
-                h2d += 3 * 8 * b.n
-            pinned.append(bl)
+            pinned.append(_pinned_beams(wk))
+            h2d += sum(3 * 8 * b.n for b in wk.beams)
 
     # ---- end to end through the C ABI with host buffers (pinned), rank-local
     e2e = None
@@ -293,7 +289,7 @@ def run_ours(args):
     # ---- serving: Poisson arrivals of batched-workload wakes, continuous batching
     serving = None
     if not args.skip_serve:
-        serving = serve_bench(args, wakes, pinned, stream, rank)
+        serving = serve_bench(args, wakes, pinned, stream, rank, ws)
 
     # ---- plain FP64 one-wake-per-launch on a bounded sample (the plain GPU baseline)
     plain = None
@@ -534,26 +530,59 @@ def _ions_roofline(ions, peak_tflops, sm_mhz):
     return ions
 
 
-def serve_bench(args, wakes, pinned, stream, rank):
-    """Continuous batching under a Poisson stream: requests drawn (seeded) from
-    the batched workload's wakes arrive at args.serve_rate per second; the
-    server admits them under a device-memory budget and steps the running
-    batch; latency = result on the host minus arrival."""
+def _pinned_beams(wk):
+    """The wake's beams as pinned float64 host tensors (for asynchronous
+    uploads inside the timed regions)."""
+    import torch
+    out = []
+    for b in wk.beams:
+        t = [torch.from_numpy(a).pin_memory() for a in (b.xi, b.r, b.w)]
+        out.append(type("B", (), {"xi": t[0], "r": t[1], "w": t[2], "q": b.q}))
+    return out
+
+
+def serve_bench(args, wakes, pinned, stream, rank, ws=1):
+    """Continuous batching under a Poisson stream: requests drawn (seeded)
+    from the batched workload's first len(wakes) members arrive at
+    args.serve_rate per second per GPU; the server admits them under a
+    device-memory budget and steps the running batch; latency = result on
+    the host minus arrival.  With N GPUs one stream of N times the requests
+    at N times the rate is dispatched over the ranks (serve.dispatch: the
+    rank with the least work assigned so far), each rank serves its share on
+    its own GPU, and the latencies of all ranks are gathered afterwards
+    (serve.gather_summary)."""
     import torch
     from paper_2603_16623_gb300 import serve
-    rng = np.random.Generator(np.random.PCG64(4 + 1000 * rank))
-    n_req = args.serve_requests
-    pick = rng.integers(0, len(wakes), n_req)
-    arrivals = serve.poisson_arrivals(n_req, args.serve_rate, 4 + 1000 * rank)
+    n_pool = len(wakes)
+    rng = np.random.Generator(np.random.PCG64(4))
+    n_req = args.serve_requests * ws
+    pick = rng.integers(0, n_pool, n_req)
+    arrivals = serve.poisson_arrivals(n_req, args.serve_rate * ws, 4)
+    params = [W.batched_params(k) for k in range(n_pool)]
+    work = [params[int(k)].n_rings * params[int(k)].n_steps for k in pick]
+    owner = serve.dispatch(work, ws)
+    mine = np.nonzero(owner == rank)[0]
+    # this rank's requests: rank 0's own wakes are the pool members; other
+    # ranks draw the members they were given
+    pool = {}
+    for k in sorted({int(pick[i]) for i in mine}):
+        if rank == 0:
+            pool[k] = (wakes[k], pinned[k])
+        else:
+            wk = W.batched_wake(k)
+            pool[k] = (wk, _pinned_beams(wk))
     # one pinned result buffer per distinct wake: requests for the same wake
     # compute the same fields, so they may share it
-    outs = [(torch.empty(wk.n_beam, dtype=torch.float32).pin_memory(),
-             torch.empty(wk.n_beam, dtype=torch.float32).pin_memory()) for wk in wakes]
+    outs = {k: (torch.empty(wk.n_beam, dtype=torch.float32).pin_memory(),
+                torch.empty(wk.n_beam, dtype=torch.float32).pin_memory()) for k, (wk, _) in pool.items()}
     reqs = []
-    for i, (k, t) in enumerate(zip(pick, arrivals)):
-        wk = wakes[int(k)]
-        reqs.append(serve.Request(rid=i, arrival=float(t), edges=wk.edges, beams=pinned[int(k)], dxi=wk.dxi,
-                                  n_steps=wk.n_steps, out_ez=outs[int(k)][0], out_wr=outs[int(k)][1]))
+    for i in mine:
+        k = int(pick[i])
+        wk, pb = pool[k]
+        reqs.append(serve.Request(rid=int(i), arrival=float(arrivals[i]), edges=wk.edges, beams=pb, dxi=wk.dxi,
+                                  n_steps=wk.n_steps, out_ez=outs[k][0], out_wr=outs[k][1]))
+    if ws > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     sm_budget = args.serve_sm_fill * sms if args.serve_sm_fill > 0 else None
@@ -561,13 +590,13 @@ def serve_bench(args, wakes, pinned, stream, rank):
                            stream=stream.cuda_stream, clock=lambda: time.perf_counter() - t0, sm_budget=sm_budget)
     stats = serve.run_stream(srv, reqs)
     torch.cuda.synchronize()
-    out = stats.summary()
-    out.update({"arrival_rate_per_s": args.serve_rate, "memory_budget_gb": args.serve_budget_gb,
+    out = serve.gather_summary(stats)
+    out.update({"arrival_rate_per_s": args.serve_rate * ws, "memory_budget_gb": args.serve_budget_gb,
                 "sm_budget": sm_budget,
                 "step_us": args.serve_step_us,
-                "requests_from": f"{len(wakes)} batched-workload wakes, drawn with seed 4",
-                "offered_ring_slices_per_s": float(sum(wakes[int(k)].n_rings * wakes[int(k)].n_steps
-                                                       for k in pick) / arrivals[-1])})
+                "requests_from": f"{n_pool} batched-workload wakes, drawn with seed 4"
+                                 + (f", dispatched over {ws} GPUs by least assigned work" if ws > 1 else ""),
+                "offered_ring_slices_per_s": float(sum(work) / arrivals[-1])})
     return out
 
 

@@ -80,17 +80,66 @@ class ServeStats:
     max_queue: int = 0
     peak_bytes: int = 0
 
+    def records(self) -> List[tuple]:
+        """(arrival, finished, ring-slices done, status) per completed request."""
+        return [(r.arrival, r.finished, r.n_rings * r.slices_done, r.status) for r in self.completed]
+
+    def counters(self) -> Dict[str, int]:
+        return {"steps": self.steps, "max_active": self.max_active, "max_queue": self.max_queue,
+                "peak_device_bytes": self.peak_bytes}
+
     def summary(self) -> Dict[str, float]:
-        lat = np.array([r.latency for r in self.completed])
-        rs = sum(r.n_rings * r.slices_done for r in self.completed)
-        t0 = min(r.arrival for r in self.completed)
-        t1 = max(r.finished for r in self.completed)
-        return {"requests": len(self.completed), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-                "ring_slices": int(rs), "ring_slices_per_s": rs / (t1 - t0), "span_s": t1 - t0,
-                "steps": self.steps, "max_active": self.max_active, "max_queue": self.max_queue,
-                "peak_device_bytes": self.peak_bytes,
-                "stopped_by_breakdown": int(sum(r.status == wm.WAKE_ENONFINITE for r in self.completed))}
+        return summarize(self.records(), [self.counters()])
+
+
+def summarize(records: Sequence[tuple], counters: Sequence[Dict[str, int]]) -> Dict[str, float]:
+    """Latency percentiles and throughput of completed requests (records of
+    ServeStats.records, from one server or several), with each server's
+    counters summed (steps) or maximised (the rest)."""
+    arr = np.array([r[0] for r in records])
+    fin = np.array([r[1] for r in records])
+    lat = fin - arr
+    rs = sum(int(r[2]) for r in records)
+    span = float(fin.max() - arr.min())
+    return {"requests": len(records), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "ring_slices": int(rs), "ring_slices_per_s": rs / span, "span_s": span,
+            "steps": int(sum(c["steps"] for c in counters)),
+            "max_active": int(max(c["max_active"] for c in counters)),
+            "max_queue": int(max(c["max_queue"] for c in counters)),
+            "peak_device_bytes": int(max(c["peak_device_bytes"] for c in counters)),
+            "stopped_by_breakdown": int(sum(r[3] == wm.WAKE_ENONFINITE for r in records))}
+
+
+def dispatch(work: Sequence[float], n_ranks: int) -> np.ndarray:
+    """The GPU (rank) that serves each request of an arrival-ordered stream
+    when wakes are partitioned over n_ranks GPUs (a wake never spans GPUs,
+    so the data path needs no collective): each request goes to the rank
+    with the least work assigned so far (work: its ring-slices, rings x
+    slices), ties to the lowest rank.  Deterministic, so every rank computes
+    the same assignment from the same stream."""
+    load = np.zeros(max(1, int(n_ranks)))
+    owner = np.empty(len(work), dtype=np.int64)
+    for i, w in enumerate(work):
+        r = int(np.argmin(load))
+        owner[i] = r
+        load[r] += float(w)
+    return owner
+
+
+def gather_summary(stats: ServeStats) -> Dict[str, float]:
+    """summarize over the requests every rank of the default process group
+    served (one object all-gather, after serving: off the data path); on a
+    single process, stats.summary()."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return stats.summary()
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, (stats.records(), stats.counters()))
+    out = summarize([r for recs, _ in parts for r in recs], [c for _, c in parts])
+    out["ranks"] = len(parts)
+    out["requests_per_rank"] = [len(recs) for recs, _ in parts]
+    return out
 
 
 class WakeServer:

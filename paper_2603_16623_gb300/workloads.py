@@ -179,11 +179,24 @@ def blowout_wake(n_drv: int = 200_000, n_wit: int = 50_000,
     return Wake("blowout", edges, [drv, wit], dxi, n_steps)
 
 
-def batched_wake(k: int) -> Wake:
-    """Member k (0..255) of the batched workload, seed 3000+k: ring count
-    log-uniform in [500, 8000], n_b0 ~ U[0.05, 20], sigma_r ~ U[0.05, 1],
-    sigma_z ~ U[0.3, 2], 50k-500k macroparticles, 1000-6000 steps of 0.01;
-    uniform spacing out to max(6, 3 x (2 sqrt(n_b0) sigma_r))."""
+@dataclass(frozen=True)
+class BatchedParams:
+    """The drawn parameters of one batched-workload member (no arrays)."""
+    n_rings: int
+    n_b0: float
+    sigma_r: float
+    sigma_z: float
+    n_mp: int
+    n_steps: int
+    r_max: float
+
+
+def batched_params(k: int) -> BatchedParams:
+    """Member k's parameters, seed 3000+k: ring count log-uniform in [500,
+    8000], n_b0 ~ U[0.05, 20], sigma_r ~ U[0.05, 1], sigma_z ~ U[0.3, 2],
+    50k-500k macroparticles, 1000-6000 steps of 0.01; uniform spacing out to
+    max(6, 3 x (2 sqrt(n_b0) sigma_r)).  Cheap: a request stream can be
+    planned (sizes, work) without drawing any beam."""
     rng = np.random.Generator(np.random.PCG64(3000 + k))
     n_rings = int(math.floor(math.exp(rng.uniform(math.log(500), math.log(8000)))))
     n_b0 = rng.uniform(0.05, 20.0)
@@ -192,9 +205,16 @@ def batched_wake(k: int) -> Wake:
     n_mp = int(rng.integers(50_000, 500_001))
     n_steps = int(rng.integers(1000, 6001))
     r_max = max(6.0, 3.0 * 2.0 * math.sqrt(n_b0) * sigma_r)
-    drv = gaussian_beam(n_mp, n_b0, sigma_r, sigma_z, TRUNC_SIGMAS * sigma_z,
+    return BatchedParams(n_rings, n_b0, sigma_r, sigma_z, n_mp, n_steps, r_max)
+
+
+def batched_wake(k: int) -> Wake:
+    """Member k (0..255) of the batched workload (parameters from
+    batched_params(k)); the driver's particles drawn with seed 10000+k."""
+    p = batched_params(k)
+    drv = gaussian_beam(p.n_mp, p.n_b0, p.sigma_r, p.sigma_z, TRUNC_SIGMAS * p.sigma_z,
                         seed=10_000 + k)
-    return Wake(f"batched[{k}]", edges_uniform(n_rings, r_max), [drv], 0.01, n_steps)
+    return Wake(f"batched[{k}]", edges_uniform(p.n_rings, p.r_max), [drv], 0.01, p.n_steps)
 
 
 def batched_workload(n_wakes: int = 256) -> List[Wake]:

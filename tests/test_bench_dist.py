@@ -59,3 +59,91 @@ def test_beam_evaluations_count_the_particles_of_marched_slices():
     assert bench.beam_evaluations([wk], [1]) == 2 * 3
     assert bench.beam_evaluations([wk], [3]) == 2 * 6
     assert bench.beam_evaluations([wk, wk], [3, 2]) == 2 * 6 + 2 * 4
+
+
+def _fake_served(rank, world, n_req=40):
+    """The requests this rank serves of one dispatched stream, completed
+    with made-up latencies (no GPU): (owner array, ServeStats)."""
+    import numpy as np
+
+    from paper_2603_16623_gb300 import serve
+    from paper_2603_16623_gb300 import workloads as W
+    rng = np.random.Generator(np.random.PCG64(4))
+    pick = rng.integers(0, 256, n_req)
+    arrivals = serve.poisson_arrivals(n_req, 500.0 * world, 4)
+    work = [W.batched_params(int(k)).n_rings * W.batched_params(int(k)).n_steps for k in pick]
+    owner = serve.dispatch(work, world)
+    st = serve.ServeStats()
+    for i in np.nonzero(owner == rank)[0]:
+        p = W.batched_params(int(pick[i]))
+        r = serve.Request(rid=int(i), arrival=float(arrivals[i]), edges=np.linspace(0, 6, p.n_rings + 1), beams=(),
+                          dxi=0.01, n_steps=p.n_steps)
+        r.finished = r.arrival + 0.001 * (1 + i % 7)
+        r.slices_done = p.n_steps
+        r.status = 0
+        st.completed.append(r)
+    st.steps, st.max_active, st.max_queue, st.peak_bytes = 10 + rank, 3 + rank, 2, 1000 * (rank + 1)
+    return owner, st
+
+
+def _serve_rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    from paper_2603_16623_gb300 import serve
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    owner, st = _fake_served(rank, world)
+    out.put((rank, owner.tolist(), serve.gather_summary(st)))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_dispatch_one_stream_and_gather_the_latencies():
+    """Every rank computes the same assignment of one request stream; the
+    gathered summary covers the union of both ranks' requests (percentiles
+    over all latencies, steps summed, peaks maximised)."""
+    import numpy as np
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_serve_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in procs), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, own0, s0), (_, own1, s1) = res
+    assert own0 == own1 and set(own0) == {0, 1}
+    assert s0 == s1
+    lat = [0.001 * (1 + i % 7) for i in range(len(own0))]
+    assert s0["requests"] == len(own0) and s0["requests_per_rank"] == [own0.count(0), own0.count(1)]
+    assert abs(s0["p50_ms"] - np.percentile(lat, 50) * 1e3) < 1e-9
+    assert abs(s0["p99_ms"] - np.percentile(lat, 99) * 1e3) < 1e-9
+    assert s0["steps"] == 21 and s0["max_active"] == 4 and s0["peak_device_bytes"] == 2000
+
+
+def test_dispatch_balances_work_and_one_rank_takes_everything():
+    import numpy as np
+
+    from paper_2603_16623_gb300 import serve
+    rng = np.random.Generator(np.random.PCG64(9))
+    work = rng.uniform(1.0, 10.0, 500)
+    for n in (2, 3, 8):
+        owner = serve.dispatch(work, n)
+        load = np.bincount(owner, weights=work, minlength=n)
+        assert load.max() - load.min() <= work.max()
+        assert np.array_equal(owner, serve.dispatch(work, n))
+    assert not serve.dispatch(work, 1).any()
+    # one server's summary is the summary of its records
+    _, st = _fake_served(0, 1)
+    assert st.summary() == serve.summarize(st.records(), [st.counters()])
+
+
+def test_batched_params_are_the_members_parameters():
+    from paper_2603_16623_gb300 import workloads as W
+    for k in (0, 5, 77):
+        p, wk = W.batched_params(k), W.batched_wake(k)
+        assert (p.n_rings, p.n_steps, p.n_mp) == (wk.n_rings, wk.n_steps, wk.beams[0].n)
+        assert wk.edges[-1] == p.r_max
