@@ -77,6 +77,9 @@ C_CASES = [
      "double fu = s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]);", "double fu = s.gam[i] * s.dpr[i] / pb - s.bp[i];"),
     ("ab2_is_euler", "test_oracle_pins.py",
      "rho[id] = s.r[i] + dxi * (1.5 * fr - 0.5 * fr_prev[id]);", "rho[id] = s.r[i] + dxi * fr;"),
+    ("sort_unstable_on_ties", "test_oracle_pins.py",
+     "dst[k++] = (key[src[j]] < key[src[i]]) ? src[j++] : src[i++];",
+     "dst[k++] = (key[src[j]] <= key[src[i]]) ? src[j++] : src[i++];"),
     # fields at an arbitrary radius (a9)
     ("fields_at_psi_without_ions", "test_oracle_pins.py",
      "*psi = (s->Ltot - s->L[k]) + S * log(x) + ion_psi(x, dens, rho_max);", "*psi = (s->Ltot - s->L[k]) + S * log(x);"),

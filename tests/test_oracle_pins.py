@@ -528,6 +528,25 @@ def test_charge_conservation_and_neutrality_through_a_run():
         assert np.all(r >= 0.0)
 
 
+def test_rings_at_equal_radii_keep_their_previous_order():
+    """c10: the radius sort is stable with respect to the previous order (at
+    a slice's start, ring id order): of rings at exactly the same radius the
+    earlier one counts as below the later ones, so the later ring's partial
+    sums include the earlier one's weight and not the other way round."""
+    edges, rho, ur, w, wh = _random_state(n=30, seed=21)
+    rho = rho.copy()
+    rho[[4, 17, 25]] = rho[9]        # four rings at one radius
+    rho[[2, 28]] = rho[13]           # two at another
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1])
+    order = list(sf["order"])
+    assert order == sorted(range(30), key=lambda i: (rho[i], i))
+    # the tied group's d_rho psi steps by each earlier member's weight
+    grp = [4, 9, 17, 25]
+    for a, b in zip(grp, grp[1:]):
+        jump = (sf["dpsidr"][b] - sf["dpsidr"][a]) * rho[a]
+        assert abs(jump - (w[a] + wh[b] - wh[a])) < 1e-12
+
+
 def test_axis_crossing_reflects_and_stays_finite():
     """A strong narrow driver throws rings through the axis; they come back at
     rho >= 0 and the march completes."""
