@@ -80,12 +80,17 @@ C_CASES = [
     ("sort_unstable_on_ties", "test_oracle_pins.py",
      "dst[k++] = (key[src[j]] < key[src[i]]) ? src[j++] : src[i++];",
      "dst[k++] = (key[src[j]] <= key[src[i]]) ? src[j++] : src[i++];"),
+    ("guard_disabled", "test_oracle_pins.py",
+     "static int ring_fields_ok(const slice_ws *s)\n{", "static int ring_fields_ok(const slice_ws *s)\n{\n    return 1;"),
     # fields at an arbitrary radius (a9)
     ("fields_at_psi_without_ions", "test_oracle_pins.py",
      "*psi = (s->Ltot - s->L[k]) + S * log(x) + ion_psi(x, dens, rho_max);", "*psi = (s->Ltot - s->L[k]) + S * log(x);"),
     ("fields_at_dzeta_index", "test_oracle_pins.py",
      "    *dpr = (S - ion_enclosed(x, dens, rho_max)) / x;\n    *dpz = -(s->Ttot - s->T[k]);",
      "    *dpr = (S - ion_enclosed(x, dens, rho_max)) / x;\n    *dpz = -(s->Ttot - s->T[k > 0 ? k - 1 : 0]);"),
+    ("axis_dzeta_zero", "test_oracle_pins.py", "*dpz = -(s->Ttot - s->T[0]);", "*dpz = 0.0;"),
+    ("axis_psi_without_rings", "test_oracle_pins.py",
+     "*psi = s->Ltot + ion_psi(0.0, dens, rho_max);", "*psi = ion_psi(0.0, dens, rho_max);"),
     ("fields_at_bp_region", "test_oracle_pins.py",
      "*bp = s->a[k] * x + s->b[k] / x;", "*bp = s->a[k > 0 ? k - 1 : 0] * x + s->b[k > 0 ? k - 1 : 0] / x;"),
     # the two-species march (orc_run_ions)

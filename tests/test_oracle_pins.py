@@ -528,6 +528,41 @@ def test_charge_conservation_and_neutrality_through_a_run():
         assert np.all(r >= 0.0)
 
 
+def test_fields_on_the_axis_are_the_limits_from_outside():
+    """At r = 0 exactly (a beam particle on the axis) the plasma fields are
+    the limits r -> 0+ of the off-axis sums: psi and E_z of all rings
+    outside, no radial field, no B^(p); the beam field is zero (no charge
+    strictly inside r = 0, though a particle sits on the axis)."""
+    edges, rho, ur, w, wh = _random_state(n=25, seed=5)
+    br = np.array([0.0, 0.3, 0.9])
+    bq = np.array([-1e-3, -2e-3, -1e-3])
+    sf = oracle.slice_fields(rho, ur, w, wh, 1.0, edges[-1], br, bq, 0.05, rq=np.array([0.0, 1e-12]))
+    assert abs(sf["q_psi"][0] - sf["q_psi"][1]) < 1e-10
+    assert abs(sf["q_ez"][0] - sf["q_ez"][1]) < 1e-12 * max(1.0, abs(sf["q_ez"][1]))
+    assert sf["q_ez"][0] != 0.0
+    for k in ("q_wr", "q_bp"):
+        assert sf[k][0] == 0.0 and abs(sf[k][1]) < 1e-9, k
+    assert sf["q_bb"][0] == 0.0 and sf["q_bt"][0] == 0.0
+
+
+def test_the_wake_stops_at_the_first_slice_where_psibar_reaches_zero():
+    """c11: a strong driver drives psibar through zero behind the first
+    bubble; the march stops there with ENONFINITE (the failing slice's
+    fields are kept, nothing after it), psibar having stayed positive and
+    every field finite before."""
+    wk = W.batched_wake(3)
+    res = oracle.run_wake(W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, 1700), beam_fields=(),
+                          ring_dumps=("psibar", "psi", "dpsidr", "dpsidz", "bp"))
+    f = res.fail_slice
+    assert res.status == 4 and 0 < f < 1700 and res.slices_run == f + 1
+    R = res.rings
+    assert np.min(R["psibar"][:f]) > 0.0
+    assert all(np.all(np.isfinite(R[k][:f])) for k in ("psi", "dpsidr", "dpsidz", "bp"))
+    bad = (R["psibar"][f] <= 0.0) | ~np.isfinite(R["psi"][f]) | ~np.isfinite(R["bp"][f])
+    assert bad.any()
+    assert np.all(R["psibar"][f + 1:] == 0.0)  # slices after the stop are never solved
+
+
 def test_rings_at_equal_radii_keep_their_previous_order():
     """c10: the radius sort is stable with respect to the previous order (at
     a slice's start, ring id order): of rings at exactly the same radius the
