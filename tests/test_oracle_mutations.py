@@ -80,6 +80,18 @@ C_CASES = [
     ("sort_unstable_on_ties", "test_oracle_pins.py",
      "dst[k++] = (key[src[j]] < key[src[i]]) ? src[j++] : src[i++];",
      "dst[k++] = (key[src[j]] <= key[src[i]]) ? src[j++] : src[i++];"),
+    # the B^(p) solves (Eq. ai_bi: banded elimination, App. A shooting)
+    ("band_source_a_factor", "test_oracle_pins.py",
+     "x[ra] = 0.25 * (2.0 * Bi + Ai * Ci);", "x[ra] = 0.25 * (2.0 * Bi - Ai * Ci);"),
+    ("band_matrix_m21_sign", "test_oracle_pins.py",
+     "SET(rb, ca0, 0.5 * Ai * r * r * r);", "SET(rb, ca0, -0.5 * Ai * r * r * r);"),
+    ("band_outer_condition_on_b", "test_oracle_pins.py",
+     "SET(m - 1, m - 2, 1.0);  /* a_N = 0 */", "SET(m - 1, m - 1, 1.0);"),
+    ("band_no_pivoting", "test_oracle_pins.py",
+     "            if (fabs(AB(r, k)) > best) {", "            if (0) {"),
+    ("shooting_m12", "test_oracle_pins.py", "double m12 = 0.5 * Ai / r;", "double m12 = 0.5 * Ai * r;"),
+    ("shooting_start_K", "test_oracle_pins.py",
+     "K[0] = 1.0; U[0] = 0.0; T[0] = 0.0; P[0] = 0.0;", "K[0] = 1.0; U[0] = 1.0; T[0] = 0.0; P[0] = 0.0;"),
     ("guard_disabled", "test_oracle_pins.py",
      "static int ring_fields_ok(const slice_ws *s)\n{", "static int ring_fields_ok(const slice_ws *s)\n{\n    return 1;"),
     # fields at an arbitrary radius (a9)
