@@ -80,6 +80,9 @@ C_CASES = [
     ("sort_unstable_on_ties", "test_oracle_pins.py",
      "dst[k++] = (key[src[j]] < key[src[i]]) ? src[j++] : src[i++];",
      "dst[k++] = (key[src[j]] <= key[src[i]]) ? src[j++] : src[i++];"),
+    ("binning_without_half", "test_oracle_pins.py",
+     "return (int64_t)floor(xi / dxi + 0.5);", "return (int64_t)floor(xi / dxi);"),
+    ("ion_psi_outside_constant", "test_oracle_pins.py", "    return -q * log(rho);", "    return -q * log(rho_max);"),
     # the B^(p) solves (Eq. ai_bi: banded elimination, App. A shooting)
     ("band_source_a_factor", "test_oracle_pins.py",
      "x[ra] = 0.25 * (2.0 * Bi + Ai * Ci);", "x[ra] = 0.25 * (2.0 * Bi - Ai * Ci);"),
@@ -147,6 +150,7 @@ C_CASES = [
      "rc = slice_core(&s, ord_s, rs, us, w, wh, dens, rho_max, &bs, NULL, 1.0, 0.0, NULL, dxi);"),
     ("rk4_equal_stage_weights", "test_oracle_rk4.py", "ws[3] = {2.0, 2.0, 1.0}", "ws[3] = {1.0, 1.0, 1.0}"),
     ("rk4_stage_steps", "test_oracle_rk4.py", "cs[3] = {0.5, 0.5, 1.0}", "cs[3] = {0.5, 1.0, 1.0}"),
+    ("rk4_first_stage_weight", "test_oracle_rk4.py", "sum_r[id] = ksr[id];", "sum_r[id] = 2.0 * ksr[id];"),
     # beam grids (Sec. IV)
     ("grid_extent_without_margin", "test_oracle_grid.py",
      "agR[b] = (agR[b] > 1e-12 ? agR[b] : 1e-12) * (1.0 + 1.0 / nr);",
@@ -167,6 +171,9 @@ C_CASES = [
     ("grid_all_species_on_one_grid", "test_oracle_grid.py",
      "int32_t b = p->beam_species ? p->beam_species[bs.idx[q]] : 0;\n                double dr = agR[b] / nr;",
      "int32_t b = 0;\n                double dr = agR[b] / nr;"),
+    ("regular_grid_ignored", "test_oracle_grid.py", "                    agR[b] = p->grid_rmax;\n", ""),
+    ("regular_grid_unchecked", "test_oracle_grid.py",
+     "                    if (!(agR[b] < p->grid_rmax))\n                        rc = ORC_EINVAL;\n", ""),
     ("grid_one_extent_for_all", "test_oracle_grid.py",
      "if (p->beam_r[k] > agR[b]) agR[b] = p->beam_r[k];",
      "for (int32_t b2 = 0; b2 < p->n_species; ++b2) if (p->beam_r[k] > agR[b2]) agR[b2] = p->beam_r[k];"),
