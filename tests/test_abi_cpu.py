@@ -72,6 +72,46 @@ def test_launch_shape_is_validated_on_the_host(precision, n, k, cl, why):
     assert why in lib.wake_last_error().decode()
 
 
+@pytest.mark.parametrize("precision,n,k,cl,why", [
+    ("mixed", 1000, 5, 0, "rings_per_thread"),
+    ("mixed", 1000, 4, 17, "cluster_ctas"),
+    ("fp64", 1000, 4, 0, "WAKE_MIXED only"),
+    ("mixed", 100, 4, 4, "empty"),
+    ("mixed", 8192, 4, 2, "do not fit"),
+    ("mixed", 70000, 0, 0, "n_rings"),
+    ("fp64", 9000, 0, 0, "n_rings"),
+])
+def test_the_shape_query_refuses_what_wake_init_refuses(precision, n, k, cl, why):
+    """wake_launch_shape (host-only) gives EINVAL with the same reason for
+    the shapes wake_init refuses."""
+    from paper_2603_16623_gb300 import wake as wm
+    wm.load()
+    with pytest.raises(wm.WakeError, match=re.escape(why)):
+        wm.wake_launch_shape(n, k, cl, precision)
+
+
+def test_the_shape_query_gives_the_automatic_and_explicit_shapes():
+    """The automatic on-chip shapes (one CTA up to 2048 rings, then
+    clusters of up to 1024, then 2048 rings per CTA, then 8 rings per
+    thread) and explicit ones, computed on the host; FP64 wakes run on the
+    one-CTA march (all zeros)."""
+    from paper_2603_16623_gb300 import wake as wm
+    wm.load()
+    assert wm.wake_launch_shape(200) == (64, 4, 1)
+    assert wm.wake_launch_shape(2048) == (512, 4, 1)
+    assert wm.wake_launch_shape(2049) == (192, 4, 3)
+    assert wm.wake_launch_shape(16384) == (256, 4, 16)
+    assert wm.wake_launch_shape(16385) == (480, 4, 9)
+    assert wm.wake_launch_shape(65536) == (512, 8, 16)
+    assert wm.wake_launch_shape(3000, 8, 0) == (384, 8, 1)
+    assert wm.wake_launch_shape(3000, 4, 3) == (256, 4, 3)
+    assert wm.wake_launch_shape(4000, precision="fp64") == (0, 0, 0)
+    for n in range(1, 65537, 997):
+        t, k, c = wm.wake_launch_shape(n)
+        assert 32 <= t <= 512 and t % 32 == 0 and k in (4, 8) and 1 <= c <= 16
+        assert t * k * c >= n and (c == 1 or t * k * (c - 1) < n)
+
+
 @pytest.mark.parametrize("case,why", [
     ({"ion_charge": -1.0, "ion_mass": 10.0}, "ion_charge > 0"),
     ({"ion_charge": 1.0, "ion_mass": 0.0}, "ion_charge > 0"),
