@@ -285,7 +285,13 @@ def tune_batch(wakes: Sequence, sizes: Sequence[int] = DEFAULT_SIZES, max_candid
 
     make(wake, shape_kwargs) -> handle and run(handles) -> seconds of one
     step are the GPU by default (a Wake per workload wake; CUDA events
-    around wake_batch_reset_run); the best of `repeats` runs counts."""
+    around wake_batch_reset_run); the best of `repeats` runs counts.  The
+    wakes must be on-chip-march wakes (electrons over the ion column, AB2,
+    no beam grids): the other marches take no rings per thread or CTAs."""
+    for wk in wakes:
+        if (getattr(wk, "ions", None) is not None or getattr(wk, "integrator", "ab2") != "ab2"
+                or getattr(wk, "grid_nr", 0)):
+            raise ValueError(f"{wk.name}: not a wake of the on-chip march (ions, RK4 or beam grids)")
     bounds = _class_bounds(sizes)
     table = TuningTable([TableEntry("mixed", b) for b in bounds])
     if make is None or run is None:

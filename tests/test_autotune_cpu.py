@@ -167,3 +167,14 @@ def test_batch_tuning_ignores_gains_below_the_noise():
         return max(1e-6 * h.n * (0.99 if h.shape else 1.0) for h in handles)
     table = at.tune_batch(wakes, sizes=(2048, 8192), make=_FakeHandle, run=run, min_gain=0.02)
     assert all(e.rings_per_cta == 0 for e in table.entries)
+
+
+def test_batch_tuning_takes_only_on_chip_wakes():
+    import dataclasses
+
+    from paper_2603_16623_gb300 import workloads as W
+    wk = W.Wake("w", W.edges_uniform(1000, 6.0), [], 0.01, 100)
+    for bad in (dataclasses.replace(wk, ions=(1.0, 1836.0)), dataclasses.replace(wk, integrator="rk4"),
+                dataclasses.replace(wk, grid_nr=16)):
+        with pytest.raises(ValueError):
+            at.tune_batch([wk, bad], sizes=(2048,), make=_FakeHandle, run=lambda hs: 1.0)
