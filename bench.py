@@ -15,6 +15,15 @@ With torchrun (N > 1) every rank solves its own batch of 256 wakes (weak
 scaling, no collective on the data path) and rank 0 prints one JSON line.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores.
+
+Besides the timed step the line carries: the same step end to end from
+pinned host beams (e2e), beam-particle field evaluations per second, the
+ALU roofline of the march, the plain FP64 one-wake-per-launch baseline,
+serving latencies under a Poisson stream, the beam push, mobile ions and a
+density profile, RK4, beam grids, the single-wake workloads, the oracle on
+the host cores, and the SM clocks sampled during the timed region.  Each
+leg has a --skip-* flag; --autotune batch|probe picks the launch shapes by
+a tuning run first.
 """
 from __future__ import annotations
 
