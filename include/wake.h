@@ -264,11 +264,17 @@ wake_status wake_batch_step(int32_t n, wake_handle *const *handles, int32_t max_
 wake_status wake_batch_progress(int32_t n, wake_handle *const *handles, int32_t *next_slice,
                                 int32_t *status);
 
-/* Device bytes the handle holds (for admission by a memory budget). */
+/* Device bytes the handle holds (for admission by a memory budget): every
+   allocation wake_init and wake_set_beam_phase_space made for it.  Host
+   call, no device
+   work.  Errors: EINVAL (NULL handle or bytes). */
 wake_status wake_get_device_bytes(wake_handle *h, int64_t *bytes);
 
 /* Progress of a wake (synchronises its stream): next slice to solve,
-   status (OK or ENONFINITE) and the failing slice (-1 if none). */
+   status (OK, ENONFINITE, or EINVAL for a slice denser than
+   wake_max_slice_particles() after an asynchronous preparation) and the
+   failing slice (-1 if none); any output may be NULL.  Errors: EINVAL
+   (NULL handle), ECUDA. */
 wake_status wake_get_progress(wake_handle *h, int32_t *next_slice, int32_t *status,
                               int32_t *fail_slice);
 
