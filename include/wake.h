@@ -266,8 +266,7 @@ wake_status wake_batch_progress(int32_t n, wake_handle *const *handles, int32_t 
 
 /* Device bytes the handle holds (for admission by a memory budget): every
    allocation wake_init and wake_set_beam_phase_space made for it.  Host
-   call, no device
-   work.  Errors: EINVAL (NULL handle or bytes). */
+   call, no device work.  Errors: EINVAL (NULL handle or bytes). */
 wake_status wake_get_device_bytes(wake_handle *h, int64_t *bytes);
 
 /* Progress of a wake (synchronises its stream): next slice to solve,
