@@ -32,7 +32,8 @@ class _Problem(C.Structure):
                 ("n_beam", C.c_int64), ("beam_xi", _dp), ("beam_r", _dp), ("beam_qw", _dp),
                 ("dxi", C.c_double), ("n_steps", C.c_int32), ("cell_density", _dp), ("integrator", C.c_int32),
                 ("grid_nr", C.c_int32), ("beam_species", _ip), ("n_species", C.c_int32),
-                ("grid_rmax", C.c_double)]
+                ("grid_rmax", C.c_double), ("init_r", _dp), ("init_ur", _dp), ("init_fr", _dp),
+                ("init_fu", _dp)]
 
 
 _RING_DUMPS = ["ring_r", "ring_ur", "ring_psi", "ring_dpsidr", "ring_dpsidz", "ring_bp",
@@ -43,7 +44,10 @@ class _Outputs(C.Structure):
     _fields_ = ([(k, _dp) for k in ["ez", "wr", "bt", "psi"]]
                 + [(k, _dp) for k in _RING_DUMPS]
                 + [("final_r", _dp), ("final_ur", _dp), ("status", C.c_int32),
-                   ("fail_slice", C.c_int32), ("slices_run", C.c_int32)])
+                   ("fail_slice", C.c_int32), ("slices_run", C.c_int32),
+                   ("n_snap", C.c_int32), ("snap_slice", _ip), ("snap", _dp)])
+
+_SNAP_FIELDS = ["r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb", "frprev", "fuprev"]
 
 
 _SLICE_RING = ["psi", "dpsidr", "dpsidz", "psibar", "gamma", "uz", "bb", "A", "B", "C", "bp"]
@@ -189,13 +193,14 @@ class OracleResult:
     rings: Dict[str, np.ndarray]
     final_r: np.ndarray
     final_ur: np.ndarray
+    snapshots: Dict[int, Dict[str, np.ndarray]] = None
 
 
 def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: float = 1.0,
         max_slices: int = 0, beam_fields: Sequence[str] = ("ez", "wr", "bt", "psi"),
         ring_dumps: Sequence[str] = (), ions: Optional[Tuple[float, float]] = None,
         cell_density=None, integrator: str = "ab2", grid_nr: int = 0, beam_species=None,
-        grid_rmax: float = 0.0) -> OracleResult:
+        grid_rmax: float = 0.0, init_state=None, snapshots: Sequence[int] = ()) -> OracleResult:
     """March the whole window (or its first max_slices slices).
 
     beam_fields: subset of ez, wr, bt, psi (per particle, caller order).
@@ -209,7 +214,13 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     (electron-only march).  grid_nr > 0: beam fields through adaptive beam
     grids of grid_nr radial cells per species (beam_species: each
     particle's species index; None: one species); grid_rmax > 0: grids of
-    that fixed extent (the regular intermediate grid)."""
+    that fixed extent (the regular intermediate grid).  init_state: None
+    (rings at rest at their cell centres), or (rho, u_r) or (rho, u_r,
+    f_rho, f_u) by ring id, the starting state (f_*: the AB2 history; without
+    it the first step is forward Euler); electron-only runs.  snapshots:
+    slices at which to keep every ring dump (r, ur, psi, dpsidr, dpsidz, bp,
+    bb, frprev, fuprev by ring id), returned as {slice: {name: array}} for
+    the slices the run reached; electron-only runs."""
     edges = _f64(edges)
     bxi, br, bqw = _f64(beam_xi), _f64(beam_r), _f64(beam_qw)
     n_e = edges.shape[0] - 1
@@ -218,9 +229,16 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     cd = None if cell_density is None else _f64(cell_density)
     sp = None if beam_species is None else np.ascontiguousarray(beam_species, dtype=np.int32)
     n_sp = 1 if sp is None or sp.shape[0] == 0 else int(sp.max()) + 1
+    init = [None] * 4
+    if init_state is not None:
+        if ions is not None:
+            raise ValueError("init_state applies to electron-only runs")
+        init[: len(init_state)] = [_f64(a) for a in init_state]
+        assert all(a is None or a.shape == (n,) for a in init)
     prob = _Problem(n_e, _ptr(edges), density, nb, _ptr(bxi), _ptr(br), _ptr(bqw), dxi, n_steps, _ptr(cd),
                     {"ab2": 0, "rk4": 1}[integrator], int(grid_nr),
-                    None if sp is None else sp.ctypes.data_as(_ip), n_sp, float(grid_rmax))
+                    None if sp is None else sp.ctypes.data_as(_ip), n_sp, float(grid_rmax),
+                    *(_ptr(a) for a in init))
     out = _Outputs()
     beam = {}
     for k in beam_fields:
@@ -234,13 +252,22 @@ def run(edges, beam_xi, beam_r, beam_qw, dxi: float, n_steps: int, density: floa
     final_r = np.empty(n)
     final_ur = np.empty(n)
     out.final_r, out.final_ur = _ptr(final_r), _ptr(final_ur)
+    snap_sl = np.ascontiguousarray(sorted(set(int(v) for v in snapshots)), dtype=np.int32)
+    snap = np.zeros((snap_sl.shape[0], len(_SNAP_FIELDS), n))
+    if snap_sl.shape[0]:
+        if ions is not None:
+            raise ValueError("snapshots apply to electron-only runs")
+        out.n_snap = snap_sl.shape[0]
+        out.snap_slice = snap_sl.ctypes.data_as(_ip)
+        out.snap = _ptr(snap)
     if ions is None:
         rc = _lib().orc_run(C.byref(prob), max_slices, C.byref(out))
     else:
         rc = _lib().orc_run_ions(C.byref(prob), float(ions[0]), float(ions[1]), max_slices, C.byref(out))
     if rc:
         raise RuntimeError(f"orc_run failed ({rc})")
-    return OracleResult(out.status, out.fail_slice, out.slices_run, beam, rings, final_r, final_ur)
+    snaps = {int(sl): dict(zip(_SNAP_FIELDS, snap[j])) for j, sl in enumerate(snap_sl) if sl < out.slices_run}
+    return OracleResult(out.status, out.fail_slice, out.slices_run, beam, rings, final_r, final_ur, snaps)
 
 
 def run_wake(wake, **kw) -> OracleResult:

@@ -637,6 +637,34 @@ static int64_t nearest_slice(double xi, double dxi)
     return (int64_t)floor(xi / dxi + 0.5);
 }
 
+/* One step of a ring's radius and radial momentum to the next slice
+   (Eqs. plasma_particle_motion_1,2 with xi = -zeta), second-order
+   Adams-Bashforth (Sec. III) with forward Euler when there is no previous
+   slice (have_prev = 0): from (r, u) with the derivatives (fr, fu) of this
+   slice and the previous slice's (*frp, *fup); *frp, *fup become this
+   slice's.  A ring pushed below the axis reappears at -rho moving the
+   other way; f_rho and f_u are odd in (rho, u_r), so its history is
+   negated too.  Both marches (one species, two species) step with it. */
+static void ab2_step(double r, double u, double fr, double fu, int have_prev, double dxi, double *rho, double *ur,
+                     double *frp, double *fup)
+{
+    if (have_prev) {
+        *rho = r + dxi * (1.5 * fr - 0.5 * *frp);
+        *ur = u + dxi * (1.5 * fu - 0.5 * *fup);
+    } else {
+        *rho = r + dxi * fr;
+        *ur = u + dxi * fu;
+    }
+    *frp = fr;
+    *fup = fu;
+    if (*rho < 0.0) {
+        *rho = -*rho;
+        *ur = -*ur;
+        *frp = -*frp;
+        *fup = -*fup;
+    }
+}
+
 int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
 {
     if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
@@ -653,6 +681,10 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
             return ORC_EINVAL;
     if (p->edges[0] != 0.0)
         return ORC_EINVAL;
+    if (p->init_r)
+        for (int32_t j = 0; j < p->n_rings; ++j)
+            if (!(p->init_r[j] >= 0.0))
+                return ORC_EINVAL;
     int32_t n = p->n_rings, ns = p->n_steps;
     int32_t nrun = (max_slices > 0 && max_slices < ns) ? max_slices : ns;
     double rho_max = p->edges[n], dens = p->density, dxi = p->dxi;
@@ -683,6 +715,19 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
     orc_ring_init(n, p->edges, dens, rho, NULL, w, wh);
     for (int32_t j = 0; j < n; ++j)
         order[j] = j;
+    int have_prev = 0;
+    if (p->init_r) {
+        /* a given starting state (weights stay those of the cells) */
+        for (int32_t j = 0; j < n; ++j) {
+            rho[j] = p->init_r[j];
+            ur[j] = p->init_ur ? p->init_ur[j] : 0.0;
+        }
+        if (p->init_fr && p->init_fu) {
+            memcpy(fr_prev, p->init_fr, (size_t)n * sizeof(double));
+            memcpy(fu_prev, p->init_fu, (size_t)n * sizeof(double));
+            have_prev = 1;
+        }
+    }
 
     /* bin the beam by nearest slice (counting sort, stable in caller order) */
     for (int64_t k = 0; k < p->n_beam; ++k) {
@@ -751,7 +796,6 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
         }
     }
 
-    int have_prev = 0;
     for (int32_t sl = 0; sl < nrun && !rc; ++sl) {
         beam_slice bs = {0, NULL, NULL, NULL};
         rc = beam_slice_build(&bs, cnt[sl + 1] - cnt[sl], parts + cnt[sl]);
@@ -796,6 +840,23 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
             if (out->ring_uz) out->ring_uz[row + id] = s.uz[i];
             if (out->ring_frprev) out->ring_frprev[row + id] = have_prev ? fr_prev[id] : 0.0;
             if (out->ring_fuprev) out->ring_fuprev[row + id] = have_prev ? fu_prev[id] : 0.0;
+        }
+        for (int32_t j = 0; j < out->n_snap && out->snap; ++j) {
+            if (out->snap_slice[j] != sl)
+                continue;
+            double *sn = out->snap + (size_t)j * ORC_SNAP_FIELDS * (size_t)n;
+            for (int32_t i = 0; i < n; ++i) {
+                int32_t id = order[i];
+                sn[id] = s.r[i];
+                sn[n + id] = s.u[i];
+                sn[2 * (size_t)n + id] = s.psi[i];
+                sn[3 * (size_t)n + id] = s.dpr[i];
+                sn[4 * (size_t)n + id] = s.dpz[i];
+                sn[5 * (size_t)n + id] = s.bp[i];
+                sn[6 * (size_t)n + id] = s.bb[i];
+                sn[7 * (size_t)n + id] = have_prev ? fr_prev[id] : 0.0;
+                sn[8 * (size_t)n + id] = have_prev ? fu_prev[id] : 0.0;
+            }
         }
         /* fields on the beam particles of this slice: directly (a9), or from
            the grid nodes (the plasma fields evaluated there, B^(b) of all
@@ -924,23 +985,7 @@ int orc_run(const orc_problem *p, int32_t max_slices, orc_outputs *out)
             double pb = s.psib[i];
             double fr = s.u[i] / pb;
             double fu = s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]);
-            if (have_prev) {
-                rho[id] = s.r[i] + dxi * (1.5 * fr - 0.5 * fr_prev[id]);
-                ur[id] = s.u[i] + dxi * (1.5 * fu - 0.5 * fu_prev[id]);
-            } else {
-                rho[id] = s.r[i] + dxi * fr;
-                ur[id] = s.u[i] + dxi * fu;
-            }
-            fr_prev[id] = fr;
-            fu_prev[id] = fu;
-            /* crossing the axis: the ring reappears at -rho moving the other
-               way; f_rho and f_u are odd in rho, so the history flips too */
-            if (rho[id] < 0.0) {
-                rho[id] = -rho[id];
-                ur[id] = -ur[id];
-                fr_prev[id] = -fr_prev[id];
-                fu_prev[id] = -fu_prev[id];
-            }
+            ab2_step(s.r[i], s.u[i], fr, fu, have_prev, dxi, &rho[id], &ur[id], &fr_prev[id], &fu_prev[id]);
         }
         have_prev = 1;
     }
@@ -1144,7 +1189,7 @@ int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_s
                  orc_outputs *out)
 {
     if (!p || !out || p->n_rings < 1 || !p->edges || !(p->dxi > 0.0) || p->n_steps < 0 ||
-        !(ion_z > 0.0) || !(ion_m > 0.0) ||
+        !(ion_z > 0.0) || !(ion_m > 0.0) || p->init_r ||
         (p->n_beam > 0 && (!p->beam_xi || !p->beam_r || !p->beam_qw)))
         return ORC_EINVAL;
     if (p->cell_density)
@@ -1362,21 +1407,8 @@ int orc_run_ions(const orc_problem *p, double ion_z, double ion_m, int32_t max_s
                 double pb = me->psib[i];
                 double fr = me->u[i] / pb;
                 double fu = -me->qm * (me->gam[i] * me->dpr[i] / pb - (me->bp[i] + me->bb[i]));
-                if (have_prev) {
-                    rho[id] = me->r[i] + dxi * (1.5 * fr - 0.5 * fr_prev[id]);
-                    ur[id] = me->u[i] + dxi * (1.5 * fu - 0.5 * fu_prev[id]);
-                } else {
-                    rho[id] = me->r[i] + dxi * fr;
-                    ur[id] = me->u[i] + dxi * fu;
-                }
-                fr_prev[id] = fr;
-                fu_prev[id] = fu;
-                if (rho[id] < 0.0) {
-                    rho[id] = -rho[id];
-                    ur[id] = -ur[id];
-                    fr_prev[id] = -fr_prev[id];
-                    fu_prev[id] = -fu_prev[id];
-                }
+                ab2_step(me->r[i], me->u[i], fr, fu, have_prev, dxi, &rho[id], &ur[id], &fr_prev[id],
+                         &fu_prev[id]);
             }
         }
         have_prev = 1;

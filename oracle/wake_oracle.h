@@ -56,6 +56,12 @@ typedef struct {
        intermediate grid); every beam particle must lie below it (else
        ORC_EINVAL).  0: the adaptive extent. */
     double grid_rmax;
+    /* initial ring state by ring id (orc_run only; NULL: the rings start
+       at rest at their cell centres, Sec. II): radii (>= 0) and radial
+       momenta, and optionally the AB2 history (the previous slice's
+       d rho/dxi and d u_r/dxi; NULL: the first step is forward Euler).
+       The counterpart of a checkpoint restored on the GPU path. */
+    const double *init_r, *init_ur, *init_fr, *init_fu;
 } orc_problem;
 
 typedef struct {
@@ -74,7 +80,16 @@ typedef struct {
     int32_t status;       /* ORC_OK or ORC_ENONFINITE */
     int32_t fail_slice;   /* first slice whose fields failed the guard, else -1 */
     int32_t slices_run;
+    /* orc_run: the ring dumps above at n_snap chosen slices only (snapshots
+       of long windows): snap [n_snap][ORC_SNAP_FIELDS][n_rings] by ring id,
+       the fields in the order r, ur, psi, dpsidr, dpsidz, bp, bb, frprev,
+       fuprev; rows of slices not reached stay as they are. */
+    int32_t n_snap;
+    const int32_t *snap_slice;
+    double *snap;
 } orc_outputs;
+
+enum { ORC_SNAP_FIELDS = 9 };
 
 /* Fields of one slice for a given ring state; everything per ring is indexed
    by ring id, per-region coefficients in radius order. */

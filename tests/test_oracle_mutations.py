@@ -7,12 +7,11 @@ ORACLE_LIB); the beam-push oracle is re-executed from altered source in
 process.  The copies and the planted mistakes live only in the temporary
 directory; the oracle itself is never changed.
 
-Two readings have no pin that a planted mistake would fail, because no
-value independent of the oracle fixes them: the sign flip of the AB2
-history when a ring is reflected at the axis, and the mirroring back of an
-RK4 stage derivative evaluated below the axis (reading c6: a ring crossing
-the axis in one step is a discrete event; the continuous ring is turned
-back by the log barrier of its own self weight).  They are not listed."""
+The axis readings (the AB2 history negated with rho and u_r when a ring
+is reflected; an RK4 stage below the axis evaluated mirrored) are pinned
+by the convergence order of a light ring's orbit through the axis against
+an independent integration (tests/axis_orbit.py); their planted mistakes
+are listed with the others."""
 import concurrent.futures
 import importlib.util
 import os
@@ -76,7 +75,7 @@ C_CASES = [
     ("push_drops_beam_field", "test_oracle_pins.py",
      "double fu = s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]);", "double fu = s.gam[i] * s.dpr[i] / pb - s.bp[i];"),
     ("ab2_is_euler", "test_oracle_pins.py",
-     "rho[id] = s.r[i] + dxi * (1.5 * fr - 0.5 * fr_prev[id]);", "rho[id] = s.r[i] + dxi * fr;"),
+     "*rho = r + dxi * (1.5 * fr - 0.5 * *frp);", "*rho = r + dxi * fr;"),
     ("sort_unstable_on_ties", "test_oracle_pins.py",
      "dst[k++] = (key[src[j]] < key[src[i]]) ? src[j++] : src[i++];",
      "dst[k++] = (key[src[j]] <= key[src[i]]) ? src[j++] : src[i++];"),
@@ -151,6 +150,17 @@ C_CASES = [
     ("rk4_equal_stage_weights", "test_oracle_rk4.py", "ws[3] = {2.0, 2.0, 1.0}", "ws[3] = {1.0, 1.0, 1.0}"),
     ("rk4_stage_steps", "test_oracle_rk4.py", "cs[3] = {0.5, 0.5, 1.0}", "cs[3] = {0.5, 1.0, 1.0}"),
     ("rk4_first_stage_weight", "test_oracle_rk4.py", "sum_r[id] = ksr[id];", "sum_r[id] = 2.0 * ksr[id];"),
+    # the axis: a stage state below it evaluated mirrored, the derivative
+    # mirrored back (r and u parts), and the reflected AB2 history
+    ("rk4_stage_rho_derivative_not_mirrored_back", "test_oracle_rk4.py",
+     "ksr[id] = sg[id] * (s.u[i] / pb);", "ksr[id] = (s.u[i] / pb);"),
+    ("rk4_stage_u_derivative_not_mirrored_back", "test_oracle_rk4.py",
+     "ksu[id] = sg[id] * (s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]));",
+     "ksu[id] = (s.gam[i] * s.dpr[i] / pb - (s.bp[i] + s.bb[i]));"),
+    ("ab2_axis_history_not_flipped", "test_oracle_pins.py",
+     "        *frp = -*frp;\n        *fup = -*fup;\n", ""),
+    ("ab2_axis_u_history_not_flipped", "test_oracle_pins.py", "        *fup = -*fup;\n", ""),
+    ("ab2_axis_u_not_reflected", "test_oracle_pins.py", "        *ur = -*ur;\n", ""),
     # beam grids (Sec. IV)
     ("grid_extent_without_margin", "test_oracle_grid.py",
      "agR[b] = (agR[b] > 1e-12 ? agR[b] : 1e-12) * (1.0 + 1.0 / nr);",

@@ -100,3 +100,21 @@ def test_rk4_linear_wake_matches_closed_form():
     amp, ph = math.hypot(*c), math.atan2(c[1], c[0])
     assert abs(amp / case["Ez_axis_amplitude"] - 1.0) < 0.01, amp
     assert abs(ph) < 0.01, ph
+
+
+def test_rk4_stays_fourth_order_through_axis_crossings():
+    """The light ring of tests/axis_orbit.py, oscillating through the axis
+    five times: the RK4 march converges to the independently integrated
+    signed orbit at fourth order, which needs each stage state below the
+    axis to be evaluated mirrored and its derivative mirrored back."""
+    import axis_orbit
+    r_ref, u_ref, crossings = axis_orbit.reference()
+    assert crossings >= 4
+    errs = []
+    for dxi in (0.16, 0.08, 0.04):
+        r, u, rmin = axis_orbit.march(dxi, "rk4")
+        assert rmin > 1e-5
+        errs.append(max(np.max(np.abs(r - r_ref)), np.max(np.abs(u - u_ref))))
+    q = [a / b for a, b in zip(errs, errs[1:])]
+    assert all(q_ > 12.0 for q_ in q), (errs, q)
+    assert errs[-1] < 1e-7, errs
