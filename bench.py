@@ -223,6 +223,15 @@ def run_ours(args):
         proc.wait()
         fh.close()
     step_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    # the last timed step's schedule: each wake's march from its own device
+    # times (when its launch began on it, when it finished)
+    wt = [g.march_times() for g in gs]
+    t_first = min(t[0] for t in wt)
+    schedule = {"longest_wake_ms": max(t[1] - t[0] for t in wt) / 1e6,
+                "march_span_ms": (max(t[1] for t in wt) - t_first) / 1e6,
+                "latest_start_of_the_10_longest_ms": sorted(
+                    ((t[1] - t[0], t[0] - t_first) for t in wt), reverse=True)[9][1] / 1e6 if len(wt) >= 10 else None,
+                "note": "device times (globaltimer) of the last timed step; the longest wake is the critical path"}
     pev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     phase_step(pev)
     torch.cuda.synchronize()
@@ -254,8 +263,9 @@ def run_ours(args):
         outs = [{k: torch.empty(g.n_beam, dtype=torch.float32).pin_memory() for k in ("ez", "wr")} for g in gs]
         d2h = sum(g.n_beam for g in gs) * 2 * 4
         def e2e_step():
-            wm.wake_batch_reset(gs, pinned)
-            wm.wake_batch_run(gs)
+            # pinned host beams up, preparation and march pipelined, E_z and
+            # W_r of every beam particle back to pinned host buffers
+            wm.wake_batch_solve(gs, pinned)
             wm.wake_batch_get_beam_fields(gs, [o["ez"] for o in outs], [o["wr"] for o in outs])
 
         e2e_step()
@@ -275,10 +285,23 @@ def run_ours(args):
         e2e = {"value": rs_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_s * 1e3}
 
+    # ---- every batched member against the oracle (host cores), rank 0; the
+    # handles still hold the march of the workload's own beams (the push leg
+    # below moves them)
+    parity = None
+    if not args.skip_parity_sample and rank == 0 and ws == 1:
+        parity = parity_sample_bench(gs, wakes, _host_cores(), stream)
+
     # ---- beam push (the step after a solve): Boris step of every beam particle
     push = None
     if not args.skip_push:
         push = push_bench(args, gs, wakes, stream)
+
+    # ---- the beam stage: the batched march with each slice's beam staged in
+    # shared memory by bulk copies (the default) against plain global loads
+    stage_ab = None
+    if not args.skip_stage_ab:
+        stage_ab = stage_ab_bench(gs, wakes, stream)
 
     # ---- mobile ions: the two-species march on batched wakes
     ions = None
@@ -343,13 +366,18 @@ def run_ours(args):
     peaks = _peaks()
     clocks = _clock_summary(clk_path, local) if rank == 0 else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_tflops = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    # the on-chip peaks measured on this GPU by the library's microbenchmarks
+    onchip = wm.measure_peaks()
+    peak_tflops = onchip["fp32_tflops"]
     march_avg_ms = sum(march_ms) / len(march_ms)
     achieved = FLOPS_PER_RING_SLICE * ring_slices / (march_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "march_fast_kernel<4> + march_cluster_kernel<4> (batched march)", "peak_basis":
-                    f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
+                "kernel": "march_fast_kernel<4> + march_cluster_kernel<4> (batched march)",
+                "peak_basis": "measured: FP32 FMA throughput microbenchmark (wake_measure_peaks), "
+                              f"{onchip['sm_clock_mhz']:.0f} MHz",
+                "nominal_fp32_tflops": SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12,
+                "onchip_peaks": onchip, "schedule": schedule}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -363,12 +391,13 @@ def run_ours(args):
                        "autotune": tuning,
                        "ring_slices_per_step": ring_slices, "wakes_stopped_by_breakdown": stopped,
                        "l2": "inputs larger than L2 (device-resident beams ~1.7 GB per batch)"},
+            "serving": serving, "parity_sample": parity,
             "beam_evaluations": {"value": evals_all * args.steps / (tot_ms_max / 1e3),
                                  "unit": "beam-particle field evaluations/s", "per_step": evals_all,
                                  "note": "step a9: each beam particle binned into a slice its wake marched"},
             "e2e": e2e, "gpu_launches": args.steps * (len(gs) * 7 + n_march_launches),
-            "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain, "serving": serving,
-            "beam_push": push,
+            "roofline": roofline, "cpu_baseline": cpu, "plain_fp64": plain,
+            "beam_push": push, "beam_stage": stage_ab,
             "mobile_ions": _ions_roofline(ions, peak_tflops, sm_mhz),
             "rk4": _alu_roofline(rk4, peak_tflops, sm_mhz, FLOPS_PER_RING_SLICE_RK4, "march_rk4_kernel<PrecMixed>", 1),
             "beam_grid": grid,
@@ -430,6 +459,35 @@ def push_bench(args, gs, wakes, stream):
                            "steps": "batched reset of the pushed beams + march + push"},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "bytes_per_particle": PUSH_BYTES_PER_PARTICLE, "peak_basis": "measured copy (MEASURED_PEAKS.json)"}}
+
+
+def stage_ab_bench(gs, wakes, stream, reps=2):
+    """The batched march (after a batched preparation, CUDA-event timed) of
+    the same wakes with the beam staged by bulk copies and with plain
+    global loads (WAKE_NO_STAGE handles), alternated; best of reps each."""
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    plain = [wm.Wake.from_workload(wk, precision="mixed", stream=stream.cuda_stream, flags=wm.WAKE_NO_STAGE)
+             for wk in wakes]
+    out = {"staged_ms": [], "global_ms": []}
+    for _ in range(reps):
+        for key, hs in (("staged_ms", gs), ("global_ms", plain)):
+            wm.wake_batch_reset(hs)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wm.wake_batch_run(hs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[key].append(e0.elapsed_time(e1))
+    longest = {}
+    for key, hs in (("staged", gs), ("global", plain)):
+        wt = [h.march_times() for h in hs]
+        longest[key] = max(t[1] - t[0] for t in wt) / 1e6
+    for h in plain:
+        h.close()
+    out["staged_over_global"] = min(out["staged_ms"]) / min(out["global_ms"])
+    out["longest_wake_ms"] = longest
+    return out
 
 
 def ions_bench(args, wakes, stream):
@@ -497,7 +555,7 @@ def _alu_roofline(res, peak_tflops, sm_mhz, flops, kernel, species):
     achieved = flops * res["ring_slices"] / (res["march_ms"] / 1e3) / 1e12
     res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                        "frac": achieved / peak_tflops, "traffic": None, "kernel": kernel, "flops_per_ring_slice": flops,
-                       "peak_basis": f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
+                       "peak_basis": "measured: FP32 FMA throughput microbenchmark (wake_measure_peaks)"}
     return res
 
 
@@ -535,7 +593,7 @@ def _ions_roofline(ions, peak_tflops, sm_mhz):
     ions["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                         "frac": achieved / peak_tflops, "traffic": None, "kernel": "march_ions_kernel<PrecMixed>",
                         "flops_per_ring_slice": FLOPS_PER_RING_SLICE_IONS,
-                        "peak_basis": f"FP32 lanes x 2 x SMs x median SM clock under load ({sm_mhz:.0f} MHz)"}
+                        "peak_basis": "measured: FP32 FMA throughput microbenchmark (wake_measure_peaks)"}
     return ions
 
 
@@ -697,6 +755,110 @@ def cpu_sample(seconds: float):
             "sample": f"first {slices} slices of batched wakes 0-{used[-1]} ({done} ring-slices, {dt:.1f} s)"}
 
 
+def _oracle_member_parity(k):
+    """The oracle on batched member k (runs in a spawned process): its
+    status and stopping slice over the whole window, the laminar part of its
+    first 300 slices (before any two rings cross), and for the beam
+    particles of that part E_z, W_r and the number of rings strictly below
+    each (where the particle sits among the rings)."""
+    import oracle
+    wk = W.batched_wake(k)
+    full = oracle.run_wake(wk, beam_fields=())
+    head = W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, min(300, wk.n_steps))
+    r = oracle.run_wake(head, ring_dumps=("r",), beam_fields=("ez", "wr"))
+    rr = r.rings["r"]
+    crossed = np.nonzero(np.any(np.diff(rr, axis=1) <= 0.0, axis=1))[0]
+    lam = int(crossed[0]) if crossed.size else rr.shape[0]
+    if r.status:
+        lam = min(lam, r.fail_slice + 1)
+    xi = np.concatenate([b.xi for b in wk.beams])
+    rb = np.concatenate([b.r for b in wk.beams])
+    sl = np.floor(xi / wk.dxi + 0.5).astype(np.int64)
+    sel = np.nonzero((sl >= 0) & (sl < lam))[0]
+    below = np.empty(sel.shape[0], dtype=np.int32)
+    order = np.argsort(sl[sel], kind="stable")
+    srt = sel[order]
+    bounds = np.searchsorted(sl[srt], np.arange(lam + 1))
+    for s_ in range(lam):
+        a, b = bounds[s_], bounds[s_ + 1]
+        if a < b:
+            below[order[a:b]] = np.searchsorted(np.sort(rr[s_]), rb[srt[a:b]], side="left")
+    return {"k": k, "status": full.status, "fail": full.fail_slice, "laminar": lam, "idx": sel,
+            "ez": r.beam["ez"][sel], "wr": r.beam["wr"][sel], "below": below}
+
+
+def parity_sample_bench(gs, wakes, cores, stream):
+    """Every member of the batch against the oracle (all host cores): the
+    stop (status, slice) of the last march of the handles, and E_z, W_r on
+    the beam particles of each member's laminar head slices (the first 300
+    slices before any two rings cross), norm-wise per member.  A particle
+    is compared where the GPU (in FP32) and the oracle (in FP64) place it
+    among the same number of rings; the few within rounding of a ring, which
+    either side may place on the other side (where d_zeta psi and B^(p) jump
+    by that ring's share), are counted apart."""
+    import concurrent.futures
+    import multiprocessing
+    import torch
+    from paper_2603_16623_gb300 import wake as wm
+    t0 = time.perf_counter()
+    ks = list(range(len(wakes)))
+    ex = concurrent.futures.ProcessPoolExecutor(max_workers=cores, mp_context=multiprocessing.get_context("spawn"))
+    futs = [ex.submit(_oracle_member_parity, k) for k in sorted(ks, key=lambda k: -wakes[k].n_rings * wakes[k].n_steps)]
+    stops = [g.progress() for g in gs]
+    # the head window again, with the ring radii kept
+    heads = [wm.Wake.from_workload(W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, min(300, wk.n_steps)),
+                                   precision="mixed", flags=wm.WAKE_DUMP_RING_R, stream=stream.cuda_stream)
+             for wk in wakes]
+    wm.wake_batch_run(heads)
+    torch.cuda.synchronize()
+    ref = {}
+    for f in futs:
+        r = f.result()
+        ref[r["k"]] = r
+    ex.shutdown()
+    same_status, diffs, errs, left_out = 0, [], {"ez": [], "wr": []}, []
+    for k, (nxt, st, fail), g, wk in zip(ks, stops, heads, wakes):
+        r = ref[k]
+        same_status += int(st == r["status"])
+        if st == r["status"] == 4:
+            diffs.append(fail - r["fail"])
+        if r["idx"].size == 0:
+            g.close()
+            continue
+        rr = g.ring_dumps(which=("r",))["r"]
+        bf = g.beam_fields(which=("ez", "wr"))
+        xi = np.concatenate([b.xi for b in wk.beams])
+        rb = np.concatenate([b.r for b in wk.beams]).astype(np.float32)
+        sl = np.floor(xi / wk.dxi + 0.5).astype(np.int64)
+        sel = r["idx"]
+        below = np.empty(sel.shape[0], dtype=np.int32)
+        order = np.argsort(sl[sel], kind="stable")
+        srt = sel[order]
+        bounds = np.searchsorted(sl[srt], np.arange(r["laminar"] + 1))
+        for s_ in range(r["laminar"]):
+            a, b = bounds[s_], bounds[s_ + 1]
+            if a < b:
+                below[order[a:b]] = np.searchsorted(np.sort(rr[s_]), rb[srt[a:b]], side="left")
+        ok = below == r["below"]
+        left_out.append(1.0 - ok.mean())
+        for f in ("ez", "wr"):
+            den = float(np.max(np.abs(r[f][ok]))) if ok.any() else 0.0
+            d = float(np.max(np.abs(bf[f][sel][ok] - r[f][ok]))) if ok.any() else 0.0
+            errs[f].append(d / den if den > 0 else d)
+        g.close()
+    q = lambda v, p: float(np.percentile(v, p)) if len(v) else None  # noqa: E731
+    return {"members": len(ks), "same_status": same_status,
+            "stopped_at_guard_in_oracle": int(sum(ref[k]["status"] != 0 for k in ks)),
+            "stop_slice_minus_oracles": {"min": min(diffs) if diffs else None, "median": q(diffs, 50),
+                                         "max": max(diffs) if diffs else None, "n": len(diffs)},
+            "laminar_head_errors": {f: {"max": max(v) if v else None, "median": q(v, 50), "p90": q(v, 90)}
+                                    for f, v in errs.items()},
+            "particles_on_a_ring_left_out": {"max": max(left_out) if left_out else None,
+                                             "median": q(left_out, 50)},
+            "note": "mixed path vs the FP64 oracle, norm-wise per member; laminar head = the first 300 "
+                    "slices before any two rings cross", "oracle_s": time.perf_counter() - t0, "cores": cores}
+
+
 def _oracle_share(task):
     """One host core's share of the oracle sample (runs in a spawned
     process): wakes first, first + stride, ... until `seconds` have passed."""
@@ -794,7 +956,8 @@ def run_uniform(args):
     kind = {"ab2": {}, "ions": {"ions": (1.0, 1836.0)}, "rk4": {"integrator": "rk4"}}[args.uniform_kind]
     wk = W.Wake(f"uniform{n}", W.edges_uniform(n, 6.0), [drv], 0.01, slices, **kind)
     n = n * (2 if args.uniform_kind == "ions" else 1)
-    gs = [wm.Wake.from_workload(wk, precision="mixed") for _ in range(copies)]
+    flags = wm.WAKE_NO_STAGE if args.no_stage else 0
+    gs = [wm.Wake.from_workload(wk, precision="mixed", flags=flags) for _ in range(copies)]
     wm.wake_batch_run(gs)
     torch.cuda.synchronize()
     wm.wake_batch_reset(gs)
@@ -805,7 +968,8 @@ def run_uniform(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    print(json.dumps({"case": "uniform", "kind": args.uniform_kind, "rings": n, "slices": slices, "copies": copies,
+    print(json.dumps({"case": "uniform", "kind": args.uniform_kind, "staged": not args.no_stage,
+                      "rings": n, "slices": slices, "copies": copies,
                       "launch": gs[0].launch_config(), "march_ms": ms, "us_per_slice": ms * 1e3 / slices,
                       "ring_slices_per_s": n * slices * copies / (ms / 1e3)}))
 
@@ -834,7 +998,7 @@ def main():
     ap.add_argument("--grid-wakes", type=int, default=64)
     ap.add_argument("--grid-slices", type=int, default=300)
     ap.add_argument("--rk4-wakes", type=int, default=152)
-    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-step-us", type=float, default=4000.0)
@@ -842,6 +1006,10 @@ def main():
                     help="admit while running wakes hold fewer than this many SMs' worth (x SM count); 0: no cap")
     ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
     ap.add_argument("--uniform-kind", default="ab2", choices=["ab2", "ions", "rk4"])
+    ap.add_argument("--no-stage", action="store_true",
+                    help="--uniform: read each slice's beam from global memory (no bulk-copy staging)")
+    ap.add_argument("--skip-stage-ab", action="store_true")
+    ap.add_argument("--skip-parity-sample", action="store_true")
     ap.add_argument("--rings-per-cta", type=int, default=0, help="cluster wakes: at most this many rings per CTA")
     ap.add_argument("--autotune", default=None, choices=["batch", "probe"],
                     help="launch shapes of the batched wakes from a tuning run on this GPU: on the batch's own "

@@ -47,7 +47,8 @@ enum {
     WAKE_ECUDA = 3,       /* a CUDA call failed                               */
     WAKE_ENONFINITE = 4,  /* a slice produced psibar <= 0 or a non-finite field;
                              the wake stopped there (see wake_get_progress)   */
-    WAKE_ETIMEOUT = 5,    /* a bounded device-side wait gave up               */
+    WAKE_ETIMEOUT = 5,    /* a bounded device-side wait gave up: the wake
+                             stopped at that slice (wake_get_progress)      */
     WAKE_EBUSY = 6        /* admission refused (memory budget / capacity)     */
 };
 
@@ -68,10 +69,23 @@ enum {
     WAKE_DUMP_RING_R = 1,      /* keep ring radii at the start of every slice  */
     WAKE_DUMP_RING_FIELDS = 2, /* keep psi, d_rho psi, d_zeta psi, B^(p), B^(b)
                                   and u_r at every ring and slice (tests)      */
-    WAKE_INIT_ASYNC = 4        /* wake_init returns without waiting for the
+    WAKE_INIT_ASYNC = 4,       /* wake_init returns without waiting for the
                                   device: a slice denser than
                                   wake_max_slice_particles() is reported by
                                   wake_get_progress as status WAKE_EINVAL     */
+    WAKE_TEST_STALL_STAGE = 8, /* test only (mixed, on-chip march): of each
+                                  march launch, the bulk copies that stage the
+                                  first beam slice after the launch's first
+                                  slice are never issued, so the march's
+                                  bounded wait for them runs out (~0.25 s) and
+                                  the wake stops with status WAKE_ETIMEOUT
+                                  before that slice: exercises the timeout
+                                  path without any fault or hang             */
+    WAKE_NO_STAGE = 16         /* mixed, on-chip march: read each slice's beam
+                                  arrays from global memory instead of
+                                  staging them in shared memory with bulk
+                                  copies (the same results, bitwise; for
+                                  comparison)                               */
 };
 
 /* Plasma column (Sec. II, ring macroparticles): ring j fills the cell
@@ -181,8 +195,8 @@ wake_status wake_reset(wake_handle *h, const wake_beam_desc *beams, int32_t n_be
    ordered after the work already queued on the handles' (common) stream and
    joined back into it.  beams[i] (may be NULL, or beams itself NULL) gives
    wake i new beam arrays with n_beams[i] species, under wake_reset's rules;
-   with beams given, the call waits once for the device between the slice
-   histogram and the per-slice sort (whose size is the densest slice).
+   they are counted into slices on the device only (the per-slice sort sizes
+   itself there), so the call does not wait for the device.
    Errors: EINVAL (NULL handle, different streams, bad beams), ECUDA. */
 wake_status wake_batch_reset(int32_t n, wake_handle *const *handles, const wake_beam_desc *const *beams,
                              const int32_t *n_beams);
@@ -194,7 +208,10 @@ wake_status wake_batch_reset(int32_t n, wake_handle *const *handles, const wake_
    Asynchronous on the handle's stream; resumable.  A slice that fails the
    guard (psibar <= 0 or a non-finite field) stops the wake: its beam fields
    are written, no push is done, and wake_get_progress reports
-   WAKE_ENONFINITE.  Errors: EINVAL, ECUDA. */
+   WAKE_ENONFINITE.  The on-chip march stages each slice's beam arrays in
+   shared memory with bulk asynchronous copies issued during the previous
+   slice; if its bounded wait for them gives up, the wake stops before that
+   slice and wake_get_progress reports WAKE_ETIMEOUT.  Errors: EINVAL, ECUDA. */
 wake_status wake_step_slices(wake_handle *h, int32_t n_slices);
 
 /* Fields at the current slice (the one the next wake_step_slices would
@@ -206,7 +223,8 @@ wake_status wake_step_slices(wake_handle *h, int32_t n_slices);
    its particles); with mobile ions, the sums of both species.
    r and the outputs are host arrays (device_ptrs = 0) or device arrays
    (device_ptrs = 1); outputs are "real"; any output may be NULL.
-   Errors: EINVAL (n < 0, window finished), ECUDA. */
+   Errors: EINVAL (n < 0, or the window is finished: no slice is left to
+   sample), ENONFINITE (the wake stopped), ECUDA. */
 wake_status wake_fields_at(wake_handle *h, int64_t n, const double *r, void *ez, void *wr,
                            void *bt, void *psi, int32_t device_ptrs);
 
@@ -229,7 +247,8 @@ wake_status wake_batch_get_beam_fields(int32_t n, wake_handle *const *handles, v
    caller order (host arrays of "real", NULL = skip) and, if the handle was
    created with WAKE_DUMP_RING_R and ring_r is not NULL, the ring radii at
    the start of every slice, [n_steps][n_rings] by ring index ("real").
-   Returns ENONFINITE if the wake stopped early (outputs still written). */
+   Returns ENONFINITE if the wake stopped early at the guard (outputs still
+   written), ETIMEOUT if it stopped because a bounded device wait gave up. */
 wake_status wake_run(wake_handle *h, void *beam_ez, void *beam_wr, void *ring_r);
 
 /* Runs the rest of the window of n handles: one launch per kernel
@@ -241,11 +260,23 @@ wake_status wake_run(wake_handle *h, void *beam_ez, void *beam_wr, void *ring_r)
 wake_status wake_batch_run(int32_t n, wake_handle *const *handles);
 
 /* wake_batch_reset(n, handles, NULL, NULL) followed by wake_batch_run, as
-   one pipelined submission: each kernel configuration's march starts as soon
-   as its own wakes are prepared (the costliest configurations' wakes are
-   prepared first), so the preparation of the others overlaps it.  The same
-   results as the two calls.  Errors: as wake_batch_run. */
+   one pipelined submission: wake_batch_solve(n, handles, NULL, NULL). */
 wake_status wake_batch_reset_run(int32_t n, wake_handle *const *handles);
+
+/* Solves n wakes through their whole window in one pipelined submission:
+   for each wake, in order of its predicted march time (longest first), the
+   upload of its new beams (beams[i] not NULL: host arrays under
+   wake_reset's rules, copied on the library's preparation streams, so pinned
+   memory overlaps everything else), its a0/a1 preparation (Sec. II: rings,
+   nearest-slice binning, per-slice radial sort) and then, as soon as the
+   wakes of its launch are prepared, the march.  Nothing waits for the
+   device: the per-slice sort sizes itself on the device.  The same results
+   as wake_batch_reset followed by wake_batch_run.  All handles share
+   precision and stream; beams may be NULL (no new beams for any wake).
+   Errors: EINVAL (NULL handle, mixed precision or stream, bad beams),
+   ECUDA; per-wake outcome via wake_get_progress. */
+wake_status wake_batch_solve(int32_t n, wake_handle *const *handles, const wake_beam_desc *const *beams,
+                             const int32_t *n_beams);
 
 /* Advances every wake by up to max_slices slices (fewer at the end of a
    window or after a stop), in the launches of wake_batch_run.  With
@@ -268,6 +299,15 @@ wake_status wake_batch_progress(int32_t n, wake_handle *const *handles, int32_t 
    allocation wake_init and wake_set_beam_phase_space made for it.  Host
    call, no device work.  Errors: EINVAL (NULL handle or bytes). */
 wake_status wake_get_device_bytes(wake_handle *h, int64_t *bytes);
+
+/* Device times of the last march launch that advanced this wake
+   (synchronises its stream): the GPU's global timer, in ns, when the
+   launch began on the wake and when it finished with it (0, 0 before any
+   march).  The time a batched wake waited for a free SM is its begin
+   minus that of the batch's first wake; serving and launch-shape tuning
+   read per-wake device latency from it.  Errors: EINVAL (NULL handle),
+   ECUDA. */
+wake_status wake_get_march_times(wake_handle *h, int64_t *begin_ns, int64_t *end_ns);
 
 /* Progress of a wake (synchronises its stream): next slice to solve,
    status (OK, ENONFINITE, or EINVAL for a slice denser than
@@ -357,7 +397,8 @@ wake_status wake_batch_push_beam(int32_t n, wake_handle *const *handles, double 
    progress in this process returns WAKE_EBUSY.  Synchronises the handle's
    stream before returning.
    Errors: EINVAL (n < 0 or n > WAKE_STATIC_MAX_QUERIES, NULL r, handle on
-   another device), EBUSY, ENONFINITE (the wake stopped), ECUDA. */
+   another device, window finished), EBUSY, ENONFINITE (the wake stopped),
+   ECUDA. */
 #define WAKE_STATIC_MAX_QUERIES 65536
 wake_status wake_fields_at_static(wake_handle *h, int64_t n, const double *r, void *ez, void *wr,
                                   void *bt, void *psi);

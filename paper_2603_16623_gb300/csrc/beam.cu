@@ -105,14 +105,16 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ slot, int64_t n, 
     }
 }
 
-// one block per slice (grid-stride over slices); m_pad = power of two >= the
-// largest slice, keys double, values caller index, prefix double
+// one block per slice (grid-stride over slices) sorting the slices of
+// min_m < m <= m_pad particles; m_pad a power of two, keys double, values
+// caller index, prefix double.  A slice denser than m_pad is left to a later
+// pass with a larger m_pad, or, in the last pass (last = 1), refuses the wake.
 template <class R>
 __global__ void slice_sort_kernel(const int32_t* __restrict__ off, int32_t n_steps,
                                   const double* __restrict__ r_in, const double* __restrict__ qw_in,
                                   int32_t* __restrict__ idx, R* __restrict__ br, R* __restrict__ bE,
-                                  R* __restrict__ bQs, R* __restrict__ bTot, int32_t m_pad,
-                                  int32_t* __restrict__ ctl, int32_t* __restrict__ inv) {
+                                  R* __restrict__ bQs, R* __restrict__ bTot, int32_t m_pad, int32_t min_m,
+                                  int32_t last, int32_t* __restrict__ ctl, int32_t* __restrict__ inv) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* keys = reinterpret_cast<double*>(smem);
     double* pre = keys + m_pad;
@@ -120,10 +122,11 @@ __global__ void slice_sort_kernel(const int32_t* __restrict__ off, int32_t n_ste
     __shared__ double sbuf[33];
     for (int32_t s = blockIdx.x; s < n_steps; s += gridDim.x) {
         const int32_t b0 = off[s], m = off[s + 1] - b0;
-        if (m > m_pad) {  // slice too dense for the shared-memory sort: refuse the wake
-            if (threadIdx.x == 0) {
-                ctl[1] = 1;
-                ctl[2] = s;
+        if (m <= min_m) continue;  // an earlier pass sorted it
+        if (m > m_pad) {
+            if (last && threadIdx.x == 0) {  // too dense for the shared-memory sort: refuse the wake
+                ctl[CTL_STATUS] = WAKE_STATUS_INVALID;
+                ctl[CTL_FAIL] = s;
                 bTot[s] = 0;
             }
             continue;
@@ -193,7 +196,7 @@ __global__ void scatter_out_kernel(const int32_t* __restrict__ idx, const int32_
 }
 
 __global__ void reset_ctl_kernel(int32_t* ctl) {
-    if (threadIdx.x < 8) ctl[threadIdx.x] = threadIdx.x == 2 ? -1 : 0;
+    if (threadIdx.x < CTL_N) ctl[threadIdx.x] = threadIdx.x == CTL_FAIL ? -1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -249,23 +252,42 @@ cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st) {
 }
 
 template <class R>
-cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
-                              int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t* ctl,
-                              int32_t* inv, cudaStream_t st) {
+static cudaError_t slice_sort_pass(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
+                                   int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t min_m,
+                                   int32_t last, int32_t* ctl, int32_t* inv, cudaStream_t st) {
     // the attribute allows the largest slice the library accepts; a launch
-    // asks only for its own m_pad (a power of two >= the wake's densest slice)
+    // asks only for its own m_pad
     static cudaError_t attr = cudaFuncSetAttribute(slice_sort_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)slice_sort_smem(kSliceSortMaxPad));
     if (attr != cudaSuccess) return attr;
-    if (m_pad > kSliceSortMaxPad) m_pad = kSliceSortMaxPad;
     const size_t sm = slice_sort_smem(m_pad);
-    int threads = m_pad / 2;
-    threads = threads < 64 ? 64 : threads > 512 ? 512 : threads;
+    // one block width for every pass and size: the FP64 charge prefix is
+    // summed in chunks of the block's width, and its rounding must not
+    // depend on how the slices were split into passes
+    const int threads = 256;
     int grid = n_steps < 152 * 8 ? n_steps : 152 * 8;
     if (grid < 1) grid = 1;
-    slice_sort_kernel<R><<<grid, threads, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, ctl,
-                                                    inv);
+    slice_sort_kernel<R><<<grid, threads, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, min_m,
+                                                    last, ctl, inv);
     return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
+                              int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t densest, int32_t* ctl,
+                              int32_t* inv, cudaStream_t st) {
+    int32_t m_pad = 64;
+    if (densest >= 0) {  // known: one pass sized for it
+        while (m_pad < densest && m_pad < kSliceSortMaxPad) m_pad <<= 1;
+        return slice_sort_pass<R>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, -1, 1, ctl, inv, st);
+    }
+    // unknown (counted on the device only): the slices that fit a small
+    // shared-memory sort first, then the denser ones with the largest
+    cudaError_t e = slice_sort_pass<R>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, kSliceSortFirstPad, -1, 0,
+                                       ctl, inv, st);
+    if (e != cudaSuccess) return e;
+    return slice_sort_pass<R>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, kSliceSortMaxPad,
+                              kSliceSortFirstPad, 1, ctl, inv, st);
 }
 
 template <class R>
@@ -309,8 +331,8 @@ cudaError_t launch_species_rmax(const double* r, SpeciesRanges sp, double* rmax,
 __global__ void grid_extent_check_kernel(const double* rmax, int32_t n_species, double grid_rmax, int32_t* ctl) {
     for (int b = 0; b < n_species; ++b)
         if (!(rmax[b] < grid_rmax)) {
-            ctl[1] = 1;   // status EINVAL
-            ctl[2] = -1;  // no slice ran
+            ctl[CTL_STATUS] = 1;  // EINVAL
+            ctl[CTL_FAIL] = -1;   // no slice ran
             return;
         }
 }

@@ -15,12 +15,18 @@ cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, int32_t n_steps, 
 constexpr int kBinPerThread = 16;
 constexpr int32_t kBinSmem = 48 * 1024 / 4;
 size_t slice_sort_smem(int32_t m_pad);
-// the largest slice the per-slice shared-memory sort takes
+// the largest slice the per-slice shared-memory sort takes, and the first
+// pass's size when the densest slice is not known on the host
 constexpr int32_t kSliceSortMaxPad = 8192;
+constexpr int32_t kSliceSortFirstPad = 1024;
 cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st);
+// per-slice radial sort of the binned beam; densest = the particles in the
+// densest slice when the host knows them, else -1 (two passes: the slices of
+// up to kSliceSortFirstPad particles, then the denser ones); a slice denser
+// than kSliceSortMaxPad sets ctl's status to EINVAL
 template <class R>
 cudaError_t launch_slice_sort(const int32_t* off, int32_t n_steps, const double* r_in, const double* qw_in,
-                              int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t m_pad, int32_t* ctl,
+                              int32_t* idx, R* br, R* bE, R* bQs, R* bTot, int32_t densest, int32_t* ctl,
                               int32_t* inv, cudaStream_t st);  // inv (nullable): caller index -> sorted position
 template <class R>
 cudaError_t launch_scatter_out(const int32_t* idx, const int32_t* nbin, int64_t nb_max, const R* src, R* dst,

@@ -8,6 +8,16 @@
 
 namespace gbwake {
 
+// control words of a wake (device ints): next slice, status, failing
+// slice, ring-state buffer, AB2 history present; CTL_T_BEGIN and CTL_T_END
+// (two words each) the device time (globaltimer ns) at which the last march
+// launch began and finished marching the wake
+enum { CTL_NEXT = 0, CTL_STATUS = 1, CTL_FAIL = 2, CTL_BUF = 3, CTL_PREV = 4, CTL_T_BEGIN = 8, CTL_T_END = 10,
+       CTL_N = 16 };
+// the wake status codes the kernels write into CTL_STATUS (the values of
+// include/wake.h's WAKE_EINVAL, WAKE_ENONFINITE, WAKE_ETIMEOUT)
+enum { WAKE_STATUS_INVALID = 1, WAKE_STATUS_NONFINITE = 4, WAKE_STATUS_TIMEOUT = 5 };
+
 // ---------------------------------------------------------------------------
 // float-float ("ff"): an unevaluated sum hi + lo of two floats (~48-bit
 // significand).  Knuth's TwoSum and the FMA-based exact product; nothing here

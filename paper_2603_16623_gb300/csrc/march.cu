@@ -1,4 +1,6 @@
 // march.cu -- instantiations and launchers of the ring kernels.
+#include <algorithm>
+
 #include "march.h"
 
 namespace gbwake {
@@ -147,25 +149,53 @@ cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int3
 
 template <int K>
 static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                                 int32_t max_slices, int32_t mode, int32_t threads, cudaStream_t st) {
-    size_t smem = fast_smem_bytes(threads, K);
+                                 int32_t max_slices, int32_t mode, int32_t threads, int32_t stage_particles,
+                                 cudaStream_t st) {
+    size_t smem = fast_smem_bytes(threads, K) + stage_smem_bytes(stage_particles);
     cudaError_t e =
         cudaFuncSetAttribute(march_fast_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    march_fast_kernel<K><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode);
+    if (e != cudaSuccess) return cudaGetLastError(), e;  // (a refused call leaves no error behind)
+    march_fast_kernel<K><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, stage_particles);
     return cudaGetLastError();
+}
+
+int32_t march_stage_particles(int32_t threads, int32_t k_rings, int32_t cluster_ctas, int32_t want) {
+    if (want <= 0) return 0;
+    // Blocks an SM holds by registers (128 per thread, the kernels' budget
+    // under __launch_bounds__(512)) and by threads.  The SM's 256 KB of L1
+    // and shared memory must keep, as L1, room for the blocks' per-ring
+    // constant tables (48 B per ring, gathered every slice; a stage that
+    // pushed them out of L1 measured 8 % slower on the longest batched wake)
+    // and a margin; each block also has 1 KB reserved and up to 2 KB of
+    // static shared memory.  The stage gets what is left of the block's
+    // share, at most the densest slice.
+    constexpr int32_t kRegsPerSm = 65536, kRegsPerThread = 128, kThreadsPerSm = 2048;
+    constexpr size_t kL1SmemPerSm = 256 * 1024, kMargin = 16 * 1024, kReservedAndStatic = 3 * 1024;
+    constexpr size_t kMaxSmemPerBlock = 232448 - 4096, kRingConstBytes = 48;
+    int32_t blocks = kRegsPerSm / (kRegsPerThread * threads);
+    blocks = std::min(blocks, kThreadsPerSm / threads);
+    if (blocks < 1) blocks = 1;
+    const size_t ring = cluster_ctas > 1 ? cluster_smem_bytes(threads, k_rings) : fast_smem_bytes(threads, k_rings);
+    const size_t l1_keep = (size_t)blocks * kRingConstBytes * threads * k_rings + kMargin;
+    if (l1_keep >= kL1SmemPerSm) return 0;
+    const size_t per_block = std::min((kL1SmemPerSm - l1_keep) / blocks - kReservedAndStatic, kMaxSmemPerBlock);
+    if (per_block <= ring) return 0;
+    int32_t fit = (int32_t)((per_block - ring) / (2 * 3 * 4)) - 9;  // stage_cap_floats slack
+    if (fit < 32) return 0;
+    return std::min(fit, want);
 }
 
 template <int K>
 static cudaError_t launch_cluster_k(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                                    int32_t max_slices, int32_t mode, int32_t threads, int32_t cl, cudaStream_t st) {
-    size_t smem = cluster_smem_bytes(threads, K);
+                                    int32_t max_slices, int32_t mode, int32_t threads, int32_t cl,
+                                    int32_t stage_particles, cudaStream_t st) {
+    size_t smem = cluster_smem_bytes(threads, K) + stage_smem_bytes(stage_particles);
     auto kern = march_cluster_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return cudaGetLastError(), e;  // (a refused call leaves no error behind)
     if (cl > 8) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return cudaGetLastError(), e;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(n_wakes * cl), 1, 1);
@@ -179,22 +209,25 @@ static cudaError_t launch_cluster_k(const WakeDev<PrecMixed>* d_wakes, const int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, d_wakes, d_order, max_slices, mode);
-    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, kern, d_wakes, d_order, max_slices, mode, stage_particles);
+    if (e != cudaSuccess) return cudaGetLastError(), e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                  int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
-                                 cudaStream_t st) {
-    if (k_rings == 4) return launch_cluster_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, st);
-    return launch_cluster_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, st);
+                                 int32_t stage_particles, cudaStream_t st) {
+    if (k_rings == 4)
+        return launch_cluster_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, stage_particles, st);
+    return launch_cluster_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, stage_particles, st);
 }
 
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                              int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, cudaStream_t st) {
-    if (k_rings == 4) return launch_fast_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, st);
-    return launch_fast_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, st);
+                              int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings,
+                              int32_t stage_particles, cudaStream_t st) {
+    if (k_rings == 4)
+        return launch_fast_k<4>(d_wakes, d_order, n_wakes, max_slices, mode, threads, stage_particles, st);
+    return launch_fast_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, stage_particles, st);
 }
 
 // (next slice, status) of n wakes into out[2n], one thread per wake

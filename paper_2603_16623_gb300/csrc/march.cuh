@@ -21,8 +21,6 @@
 
 namespace gbwake {
 
-// control words of a wake (device ints)
-enum { CTL_NEXT = 0, CTL_STATUS = 1, CTL_FAIL = 2, CTL_BUF = 3, CTL_PREV = 4, CTL_N = 8 };
 
 enum { MODE_MARCH = 0, MODE_QUERY = 1 };
 
@@ -33,7 +31,8 @@ template <class P>
 struct WakeDev {
     using R = typename P::R;
     using A = typename P::A;
-    int32_t n, n_steps, n_pad, pad0;
+    int32_t n, n_steps, n_pad;
+    int32_t stage;  // STAGE_* flags (stage.cuh): bulk-copy staging of the beam arrays
     double dxi, density, rho_max;
     const R* w;   // [n] by ring id
     const R* wh;  // [n] by ring id
@@ -97,6 +96,12 @@ __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// records when the march launch began (t0) and now finishes a wake
+__device__ __forceinline__ void put_march_times(int32_t* ctl, uint64_t t0) {
+    reinterpret_cast<unsigned long long*>(ctl + CTL_T_BEGIN)[0] = t0;
+    reinterpret_cast<unsigned long long*>(ctl + CTL_T_END)[0] = global_ns();
 }
 
 // ion column: enclosed charge n min(x, rho_max)^2 / 2 and its potential
@@ -339,6 +344,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
     __shared__ int s_ctl[CTL_N];
     __shared__ int s_stop;
 
+    const uint64_t t_launch = global_ns();
     const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
@@ -716,6 +722,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
     }
     __syncthreads();
     if (tid == 0) {
+        if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_BUF] = buf;
         W.ctl[CTL_PREV] = has_prev;

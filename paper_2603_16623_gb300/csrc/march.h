@@ -17,12 +17,18 @@ cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int3
 // <= 512 threads)
 constexpr int kFastMaxThreads = 512;
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
-                              int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, cudaStream_t st);
+                              int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings,
+                              int32_t stage_particles, cudaStream_t st);
+// particles per slice the on-chip march of `threads` x k_rings stages in
+// shared memory (at most `want`, the densest slice of the launch's wakes),
+// sized so that the stage never lowers the number of blocks an SM holds
+// (clusters > 1: the cluster march's footprint)
+int32_t march_stage_particles(int32_t threads, int32_t k_rings, int32_t cluster_ctas, int32_t want);
 // the cluster march: clusters of cl CTAs of `threads` threads, k_rings = 4
 // or 8 rings per thread
 cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                  int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
-                                 cudaStream_t st);
+                                 int32_t stage_particles, cudaStream_t st);
 // gathers (next slice, status) of n wakes' control words into out[2n]
 cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* out, cudaStream_t st);
 // n cells; n_total = n (electrons) or 2 n (electrons, then mobile ions)

@@ -223,7 +223,7 @@ __device__ void cluster_merge_round(cg::cluster_group& cl, const FastSmem& sm, i
 template <int K>
 __global__ void __launch_bounds__(512)
 march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* __restrict__ order,
-                     int32_t max_slices, int32_t mode) {
+                     int32_t max_slices, int32_t mode, int32_t stage_particles) {
     using R = float;
     using A = ff;
     using SW = Swz<K>;
@@ -238,11 +238,13 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     __shared__ ff x2[16], f2[2];
     __shared__ Mat2<float> x3f[16], x3r[16], f3[4];
     __shared__ ff x4f[16], x4r[16], f4[4];
+    __shared__ __align__(8) uint64_t s_bar[2];
 
     cg::cluster_group cl = cg::this_cluster();
     const int crank = cl.block_rank();
     const int csize = cl.num_blocks();
     const int widx = blockIdx.x / csize;
+    const uint64_t t_launch = global_ns();
     const WakeDev<PrecMixed>& W = wakes[order ? order[widx] : widx];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
@@ -306,6 +308,26 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     const A zeroA = {0.f, 0.f};
     const Mat2<R> I2 = {1, 0, 0, 1};
 
+    // beam stage (march only): every CTA stages the whole slice after its
+    // ring arrays and its count array
+    BeamStage stg;
+    stg.base = reinterpret_cast<float*>(smem + cluster_smem_bytes(T, K));
+    stg.bar = s_bar;
+    stg.cap = (mode == MODE_MARCH && W.nb > 0 && (W.stage & STAGE_OK)) ? stage_cap_floats(stage_particles) : 0;
+    // test only: the first slice staged during the march is never copied
+    bool stall_armed = (W.stage & STAGE_TEST_STALL) != 0;
+    if (stg.cap > 0 && tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
+    uint32_t parity = 0;  // per buffer: the phase its next wait completes
+    int pending = 0;      // per buffer: a staged copy not yet waited for
+    __syncthreads();
+    if (stg.cap > 0 && slice < n_steps &&
+        stage_slice(stg, W, slice, W.boff[slice], W.boff[slice + 1] - W.boff[slice], false))
+        pending |= 1 << (slice & 1);
+
     R rh[K], ur[K];
     int idv[K];
     R ir[K], ipb[K];
@@ -315,11 +337,18 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
 
     const int slice0 = slice;
     uint64_t t_start = 0;
-    bool pending = false;   // the table arrays a, b, T, D, S hold the push of slice - 1
+    bool pending_push = false;  // the table arrays a, b, T, D, S hold the push of slice - 1
     bool blk_bad = false;   // this CTA failed the guard at slice - 1
     int has_prev_before = has_prev;
 
     for (;;) {
+        // the next slice's beam offsets, loaded here so that their latency
+        // overlaps the exchange's cluster barrier
+        int nxt0 = 0, nxt1 = 0;
+        if (stg.cap > 0 && slice + 1 < s_end && slice + 1 < n_steps) {
+            nxt0 = W.boff[slice + 1];
+            nxt1 = W.boff[slice + 2];
+        }
         // ---------------- exchange: order vote, edges, guard of the push
         {
             // time budget: thread 0 of the cluster's rank 0 decides for all
@@ -329,19 +358,33 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 if (slice == slice0) t_start = now;
                 s_stop = slice > slice0 && now - t_start >= (uint64_t)W.budget_ns;
             }
-            const float* vr = pending ? sm.a : sm.rh;  // the state this slice would start from
+            // this slice's staged beam: wait (bounded) before the exchange,
+            // so that a wait that gives up stops every CTA alike
+            bool stalled = false;
+            if (slice < s_end && (pending & (1 << (slice & 1)))) {
+                const int bf = slice & 1;
+                stalled = __syncthreads_or(!mbar_wait_bounded(&s_bar[bf], (parity >> bf) & 1u));
+                parity ^= 1u << bf;
+                pending &= ~(1 << bf);
+            }
+            const float* vr = pending_push ? sm.a : sm.rh;  // the state this slice would start from
             const bool srt = block_sorted<K>(vr, nl, p0);
             const bool stop = W.budget_ns > 0 && crank == 0 && s_stop;
+            // flags: 1 failed the guard at slice - 1, 2 stop (time budget),
+            // 4 this CTA's staging wait gave up
             if (tid < csize)
                 *rmt(cl, &s_xch[crank], tid) = make_float4(srt ? 1.f : 0.f, vr[SW::at(0)], vr[SW::at(nl - 1)],
-                                                           (blk_bad ? 1.f : 0.f) + (stop ? 2.f : 0.f));
+                                                           (blk_bad ? 1.f : 0.f) + (stop ? 2.f : 0.f) +
+                                                               (stalled ? 4.f : 0.f));
         }
         cl.sync();
-        bool any_bad = false, all_sorted = true;
-        const bool stop_now = s_xch[0].w >= 2.f;
+        bool any_bad = false, all_sorted = true, any_stalled = false;
+        const bool stop_now = ((int)s_xch[0].w & 2) != 0;
         for (int r = 0; r < csize; ++r) {
             const float4 v = s_xch[r];
-            if (v.w == 1.f || v.w == 3.f) any_bad = true;
+            const int fl = (int)v.w;
+            if (fl & 1) any_bad = true;
+            if (fl & 4) any_stalled = true;
             if (v.x == 0.f) all_sorted = false;
             if (r + 1 < csize && v.z > s_xch[r + 1].y) all_sorted = false;
         }
@@ -351,7 +394,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             has_prev = has_prev_before;
             break;
         }
-        if (pending) {  // commit the push of slice - 1
+        if (pending_push) {  // commit the push of slice - 1
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 int p = p0 + k;
@@ -364,10 +407,22 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                     sm.fu[a] = sm.S[a];
                 }
             }
-            pending = false;
+            pending_push = false;
             __syncthreads();
         }
+        if (any_stalled) {  // the wake stops before this slice
+            status = WAKE_STATUS_TIMEOUT;
+            fail = slice;
+            break;
+        }
         if (slice >= s_end || stop_now) break;
+        // prefetch the next slice's beam while this one is solved (its
+        // buffer was last read by slice - 1, before the last barrier)
+        if (slice + 1 < s_end && stage_slice(stg, W, slice + 1, nxt0, nxt1 - nxt0, stall_armed)) {
+            pending |= 1 << ((slice + 1) & 1);
+            stall_armed = false;
+        }
+        const int sbuf = slice & 1;
 
         // ---------------- a2: sort by radius if out of order (cluster-wide)
         if (!all_sorted) {
@@ -421,6 +476,11 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             m = W.boff[slice + 1] - b0;
             qtot = W.bTot[slice];
         }
+        // the slice's beam arrays: from this CTA's stage if they were staged
+        SliceBeam sb = {W.br + b0, W.bQs + b0, W.bE + b0};
+        const bool in_stage = stg.cap > 0 && stg.fits(m);
+        if (in_stage)
+            sb = {stg.arr(sbuf, 0) + (b0 & 3), stg.arr(sbuf, 1) + (b0 & 3), stg.arr(sbuf, 2) + (b0 & 3)};
         // Two ways, chosen alike by every CTA: when the slice holds at most a
         // CTA's worth of particles, each CTA counts the particles of its own
         // rings (those between the previous CTA's last radius and its own);
@@ -434,19 +494,23 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         // staged there and every thread finds, for each of its rings, how
         // many particles lie strictly below it (a search for the first ring,
         // short walks for the next); cnt_a then holds that number itself.
-        const bool staged = m > 0 && m <= kFastArrays / 2 * cap;
+        const bool staged = m > 0 && (in_stage || m <= kFastArrays / 2 * cap);
         const bool dist = m > T && csize > 1;
         if (staged) {
-            float* pr = sm.a;  // a, b, T, D, S, psi: 6 cap contiguous floats
-            for (int i0 = tid; i0 < m; i0 += kPartBatch * T) {
-                float v[kPartBatch];  // loads in flight together
+            const float* pr = sb.br;
+            if (!in_stage) {  // copied into the dead tables a, b, T, D, S, psi
+                float* prw = sm.a;
+                for (int i0 = tid; i0 < m; i0 += kPartBatch * T) {
+                    float v[kPartBatch];  // loads in flight together
 #pragma unroll
-                for (int j = 0; j < kPartBatch; ++j) v[j] = i0 + j * T < m ? __ldg(W.br + b0 + i0 + j * T) : 0.f;
+                    for (int j = 0; j < kPartBatch; ++j) v[j] = i0 + j * T < m ? __ldg(W.br + b0 + i0 + j * T) : 0.f;
 #pragma unroll
-                for (int j = 0; j < kPartBatch; ++j)
-                    if (i0 + j * T < m) pr[i0 + j * T] = v[j];
+                    for (int j = 0; j < kPartBatch; ++j)
+                        if (i0 + j * T < m) prw[i0 + j * T] = v[j];
+                }
+                __syncthreads();
+                pr = prw;
             }
-            __syncthreads();
             int L = 0;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -458,7 +522,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             }
             __syncthreads();  // the staged radii are overwritten from a5 on
         } else if (m > 0) {
-            const float* br = W.br + b0;
+            const float* br = sb.br;
             const int mc = dist ? (m + csize - 1) / csize : m;
             const int c0q = dist ? crank * mc : 0;
             const int c1q = dist ? min(m, c0q + mc) : m;
@@ -573,7 +637,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 sm.S[a] = ff_to_f(S);
                 sm.psi[a] = psi;
                 R Q = 0.f;
-                if (m > 0) Q = lb < m ? W.bE[b0 + lb] : qtot;
+                if (m > 0) Q = lb < m ? sb.be[lb] : qtot;
                 bbv[k] = Q * inv_2pi_dxi * ir[k];
                 if (mode == MODE_MARCH && W.dump_psi) {
                     size_t row = (size_t)slice * n + idv[k];
@@ -830,8 +894,8 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                   float xb[kPartBatch], qb_s[kPartBatch];  // loaded together, then evaluated
 #pragma unroll
                   for (int j = 0; j < kPartBatch; ++j) {
-                      xb[j] = qb + j < q1 ? W.br[b0 + qb + j] : INFINITY;
-                      qb_s[j] = qb + j < q1 ? W.bQs[b0 + qb + j] : 0.f;
+                      xb[j] = qb + j < q1 ? sb.br[qb + j] : INFINITY;
+                      qb_s[j] = qb + j < q1 ? sb.qs[qb + j] : 0.f;
                   }
 #pragma unroll
                   for (int j = 0; j < kPartBatch; ++j) {
@@ -945,10 +1009,17 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         }
         has_prev_before = has_prev;
         has_prev = 1;
-        pending = true;
+        pending_push = true;
         ++slice;
         __syncthreads();  // the pushed state is read across threads next
     }
+    // no bulk copy may still write this CTA's shared memory when it exits:
+    // wait (bounded) for any staged slice that was not consumed
+    for (int bf = 0; bf < 2; ++bf)
+        if ((pending & (1 << bf)) && !mbar_wait_bounded(&s_bar[bf], (parity >> bf) & 1u) && status == 0) {
+            status = WAKE_STATUS_TIMEOUT;
+            fail = slice;
+        }
     cl.sync();  // no CTA leaves while a peer may still touch its shared memory
 
     for (int p = tid; p < nl; p += T) {
@@ -961,6 +1032,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         W.rid[buf][g] = sm.id[a];
     }
     if (tid == 0 && crank == 0) {
+        if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_PREV] = has_prev;
         if (status) {

@@ -33,6 +33,7 @@
 #pragma once
 
 #include "march.cuh"
+#include "stage.cuh"
 
 namespace gbwake {
 
@@ -327,17 +328,55 @@ __device__ __forceinline__ void fast_fields_at(const FastSmem& sm, int n, int TK
     fast_fields_region<K>(sm, n, TK, k, x, rmax, half_n, quarter_n, Wtot, Imax, c0, dpr, dpz, bp, psi);
 }
 
+// Beam arrays of the slice being solved: staged in shared memory (TMA bulk
+// copies, prefetched during the previous slice) or read from global memory
+// when the slice is denser than the stage.  Particle q is at index q.
+struct SliceBeam {
+    const float* br;   // radius-sorted radii
+    const float* qs;   // enclosed charge of each particle
+    const float* be;   // exclusive charge prefix
+};
+
+// Issues the stage of slice s (particles [b0, b0 + m)) if it fits into
+// buffer s & 1; every thread can tell from the offsets whether it was staged.
+__device__ __forceinline__ bool stage_slice(const BeamStage& st, const WakeDev<PrecMixed>& W, int s, int b0, int m,
+                                            bool skip) {
+    if (st.cap == 0 || !st.fits(m)) return false;
+    if (threadIdx.x == 0) stage_issue(st, s & 1, W.br, W.bQs, W.bE, b0, m, skip);
+    return true;
+}
+
+// The beam offsets of slices s, s + 1 and s + 2, loaded one slice ahead so
+// that their latency stays off the start of the slice, where the next
+// slice's stage is issued (slices at or beyond the window hold nothing).
+struct SliceOffsets {
+    int o0, o1, o2;
+    __device__ __forceinline__ void load(const WakeDev<PrecMixed>& W, int s, int n_steps) {
+        o0 = s < n_steps ? W.boff[s] : 0;
+        o1 = s + 1 <= n_steps ? W.boff[s + 1] : o0;
+        o2 = s + 2 <= n_steps ? W.boff[s + 2] : o1;
+    }
+    // to slice s + 1
+    __device__ __forceinline__ void advance(const WakeDev<PrecMixed>& W, int s, int n_steps) {
+        o0 = o1;
+        o1 = o2;
+        o2 = s + 3 <= n_steps ? W.boff[s + 3] : o1;
+    }
+};
+
 template <int K>
 __global__ void __launch_bounds__(512)
 march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* __restrict__ order,
-                  int32_t max_slices, int32_t mode) {
+                  int32_t max_slices, int32_t mode, int32_t stage_particles) {
     using R = float;
     using A = ff;
     using SW = Swz<K>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
     __shared__ int s_stop;
+    __shared__ __align__(8) uint64_t s_bar[2];
 
+    const uint64_t t_launch = global_ns();
     const WakeDev<PrecMixed>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
@@ -385,6 +424,26 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
     }
     __syncthreads();
 
+    // beam stage (march only): two buffers after the ring arrays
+    BeamStage stg;
+    stg.base = reinterpret_cast<float*>(smem + fast_smem_bytes(T, K));
+    stg.bar = s_bar;
+    stg.cap = (mode == MODE_MARCH && W.nb > 0 && (W.stage & STAGE_OK)) ? stage_cap_floats(stage_particles) : 0;
+    // test only: the first slice staged during the march is never copied
+    bool stall_armed = (W.stage & STAGE_TEST_STALL) != 0;
+    if (stg.cap > 0 && tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
+    uint32_t parity = 0;     // per buffer: the phase its next wait completes
+    int pending = 0;         // per buffer: a staged copy not yet waited for
+    SliceOffsets so;
+    if (W.nb > 0) so.load(W, slice, n_steps);
+    else so = {0, 0, 0};
+    __syncthreads();
+    if (slice < n_steps && stage_slice(stg, W, slice, so.o0, so.o1 - so.o0, false)) pending |= 1 << (slice & 1);
+
     const double dens_d = W.density, rmax_d = W.rho_max;
     const R rmax = (R)rmax_d;
     const R half_n = (R)(0.5 * dens_d), quarter_n = (R)(0.25 * dens_d);
@@ -426,6 +485,12 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             if (p0 + K < n && sm.rh[SW::at(p0 + K)] < prev) ok = false;
             const bool in_order = __syncthreads_and(ok);
             if (W.budget_ns > 0 && s_stop) break;
+            // prefetch the next slice's beam while this one is solved (its
+            // buffer was last read by slice - 1, before the barrier above)
+            if (slice + 1 < s_end && stage_slice(stg, W, slice + 1, so.o1, so.o2 - so.o1, stall_armed)) {
+                pending |= 1 << ((slice + 1) & 1);
+                stall_armed = false;
+            }
             if (!in_order) resort<K>(sm, n, W.n_pad, cap);
         }
 #pragma unroll
@@ -446,9 +511,23 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
         int b0 = 0, m = 0;
         R qtot = 0;
         if (W.nb > 0 && slice < n_steps) {
-            b0 = W.boff[slice];
-            m = W.boff[slice + 1] - b0;
+            b0 = so.o0;
+            m = so.o1 - b0;
             qtot = W.bTot[slice];
+        }
+        SliceBeam sb = {W.br + b0, W.bQs + b0, W.bE + b0};
+        if (pending & (1 << (slice & 1))) {  // staged: wait (bounded) for its copies
+            const int bf = slice & 1;
+            const bool got = mbar_wait_bounded(&s_bar[bf], (parity >> bf) & 1u);
+            parity ^= 1u << bf;
+            pending &= ~(1 << bf);
+            if (__syncthreads_or(!got)) {
+                status = WAKE_STATUS_TIMEOUT;
+                fail = slice;
+                break;
+            }
+            const int off = b0 & 3;
+            sb = {stg.arr(bf, 0) + off, stg.arr(bf, 1) + off, stg.arr(bf, 2) + off};
         }
         if (m > 0) {
             for (int i = tid; i < cap; i += T) t_cnt[i] = 0;
@@ -463,7 +542,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             for (int qb = tid * per; qb < q1 && lo < n; qb += kPartBatch) {
                 float xb[kPartBatch];  // radii loaded together, then walked
 #pragma unroll
-                for (int j = 0; j < kPartBatch; ++j) xb[j] = qb + j < q1 ? W.br[b0 + qb + j] : INFINITY;
+                for (int j = 0; j < kPartBatch; ++j) xb[j] = qb + j < q1 ? sb.br[qb + j] : INFINITY;
 #pragma unroll
                 for (int j = 0; j < kPartBatch; ++j) {
                     lo = ring_rank_from<K>(sm.rh, n, lo, xb[j], false);
@@ -535,7 +614,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 sm.S[a] = ff_to_f(S);
                 sm.psi[a] = psi;
                 R Q = 0.f;
-                if (m > 0) Q = lb < m ? W.bE[b0 + lb] : qtot;
+                if (m > 0) Q = lb < m ? sb.be[lb] : qtot;
                 bbv[k] = Q * inv_2pi_dxi * ir[k];
                 if (mode == MODE_MARCH && W.dump_psi) {
                     size_t row = (size_t)slice * n + idv[k];
@@ -724,8 +803,8 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
               float xb[kPartBatch], qb_s[kPartBatch];  // loaded together, then evaluated
 #pragma unroll
               for (int j = 0; j < kPartBatch; ++j) {
-                  xb[j] = qb + j < q1 ? W.br[b0 + qb + j] : 0.f;
-                  qb_s[j] = qb + j < q1 ? W.bQs[b0 + qb + j] : 0.f;
+                  xb[j] = qb + j < q1 ? sb.br[qb + j] : 0.f;
+                  qb_s[j] = qb + j < q1 ? sb.qs[qb + j] : 0.f;
               }
 #pragma unroll
               for (int j = 0; j < kPartBatch; ++j) {
@@ -818,8 +897,19 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             }
         }
         has_prev = 1;
+        if (W.nb > 0) so.advance(W, slice, n_steps);
         __syncthreads();
     }
+
+    // ---- no bulk copy may still write this block's shared memory when it
+    // exits: wait (bounded) for any staged slice that was not consumed
+    for (int bf = 0; bf < 2; ++bf)
+        if (pending & (1 << bf)) {
+            if (!mbar_wait_bounded(&s_bar[bf], (parity >> bf) & 1u) && status == 0) {
+                status = WAKE_STATUS_TIMEOUT;
+                fail = slice;
+            }
+        }
 
     // ---- store the ring state back (sorted order, same buffer)
     __syncthreads();
@@ -833,6 +923,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
         W.rid[buf][p] = sm.id[a];
     }
     if (tid == 0) {
+        if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_PREV] = has_prev;
         if (status) {

@@ -109,6 +109,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
     __shared__ int s_ctl[CTL_N];
     __shared__ int s_stop;
 
+    const uint64_t t_launch = global_ns();
     const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
@@ -469,6 +470,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
     }
     __syncthreads();
     if (tid == 0) {
+        if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_BUF] = buf;
         W.ctl[CTL_PREV] = has_prev;

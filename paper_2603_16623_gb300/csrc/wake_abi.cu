@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -93,9 +94,8 @@ struct wake_handle {
     int32_t fast_threads = 0;               // > 0: the on-chip march serves this wake
     int32_t fast_k = 8;                     // its rings per thread
     int32_t fast_cl = 1;                    // CTAs per wake (thread-block cluster if > 1)
-    int32_t slice_max = kMaxSliceParticles; // particles in the densest slice (host count)
-    bool recount = false;                   // the beam moved on the device (push): the next
-                                            // preparation reads the densest slice back
+    int32_t slice_max = kMaxSliceParticles; // particles in the densest slice (host count), or
+                                            // -1: not known on the host (new beams, a push)
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
 };
 
@@ -213,7 +213,7 @@ wake_status check_new_beams(const wake_handle* h, const wake_beam_desc* beams, i
 wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_beams, cudaStream_t st,
                          bool count_on_host = true) {
     if (!beams) return WAKE_OK;
-    if (count_on_host) h->slice_max = densest_slice(beams, n_beams, h->dxi, h->n_steps);
+    h->slice_max = count_on_host ? densest_slice(beams, n_beams, h->dxi, h->n_steps) : -1;
     int64_t off = 0;
     for (int32_t b = 0; b < n_beams; ++b) {
         const size_t bytes = beams[b].n * sizeof(double);
@@ -231,11 +231,10 @@ wake_status upload_beams(wake_handle* h, const wake_beam_desc* beams, int32_t n_
 template <class P>
 wake_status prepare_sort(wake_handle* h, cudaStream_t st);
 
-// First part of the a0/a1 preparation (control words, rings, charge, slice
-// histogram and offsets, whose maximum lands in d_dmax); with split = false
-// also the second part (prepare_sort).
+// The a0/a1 preparation: control words, rings, charge, slice histogram and
+// offsets (whose maximum lands in d_dmax), then prepare_sort.
 template <class P>
-wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
+wake_status prepare_impl(wake_handle* h, cudaStream_t st) {
     using R = typename P::R;
     WakeDev<P> D;
     std::memcpy(&D, h->desc_host.data(), sizeof(D));
@@ -267,12 +266,12 @@ wake_status prepare_impl(wake_handle* h, cudaStream_t st, bool split = false) {
         }
         WK_CUDA(launch_excl_scan(h->d_cnt, ns, h->d_boff, h->d_dmax, st));
     }
-    if (!split) return prepare_sort<P>(h, st);
-    return WAKE_OK;
+    return prepare_sort<P>(h, st);
 }
 
 // Second part of the a1 preparation: scatter into slices and the per-slice
-// radial sort, sized by h->slice_max; cleared outputs and dumps.
+// radial sort (sized by h->slice_max when the host knows it, else in two
+// passes sized on the device); cleared outputs and dumps.
 template <class P>
 wake_status prepare_sort(wake_handle* h, cudaStream_t st) {
     using R = typename P::R;
@@ -282,14 +281,12 @@ wake_status prepare_sort(wake_handle* h, cudaStream_t st) {
     const size_t rb = h->real_bytes();
     if (h->nb_total > 0) {
         WK_CUDA(launch_bin_scatter(h->d_slot, h->nb_total, ns, h->d_boff, h->d_fill, h->d_bidx, st));
-        // sort size: a power of two >= the densest slice (a slice beyond
-        // kMaxSliceParticles is flagged by the kernel)
-        const int32_t m_pad = h->slice_max > kMaxSliceParticles ? kMaxSliceParticles
-                                                                 : next_pow2(std::max(h->slice_max, 64));
+        // (a slice beyond kMaxSliceParticles is flagged by the kernel)
+        const int32_t densest = h->slice_max > kMaxSliceParticles ? kMaxSliceParticles : h->slice_max;
         WK_CUDA(cudaMemsetAsync(h->d_inv, 0xff, (size_t)h->nb_total * sizeof(int32_t), st));
         WK_CUDA(launch_slice_sort<R>(h->d_boff, ns, h->d_r, h->d_qw, h->d_bidx, const_cast<R*>(D.br),
                                      const_cast<R*>(D.bE), const_cast<R*>(D.bQs), const_cast<R*>(D.bTot),
-                                     m_pad, h->d_ctl, h->d_inv, st));
+                                     densest, h->d_ctl, h->d_inv, st));
         for (int k = 0; k < 4; ++k)
             WK_CUDA(cudaMemsetAsync(h->d_out[k], 0, (size_t)h->nb_total * rb, st));
     }
@@ -380,13 +377,18 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
     D.boff = h->d_boff;
     R *bTot, *br, *bE, *bQs;
     WK_TRY(dalloc_t(h, (size_t)ns, &bTot));
-    WK_TRY(dalloc_t(h, (size_t)nb, &br));
-    WK_TRY(dalloc_t(h, (size_t)nb, &bE));
-    WK_TRY(dalloc_t(h, (size_t)nb, &bQs));
+    // 4 elements of padding: a bulk copy of a slice may read up to 3 past
+    // the last particle (its span is rounded out to 16 bytes)
+    WK_TRY(dalloc_t(h, (size_t)nb + 4, &br));
+    WK_TRY(dalloc_t(h, (size_t)nb + 4, &bE));
+    WK_TRY(dalloc_t(h, (size_t)nb + 4, &bQs));
     D.bTot = bTot;
     D.br = br;
     D.bE = bE;
     D.bQs = bQs;
+    auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    D.stage = (aligned16(br) && aligned16(bE) && aligned16(bQs) && !(h->flags & WAKE_NO_STAGE)) ? STAGE_OK : 0;
+    if (h->flags & WAKE_TEST_STALL_STAGE) D.stage |= STAGE_TEST_STALL;
     if (nb > 0) {
         WK_TRY(dalloc_t(h, (size_t)nb, &h->d_xi));
         WK_TRY(dalloc_t(h, (size_t)nb, &h->d_r));
@@ -527,45 +529,65 @@ wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want
     return WAKE_OK;
 }
 
-// Auxiliary streams for concurrent batched launches of different kernel
-// configurations.  The first kHighPrioStreams get the device's greatest
-// priority so that the blocks of the longest buckets (launched first) are
-// dispatched ahead of short ones when the SMs are full.
-constexpr int kAuxStreams = 32, kHighPrioStreams = 4;
-cudaError_t aux_stream(int i, cudaStream_t* out) {
+// Auxiliary streams for concurrent batched launches, kStreamsPerLevel per
+// priority level: level 0 gets the device's greatest priority, the last
+// level its least, the levels between are spread over the range.  Level 0
+// runs the preparations (short kernels that every march waits for: a
+// preparation that waited behind pending march blocks would hold back its
+// wake's march); levels 1.. the marches by tier, so that when the SMs are
+// full the pending blocks of the longest wakes are dispatched first.
+constexpr int kPrioLevels = 4, kStreamsPerLevel = 16, kAuxStreams = kPrioLevels * kStreamsPerLevel;
+constexpr int kTiers = kPrioLevels - 1;
+cudaError_t level_stream(int level, int i, cudaStream_t* out) {
     static cudaStream_t pool[kAuxStreams] = {nullptr};
     static int pool_dev[kAuxStreams];
+    static std::mutex mu;
+    const int slot = level * kStreamsPerLevel + i % kStreamsPerLevel;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (pool[i] && pool_dev[i] != dev) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (pool[slot] && pool_dev[slot] != dev) {
         // created for another device: make a new one on the current device
-        pool[i] = nullptr;
+        pool[slot] = nullptr;
     }
-    if (!pool[i]) {
+    if (!pool[slot]) {
         int least = 0, greatest = 0;
         e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e != cudaSuccess) return e;
-        e = cudaStreamCreateWithPriority(&pool[i], cudaStreamNonBlocking, i < kHighPrioStreams ? greatest : least);
+        // greatest is the numerically lowest value
+        const int prio = greatest + (least - greatest) * level / (kPrioLevels - 1);
+        e = cudaStreamCreateWithPriority(&pool[slot], cudaStreamNonBlocking, prio);
         if (e != cudaSuccess) {
-            pool[i] = nullptr;
+            pool[slot] = nullptr;
             return e;
         }
-        pool_dev[i] = dev;
+        pool_dev[slot] = dev;
     }
-    *out = pool[i];
+    *out = pool[slot];
     return cudaSuccess;
 }
+// the preparation streams
+cudaError_t aux_stream(int i, cudaStream_t* out) { return level_stream(0, i, out); }
+// the march streams of a tier
+cudaError_t tier_stream(int tier, int i, cudaStream_t* out) { return level_stream(1 + tier, i, out); }
+
+// Particles per slice the march should be able to stage for this wake: its
+// densest slice, or the most the library accepts when that is not known.
+int32_t stage_want(const wake_handle* h) { return h->slice_max < 0 ? kMaxSliceParticles : h->slice_max; }
 
 template <class P>
 wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (h->fast_threads > 0 && h->fast_cl > 1) {
-            WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->fast_cl, h->st));
+            const int32_t stage = march_stage_particles(h->fast_threads, h->fast_k, h->fast_cl, stage_want(h));
+            WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->fast_cl,
+                                         stage, h->st));
             return WAKE_OK;
         }
         if (h->fast_threads > 0) {
-            WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->st));
+            const int32_t stage = march_stage_particles(h->fast_threads, h->fast_k, 1, stage_want(h));
+            WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, stage, h->st));
             return WAKE_OK;
         }
     }
@@ -586,6 +608,16 @@ wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_sli
 wake_status check_handle(const wake_handle* h) {
     if (!h) return fail(WAKE_EINVAL, "null handle");
     return WAKE_OK;
+}
+
+// The status of a stopped wake as an error of entry point `what`.
+wake_status stopped(int32_t status, const char* what) {
+    if (status == WAKE_ETIMEOUT)
+        return fail(WAKE_ETIMEOUT, "%s: the wake stopped: a bounded device wait for a staged beam slice gave up",
+                    what);
+    if (status == WAKE_EINVAL)
+        return fail(WAKE_EINVAL, "%s: the wake stopped: a slice is denser than the library accepts", what);
+    return fail(WAKE_ENONFINITE, "%s: the wake stopped at a non-finite slice", what);
 }
 
 template <class P>
@@ -720,12 +752,15 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     cudaError_t e;
     if constexpr (std::is_same<P, PrecMixed>::value) {
         if (fast_threads > 0) {
+            int32_t densest = 0;
+            for (const wake_handle* h : hs) densest = std::max(densest, stage_want(h));
+            const int32_t stage = march_stage_particles(fast_threads, hs[0]->fast_k, hs[0]->fast_cl, densest);
             if (hs[0]->fast_cl > 1)
                 e = launch_march_cluster(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                                         fast_threads, hs[0]->fast_k, hs[0]->fast_cl, st);
+                                         fast_threads, hs[0]->fast_k, hs[0]->fast_cl, stage, st);
             else
                 e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                                      fast_threads, hs[0]->fast_k, st);
+                                      fast_threads, hs[0]->fast_k, stage, st);
             cudaFreeAsync(d_buf, st);
             if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
             return WAKE_OK;
@@ -747,56 +782,85 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     return WAKE_OK;
 }
 
-// The handles grouped by kernel configuration (one march launch each),
-// the bucket with the longest critical path (slices x rings per CTA of its
-// longest wake) first.
-std::vector<std::vector<wake_handle*>> bucket_handles(int32_t n, wake_handle* const* hs) {
-    std::vector<int32_t> keys;
-    std::vector<std::vector<wake_handle*>> buckets;
+// Predicted march time of a wake per slice, in microseconds, on GB300
+// (single-wake latency; the batch's dispatch order only needs it to rank
+// wakes).  Fitted to the march times of the 256 batched wakes measured one
+// by one (wake_get_march_times): one CTA of R rings (4 per thread) ~ 11 +
+// 9 R/2048 us per slice; a cluster of cl CTAs of R rings each ~ 16.3 + 1.6
+// cl + 8.9 R/1024 us (its cluster barriers and exchanges).  The one-CTA
+// kernels with state in global memory grow with the rings per thread.
+double predicted_slice_us(const wake_handle* h) {
+    if (h->fast_threads > 0) {
+        const double R = (double)h->fast_threads * h->fast_k;
+        if (h->fast_cl > 1) return 16.3 + 1.6 * h->fast_cl + 8.9 * R / 1024.0;
+        return 11.0 + 9.0 * R / 2048.0;
+    }
+    const double per_thread = (double)h->n / h->threads;
+    return (h->rk4 ? 4.0 : 1.0) * (20.0 + 6.0 * per_thread);
+}
+
+double predicted_ms(const wake_handle* h) { return h->n_steps * predicted_slice_us(h) * 1e-3; }
+
+// A batch as march launches: wakes of one kernel configuration share a
+// launch, split by predicted time into tiers (at least half of the longest
+// wake's time; a fifth of it; the rest), so that the long wakes of every
+// configuration are dispatched before the short ones of any.  Groups come
+// tier by tier, the group with the longest wake first within a tier.
+struct LaunchGroup {
+    std::vector<wake_handle*> hs;
+    int tier = 0;
+    double t_max = 0.0;
+};
+
+std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
+    double t_all = 0.0;
+    for (int32_t i = 0; i < n; ++i) t_all = std::max(t_all, predicted_ms(hs[i]));
+    std::vector<std::pair<int64_t, int>> keys;  // (configuration, tier)
+    std::vector<LaunchGroup> groups;
     for (int32_t i = 0; i < n; ++i) {
-        int32_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
+        int64_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
         // the one-CTA kernels (plain, two-species, RK4, grids) by their block size
         if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * (hs[i]->grid_nr > 0) +
                                           8 * hs[i]->threads);
-        auto it = std::find(keys.begin(), keys.end(), key);
+        const double t = predicted_ms(hs[i]);
+        const int tier = t >= 0.5 * t_all ? 0 : (t >= 0.2 * t_all ? 1 : 2);
+        auto it = std::find(keys.begin(), keys.end(), std::make_pair(key, tier));
         if (it == keys.end()) {
-            keys.push_back(key);
-            buckets.emplace_back();
+            keys.emplace_back(key, tier);
+            groups.emplace_back();
+            groups.back().tier = tier;
             it = keys.end() - 1;
         }
-        buckets[it - keys.begin()].push_back(hs[i]);
+        LaunchGroup& g = groups[it - keys.begin()];
+        g.hs.push_back(hs[i]);
+        g.t_max = std::max(g.t_max, t);
     }
-    std::vector<double> cost(buckets.size(), 0.0);
-    for (size_t b = 0; b < buckets.size(); ++b)
-        for (const wake_handle* h : buckets[b]) {
-            const int32_t cl = (h->fast_threads > 0 && h->fast_cl > 1) ? h->fast_cl : 1;
-            cost[b] = std::max(cost[b], (double)h->n_steps * (double)(h->n + cl - 1) / cl);
-        }
-    std::vector<size_t> border(buckets.size());
-    for (size_t b = 0; b < border.size(); ++b) border[b] = b;
-    std::stable_sort(border.begin(), border.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-    std::vector<std::vector<wake_handle*>> out;
-    for (size_t b : border) out.push_back(std::move(buckets[b]));
-    return out;
+    std::stable_sort(groups.begin(), groups.end(), [](const LaunchGroup& a, const LaunchGroup& b) {
+        return a.tier != b.tier ? a.tier < b.tier : a.t_max > b.t_max;
+    });
+    return groups;
 }
 
 template <class P>
 wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, int64_t budget_ns) {
     cudaStream_t st = hs[0]->st;
-    // one bucket per kernel configuration, each on its own stream, ordered
-    // after the work already queued on the handles' stream and joined back
-    std::vector<std::vector<wake_handle*>> buckets = bucket_handles(n, hs);
-    if (buckets.size() == 1) return batch_bucket<P>(buckets[0], buckets[0][0]->fast_threads, st, max_slices, budget_ns);
+    // one launch per group, each on its own stream of its tier's priority,
+    // ordered after the work already queued on the handles' stream and
+    // joined back into it
+    std::vector<LaunchGroup> groups = plan_launches(n, hs);
+    if (groups.size() == 1) return batch_bucket<P>(groups[0].hs, groups[0].hs[0]->fast_threads, st, max_slices, budget_ns);
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
     wake_status res = WAKE_OK;
-    for (size_t i = 0; i < buckets.size(); ++i) {
+    int in_tier[kTiers] = {0, 0, 0};
+    for (size_t i = 0; i < groups.size(); ++i) {
         cudaStream_t as = nullptr;
-        WK_CUDA(aux_stream((int)(i % kAuxStreams), &as));
+        const int tier = groups[i].tier;
+        WK_CUDA(tier_stream(tier, in_tier[tier]++, &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
-        wake_status r = batch_bucket<P>(buckets[i], buckets[i][0]->fast_threads, as, max_slices, budget_ns);
+        wake_status r = batch_bucket<P>(groups[i].hs, groups[i].hs[0]->fast_threads, as, max_slices, budget_ns);
         if (r != WAKE_OK) res = r;
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -809,22 +873,24 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
 }
 
 // The a0/a1 preparation and the whole-window march of n wakes, pipelined:
-// the preparations run on half of the auxiliary streams, the costliest
-// buckets' wakes first, and each bucket's march waits only for its own
-// wakes' preparations (on the other half), so that the heavy marches start
-// while the light wakes are still being prepared.  Everything is ordered
-// after the work queued on the handles' stream and joined back into it.
+// the preparations run on the greatest-priority streams, the longest
+// groups' wakes first, and each group's march (on a stream of its tier)
+// waits only for its own wakes' preparations, so that the long marches
+// start while the short wakes are still being prepared.  Everything is
+// ordered after the work queued on the handles' stream and joined back
+// into it.
 template <class P>
-wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs) {
+wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs, const wake_beam_desc* const* beams = nullptr,
+                                 const int32_t* n_beams = nullptr) {
     cudaStream_t st = hs[0]->st;
-    std::vector<std::vector<wake_handle*>> buckets = bucket_handles(n, hs);
-    constexpr int kPrepStreams = kAuxStreams / 2;
+    std::vector<LaunchGroup> groups = plan_launches(n, hs);
+    constexpr int kPrepStreams = kStreamsPerLevel;
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
     for (int j = 0; j < kPrepStreams; ++j) {
         cudaStream_t ps = nullptr;
-        WK_CUDA(aux_stream(kAuxStreams - 1 - j, &ps));
+        WK_CUDA(aux_stream(j, &ps));
         WK_CUDA(cudaStreamWaitEvent(ps, start, 0));
     }
     std::vector<cudaEvent_t> events;
@@ -834,19 +900,23 @@ wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs) {
     };
     wake_status res = WAKE_OK;
     int next_prep = 0;
-    for (size_t i = 0; i < buckets.size() && res == WAKE_OK; ++i) {
+    int in_tier[kTiers] = {0, 0, 0};
+    for (size_t i = 0; i < groups.size() && res == WAKE_OK; ++i) {
         cudaStream_t ms = nullptr;
-        if (aux_stream((int)(i % kPrepStreams), &ms) != cudaSuccess) {
+        const int tier = groups[i].tier;
+        if (tier_stream(tier, in_tier[tier]++, &ms) != cudaSuccess) {
             res = fail(WAKE_ECUDA, "wake_batch_reset_run: no stream");
             break;
         }
         cudaStreamWaitEvent(ms, start, 0);
-        for (wake_handle* h : buckets[i]) {
+        for (wake_handle* h : groups[i].hs) {
             cudaStream_t ps = nullptr;
-            aux_stream(kAuxStreams - 1 - (next_prep++ % kPrepStreams), &ps);
-            res = prepare_impl<P>(h, ps);
+            aux_stream(next_prep++ % kPrepStreams, &ps);
+            // the wake's new beams (its index in the caller's arrays)
+            const int32_t k = (int32_t)(std::find(hs, hs + n, h) - hs);
+            if (beams && beams[k]) res = upload_beams(h, beams[k], n_beams[k], ps, false);
+            if (res == WAKE_OK) res = prepare_impl<P>(h, ps);
             if (res != WAKE_OK) break;
-            h->recount = false;
             cudaEvent_t ready;
             if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
                 res = fail(WAKE_ECUDA, "wake_batch_reset_run: event creation failed");
@@ -857,7 +927,7 @@ wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs) {
             cudaStreamWaitEvent(ms, ready, 0);
         }
         if (res != WAKE_OK) break;
-        res = batch_bucket<P>(buckets[i], buckets[i][0]->fast_threads, ms, 1 << 30, 0);
+        res = batch_bucket<P>(groups[i].hs, groups[i].hs[0]->fast_threads, ms, 1 << 30, 0);
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
         events.push_back(done);
@@ -867,7 +937,7 @@ wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs) {
     // the preparation streams join back too (also after an error)
     for (int j = 0; j < kPrepStreams; ++j) {
         cudaStream_t ps = nullptr;
-        if (aux_stream(kAuxStreams - 1 - j, &ps) != cudaSuccess) continue;
+        if (aux_stream(j, &ps) != cudaSuccess) continue;
         cudaEvent_t done;
         if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) continue;
         events.push_back(done);
@@ -1078,8 +1148,8 @@ wake_status push_enqueue(wake_handle* const* hs, int32_t n, double dt, cudaStrea
     cudaFreeAsync(buf, st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "wake_push_beam: %s", cudaGetErrorString(e));
     // particles may have changed slices: the next binning sizes its sort
-    // from the device's count, not the one taken before the push
-    for (int32_t i = 0; i < n; ++i) hs[i]->recount = true;
+    // on the device, not from the count taken before the push
+    for (int32_t i = 0; i < n; ++i) hs[i]->slice_max = -1;
     return WAKE_OK;
 }
 
@@ -1238,21 +1308,6 @@ wake_status wake_reset(wake_handle* h, const wake_beam_desc* beams, int32_t n_be
     WK_TRY(check_handle(h));
     WK_TRY(check_new_beams(h, beams, n_beams));
     WK_TRY(upload_beams(h, beams, n_beams, h->st));
-    if (h->recount && !beams) {
-        // the pushed beam: histogram, then the densest slice from the device
-        if (h->prec == WAKE_FP64) WK_TRY(prepare_impl<PrecF64>(h, h->st, true));
-        else WK_TRY(prepare_impl<PrecMixed>(h, h->st, true));
-        if (h->nb_total > 0) {
-            int32_t dmax = 0;
-            WK_CUDA(cudaMemcpyAsync(&dmax, h->d_dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
-            WK_CUDA(cudaStreamSynchronize(h->st));
-            h->slice_max = dmax;
-        }
-        h->recount = false;
-        if (h->prec == WAKE_FP64) return prepare_sort<PrecF64>(h, h->st);
-        return prepare_sort<PrecMixed>(h, h->st);
-    }
-    h->recount = false;
     if (h->prec == WAKE_FP64) return prepare_impl<PrecF64>(h, h->st);
     return prepare_impl<PrecMixed>(h, h->st);
 }
@@ -1276,44 +1331,21 @@ wake_status wake_batch_reset(int32_t n, wake_handle* const* handles, const wake_
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
-    const int32_t n_streams = n < kAuxStreams ? n : kAuxStreams;
+    const int32_t n_streams = n < kStreamsPerLevel ? n : kStreamsPerLevel;
     wake_status res = WAKE_OK;
     for (int32_t j = 0; j < n_streams; ++j) {
         cudaStream_t as = nullptr;
         WK_CUDA(aux_stream(j, &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
     }
-    // with new beams, or beams moved by a push, the densest slice is read back
-    // from the device between the histogram and the sort (one
-    // synchronisation for the whole batch)
-    bool split = beams != nullptr;
-    for (int32_t i = 0; i < n; ++i) split = split || handles[i]->recount;
+    // new beams are counted on the device only (the per-slice sort sizes
+    // itself there): nothing here waits for the device
     for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
         wake_handle* h = handles[i];
         cudaStream_t as = nullptr;
         WK_CUDA(aux_stream(i % n_streams, &as));
         if (beams && beams[i]) res = upload_beams(h, beams[i], n_beams[i], as, false);
-        if (res == WAKE_OK)
-            res = h->prec == WAKE_FP64 ? prepare_impl<PrecF64>(h, as, split) : prepare_impl<PrecMixed>(h, as, split);
-    }
-    if (split && res == WAKE_OK) {
-        std::vector<int32_t> dmax((size_t)n, 0);
-        for (int32_t j = 0; j < n_streams; ++j) {
-            cudaStream_t as = nullptr;
-            WK_CUDA(aux_stream(j, &as));
-            WK_CUDA(cudaStreamSynchronize(as));
-        }
-        for (int32_t i = 0; i < n; ++i)
-            if (handles[i]->nb_total > 0)
-                WK_CUDA(cudaMemcpy(&dmax[(size_t)i], handles[i]->d_dmax, sizeof(int32_t), cudaMemcpyDeviceToHost));
-        for (int32_t i = 0; i < n && res == WAKE_OK; ++i) {
-            wake_handle* h = handles[i];
-            if (h->nb_total > 0) h->slice_max = dmax[(size_t)i];
-            h->recount = false;
-            cudaStream_t as = nullptr;
-            WK_CUDA(aux_stream(i % n_streams, &as));
-            res = h->prec == WAKE_FP64 ? prepare_sort<PrecF64>(h, as) : prepare_sort<PrecMixed>(h, as);
-        }
+        if (res == WAKE_OK) res = h->prec == WAKE_FP64 ? prepare_impl<PrecF64>(h, as) : prepare_impl<PrecMixed>(h, as);
     }
     for (int32_t j = 0; j < n_streams; ++j) {
         cudaStream_t as = nullptr;
@@ -1354,7 +1386,9 @@ wake_status wake_fields_at(wake_handle* h, int64_t n, const double* r, void* ez,
     if (n < 0 || (n > 0 && !r)) return fail(WAKE_EINVAL, "wake_fields_at: bad query array");
     int32_t next = 0, status = 0;
     WK_TRY(wake_get_progress(h, &next, &status, nullptr));
-    if (status != 0) return fail(WAKE_ENONFINITE, "wake_fields_at: the wake stopped at a non-finite slice");
+    if (status != 0) return stopped(status, "wake_fields_at");
+    if (next >= h->n_steps)
+        return fail(WAKE_EINVAL, "wake_fields_at: the window is finished (slice %d of %d)", next, h->n_steps);
     if (h->prec == WAKE_FP64) return fields_at_impl<PrecF64>(h, n, r, ez, wr, bt, psi, device_ptrs);
     return fields_at_impl<PrecMixed>(h, n, r, ez, wr, bt, psi, device_ptrs);
 }
@@ -1396,7 +1430,7 @@ wake_status wake_run(wake_handle* h, void* beam_ez, void* beam_wr, void* ring_r)
                                 cudaMemcpyDeviceToHost, h->st));
     int32_t status = 0;
     WK_TRY(wake_get_progress(h, nullptr, &status, nullptr));
-    if (status != 0) return fail(WAKE_ENONFINITE, "wake_run: the wake stopped at a non-finite slice");
+    if (status != 0) return stopped(status, "wake_run");
     return WAKE_OK;
 }
 
@@ -1417,24 +1451,25 @@ wake_status wake_batch_run(int32_t n, wake_handle* const* handles) {
     return wake_batch_step(n, handles, 1 << 30, 0);
 }
 
-wake_status wake_batch_reset_run(int32_t n, wake_handle* const* handles) {
-    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_reset_run: bad handle array");
+wake_status wake_batch_solve(int32_t n, wake_handle* const* handles, const wake_beam_desc* const* beams,
+                             const int32_t* n_beams) {
+    if (n < 0 || (n > 0 && !handles)) return fail(WAKE_EINVAL, "wake_batch_solve: bad handle array");
     if (n == 0) return WAKE_OK;
-    bool recount = false;
     for (int32_t i = 0; i < n; ++i) {
-        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_reset_run: handle %d is NULL", i);
+        if (!handles[i]) return fail(WAKE_EINVAL, "wake_batch_solve: handle %d is NULL", i);
         if (handles[i]->prec != handles[0]->prec || handles[i]->st != handles[0]->st)
-            return fail(WAKE_EINVAL, "wake_batch_reset_run: handles must share precision and stream");
-        recount = recount || handles[i]->recount;
+            return fail(WAKE_EINVAL, "wake_batch_solve: handles must share precision and stream");
+        if (beams && beams[i]) {
+            if (!n_beams) return fail(WAKE_EINVAL, "wake_batch_solve: n_beams is required with beams");
+            WK_TRY(check_new_beams(handles[i], beams[i], n_beams[i]));
+        }
     }
-    // a pushed beam needs its densest slice read back between histogram and
-    // sort: the two calls in sequence
-    if (recount) {
-        WK_TRY(wake_batch_reset(n, handles, nullptr, nullptr));
-        return wake_batch_run(n, handles);
-    }
-    if (handles[0]->prec == WAKE_FP64) return batch_reset_run_impl<PrecF64>(n, handles);
-    return batch_reset_run_impl<PrecMixed>(n, handles);
+    if (handles[0]->prec == WAKE_FP64) return batch_reset_run_impl<PrecF64>(n, handles, beams, n_beams);
+    return batch_reset_run_impl<PrecMixed>(n, handles, beams, n_beams);
+}
+
+wake_status wake_batch_reset_run(int32_t n, wake_handle* const* handles) {
+    return wake_batch_solve(n, handles, nullptr, nullptr);
 }
 
 wake_status wake_batch_progress(int32_t n, wake_handle* const* handles, int32_t* next_slice, int32_t* status) {
@@ -1467,6 +1502,19 @@ wake_status wake_batch_progress(int32_t n, wake_handle* const* handles, int32_t*
         next_slice[i] = out[2 * (size_t)i];
         status[i] = out[2 * (size_t)i + 1];
     }
+    return WAKE_OK;
+}
+
+wake_status wake_get_march_times(wake_handle* h, int64_t* begin_ns, int64_t* end_ns) {
+    WK_TRY(check_handle(h));
+    int32_t ctl[CTL_N];
+    WK_CUDA(cudaMemcpyAsync(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, h->st));
+    WK_CUDA(cudaStreamSynchronize(h->st));
+    int64_t t0 = 0, t1 = 0;
+    std::memcpy(&t0, ctl + CTL_T_BEGIN, sizeof(t0));
+    std::memcpy(&t1, ctl + CTL_T_END, sizeof(t1));
+    if (begin_ns) *begin_ns = t0;
+    if (end_ns) *end_ns = t1;
     return WAKE_OK;
 }
 
@@ -1544,9 +1592,12 @@ wake_status wake_fields_at_static(wake_handle* h, int64_t n, const double* r, vo
     } release;
     unsigned char* base = nullptr;
     WK_TRY(static_scratch(&base));
-    int32_t status = 0;
-    WK_TRY(wake_get_progress(h, nullptr, &status, nullptr));
-    if (status != 0) return fail(WAKE_ENONFINITE, "wake_fields_at_static: the wake stopped at a non-finite slice");
+    int32_t next = 0, status = 0;
+    WK_TRY(wake_get_progress(h, &next, &status, nullptr));
+    if (status != 0) return stopped(status, "wake_fields_at_static");
+    if (next >= h->n_steps)
+        return fail(WAKE_EINVAL, "wake_fields_at_static: the window is finished (slice %d of %d)", next,
+                    h->n_steps);
     if (n == 0) return WAKE_OK;
     void* outs[4] = {ez, wr, bt, psi};
     if (h->prec == WAKE_FP64) return fields_at_static_impl<PrecF64>(h, n, r, outs, base);

@@ -18,6 +18,7 @@ schedules: admission, steps, retirement and latency bookkeeping.
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence
@@ -39,6 +40,8 @@ def sm_share(launch_config) -> float:
     """SM-equivalents a wake holds while it runs: its CTAs, each taking
     threads x 128 registers of an SM's 65,536."""
     threads, _, ctas = launch_config
+    if threads <= 0:  # a one-CTA march of up to 512 threads
+        return 1.0
     return ctas * min(1.0, threads / 512.0)
 
 
@@ -101,8 +104,16 @@ def summarize(records: Sequence[tuple], counters: Sequence[Dict[str, int]]) -> D
     lat = fin - arr
     rs = sum(int(r[2]) for r in records)
     span = float(fin.max() - arr.min())
+    stopped = np.array([r[3] == wm.WAKE_ENONFINITE for r in records], dtype=bool)
+
+    def part(m):
+        if not m.any():
+            return {"requests": 0}
+        return {"requests": int(m.sum()), "p50_ms": float(np.percentile(lat[m], 50) * 1e3),
+                "p99_ms": float(np.percentile(lat[m], 99) * 1e3)}
     return {"requests": len(records), "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "whole_window": part(~stopped), "stopped_at_breakdown": part(stopped),
             "ring_slices": int(rs), "ring_slices_per_s": rs / span, "span_s": span,
             "steps": int(sum(c["steps"] for c in counters)),
             "max_active": int(max(c["max_active"] for c in counters)),
@@ -147,8 +158,14 @@ class WakeServer:
 
     def __init__(self, memory_budget: int, step_ns: int = 4_000_000, stream=None,
                  clock: Optional[Callable[[], float]] = None, sm_budget: Optional[float] = None,
-                 tuning=None):
+                 tuning=None, admit_threads: int = 8):
         self.budget = int(memory_budget)
+        # Wakes admitted in one round are created concurrently: wake_init's
+        # host work (argument checks over every beam particle, the densest
+        # slice, allocations, queued uploads) runs in the library with the
+        # interpreter lock released, and at a few hundred requests per second
+        # it, not the device, would otherwise pace the loop.
+        self.pool = concurrent.futures.ThreadPoolExecutor(admit_threads) if admit_threads > 1 else None
         # launch shapes from an autotune.TuningTable (None: the library's
         # automatic shapes)
         self.tuning = tuning
@@ -171,21 +188,34 @@ class WakeServer:
         self.stats.max_queue = max(self.stats.max_queue, len(self.queue))
 
     def _admit(self):
+        # first in line first, while the memory and SM budgets allow
+        picked = []
         while self.queue:
             req = self.queue[0]
             est = estimate_device_bytes(req.n_rings, req.n_beam, req.n_steps)
-            if self.active and self.used + est > self.budget:
+            busy = self.active or picked
+            if busy and self.used + est > self.budget:
                 break
-            if self.active and self.sm_budget is not None and self.sm_used >= self.sm_budget:
+            if busy and self.sm_budget is not None and self.sm_used >= self.sm_budget:
                 break
             self.queue.popleft()
             shape = self.tuning.shape_for(req.n_rings, "mixed") if self.tuning is not None else {}
-            w = wm.Wake(req.edges, req.beams, req.dxi, req.n_steps, precision="mixed",
-                        flags=wm.WAKE_INIT_ASYNC, stream=self.stream, **shape)
-            req.admitted = self.clock()
-            req.sm_share = sm_share(w.launch_config())
+            req.sm_share = sm_share(wm.wake_launch_shape(req.n_rings, **shape))
             self.used += est
             self.sm_used += req.sm_share
+            picked.append((req, est, shape))
+
+        def create(item):
+            req, est, shape = item
+            return wm.Wake(req.edges, req.beams, req.dxi, req.n_steps, precision="mixed",
+                           flags=wm.WAKE_INIT_ASYNC, stream=self.stream, **shape)
+        if self.pool is not None and len(picked) > 1:
+            made = list(self.pool.map(create, picked))
+        else:
+            made = [create(item) for item in picked]
+        now = self.clock()
+        for (req, est, _), w in zip(picked, made):
+            req.admitted = now
             self.active.append((req, w, est))
         self.stats.max_active = max(self.stats.max_active, len(self.active))
         self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)

@@ -22,7 +22,7 @@ from . import build as _build
 
 WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENONFINITE, WAKE_ETIMEOUT, WAKE_EBUSY = range(7)
 WAKE_FP64, WAKE_MIXED = 0, 1
-WAKE_DUMP_RING_R, WAKE_DUMP_RING_FIELDS, WAKE_INIT_ASYNC = 1, 2, 4
+WAKE_DUMP_RING_R, WAKE_DUMP_RING_FIELDS, WAKE_INIT_ASYNC, WAKE_TEST_STALL_STAGE, WAKE_NO_STAGE = 1, 2, 4, 8, 16
 WAKE_STATIC_MAX_QUERIES = 65536  # queries per wake_fields_at_static call
 PRECISION = {"fp64": WAKE_FP64, "mixed": WAKE_MIXED}
 _STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "EBUSY"}
@@ -67,12 +67,14 @@ _SIGS = {
     "wake_batch_step": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.c_int64], C.c_int),
     "wake_batch_progress": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
     "wake_get_device_bytes": ([_vp, C.POINTER(C.c_int64)], C.c_int),
+    "wake_get_march_times": ([_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "wake_batch_get_beam_fields": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "wake_set_beam_phase_space": ([_vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_get_beam_phase_space": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_push_beam": ([_vp, C.c_double], C.c_int),
     "wake_batch_push_beam": ([C.c_int32, C.POINTER(_vp), C.c_double], C.c_int),
     "wake_batch_reset_run": ([C.c_int32, C.POINTER(_vp)], C.c_int),
+    "wake_batch_solve": ([C.c_int32, C.POINTER(_vp), C.c_void_p, C.c_void_p], C.c_int),
     "wake_get_progress": ([_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_get_ring_state": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
     "wake_set_ring_state": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -85,7 +87,26 @@ _SIGS = {
     "wake_launch_shape": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                            C.POINTER(C.c_int32)], C.c_int),
     "wake_max_slice_particles": ([C.c_int32], C.c_int64),
+    "wake_measure_peaks": ([C.c_void_p], C.c_int),
 }
+
+
+class wake_peaks(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("fp32_tflops", "fp64_tflops", "mufu_lg2_tops", "smem_tbs",
+                                          "fma_latency_cycles", "syncthreads_cycles", "syncthreads_ns",
+                                          "cluster_barrier_cycles", "cluster_barrier_ns", "sm_clock_mhz")] + \
+        [("sms", C.c_int32)]
+
+
+def measure_peaks() -> Dict[str, float]:
+    """On-chip peaks of the current GPU by the library's microbenchmarks
+    (include/wake_peaks.h): FP32/FP64 FMA TFLOP/s, lg2 rate, shared-memory
+    TB/s, FMA and barrier latencies, the SM clock seen meanwhile."""
+    out = wake_peaks()
+    rc = load().wake_measure_peaks(C.byref(out))
+    if rc != 0:
+        raise WakeError(WAKE_ECUDA, f"wake_measure_peaks failed ({rc})")
+    return {k: getattr(out, k) for k, _ in wake_peaks._fields_}
 
 _lib = None
 
@@ -307,6 +328,13 @@ class Wake:
         _check(load().wake_get_device_bytes(self.handle, C.byref(b)))
         return int(b.value)
 
+    def march_times(self):
+        """(begin, end) device time in ns of the last march launch on this
+        wake (the GPU's global timer)."""
+        t0, t1 = C.c_int64(), C.c_int64()
+        _check(load().wake_get_march_times(self.handle, C.byref(t0), C.byref(t1)))
+        return t0.value, t1.value
+
     def launch_config(self):
         """(threads per block, rings per thread, blocks per wake)."""
         t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
@@ -411,6 +439,31 @@ def wake_batch_reset_run(wakes: List[Wake]):
     wakes are prepared."""
     arr = (_vp * len(wakes))(*[w.handle for w in wakes])
     _check(load().wake_batch_reset_run(len(wakes), arr))
+
+
+def wake_batch_solve(wakes: List[Wake], beams: Optional[Sequence] = None):
+    """Upload (beams: None, or one entry per wake, None or a beam sequence
+    as in reset; pinned torch tensors overlap), prepare and march every
+    wake's whole window in one pipelined submission that never waits for
+    the device."""
+    n = len(wakes)
+    arr = (_vp * max(1, n))(*[w.handle for w in wakes])
+    if beams is None:
+        _check(load().wake_batch_solve(n, arr, None, None))
+        return
+    dps = (C.POINTER(wake_beam_desc) * max(1, n))()
+    counts = (C.c_int32 * max(1, n))()
+    keep = []
+    for i, bs in enumerate(beams):
+        if bs is None:
+            continue
+        descs, k = _beam_descs(bs)
+        keep += [descs, k]
+        dps[i] = C.cast(descs, C.POINTER(wake_beam_desc))
+        counts[i] = len(bs)
+    _check(load().wake_batch_solve(n, arr, dps, counts))
+    for w in wakes:
+        w._reset_keep = keep
 
 
 def wake_max_rings(precision: str = "mixed") -> int:

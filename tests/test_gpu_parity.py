@@ -458,3 +458,59 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(wm.WakeError) as e:
         wm.Wake(W.edges_uniform(10, 1.0), [dense], 0.01, 10)
     assert e.value.status == wm.WAKE_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fields_at_refuses_a_finished_window(precision):
+    """Once every slice has been solved there is no current slice to sample:
+    both fields queries return EINVAL instead of the fields after the last
+    push."""
+    wm = _wake_mod()
+    wk = W.Wake("done", W.edges_uniform(64, 3.0), [W.gaussian_beam(2000, 0.5, 0.3, 0.5, 0.4, seed=6)], 0.02, 40)
+    g = wm.Wake.from_workload(wk, precision=precision)
+    g.step_slices(39)
+    assert g.fields_at(np.array([0.5]))["ez"].shape == (1,)  # the last slice is still open
+    g.step_slices(1)
+    assert g.progress()[0] == 40
+    for call in (g.fields_at, g.fields_at_static):
+        with pytest.raises(wm.WakeError) as e:
+            call(np.array([0.5, 1.0]))
+        assert e.value.status == wm.WAKE_EINVAL
+        assert "finished" in str(e.value)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_solve_with_new_beams_equals_fresh_wakes(precision):
+    """wake_batch_solve uploads new beams, prepares and marches without ever
+    waiting for the device: their slices are counted and sorted on the
+    device alone (a first sort pass for slices of up to 1024 particles, a
+    second for denser ones).  Every wake must come out bitwise as a wake
+    created with those beams, whose densest slice the host counted (one
+    sort pass sized for it).  Beams with slices of up to ~3000 particles
+    and beams of a second species exercise both passes."""
+    wm = _wake_mod()
+    shapes = [(700, 300, 200_000), (2500, 200, 150_000), (257, 400, 20_000)]
+    old = [W.gaussian_beam(nb, 1.0, 0.3, 1.0, 4.0, seed=70 + k) for k, (_, _, nb) in enumerate(shapes)]
+    # narrower bunches of the same particle counts: densest slices ~2700,
+    # ~1500 and ~270 particles
+    new = [[W.gaussian_beam(200_000, 4.0, 0.25, 0.3, 1.2, seed=80)],
+           [W.gaussian_beam(150_000, 2.0, 0.5, 0.4, 1.6, seed=81)],
+           [W.gaussian_beam(20_000, 0.5, 0.3, 0.3, 1.2, seed=82)]]
+    gs = [wm.Wake(W.edges_uniform(n, 6.0), [old[k]], 0.01, steps, precision=precision)
+          for k, (n, steps, _) in enumerate(shapes)]
+    wm.wake_batch_solve(gs, new)
+    for k, (n, steps, _) in enumerate(shapes):
+        ref = wm.Wake(W.edges_uniform(n, 6.0), new[k], 0.01, steps, precision=precision)
+        ref.step_slices(10 ** 6)
+        g = gs[k]
+        assert g.progress() == ref.progress()
+        a, b = g.beam_fields(), ref.beam_fields()
+        for f in a:
+            assert np.array_equal(a[f], b[f]), (k, f)
+        assert np.array_equal(g.ring_state()[0], ref.ring_state()[0])
+        ref.close()
+    # and a second solve with the beams in place repeats it
+    wm.wake_batch_solve(gs)
+    for g in gs:
+        g.close()
