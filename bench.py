@@ -461,7 +461,7 @@ def push_bench(args, gs, wakes, stream):
                          "bytes_per_particle": PUSH_BYTES_PER_PARTICLE, "peak_basis": "measured copy (MEASURED_PEAKS.json)"}}
 
 
-def stage_ab_bench(gs, wakes, stream, reps=2):
+def stage_ab_bench(gs, wakes, stream, reps=3):
     """The batched march (after a batched preparation, CUDA-event timed) of
     the same wakes with the beam staged by bulk copies and with plain
     global loads (WAKE_NO_STAGE handles), alternated; best of reps each."""
@@ -1001,8 +1001,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
-    ap.add_argument("--serve-step-us", type=float, default=4000.0)
-    ap.add_argument("--serve-sm-fill", type=float, default=1.5,
+    ap.add_argument("--serve-step-us", type=float, default=10000.0)
+    ap.add_argument("--serve-sm-fill", type=float, default=2.0,
                     help="admit while running wakes hold fewer than this many SMs' worth (x SM count); 0: no cap")
     ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
     ap.add_argument("--uniform-kind", default="ab2", choices=["ab2", "ions", "rk4"])

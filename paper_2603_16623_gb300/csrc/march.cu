@@ -147,6 +147,22 @@ cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int3
     return cudaGetLastError();
 }
 
+// Asks for a shared-memory carveout no larger than the blocks an SM holds
+// need (by registers: 128 per thread), so that the rest of the SM's 256 KB
+// stays L1 for the per-ring constant table gathered every slice (left to
+// itself the driver may pick the largest carveout, and the table then
+// misses to L2).
+template <class F>
+static cudaError_t set_carveout(F kern, int32_t threads, size_t dyn_smem) {
+    constexpr size_t kSmemMax = 233472, kPerBlockExtra = 3 * 1024;  // reserved + static
+    int32_t blocks = 65536 / (128 * threads);
+    blocks = std::max(1, std::min(blocks, 2048 / threads));
+    const size_t need = (size_t)blocks * (dyn_smem + kPerBlockExtra);
+    int pct = (int)((need * 100 + kSmemMax - 1) / kSmemMax);
+    pct = std::max(1, std::min(pct, 100));
+    return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 template <int K>
 static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                  int32_t max_slices, int32_t mode, int32_t threads, int32_t stage_particles,
@@ -154,6 +170,7 @@ static cudaError_t launch_fast_k(const WakeDev<PrecMixed>* d_wakes, const int32_
     size_t smem = fast_smem_bytes(threads, K) + stage_smem_bytes(stage_particles);
     cudaError_t e =
         cudaFuncSetAttribute(march_fast_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = set_carveout(march_fast_kernel<K>, threads, smem);
     if (e != cudaSuccess) return cudaGetLastError(), e;  // (a refused call leaves no error behind)
     march_fast_kernel<K><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, stage_particles);
     return cudaGetLastError();
@@ -192,6 +209,7 @@ static cudaError_t launch_cluster_k(const WakeDev<PrecMixed>* d_wakes, const int
     size_t smem = cluster_smem_bytes(threads, K) + stage_smem_bytes(stage_particles);
     auto kern = march_cluster_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = set_carveout(kern, threads, smem);
     if (e != cudaSuccess) return cudaGetLastError(), e;  // (a refused call leaves no error behind)
     if (cl > 8) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
