@@ -957,7 +957,11 @@ def run_uniform(args):
     wk = W.Wake(f"uniform{n}", W.edges_uniform(n, 6.0), [drv], 0.01, slices, **kind)
     n = n * (2 if args.uniform_kind == "ions" else 1)
     flags = wm.WAKE_NO_STAGE if args.no_stage else 0
-    gs = [wm.Wake.from_workload(wk, precision="mixed", flags=flags) for _ in range(copies)]
+    shape = {}
+    if args.uniform_shape:
+        k, cl = (int(v) for v in args.uniform_shape.split(","))
+        shape = {"rings_per_thread": k, "cluster_ctas": cl}
+    gs = [wm.Wake.from_workload(wk, precision="mixed", flags=flags, **shape) for _ in range(copies)]
     wm.wake_batch_run(gs)
     torch.cuda.synchronize()
     wm.wake_batch_reset(gs)
@@ -1006,6 +1010,8 @@ def main():
                     help="admit while running wakes hold fewer than this many SMs' worth (x SM count); 0: no cap")
     ap.add_argument("--uniform", default=None, help="RINGS,SLICES,COPIES: one batch of identical wakes")
     ap.add_argument("--uniform-kind", default="ab2", choices=["ab2", "ions", "rk4"])
+    ap.add_argument("--uniform-shape", default=None,
+                    help="--uniform: RINGS_PER_THREAD,CTAS (the on-chip march's launch shape; default automatic)")
     ap.add_argument("--no-stage", action="store_true",
                     help="--uniform: read each slice's beam from global memory (no bulk-copy staging)")
     ap.add_argument("--skip-stage-ab", action="store_true")

@@ -139,13 +139,14 @@ typedef struct {
     int32_t block_threads;    /* FP64, mobile ions, RK4: threads per wake
                                  (multiple of 32, 64..512); 0 = library
                                  default (256; 512 with mobile ions or RK4)    */
-    int32_t rings_per_thread; /* MIXED: 4 or 8 rings per thread; 0 = automatic  */
+    int32_t rings_per_thread; /* MIXED: 2, 4 or 8 rings per thread; 0 = auto  */
     int32_t cluster_ctas;     /* MIXED: CTAs per wake, 1..16 (> 1: a thread-
                                  block cluster); 0 = automatic.  The threads
                                  per CTA follow: ceil(n / (rings_per_thread x
                                  cluster_ctas)) rounded up to a multiple of 32,
                                  at most 512, and no CTA may be left empty.
-                                 Both must be 0 for WAKE_FP64.                  */
+                                 Both must be 0 for WAKE_FP64.  Automatic
+                                 (both 0): see wake_launch_shape.             */
     int32_t integrator;       /* WAKE_AB2 (0) or WAKE_RK4                        */
     int32_t grid_nr;          /* 0: gridless beam coupling (fields at each beam
                                  particle); 1..1024: adaptive beam grids
@@ -346,6 +347,7 @@ wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, vo
 wake_status wake_get_launch_config(wake_handle *h, int32_t *threads, int32_t *rings_per_thread,
                                    int32_t *blocks_per_wake);
 
+
 /* Beam push between wake solves (Sec. V: the beam moves over a time step in
    the fields the wake gave at each particle; Boris method).  The beam needs
    a full phase space for it: x, y, u_x, u_y, u_z (u = p/(m c)) per beam
@@ -414,19 +416,52 @@ int64_t wake_max_slice_particles(int32_t precision); /* beam particles per slice
 
 /* The launch shape wake_init gives the on-chip march (mixed precision,
    electrons over the ion column, no beam grids) for a wake of n_rings rings
-   and the config's rings_per_thread and cluster_ctas (both 0: the automatic
-   shape), computed on the host: no device, no handle, nothing allocated.
-   Outputs (each may be NULL): threads per CTA, rings per thread and CTAs
-   per wake (> 1: a thread-block cluster); all three 0 when the wake runs on
-   a one-CTA march instead (FP64, or the automatic shape beyond the on-chip
+   and n_steps slices and the config's rings_per_thread and cluster_ctas,
+   computed on the host: no device, no handle, nothing allocated.  Both 0:
+   the automatic shape, which is the batch shape (the least SM time per
+   slice: one CTA of up to 512 threads x 4 rings up to 2048 rings; up to
+   16,384 rings a cluster of ceil(n / 1024) CTAs of 4 rings per thread; up
+   to 32,768 ceil(n / 2048) CTAs; beyond, 8 rings per thread), or, when its
+   predicted march time is at least wake_get_latency_shape_ms(), the latency
+   shape (wake_launch_shape_latency).  n_steps 0: the batch shape.  Outputs
+   (each may be NULL): threads per CTA, rings per thread and CTAs per wake
+   (> 1: a thread-block cluster); all three 0 when the wake runs on a
+   one-CTA march instead (FP64, or the automatic shape beyond the on-chip
    march's 65,536 rings).  The launch-shape autotuner enumerates its
    candidates with it.  Errors: EINVAL for a precision other than WAKE_FP64
-   or WAKE_MIXED, n_rings outside [1, wake_max_rings(precision)], or the
-   shape wake_init would refuse (rings_per_thread not 0, 4 or 8;
-   cluster_ctas outside [0, 16]; more than 512 threads per CTA; an empty
-   last CTA; either field set with FP64). */
-wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t rings_per_thread, int32_t cluster_ctas,
-                              int32_t *threads, int32_t *rings_per_thread_out, int32_t *blocks_per_wake);
+   or WAKE_MIXED, n_rings outside [1, wake_max_rings(precision)], a negative
+   n_steps, or the shape wake_init would refuse (rings_per_thread not 0, 2,
+   4 or 8; cluster_ctas outside [0, 16]; more than 512 threads per CTA; an
+   empty last CTA; either field set with FP64). */
+wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t n_steps, int32_t rings_per_thread,
+                              int32_t cluster_ctas, int32_t *threads, int32_t *rings_per_thread_out,
+                              int32_t *blocks_per_wake);
+
+/* The latency shape of an automatic-shape wake of n_rings rings (mixed
+   precision), computed on the host: 2 rings per thread, the shortest time
+   per slice (about 0.7x the batch shape's per slice on clusters) for about
+   1.3x its SM time.  Up to 1024 rings one CTA of ceil(n / 2) threads
+   (rounded up to a multiple of 32); up to 8192 rings a cluster of
+   ceil(n / 512) CTAs of at most 256 threads; up to 16,384 rings
+   ceil(n / 1024) CTAs of at most 512 threads; beyond, the batch shape.
+   Outputs as wake_launch_shape (all 0 for WAKE_FP64).  Errors: EINVAL as
+   wake_launch_shape. */
+wake_status wake_launch_shape_latency(int32_t precision, int32_t n_rings, int32_t *threads,
+                                      int32_t *rings_per_thread_out, int32_t *blocks_per_wake);
+
+/* The threshold, in milliseconds of predicted march time, at and above
+   which wake_init gives an automatic-shape wake its latency shape rather
+   than its batch shape (process-wide; default INFINITY: none; 0: every
+   wake).  Alone, the latency shape marches a wake 10-35 % faster; in a
+   batch that fills the GPU its larger clusters are placed late and the
+   batch takes longer, hence the default.  The prediction is the library's model of the on-chip
+   march's time per slice on GB300 for the batch shape x n_steps.  A
+   wake's shape is fixed when it is created, so a wake gives the same
+   results alone and in any batch.  Errors: EINVAL for a negative value or
+   NaN. */
+wake_status wake_set_latency_shape_ms(double ms);
+double wake_get_latency_shape_ms(void);
+
 
 #ifdef __cplusplus
 }

@@ -2,7 +2,7 @@
 
 A mixed-precision wake runs on the on-chip march as one CTA (up to 2048
 rings) or as a thread-block cluster of up to 16 CTAs; its rings per thread
-(4 or 8) and CTAs per wake fix the threads per CTA.  Fewer, wider CTAs mean
+(2, 4 or 8) and CTAs per wake fix the threads per CTA.  Fewer, wider CTAs mean
 fewer cluster barriers per slice; more, narrower ones a shorter chain of
 block-wide steps per slice and more CTAs resident per SM.  Which wins
 depends on the ring count and on how full the GPU is, so the tuner measures
@@ -50,7 +50,7 @@ DEFAULT_SIZES = (512, 1024, 2048, 3072, 4096, 6144, 8192, 12288, 16384, 32768, 6
 class Candidate:
     """Arguments of wake_init for one launch shape, with what they resolve
     to for the size they were made for."""
-    rings_per_thread: int = 0   # on-chip march: 0 (automatic), 4 or 8
+    rings_per_thread: int = 0   # on-chip march: 0 (automatic), 2, 4 or 8
     cluster_ctas: int = 0       # on-chip march: 0 (automatic) or 1-16
     block_threads: int = 0      # one-CTA marches: 0 (the library's default) or 64-512
     threads: int = 0            # resolved threads per CTA (on-chip march)
@@ -93,7 +93,7 @@ def candidates(n_rings: int, kind: str = "mixed", max_candidates: int = 8,
     auto = Candidate(threads=t0, ctas=c0)
     seen = {(t0, k0, c0)}
     rest = []
-    for k in (4, 8):
+    for k in (2, 4, 8):
         for cl in range(1, 17):
             try:
                 t, kk, cc = wm.wake_launch_shape(n_rings, k, cl)

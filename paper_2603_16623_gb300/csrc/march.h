@@ -13,7 +13,7 @@ namespace gbwake {
 template <class P>
 cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
                          int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st);
-// the on-chip march (mixed precision, k_rings = 4 or 8 rings per thread,
+// the on-chip march (mixed precision, k_rings = 2, 4 or 8 rings per thread,
 // <= 512 threads)
 constexpr int kFastMaxThreads = 512;
 cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
@@ -24,8 +24,8 @@ cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* 
 // sized so that the stage never lowers the number of blocks an SM holds
 // (clusters > 1: the cluster march's footprint)
 int32_t march_stage_particles(int32_t threads, int32_t k_rings, int32_t cluster_ctas, int32_t want);
-// the cluster march: clusters of cl CTAs of `threads` threads, k_rings = 4
-// or 8 rings per thread
+// the cluster march: clusters of cl CTAs of `threads` threads, k_rings = 2,
+// 4 or 8 rings per thread
 cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                  int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
                                  int32_t stage_particles, cudaStream_t st);

@@ -42,7 +42,7 @@ struct Swz {
     // position p (thread p/K, slot p%K) -> shared-memory word; XOR-swizzle of
     // the slot by the thread's group so that the K-strided accesses of a warp
     // hit 32 distinct banks
-    static constexpr int kShift = (K == 4) ? 3 : (K == 8 ? 2 : (K == 16 ? 1 : 0));
+    static constexpr int kShift = (K == 2) ? 4 : (K == 4) ? 3 : (K == 8 ? 2 : (K == 16 ? 1 : 0));
     __device__ __forceinline__ static int at(int p) {
         int t = p / K, j = p % K;
         return t * K + (j ^ ((t >> kShift) & (K - 1)));

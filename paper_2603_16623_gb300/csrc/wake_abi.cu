@@ -472,7 +472,7 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
 // thread-block cluster of ceil(n / 1024) CTAs; up to 32,768 one of
 // ceil(n / 2048) CTAs (16 is the largest cluster GB300 allows); beyond, 8
 // rings per thread.  A caller (or the autotuner) may instead fix the rings per thread
-// (4 or 8) and the CTAs per wake; the threads per CTA then follow from n.
+// (2, 4 or 8) and the CTAs per wake; the threads per CTA then follow from n.
 constexpr int32_t kRingsPerCta = 4 * kFastMaxThreads;
 constexpr int32_t kMaxClusterCtas = 16;
 
@@ -488,7 +488,8 @@ wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want
         *out = f;
         return WAKE_OK;
     }
-    if (want_k != 0 && want_k != 4 && want_k != 8) return fail(WAKE_EINVAL, "wake_init: rings_per_thread must be 0, 4 or 8");
+    if (want_k != 0 && want_k != 2 && want_k != 4 && want_k != 8)
+        return fail(WAKE_EINVAL, "wake_init: rings_per_thread must be 0, 2, 4 or 8");
     if (want_cl < 0 || want_cl > kMaxClusterCtas)
         return fail(WAKE_EINVAL, "wake_init: cluster_ctas must be in [0, %d]", kMaxClusterCtas);
     // automatic: one CTA up to 2048 rings; beyond, clusters of CTAs of at
@@ -526,6 +527,48 @@ wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want
     if (f.cl > 1 && (int64_t)f.threads * f.k * (f.cl - 1) >= n)
         return fail(WAKE_EINVAL, "wake_init: %d rings leave the last of %d CTAs empty", n, f.cl);
     *out = f;
+    return WAKE_OK;
+}
+
+// The latency shape of an automatic-shape wake: 2 rings per thread, which
+// halves each thread's chain of per-ring work in every slice (measured on
+// GB300, one wake alone: 8000 rings 27.8 -> 21.0 us per slice, 4000 rings
+// 29.4 -> 19.2, 1000 rings 17.5 -> 15.3), at ~1.3x the SM time per slice of
+// the batch shape (fast_shape_for).  Up to 1024 rings one CTA; up to 8192 a
+// cluster of CTAs of at most 256 threads x 2 rings (two CTAs share an SM);
+// up to 16,384 CTAs of 512 threads x 2 rings; beyond, the batch shape.
+FastShape latency_shape_for(int32_t n, const FastShape& batch) {
+    if (batch.threads == 0 || n > kMaxClusterCtas * 2 * kFastMaxThreads) return batch;
+    FastShape f;
+    f.k = 2;
+    if (n <= 2 * kFastMaxThreads) f.cl = 1;
+    else if (n <= kMaxClusterCtas * 512) f.cl = (n + 511) / 512;
+    else f.cl = (n + 2 * kFastMaxThreads - 1) / (2 * kFastMaxThreads);
+    const int32_t per_cta = (n + f.cl - 1) / f.cl;
+    const int32_t t = ((per_cta + 1) / 2 + 31) / 32 * 32;
+    f.threads = t < 32 ? 32 : t;
+    return f;  // (2 t (cl - 1) <= 512 (cl - 1) < n, resp. 1024 (cl - 1) < n: no CTA is empty)
+}
+
+double predicted_fast_slice_us(const FastShape& f);
+
+// Automatic-shape wakes whose predicted march time on the batch shape is at
+// least this many milliseconds take their latency shape (process-wide).
+// Off by default: in a full batch the latency shape's larger clusters wait
+// for room in one GPC while the rest of the batch holds the SMs, and on the
+// batched wakes (dense beams, rings crossing CTA boundaries) it gains less
+// than alone on uniform wakes (256-wake step: 9 long wakes on it 358-366 ms
+// against 273-283 ms; the longest wake alone 183 against 201 ms).
+double g_latency_shape_ms = INFINITY;
+
+// The shape wake_init gives a wake of n rings and n_steps slices: the
+// caller's, else the batch shape, or the latency shape for a long wake.
+wake_status wake_shape_for(int32_t prec, int32_t n, int32_t n_steps, int32_t want_k, int32_t want_cl,
+                           FastShape* out) {
+    WK_TRY(fast_shape_for(prec, n, want_k, want_cl, out));
+    if (want_k || want_cl || out->threads == 0) return WAKE_OK;
+    if ((double)n_steps * predicted_fast_slice_us(*out) * 1e-3 >= g_latency_shape_ms)
+        *out = latency_shape_for(n, *out);
     return WAKE_OK;
 }
 
@@ -579,15 +622,11 @@ int32_t stage_want(const wake_handle* h) { return h->slice_max < 0 ? kMaxSlicePa
 template <class P>
 wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_slices, int32_t mode) {
     if constexpr (std::is_same<P, PrecMixed>::value) {
-        if (h->fast_threads > 0 && h->fast_cl > 1) {
-            const int32_t stage = march_stage_particles(h->fast_threads, h->fast_k, h->fast_cl, stage_want(h));
-            WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, h->fast_cl,
-                                         stage, h->st));
-            return WAKE_OK;
-        }
-        if (h->fast_threads > 0) {
-            const int32_t stage = march_stage_particles(h->fast_threads, h->fast_k, 1, stage_want(h));
-            WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, h->fast_threads, h->fast_k, stage, h->st));
+        const int32_t t = h->fast_threads, k = h->fast_k, cl = h->fast_cl;
+        if (t > 0) {
+            const int32_t stage = march_stage_particles(t, k, cl, stage_want(h));
+            if (cl > 1) WK_CUDA(launch_march_cluster(d_desc, nullptr, 1, max_slices, mode, t, k, cl, stage, h->st));
+            else WK_CUDA(launch_march_fast(d_desc, nullptr, 1, max_slices, mode, t, k, stage, h->st));
             return WAKE_OK;
         }
     }
@@ -725,9 +764,21 @@ wake_status beam_fields_impl(wake_handle* h, void* const outs_user[4], int32_t d
     return WAKE_OK;
 }
 
+double predicted_ms(const wake_handle* h);
+
+// the on-chip shape of a wake (threads 0: a one-CTA kernel)
+FastShape wake_shape(const wake_handle* h) {
+    FastShape f;
+    f.threads = h->fast_threads;
+    f.k = h->fast_k;
+    f.cl = h->fast_cl;
+    return f;
+}
+
 template <class P>
-wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threads, cudaStream_t st,
+wake_status batch_bucket(const std::vector<wake_handle*>& hs, const FastShape& shape, cudaStream_t st,
                          int32_t max_slices, int64_t budget_ns) {
+    const int32_t fast_threads = shape.threads;
     const int32_t n = (int32_t)hs.size();
     std::vector<WakeDev<P>> descs(n);
     std::vector<int32_t> order(n);
@@ -739,10 +790,10 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
         n_max = std::max(n_max, hs[i]->n);
         pad_max = std::max(pad_max, hs[i]->n_pad);
     }
-    // largest work first: blocks are dispatched roughly in index order
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return (int64_t)hs[a]->n * hs[a]->n_steps > (int64_t)hs[b]->n * hs[b]->n_steps;
-    });
+    // longest predicted march first: blocks are dispatched roughly in index order
+    std::vector<double> t_pred(n);
+    for (int32_t i = 0; i < n; ++i) t_pred[i] = predicted_ms(hs[i]);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return t_pred[a] > t_pred[b]; });
     const size_t desc_bytes = sizeof(WakeDev<P>) * (size_t)n;
     void* d_buf = nullptr;
     WK_CUDA(cudaMallocAsync(&d_buf, desc_bytes + sizeof(int32_t) * (size_t)n, st));
@@ -754,13 +805,13 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
         if (fast_threads > 0) {
             int32_t densest = 0;
             for (const wake_handle* h : hs) densest = std::max(densest, stage_want(h));
-            const int32_t stage = march_stage_particles(fast_threads, hs[0]->fast_k, hs[0]->fast_cl, densest);
-            if (hs[0]->fast_cl > 1)
+            const int32_t stage = march_stage_particles(fast_threads, shape.k, shape.cl, densest);
+            if (shape.cl > 1)
                 e = launch_march_cluster(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                                         fast_threads, hs[0]->fast_k, hs[0]->fast_cl, stage, st);
+                                         fast_threads, shape.k, shape.cl, stage, st);
             else
                 e = launch_march_fast(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                                      fast_threads, hs[0]->fast_k, stage, st);
+                                      fast_threads, shape.k, stage, st);
             cudaFreeAsync(d_buf, st);
             if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
             return WAKE_OK;
@@ -782,18 +833,32 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, int32_t fast_threa
     return WAKE_OK;
 }
 
-// Predicted march time of a wake per slice, in microseconds, on GB300
-// (single-wake latency; the batch's dispatch order only needs it to rank
-// wakes).  Fitted to the march times of the 256 batched wakes measured one
-// by one (wake_get_march_times): one CTA of R rings (4 per thread) ~ 11 +
-// 9 R/2048 us per slice; a cluster of cl CTAs of R rings each ~ 16.3 + 1.6
-// cl + 8.9 R/1024 us (its cluster barriers and exchanges).  The one-CTA
-// kernels with state in global memory grow with the rings per thread.
+// Predicted march time per slice, in microseconds, on GB300, of the
+// on-chip march in shape f (threads > 0) or of a one-CTA kernel in blocks of
+// `threads` (per_thread rings each); the batch's plan only needs it to rank
+// wakes, wake_init to compare a wake with the latency-shape threshold.
+// Fitted to march times measured one wake at a time (wake_get_march_times):
+// at 4 rings per thread one CTA of R rings ~ 11 + 9 R/2048 us per slice and
+// a cluster of cl CTAs of R rings each ~ 16.3 + 1.6 cl + 8.9 R/1024 us (its
+// cluster barriers and exchanges), on the batched wakes; at 2 rings per
+// thread, from uniform wakes scaled by the batched wakes' 1.2x, one CTA
+// ~ 0.875 of the 4-ring time and a cluster ~ 17.8 + 0.26 cl + 6.4 R/1024 us.
+// The one-CTA kernels with state in global memory grow with the rings per
+// thread.
+double predicted_fast_slice_us(const FastShape& f) {
+    const double R = (double)f.threads * f.k;
+    if (f.k == 2) return f.cl > 1 ? 17.8 + 0.26 * f.cl + 6.4 * R / 1024.0 : 0.875 * (11.0 + 9.0 * R / 2048.0);
+    if (f.cl > 1) return 16.3 + 1.6 * f.cl + 8.9 * R / 1024.0;
+    return 11.0 + 9.0 * R / 2048.0;
+}
+
 double predicted_slice_us(const wake_handle* h) {
     if (h->fast_threads > 0) {
-        const double R = (double)h->fast_threads * h->fast_k;
-        if (h->fast_cl > 1) return 16.3 + 1.6 * h->fast_cl + 8.9 * R / 1024.0;
-        return 11.0 + 9.0 * R / 2048.0;
+        FastShape f;
+        f.threads = h->fast_threads;
+        f.k = h->fast_k;
+        f.cl = h->fast_cl;
+        return predicted_fast_slice_us(f);
     }
     const double per_thread = (double)h->n / h->threads;
     return (h->rk4 ? 4.0 : 1.0) * (20.0 + 6.0 * per_thread);
@@ -802,15 +867,23 @@ double predicted_slice_us(const wake_handle* h) {
 double predicted_ms(const wake_handle* h) { return h->n_steps * predicted_slice_us(h) * 1e-3; }
 
 // A batch as march launches: wakes of one kernel configuration share a
-// launch, split by predicted time into tiers (at least half of the longest
-// wake's time; a fifth of it; the rest), so that the long wakes of every
-// configuration are dispatched before the short ones of any.  Groups come
-// tier by tier, the group with the longest wake first within a tier.
+// launch, split by predicted time into three tiers (at least half of the
+// longest wake's time; a fifth of it; the rest), one stream priority each, so
+// that the hardware dispatches the blocks of the long wakes of every
+// configuration before the short ones of any (an approximation of longest-
+// processing-time-first list scheduling, whose makespan a wake started late
+// lengthens by its whole march).  Groups come tier by tier, the group with
+// the longest wake first within a tier.
 struct LaunchGroup {
     std::vector<wake_handle*> hs;
     int tier = 0;
     double t_max = 0.0;
 };
+
+// lower bounds of the tiers' predicted times, as fractions of the longest
+// (GB300 offers four stream priorities: the preparations' and three tiers';
+// two levels sharing a priority measured 15-20 % slower steps)
+constexpr double kTierFrac[kTiers - 1] = {0.5, 0.2};
 
 std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
     double t_all = 0.0;
@@ -818,13 +891,14 @@ std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
     std::vector<std::pair<int64_t, int>> keys;  // (configuration, tier)
     std::vector<LaunchGroup> groups;
     for (int32_t i = 0; i < n; ++i) {
-        int64_t key = (hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
+        int64_t key = ((int64_t)hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
         // the one-CTA kernels (plain, two-species, RK4, grids) by their block size
         if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * (hs[i]->grid_nr > 0) +
                                           8 * hs[i]->threads);
         const double t = predicted_ms(hs[i]);
-        const int tier = t >= 0.5 * t_all ? 0 : (t >= 0.2 * t_all ? 1 : 2);
+        int tier = 0;
+        while (tier + 1 < kTiers && t < kTierFrac[tier] * t_all) ++tier;
         auto it = std::find(keys.begin(), keys.end(), std::make_pair(key, tier));
         if (it == keys.end()) {
             keys.emplace_back(key, tier);
@@ -849,18 +923,18 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
     // ordered after the work already queued on the handles' stream and
     // joined back into it
     std::vector<LaunchGroup> groups = plan_launches(n, hs);
-    if (groups.size() == 1) return batch_bucket<P>(groups[0].hs, groups[0].hs[0]->fast_threads, st, max_slices, budget_ns);
+    if (groups.size() == 1) return batch_bucket<P>(groups[0].hs, wake_shape(groups[0].hs[0]), st, max_slices, budget_ns);
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
     wake_status res = WAKE_OK;
-    int in_tier[kTiers] = {0, 0, 0};
+    int in_tier[kTiers] = {};
     for (size_t i = 0; i < groups.size(); ++i) {
         cudaStream_t as = nullptr;
         const int tier = groups[i].tier;
         WK_CUDA(tier_stream(tier, in_tier[tier]++, &as));
         WK_CUDA(cudaStreamWaitEvent(as, start, 0));
-        wake_status r = batch_bucket<P>(groups[i].hs, groups[i].hs[0]->fast_threads, as, max_slices, budget_ns);
+        wake_status r = batch_bucket<P>(groups[i].hs, wake_shape(groups[i].hs[0]), as, max_slices, budget_ns);
         if (r != WAKE_OK) res = r;
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -900,7 +974,7 @@ wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs, const wake_b
     };
     wake_status res = WAKE_OK;
     int next_prep = 0;
-    int in_tier[kTiers] = {0, 0, 0};
+    int in_tier[kTiers] = {};
     for (size_t i = 0; i < groups.size() && res == WAKE_OK; ++i) {
         cudaStream_t ms = nullptr;
         const int tier = groups[i].tier;
@@ -927,7 +1001,7 @@ wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs, const wake_b
             cudaStreamWaitEvent(ms, ready, 0);
         }
         if (res != WAKE_OK) break;
-        res = batch_bucket<P>(groups[i].hs, groups[i].hs[0]->fast_threads, ms, 1 << 30, 0);
+        res = batch_bucket<P>(groups[i].hs, wake_shape(groups[i].hs[0]), ms, 1 << 30, 0);
         cudaEvent_t done;
         WK_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
         events.push_back(done);
@@ -1178,18 +1252,43 @@ int64_t wake_max_slice_particles(int32_t precision) {
     return kMaxSliceParticles;
 }
 
-wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t rings_per_thread, int32_t cluster_ctas,
-                              int32_t* threads, int32_t* rings_per_thread_out, int32_t* blocks_per_wake) {
+wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t n_steps, int32_t rings_per_thread,
+                              int32_t cluster_ctas, int32_t* threads, int32_t* rings_per_thread_out,
+                              int32_t* blocks_per_wake) {
     if (precision != WAKE_FP64 && precision != WAKE_MIXED) return fail(WAKE_EINVAL, "wake_launch_shape: bad precision");
     if (n_rings < 1 || n_rings > wake_max_rings(precision))
         return fail(WAKE_EINVAL, "wake_launch_shape: n_rings must be in [1, %d]", wake_max_rings(precision));
+    if (n_steps < 0) return fail(WAKE_EINVAL, "wake_launch_shape: n_steps must be >= 0");
     FastShape f;
-    WK_TRY(fast_shape_for(precision, n_rings, rings_per_thread, cluster_ctas, &f));
+    WK_TRY(wake_shape_for(precision, n_rings, n_steps, rings_per_thread, cluster_ctas, &f));
     if (threads) *threads = f.threads;
     if (rings_per_thread_out) *rings_per_thread_out = f.threads ? f.k : 0;
     if (blocks_per_wake) *blocks_per_wake = f.threads ? f.cl : 0;
     return WAKE_OK;
 }
+
+wake_status wake_launch_shape_latency(int32_t precision, int32_t n_rings, int32_t* threads,
+                                      int32_t* rings_per_thread_out, int32_t* blocks_per_wake) {
+    if (precision != WAKE_FP64 && precision != WAKE_MIXED)
+        return fail(WAKE_EINVAL, "wake_launch_shape_latency: bad precision");
+    if (n_rings < 1 || n_rings > wake_max_rings(precision))
+        return fail(WAKE_EINVAL, "wake_launch_shape_latency: n_rings must be in [1, %d]", wake_max_rings(precision));
+    FastShape f;
+    WK_TRY(fast_shape_for(precision, n_rings, 0, 0, &f));
+    f = latency_shape_for(n_rings, f);
+    if (threads) *threads = f.threads;
+    if (rings_per_thread_out) *rings_per_thread_out = f.threads ? f.k : 0;
+    if (blocks_per_wake) *blocks_per_wake = f.threads ? f.cl : 0;
+    return WAKE_OK;
+}
+
+wake_status wake_set_latency_shape_ms(double ms) {
+    if (!(ms >= 0.0)) return fail(WAKE_EINVAL, "wake_set_latency_shape_ms: ms must be >= 0 (or infinity)");
+    g_latency_shape_ms = ms;
+    return WAKE_OK;
+}
+
+double wake_get_latency_shape_ms(void) { return g_latency_shape_ms; }
 
 wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, const wake_beam_desc* beams,
                       int32_t n_beams, void* cuda_stream, wake_handle** out) {
@@ -1281,7 +1380,8 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     FastShape shape;
     {
         wake_status fs = (ions || rk4 || cfg->grid_nr > 0) ? WAKE_OK
-                                       : fast_shape_for(h->prec, n, cfg->rings_per_thread, cfg->cluster_ctas, &shape);
+                                       : wake_shape_for(h->prec, n, cfg->n_steps, cfg->rings_per_thread,
+                                                        cfg->cluster_ctas, &shape);
         if (fs != WAKE_OK) {
             delete h;
             return fs;

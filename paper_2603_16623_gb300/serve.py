@@ -200,7 +200,7 @@ class WakeServer:
                 break
             self.queue.popleft()
             shape = self.tuning.shape_for(req.n_rings, "mixed") if self.tuning is not None else {}
-            req.sm_share = sm_share(wm.wake_launch_shape(req.n_rings, **shape))
+            req.sm_share = sm_share(wm.wake_launch_shape(req.n_rings, n_steps=req.n_steps, **shape))
             self.used += est
             self.sm_used += req.sm_share
             picked.append((req, est, shape))

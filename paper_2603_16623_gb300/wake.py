@@ -84,8 +84,12 @@ _SIGS = {
     "wake_destroy": ([_vp], None),
     "wake_last_error": ([], C.c_char_p),
     "wake_max_rings": ([C.c_int32], C.c_int32),
-    "wake_launch_shape": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                           C.POINTER(C.c_int32)], C.c_int),
+    "wake_launch_shape": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+    "wake_launch_shape_latency": ([C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)], C.c_int),
+    "wake_set_latency_shape_ms": ([C.c_double], C.c_int),
+    "wake_get_latency_shape_ms": ([], C.c_double),
     "wake_max_slice_particles": ([C.c_int32], C.c_int64),
     "wake_measure_peaks": ([C.c_void_p], C.c_int),
 }
@@ -470,15 +474,38 @@ def wake_max_rings(precision: str = "mixed") -> int:
     return int(load().wake_max_rings(PRECISION[precision]))
 
 
-def wake_launch_shape(n_rings: int, rings_per_thread: int = 0, cluster_ctas: int = 0, precision: str = "mixed"):
+def wake_launch_shape(n_rings: int, rings_per_thread: int = 0, cluster_ctas: int = 0, precision: str = "mixed",
+                      n_steps: int = 0):
     """(threads per CTA, rings per thread, CTAs per wake) that wake_init
     gives the on-chip march for these fields, computed on the host; (0, 0,
-    0) when the wake runs on a one-CTA march.  WakeError for a shape
-    wake_init would refuse."""
+    0) when the wake runs on a one-CTA march.  n_steps 0: the batch shape;
+    else an automatic-shape wake long enough (latency_shape_ms()) gets the
+    latency shape.  WakeError for a shape wake_init would refuse."""
     t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(load().wake_launch_shape(PRECISION[precision], int(n_rings), int(rings_per_thread), int(cluster_ctas),
-                                    C.byref(t), C.byref(k), C.byref(c)))
+    _check(load().wake_launch_shape(PRECISION[precision], int(n_rings), int(n_steps), int(rings_per_thread),
+                                    int(cluster_ctas), C.byref(t), C.byref(k), C.byref(c)))
     return t.value, k.value, c.value
+
+
+def wake_launch_shape_latency(n_rings: int, precision: str = "mixed"):
+    """(threads per CTA, rings per thread, CTAs per wake) of the latency
+    shape: 2 rings per thread, the shortest time per slice, which wake_init
+    gives automatic-shape wakes whose predicted march time reaches
+    latency_shape_ms()."""
+    t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().wake_launch_shape_latency(PRECISION[precision], int(n_rings), C.byref(t), C.byref(k), C.byref(c)))
+    return t.value, k.value, c.value
+
+
+def set_latency_shape_ms(ms: float) -> None:
+    """Wakes created afterwards whose predicted march time on the batch
+    shape is at least ms milliseconds take the latency shape (0: all;
+    math.inf: none)."""
+    _check(load().wake_set_latency_shape_ms(float(ms)))
+
+
+def latency_shape_ms() -> float:
+    return float(load().wake_get_latency_shape_ms())
 
 
 def wake_max_slice_particles(precision: str = "mixed") -> int:

@@ -105,11 +105,73 @@ def test_the_shape_query_gives_the_automatic_and_explicit_shapes():
     assert wm.wake_launch_shape(65536) == (512, 8, 16)
     assert wm.wake_launch_shape(3000, 8, 0) == (384, 8, 1)
     assert wm.wake_launch_shape(3000, 4, 3) == (256, 4, 3)
+    assert wm.wake_launch_shape(3000, 2, 3) == (512, 2, 3)
+    assert wm.wake_launch_shape(1000, 2, 1) == (512, 2, 1)
     assert wm.wake_launch_shape(4000, precision="fp64") == (0, 0, 0)
     for n in range(1, 65537, 997):
         t, k, c = wm.wake_launch_shape(n)
-        assert 32 <= t <= 512 and t % 32 == 0 and k in (4, 8) and 1 <= c <= 16
+        assert 32 <= t <= 512 and t % 32 == 0 and k in (2, 4, 8) and 1 <= c <= 16
         assert t * k * c >= n and (c == 1 or t * k * (c - 1) < n)
+
+
+def test_the_latency_shape_query():
+    """The latency shapes (2 rings per thread: one CTA up to 1024 rings,
+    clusters of CTAs of <= 512 rings up to 8192, of <= 1024 rings up to
+    16,384, then the batch shape); every CTA holds rings and none more than
+    its threads x 2; an explicit request for the same shape gives it."""
+    from paper_2603_16623_gb300 import wake as wm
+    wm.load()
+    assert wm.wake_launch_shape_latency(200) == (128, 2, 1)
+    assert wm.wake_launch_shape_latency(1024) == (512, 2, 1)
+    assert wm.wake_launch_shape_latency(1025) == (192, 2, 3)
+    assert wm.wake_launch_shape_latency(6587) == (256, 2, 13)
+    assert wm.wake_launch_shape_latency(8192) == (256, 2, 16)
+    assert wm.wake_launch_shape_latency(8193) == (480, 2, 9)
+    assert wm.wake_launch_shape_latency(16384) == (512, 2, 16)
+    assert wm.wake_launch_shape_latency(16385) == wm.wake_launch_shape(16385)
+    assert wm.wake_launch_shape_latency(65536) == (512, 8, 16)
+    assert wm.wake_launch_shape_latency(4000, precision="fp64") == (0, 0, 0)
+    for n in range(1, 16385, 37):
+        t, k, c = wm.wake_launch_shape_latency(n)
+        assert k == 2 and 32 <= t <= 512 and t % 32 == 0 and 1 <= c <= 16
+        assert t * k * c >= n and (c == 1 or t * k * (c - 1) < n)
+        assert wm.wake_launch_shape(n, k, c) == (t, k, c)
+    for bad in (0, 65537):
+        with pytest.raises(wm.WakeError):
+            wm.wake_launch_shape_latency(bad)
+
+
+def test_long_wakes_get_the_latency_shape():
+    """An automatic-shape wake whose predicted march time on the batch shape
+    reaches the threshold (off by default) gets the latency shape; a short
+    one, n_steps 0 and explicit shapes keep theirs; the threshold is
+    validated and applies to what is created afterwards."""
+    import math
+    from paper_2603_16623_gb300 import wake as wm
+    wm.load()
+    assert wm.latency_shape_ms() == math.inf
+    assert wm.wake_launch_shape(6587, n_steps=10 ** 6) == (256, 4, 7)
+    wm.set_latency_shape_ms(100.0)
+    batch = wm.wake_launch_shape(6587)
+    assert batch == (256, 4, 7)
+    assert wm.wake_launch_shape(6587, n_steps=5664) == wm.wake_launch_shape_latency(6587)  # ~206 ms predicted
+    assert wm.wake_launch_shape(6587, n_steps=1000) == batch  # ~36 ms
+    assert wm.wake_launch_shape(6587, 4, 7, n_steps=5664) == batch
+    assert wm.wake_launch_shape(700, n_steps=6000) == (192, 4, 1)  # ~86 ms
+    assert wm.wake_launch_shape(700, n_steps=8000) == wm.wake_launch_shape_latency(700)  # ~115 ms
+    assert wm.wake_launch_shape(4000, n_steps=10 ** 6, precision="fp64") == (0, 0, 0)
+    with pytest.raises(wm.WakeError):
+        wm.wake_launch_shape(6587, n_steps=-1)
+    for bad in (-0.1, float("nan")):
+        with pytest.raises(wm.WakeError):
+            wm.set_latency_shape_ms(bad)
+    try:
+        wm.set_latency_shape_ms(math.inf)
+        assert wm.wake_launch_shape(6587, n_steps=10 ** 6) == batch
+        wm.set_latency_shape_ms(0.0)
+        assert wm.wake_launch_shape(3000, n_steps=1) == wm.wake_launch_shape_latency(3000)
+    finally:
+        wm.set_latency_shape_ms(math.inf)
 
 
 @pytest.mark.parametrize("case,why", [

@@ -182,33 +182,68 @@ def test_mixed_blowout_first_1000_steps_within_tolerance():
 
 
 def test_mixed_ring_crossings_within_tolerance():
-    _mixed_window_check(axis_wake(steps=500), 128)
+    # automatic shape and 2 rings per thread (the re-sort's merge rounds move
+    # rings K places per round)
+    _mixed_window_check(axis_wake(steps=500), 128, shapes=((0, 0), (2, 1)))
 
 
 def test_mixed_cluster_wakes_match_oracle():
-    """Wakes wider than one CTA run on a thread-block cluster (2048 rings per
-    CTA): a nearly empty second CTA (2049 rings), three CTAs with a wide
-    driver pushing rings across the first CTA boundary (ring 2048 sits at
-    rho ~ 2.5 inside the blowout sheath), and four full CTAs."""
-    cases = [(2049, 5.0, 0.5, 0.5), (4915, 6.0, 2.0, 1.0), (8192, 6.0, 1.0, 0.6)]
-    for n, r_max, nb0, sr in cases:
+    """Wakes wider than one CTA run on a thread-block cluster: a nearly empty
+    last CTA (2049 rings), a wide driver pushing rings across the CTA
+    boundaries (4915 rings, also on five CTAs of 512 threads x 2 rings), and
+    full CTAs (8192 rings)."""
+    cases = [(2049, 5.0, 0.5, 0.5, ((0, 0),)), (4915, 6.0, 2.0, 1.0, ((0, 0), (2, 5))),
+             (8192, 6.0, 1.0, 0.6, ((0, 0),))]
+    for n, r_max, nb0, sr, shapes in cases:
         drv = W.gaussian_beam(40_000, nb0, sr, 0.6, 2.4, seed=n)
         wk = W.Wake(f"cl{n}", W.edges_uniform(n, r_max), [drv], 0.01, 300)
-        _mixed_window_check(wk, 0)
+        _mixed_window_check(wk, 0, shapes)
 
 
 def test_mixed_explicit_launch_shapes_match_oracle():
     """Every (rings per thread, CTAs per wake) shape the caller may pick gives
-    the oracle's wake: 8 rings per thread in one CTA, clusters of 2-6 CTAs of
-    4 or 8 rings per thread.  (With n_b0 = 2 and sigma_r = 1 the 6000-ring
+    the oracle's wake: 2 or 8 rings per thread in one CTA, clusters of 2-6
+    CTAs of 2, 4 or 8 rings per thread.  (With n_b0 = 2 and sigma_r = 1 the 6000-ring
     wake's trajectories part from the oracle's after ~140 slices in every
     shape alike, the automatic one included: that wake's sensitivity, not a
     shape's error; hence the milder driver there.)"""
-    for n, nb0, sr, shapes in ((3000, 2.0, 1.0, ((8, 1), (4, 3), (8, 2))),
-                               (6000, 1.0, 0.6, ((8, 2), (4, 6), (8, 3)))):
+    for n, nb0, sr, shapes in ((1000, 2.0, 1.0, ((2, 1),)),
+                               (3000, 2.0, 1.0, ((8, 1), (4, 3), (8, 2), (2, 3))),
+                               (6000, 1.0, 0.6, ((8, 2), (4, 6), (8, 3), (2, 6)))):
         drv = W.gaussian_beam(40_000, nb0, sr, 0.6, 2.4, seed=n)
         wk = W.Wake(f"shape{n}", W.edges_uniform(n, 6.0), [drv], 0.01, 300)
         _mixed_window_check(wk, 0, shapes)
+
+
+def test_long_wakes_take_the_latency_shape():
+    """With the latency-shape threshold at 0 every automatic-shape wake is
+    created on its latency shape (2 rings per thread): the oracle's wake,
+    and bitwise the wake created with that shape asked for explicitly; a
+    batch of such wakes equals them alone."""
+    wm = _wake_mod()
+    drv = W.gaussian_beam(40_000, 2.0, 1.0, 0.6, 2.4, seed=3000)
+    wk = W.Wake("lat3000", W.edges_uniform(3000, 6.0), [drv], 0.01, 300)
+    small = W.Wake("lat700", W.edges_uniform(700, 6.0), [drv], 0.01, 300)
+    try:
+        wm.set_latency_shape_ms(0.0)
+        assert wm.wake_launch_shape(3000, n_steps=300) == wm.wake_launch_shape_latency(3000) == (256, 2, 6)
+        _mixed_window_check(wk, 0)
+        a = gpu_run(wk, "mixed")
+        gs = [wm.Wake.from_workload(w, precision="mixed") for w in (wk, small)]
+        assert gs[0].launch_config() == (256, 2, 6) and gs[1].launch_config() == (352, 2, 1)
+        wm.wake_batch_run(gs)
+        batched = [g.beam_fields() for g in gs]
+        alone_small = gpu_run(small, "mixed", dumps=False)
+    finally:
+        wm.set_latency_shape_ms(float("inf"))
+    b = gpu_run(wk, "mixed", shape=(2, 6))
+    for k in a["beam"]:
+        assert np.array_equal(a["beam"][k], b["beam"][k]), k
+        assert np.array_equal(batched[0][k], b["beam"][k]), k
+        assert np.array_equal(batched[1][k], alone_small["beam"][k]), k
+    assert np.array_equal(a["final"][0], b["final"][0])
+    for g in gs:
+        g.close()
 
 
 def test_mixed_large_wake_65536_rings_first_slices():
