@@ -578,8 +578,12 @@ wake_status wake_shape_for(int32_t prec, int32_t n, int32_t n_steps, int32_t wan
 // runs the preparations (short kernels that every march waits for: a
 // preparation that waited behind pending march blocks would hold back its
 // wake's march); levels 1.. the marches by tier, so that when the SMs are
-// full the pending blocks of the longest wakes are dispatched first.
-constexpr int kPrioLevels = 4, kStreamsPerLevel = 16, kAuxStreams = kPrioLevels * kStreamsPerLevel;
+// full the pending blocks of the longest wakes are dispatched first.  Each
+// launch group of a tier needs a stream of its own: two launches on one
+// stream run one after the other, so a group queued behind a long one
+// would start only when that one ends (with 16 streams per level the
+// 256-wake batch's 25 tier-1 groups did exactly that).
+constexpr int kPrioLevels = 4, kStreamsPerLevel = 128, kAuxStreams = kPrioLevels * kStreamsPerLevel;
 constexpr int kTiers = kPrioLevels - 1;
 cudaError_t level_stream(int level, int i, cudaStream_t* out) {
     static cudaStream_t pool[kAuxStreams] = {nullptr};
@@ -888,7 +892,7 @@ constexpr double kTierFrac[kTiers - 1] = {0.5, 0.2};
 std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
     double t_all = 0.0;
     for (int32_t i = 0; i < n; ++i) t_all = std::max(t_all, predicted_ms(hs[i]));
-    std::vector<std::pair<int64_t, int>> keys;  // (configuration, tier)
+    std::vector<std::pair<int64_t, int>> keys;  // (configuration and band, tier)
     std::vector<LaunchGroup> groups;
     for (int32_t i = 0; i < n; ++i) {
         int64_t key = ((int64_t)hs[i]->fast_threads * 16 + (hs[i]->fast_threads ? hs[i]->fast_k : 0)) * 32 +
@@ -899,6 +903,13 @@ std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
         const double t = predicted_ms(hs[i]);
         int tier = 0;
         while (tier + 1 < kTiers && t < kTierFrac[tier] * t_all) ++tier;
+        // bands of predicted time (each 1/1.25 of the one before) split a
+        // configuration's wakes into launches, so that the launches of a tier,
+        // submitted longest band first, reach the SMs longest first across
+        // configurations (same-priority launches are dispatched in about the
+        // order they were submitted)
+        const int band = t > 0.0 && t_all > 0.0 ? std::min(63, (int)std::floor(std::log(t_all / t) / std::log(1.25))) : 63;
+        key = key * 64 + band;
         auto it = std::find(keys.begin(), keys.end(), std::make_pair(key, tier));
         if (it == keys.end()) {
             keys.emplace_back(key, tier);
@@ -958,7 +969,7 @@ wake_status batch_reset_run_impl(int32_t n, wake_handle* const* hs, const wake_b
                                  const int32_t* n_beams = nullptr) {
     cudaStream_t st = hs[0]->st;
     std::vector<LaunchGroup> groups = plan_launches(n, hs);
-    constexpr int kPrepStreams = kStreamsPerLevel;
+    constexpr int kPrepStreams = 16;
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     WK_CUDA(cudaEventRecord(start, st));
