@@ -227,11 +227,23 @@ def run_ours(args):
     # times (when its launch began on it, when it finished)
     wt = [g.march_times() for g in gs]
     t_first = min(t[0] for t in wt)
+    # the throughput bound: each wake's SM share (its CTAs' share of an SM's
+    # registers at 128 per thread, or of its 2048 thread slots) x its march
+    # time in the batch, summed and spread over the SMs
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def sm_share(g):
+        threads, _, ctas = g.launch_config()
+        per_sm = max(1, min(65536 // (128 * threads), 2048 // threads))
+        return ctas / per_sm
+
     schedule = {"longest_wake_ms": max(t[1] - t[0] for t in wt) / 1e6,
                 "march_span_ms": (max(t[1] for t in wt) - t_first) / 1e6,
+                "sm_time_bound_ms": sum(sm_share(g) * (t[1] - t[0]) for g, t in zip(gs, wt)) / 1e6 / sms,
                 "latest_start_of_the_10_longest_ms": sorted(
                     ((t[1] - t[0], t[0] - t_first) for t in wt), reverse=True)[9][1] / 1e6 if len(wt) >= 10 else None,
-                "note": "device times (globaltimer) of the last timed step; the longest wake is the critical path"}
+                "note": "device times (globaltimer) of the last timed step; the longest wake is the critical path, "
+                        "sm_time_bound the throughput bound (SM shares by registers x in-batch march times / SMs)"}
     pev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     phase_step(pev)
     torch.cuda.synchronize()

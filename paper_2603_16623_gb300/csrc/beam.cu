@@ -105,6 +105,105 @@ __global__ void bin_scatter_kernel(const int32_t* __restrict__ slot, int64_t n, 
     }
 }
 
+// the slice sort's order: radius, then caller index (distinct but for the
+// padding entries, which go last)
+__device__ __forceinline__ bool kv_less(double ka, int32_t va, double kb, int32_t vb) {
+    return ka < kb || (ka == kb && va < vb);
+}
+
+// Sorts keys/vals[0, mp) in shared memory (mp a power of two >= 4, padded
+// with (+inf, INT_MAX)); keys2/vals2 are as large, scratch.  Runs of four
+// entries are sorted in registers (a bitonic network), then runs of 4, 8,
+// ... are merged pairwise from one buffer into the other: each group of
+// four outputs finds by a merge-path search how many of its predecessors
+// come from the first run and merges its four outputs sequentially; the
+// block's threads take the groups in turn.  log2(mp / 4) rounds of one
+// block barrier and O(mp log mp) shared-memory traffic (a bitonic network
+// over the block costs O(mp log^2 mp) with a barrier per stage).  The
+// order is total, so the result is the one sort.
+constexpr int kRun = 4;
+__device__ __forceinline__ void merge_sort_smem(double* keys, int32_t* vals, double* keys2, int32_t* vals2,
+                                                int32_t mp) {
+    for (int32_t p0 = (int32_t)threadIdx.x * kRun; p0 < mp; p0 += (int32_t)blockDim.x * kRun) {
+        double k[kRun];
+        int32_t v[kRun];
+#pragma unroll
+        for (int e = 0; e < kRun; ++e) {
+            k[e] = keys[p0 + e];
+            v[e] = vals[p0 + e];
+        }
+#pragma unroll
+        for (int k2 = 2; k2 <= kRun; k2 <<= 1)
+#pragma unroll
+            for (int j = k2 >> 1; j > 0; j >>= 1)
+#pragma unroll
+                for (int i = 0; i < kRun; ++i) {
+                    const int l = i ^ j;
+                    if (l > i && kv_less(k[l], v[l], k[i], v[i]) == ((i & k2) == 0)) {
+                        const double tk = k[i];
+                        const int32_t tv = v[i];
+                        k[i] = k[l];
+                        v[i] = v[l];
+                        k[l] = tk;
+                        v[l] = tv;
+                    }
+                }
+#pragma unroll
+        for (int e = 0; e < kRun; ++e) {
+            keys[p0 + e] = k[e];
+            vals[p0 + e] = v[e];
+        }
+    }
+    __syncthreads();
+    double* sk = keys;
+    int32_t* sv = vals;
+    double* dk = keys2;
+    int32_t* dv = vals2;
+    for (int32_t L = kRun; L < mp; L <<= 1) {
+        for (int32_t p0 = (int32_t)threadIdx.x * kRun; p0 < mp; p0 += (int32_t)blockDim.x * kRun) {
+            const int32_t base = p0 & ~(2 * L - 1), d = p0 - base;
+            const double* ak = sk + base;
+            const int32_t* av = sv + base;
+            const double* bk = ak + L;
+            const int32_t* bv = av + L;
+            int32_t lo = d > L ? d - L : 0, hi = d < L ? d : L;
+            while (lo < hi) {  // outputs before d taken from the first run (it goes first on equality)
+                const int32_t mid = (lo + hi) >> 1;
+                if (kv_less(bk[d - 1 - mid], bv[d - 1 - mid], ak[mid], av[mid])) hi = mid;
+                else lo = mid + 1;
+            }
+            int32_t i = lo, j = d - lo;
+#pragma unroll
+            for (int e = 0; e < kRun; ++e) {
+                const bool take_a = j >= L || (i < L && !kv_less(bk[j], bv[j], ak[i], av[i]));
+                if (take_a) {
+                    dk[p0 + e] = ak[i];
+                    dv[p0 + e] = av[i];
+                    ++i;
+                } else {
+                    dk[p0 + e] = bk[j];
+                    dv[p0 + e] = bv[j];
+                    ++j;
+                }
+            }
+        }
+        __syncthreads();
+        double* tk = sk;
+        sk = dk;
+        dk = tk;
+        int32_t* tv = sv;
+        sv = dv;
+        dv = tv;
+    }
+    if (sk != keys) {  // an odd number of rounds: back into keys/vals
+        for (int32_t i = threadIdx.x; i < mp; i += blockDim.x) {
+            keys[i] = sk[i];
+            vals[i] = sv[i];
+        }
+        __syncthreads();
+    }
+}
+
 // one block per slice (grid-stride over slices) sorting the slices of
 // min_m < m <= m_pad particles; m_pad a power of two, keys double, values
 // caller index, prefix double.  A slice denser than m_pad is left to a later
@@ -131,7 +230,7 @@ __global__ void slice_sort_kernel(const int32_t* __restrict__ off, int32_t n_ste
             }
             continue;
         }
-        int32_t mp = 1;
+        int32_t mp = kRun;
         while (mp < m) mp <<= 1;
         for (int32_t i = threadIdx.x; i < mp; i += blockDim.x) {
             if (i < m) {
@@ -144,23 +243,7 @@ __global__ void slice_sort_kernel(const int32_t* __restrict__ off, int32_t n_ste
             }
         }
         __syncthreads();
-        for (int32_t k = 2; k <= mp; k <<= 1) {
-            for (int32_t j = k >> 1; j > 0; j >>= 1) {
-                for (int32_t i = threadIdx.x; i < mp; i += blockDim.x) {
-                    int32_t ixj = i ^ j;
-                    if (ixj > i) {
-                        double ki = keys[i], kj = keys[ixj];
-                        int32_t vi = vals[i], vj = vals[ixj];
-                        bool gt = (ki > kj) || (ki == kj && vi > vj);
-                        if (gt == ((i & k) == 0)) {
-                            keys[i] = kj; keys[ixj] = ki;
-                            vals[i] = vj; vals[ixj] = vi;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        merge_sort_smem(keys, vals, pre, vals + m_pad, mp);
         // exclusive prefix of charge x weight in sorted order (FP64)
         double carry = 0.0;
         for (int32_t base = 0; base < m; base += blockDim.x) {
@@ -244,7 +327,7 @@ cudaError_t launch_bin_scatter(const int32_t* slot, int64_t n, int32_t n_steps, 
     return cudaGetLastError();
 }
 
-size_t slice_sort_smem(int32_t m_pad) { return (size_t)m_pad * (8 + 8 + 4); }
+size_t slice_sort_smem(int32_t m_pad) { return (size_t)m_pad * (8 + 8 + 4 + 4); }  // keys, prefix, values, scratch
 
 cudaError_t launch_reset_ctl(int32_t* ctl, cudaStream_t st) {
     reset_ctl_kernel<<<1, 32, 0, st>>>(ctl);
