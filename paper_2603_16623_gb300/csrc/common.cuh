@@ -140,6 +140,12 @@ __device__ __forceinline__ float shfl_up_t(float v, int o) { return __shfl_up_sy
 __device__ __forceinline__ float shfl_dn_t(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ ff shfl_up_t(ff v, int o) { return {shfl_up_t(v.hi, o), shfl_up_t(v.lo, o)}; }
 __device__ __forceinline__ ff shfl_dn_t(ff v, int o) { return {shfl_dn_t(v.hi, o), shfl_dn_t(v.lo, o)}; }
+__device__ __forceinline__ double shfl_idx_t(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ float shfl_idx_t(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ int64_t shfl_idx_t(int64_t v, int l) {
+    return (int64_t)__shfl_sync(0xffffffffu, (long long)v, l);
+}
+__device__ __forceinline__ ff shfl_idx_t(ff v, int l) { return {shfl_idx_t(v.hi, l), shfl_idx_t(v.lo, l)}; }
 
 template <class T>
 struct Pair {
@@ -149,6 +155,8 @@ template <class T>
 __device__ __forceinline__ Pair<T> shfl_up_t(Pair<T> v, int o) { return {shfl_up_t(v.x, o), shfl_up_t(v.y, o)}; }
 template <class T>
 __device__ __forceinline__ Pair<T> shfl_dn_t(Pair<T> v, int o) { return {shfl_dn_t(v.x, o), shfl_dn_t(v.y, o)}; }
+template <class T>
+__device__ __forceinline__ Pair<T> shfl_idx_t(Pair<T> v, int l) { return {shfl_idx_t(v.x, l), shfl_idx_t(v.y, l)}; }
 
 // two accumulators and an integer count scanned together
 template <class T>
@@ -163,6 +171,10 @@ __device__ __forceinline__ Trip<T> shfl_up_t(Trip<T> v, int o) {
 template <class T>
 __device__ __forceinline__ Trip<T> shfl_dn_t(Trip<T> v, int o) {
     return {shfl_dn_t(v.x, o), shfl_dn_t(v.y, o), shfl_dn_t(v.c, o)};
+}
+template <class T>
+__device__ __forceinline__ Trip<T> shfl_idx_t(Trip<T> v, int l) {
+    return {shfl_idx_t(v.x, l), shfl_idx_t(v.y, l), shfl_idx_t(v.c, l)};
 }
 
 // 2x2 matrix and the affine map x -> M x + c
@@ -181,6 +193,10 @@ __device__ __forceinline__ Mat2<R> shfl_up_t(Mat2<R> v, int o) {
 template <class R>
 __device__ __forceinline__ Mat2<R> shfl_dn_t(Mat2<R> v, int o) {
     return {shfl_dn_t(v.m00, o), shfl_dn_t(v.m01, o), shfl_dn_t(v.m10, o), shfl_dn_t(v.m11, o)};
+}
+template <class R>
+__device__ __forceinline__ Mat2<R> shfl_idx_t(Mat2<R> v, int l) {
+    return {shfl_idx_t(v.m00, l), shfl_idx_t(v.m01, l), shfl_idx_t(v.m10, l), shfl_idx_t(v.m11, l)};
 }
 template <class R>
 __device__ __forceinline__ Aff2<R> shfl_up_t(Aff2<R> v, int o) {
@@ -366,6 +382,85 @@ __device__ void block_excl_scan_mat_fwd_rev(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>
                                             Mat2<R>& er) {
     Mat2<R> tf, tr;
     block_excl_scan_mat_fwd_rev_t<false>(mf, mr, sbuf, ef, er, tf, tr);
+}
+
+// One-barrier forms of the three block scans above, with the same
+// arithmetic in the same order (bitwise the same results): every warp scans
+// the warp totals itself instead of warp 0 scanning them between two more
+// barriers.  sbuf needs nw (not 33) values; every warp reads it after the
+// one barrier, so it must not be written again before a later barrier:
+// consecutive calls without a barrier between them alternate two buffers.
+template <bool REV, class T, class Op>
+__device__ __forceinline__ T block_excl_scan1(T v, Op op, T ident, T* sbuf, T& total) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    T inc = warp_incl_scan<REV>(v, op);
+    T lex = REV ? shfl_dn_t(inc, 1) : shfl_up_t(inc, 1);
+    if (REV ? (lane == 31) : (lane == 0)) lex = ident;
+    if (REV ? (lane == 0) : (lane == 31)) sbuf[warp] = inc;
+    __syncthreads();
+    T wv = lane < nw ? sbuf[lane] : ident;
+    T winc = warp_incl_scan<REV>(wv, op);
+    T wex = REV ? shfl_dn_t(winc, 1) : shfl_up_t(winc, 1);
+    if (REV ? (lane == 31) : (lane == 0)) wex = ident;
+    total = shfl_idx_t(winc, REV ? 0 : 31);
+    return op(shfl_idx_t(wex, warp), lex);
+}
+
+template <class T>
+__device__ __forceinline__ Pair<T> block_excl_scan_fwd_rev1(T fx, T ry, T zero, Pair<T>* sbuf, T& tx, T& ty) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    T ix = warp_incl_scan<false>(fx, OpAdd());
+    T iy = warp_incl_scan<true>(ry, OpAdd());
+    T ex = shfl_up_t(ix, 1), ey = shfl_dn_t(iy, 1);
+    if (lane == 0) ex = zero;
+    if (lane == 31) ey = zero;
+    if (lane == 31) sbuf[warp].x = ix;
+    if (lane == 0) sbuf[warp].y = iy;
+    __syncthreads();
+    T wx = lane < nw ? sbuf[lane].x : zero;
+    T wy = lane < nw ? sbuf[lane].y : zero;
+    T sx = warp_incl_scan<false>(wx, OpAdd());
+    T sy = warp_incl_scan<true>(wy, OpAdd());
+    T qx = shfl_up_t(sx, 1), qy = shfl_dn_t(sy, 1);
+    if (lane == 0) qx = zero;
+    if (lane == 31) qy = zero;
+    tx = shfl_idx_t(sx, 31);
+    ty = shfl_idx_t(sy, 0);
+    return {acc_add(shfl_idx_t(qx, warp), ex), acc_add(shfl_idx_t(qy, warp), ey)};
+}
+
+template <bool TOT, class R>
+__device__ __forceinline__ void block_excl_scan_mat_fwd_rev1(Mat2<R> mf, Mat2<R> mr, Pair<Mat2<R>>* sbuf,
+                                                             Mat2<R>& ef, Mat2<R>& er, Mat2<R>& tf, Mat2<R>& tr) {
+    const Mat2<R> I2 = {1, 0, 0, 1};
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    Mat2<R> ix = warp_incl_scan<false>(mf, OpMatLeft());
+    Mat2<R> iy = warp_incl_scan<true>(mr, OpMatLeft());
+    Mat2<R> ex = shfl_up_t(ix, 1), ey = shfl_dn_t(iy, 1);
+    if (lane == 0) ex = I2;
+    if (lane == 31) ey = I2;
+    if (lane == 31) sbuf[warp].x = ix;
+    if (lane == 0) sbuf[warp].y = iy;
+    __syncthreads();
+    Mat2<R> wx = lane < nw ? sbuf[lane].x : I2;
+    Mat2<R> wy = lane < nw ? sbuf[lane].y : I2;
+    Mat2<R> sx = warp_incl_scan<false>(wx, OpMatLeft());
+    Mat2<R> sy = warp_incl_scan<true>(wy, OpMatLeft());
+    Mat2<R> qx = shfl_up_t(sx, 1), qy = shfl_dn_t(sy, 1);
+    if (lane == 0) qx = I2;
+    if (lane == 31) qy = I2;
+    ef = OpMatLeft()(shfl_idx_t(qx, warp), ex);
+    er = OpMatLeft()(shfl_idx_t(qy, warp), ey);
+    if (TOT) {
+        tf = shfl_idx_t(sx, 31);
+        tr = shfl_idx_t(sy, 0);
+    }
 }
 
 // first index i in [0, n) with a[i] >= x (n if none)

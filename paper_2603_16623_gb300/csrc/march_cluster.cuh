@@ -592,8 +592,9 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         A Wtot, Ltot;
         {
             Trip<A> tot1, pre1, all1;
-            ex1 = block_excl_scan<false>(Trip<A>{sw, sl, cnt}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
-                                         reinterpret_cast<Trip<A>*>(sscan), tot1);
+            // (one-barrier scans: a cluster barrier separates each from the next)
+            ex1 = block_excl_scan1<false>(Trip<A>{sw, sl, cnt}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
+                                          reinterpret_cast<Trip<A>*>(sscan), tot1);
             cluster_push(cl, x1, tot1);
             cl.sync();
             fold_fwd_shared(x1, crank, csize, Trip<A>{zeroA, zeroA, 0}, OpAddTrip(), &f1[0], &f1[1]);
@@ -654,7 +655,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         A Tex, Ttot;
         {
             A Ttot_blk, pre2;
-            Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot_blk);
+            Tex = block_excl_scan1<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot_blk);
             cluster_push(cl, x2, Ttot_blk);
             cl.sync();
             fold_fwd_shared(x2, crank, csize, zeroA, OpAdd(), &f2[0], &f2[1]);
@@ -712,7 +713,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
         {
             // this CTA's forward and reverse products go to every CTA
             Mat2<R> tf, tb;
-            block_excl_scan_mat_fwd_rev_t<true>(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb, tf, tb);
+            block_excl_scan_mat_fwd_rev1<true>(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb, tf, tb);
             if (tid < csize) {
                 *rmt(cl, &x3f[crank], tid) = tf;
                 *rmt(cl, &x3r[crank], tid) = tb;
@@ -770,7 +771,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
             Dp0b = Y.m11;
         }
         A g_tot, d_tot;
-        Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
+        Pair<A> gd = block_excl_scan_fwd_rev1(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
         A all4f;
         {
             if (tid < csize) {

@@ -578,8 +578,10 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             }
         }
         Trip<A> tot1;
-        Trip<A> ex1 = block_excl_scan<false>(Trip<A>{sw, sl, cl}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
-                                             reinterpret_cast<Trip<A>*>(sscan), tot1);
+        // (the four scans of a slice alternate the two halves of sscan: each
+        // half is rewritten only after another scan's barrier)
+        Trip<A> ex1 = block_excl_scan1<false>(Trip<A>{sw, sl, cl}, OpAddTrip(), Trip<A>{zeroA, zeroA, 0},
+                                              reinterpret_cast<Trip<A>*>(sscan), tot1);
         const A Wtot = tot1.x, Ltot = tot1.y;
 
         // ---------------- a5: psi, d_rho psi, psibar, gamma, t; beam field
@@ -629,7 +631,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             }
         }
         A Ttot;
-        A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot);
+        A Tex = block_excl_scan1<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan + kScanBytes / 2), Ttot);
 
         // ---------------- a6 + a7: d_zeta psi, A, B, C, ring sources
         const Mat2<R> I2 = {1, 0, 0, 1};
@@ -678,7 +680,10 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
 
         // ---------------- a8: B_theta^(p) region coefficients
         Mat2<R> Yf, Yb;
-        block_excl_scan_mat_fwd_rev(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb);
+        {
+            Mat2<R> tf, tb;
+            block_excl_scan_mat_fwd_rev1<false>(Mf, Mb, reinterpret_cast<Pair<Mat2<R>>*>(sscan), Yf, Yb, tf, tb);
+        }
         R Rra[K], Rrb[K], Dda[K], Ddb[K];  // R_{p+1}, D_{p+1}
         {
             Mat2<R> Y = Yf;
@@ -724,7 +729,8 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
         // G_k = sum_{p >= k} gamma_p must be a true suffix sum: a total minus a
         // prefix cancels where G_k is small and multiplies R_k ~ e^rho
         A g_tot, d_tot;
-        Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
+        Pair<A> gd = block_excl_scan_fwd_rev1(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan + kScanBytes / 2), d_tot,
+                                              g_tot);
         {
             R Gk[K];
             A Gsuf = gd.y;  // sum over rings >= p0 + K
