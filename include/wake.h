@@ -410,6 +410,14 @@ wake_status wake_fields_at_static(wake_handle *h, int64_t n, const double *r, vo
    the call does not wait for the device. */
 void wake_destroy(wake_handle *h);
 
+/* Debug builds only (compiled with -DWAKE_BOUNDS_CHECK: python -m
+   paper_2603_16623_gb300.build --bounds-check): how many swizzled
+   shared-memory positions and DSMEM peer ranks out of range the on-chip
+   marches met since the last call (each was replaced by 0, an index in
+   range, and counted), and resets the count.  -1 in a build without the
+   checks, -2 if the counters could not be read (a CUDA error). */
+int64_t wake_debug_bounds_violations(void);
+
 const char *wake_last_error(void);
 int32_t wake_max_rings(int32_t precision);          /* rings per wake supported */
 int64_t wake_max_slice_particles(int32_t precision); /* beam particles per slice */

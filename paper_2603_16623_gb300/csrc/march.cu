@@ -194,6 +194,17 @@ cudaError_t launch_march_fast(const WakeDev<PrecMixed>* d_wakes, const int32_t* 
     return launch_fast_k<8>(d_wakes, d_order, n_wakes, max_slices, mode, threads, stage_particles, st);
 }
 
+int64_t march_bounds_violations() {
+#ifdef WAKE_BOUNDS_CHECK
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_violations, sizeof(v)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(g_bounds_violations, &z, sizeof(z)) != cudaSuccess) return -2;
+    return (int64_t)v;
+#else
+    return -1;
+#endif
+}
+
 // (next slice, status) of n wakes into out[2n], one thread per wake
 __global__ void gather_ctl_kernel(const int32_t* const* __restrict__ ctls, int32_t n, int32_t* __restrict__ out) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;

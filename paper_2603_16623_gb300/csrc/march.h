@@ -29,6 +29,11 @@ int32_t march_stage_particles(int32_t threads, int32_t k_rings, int32_t cluster_
 cudaError_t launch_march_cluster(const WakeDev<PrecMixed>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                                  int32_t max_slices, int32_t mode, int32_t threads, int32_t k_rings, int32_t cl,
                                  int32_t stage_particles, cudaStream_t st);
+// debug build (WAKE_BOUNDS_CHECK): out-of-range shared-memory positions and
+// DSMEM ranks the on-chip marches met since the last call (march.cu's and
+// march_k2.cu's kernels respectively); -1 in other builds, -2 on a CUDA error
+int64_t march_bounds_violations();
+int64_t march_k2_bounds_violations();
 // gathers (next slice, status) of n wakes' control words into out[2n]
 cudaError_t launch_gather_ctl(const int32_t* const* ctls, int32_t n, int32_t* out, cudaStream_t st);
 // n cells; n_total = n (electrons) or 2 n (electrons, then mobile ions)

@@ -31,6 +31,9 @@ namespace cg = cooperative_groups;
 
 template <class T>
 __device__ __forceinline__ T* rmt(cg::cluster_group& cl, T* p, int rank) {
+#ifdef WAKE_BOUNDS_CHECK
+    rank = bounds_checked(rank, (int)cl.num_blocks());
+#endif
     return cl.map_shared_rank(p, rank);
 }
 

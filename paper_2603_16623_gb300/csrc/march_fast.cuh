@@ -37,6 +37,21 @@
 
 namespace gbwake {
 
+#ifdef WAKE_BOUNDS_CHECK
+// Debug build: every swizzled shared-memory position and every DSMEM peer
+// rank is checked; one out of range is counted here (one counter per
+// translation unit, read by the march_*_bounds_violations functions) and
+// replaced by 0, which is always in range, so that the kernel goes on.
+static __device__ unsigned long long g_bounds_violations;
+__device__ __forceinline__ int bounds_checked(int i, int n) {
+    if (i < 0 || i >= n) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        return 0;
+    }
+    return i;
+}
+#endif
+
 template <int K>
 struct Swz {
     // position p (thread p/K, slot p%K) -> shared-memory word; XOR-swizzle of
@@ -44,6 +59,9 @@ struct Swz {
     // hit 32 distinct banks
     static constexpr int kShift = (K == 2) ? 4 : (K == 4) ? 3 : (K == 8 ? 2 : (K == 16 ? 1 : 0));
     __device__ __forceinline__ static int at(int p) {
+#ifdef WAKE_BOUNDS_CHECK
+        p = bounds_checked(p, (int)blockDim.x * K);
+#endif
         int t = p / K, j = p % K;
         return t * K + (j ^ ((t >> kShift) & (K - 1)));
     }

@@ -18,4 +18,15 @@ cudaError_t launch_march_cluster_k2(const WakeDev<PrecMixed>* d_wakes, const int
     return launch_cluster_k<2>(d_wakes, d_order, n_wakes, max_slices, mode, threads, cl, stage_particles, st);
 }
 
+int64_t march_k2_bounds_violations() {
+#ifdef WAKE_BOUNDS_CHECK
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_violations, sizeof(v)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(g_bounds_violations, &z, sizeof(z)) != cudaSuccess) return -2;
+    return (int64_t)v;
+#else
+    return -1;
+#endif
+}
+
 }  // namespace gbwake

@@ -1254,6 +1254,13 @@ extern "C" {
 
 const char* wake_last_error(void) { return g_err.c_str(); }
 
+int64_t wake_debug_bounds_violations(void) {
+    const int64_t a = march_bounds_violations(), b = march_k2_bounds_violations();
+    if (a == -1 && b == -1) return -1;
+    if (a < 0 || b < 0) return -2;
+    return a + b;
+}
+
 int32_t wake_max_rings(int32_t precision) {
     return precision == WAKE_MIXED ? kMaxRingsMixed : kMaxRings;
 }

@@ -92,6 +92,7 @@ _SIGS = {
     "wake_get_latency_shape_ms": ([], C.c_double),
     "wake_max_slice_particles": ([C.c_int32], C.c_int64),
     "wake_measure_peaks": ([C.c_void_p], C.c_int),
+    "wake_debug_bounds_violations": ([], C.c_int64),
 }
 
 
@@ -115,20 +116,26 @@ def measure_peaks() -> Dict[str, float]:
 _lib = None
 
 
+def _bounds_check() -> bool:
+    return os.environ.get("GBWAKE_BOUNDS_CHECK", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.lib_for(_bounds_check())
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
-    """Load libwake.so (building it first if needed).  Raises if it cannot
-    be loaded: the solver has no other implementation."""
+    """Load libwake.so (building it first if needed; the bounds-checking
+    debug build when GBWAKE_BOUNDS_CHECK=1).  Raises if it cannot be loaded:
+    the solver has no other implementation."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not os.path.exists(path) or not _build.up_to_date():
+        bc = _bounds_check()
+        path = _build.lib_for(bc)
+        if not os.path.exists(path) or not _build.up_to_date(bc):
             if not build_if_missing:
                 raise OSError(f"{path} is missing; run python -m paper_2603_16623_gb300.build")
-            _build.build()
+            _build.build(bounds_check=bc)
         lib = C.CDLL(path)
         for name, (args, res) in _SIGS.items():
             fn = getattr(lib, name)
@@ -506,6 +513,12 @@ def set_latency_shape_ms(ms: float) -> None:
 
 def latency_shape_ms() -> float:
     return float(load().wake_get_latency_shape_ms())
+
+
+def debug_bounds_violations() -> int:
+    """Out-of-range shared-memory positions and DSMEM ranks met since the
+    last call (bounds-checking debug build); -1 in the normal build."""
+    return int(load().wake_debug_bounds_violations())
 
 
 def wake_max_slice_particles(precision: str = "mixed") -> int:

@@ -114,6 +114,16 @@ def test_the_shape_query_gives_the_automatic_and_explicit_shapes():
         assert t * k * c >= n and (c == 1 or t * k * (c - 1) < n)
 
 
+def test_the_normal_build_has_no_bounds_checks():
+    """wake_debug_bounds_violations answers -1 (no checks compiled in)
+    without touching a device; the checking build is a separate library."""
+    from paper_2603_16623_gb300 import build, wake as wm
+    wm.load()
+    if os.environ.get("GBWAKE_BOUNDS_CHECK", "") != "1":
+        assert wm.debug_bounds_violations() == -1
+    assert build.lib_for(True) != build.lib_for(False)
+
+
 def test_the_latency_shape_query():
     """The latency shapes (2 rings per thread: one CTA up to 1024 rings,
     clusters of CTAs of <= 512 rings up to 8192, of <= 1024 rings up to
