@@ -889,7 +889,10 @@ struct LaunchGroup {
 // two levels sharing a priority measured 15-20 % slower steps)
 constexpr double kTierFrac[kTiers - 1] = {0.5, 0.2};
 
-std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
+// whole_window = false (steps bounded by a time budget, as the serving loop
+// runs them): one launch per configuration, all in tier 0 -- every step ends
+// at the budget anyway, and fewer launches mean less host time per step.
+std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs, bool whole_window = true) {
     double t_all = 0.0;
     for (int32_t i = 0; i < n; ++i) t_all = std::max(t_all, predicted_ms(hs[i]));
     std::vector<std::pair<int64_t, int>> keys;  // (configuration and band, tier)
@@ -902,13 +905,15 @@ std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs) {
                                           8 * hs[i]->threads);
         const double t = predicted_ms(hs[i]);
         int tier = 0;
-        while (tier + 1 < kTiers && t < kTierFrac[tier] * t_all) ++tier;
+        while (whole_window && tier + 1 < kTiers && t < kTierFrac[tier] * t_all) ++tier;
         // bands of predicted time (each 1/1.25 of the one before) split a
         // configuration's wakes into launches, so that the launches of a tier,
         // submitted longest band first, reach the SMs longest first across
         // configurations (same-priority launches are dispatched in about the
         // order they were submitted)
-        const int band = t > 0.0 && t_all > 0.0 ? std::min(63, (int)std::floor(std::log(t_all / t) / std::log(1.25))) : 63;
+        const int band = !whole_window ? 0
+                       : t > 0.0 && t_all > 0.0 ? std::min(63, (int)std::floor(std::log(t_all / t) / std::log(1.25)))
+                                                : 63;
         key = key * 64 + band;
         auto it = std::find(keys.begin(), keys.end(), std::make_pair(key, tier));
         if (it == keys.end()) {
@@ -933,7 +938,7 @@ wake_status batch_impl(int32_t n, wake_handle* const* hs, int32_t max_slices, in
     // one launch per group, each on its own stream of its tier's priority,
     // ordered after the work already queued on the handles' stream and
     // joined back into it
-    std::vector<LaunchGroup> groups = plan_launches(n, hs);
+    std::vector<LaunchGroup> groups = plan_launches(n, hs, budget_ns <= 0);
     if (groups.size() == 1) return batch_bucket<P>(groups[0].hs, wake_shape(groups[0].hs[0]), st, max_slices, budget_ns);
     cudaEvent_t start;
     WK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
