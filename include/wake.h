@@ -426,8 +426,8 @@ int64_t wake_max_slice_particles(int32_t precision); /* beam particles per slice
    electrons over the ion column, no beam grids) for a wake of n_rings rings
    and n_steps slices and the config's rings_per_thread and cluster_ctas,
    computed on the host: no device, no handle, nothing allocated.  Both 0:
-   the automatic shape, which is the batch shape (the least SM time per
-   slice: one CTA of up to 512 threads x 4 rings up to 2048 rings; up to
+   the automatic shape, which is the batch shape (one CTA of up to 512
+   threads x 2 rings up to 1024 rings, x 4 rings up to 2048 rings; up to
    16,384 rings a cluster of ceil(n / 1024) CTAs of 4 rings per thread; up
    to 32,768 ceil(n / 2048) CTAs; beyond, 8 rings per thread), or, when its
    predicted march time is at least wake_get_latency_shape_ms(), the latency

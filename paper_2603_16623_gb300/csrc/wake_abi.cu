@@ -468,7 +468,8 @@ wake_status init_impl(wake_handle* h, const wake_config* cfg, const wake_plasma_
 }
 
 // The on-chip march (mixed precision).  Automatic shape: one CTA of up to
-// 512 threads x 4 rings for wakes up to 2048 rings; up to 16,384 rings a
+// 512 threads x 2 rings for wakes up to 1024 rings, of up to 512 threads x 4
+// rings up to 2048 rings; up to 16,384 rings a
 // thread-block cluster of ceil(n / 1024) CTAs; up to 32,768 one of
 // ceil(n / 2048) CTAs (16 is the largest cluster GB300 allows); beyond, 8
 // rings per thread.  A caller (or the autotuner) may instead fix the rings per thread
@@ -500,6 +501,13 @@ wake_status fast_shape_for(int32_t prec, int32_t n, int32_t want_k, int32_t want
     if (want_k || want_cl) {
         f.k = want_k ? want_k : 4;
         f.cl = want_cl ? want_cl : (n + f.k * kFastMaxThreads - 1) / (f.k * kFastMaxThreads);
+    } else if (n <= 2 * kFastMaxThreads) {
+        // up to 1024 rings: one CTA at 2 rings per thread (measured on GB300
+        // against 4 per thread: 200 rings 10.4 -> 7.3 us per slice alone, 512
+        // rings 10.4 -> 7.9, 1024 rings 11.5 -> 10.1; packed at its capacity
+        // 14-19 % more ring-slices/s; the 256-wake step unchanged)
+        f.k = 2;
+        f.cl = 1;
     } else if (n <= kRingsPerCta) {
         f.k = 4;
         f.cl = 1;

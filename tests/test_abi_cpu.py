@@ -97,7 +97,9 @@ def test_the_shape_query_gives_the_automatic_and_explicit_shapes():
     one-CTA march (all zeros)."""
     from paper_2603_16623_gb300 import wake as wm
     wm.load()
-    assert wm.wake_launch_shape(200) == (64, 4, 1)
+    assert wm.wake_launch_shape(200) == (128, 2, 1)
+    assert wm.wake_launch_shape(1024) == (512, 2, 1)
+    assert wm.wake_launch_shape(1025) == (288, 4, 1)
     assert wm.wake_launch_shape(2048) == (512, 4, 1)
     assert wm.wake_launch_shape(2049) == (192, 4, 3)
     assert wm.wake_launch_shape(16384) == (256, 4, 16)
@@ -167,8 +169,8 @@ def test_long_wakes_get_the_latency_shape():
     assert wm.wake_launch_shape(6587, n_steps=5664) == wm.wake_launch_shape_latency(6587)  # ~206 ms predicted
     assert wm.wake_launch_shape(6587, n_steps=1000) == batch  # ~36 ms
     assert wm.wake_launch_shape(6587, 4, 7, n_steps=5664) == batch
-    assert wm.wake_launch_shape(700, n_steps=6000) == (192, 4, 1)  # ~86 ms
-    assert wm.wake_launch_shape(700, n_steps=8000) == wm.wake_launch_shape_latency(700)  # ~115 ms
+    assert wm.wake_launch_shape(1500, n_steps=4000) == (384, 4, 1)  # ~75 ms
+    assert wm.wake_launch_shape(1500, n_steps=6000) == wm.wake_launch_shape_latency(1500)  # ~113 ms
     assert wm.wake_launch_shape(4000, n_steps=10 ** 6, precision="fp64") == (0, 0, 0)
     with pytest.raises(wm.WakeError):
         wm.wake_launch_shape(6587, n_steps=-1)

@@ -27,7 +27,7 @@ axis = W.Wake("axis", W.edges_uniform(300, 5.0), [W.gaussian_beam(60_000, 5.0, 0
 cross = W.Wake("cross", W.edges_uniform(4915, 6.0), [W.gaussian_beam(40_000, 2.0, 1.0, 0.6, 2.4, seed=4915)], 0.01,
                300)
 dense = W.Wake("dense", W.edges_uniform(200, 5.0), [W.gaussian_beam(400_000, 5.0, 0.2, 0.3, 1.2, seed=12)], 0.01, 300)
-cases = [(axis, (0, 0)), (axis, (2, 1)), (cross, (0, 0)), (cross, (2, 5)), (cross, (8, 2)), (dense, (0, 0))]
+cases = [(axis, (4, 1)), (axis, (2, 1)), (cross, (0, 0)), (cross, (2, 5)), (cross, (8, 2)), (dense, (4, 1))]
 out = {"violations_before": wm.debug_bounds_violations(), "runs": []}
 for wk, (k, cl) in cases:
     g = wm.Wake.from_workload(wk, precision="mixed", rings_per_thread=k, cluster_ctas=cl)

@@ -45,9 +45,13 @@ def _cases():
     ]
 
 
+# the dense case keeps one CTA of 64 threads x 4 rings: a small stage
+SHAPES = {"dense": {"rings_per_thread": 4, "cluster_ctas": 1}}
+
+
 def _run(wk, flags):
     wm = _wm()
-    g = wm.Wake.from_workload(wk, precision="mixed", flags=flags)
+    g = wm.Wake.from_workload(wk, precision="mixed", flags=flags, **SHAPES.get(wk.name, {}))
     st, _, _, _ = g.run()
     out = {"status": st, "progress": g.progress(), "beam": g.beam_fields(), "state": g.ring_state(history=True),
            "launch": g.launch_config()}
@@ -75,7 +79,7 @@ def test_staged_batch_equals_global_loads_bitwise():
     wakes = _cases()
     out = []
     for flags in (0, wm.WAKE_NO_STAGE):
-        gs = [wm.Wake.from_workload(wk, precision="mixed", flags=flags) for wk in wakes]
+        gs = [wm.Wake.from_workload(wk, precision="mixed", flags=flags, **SHAPES.get(wk.name, {})) for wk in wakes]
         wm.wake_batch_run(gs)
         out.append([(g.progress(), g.beam_fields(which=("ez", "wr")), g.ring_state()) for g in gs])
         for g in gs:
