@@ -221,8 +221,8 @@ class WakeServer:
         self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
 
     def step(self) -> List[Request]:
-        """One scheduling round: advance the running wakes, admit, retire.
-        Returns the requests that finished in this round."""
+        """One scheduling step: advance the running wakes, admit, retire.
+        Returns the requests that finished in this step."""
         # the step is queued first, so that creating the newly admitted
         # wakes (host-side checks and uploads) overlaps it on the device
         stepped = [w for _, w, _ in self.active]
