@@ -477,6 +477,16 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
     R pbv[K], dprv[K], bbv[K];  // psibar, d_rho psi, B^(b) at the rings
     R s0v[K], s1v[K], hav[K];   // B^(p) ring sources c_p and A_p / 2
     R tv[K];                    // t, then d_zeta psi
+    // at 8 rings per thread recomputed where used (the same rounding: the
+    // same reciprocal of the same value), which keeps 16 registers free
+    auto IR = [&](int k) -> R {
+        if constexpr (K >= 8) return __frcp_rn(rh[k]);
+        else return ir[k];
+    };
+    auto IPB = [&](int k) -> R {
+        if constexpr (K >= 8) return __frcp_rn(pbv[k]);
+        else return ipb[k];
+    };
 
     const int slice0 = slice;
     uint64_t t_start = 0;
@@ -623,19 +633,19 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 A psion = r <= rmax ? ff_acc(c0, ff_neg(ff_mul_f(r2, quarter_n))) : ff_neg(ff_mul(Imax, lnr));
                 R psi = ff_to_f(ff_acc(ff_acc(ff_acc(Ltot, ff_neg(L)), ff_mul(S, lnr)), psion));
                 A Sm = ff_acc(S, ff_neg(Ir));
-                R dpr = ff_to_f(ff_acc(Sm, c.wh)) * ir[k];
+                R dpr = ff_to_f(ff_acc(Sm, c.wh)) * IR(k);
                 R pb = 1.f + psi;
                 R ip = __frcp_rn(pb);
                 pbv[k] = pb;
                 ipb[k] = ip;
                 dprv[k] = dpr;
-                tv[k] = c.w.hi * u * ir[k] * ip;
+                tv[k] = c.w.hi * u * IR(k) * ip;
                 sm.D[a] = ff_to_f(Sm);
                 sm.S[a] = ff_to_f(S);
                 sm.psi[a] = psi;
                 R Q = 0.f;
                 if (m > 0) Q = lb < m ? sb.be[lb] : qtot;
-                bbv[k] = Q * inv_2pi_dxi * ir[k];
+                bbv[k] = Q * inv_2pi_dxi * IR(k);
                 if (mode == MODE_MARCH && W.dump_psi) {
                     size_t row = (size_t)slice * n + idv[k];
                     W.dump_psi[row] = psi;
@@ -663,7 +673,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                     const int a = SW::at(p);
                     const float4 cw = __ldg(ctab + 3 * idv[k] + 1);  // w, what (hi parts)
                     const R w = cw.x, wh = cw.z;
-                    R r = rh[k], u = ur[k], dpr = dprv[k], ip = ipb[k], iR = ir[k];
+                    R r = rh[k], u = ur[k], dpr = dprv[k], ip = IPB(k), iR = IR(k);
                     sm.T[a] = ff_to_f(ff_acc(Ttot, ff_neg(Tacc)));
                     Tacc = ff_add_f(Tacc, tv[k]);
                     R above = ff_to_f(ff_acc(Ttot, ff_neg(Tacc)));
@@ -690,7 +700,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             for (int k = K - 1; k >= 0; --k) {
                 if (p0 + k < n) {
                     R r = rh[k], hA = hav[k];
-                    Mat2<R> Mi = {1.f - hA * r, -hA * ir[k], hA * r * r * r, 1.f + hA * r};
+                    Mat2<R> Mi = {1.f - hA * r, -hA * IR(k), hA * r * r * r, 1.f + hA * r};
                     Mb = OpMatLeft()(Mb, Mi);
                 }
             }
@@ -709,7 +719,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             for (int k = 0; k < K; ++k) {
                 if (p0 + k < n) {
                     R r = rh[k], hA = hav[k];
-                    Mat2<R> M = {1.f + hA * r, hA * ir[k], -hA * r * r * r, 1.f - hA * r};
+                    Mat2<R> M = {1.f + hA * r, hA * IR(k), -hA * r * r * r, 1.f - hA * r};
                     Y = OpMatLeft()(Y, M);
                 }
                 Rra[k] = Y.m00;
@@ -737,7 +747,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                     gl = ff_add_f(gl, gp);
                     dl = ff_add_f(dl, dp);
                     R r = rh[k], hA = hav[k];
-                    Mat2<R> Mi = {1.f - hA * r, -hA * ir[k], hA * r * r * r, 1.f + hA * r};
+                    Mat2<R> Mi = {1.f - hA * r, -hA * IR(k), hA * r * r * r, 1.f + hA * r};
                     Y = OpMatLeft()(Y, Mi);
                 }
             }
@@ -800,7 +810,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 const int a = SW::at(p);
                 const int a1 = (p + 1 < TK) ? SW::at(p + 1) : TK;
                 R r = rh[k];
-                bpv[k] = 0.5f * ((sm.a[a] + sm.a[a1]) * r + (sm.b[a] + sm.b[a1]) * ir[k]);
+                bpv[k] = 0.5f * ((sm.a[a] + sm.a[a1]) * r + (sm.b[a] + sm.b[a1]) * IR(k));
                 R pb = pbv[k];
                 if (!(pb > 0.f) || !isfinite(pb) || !isfinite(dprv[k]) || !isfinite(tv[k]) || !isfinite(bpv[k]) ||
                     !isfinite(bbv[k]))
@@ -893,7 +903,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
             int p = p0 + k;
             if (p < n) {
                 const int a = SW::at(p);
-                R u = ur[k], pb = pbv[k], ip = ipb[k];
+                R u = ur[k], pb = pbv[k], ip = IPB(k);
                 R g = 0.5f * (1.f + u * u + pb * pb) * ip;
                 R fr = u * ip;
                 R fu = g * dprv[k] * ip - (bpv[k] + bbv[k]);
