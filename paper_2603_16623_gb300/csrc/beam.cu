@@ -348,7 +348,12 @@ static cudaError_t slice_sort_pass(const int32_t* off, int32_t n_steps, const do
     // summed in chunks of the block's width, and its rounding must not
     // depend on how the slices were split into passes
     const int threads = 256;
-    int grid = n_steps < 152 * 8 ? n_steps : 152 * 8;
+    // a pass after the first (min_m > 0) sorts only the rare slices denser
+    // than the first pass took, with up to 196 KB of shared memory per block
+    // (one block per SM): a few blocks that walk the offsets, rather than one
+    // per slice that mostly finds nothing to do
+    const int cap = min_m > 0 ? 16 : 152 * 8;
+    int grid = n_steps < cap ? n_steps : cap;
     if (grid < 1) grid = 1;
     slice_sort_kernel<R><<<grid, threads, sm, st>>>(off, n_steps, r_in, qw_in, idx, br, bE, bQs, bTot, m_pad, min_m,
                                                     last, ctl, inv);
