@@ -41,7 +41,9 @@ __global__ void ring_init_kernel(const double* __restrict__ edges, const double*
             float2 a = split_ff(c), b = split_ff(l0), e = split_ff(wj), f = split_ff(whj), g = split_ff(wj * l0);
             ctab[3 * j] = make_float4(a.x, a.y, b.x, b.y);
             ctab[3 * j + 1] = make_float4(e.x, e.y, f.x, f.y);
-            ctab[3 * j + 2] = make_float4(g.x, g.y, 0.f, 0.f);
+            // the spare slots: 1/w and 1/rho0 as the march takes them (the
+            // same float reciprocals it would take of the same floats)
+            ctab[3 * j + 2] = make_float4(g.x, g.y, __frcp_rn(e.x), __frcp_rn(a.x));
         }
         ur[j] = 0;
         frho[j] = 0;

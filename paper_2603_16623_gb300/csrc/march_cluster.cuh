@@ -595,7 +595,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 const int a = SW::at(p);
                 RingConst c = ring_const(ctab, idv[k]);
                 const R dl = ff_to_f(ff_acc(ff{rh[k], sm.rl[a]}, ff_neg(c.r0)));
-                lp[k] = log1pf(dl * __frcp_rn(c.r0.hi));
+                lp[k] = log1pf(dl * c.ir0);
                 sw = ff_acc(sw, c.w);
                 sl = ff_acc(sl, ff_acc(c.wl0, ff_two_prod(c.w.hi, lp[k])));
                 if (m > 0 && !staged) cnt += cnt_a[a];
@@ -692,7 +692,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                     sm.T[a] = ff_to_f(ff_acc(Ttot, ff_neg(Tacc)));
                     Tacc = ff_add_f(Tacc, tv[k]);
                     R above = ff_to_f(ff_acc(Ttot, ff_neg(Tacc)));
-                    R dpz = -(above + (1.f - wh * __frcp_rn(w)) * tv[k]);
+                    R dpz = -(above + (1.f - wh * __ldg(reinterpret_cast<const float*>(ctab + 3 * idv[k] + 2) + 2)) * tv[k]);
                     tv[k] = dpz;
                     R pb = pbv[k];
                     R g = 0.5f * (1.f + u * u + pb * pb) * ip;

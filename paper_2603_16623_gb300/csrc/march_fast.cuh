@@ -77,10 +77,11 @@ __host__ __device__ inline size_t fast_smem_bytes(int T, int K) {
 
 struct RingConst {
     ff r0, ln0, w, wh, wl0;  // rho0, ln rho0, w, what, w ln rho0
+    float iw, ir0;           // 1/w and 1/rho0 (of the high parts, rounded to nearest)
 };
 __device__ __forceinline__ RingConst ring_const(const float4* __restrict__ ctab, int id) {
     float4 a = __ldg(ctab + 3 * id), b = __ldg(ctab + 3 * id + 1), c = __ldg(ctab + 3 * id + 2);
-    return {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}, {c.x, c.y}};
+    return {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}, {c.x, c.y}, c.z, c.w};
 }
 
 // shared-memory arrays of the fast march
@@ -599,7 +600,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                 const int a = SW::at(p);
                 RingConst c = ring_const(ctab, idv[k]);
                 const R dl = ff_to_f(ff_acc(ff{rh[k], sm.rl[a]}, ff_neg(c.r0)));  // rho - rho0
-                lp[k] = log1pf(dl * __frcp_rn(c.r0.hi));
+                lp[k] = log1pf(dl * c.ir0);
                 sw = ff_acc(sw, c.w);
                 sl = ff_acc(sl, ff_acc(c.wl0, ff_two_prod(c.w.hi, lp[k])));
                 if (m > 0) cl += t_cnt[a];
@@ -677,7 +678,7 @@ march_fast_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t* _
                     sm.T[a] = ff_to_f(ff_acc(Ttot, ff_neg(Tacc)));
                     Tacc = ff_add_f(Tacc, tv[k]);
                     R above = ff_to_f(ff_acc(Ttot, ff_neg(Tacc)));
-                    R dpz = -(above + (1.f - wh * __frcp_rn(w)) * tv[k]);
+                    R dpz = -(above + (1.f - wh * __ldg(reinterpret_cast<const float*>(ctab + 3 * idv[k] + 2) + 2)) * tv[k]);
                     tv[k] = dpz;
                     R pb = pbv[k];
                     R g = 0.5f * (1.f + u * u + pb * pb) * ip;
