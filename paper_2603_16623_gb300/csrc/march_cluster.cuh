@@ -235,7 +235,8 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
     __shared__ float4 s_xch[16];   // per rank: (in order?, first radius, last radius, failed the guard?)
     __shared__ float s_last[16];   // last radius held by every CTA, this slice
     __shared__ float s_edge[2];    // this CTA's first and last radius (merge rounds)
-    __shared__ int s_vote_out, s_stop;
+    __shared__ float2 s_edges[16];  // every CTA's first and last radius (merge rounds)
+    __shared__ int s_stop;
     __shared__ float2 s_nab;       // (a, b) of the next CTA's first region
     __shared__ Trip<ff> x1[16], f1[2];
     __shared__ ff x2[16], f2[2];
@@ -448,19 +449,23 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                     s_edge[1] = sm.rh[SW::at(nl - 1)];
                 }
                 cl.sync();
-                if (tid == 0) {
-                    int all = 1;
-                    for (int r = 0; r + 1 < csize; ++r)
-                        if (*rmt(cl, &s_edge[1], r) > *rmt(cl, &s_edge[0], r + 1)) all = 0;
-                    s_vote_out = all;
+                // every CTA's edges, one peer per thread (DSMEM loads in
+                // flight together), then the vote from the local copies (the
+                // same for every thread)
+                if (tid < csize) {
+                    const float* e = rmt(cl, s_edge, tid);
+                    s_edges[tid] = make_float2(e[0], e[1]);
                 }
                 __syncthreads();
+                bool all = true;
+                for (int r = 0; r + 1 < csize; ++r)
+                    if (s_edges[r].y > s_edges[r + 1].x) all = false;
                 // (csize rounds sort any order; the bound is a safeguard)
-                if (s_vote_out || round == 2 * csize + 2) break;
+                if (all || round == 2 * csize + 2) break;
                 cl.sync();  // everyone has read the edges before they change
                 cluster_merge_round<K>(cl, sm, n, TK, round & 1);
             }
-            if (tid < csize) s_last[tid] = *rmt(cl, &s_edge[1], tid);
+            if (tid < csize) s_last[tid] = s_edges[tid].y;
         } else if (tid < csize) {
             s_last[tid] = s_xch[tid].z;
         }
