@@ -145,7 +145,13 @@ __device__ __forceinline__ bool block_sorted(const float* rh, int nl, int p0) {
 // dead region tables (b, T, D, S, psi; ids in registers) and written back
 // once every CTA has read the old ranges.
 template <int K>
-__device__ void cluster_merge_round(cg::cluster_group& cl, const FastSmem& sm, int n, int TK, int parity) {
+// scratch: TK words of this CTA's shared memory, zero on entry and on
+// return (the beam count array): the partner's radii are copied there first
+// (one DSMEM load per word, in flight together), so that the merge-path
+// search and the merge read them locally instead of one remote load after
+// another.
+__device__ void cluster_merge_round(cg::cluster_group& cl, const FastSmem& sm, int n, int TK, int parity,
+                                    float* scratch) {
     using SW = Swz<K>;
     const int rank = cl.block_rank(), size = cl.num_blocks();
     const int tid = threadIdx.x;
@@ -159,8 +165,11 @@ __device__ void cluster_merge_round(cg::cluster_group& cl, const FastSmem& sm, i
     if (active) {
         const int nA = min(TK, n - left * TK);
         const int nB = min(TK, n - (left + 1) * TK);
-        const float* Arh = rmt(cl, sm.rh, left);
-        const float* Brh = rmt(cl, sm.rh, left + 1);
+        const float* partner = rmt(cl, sm.rh, rank == left ? left + 1 : left);
+        for (int i = tid; i < TK; i += blockDim.x) scratch[i] = partner[i];
+        __syncthreads();  // (active is the same for the whole CTA)
+        const float* Arh = rank == left ? sm.rh : scratch;
+        const float* Brh = rank == left ? scratch : sm.rh;
         const int off = (rank == left) ? 0 : nA;  // merged position of my local 0
         my_n = (rank == left) ? nA : nB;
         const int d = off + tid * K;
@@ -184,6 +193,7 @@ __device__ void cluster_merge_round(cg::cluster_group& cl, const FastSmem& sm, i
             }
         }
         __syncthreads();
+        for (int i = tid; i < TK; i += blockDim.x) scratch[i] = 0.f;  // (every search is done)
         const FastSmem A = rmt_sm(cl, sm, left), B = rmt_sm(cl, sm, left + 1);
         for (int l = tid; l < my_n; l += blockDim.x) {
             const int c = code[l];
@@ -463,7 +473,7 @@ march_cluster_kernel(const WakeDev<PrecMixed>* __restrict__ wakes, const int32_t
                 // (csize rounds sort any order; the bound is a safeguard)
                 if (all || round == 2 * csize + 2) break;
                 cl.sync();  // everyone has read the edges before they change
-                cluster_merge_round<K>(cl, sm, n, TK, round & 1);
+                cluster_merge_round<K>(cl, sm, n, TK, round & 1, reinterpret_cast<float*>(cnt_a));
             }
             if (tid < csize) s_last[tid] = s_edges[tid].y;
         } else if (tid < csize) {
