@@ -505,10 +505,16 @@ def stage_ab_bench(gs, wakes, stream, reps=3):
 def ions_bench(args, wakes, stream):
     """A batch of the workload's wakes of <= 4096 rings with mobile hydrogen
     ions (Z = 1, M = 1836) in place of the ion column: batched reset + march,
-    CUDA-event timed; ring-slices count both species."""
-    sel = [dataclasses.replace(wk, ions=(1.0, 1836.0)) for wk in wakes if wk.n_rings <= 4096][: args.ion_wakes]
+    CUDA-event timed; ring-slices count both species.  The same wakes with
+    the immobile ion column (the on-chip AB2 march) give the per-ring-slice
+    comparison."""
+    base = [wk for wk in wakes if wk.n_rings <= 4096][: args.ion_wakes]
+    sel = [dataclasses.replace(wk, ions=(1.0, 1836.0)) for wk in base]
     res = _ions_batch(sel, stream)
     res["ions"] = "Z = 1, M = 1836 (hydrogen), same cells as the electrons"
+    ref = _ions_batch(base, stream, species=1)
+    res["electron_only_same_wakes"] = {k: ref[k] for k in ("ring_slices", "ms_per_step", "value", "unit")}
+    res["electron_only_over_ions_per_ring_slice"] = ref["value"] / res["value"]
     # a radial profile changes only the ring weights: the parabolic channel
     # n = 1 + 4 r^2 / w0^4 (w0 = 3) with static ion rings
     prof = [dataclasses.replace(wk, ions=(1.0, float("inf")), cell_density=W.parabolic_profile(wk.edges, 1.0, 3.0))
@@ -519,11 +525,16 @@ def ions_bench(args, wakes, stream):
 
 def rk4_bench(args, wakes, stream):
     """The batched workload's wakes of <= 8192 rings with the RK4 ring
-    integrator (one CTA of 512 threads per wake): batched reset + march,
-    CUDA-event timed."""
-    sel = [dataclasses.replace(wk, integrator="rk4") for wk in wakes if wk.n_rings <= 8192][: args.rk4_wakes]
+    integrator (blocks of 512 threads, a cluster of up to 8 for the wide
+    wakes): batched reset + march, CUDA-event timed.  The same wakes with
+    AB2 (the on-chip march) give the per-ring-slice comparison."""
+    base = [wk for wk in wakes if wk.n_rings <= 8192][: args.rk4_wakes]
+    sel = [dataclasses.replace(wk, integrator="rk4") for wk in base]
     res = _ions_batch(sel, stream, species=1)
     res["integrator"] = "classical RK4 per slice (four field evaluations), electrons over the ion column"
+    ref = _ions_batch(base, stream, species=1)
+    res["ab2_same_wakes"] = {k: ref[k] for k in ("ring_slices", "ms_per_step", "value", "unit")}
+    res["ab2_over_rk4_per_ring_slice"] = ref["value"] / res["value"]
     return res
 
 
@@ -585,16 +596,18 @@ def _ions_batch(sel, stream, species=2):
     wm.wake_batch_run(gs)
     ev[2].record(stream)
     torch.cuda.synchronize()
-    ring_slices, stopped = 0, 0
+    ring_slices, stopped, blocks = 0, 0, []
     for g, wk in zip(gs, sel):
         nxt, st, _ = g.progress()
         ring_slices += species * wk.n_rings * nxt
         stopped += int(st != 0)
+        blocks.append(g.launch_config()[2])
         g.close()
     march_ms = ev[1].elapsed_time(ev[2])
     step_ms = ev[0].elapsed_time(ev[2])
     return {"wakes": len(sel), "cells": [min(wk.n_rings for wk in sel), max(wk.n_rings for wk in sel)],
             "ring_slices": ring_slices, "wakes_stopped_by_breakdown": stopped,
+            "blocks_per_wake": [min(blocks), max(blocks)], "blocks": sum(blocks),
             "ms_per_step": step_ms, "march_ms": march_ms, "value": ring_slices / (step_ms / 1e3), "unit": UNIT}
 
 

@@ -61,7 +61,13 @@ enum {
                       names: four field evaluations per slice, the beam source at
                       the half step the mean of the two slices; a stage state
                       below the axis is evaluated mirrored.  Electron-only wakes
-                      (no mobile ions), on the one-CTA march. */
+                      (no mobile ions) of at most 16384 rings, on the global-
+                      memory march: one block per wake, or a thread-block
+                      cluster of cluster_ctas (1..8) blocks that split the
+                      sorted rings (block 0 sorts the state and the stage
+                      states); 0 = automatic, the fewest blocks (at most 8)
+                      that hold at most 2 rings per thread.  rings_per_thread
+                      must be 0. */
 };
 
 /* flags of wake_config */
@@ -100,8 +106,13 @@ enum {
    interpolation between its ring values; B_theta^(p) comes from the
    electrons only; ions move with q/m = Z/M.  A wake then has 2 n_rings
    rings: ids 0..n_rings-1 electrons, n_rings..2 n_rings-1 ions, in every
-   per-ring array of this interface (ring state, dumps).  n_rings <= 4096,
-   the one-CTA march (rings_per_thread and cluster_ctas must be 0).
+   per-ring array of this interface (ring state, dumps).  n_rings <= 4096;
+   rings_per_thread must be 0, and cluster_ctas (0..8) sets the thread
+   blocks of the march: one block per wake, or a thread-block cluster whose
+   blocks split each species' sorted rings in rank order (scans folded over
+   the cluster, cluster barriers between the phases).  0 = automatic: the
+   fewest blocks (at most 8) that hold at most 2 rings of each species per
+   thread (one block up to 1024 cells at 512 threads).
    ion_mass = +inf gives ion rings that never move.
 
    Radial density profile (Sec. II, arbitrary profiles): cell_density (host,
@@ -146,7 +157,10 @@ typedef struct {
                                  cluster_ctas)) rounded up to a multiple of 32,
                                  at most 512, and no CTA may be left empty.
                                  Both must be 0 for WAKE_FP64.  Automatic
-                                 (both 0): see wake_launch_shape.             */
+                                 (both 0): see wake_launch_shape.  With
+                                 mobile ions or RK4 (FP64 or MIXED)
+                                 cluster_ctas is 0..8 and rings_per_thread 0
+                                 (see above).                                 */
     int32_t integrator;       /* WAKE_AB2 (0) or WAKE_RK4                        */
     int32_t grid_nr;          /* 0: gridless beam coupling (fields at each beam
                                  particle); 1..1024: adaptive beam grids
@@ -339,8 +353,8 @@ wake_status wake_get_ring_dumps(wake_handle *h, void *r, void *ur, void *psi, vo
                                 void *dpsidz, void *bp, void *bb);
 
 /* How the march kernels serve this wake: threads per block, rings per
-   thread (on the one-CTA marches: ceil(rings / threads), both species
-   counted with mobile ions), and thread blocks per wake (> 1: a thread-
+   thread (on the global-memory marches: ceil(rings / (threads x blocks)),
+   both species counted with mobile ions), and thread blocks per wake (> 1: a thread-
    block cluster).  For batched launches, wakes of the same march (on-chip,
    plain, two-species, RK4, beam grids) with equal triples share one
    launch. */

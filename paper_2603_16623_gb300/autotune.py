@@ -11,8 +11,10 @@ fills the GPU with copies of it (about `fill` x the SM count in CTAs, as a
 large batch does), times one batched march per candidate shape with CUDA
 events and keeps the fastest in ring-slices per second.  The automatic
 shape stays unless a candidate beats it by `min_gain`, so timing noise does
-not churn the table.  The one-CTA marches (FP64, mobile ions, RK4, beam
-grids) are tuned the same way over their block size (block_threads).
+not churn the table.  The global-memory marches (FP64, mobile ions, RK4,
+beam grids) are tuned the same way over their block size (block_threads),
+and those with mobile ions or RK4 also over their blocks per wake (a
+thread-block cluster of 2, 4 or 8 blocks of 512 threads).
 
 The candidates come from the library itself (wake_launch_shape: the shape
 wake_init would give, computed on the host), so the tuner never proposes a
@@ -37,12 +39,14 @@ from . import wake as wm
 from . import workloads as W
 
 # the kinds of march a table entry applies to: the on-chip march (mixed,
-# electrons over the ion column) and the one-CTA marches
+# electrons over the ion column) and the global-memory marches
 KINDS = ("mixed", "fp64", "ions", "rk4", "grid")
 BLOCK_THREADS = (64, 128, 256, 512)
 # the block size wake_init takes when block_threads is 0 (timed as the
 # automatic candidate, so not again as an explicit one)
 DEFAULT_BLOCK_THREADS = {"fp64": 256, "grid": 256, "ions": 512, "rk4": 512}
+# the global-memory marches that also run as thread-block clusters
+GM_CLUSTER_KINDS = ("ions", "rk4")
 DEFAULT_SIZES = (512, 1024, 2048, 3072, 4096, 6144, 8192, 12288, 16384, 32768, 65536)
 
 
@@ -51,8 +55,8 @@ class Candidate:
     """Arguments of wake_init for one launch shape, with what they resolve
     to for the size they were made for."""
     rings_per_thread: int = 0   # on-chip march: 0 (automatic), 2, 4 or 8
-    cluster_ctas: int = 0       # on-chip march: 0 (automatic) or 1-16
-    block_threads: int = 0      # one-CTA marches: 0 (the library's default) or 64-512
+    cluster_ctas: int = 0       # on-chip march: 0 (automatic) or 1-16; ions, RK4: 0 or 1-8
+    block_threads: int = 0      # global-memory marches: 0 (the library's default) or 64-512
     threads: int = 0            # resolved threads per CTA (on-chip march)
     ctas: int = 1               # resolved CTAs per wake
 
@@ -75,7 +79,7 @@ def max_rings(kind: str) -> int:
         return wm.wake_max_rings("mixed")
     if kind == "ions":
         return 4096  # cells per species with mobile ions
-    return wm.wake_max_rings("fp64")  # the one-CTA marches: 8192 rings
+    return wm.wake_max_rings("fp64")  # the other global-memory marches: 8192 rings
 
 
 def candidates(n_rings: int, kind: str = "mixed", max_candidates: int = 8,
@@ -83,12 +87,16 @@ def candidates(n_rings: int, kind: str = "mixed", max_candidates: int = 8,
     """The shapes worth timing for a wake of n_rings rings: the automatic
     one first, then (on-chip march) every valid (rings per thread, CTAs per
     wake) with at least min_threads threads per CTA, thinned evenly to
-    max_candidates; or (one-CTA marches) the block sizes 64-512."""
+    max_candidates; or (global-memory marches) the block sizes 64-512 and,
+    with mobile ions or RK4, clusters of 2, 4 and 8 blocks of 512 threads."""
     if not 1 <= n_rings <= max_rings(kind):
         raise ValueError(f"{n_rings} rings: outside [1, {max_rings(kind)}] for the {kind} march")
     if kind != "mixed":
-        return [Candidate()] + [Candidate(block_threads=t) for t in BLOCK_THREADS
-                                if t != DEFAULT_BLOCK_THREADS[kind]]
+        out = [Candidate()] + [Candidate(block_threads=t, cluster_ctas=1 if kind in GM_CLUSTER_KINDS else 0)
+                               for t in BLOCK_THREADS if t != DEFAULT_BLOCK_THREADS[kind]]
+        if kind in GM_CLUSTER_KINDS:
+            out += [Candidate(cluster_ctas=cl, ctas=cl) for cl in (2, 4, 8)]
+        return out
     t0, k0, c0 = wm.wake_launch_shape(n_rings)
     auto = Candidate(threads=t0, ctas=c0)
     seen = {(t0, k0, c0)}
@@ -211,7 +219,12 @@ class TuningTable:
         if e is None:
             return {}
         if kind != "mixed":
-            return {"block_threads": e.block_threads} if e.block_threads else {}
+            out = {"block_threads": e.block_threads} if e.block_threads else {}
+            if kind in GM_CLUSTER_KINDS and (e.rings_per_cta or e.block_threads):
+                # the stored blocks per wake for this size (1 with a block size alone;
+                # n_rings counts cells per species with ions)
+                out["cluster_ctas"] = max(1, min(8, math.ceil(n_rings / e.rings_per_cta))) if e.rings_per_cta else 1
+            return out
         if not e.rings_per_cta:
             return {}
         cl = max(1, math.ceil(n_rings / e.rings_per_cta))
@@ -242,7 +255,8 @@ class TuningTable:
 def entry_from(result: SizeResult, n_max: int) -> TableEntry:
     c = result.chosen
     if result.kind != "mixed":
-        return TableEntry(result.kind, n_max, block_threads=c.block_threads)
+        per_cta = math.ceil(result.n_rings / c.ctas) if c.cluster_ctas > 1 else 0
+        return TableEntry(result.kind, n_max, rings_per_cta=per_cta, block_threads=c.block_threads)
     if c.automatic:
         return TableEntry("mixed", n_max)
     return TableEntry("mixed", n_max, c.rings_per_thread, math.ceil(result.n_rings / c.ctas))

@@ -141,6 +141,37 @@ size_t march_smem(int32_t n_max, int32_t n_pad_max, size_t real_bytes, int32_t m
     return (size_t)kScanBytes + region;
 }
 
+// a global-memory march: one block per wake, or clusters of cluster_ctas
+// (<= kMaxWakeCtas) blocks, one cluster per wake
+template <class P>
+static cudaError_t launch_gm(void (*kern)(const WakeDev<P>*, const int32_t*, int32_t, int32_t, int32_t),
+                             const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
+                             int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
+                             int32_t cluster_ctas, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (cluster_ctas <= 1) {
+        kern<<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, mb_cap);
+        return cudaGetLastError();
+    }
+    if (cluster_ctas > kMaxWakeCtas) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_wakes * cluster_ctas), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster_ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, d_wakes, d_order, max_slices, mode, mb_cap);
+    if (e != cudaSuccess) return cudaGetLastError(), e;
+    return cudaGetLastError();
+}
+
 template <class P>
 cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
                          int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st) {
@@ -234,12 +265,9 @@ cudaError_t launch_ring_init(const double* edges, const double* cell_density, in
 template <class P>
 cudaError_t launch_march_ions(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                               int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
-                              cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(march_ions_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    march_ions_kernel<P><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, mb_cap);
-    return cudaGetLastError();
+                              int32_t cluster_ctas, cudaStream_t st) {
+    return launch_gm(march_ions_kernel<P>, d_wakes, d_order, n_wakes, max_slices, mode, threads, smem, mb_cap,
+                     cluster_ctas, st);
 }
 
 template <class R>
@@ -262,22 +290,19 @@ template cudaError_t launch_ring_init<float>(const double*, const double*, int32
 template <class P>
 cudaError_t launch_march_rk4(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                              int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
-                             cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(march_rk4_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    march_rk4_kernel<P><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, mb_cap);
-    return cudaGetLastError();
+                             int32_t cluster_ctas, cudaStream_t st) {
+    return launch_gm(march_rk4_kernel<P>, d_wakes, d_order, n_wakes, max_slices, mode, threads, smem, mb_cap,
+                     cluster_ctas, st);
 }
 
 template cudaError_t launch_march_rk4<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
-                                               int32_t, size_t, int32_t, cudaStream_t);
+                                               int32_t, size_t, int32_t, int32_t, cudaStream_t);
 template cudaError_t launch_march_rk4<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t,
-                                                 int32_t, int32_t, size_t, int32_t, cudaStream_t);
+                                                 int32_t, int32_t, size_t, int32_t, int32_t, cudaStream_t);
 template cudaError_t launch_march_ions<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
-                                                int32_t, size_t, int32_t, cudaStream_t);
+                                                int32_t, size_t, int32_t, int32_t, cudaStream_t);
 template cudaError_t launch_march_ions<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t,
-                                                  int32_t, int32_t, size_t, int32_t, cudaStream_t);
+                                                  int32_t, int32_t, size_t, int32_t, int32_t, cudaStream_t);
 template cudaError_t launch_gather_by_id<double>(const int32_t*, const double*, double*, int32_t, cudaStream_t);
 template cudaError_t launch_gather_by_id<float>(const int32_t*, const float*, float*, int32_t, cudaStream_t);
 

@@ -17,6 +17,8 @@
 //   a10 AB2 push with axis reflection
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace gbwake {
@@ -220,14 +222,121 @@ __device__ __forceinline__ void ring_weights(const float4* ctab, const float*, c
 __device__ __forceinline__ double acc_add_prod(double a, double x, double y) { return a + x * y; }
 __device__ __forceinline__ ff acc_add_prod(ff a, float x, float y) { return ff_add(a, ff_two_prod(x, y)); }
 
+// ---------------------------------------------------------------------------
+// The thread blocks of one wake on the global-memory marches: one block (a
+// plain launch), or a thread-block cluster whose blocks split the wake's
+// sorted positions in rank order.  sync() orders the wake's global-memory
+// arrays between all of its threads: a block barrier, or a cluster barrier
+// (arrive with release, wait with acquire at cluster scope: every write
+// before it, global or shared, is visible to every thread of the cluster
+// after it).  The scans below fold the blocks' totals in rank order after a
+// block scan; the totals travel through `part` (shared memory, two buffers
+// used in turn, so that a buffer is written again only after a later call's
+// barrier, which every block passes only after it read the buffer).
+// ---------------------------------------------------------------------------
+constexpr int kMaxWakeCtas = 8;
+constexpr int kPartSlot = 32;                          // bytes per block total
+constexpr int kPartBuf = kMaxWakeCtas * kPartSlot;     // one buffer
+struct WakeCtas {
+    int rank = 0, size = 1;
+    unsigned char* part = nullptr;  // 2 x kPartBuf bytes of shared memory (size > 1)
+    int flip = 0;
+    __device__ __forceinline__ void sync() const {
+        if (size > 1) {
+            asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                             : "memory");
+        } else {
+            __syncthreads();
+        }
+    }
+    // this block's value v to slot `rank` of every block's current buffer,
+    // then the barrier; returns the buffer (its slots in rank order)
+    template <class T>
+    __device__ __forceinline__ const T* exchange(T v) {
+        static_assert(sizeof(T) <= kPartSlot, "scan value too large for the exchange");
+        T* buf = reinterpret_cast<T*>(part + flip * kPartBuf);
+        flip ^= 1;
+        if ((int)threadIdx.x < size) {
+            T* dst = cooperative_groups::this_cluster().map_shared_rank(buf, (int)threadIdx.x);
+            *reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(dst) + rank * kPartSlot) = v;
+        }
+        sync();
+        return buf;
+    }
+    template <class T>
+    __device__ __forceinline__ T slot(const T* buf, int r) const {
+        return *reinterpret_cast<const T*>(reinterpret_cast<const unsigned char*>(buf) + r * kPartSlot);
+    }
+};
+
+// exclusive scan over the wake's threads (REV: from the last thread of the
+// last block down); `total` the fold over all of them
+template <bool REV, class T, class Op>
+__device__ __forceinline__ T wake_excl_scan(WakeCtas& C, T v, Op op, T ident, T* sbuf, T& total) {
+    T bt;
+    T ex = block_excl_scan<REV>(v, op, ident, sbuf, bt);
+    if (C.size == 1) {
+        total = bt;
+        return ex;
+    }
+    const T* buf = C.exchange(bt);
+    T pre = ident, tot = ident;
+    for (int i = 0; i < C.size; ++i) {
+        const int r = REV ? C.size - 1 - i : i;
+        if (r == C.rank) pre = tot;
+        tot = op(tot, C.slot(buf, r));
+    }
+    total = tot;
+    return op(pre, ex);
+}
+
+// the forward sum of fx and the reverse (suffix) sum of ry over the wake's
+// threads, exclusive; totals in tx, ty
+template <class T>
+__device__ __forceinline__ Pair<T> wake_excl_scan_fwd_rev(WakeCtas& C, T fx, T ry, T zero, Pair<T>* sbuf, T& tx,
+                                                          T& ty) {
+    T bx, by;
+    Pair<T> e = block_excl_scan_fwd_rev(fx, ry, zero, sbuf, bx, by);
+    if (C.size == 1) {
+        tx = bx;
+        ty = by;
+        return e;
+    }
+    const Pair<T>* buf = C.exchange(Pair<T>{bx, by});
+    T px = zero, ax = zero, py = zero, ay = zero;
+    for (int r = 0; r < C.size; ++r) {
+        if (r == C.rank) px = ax;
+        ax = acc_add(ax, C.slot(buf, r).x);
+    }
+    for (int r = C.size - 1; r >= 0; --r) {
+        if (r == C.rank) py = ay;
+        ay = acc_add(ay, C.slot(buf, r).y);
+    }
+    tx = ax;
+    ty = ay;
+    return {acc_add(px, e.x), acc_add(py, e.y)};
+}
+
+// the AND (all = true) or OR (all = false) of v over the wake's threads
+__device__ __forceinline__ bool wake_vote(WakeCtas& C, bool v, bool all) {
+    const bool b = all ? __syncthreads_and(v) : __syncthreads_or(v);
+    if (C.size == 1) return b;
+    const int* buf = C.exchange((int)b);
+    bool r = all;
+    for (int i = 0; i < C.size; ++i) r = all ? (r && C.slot(buf, i) != 0) : (r || C.slot(buf, i) != 0);
+    return r;
+}
+
 // a8: the region coefficients a_k, b_k of B_theta^(p) = a_k rho + b_k / rho
 // (Eq. ai_bi with b_0 = 0, a_n = 0) for the rings at sorted positions
 // [0, n) (radii sR, coefficients W.cA, W.cB, W.cC; this thread's positions
 // [p0, p1)), in W.ak, W.bk [0..n].  W.cB, W.cC are overwritten with the ring
 // sources gamma_p, delta_p.  Ends without a barrier after the last writes.
+// With a cluster (C.size > 1) the positions span its blocks and the scans
+// fold over them; the end values (R_0, D_n, a_n, b_n) are block 0's.
 template <class P>
 __device__ void bp_region_solve(const WakeDev<P>& W, const typename P::R* sR, int n, int p0, int p1,
-                                unsigned char* sscan) {
+                                unsigned char* sscan, WakeCtas& C) {
     using R = typename P::R;
     using A = typename P::A;
     const int tid = threadIdx.x;
@@ -249,9 +358,9 @@ __device__ void bp_region_solve(const WakeDev<P>& W, const typename P::R* sR, in
         Mb = OpMatLeft()(Mb, Mi);
     }
     Mat2<R> tf, tb;
-    Mat2<R> Yf = block_excl_scan<false>(Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
-    Mat2<R> Yb = block_excl_scan<true>(Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
-    if (tid == 0) {
+    Mat2<R> Yf = wake_excl_scan<false>(C, Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
+    Mat2<R> Yb = wake_excl_scan<true>(C, Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
+    if (C.rank == 0 && tid == 0) {
         W.Ra[0] = 1;
         W.Rb[0] = 0;
         W.Da[n] = 0;
@@ -287,8 +396,9 @@ __device__ void bp_region_solve(const WakeDev<P>& W, const typename P::R* sR, in
     // G_k = sum_{p >= k} gamma_p as a true suffix sum (a total minus a
     // prefix would cancel where G_k is small and R_k ~ e^rho is large)
     A g_tot, d_tot;
-    Pair<A> gd = block_excl_scan_fwd_rev(dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
-    // the scan's barriers order the R/D writes above before these reads
+    Pair<A> gd = wake_excl_scan_fwd_rev(C, dl, gl, zeroA, reinterpret_cast<Pair<A>*>(sscan), d_tot, g_tot);
+    // the scan's barriers order the R/D writes above before these reads (a
+    // block's first R_p comes from the block before it in a cluster)
     A Gsuf = gd.y;  // sum of gamma over rings >= p1
     for (int p = p1 - 1; p >= p0; --p) {
         Gsuf = acc_add_r(Gsuf, W.cB[p]);  // sum over rings >= p
@@ -303,7 +413,7 @@ __device__ void bp_region_solve(const WakeDev<P>& W, const typename P::R* sR, in
         W.bk[p] += H * W.Db[p];
         Hex = acc_add_r(Hex, W.cC[p]);
     }
-    if (tid == 0) {
+    if (C.rank == 0 && tid == 0) {
         R H = acc_to_r(d_tot);
         W.ak[n] = H * W.Da[n];
         W.bk[n] = H * W.Db[n];
@@ -563,7 +673,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         }
 
         // ---------------- a8: B_theta^(p) region coefficients a_k, b_k
-        bp_region_solve(W, sR, n, p0, p1, sscan);
+        WakeCtas one;
+        bp_region_solve(W, sR, n, p0, p1, sscan, one);
         __syncthreads();
 
         // ---------------- B^(p) at the rings, guard, dumps

@@ -43,15 +43,17 @@ cudaError_t launch_ring_init(const double* edges, const double* cell_density, in
                              double density, R* w, R* wh, R* rho, R* rho_lo, R* ur, R* frho, R* fur, int32_t* rid,
                              float4* ctab, cudaStream_t st);
 // the march with the RK4 ring integrator (march_rk4.cuh), one block per wake
+// or a thread-block cluster of cluster_ctas (<= 8) blocks per wake
 template <class P>
 cudaError_t launch_march_rk4(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                              int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
-                             cudaStream_t st);
-// the march of wakes with mobile ions (march_ions.cuh), one block per wake
+                             int32_t cluster_ctas, cudaStream_t st);
+// the march of wakes with mobile ions (march_ions.cuh), one block per wake or
+// a thread-block cluster of cluster_ctas (<= 8) blocks per wake
 template <class P>
 cudaError_t launch_march_ions(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes,
                               int32_t max_slices, int32_t mode, int32_t threads, size_t smem, int32_t mb_cap,
-                              cudaStream_t st);
+                              int32_t cluster_ctas, cudaStream_t st);
 template <class R>
 cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_t n, cudaStream_t st);
 template <class R>

@@ -8,8 +8,14 @@
 // for neutrality), so that per species
 //   psi = sum c ln max(rho, rho_j),  d_rho psi = (1/rho) sum_{rho_j<rho} c_j,
 //   d_zeta psi = -sum_{rho_j>=rho} c_j u_j / (rho_j psibar_j),
-// psibar = 1 - (q/m) psi.  One block owns one wake; per slice:
-//   a2 sort each segment (stable w.r.t. the previous order)
+// psibar = 1 - (q/m) psi.  One block owns one wake, or a thread-block
+// cluster of up to 8 (for wide wakes): its blocks split each species'
+// sorted positions in rank order, their scans fold over the cluster, and
+// cluster barriers order the wake's global-memory arrays between them (the
+// phases and their arithmetic are the same; only the fold order of the scans
+// changes with the split).  Per slice:
+//   a2 sort each segment (stable w.r.t. the previous order; in a cluster
+//      block s sorts segment s)
 //   a3 B^(b) at all rings
 //   a4 per species: block scan of (c, c ln rho) -> its own psi, d_rho psi
 //      at its rings (self weight in d_rho psi)
@@ -108,16 +114,30 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
     __shared__ int s_stop;
+    __shared__ __align__(16) unsigned char s_part[2 * kPartBuf];
 
     const uint64_t t_launch = global_ns();
-    const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
+    WakeCtas C;
+    {
+        unsigned r, c;
+        asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(c));
+        C.rank = (int)r;
+        C.size = (int)c;
+        C.part = s_part;
+    }
+    const int wi = blockIdx.x / C.size;
+    const WakeDev<P>& W = wakes[order ? order[wi] : wi];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
+    const int gt = C.rank * T + tid;  // the thread's place in the wake
+    const int GT = C.size * T;
     const int n = W.n;           // all rings
     const int N = W.n_ion;       // rings per species
-    const int K = (N + T - 1) / T;
-    const int q0 = min(N, tid * K);
+    const int K = (N + GT - 1) / GT;
+    const int q0 = min(N, gt * K);
     const int q1 = min(N, q0 + K);
+    const bool lead = C.rank == 0 && tid == 0;  // writes the wake's single values
     const R qm[2] = {(R)-1, (R)W.ion_qm};
 
     unsigned char* sscan = smem;
@@ -159,11 +179,23 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             for (int s = 0; s < 2; ++s)
                 for (int q = q0; q < q1; ++q)
                     if (q + 1 < N && rho[s * N + q + 1] < rho[s * N + q]) ok = false;
-            const bool in_order = __syncthreads_and(ok);
-            if (W.budget_ns > 0 && s_stop) break;
+            bool in_order = __syncthreads_and(ok);
+            bool stop = W.budget_ns > 0 && s_stop;
+            if (C.size > 1) {  // the cluster's blocks agree on both
+                const int* v = C.exchange((int)in_order | (stop ? 2 : 0));
+                in_order = true;
+                stop = false;
+                for (int r = 0; r < C.size; ++r) {
+                    const int f = C.slot(v, r);
+                    in_order = in_order && (f & 1) != 0;
+                    stop = stop || (f & 2) != 0;
+                }
+            }
+            if (stop) break;
             if (!in_order) {
                 const int nb = buf ^ 1;
                 for (int s = 0; s < 2; ++s) {
+                    if (C.size > 1 && C.rank != s) continue;
                     const int base = s * N;
                     for (int i = tid; i < W.n_pad; i += T) {
                         keys[i] = i < N ? rho[base + i] : (R)INFINITY;
@@ -184,6 +216,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                     for (int i = tid; i < N; i += T) W.rho_lo[base + i] = keys[i];
                     __syncthreads();
                 }
+                if (C.size > 1) C.sync();
                 buf = nb;
             }
         }
@@ -230,7 +263,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 loc.y = acc_add(loc.y, acc_mul_r(ring_log(W.ctab, id, r, W.rho_lo[p]), c));
             }
             Pair<A> tot;
-            Pair<A> ex = block_excl_scan<false>(loc, OpAddPair(), Pair<A>{zeroA, zeroA},
+            Pair<A> ex = wake_excl_scan<false>(C, loc, OpAddPair(), Pair<A>{zeroA, zeroA},
                                                 reinterpret_cast<Pair<A>*>(sscan), tot);
             Stot[s] = tot.x;
             Ltot[s] = tot.y;
@@ -251,13 +284,13 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 S = acc_add_r(S, c);
                 L = acc_add(L, acc_mul_r(lnr, c));
             }
-            if (tid == 0) {
+            if (lead) {
                 W.regS[rb + N] = tot.x;
                 W.regL[rb + N] = zeroA;
                 W.regT[rb + N] = (R)0;
             }
         }
-        __syncthreads();
+        C.sync();  // own-species fields, before the other species gathers them
 
         // ---------------- a5: totals of psi, d_rho psi; psibar, gamma, t
         for (int s = 0; s < 2; ++s) {
@@ -299,7 +332,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             const int base = s * N, rb = s * (N + 1);
             A tl = zeroA;
             for (int q = q0; q < q1; ++q) tl = acc_add_r(tl, W.tt[base + q]);
-            A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot[s]);
+            A Tex = wake_excl_scan<false>(C, tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot[s]);
             A Tacc = Tex;
             for (int q = q0; q < q1; ++q) {
                 const int p = base + q;
@@ -312,7 +345,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 W.dpzo[p] = -(above + ((R)1 - ch / c) * t);
             }
         }
-        __syncthreads();
+        C.sync();
         for (int s = 0; s < 2; ++s) {
             const int base = s * N, ob = (1 - s) * N;
             const R oT = acc_to_r(Ttot[1 - s]);
@@ -340,14 +373,14 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         }
 
         // ---------------- a8: B_theta^(p) of the electrons (regions 0..N)
-        bp_region_solve(W, sR, N, q0, q1, sscan);
-        __syncthreads();
+        bp_region_solve(W, sR, N, q0, q1, sscan, C);
+        C.sync();
         // B^(p) at the electron rings, then interpolated at the ion rings
         for (int p = q0; p < q1; ++p) {
             R r = sR[p];
             W.cA[p] = (R)0.5 * ((W.ak[p] + W.ak[p + 1]) * r + (W.bk[p] + W.bk[p + 1]) / r);
         }
-        __syncthreads();
+        C.sync();
         {
             const R bN = W.bk[N];
             for (int q = q0; q < q1; ++q) {
@@ -379,12 +412,12 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                     }
                 }
             }
-        bad = __syncthreads_or(bad);
+        bad = wake_vote(C, bad, false);
 
         // ---------------- a9: fields on beam particles (or query radii)
         {
             const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
-            for (int64_t q = tid; q < nq; q += T) {
+            for (int64_t q = gt; q < nq; q += GT) {
                 R x;
                 if (mode == MODE_MARCH) x = staged ? beamR[q] : W.br[b0 + q];
                 else x = (R)W.rq[q];
@@ -466,10 +499,10 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 fur[p] = fu;
             }
         has_prev = 1;
-        __syncthreads();
+        C.sync();
     }
-    __syncthreads();
-    if (tid == 0) {
+    C.sync();
+    if (lead) {
         if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_BUF] = buf;

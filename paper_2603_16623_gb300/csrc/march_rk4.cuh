@@ -62,7 +62,7 @@ __device__ bool rk_stage(const WakeDev<P>& W, unsigned char* sscan, const typena
                          const typename P::R* rlo, const typename P::R* us, const int32_t* rid, const int32_t* perm,
                          const typename P::R* sg, const RkSource<typename P::R>& src, typename P::R* kr,
                          typename P::R* ku, typename P::R* sum_r, typename P::R* sum_u, typename P::R wsum,
-                         bool first, int slice, int mode, int p0, int p1) {
+                         bool first, int slice, int mode, int p0, int p1, WakeCtas& C) {
     using R = typename P::R;
     using A = typename P::A;
     const int n = W.n;
@@ -88,8 +88,8 @@ __device__ bool rk_stage(const WakeDev<P>& W, unsigned char* sscan, const typena
         loc.y = acc_add(loc.y, acc_mul_a(ring_log(W.ctab, id, sR[i], rlo[q]), wa));
     }
     Pair<A> tot;
-    Pair<A> ex = block_excl_scan<false>(loc, OpAddPair(), Pair<A>{zeroA, zeroA}, reinterpret_cast<Pair<A>*>(sscan),
-                                        tot);
+    Pair<A> ex = wake_excl_scan<false>(C, loc, OpAddPair(), Pair<A>{zeroA, zeroA},
+                                       reinterpret_cast<Pair<A>*>(sscan), tot);
     const A Ltot = tot.y;
 
     // a5: psi, d_rho psi (self weight), psibar, gamma, t
@@ -128,13 +128,13 @@ __device__ bool rk_stage(const WakeDev<P>& W, unsigned char* sscan, const typena
         L = acc_add(L, acc_mul_a(lnr, wa));
         tl = acc_add_r(tl, t);
     }
-    if (tid == 0) {
+    if (C.rank == 0 && tid == 0) {
         W.regS[n] = tot.x;
         W.regL[n] = zeroA;
         W.regT[n] = (R)0;
     }
     A Ttot;
-    A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot);
+    A Tex = wake_excl_scan<false>(C, tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot);
 
     // a6 + a7: d_zeta psi, A, B, C
     {
@@ -161,8 +161,8 @@ __device__ bool rk_stage(const WakeDev<P>& W, unsigned char* sscan, const typena
     }
 
     // a8: B_theta^(p) (the two-sided solve of march.cuh)
-    bp_region_solve(W, sR, n, p0, p1, sscan);
-    __syncthreads();
+    bp_region_solve(W, sR, n, p0, p1, sscan, C);
+    C.sync();
 
     // B^(p) at the rings, guard, dumps, derivatives
     bool bad = false;
@@ -197,7 +197,7 @@ __device__ bool rk_stage(const WakeDev<P>& W, unsigned char* sscan, const typena
             sum_u[q] += wsum * fu;
         }
     }
-    return __syncthreads_or(bad);
+    return wake_vote(C, bad, false);
 }
 
 template <class P>
@@ -209,15 +209,29 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
     __shared__ int s_stop;
+    __shared__ __align__(16) unsigned char s_part[2 * kPartBuf];
 
     const uint64_t t_launch = global_ns();
-    const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
+    WakeCtas C;  // one block per wake, or a cluster (block 0 sorts)
+    {
+        unsigned r, c;
+        asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(c));
+        C.rank = (int)r;
+        C.size = (int)c;
+        C.part = s_part;
+    }
+    const int wi = blockIdx.x / C.size;
+    const WakeDev<P>& W = wakes[order ? order[wi] : wi];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
+    const int gt = C.rank * T + tid;  // the thread's place in the wake
+    const int GT = C.size * T;
     const int n = W.n;
-    const int K = (n + T - 1) / T;
-    const int p0 = min(n, tid * K);
+    const int K = (n + GT - 1) / GT;
+    const int p0 = min(n, gt * K);
     const int p1 = min(n, p0 + K);
+    const bool sorter = C.rank == 0;
 
     unsigned char* sscan = smem;
     R* keys = reinterpret_cast<R*>(smem + kScanBytes);
@@ -250,27 +264,40 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
             bool ok = true;
             for (int p = p0; p < p1; ++p)
                 if (p + 1 < n && rho[p + 1] < rho[p]) ok = false;
-            const bool in_order = __syncthreads_and(ok);
-            if (W.budget_ns > 0 && s_stop) break;
+            bool in_order = __syncthreads_and(ok);
+            bool stop = W.budget_ns > 0 && s_stop;
+            if (C.size > 1) {  // the cluster's blocks agree on both
+                const int* v = C.exchange((int)in_order | (stop ? 2 : 0));
+                in_order = true;
+                stop = false;
+                for (int r = 0; r < C.size; ++r) {
+                    const int f = C.slot(v, r);
+                    in_order = in_order && (f & 1) != 0;
+                    stop = stop || (f & 2) != 0;
+                }
+            }
+            if (stop) break;
             if (!in_order) {
-                for (int i = tid; i < W.n_pad; i += T) {
-                    keys[i] = i < n ? rho[i] : (R)INFINITY;
-                    vals[i] = i;
-                }
-                __syncthreads();
-                block_bitonic_sort(keys, vals, W.n_pad);
                 const int nb = buf ^ 1;
-                for (int p = tid; p < n; p += T) {
-                    int src = vals[p];
-                    W.rho[nb][p] = W.rho[buf][src];
-                    W.ur[nb][p] = W.ur[buf][src];
-                    W.rid[nb][p] = W.rid[buf][src];
-                    keys[p] = W.rho_lo[src];
+                if (sorter) {
+                    for (int i = tid; i < W.n_pad; i += T) {
+                        keys[i] = i < n ? rho[i] : (R)INFINITY;
+                        vals[i] = i;
+                    }
+                    __syncthreads();
+                    block_bitonic_sort(keys, vals, W.n_pad);
+                    for (int p = tid; p < n; p += T) {
+                        int src = vals[p];
+                        W.rho[nb][p] = W.rho[buf][src];
+                        W.ur[nb][p] = W.ur[buf][src];
+                        W.rid[nb][p] = W.rid[buf][src];
+                        keys[p] = W.rho_lo[src];
+                    }
+                    __syncthreads();
+                    for (int p = tid; p < n; p += T) W.rho_lo[p] = keys[p];
                 }
-                __syncthreads();
-                for (int p = tid; p < n; p += T) W.rho_lo[p] = keys[p];
                 buf = nb;
-                __syncthreads();
+                C.sync();
             }
         }
         R* rho = W.rho[buf];
@@ -301,7 +328,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
         // ---------------- stage 1 at (xi_n, y_n): the slice's fields
         RkSource<R> s1 = {b0, m, 0, 0, (R)1, (R)0, qtot, (R)0, beamR};
         bool bad = rk_stage(W, sscan, sR, W.rho_lo, ur, rid, nullptr, nullptr, s1, W.rk_kr, W.rk_ku, W.frho[0],
-                            W.fur[0], (R)0, true, slice, mode, p0, p1);
+                            W.fur[0], (R)0, true, slice, mode, p0, p1, C);
 
         // ---------------- a9: fields on beam particles (or query radii)
         {
@@ -310,7 +337,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
             const A Imax = acc_from_d(0.5 * dens_d * rmax_d * rmax_d, A());
             const A c0 = acc_from_d(0.25 * dens_d * rmax_d * rmax_d - 0.5 * dens_d * rmax_d * rmax_d * log(rmax_d), A());
             const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
-            for (int64_t q = tid; q < nq; q += T) {
+            for (int64_t q = gt; q < nq; q += GT) {
                 R x;
                 if (mode == MODE_MARCH) x = staged ? beamR[q] : W.br[b0 + q];
                 else x = (R)W.rq[q];
@@ -364,7 +391,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
         const R cst[3] = {(R)0.5, (R)0.5, (R)1};
         const R wst[3] = {(R)2, (R)2, (R)1};
         for (int stg = 0; stg < 3 && !bad; ++stg) {
-            __syncthreads();
+            C.sync();
             // the stage state in base (sorted y_n) order, mirrored at the axis
             bool ok = true;
             for (int p = p0; p < p1; ++p) {
@@ -377,20 +404,22 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
                 W.rk_u[p] = s * u;
                 W.rk_sg[p] = s;
             }
-            __syncthreads();
+            C.sync();
             for (int p = p0; p < p1; ++p)
                 if (p + 1 < n && W.rk_r[p + 1] < W.rk_r[p]) ok = false;
             const int32_t* perm = nullptr;
-            if (!__syncthreads_and(ok)) {
-                for (int i = tid; i < W.n_pad; i += T) {
-                    keys[i] = i < n ? W.rk_r[i] : (R)INFINITY;
-                    vals[i] = i;
+            if (!wake_vote(C, ok, true)) {
+                if (sorter) {
+                    for (int i = tid; i < W.n_pad; i += T) {
+                        keys[i] = i < n ? W.rk_r[i] : (R)INFINITY;
+                        vals[i] = i;
+                    }
+                    __syncthreads();
+                    block_bitonic_sort(keys, vals, W.n_pad);
+                    for (int i = tid; i < n; i += T) W.rk_perm[i] = vals[i];
                 }
-                __syncthreads();
-                block_bitonic_sort(keys, vals, W.n_pad);
-                for (int i = tid; i < n; i += T) W.rk_perm[i] = vals[i];
                 perm = W.rk_perm;
-                __syncthreads();
+                C.sync();
             }
             for (int i = tid; i < n; i += T) sR[i] = W.rk_r[perm ? perm[i] : i];
             // the sort's scratch overlaps the staged beam radii: stage them again
@@ -401,7 +430,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
             if (stg < 2) sst = {b0, m, b1, m1, (R)0.5, (R)0.5, qtot, qtot1, beamR};
             else sst = {b1, m1, 0, 0, (R)1, (R)0, qtot1, (R)0, W.br + b1};
             bad = rk_stage(W, sscan, sR, W.rk_rlo, W.rk_u, rid, perm, W.rk_sg, sst, W.rk_kr, W.rk_ku, W.frho[0],
-                           W.fur[0], wst[stg], false, slice, mode, p0, p1);
+                           W.fur[0], wst[stg], false, slice, mode, p0, p1, C);
         }
         if (bad) {
             status = 4;
@@ -411,7 +440,7 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
         }
 
         // ---------------- y_{n+1} = y_n + h/6 (k1 + 2 k2 + 2 k3 + k4), reflection
-        __syncthreads();
+        C.sync();
         for (int p = p0; p < p1; ++p) {
             R r = rho[p], rl = W.rho_lo[p];
             radius_add(r, rl, dxi / (R)6 * W.frho[0][p]);
@@ -425,10 +454,10 @@ march_rk4_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict
             W.rho_lo[p] = rl;
             ur[p] = u;
         }
-        __syncthreads();
+        C.sync();
     }
-    __syncthreads();
-    if (tid == 0) {
+    C.sync();
+    if (C.rank == 0 && tid == 0) {
         if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_BUF] = buf;

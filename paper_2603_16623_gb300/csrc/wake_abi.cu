@@ -49,7 +49,14 @@ wake_status fail(wake_status st, const char* fmt, ...) {
 
 constexpr int32_t kMaxRings = 8192;           // FP64 path (one CTA per wake, sort in shared memory)
 constexpr int32_t kMaxIonCells = 4096;        // mobile ions: rings per species (2 x 4096 rings per wake)
+// the global-memory marches with mobile ions or RK4 on thread-block clusters:
+// the automatic cluster's positions per thread (of each species with ions),
+// and a cluster's barriers per slice (per stage with RK4), us
+constexpr int32_t kIonRingsPerThread = 2;
+constexpr int32_t kRk4RingsPerThread = 2;
+constexpr double kGmClusterSliceUs = 20.0;
 constexpr int32_t kMaxRingsMixed = 65536;     // mixed path: a 16-CTA cluster of 512 threads x 8 rings
+constexpr int32_t kMaxRk4Rings = 16384;       // RK4: the stage-state sort of one block (8 B per ring)
 constexpr int32_t kMaxSliceParticles = 8192;
 constexpr int32_t kDefaultThreads = 256;
 
@@ -94,6 +101,7 @@ struct wake_handle {
     int32_t fast_threads = 0;               // > 0: the on-chip march serves this wake
     int32_t fast_k = 8;                     // its rings per thread
     int32_t fast_cl = 1;                    // CTAs per wake (thread-block cluster if > 1)
+    int32_t gm_cl = 1;                      // mobile ions, RK4: CTAs per wake of their march
     int32_t slice_max = kMaxSliceParticles; // particles in the densest slice (host count), or
                                             // -1: not known on the host (new beams, a push)
     size_t real_bytes() const { return prec == WAKE_FP64 ? 8 : 4; }
@@ -645,11 +653,13 @@ wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_sli
     int32_t mb_cap = 0;
     size_t smem = march_smem(h->n, h->n_pad, h->real_bytes(), kMaxSliceParticles, &mb_cap);
     if (h->n_ion) {
-        WK_CUDA(launch_march_ions<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
+        WK_CUDA(launch_march_ions<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->gm_cl,
+                                     h->st));
         return WAKE_OK;
     }
     if (h->rk4) {
-        WK_CUDA(launch_march_rk4<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
+        WK_CUDA(launch_march_rk4<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->gm_cl,
+                                    h->st));
         return WAKE_OK;
     }
     WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
@@ -833,10 +843,10 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, const FastShape& s
     size_t smem = march_smem(n_max, pad_max, hs[0]->real_bytes(), kMaxSliceParticles, &mb_cap);
     if (hs[0]->n_ion)
         e = launch_march_ions<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                                 hs[0]->threads, smem, mb_cap, st);
+                                 hs[0]->threads, smem, mb_cap, hs[0]->gm_cl, st);
     else if (hs[0]->rk4)
         e = launch_march_rk4<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                                hs[0]->threads, smem, mb_cap, st);
+                                hs[0]->threads, smem, mb_cap, hs[0]->gm_cl, st);
     else
         e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
                             hs[0]->threads, smem, mb_cap, st);
@@ -864,6 +874,14 @@ double predicted_fast_slice_us(const FastShape& f) {
     return 11.0 + 9.0 * R / 2048.0;
 }
 
+// Blocks per wake of the two-species and RK4 marches: a cluster once one
+// block would hold more than per_thread sorted positions (of each species,
+// with ions) per thread, at most kMaxWakeCtas blocks.
+int32_t gm_cluster_for(int32_t positions, int32_t threads, int32_t per_thread) {
+    const int32_t per_block = per_thread * threads;
+    return std::max(1, std::min(kMaxWakeCtas, (positions + per_block - 1) / per_block));
+}
+
 double predicted_slice_us(const wake_handle* h) {
     if (h->fast_threads > 0) {
         FastShape f;
@@ -872,8 +890,9 @@ double predicted_slice_us(const wake_handle* h) {
         f.cl = h->fast_cl;
         return predicted_fast_slice_us(f);
     }
-    const double per_thread = (double)h->n / h->threads;
-    return (h->rk4 ? 4.0 : 1.0) * (20.0 + 6.0 * per_thread);
+    const double per_thread = (double)h->n / ((double)h->threads * h->gm_cl);
+    const double cluster = h->gm_cl > 1 ? kGmClusterSliceUs : 0.0;
+    return (h->rk4 ? 4.0 : 1.0) * (20.0 + 6.0 * per_thread + cluster);
 }
 
 double predicted_ms(const wake_handle* h) { return h->n_steps * predicted_slice_us(h) * 1e-3; }
@@ -910,7 +929,7 @@ std::vector<LaunchGroup> plan_launches(int32_t n, wake_handle* const* hs, bool w
                       (hs[i]->fast_threads ? hs[i]->fast_cl : 0);
         // the one-CTA kernels (plain, two-species, RK4, grids) by their block size
         if (!hs[i]->fast_threads) key = -(1 + (hs[i]->n_ion ? 1 : 0) + 2 * hs[i]->rk4 + 4 * (hs[i]->grid_nr > 0) +
-                                          8 * hs[i]->threads);
+                                          8 * (hs[i]->threads + 1024 * (hs[i]->gm_cl - 1)));
         const double t = predicted_ms(hs[i]);
         int tier = 0;
         while (whole_window && tier + 1 < kTiers && t < kTierFrac[tier] * t_all) ++tier;
@@ -1341,8 +1360,9 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
         return fail(WAKE_EINVAL, "wake_init: mobile ions need ion_charge > 0 and ion_mass > 0 (or +inf)");
     if (plasma->cell_density && !ions)
         return fail(WAKE_EINVAL, "wake_init: a density profile needs ion rings (ion_charge > 0)");
-    if (ions && (cfg->rings_per_thread || cfg->cluster_ctas))
-        return fail(WAKE_EINVAL, "wake_init: rings_per_thread and cluster_ctas do not apply with mobile ions");
+    if (ions && (cfg->rings_per_thread || cfg->cluster_ctas < 0 || cfg->cluster_ctas > kMaxWakeCtas))
+        return fail(WAKE_EINVAL, "wake_init: with mobile ions rings_per_thread must be 0 and cluster_ctas in [0, %d]",
+                    kMaxWakeCtas);
     const int32_t max_rings = ions ? kMaxIonCells : wake_max_rings(cfg->precision);
     if (n_cells < 1 || n_cells > max_rings)
         return fail(WAKE_EINVAL, "wake_init: n_rings must be in [1, %d]%s", max_rings, ions ? " with mobile ions" : "");
@@ -1350,9 +1370,12 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     if (cfg->integrator != WAKE_AB2 && cfg->integrator != WAKE_RK4)
         return fail(WAKE_EINVAL, "wake_init: unknown integrator %d", cfg->integrator);
     const bool rk4 = cfg->integrator == WAKE_RK4;
-    if (rk4 && (ions || cfg->rings_per_thread || cfg->cluster_ctas))
-        return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the one-CTA march (no mobile ions, "
-                                 "rings_per_thread and cluster_ctas 0)");
+    if (rk4 && n_cells > kMaxRk4Rings)
+        return fail(WAKE_EINVAL, "wake_init: RK4 wakes have at most %d rings (block 0 sorts the stage states in its "
+                                 "shared memory)", kMaxRk4Rings);
+    if (rk4 && (ions || cfg->rings_per_thread || cfg->cluster_ctas < 0 || cfg->cluster_ctas > kMaxWakeCtas))
+        return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the global-memory march (no mobile "
+                                 "ions, rings_per_thread 0, cluster_ctas in [0, %d])", kMaxWakeCtas);
     if (cfg->grid_nr < 0 || cfg->grid_nr > 1024) return fail(WAKE_EINVAL, "wake_init: grid_nr must be in [0, 1024]");
     if (!(cfg->grid_rmax >= 0.0) || !std::isfinite(cfg->grid_rmax) || (cfg->grid_rmax > 0.0 && cfg->grid_nr == 0))
         return fail(WAKE_EINVAL, "wake_init: grid_rmax must be finite, >= 0, and set only with grid_nr > 0");
@@ -1403,6 +1426,10 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->n_steps = cfg->n_steps;
     h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;
+    h->gm_cl = cfg->cluster_ctas && (ions || rk4) ? cfg->cluster_ctas
+             : ions                              ? gm_cluster_for(n, threads, kIonRingsPerThread)
+             : rk4                               ? gm_cluster_for(n, threads, kRk4RingsPerThread)
+                                                 : 1;
     h->flags = cfg->flags;
     h->dxi = cfg->dxi;
     h->density = plasma->density;
@@ -1697,8 +1724,9 @@ wake_status wake_get_launch_config(wake_handle* h, int32_t* threads, int32_t* ri
     WK_TRY(check_handle(h));
     const bool fast = h->fast_threads > 0;
     if (threads) *threads = fast ? h->fast_threads : h->threads;
-    if (rings_per_thread) *rings_per_thread = fast ? h->fast_k : (h->n + h->threads - 1) / h->threads;
-    if (blocks_per_wake) *blocks_per_wake = fast ? h->fast_cl : 1;
+    const int32_t cta_threads = h->threads * h->gm_cl;
+    if (rings_per_thread) *rings_per_thread = fast ? h->fast_k : (h->n + cta_threads - 1) / cta_threads;
+    if (blocks_per_wake) *blocks_per_wake = fast ? h->fast_cl : h->gm_cl;
     return WAKE_OK;
 }
 

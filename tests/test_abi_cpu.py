@@ -190,13 +190,17 @@ def test_long_wakes_get_the_latency_shape():
     ({"ion_charge": -1.0, "ion_mass": 10.0}, "ion_charge > 0"),
     ({"ion_charge": 1.0, "ion_mass": 0.0}, "ion_charge > 0"),
     ({"ion_charge": 1.0, "ion_mass": float("nan")}, "ion_charge > 0"),
-    ({"ion_charge": 1.0, "ion_mass": 100.0, "k": 4}, "do not apply with mobile ions"),
+    ({"ion_charge": 1.0, "ion_mass": 100.0, "k": 4}, "with mobile ions rings_per_thread must be 0"),
+    ({"ion_charge": 1.0, "ion_mass": 100.0, "cl": 9}, "cluster_ctas in [0, 8]"),
+    ({"ion_charge": 1.0, "ion_mass": 100.0, "cl": -1, "precision": "fp64"}, "cluster_ctas in [0, 8]"),
     ({"ion_charge": 1.0, "ion_mass": 100.0, "n": 4097}, "with mobile ions"),
     ({"profile": 1.0}, "needs ion rings"),
     ({"ion_charge": 1.0, "ion_mass": 100.0, "profile": -1.0}, "cell_density[7]"),
     ({"integrator": 7}, "unknown integrator"),
     ({"integrator": 1, "ion_charge": 1.0, "ion_mass": 100.0}, "RK4 runs electron-only"),
-    ({"integrator": 1, "cl": 2}, "RK4 runs electron-only"),
+    ({"integrator": 1, "cl": 9}, "RK4 runs electron-only"),
+    ({"integrator": 1, "k": 4}, "RK4 runs electron-only"),
+    ({"integrator": 1, "n": 16385}, "RK4 wakes have at most 16384 rings"),
     ({"grid_nr": 2000, "precision": "fp64"}, "grid_nr must be"),
     ({"grid_nr": 16, "ion_charge": 1.0, "ion_mass": 100.0}, "beam grids run WAKE_AB2"),
     ({"grid_nr": 16, "precision": "fp64", "integrator": 1}, "beam grids run WAKE_AB2"),

@@ -43,11 +43,20 @@ def test_candidates_span_the_cluster_sizes():
     assert cands[1] == full[1] and cands[-1] == full[-1]  # the thinning keeps both ends
 
 
-def test_one_cta_marches_tune_the_block_size():
+def test_global_memory_marches_tune_the_block_size_and_clusters():
     for kind, default in (("fp64", 256), ("ions", 512), ("rk4", 512), ("grid", 256)):
         cands = at.candidates(1000, kind)
         assert cands[0].automatic
-        assert sorted(c.block_threads for c in cands[1:]) == sorted(t for t in (64, 128, 256, 512) if t != default)
+        sized = [c for c in cands[1:] if c.block_threads]
+        assert sorted(c.block_threads for c in sized) == sorted(t for t in (64, 128, 256, 512) if t != default)
+        clustered = [c for c in cands[1:] if not c.block_threads]
+        if kind in ("ions", "rk4"):
+            # a block size alone means one block per wake; then clusters of 512 threads
+            assert all(c.cluster_ctas == 1 and c.wake_kwargs()["cluster_ctas"] == 1 for c in sized)
+            assert [(c.cluster_ctas, c.ctas) for c in clustered] == [(2, 2), (4, 4), (8, 8)]
+            assert clustered[1].wake_kwargs() == {"rings_per_thread": 0, "cluster_ctas": 4}
+        else:
+            assert not clustered and all(c.cluster_ctas == 0 for c in sized)
     with pytest.raises(ValueError):
         at.candidates(5000, "ions")  # more cells than the two-species march takes
     with pytest.raises(ValueError):
@@ -106,6 +115,15 @@ def test_a_stored_shape_that_does_not_fit_falls_back_to_the_automatic_one():
     assert at.TuningTable().shape_for(3000) == {}
     one = at.TuningTable([at.TableEntry("fp64", 8192, block_threads=128)])
     assert one.shape_for(3000, "fp64") == {"block_threads": 128} and one.shape_for(3000, "mixed") == {}
+    # mobile ions / RK4: a cluster stored as positions per block, a block size as one block
+    ions = at.TuningTable([at.TableEntry("ions", 2048, block_threads=128), at.TableEntry("ions", 4096, rings_per_cta=1000)])
+    assert ions.shape_for(1500, "ions") == {"block_threads": 128, "cluster_ctas": 1}
+    assert ions.shape_for(3993, "ions") == {"cluster_ctas": 4}
+    assert ions.shape_for(3993, "rk4") == {}
+    res = at.SizeResult(6000, "rk4", [], at.Candidate(cluster_ctas=4, ctas=4))
+    e = at.entry_from(res, 8192)
+    assert (e.kind, e.rings_per_cta, e.block_threads) == ("rk4", 1500, 0)
+    assert at.TuningTable([e]).shape_for(7905, "rk4") == {"cluster_ctas": 6}
 
 
 class _FakeHandle:

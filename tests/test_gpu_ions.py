@@ -236,3 +236,126 @@ def test_profile_rejects_bad_use():
     bad[7] = -1.0
     with pytest.raises(wm.WakeError):
         wm.Wake.from_workload(wk, precision="mixed", cell_density=bad)
+
+
+# ---------------------------------------------------------------------------
+# the two-species march on a thread-block cluster (wide wakes): its blocks
+# split each species' positions, the scans fold over the cluster
+# ---------------------------------------------------------------------------
+def gpu_run_cl(wk, precision, threads, cluster, dumps=True):
+    from paper_2603_16623_gb300 import wake as wm
+    g = wm.Wake.from_workload(wk, precision=precision, block_threads=threads, cluster_ctas=cluster,
+                              flags=wm.WAKE_DUMP_RING_FIELDS if dumps else 0)
+    cfg = g.launch_config()
+    st, _, _, _ = g.run()
+    out = {"status": st, "progress": g.progress(), "beam": g.beam_fields(), "final": g.ring_state(), "cfg": cfg}
+    if dumps:
+        out["rings"] = g.ring_dumps()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("threads,cluster", [(64, 2), (64, 3), (128, 4), (64, 8)])
+def test_fp64_ion_wake_on_a_cluster_matches_oracle(threads, cluster):
+    """300 cells: 2-3 rings per species and thread over 2-3 blocks (ragged),
+    and 8 blocks of which the last three hold no ring."""
+    wk = ion_wake()
+    ref = oracle_run(wk)
+    assert ref.status == 0
+    got = gpu_run_cl(wk, "fp64", threads, cluster)
+    assert got["cfg"][0] == threads and got["cfg"][2] == cluster
+    assert got["status"] == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_fp64_ion_cluster_on_refined_cells():
+    """Refined cells with a ragged ring count, Z = 2, M = 25, on 3 blocks of
+    96 threads."""
+    wk = ion_wake(steps=400, nb0=3.0, ions=(2.0, 25.0), seed=62, edges=W.edges_refined(150, 1.0, 133, 5.0))
+    ref = oracle_run(wk)
+    got = gpu_run_cl(wk, "fp64", 96, 3)
+    assert got["status"] == ref.status == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_mixed_ion_wake_on_a_cluster_within_tolerance():
+    wk = ion_wake(n=500, steps=600, seed=63)
+    ref = oracle_run(wk)
+    got = gpu_run_cl(wk, "mixed", 128, 4)
+    assert got["status"] == ref.status == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    ok = unambiguous(wk, ref.rings["r"], got["rings"]["r"])
+    assert ok.mean() > 0.95
+    for k in ("ez", "wr"):
+        assert nerr(got["beam"][k][ok], ref.beam[k][ok]) < MIXED_TOL, k
+
+
+def test_ion_cluster_shapes_and_rejections():
+    from paper_2603_16623_gb300 import wake as wm
+    # automatic: a cluster once a block of 512 threads would hold more than 2
+    # rings of each species per thread
+    for cells, blocks in ((1024, 1), (1025, 2), (2048, 2), (3000, 3), (4096, 4)):
+        wk = W.Wake("shape", W.edges_uniform(cells, 5.0), [], 0.01, 10, ions=(1.0, 100.0))
+        g = wm.Wake.from_workload(wk, precision="mixed")
+        assert g.launch_config() == (512, -(-2 * cells // (512 * blocks)), blocks), cells
+        g.close()
+    wk = ion_wake(n=50, steps=20)
+    for bad in (-1, 9, 16):
+        with pytest.raises(wm.WakeError):
+            wm.Wake.from_workload(wk, precision="mixed", cluster_ctas=bad)
+
+
+def test_ion_cluster_static_query_and_budgeted_steps():
+    """Fields at query radii between slices, and steps bounded by a time
+    budget (the blocks agree on where to stop), resumed to the window's end:
+    the same bits as an unbounded run on the same cluster."""
+    from paper_2603_16623_gb300 import wake as wm
+    wk = ion_wake(n=400, steps=300, seed=69)
+    a = wm.Wake.from_workload(wk, precision="fp64", block_threads=64, cluster_ctas=4)
+    b = wm.Wake.from_workload(wk, precision="fp64", block_threads=64, cluster_ctas=1)
+    for g in (a, b):
+        wm.wake_batch_step([g], 120)
+    rq = np.linspace(0.0, 6.0, 777)
+    fa, fb = a.fields_at_static(rq), b.fields_at_static(rq)
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(fa[k], fb[k]) < FP64_TOL, k
+    a.run()
+    ref = (a.ring_state(), a.beam_fields())
+    a.close()
+    c = wm.Wake.from_workload(wk, precision="fp64", block_threads=64, cluster_ctas=4)
+    while c.progress()[0] < wk.n_steps:
+        wm.wake_batch_step([c], wk.n_steps, time_budget_ns=200_000)
+    assert all(np.array_equal(x, y) for x, y in zip(c.ring_state(), ref[0]))
+    fc = c.beam_fields()
+    assert all(np.array_equal(fc[k], ref[1][k]) for k in ref[1])
+    c.close()
+    b.close()
+
+
+def test_ion_cluster_wakes_batched_equal_alone():
+    """A batch mixing one-block and cluster shapes (automatic: 1100 cells
+    take 2 blocks) gives each wake the bits of its run alone."""
+    from paper_2603_16623_gb300 import wake as wm
+    wakes = [ion_wake(n=1100, steps=120, seed=71), ion_wake(n=300, steps=150, seed=72),
+             ion_wake(n=1500, steps=100, ions=(1.0, 400.0), seed=73)]
+    alone = []
+    for wk in wakes:
+        g = wm.Wake.from_workload(wk, precision="mixed")
+        g.run()
+        alone.append((g.launch_config(), g.ring_state(), g.beam_fields(("ez", "wr"))))
+        g.close()
+    assert [c[2] for c, _, _ in alone] == [2, 1, 2]
+    gs = [wm.Wake.from_workload(wk, precision="mixed") for wk in wakes]
+    wm.wake_batch_run(gs)
+    for g, (_, st, bf) in zip(gs, alone):
+        r, u = g.ring_state()
+        assert np.array_equal(r, st[0]) and np.array_equal(u, st[1])
+        f = g.beam_fields(("ez", "wr"))
+        assert np.array_equal(f["ez"], bf["ez"]) and np.array_equal(f["wr"], bf["wr"])
+        g.close()

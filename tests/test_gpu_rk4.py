@@ -155,3 +155,122 @@ def test_rk4_rejects_bad_use():
         wm.Wake.from_workload(wk, precision="mixed", ions=(1.0, 100.0))
     with pytest.raises(wm.WakeError):
         wm.Wake.from_workload(wk, precision="mixed", rings_per_thread=4)
+
+
+# ---------------------------------------------------------------------------
+# RK4 on a thread-block cluster (wide wakes): the blocks split the sorted
+# positions, the scans fold over the cluster, block 0 sorts the state and the
+# stage states
+# ---------------------------------------------------------------------------
+def gpu_run_cl(wk, precision, threads, cluster, dumps=True):
+    from paper_2603_16623_gb300 import wake as wm
+    g = wm.Wake.from_workload(wk, precision=precision, block_threads=threads, cluster_ctas=cluster,
+                              flags=wm.WAKE_DUMP_RING_FIELDS if dumps else 0)
+    cfg = g.launch_config()
+    st, _, _, _ = g.run()
+    out = {"status": st, "progress": g.progress(), "beam": g.beam_fields(), "final": g.ring_state(), "cfg": cfg}
+    if dumps:
+        out["rings"] = g.ring_dumps()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("threads,cluster", [(64, 2), (64, 3), (128, 4), (64, 8)])
+def test_fp64_rk4_wake_on_a_cluster_matches_oracle(threads, cluster):
+    """300 rings over 2-8 blocks (ragged; with 8 blocks of 64 threads at one
+    ring each, the last three blocks hold no ring)."""
+    wk = rk4_wake()
+    ref = oracle_run(wk)
+    got = gpu_run_cl(wk, "fp64", threads, cluster)
+    assert got["cfg"][0] == threads and got["cfg"][2] == cluster
+    assert got["status"] == ref.status == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+    assert nerr(got["final"][0], ref.final_r) < FP64_TOL
+
+
+def test_fp64_rk4_axis_crossings_on_a_cluster_match_oracle():
+    """Rings crossing each other and the axis: the state and the stage
+    states are re-sorted by block 0 for all three blocks."""
+    wk = rk4_wake(steps=450, nb0=5.0, sig_r=0.15, seed=82, edges=W.edges_refined(140, 1.0, 157, 5.0))
+    ref = oracle_run(wk)
+    assert np.any(np.diff(np.sign(ref.rings["ur"]), axis=0) != 0)
+    got = gpu_run_cl(wk, "fp64", 64, 3)
+    assert got["status"] == ref.status == 0
+    for k in ("r", "ur", "psi", "dpsidz", "bp"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+def test_mixed_rk4_wake_on_a_cluster_within_tolerance():
+    wk = rk4_wake(n=600, steps=600, seed=83)
+    ref = oracle_run(wk)
+    got = gpu_run_cl(wk, "mixed", 128, 4)
+    assert got["status"] == ref.status == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < MIXED_TOL
+    ok = unambiguous(wk, ref.rings["r"], got["rings"]["r"])
+    assert ok.mean() > 0.95
+    for k in ("ez", "wr"):
+        assert nerr(got["beam"][k][ok], ref.beam[k][ok]) < MIXED_TOL, k
+
+
+def test_one_step_parity_on_a_strong_rk4_wake_on_a_cluster():
+    """The strong wake's slices from the oracle's state, one slice each on a
+    cluster of 4 blocks (FP64)."""
+    from paper_2603_16623_gb300 import wake as wm
+    drv = W.gaussian_beam(60_000, 10.0, 0.15, 0.5, 2.0, seed=84)
+    wk = W.Wake("strong_rk4", W.edges_uniform(400, 4.0), [drv], 0.01, 800, integrator="rk4")
+    ref = oracle.run_wake(wk, ring_dumps=("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"))
+    R = ref.rings
+    bad = []
+    for n in range(60, ref.slices_run - 1, 120):
+        g = wm.Wake.from_workload(wk, precision="fp64", block_threads=64, cluster_ctas=4,
+                                  flags=wm.WAKE_DUMP_RING_FIELDS)
+        g.set_ring_state(n, R["r"][n], R["ur"][n])
+        g.step_slices(1)
+        assert g.progress()[:2] == (n + 1, 0)
+        d = g.ring_dumps()
+        rho, ur = g.ring_state()
+        e = {k: nerr(d[k][n], R[k][n]) for k in ("psi", "dpsidr", "dpsidz", "bp", "bb")}
+        e["r"] = nerr(rho, R["r"][n + 1])
+        e["ur"] = nerr(ur, R["ur"][n + 1])
+        g.close()
+        bad += [(n, k, v) for k, v in e.items() if not v < max(FP64_TOL, 1e-14 if k == "ur" else 0.0)]
+    assert not bad, bad
+
+
+def test_rk4_cluster_shapes_batches_and_rejections():
+    """Automatic blocks per wake (a cluster once a block of 512 threads would
+    hold more than 2 rings per thread); a batch mixing one-block and cluster
+    shapes gives each wake the bits of its run alone; bad cluster sizes are
+    refused."""
+    from paper_2603_16623_gb300 import wake as wm
+    for rings, blocks in ((1024, 1), (1025, 2), (3000, 3), (7905, 8), (16384, 8)):
+        wk = W.Wake("shape", W.edges_uniform(rings, 5.0), [], 0.01, 10, integrator="rk4")
+        g = wm.Wake.from_workload(wk, precision="mixed")
+        assert g.launch_config() == (512, -(-rings // (512 * blocks)), blocks), rings
+        g.close()
+    wakes = [rk4_wake(n=1500, steps=60, seed=88), rk4_wake(n=300, steps=80, seed=89),
+             rk4_wake(n=600, steps=70, seed=90)]
+    shapes = [0, 0, 3]
+    alone = []
+    for wk, cl in zip(wakes, shapes):
+        g = wm.Wake.from_workload(wk, precision="mixed", cluster_ctas=cl)
+        g.run()
+        alone.append((g.launch_config(), g.ring_state(), g.beam_fields(("ez", "wr"))))
+        g.close()
+    assert [c[2] for c, _, _ in alone] == [2, 1, 3]
+    gs = [wm.Wake.from_workload(wk, precision="mixed", cluster_ctas=cl) for wk, cl in zip(wakes, shapes)]
+    wm.wake_batch_run(gs)
+    for g, (_, st, bf) in zip(gs, alone):
+        r, u = g.ring_state()
+        assert np.array_equal(r, st[0]) and np.array_equal(u, st[1])
+        f = g.beam_fields(("ez", "wr"))
+        assert np.array_equal(f["ez"], bf["ez"]) and np.array_equal(f["wr"], bf["wr"])
+        g.close()
+    for bad in (-1, 9):
+        with pytest.raises(wm.WakeError):
+            wm.Wake.from_workload(rk4_wake(n=50, steps=20), precision="mixed", cluster_ctas=bad)
