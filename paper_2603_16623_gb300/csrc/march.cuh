@@ -235,7 +235,7 @@ __device__ __forceinline__ ff acc_add_prod(ff a, float x, float y) { return ff_a
 // barrier, which every block passes only after it read the buffer).
 // ---------------------------------------------------------------------------
 constexpr int kMaxWakeCtas = 8;
-constexpr int kPartSlot = 32;                          // bytes per block total
+constexpr int kPartSlot = 64;                          // bytes per block total
 constexpr int kPartBuf = kMaxWakeCtas * kPartSlot;     // one buffer
 struct WakeCtas {
     int rank = 0, size = 1;
@@ -288,6 +288,42 @@ __device__ __forceinline__ T wake_excl_scan(WakeCtas& C, T v, Op op, T ident, T*
     }
     total = tot;
     return op(pre, ex);
+}
+
+// two scans over the wake's threads whose block totals travel in one
+// exchange (one cluster barrier instead of two); each result as
+// wake_excl_scan's
+template <class T, class U>
+struct TwoVals {
+    T a;
+    U b;
+};
+template <bool REV0, bool REV1, class T, class Op0, class U, class Op1>
+__device__ __forceinline__ void wake_excl_scan2(WakeCtas& C, T v0, Op0 op0, T id0, T* sbuf0, T& ex0, T& tot0,
+                                                U v1, Op1 op1, U id1, U* sbuf1, U& ex1, U& tot1) {
+    T bt0;
+    U bt1;
+    ex0 = block_excl_scan<REV0>(v0, op0, id0, sbuf0, bt0);
+    ex1 = block_excl_scan<REV1>(v1, op1, id1, sbuf1, bt1);
+    if (C.size == 1) {
+        tot0 = bt0;
+        tot1 = bt1;
+        return;
+    }
+    const TwoVals<T, U>* buf = C.exchange(TwoVals<T, U>{bt0, bt1});
+    T pre0 = id0, t0 = id0;
+    U pre1 = id1, t1 = id1;
+    for (int i = 0; i < C.size; ++i) {
+        const int r0 = REV0 ? C.size - 1 - i : i, r1 = REV1 ? C.size - 1 - i : i;
+        if (r0 == C.rank) pre0 = t0;
+        if (r1 == C.rank) pre1 = t1;
+        t0 = op0(t0, C.slot(buf, r0).a);
+        t1 = op1(t1, C.slot(buf, r1).b);
+    }
+    tot0 = t0;
+    tot1 = t1;
+    ex0 = op0(pre0, ex0);
+    ex1 = op1(pre1, ex1);
 }
 
 // the forward sum of fx and the reverse (suffix) sum of ry over the wake's
@@ -358,8 +394,9 @@ __device__ void bp_region_solve(const WakeDev<P>& W, const typename P::R* sR, in
         Mb = OpMatLeft()(Mb, Mi);
     }
     Mat2<R> tf, tb;
-    Mat2<R> Yf = wake_excl_scan<false>(C, Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tf);
-    Mat2<R> Yb = wake_excl_scan<true>(C, Mb, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), tb);
+    Mat2<R> Yf, Yb;
+    wake_excl_scan2<false, true>(C, Mf, OpMatLeft(), I2, reinterpret_cast<Mat2<R>*>(sscan), Yf, tf, Mb, OpMatLeft(),
+                                 I2, reinterpret_cast<Mat2<R>*>(sscan), Yb, tb);
     if (C.rank == 0 && tid == 0) {
         W.Ra[0] = 1;
         W.Rb[0] = 0;

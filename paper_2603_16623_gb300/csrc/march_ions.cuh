@@ -244,9 +244,10 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
 
         // ---------------- a3 + a4: beam field at rings; per species own psi, d_rho psi
         A Stot[2], Ltot[2];
+        Pair<A> loc[2], exs[2], tots[2];
         for (int s = 0; s < 2; ++s) {
-            const int base = s * N, rb = s * (N + 1);
-            Pair<A> loc = {zeroA, zeroA};
+            const int base = s * N;
+            loc[s] = {zeroA, zeroA};
             for (int q = q0; q < q1; ++q) {
                 const int p = base + q;
                 R r = sR[p];
@@ -259,12 +260,17 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                     bbv = Q * inv_2pi_dxi / r;
                 }
                 W.bb[p] = bbv;
-                loc.x = acc_add_r(loc.x, c);
-                loc.y = acc_add(loc.y, acc_mul_r(ring_log(W.ctab, id, r, W.rho_lo[p]), c));
+                loc[s].x = acc_add_r(loc[s].x, c);
+                loc[s].y = acc_add(loc[s].y, acc_mul_r(ring_log(W.ctab, id, r, W.rho_lo[p]), c));
             }
-            Pair<A> tot;
-            Pair<A> ex = wake_excl_scan<false>(C, loc, OpAddPair(), Pair<A>{zeroA, zeroA},
-                                                reinterpret_cast<Pair<A>*>(sscan), tot);
+        }
+        // both species' scans, their block totals in one exchange
+        wake_excl_scan2<false, false>(C, loc[0], OpAddPair(), Pair<A>{zeroA, zeroA},
+                                      reinterpret_cast<Pair<A>*>(sscan), exs[0], tots[0], loc[1], OpAddPair(),
+                                      Pair<A>{zeroA, zeroA}, reinterpret_cast<Pair<A>*>(sscan), exs[1], tots[1]);
+        for (int s = 0; s < 2; ++s) {
+            const int base = s * N, rb = s * (N + 1);
+            const Pair<A> tot = tots[s], ex = exs[s];
             Stot[s] = tot.x;
             Ltot[s] = tot.y;
             A S = ex.x, L = ex.y;
@@ -327,13 +333,16 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         }
 
         // ---------------- a6: per species own d_zeta psi, then the totals
-        A Ttot[2];
+        A Ttot[2], tl[2], Tex[2];
+        for (int s = 0; s < 2; ++s) {
+            tl[s] = zeroA;
+            for (int q = q0; q < q1; ++q) tl[s] = acc_add_r(tl[s], W.tt[s * N + q]);
+        }
+        wake_excl_scan2<false, false>(C, tl[0], OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Tex[0], Ttot[0], tl[1],
+                                      OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Tex[1], Ttot[1]);
         for (int s = 0; s < 2; ++s) {
             const int base = s * N, rb = s * (N + 1);
-            A tl = zeroA;
-            for (int q = q0; q < q1; ++q) tl = acc_add_r(tl, W.tt[base + q]);
-            A Tex = wake_excl_scan<false>(C, tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot[s]);
-            A Tacc = Tex;
+            A Tacc = Tex[s];
             for (int q = q0; q < q1; ++q) {
                 const int p = base + q;
                 int id = rid[p];
