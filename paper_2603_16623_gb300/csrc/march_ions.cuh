@@ -105,6 +105,10 @@ __device__ __forceinline__ R gather_r(const Locate<A, R>& L, const R* F, int n, 
     return lo + (up - lo) * L.wgt;
 }
 
+// the per-ring values only their own thread reads (kept in shared memory
+// when the launch has room): B^(b), psibar, gamma, d_rho psi, t / d_zeta psi
+enum { kOwnBb = 0, kOwnPsib, kOwnGam, kOwnDpr, kOwnT, kOwnArrays };
+
 template <class P>
 __global__ void __launch_bounds__(512)
 march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ order, int32_t max_slices,
@@ -145,6 +149,28 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
     int32_t* vals = reinterpret_cast<int32_t*>(keys + W.n_pad);
     R* sR = keys;      // sorted ring radii, both segments (after the sort)
     R* sB = keys + n;  // staged beam radii of the slice
+    // Per-ring values only their own thread reads (B^(b), psibar, gamma,
+    // d_rho psi, t and then d_zeta psi): in shared memory after the sort and
+    // staging region when the launch left room for them (the host adds it
+    // when it fits), else in the wake's global arrays.
+    const int TK = T * K;             // a block's positions of each species
+    const int qb = min(N, C.rank * TK);
+    R* own = nullptr;
+    {
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        size_t used = (size_t)(n + mb_cap) * sizeof(R);
+        const size_t sort_used = (size_t)W.n_pad * (sizeof(R) + 4);
+        used = kScanBytes + (used > sort_used ? used : sort_used);
+        used = (used + 15) & ~(size_t)15;
+        if (used + (size_t)kOwnArrays * 2 * TK * sizeof(R) <= dyn) own = reinterpret_cast<R*>(smem + used);
+    }
+    // the value `a` (kOwn*) of species s, sorted position q (this thread's)
+    auto scr = [&](int a, int s, int q) -> R& {
+        if (own) return own[(a * 2 + s) * TK + (q - qb)];
+        R* g = a == kOwnBb ? W.bb : a == kOwnPsib ? W.psib : a == kOwnGam ? W.gam : a == kOwnDpr ? W.dpr : W.tt;
+        return g[s * N + q];
+    };
 
     if (tid < CTL_N) s_ctl[tid] = W.ctl[tid];
     __syncthreads();
@@ -259,7 +285,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                     R Q = lb < m ? W.bE[b0 + lb] : qtot;
                     bbv = Q * inv_2pi_dxi / r;
                 }
-                W.bb[p] = bbv;
+                scr(kOwnBb, s, q) = bbv;
                 loc[s].x = acc_add_r(loc[s].x, c);
                 loc[s].y = acc_add(loc[s].y, acc_mul_r(ring_log(W.ctab, id, r, W.rho_lo[p]), c));
             }
@@ -320,10 +346,10 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 R psi = acc_to_r(acc_add(W.psio[p], psiA));
                 R dprv = acc_to_r(acc_add(W.dpro[p], dprA));
                 R pb = (R)1 - qm[s] * psi;
-                W.psib[p] = pb;
-                W.gam[p] = ((R)1 + u * u + pb * pb) / ((R)2 * pb);
-                W.dpr[p] = dprv;
-                W.tt[p] = c * u / (r * pb);
+                scr(kOwnPsib, s, q) = pb;
+                scr(kOwnGam, s, q) = ((R)1 + u * u + pb * pb) / ((R)2 * pb);
+                scr(kOwnDpr, s, q) = dprv;
+                scr(kOwnT, s, q) = c * u / (r * pb);
                 if (mode == MODE_MARCH && W.dump_psi) {
                     size_t row = (size_t)slice * n + rid[p];
                     W.dump_psi[row] = psi;
@@ -336,7 +362,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         A Ttot[2], tl[2], Tex[2];
         for (int s = 0; s < 2; ++s) {
             tl[s] = zeroA;
-            for (int q = q0; q < q1; ++q) tl[s] = acc_add_r(tl[s], W.tt[s * N + q]);
+            for (int q = q0; q < q1; ++q) tl[s] = acc_add_r(tl[s], scr(kOwnT, s, q));
         }
         wake_excl_scan2<false, false>(C, tl[0], OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Tex[0], Ttot[0], tl[1],
                                       OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Tex[1], Ttot[1]);
@@ -347,7 +373,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 const int p = base + q;
                 int id = rid[p];
                 R c = W.w[id], ch = W.wh[id];
-                R t = W.tt[p];
+                R t = scr(kOwnT, s, q);
                 W.regT[rb + q] = acc_to_r(acc_sub(Ttot[s], Tacc));
                 Tacc = acc_add_r(Tacc, t);
                 R above = acc_to_r(acc_sub(Ttot[s], Tacc));
@@ -363,7 +389,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 const auto Lc = locate(sR + ob, W.rho_lo + ob, N, edge, Xe, ring_radius(sR, W.rho_lo, p), sR[p]);
                 // no ring of the other species above: no d_zeta psi from it
                 R dpz = W.dpzo[p] + (Lc.where == 2 ? (R)0 : gather_r(Lc, W.dpzo + ob, N, -oT, (R)0));
-                W.tt[p] = dpz;  // t no longer needed: keep d_zeta psi
+                scr(kOwnT, s, q) = dpz;  // t no longer needed: keep d_zeta psi
                 if (mode == MODE_MARCH && W.dump_dpz) W.dump_dpz[(size_t)slice * n + rid[p]] = dpz;
             }
         }
@@ -373,7 +399,8 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             const int p = q;
             R r = sR[p], u = ur[p];
             R w = W.w[rid[p]];
-            R pb = W.psib[p], g = W.gam[p], dprv = W.dpr[p], dpz = W.tt[p], bbv = W.bb[p];
+            R pb = scr(kOwnPsib, 0, q), g = scr(kOwnGam, 0, q), dprv = scr(kOwnDpr, 0, q), dpz = scr(kOwnT, 0, q),
+              bbv = scr(kOwnBb, 0, q);
             R wr = w / r, pb2 = pb * pb;
             W.cA[p] = wr / pb;
             W.cB[p] = -wr * g * dprv / pb2 + wr * bbv / pb + (w / (r * r)) * u * u / pb2 +
@@ -407,9 +434,10 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                 const int p = s * N + q;
                 R r = sR[p];
                 R bpv = W.cA[p];
-                R pb = W.psib[p];
-                if (!(pb > (R)0) || !real_finite(pb) || !real_finite(W.dpr[p]) || !real_finite(W.tt[p]) ||
-                    !real_finite(bpv) || !real_finite(W.bb[p]) || !real_finite(W.gam[p]))
+                R pb = scr(kOwnPsib, s, q);
+                if (!(pb > (R)0) || !real_finite(pb) || !real_finite(scr(kOwnDpr, s, q)) ||
+                    !real_finite(scr(kOwnT, s, q)) || !real_finite(bpv) || !real_finite(scr(kOwnBb, s, q)) ||
+                    !real_finite(scr(kOwnGam, s, q)))
                     bad = true;
                 if (mode == MODE_MARCH) {
                     size_t row = (size_t)slice * n + rid[p];
@@ -417,7 +445,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                     if (W.dump_ur) {
                         W.dump_ur[row] = ur[p];
                         W.dump_bp[row] = bpv;
-                        W.dump_bb[row] = W.bb[p];
+                        W.dump_bb[row] = scr(kOwnBb, s, q);
                     }
                 }
             }
@@ -483,9 +511,9 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             for (int q = q0; q < q1; ++q) {
                 const int p = s * N + q;
                 R r = sR[p], u = ur[p];
-                R pb = W.psib[p];
+                R pb = scr(kOwnPsib, s, q);
                 R fr = u / pb;
-                R fu = -qm[s] * (W.gam[p] * W.dpr[p] / pb - (W.cA[p] + W.bb[p]));
+                R fu = -qm[s] * (scr(kOwnGam, s, q) * scr(kOwnDpr, s, q) / pb - (W.cA[p] + scr(kOwnBb, s, q)));
                 R rn = r, rlo = W.rho_lo[p], un;
                 if (has_prev) {
                     radius_add(rn, rlo, dxi * ((R)1.5 * fr - (R)0.5 * frho[p]));

@@ -635,6 +635,22 @@ cudaError_t aux_stream(int i, cudaStream_t* out) { return level_stream(0, i, out
 // the march streams of a tier
 cudaError_t tier_stream(int tier, int i, cudaStream_t* out) { return level_stream(1 + tier, i, out); }
 
+// The two-species march keeps the per-ring values only their own thread
+// reads (5 per ring of each species, kOwnArrays in march_ions.cuh) in shared
+// memory after its sort and staging region when the launch has room for
+// them: their bytes for this wake's block, and the launch's dynamic shared
+// memory with them added if that stays within a block's limit (else the
+// kernel keeps them in global memory).
+size_t ion_own_bytes(const wake_handle* h) {
+    const int64_t per_block = (int64_t)h->threads * h->gm_cl;
+    const int64_t k = (h->n_ion + per_block - 1) / per_block;
+    return (size_t)kOwnArrays * 2 * (size_t)h->threads * (size_t)k * h->real_bytes();
+}
+size_t with_ion_own(size_t smem, size_t own) {
+    constexpr size_t kBlockSmemMax = 227 * 1024 - 4096;  // the opt-in limit less the static shared memory
+    return smem + own <= kBlockSmemMax ? smem + own : smem;
+}
+
 // Particles per slice the march should be able to stage for this wake: its
 // densest slice, or the most the library accepts when that is not known.
 int32_t stage_want(const wake_handle* h) { return h->slice_max < 0 ? kMaxSliceParticles : h->slice_max; }
@@ -653,6 +669,7 @@ wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_sli
     int32_t mb_cap = 0;
     size_t smem = march_smem(h->n, h->n_pad, h->real_bytes(), kMaxSliceParticles, &mb_cap);
     if (h->n_ion) {
+        smem = with_ion_own(smem, ion_own_bytes(h));
         WK_CUDA(launch_march_ions<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->gm_cl,
                                      h->st));
         return WAKE_OK;
@@ -841,6 +858,11 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, const FastShape& s
     }
     int32_t mb_cap = 0;
     size_t smem = march_smem(n_max, pad_max, hs[0]->real_bytes(), kMaxSliceParticles, &mb_cap);
+    if (hs[0]->n_ion) {
+        size_t own = 0;
+        for (const wake_handle* h : hs) own = std::max(own, ion_own_bytes(h));
+        smem = with_ion_own(smem, own);
+    }
     if (hs[0]->n_ion)
         e = launch_march_ions<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
                                  hs[0]->threads, smem, mb_cap, hs[0]->gm_cl, st);

@@ -359,3 +359,18 @@ def test_ion_cluster_wakes_batched_equal_alone():
         f = g.beam_fields(("ez", "wr"))
         assert np.array_equal(f["ez"], bf["ez"]) and np.array_equal(f["wr"], bf["wr"])
         g.close()
+
+
+def test_ion_scratch_in_global_memory_when_shared_memory_is_short():
+    """A block keeps its rings' own-thread values in shared memory when the
+    launch has room; 4096 cells on one block of 512 threads (8 rings of each
+    species per thread) leave none, and the kernel keeps them in global
+    memory: the results agree with the same wake on 4 blocks (FP64 1e-10)."""
+    wk = ion_wake(n=4096, steps=80, ions=(1.0, 1836.0), seed=74)
+    one = gpu_run_cl(wk, "fp64", 512, 1, dumps=False)
+    four = gpu_run_cl(wk, "fp64", 512, 4, dumps=False)
+    assert one["cfg"] == (512, 16, 1) and four["cfg"] == (512, 4, 4)
+    assert one["status"] == four["status"] == 0
+    assert nerr(one["final"][0], four["final"][0]) < FP64_TOL
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(one["beam"][k], four["beam"][k]) < FP64_TOL, k
