@@ -107,7 +107,8 @@ __device__ __forceinline__ R gather_r(const Locate<A, R>& L, const R* F, int n, 
 
 // the per-ring values only their own thread reads (kept in shared memory
 // when the launch has room): B^(b), psibar, gamma, d_rho psi, t / d_zeta psi
-enum { kOwnBb = 0, kOwnPsib, kOwnGam, kOwnDpr, kOwnT, kOwnArrays };
+// and the ring's weights c, c-hat (real type), then ln rho (accumulator type)
+enum { kOwnBb = 0, kOwnPsib, kOwnGam, kOwnDpr, kOwnT, kOwnW, kOwnWh, kOwnArrays };
 
 template <class P>
 __global__ void __launch_bounds__(512)
@@ -163,8 +164,10 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         const size_t sort_used = (size_t)W.n_pad * (sizeof(R) + 4);
         used = kScanBytes + (used > sort_used ? used : sort_used);
         used = (used + 15) & ~(size_t)15;
-        if (used + (size_t)kOwnArrays * 2 * TK * sizeof(R) <= dyn) own = reinterpret_cast<R*>(smem + used);
+        if (used + (size_t)kOwnArrays * 2 * TK * sizeof(R) + 2 * (size_t)TK * sizeof(A) <= dyn)
+            own = reinterpret_cast<R*>(smem + used);
     }
+    A* own_ln = own ? reinterpret_cast<A*>(own + kOwnArrays * 2 * TK) : nullptr;
     // the value `a` (kOwn*) of species s, sorted position q (this thread's)
     auto scr = [&](int a, int s, int q) -> R& {
         if (own) return own[(a * 2 + s) * TK + (q - qb)];
@@ -251,6 +254,11 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         R* frho = W.frho[buf];
         R* fur = W.fur[buf];
         const int32_t* rid = W.rid[buf];
+        // the weights c, c-hat of this thread's ring (s, q)
+        auto wgt = [&](int a, int s, int q) -> R {
+            if (own) return own[(a * 2 + s) * TK + (q - qb)];
+            return (a == kOwnW ? W.w : W.wh)[rid[s * N + q]];
+        };
 
         // ---------------- stage ring radii and this slice's beam radii
         const bool have_beam = W.nb > 0 && slice < W.n_steps;
@@ -286,8 +294,14 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
                     bbv = Q * inv_2pi_dxi / r;
                 }
                 scr(kOwnBb, s, q) = bbv;
+                const A lnr = ring_log(W.ctab, id, r, W.rho_lo[p]);
+                if (own) {
+                    own[(kOwnW * 2 + s) * TK + (q - qb)] = c;
+                    own[(kOwnWh * 2 + s) * TK + (q - qb)] = W.wh[id];
+                    own_ln[s * TK + (q - qb)] = lnr;
+                }
                 loc[s].x = acc_add_r(loc[s].x, c);
-                loc[s].y = acc_add(loc[s].y, acc_mul_r(ring_log(W.ctab, id, r, W.rho_lo[p]), c));
+                loc[s].y = acc_add(loc[s].y, acc_mul_r(lnr, c));
             }
         }
         // both species' scans, their block totals in one exchange
@@ -303,9 +317,8 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             for (int q = q0; q < q1; ++q) {
                 const int p = base + q;
                 R r = sR[p];
-                int id = rid[p];
-                R c = W.w[id], ch = W.wh[id];
-                const A lnr = ring_log(W.ctab, id, r, W.rho_lo[p]);
+                const R c = wgt(kOwnW, s, q), ch = wgt(kOwnWh, s, q);
+                const A lnr = own ? own_ln[s * TK + (q - qb)] : ring_log(W.ctab, rid[p], r, W.rho_lo[p]);
                 A Lsuf = acc_sub(tot.y, L);
                 W.regS[rb + q] = S;
                 W.regL[rb + q] = Lsuf;
@@ -332,7 +345,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             for (int q = q0; q < q1; ++q) {
                 const int p = base + q;
                 R r = sR[p], u = ur[p];
-                R c = W.w[rid[p]];
+                R c = wgt(kOwnW, s, q);
                 const A X = ring_radius(sR, W.rho_lo, p);
                 const auto Lc = locate(sR + ob, W.rho_lo + ob, N, edge, Xe, X, r);
                 A psiA, dprA;
@@ -371,8 +384,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
             A Tacc = Tex[s];
             for (int q = q0; q < q1; ++q) {
                 const int p = base + q;
-                int id = rid[p];
-                R c = W.w[id], ch = W.wh[id];
+                R c = wgt(kOwnW, s, q), ch = wgt(kOwnWh, s, q);
                 R t = scr(kOwnT, s, q);
                 W.regT[rb + q] = acc_to_r(acc_sub(Ttot[s], Tacc));
                 Tacc = acc_add_r(Tacc, t);
@@ -398,7 +410,7 @@ march_ions_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restric
         for (int q = q0; q < q1; ++q) {
             const int p = q;
             R r = sR[p], u = ur[p];
-            R w = W.w[rid[p]];
+            R w = wgt(kOwnW, 0, q);
             R pb = scr(kOwnPsib, 0, q), g = scr(kOwnGam, 0, q), dprv = scr(kOwnDpr, 0, q), dpz = scr(kOwnT, 0, q),
               bbv = scr(kOwnBb, 0, q);
             R wr = w / r, pb2 = pb * pb;

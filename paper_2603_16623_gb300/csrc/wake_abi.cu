@@ -636,7 +636,7 @@ cudaError_t aux_stream(int i, cudaStream_t* out) { return level_stream(0, i, out
 cudaError_t tier_stream(int tier, int i, cudaStream_t* out) { return level_stream(1 + tier, i, out); }
 
 // The two-species march keeps the per-ring values only their own thread
-// reads (5 per ring of each species, kOwnArrays in march_ions.cuh) in shared
+// reads (kOwnArrays in march_ions.cuh, and ln rho) in shared
 // memory after its sort and staging region when the launch has room for
 // them: their bytes for this wake's block, and the launch's dynamic shared
 // memory with them added if that stays within a block's limit (else the
@@ -644,7 +644,8 @@ cudaError_t tier_stream(int tier, int i, cudaStream_t* out) { return level_strea
 size_t ion_own_bytes(const wake_handle* h) {
     const int64_t per_block = (int64_t)h->threads * h->gm_cl;
     const int64_t k = (h->n_ion + per_block - 1) / per_block;
-    return (size_t)kOwnArrays * 2 * (size_t)h->threads * (size_t)k * h->real_bytes();
+    // (and ln rho in the accumulator type: 8 bytes, a float-float or a double)
+    return ((size_t)kOwnArrays * h->real_bytes() + 8) * 2 * (size_t)h->threads * (size_t)k;
 }
 size_t with_ion_own(size_t smem, size_t own) {
     constexpr size_t kBlockSmemMax = 227 * 1024 - 4096;  // the opt-in limit less the static shared memory
