@@ -174,11 +174,10 @@ static cudaError_t launch_gm(void (*kern)(const WakeDev<P>*, const int32_t*, int
 
 template <class P>
 cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
-                         int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(march_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    march_kernel<P><<<n_wakes, threads, smem, st>>>(d_wakes, d_order, max_slices, mode, mb_cap);
-    return cudaGetLastError();
+                         int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, int32_t cluster_ctas,
+                         cudaStream_t st) {
+    return launch_gm(march_kernel<P>, d_wakes, d_order, n_wakes, max_slices, mode, threads, smem, mb_cap,
+                     cluster_ctas, st);
 }
 
 int32_t march_stage_particles(int32_t threads, int32_t k_rings, int32_t cluster_ctas, int32_t want) {
@@ -278,9 +277,9 @@ cudaError_t launch_gather_by_id(const int32_t* rid, const R* src, R* dst, int32_
 }
 
 template cudaError_t launch_march<PrecF64>(const WakeDev<PrecF64>*, const int32_t*, int32_t, int32_t, int32_t,
-                                           int32_t, size_t, int32_t, cudaStream_t);
+                                           int32_t, size_t, int32_t, int32_t, cudaStream_t);
 template cudaError_t launch_march<PrecMixed>(const WakeDev<PrecMixed>*, const int32_t*, int32_t, int32_t, int32_t,
-                                             int32_t, size_t, int32_t, cudaStream_t);
+                                             int32_t, size_t, int32_t, int32_t, cudaStream_t);
 template cudaError_t launch_ring_init<double>(const double*, const double*, int32_t, int32_t, double, double*,
                                               double*, double*, double*, double*, double*, double*, int32_t*,
                                               float4*, cudaStream_t);

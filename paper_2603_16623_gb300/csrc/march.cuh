@@ -490,15 +490,32 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_ctl[CTL_N];
     __shared__ int s_stop;
+    __shared__ __align__(16) unsigned char s_part[2 * kPartBuf];
 
     const uint64_t t_launch = global_ns();
-    const WakeDev<P>& W = wakes[order ? order[blockIdx.x] : blockIdx.x];
+    // one block per wake, or (beam-grid wakes) a thread-block cluster whose
+    // blocks split the sorted rings, the grid nodes and the particles; block
+    // 0 sorts and sums the node charges
+    WakeCtas C;
+    {
+        unsigned r, c;
+        asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(c));
+        C.rank = (int)r;
+        C.size = (int)c;
+        C.part = s_part;
+    }
+    const int wi = blockIdx.x / C.size;
+    const WakeDev<P>& W = wakes[order ? order[wi] : wi];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
+    const int gt = C.rank * T + tid;  // the thread's place in the wake
+    const int GT = C.size * T;
     const int n = W.n;
-    const int K = (n + T - 1) / T;
-    const int p0 = min(n, tid * K);
+    const int K = (n + GT - 1) / GT;
+    const int p0 = min(n, gt * K);
     const int p1 = min(n, p0 + K);
+    const bool sorter = C.rank == 0;
 
     unsigned char* sscan = smem;
     R* keys = reinterpret_cast<R*>(smem + kScanBytes);
@@ -538,30 +555,43 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         bool ok = true;
         for (int p = p0; p < p1; ++p)
             if (p + 1 < n && rho[p + 1] < rho[p]) ok = false;
-        const bool in_order = __syncthreads_and(ok);
-        if (W.budget_ns > 0 && s_stop) break;
+        bool in_order = __syncthreads_and(ok);
+        bool stop = W.budget_ns > 0 && s_stop;
+        if (C.size > 1) {  // the cluster's blocks agree on both
+            const int* v = C.exchange((int)in_order | (stop ? 2 : 0));
+            in_order = true;
+            stop = false;
+            for (int r = 0; r < C.size; ++r) {
+                const int f = C.slot(v, r);
+                in_order = in_order && (f & 1) != 0;
+                stop = stop || (f & 2) != 0;
+            }
+        }
+        if (stop) break;
         if (!in_order) {
-            for (int i = tid; i < W.n_pad; i += T) {
-                keys[i] = i < n ? rho[i] : (R)INFINITY;
-                vals[i] = i;
-            }
-            __syncthreads();
-            block_bitonic_sort(keys, vals, W.n_pad);
             const int nb = buf ^ 1;
-            for (int p = tid; p < n; p += T) {
-                int src = vals[p];
-                W.rho[nb][p] = W.rho[buf][src];
-                W.ur[nb][p] = W.ur[buf][src];
-                W.frho[nb][p] = W.frho[buf][src];
-                W.fur[nb][p] = W.fur[buf][src];
-                W.rid[nb][p] = W.rid[buf][src];
-                keys[p] = W.rho_lo[src];  // the sort keys are no longer needed
+            if (sorter) {
+                for (int i = tid; i < W.n_pad; i += T) {
+                    keys[i] = i < n ? rho[i] : (R)INFINITY;
+                    vals[i] = i;
+                }
+                __syncthreads();
+                block_bitonic_sort(keys, vals, W.n_pad);
+                for (int p = tid; p < n; p += T) {
+                    int src = vals[p];
+                    W.rho[nb][p] = W.rho[buf][src];
+                    W.ur[nb][p] = W.ur[buf][src];
+                    W.frho[nb][p] = W.frho[buf][src];
+                    W.fur[nb][p] = W.fur[buf][src];
+                    W.rid[nb][p] = W.rid[buf][src];
+                    keys[p] = W.rho_lo[src];  // the sort keys are no longer needed
+                }
+                __syncthreads();
+                for (int p = tid; p < n; p += T) W.rho_lo[p] = keys[p];
             }
-            __syncthreads();
-            for (int p = tid; p < n; p += T) W.rho_lo[p] = keys[p];
             buf = nb;
             rho = W.rho[buf];
-            __syncthreads();
+            C.sync();
         }
         R* ur = W.ur[buf];
         R* frho = W.frho[buf];
@@ -588,17 +618,18 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         const int nr = W.grid_nr;
         if (nr > 0) {
             const int nn = W.n_species * (nr + 1);
-            for (int i = tid; i < nn; i += T) W.agB[i] = 0;
-            __syncthreads();
-            for (int q = tid; q < m; q += T) {  // each particle's charge reaches the nodes above it
+            if (sorter)
+                for (int i = tid; i < nn; i += T) W.agB[i] = 0;
+            C.sync();
+            for (int q = gt; q < m; q += GT) {  // each particle's charge reaches the nodes above it
                 const int64_t k = W.bidx[b0 + q];
                 const int b = ag_species(W, k);
                 const double dr = ag_extent(W, b) / nr;
                 const int j = ag_cell(W.rc[k], dr, nr) + 1;
                 atomicAdd(W.agB + (size_t)b * (nr + 1) + j, (R)W.qw[k]);
             }
-            __syncthreads();
-            if (tid < W.n_species) {
+            C.sync();
+            if (sorter && tid < W.n_species) {
                 R* B = W.agB + (size_t)tid * (nr + 1);
                 const double dr = ag_extent(W, tid) / nr;
                 double acc = 0.0;
@@ -608,7 +639,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                     B[j] = (R)(acc / (6.283185307179586476925286766559 * W.dxi * ((double)j * dr)));
                 }
             }
-            __syncthreads();
+            C.sync();
         }
 
         // ---------------- a3 + a4: beam field at rings, local sums
@@ -631,8 +662,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
             loc.y = acc_add(loc.y, acc_mul_a(ring_log(W.ctab, id, r, W.rho_lo[p]), wa));
         }
         Pair<A> tot;
-        Pair<A> ex = block_excl_scan<false>(loc, OpAddPair(), Pair<A>{zeroA, zeroA},
-                                            reinterpret_cast<Pair<A>*>(sscan), tot);
+        Pair<A> ex = wake_excl_scan<false>(C, loc, OpAddPair(), Pair<A>{zeroA, zeroA},
+                                           reinterpret_cast<Pair<A>*>(sscan), tot);
         const A Wtot = tot.x, Ltot = tot.y;
 
         // ---------------- a5: psi, d_rho psi, psibar, gamma, t
@@ -674,13 +705,13 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
             L = acc_add(L, acc_mul_a(lnr, wa));
             tl = acc_add_r(tl, t);
         }
-        if (tid == 0) {
+        if (C.rank == 0 && tid == 0) {
             W.regS[n] = Wtot;
             W.regL[n] = zeroA;
             W.regT[n] = (R)0;
         }
         A Ttot;
-        A Tex = block_excl_scan<false>(tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot);
+        A Tex = wake_excl_scan<false>(C, tl, OpAdd(), zeroA, reinterpret_cast<A*>(sscan), Ttot);
 
         // ---------------- a6 + a7: d_zeta psi, A, B, C
         {
@@ -710,9 +741,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         }
 
         // ---------------- a8: B_theta^(p) region coefficients a_k, b_k
-        WakeCtas one;
-        bp_region_solve(W, sR, n, p0, p1, sscan, one);
-        __syncthreads();
+        bp_region_solve(W, sR, n, p0, p1, sscan, C);
+        C.sync();
 
         // ---------------- B^(p) at the rings, guard, dumps
         bool bad = false;
@@ -735,12 +765,12 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 }
             }
         }
-        bad = __syncthreads_or(bad);
+        bad = wake_vote(C, bad, false);
 
         // ---------------- adaptive grids: the plasma fields at the nodes
         if (nr > 0 && mode == MODE_MARCH) {
             const int nn = W.n_species * (nr + 1);
-            for (int i = tid; i < nn; i += T) {
+            for (int i = gt; i < nn; i += GT) {
                 const int b = i / (nr + 1), j = i - b * (nr + 1);
                 const double dr = ag_extent(W, b) / nr;
                 const R x = (R)((double)j * dr);
@@ -765,8 +795,8 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
                 F[2] = dpz;
                 F[3] = bpv;
             }
-            __syncthreads();
-            for (int q = tid; q < m; q += T) {
+            C.sync();
+            for (int q = gt; q < m; q += GT) {
                 const int64_t kc = W.bidx[b0 + q];
                 const int b = ag_species(W, kc);
                 const double dr = ag_extent(W, b) / nr;
@@ -786,7 +816,7 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
         // ---------------- a9: fields on beam particles (or query radii)
         if (!(nr > 0 && mode == MODE_MARCH)) {
             const int64_t nq = mode == MODE_MARCH ? (int64_t)m : W.nq;
-            for (int64_t q = tid; q < nq; q += T) {
+            for (int64_t q = gt; q < nq; q += GT) {
                 R x;
                 if (mode == MODE_MARCH) x = staged ? beamR[q] : W.br[b0 + q];
                 else x = (R)W.rq[q];
@@ -866,10 +896,10 @@ march_kernel(const WakeDev<P>* __restrict__ wakes, const int32_t* __restrict__ o
             fur[p] = fu;
         }
         has_prev = 1;
-        __syncthreads();
+        C.sync();
     }
-    __syncthreads();
-    if (tid == 0) {
+    C.sync();
+    if (C.rank == 0 && tid == 0) {
         if (mode == MODE_MARCH) put_march_times(W.ctl, t_launch);
         W.ctl[CTL_NEXT] = mode == MODE_MARCH ? slice : s_ctl[CTL_NEXT];
         W.ctl[CTL_BUF] = buf;

@@ -12,7 +12,8 @@
 namespace gbwake {
 template <class P>
 cudaError_t launch_march(const WakeDev<P>* d_wakes, const int32_t* d_order, int32_t n_wakes, int32_t max_slices,
-                         int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, cudaStream_t st);
+                         int32_t mode, int32_t threads, size_t smem, int32_t mb_cap, int32_t cluster_ctas,
+                         cudaStream_t st);
 // the on-chip march (mixed precision, k_rings = 2, 4 or 8 rings per thread,
 // <= 512 threads)
 constexpr int kFastMaxThreads = 512;

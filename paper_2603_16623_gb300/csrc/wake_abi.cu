@@ -49,14 +49,16 @@ wake_status fail(wake_status st, const char* fmt, ...) {
 
 constexpr int32_t kMaxRings = 8192;           // FP64 path (one CTA per wake, sort in shared memory)
 constexpr int32_t kMaxIonCells = 4096;        // mobile ions: rings per species (2 x 4096 rings per wake)
-// the global-memory marches with mobile ions or RK4 on thread-block clusters:
-// the automatic cluster's positions per thread (of each species with ions),
-// and a cluster's barriers per slice (per stage with RK4), us
+// the global-memory marches with mobile ions, RK4 or beam grids on thread-
+// block clusters: the automatic cluster's positions per thread (of each
+// species with ions), and a cluster's barriers per slice (per stage with
+// RK4), us
 constexpr int32_t kIonRingsPerThread = 2;
 constexpr int32_t kRk4RingsPerThread = 2;
+constexpr int32_t kGridRingsPerThread = 4;
 constexpr double kGmClusterSliceUs = 20.0;
 constexpr int32_t kMaxRingsMixed = 65536;     // mixed path: a 16-CTA cluster of 512 threads x 8 rings
-constexpr int32_t kMaxRk4Rings = 16384;       // RK4: the stage-state sort of one block (8 B per ring)
+constexpr int32_t kMaxRk4Rings = 16384;       // RK4, beam grids: the sort of one block (8 B per ring)
 constexpr int32_t kMaxSliceParticles = 8192;
 constexpr int32_t kDefaultThreads = 256;
 
@@ -680,7 +682,7 @@ wake_status launch_one(wake_handle* h, const WakeDev<P>* d_desc, int32_t max_sli
                                     h->st));
         return WAKE_OK;
     }
-    WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->st));
+    WK_CUDA(launch_march<P>(d_desc, nullptr, 1, max_slices, mode, h->threads, smem, mb_cap, h->gm_cl, h->st));
     return WAKE_OK;
 }
 
@@ -872,7 +874,7 @@ wake_status batch_bucket(const std::vector<wake_handle*>& hs, const FastShape& s
                                 hs[0]->threads, smem, mb_cap, hs[0]->gm_cl, st);
     else
         e = launch_march<P>(static_cast<const WakeDev<P>*>(d_buf), d_order, n, max_slices, MODE_MARCH,
-                            hs[0]->threads, smem, mb_cap, st);
+                            hs[0]->threads, smem, mb_cap, hs[0]->gm_cl, st);
     cudaFreeAsync(d_buf, st);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, "batched march launch failed: %s", cudaGetErrorString(e));
     return WAKE_OK;
@@ -1400,6 +1402,12 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
         return fail(WAKE_EINVAL, "wake_init: RK4 runs electron-only wakes on the global-memory march (no mobile "
                                  "ions, rings_per_thread 0, cluster_ctas in [0, %d])", kMaxWakeCtas);
     if (cfg->grid_nr < 0 || cfg->grid_nr > 1024) return fail(WAKE_EINVAL, "wake_init: grid_nr must be in [0, 1024]");
+    if (cfg->grid_nr > 0 && (cfg->rings_per_thread || cfg->cluster_ctas < 0 || cfg->cluster_ctas > kMaxWakeCtas))
+        return fail(WAKE_EINVAL, "wake_init: beam-grid wakes take rings_per_thread 0 and cluster_ctas in [0, %d]",
+                    kMaxWakeCtas);
+    if (cfg->grid_nr > 0 && n_cells > kMaxRk4Rings)
+        return fail(WAKE_EINVAL, "wake_init: beam-grid wakes have at most %d rings (block 0 sorts them in its "
+                                 "shared memory)", kMaxRk4Rings);
     if (!(cfg->grid_rmax >= 0.0) || !std::isfinite(cfg->grid_rmax) || (cfg->grid_rmax > 0.0 && cfg->grid_nr == 0))
         return fail(WAKE_EINVAL, "wake_init: grid_rmax must be finite, >= 0, and set only with grid_nr > 0");
     if (cfg->grid_rmax > 0.0)
@@ -1449,10 +1457,12 @@ wake_status wake_init(const wake_config* cfg, const wake_plasma_desc* plasma, co
     h->n_steps = cfg->n_steps;
     h->n_pad = next_pow2(std::max(n, 2));  // sorts one species at a time
     h->threads = threads;
-    h->gm_cl = cfg->cluster_ctas && (ions || rk4) ? cfg->cluster_ctas
-             : ions                              ? gm_cluster_for(n, threads, kIonRingsPerThread)
-             : rk4                               ? gm_cluster_for(n, threads, kRk4RingsPerThread)
-                                                 : 1;
+    const bool grid = cfg->grid_nr > 0;
+    h->gm_cl = cfg->cluster_ctas && (ions || rk4 || grid) ? cfg->cluster_ctas
+             : ions                                      ? gm_cluster_for(n, threads, kIonRingsPerThread)
+             : rk4                                       ? gm_cluster_for(n, threads, kRk4RingsPerThread)
+             : grid                                      ? gm_cluster_for(n, threads, kGridRingsPerThread)
+                                                         : 1;
     h->flags = cfg->flags;
     h->dxi = cfg->dxi;
     h->density = plasma->density;

@@ -204,6 +204,9 @@ def test_long_wakes_get_the_latency_shape():
     ({"grid_nr": 2000, "precision": "fp64"}, "grid_nr must be"),
     ({"grid_nr": 16, "ion_charge": 1.0, "ion_mass": 100.0}, "beam grids run WAKE_AB2"),
     ({"grid_nr": 16, "precision": "fp64", "integrator": 1}, "beam grids run WAKE_AB2"),
+    ({"grid_nr": 16, "cl": 9}, "beam-grid wakes take rings_per_thread 0"),
+    ({"grid_nr": 16, "k": 4, "precision": "fp64"}, "beam-grid wakes take rings_per_thread 0"),
+    ({"grid_nr": 16, "n": 16385}, "beam-grid wakes have at most 16384 rings"),
     ({"grid_rmax": 2.0}, "grid_rmax must be"),
     ({"grid_nr": 16, "grid_rmax": -1.0}, "grid_rmax must be"),
 ])

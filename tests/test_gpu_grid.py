@@ -151,3 +151,92 @@ def test_a_particle_moved_beyond_a_fixed_grid_stops_the_wake():
     nxt, status, fail = g.progress()
     assert status == wm.WAKE_EINVAL and nxt == 0
     g.close()
+
+
+# ---------------------------------------------------------------------------
+# beam-grid wakes on a thread-block cluster: the blocks split the sorted
+# rings, the grid nodes and the slice's particles; block 0 sorts the rings
+# and sums the node charges (deposited by every block with atomics)
+# ---------------------------------------------------------------------------
+def gpu_run_cl(wk, precision, threads, cluster):
+    from paper_2603_16623_gb300 import wake as wm
+    g = wm.Wake.from_workload(wk, precision=precision, block_threads=threads, cluster_ctas=cluster,
+                              flags=wm.WAKE_DUMP_RING_FIELDS)
+    cfg = g.launch_config()
+    st, _, _, _ = g.run()
+    out = {"status": st, "beam": g.beam_fields(), "rings": g.ring_dumps(), "final": g.ring_state(), "cfg": cfg}
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("threads,cluster", [(64, 2), (96, 3), (64, 8)])
+def test_fp64_grid_wake_on_a_cluster_matches_oracle(threads, cluster):
+    """300 rings over 2, 3 and 8 blocks (with 8 blocks of 64 threads, the
+    last three hold no ring), two beams with grids of different extents."""
+    wk = grid_wake(24, steps=420, seed=93, two_beams=True)
+    ref = oracle.run_wake(wk, ring_dumps=("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"))
+    assert ref.status == 0
+    got = gpu_run_cl(wk, "fp64", threads, cluster)
+    assert got["cfg"][0] == threads and got["cfg"][2] == cluster
+    assert got["status"] == 0
+    for k in ("r", "ur", "psi", "dpsidr", "dpsidz", "bp", "bb"):
+        assert nerr(got["rings"][k], ref.rings[k]) < FP64_TOL, k
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(got["beam"][k], ref.beam[k]) < FP64_TOL, k
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", 1e-5)])
+def test_regular_and_mixed_grids_on_a_cluster(precision, tol):
+    """The regular grid (fixed extent 2.5) on 4 blocks against the oracle."""
+    wk = grid_wake(48, n=300, steps=400, seed=98, two_beams=True)
+    wk = W.Wake(wk.name, wk.edges, wk.beams, wk.dxi, wk.n_steps, grid_nr=48, grid_rmax=2.5)
+    ref = oracle.run_wake(wk, ring_dumps=("r",))
+    got = gpu_run_cl(wk, precision, 64, 4)
+    assert got["status"] == ref.status == 0
+    assert nerr(got["rings"]["r"], ref.rings["r"]) < tol
+    for k in ("ez", "wr", "bt"):
+        assert nerr(got["beam"][k], ref.beam[k]) < tol, k
+
+
+def test_grid_cluster_shapes_batches_queries_and_rejections():
+    """Automatic blocks per wake (a cluster once a block of 256 threads would
+    hold more than 4 rings per thread); a batch mixing one-block and cluster
+    grid wakes matches the wakes alone (1e-12: node charges summed with
+    atomics); fields at query radii between slices on a cluster match one
+    block; bad shapes refused."""
+    from paper_2603_16623_gb300 import wake as wm
+    for rings, blocks in ((1024, 1), (1025, 2), (3000, 3), (8192, 8)):
+        wk = W.Wake("shape", W.edges_uniform(rings, 5.0), [], 0.01, 10, grid_nr=16)
+        g = wm.Wake.from_workload(wk, precision="fp64")
+        assert g.launch_config() == (256, -(-rings // (256 * blocks)), blocks), rings
+        g.close()
+    wakes = [grid_wake(16, n=1500, steps=150, seed=101), grid_wake(40, n=260, steps=200, seed=96, two_beams=True)]
+    alone = []
+    for wk in wakes:
+        g = wm.Wake.from_workload(wk, precision="fp64")
+        g.run()
+        alone.append((g.launch_config(), g.ring_state(), g.beam_fields(("ez", "wr"))))
+        g.close()
+    assert [c[2] for c, _, _ in alone] == [2, 1]
+    gs = [wm.Wake.from_workload(wk, precision="fp64") for wk in wakes]
+    wm.wake_batch_run(gs)
+    for g, (_, st, bf) in zip(gs, alone):
+        r, _ = g.ring_state()
+        assert nerr(r, st[0]) < 1e-12
+        f = g.beam_fields(("ez", "wr"))
+        assert nerr(f["ez"], bf["ez"]) < 1e-12 and nerr(f["wr"], bf["wr"]) < 1e-12
+        g.close()
+    wk = grid_wake(32, n=400, steps=300, seed=102)
+    a = wm.Wake.from_workload(wk, precision="fp64", block_threads=64, cluster_ctas=4)
+    b = wm.Wake.from_workload(wk, precision="fp64", block_threads=64, cluster_ctas=1)
+    for g in (a, b):
+        wm.wake_batch_step([g], 150)
+    rq = np.linspace(0.0, 6.0, 555)
+    fa, fb = a.fields_at_static(rq), b.fields_at_static(rq)
+    for k in ("ez", "wr", "bt", "psi"):
+        assert nerr(fa[k], fb[k]) < FP64_TOL, k
+    a.close()
+    b.close()
+    for kw in ({"cluster_ctas": 9}, {"cluster_ctas": -1}, {"rings_per_thread": 4}):
+        with pytest.raises(wm.WakeError):
+            wm.Wake.from_workload(grid_wake(8, n=50, steps=20), precision="mixed", **kw)
