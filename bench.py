@@ -542,17 +542,22 @@ def grid_bench(args, wakes, stream):
     """The paper's grid coupling (adaptive beam grids of 32 radial cells per
     beam) against the gridless one on the same batched wakes of <= 8192
     rings over a bounded window (their first args.grid_slices slices):
-    FP64 (both on the one-CTA march) and mixed (grids on the one-CTA march,
-    gridless on the on-chip one); batched reset + step, CUDA-event timed."""
+    FP64 on the global-memory march, both on one block per wake (the grid's
+    own cost), and the grids on their automatic clusters; mixed, the grids
+    on their automatic clusters against the gridless on-chip march; batched
+    reset + step, CUDA-event timed."""
     import torch
     from paper_2603_16623_gb300 import wake as wm
     sel = [wk for wk in wakes if wk.n_rings <= 8192][: args.grid_wakes]
     out = {"wakes": len(sel), "slices": args.grid_slices, "grid_nr": 32,
-           "note": "fp64: both on the one-CTA march; mixed: grids on the one-CTA march, gridless on the on-chip one"}
-    for name, nr, prec in (("gridless", 0, "fp64"), ("grid", 32, "fp64"), ("mixed_gridless", 0, "mixed"),
-                           ("mixed_grid", 32, "mixed")):
-        gs = [wm.Wake.from_workload(dataclasses.replace(wk, grid_nr=nr), precision=prec, stream=stream.cuda_stream)
-              for wk in sel]
+           "note": "fp64: gridless and grid on one block per wake, grid_clusters on the automatic clusters; "
+                   "mixed: grids on the automatic clusters, gridless on the on-chip march"}
+    # (name, grid cells, precision, blocks per wake: 1, or 0 = automatic)
+    for name, nr, prec, cl in (("gridless", 0, "fp64", 0), ("grid", 32, "fp64", 1), ("grid_clusters", 32, "fp64", 0),
+                               ("mixed_gridless", 0, "mixed", 0), ("mixed_grid", 32, "mixed", 0)):
+        shape = {"cluster_ctas": cl} if nr else {}
+        gs = [wm.Wake.from_workload(dataclasses.replace(wk, grid_nr=nr), precision=prec, stream=stream.cuda_stream,
+                                    **shape) for wk in sel]
         wm.wake_batch_reset(gs)
         wm.wake_batch_step(gs, args.grid_slices)  # warm-up
         torch.cuda.synchronize()
@@ -564,7 +569,9 @@ def grid_bench(args, wakes, stream):
         torch.cuda.synchronize()
         rs = sum(wk.n_rings * g.progress()[0] for g, wk in zip(gs, sel))
         ms = ev[0].elapsed_time(ev[1])
-        out[name] = {"ring_slices": rs, "ms_per_step": ms, "value": rs / (ms / 1e3), "unit": UNIT}
+        blocks = [g.launch_config()[2] for g in gs]
+        out[name] = {"ring_slices": rs, "ms_per_step": ms, "value": rs / (ms / 1e3), "unit": UNIT,
+                     "blocks_per_wake": [min(blocks), max(blocks)]}
         for g in gs:
             g.close()
     out["grid_over_gridless_time"] = out["grid"]["ms_per_step"] / out["gridless"]["ms_per_step"]

@@ -158,9 +158,9 @@ typedef struct {
                                  at most 512, and no CTA may be left empty.
                                  Both must be 0 for WAKE_FP64.  Automatic
                                  (both 0): see wake_launch_shape.  With
-                                 mobile ions or RK4 (FP64 or MIXED)
-                                 cluster_ctas is 0..8 and rings_per_thread 0
-                                 (see above).                                 */
+                                 mobile ions, RK4 or beam grids (FP64 or
+                                 MIXED) cluster_ctas is 0..8 and
+                                 rings_per_thread 0 (see above and grid_nr). */
     int32_t integrator;       /* WAKE_AB2 (0) or WAKE_RK4                        */
     int32_t grid_nr;          /* 0: gridless beam coupling (fields at each beam
                                  particle); 1..1024: adaptive beam grids
@@ -170,7 +170,13 @@ typedef struct {
                                  the rings from the grids (B_N r_N / rho
                                  beyond), beam-particle fields interpolated
                                  from the nodes.  WAKE_AB2, no mobile ions,
-                                 at most 8 beam species; both precisions. */
+                                 at most 8 beam species, at most 16384
+                                 rings; both precisions.  One block per wake
+                                 or a thread-block cluster (cluster_ctas
+                                 0..8; 0 = automatic: the fewest blocks, at
+                                 most 8, that hold at most 4 rings per
+                                 thread); block 0 sorts the rings and sums
+                                 the node charges. */
     double grid_rmax;         /* with grid_nr > 0: 0 = adaptive extents; > 0 =
                                  every grid spans [0, grid_rmax] (the regular
                                  intermediate grid).  Every beam particle must
