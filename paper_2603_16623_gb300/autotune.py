@@ -13,8 +13,8 @@ events and keeps the fastest in ring-slices per second.  The automatic
 shape stays unless a candidate beats it by `min_gain`, so timing noise does
 not churn the table.  The global-memory marches (FP64, mobile ions, RK4,
 beam grids) are tuned the same way over their block size (block_threads),
-and those with mobile ions or RK4 also over their blocks per wake (a
-thread-block cluster of 2, 4 or 8 blocks of 512 threads).
+and those with mobile ions, RK4 or beam grids also over their blocks per
+wake (a thread-block cluster of 2, 4 or 8 blocks of the default size).
 
 The candidates come from the library itself (wake_launch_shape: the shape
 wake_init would give, computed on the host), so the tuner never proposes a
@@ -46,7 +46,7 @@ BLOCK_THREADS = (64, 128, 256, 512)
 # automatic candidate, so not again as an explicit one)
 DEFAULT_BLOCK_THREADS = {"fp64": 256, "grid": 256, "ions": 512, "rk4": 512}
 # the global-memory marches that also run as thread-block clusters
-GM_CLUSTER_KINDS = ("ions", "rk4")
+GM_CLUSTER_KINDS = ("ions", "rk4", "grid")
 DEFAULT_SIZES = (512, 1024, 2048, 3072, 4096, 6144, 8192, 12288, 16384, 32768, 65536)
 
 
@@ -55,7 +55,7 @@ class Candidate:
     """Arguments of wake_init for one launch shape, with what they resolve
     to for the size they were made for."""
     rings_per_thread: int = 0   # on-chip march: 0 (automatic), 2, 4 or 8
-    cluster_ctas: int = 0       # on-chip march: 0 (automatic) or 1-16; ions, RK4: 0 or 1-8
+    cluster_ctas: int = 0       # on-chip march: 0 (automatic) or 1-16; ions, RK4, grids: 0 or 1-8
     block_threads: int = 0      # global-memory marches: 0 (the library's default) or 64-512
     threads: int = 0            # resolved threads per CTA (on-chip march)
     ctas: int = 1               # resolved CTAs per wake
@@ -88,7 +88,8 @@ def candidates(n_rings: int, kind: str = "mixed", max_candidates: int = 8,
     one first, then (on-chip march) every valid (rings per thread, CTAs per
     wake) with at least min_threads threads per CTA, thinned evenly to
     max_candidates; or (global-memory marches) the block sizes 64-512 and,
-    with mobile ions or RK4, clusters of 2, 4 and 8 blocks of 512 threads."""
+    with mobile ions, RK4 or beam grids, clusters of 2, 4 and 8 blocks of
+    the default size."""
     if not 1 <= n_rings <= max_rings(kind):
         raise ValueError(f"{n_rings} rings: outside [1, {max_rings(kind)}] for the {kind} march")
     if kind != "mixed":

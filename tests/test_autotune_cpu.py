@@ -50,7 +50,7 @@ def test_global_memory_marches_tune_the_block_size_and_clusters():
         sized = [c for c in cands[1:] if c.block_threads]
         assert sorted(c.block_threads for c in sized) == sorted(t for t in (64, 128, 256, 512) if t != default)
         clustered = [c for c in cands[1:] if not c.block_threads]
-        if kind in ("ions", "rk4"):
+        if kind in ("ions", "rk4", "grid"):
             # a block size alone means one block per wake; then clusters of 512 threads
             assert all(c.cluster_ctas == 1 and c.wake_kwargs()["cluster_ctas"] == 1 for c in sized)
             assert [(c.cluster_ctas, c.ctas) for c in clustered] == [(2, 2), (4, 4), (8, 8)]
