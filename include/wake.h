@@ -490,6 +490,23 @@ wake_status wake_launch_shape_latency(int32_t precision, int32_t n_rings, int32_
 wake_status wake_set_latency_shape_ms(double ms);
 double wake_get_latency_shape_ms(void);
 
+/* the global-memory marches whose wakes also run on thread-block clusters */
+enum { WAKE_GM_IONS = 1, WAKE_GM_RK4 = 2, WAKE_GM_GRID = 3 };
+
+/* The launch shape wake_init gives a wake of the two-species march
+   (WAKE_GM_IONS: n_cells per species), the RK4 march (WAKE_GM_RK4) or a
+   beam-grid wake (WAKE_GM_GRID: n_cells rings), computed on the host from
+   the config's block_threads (0: the default, 512 for ions and RK4, 256 for
+   grids) and cluster_ctas (0: automatic, the fewest blocks, at most 8, that
+   hold at most 2 rings of each species (ions), 2 rings (RK4) or 4 rings
+   (grids) per thread).  Outputs (each may be NULL): threads per block,
+   rings per thread (both species counted with ions) and blocks per wake,
+   as wake_get_launch_config reports them.  Errors: EINVAL for an unknown
+   march, n_cells outside [1, 4096] (ions) or [1, 16384], block_threads not
+   0 or a multiple of 32 in [64, 512], cluster_ctas outside [0, 8]. */
+wake_status wake_gm_launch_shape(int32_t march, int32_t n_cells, int32_t block_threads, int32_t cluster_ctas,
+                                 int32_t *threads, int32_t *rings_per_thread, int32_t *blocks_per_wake);
+
 
 #ifdef __cplusplus
 }

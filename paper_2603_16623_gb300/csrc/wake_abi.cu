@@ -1342,6 +1342,30 @@ wake_status wake_launch_shape(int32_t precision, int32_t n_rings, int32_t n_step
     return WAKE_OK;
 }
 
+wake_status wake_gm_launch_shape(int32_t march, int32_t n_cells, int32_t block_threads, int32_t cluster_ctas,
+                                int32_t* threads, int32_t* rings_per_thread_out, int32_t* blocks_per_wake) {
+    if (march != WAKE_GM_IONS && march != WAKE_GM_RK4 && march != WAKE_GM_GRID)
+        return fail(WAKE_EINVAL, "wake_gm_launch_shape: unknown march %d", march);
+    const int32_t max_cells = march == WAKE_GM_IONS ? kMaxIonCells : kMaxRk4Rings;
+    if (n_cells < 1 || n_cells > max_cells)
+        return fail(WAKE_EINVAL, "wake_gm_launch_shape: n_cells must be in [1, %d]", max_cells);
+    const bool default_threads = block_threads == 0;
+    const int32_t t = default_threads ? (march == WAKE_GM_GRID ? kDefaultThreads : 512) : block_threads;
+    if (t < 64 || t > 512 || t % 32)
+        return fail(WAKE_EINVAL, "wake_gm_launch_shape: block_threads must be 0 or a multiple of 32 in [64, 512]");
+    if (cluster_ctas < 0 || cluster_ctas > kMaxWakeCtas)
+        return fail(WAKE_EINVAL, "wake_gm_launch_shape: cluster_ctas must be in [0, %d]", kMaxWakeCtas);
+    const int32_t per_thread = march == WAKE_GM_IONS ? kIonRingsPerThread
+                             : march == WAKE_GM_RK4  ? kRk4RingsPerThread
+                                                     : kGridRingsPerThread;
+    const int32_t cl = cluster_ctas ? cluster_ctas : gm_cluster_for(n_cells, t, per_thread);
+    const int32_t rings = march == WAKE_GM_IONS ? 2 * n_cells : n_cells;
+    if (threads) *threads = t;
+    if (rings_per_thread_out) *rings_per_thread_out = (rings + t * cl - 1) / (t * cl);
+    if (blocks_per_wake) *blocks_per_wake = cl;
+    return WAKE_OK;
+}
+
 wake_status wake_launch_shape_latency(int32_t precision, int32_t n_rings, int32_t* threads,
                                       int32_t* rings_per_thread_out, int32_t* blocks_per_wake) {
     if (precision != WAKE_FP64 && precision != WAKE_MIXED)

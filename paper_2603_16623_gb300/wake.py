@@ -88,6 +88,8 @@ _SIGS = {
                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_launch_shape_latency": ([C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)], C.c_int),
+    "wake_gm_launch_shape": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                              C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "wake_set_latency_shape_ms": ([C.c_double], C.c_int),
     "wake_get_latency_shape_ms": ([], C.c_double),
     "wake_max_slice_particles": ([C.c_int32], C.c_int64),
@@ -501,6 +503,19 @@ def wake_launch_shape_latency(n_rings: int, precision: str = "mixed"):
     latency_shape_ms()."""
     t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
     _check(load().wake_launch_shape_latency(PRECISION[precision], int(n_rings), C.byref(t), C.byref(k), C.byref(c)))
+    return t.value, k.value, c.value
+
+
+GM_MARCHES = {"ions": 1, "rk4": 2, "grid": 3}
+
+
+def wake_gm_launch_shape(n_cells: int, march: str = "ions", block_threads: int = 0, cluster_ctas: int = 0):
+    """(threads per block, rings per thread, blocks per wake) that wake_init
+    gives a wake of the two-species march ("ions": n_cells per species), the
+    RK4 march or a beam-grid wake, computed on the host."""
+    t, k, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().wake_gm_launch_shape(GM_MARCHES[march], int(n_cells), int(block_threads), int(cluster_ctas),
+                                       C.byref(t), C.byref(k), C.byref(c)))
     return t.value, k.value, c.value
 
 

@@ -248,3 +248,29 @@ def test_a_beam_beyond_a_fixed_grid_is_refused_on_the_host():
     st = lib.wake_init(ctypes.byref(cfg), ctypes.byref(plasma), ctypes.byref(beam), 1, None, ctypes.byref(h))
     assert st == wm.WAKE_EINVAL and not h.value
     assert "beyond grid_rmax" in lib.wake_last_error().decode()
+
+
+def test_global_memory_march_shapes_on_the_host():
+    """wake_gm_launch_shape: the blocks per wake wake_init gives the
+    two-species, RK4 and beam-grid marches -- the fewest blocks (at most 8)
+    that hold at most 2 rings of each species, 2 rings and 4 rings per
+    thread -- and the rings per thread wake_get_launch_config reports."""
+    from paper_2603_16623_gb300 import wake as wm
+    cases = {("ions", 1024): (512, 4, 1), ("ions", 1025): (512, 3, 2), ("ions", 2048): (512, 4, 2),
+             ("ions", 3993): (512, 4, 4), ("ions", 4096): (512, 4, 4), ("rk4", 1024): (512, 2, 1),
+             ("rk4", 1025): (512, 2, 2), ("rk4", 7905): (512, 2, 8), ("rk4", 16384): (512, 4, 8),
+             ("grid", 1024): (256, 4, 1), ("grid", 1025): (256, 3, 2), ("grid", 8192): (256, 4, 8)}
+    for (march, n), shape in cases.items():
+        assert wm.wake_gm_launch_shape(n, march) == shape, (march, n)
+    # explicit shapes: a block size alone keeps the automatic blocks for it
+    assert wm.wake_gm_launch_shape(4096, "ions", 512, 1) == (512, 16, 1)
+    assert wm.wake_gm_launch_shape(300, "ions", 64, 8) == (64, 2, 8)
+    assert wm.wake_gm_launch_shape(3000, "rk4", 256, 0) == (256, 2, 6)
+    assert wm.wake_gm_launch_shape(300, "grid", 96, 3) == (96, 2, 3)
+    for args in ((0, "ions"), (4097, "ions"), (16385, "rk4"), (100, "grid", 48), (100, "grid", 0, 9),
+                 (100, "rk4", 0, -1), (100, "ions", 1024)):
+        with pytest.raises(wm.WakeError):
+            wm.wake_gm_launch_shape(*args)
+    lib = wm.load()
+    t = ctypes.c_int32()
+    assert lib.wake_gm_launch_shape(7, 100, 0, 0, ctypes.byref(t), None, None) == wm.WAKE_EINVAL

@@ -209,6 +209,7 @@ def test_grid_cluster_shapes_batches_queries_and_rejections():
         wk = W.Wake("shape", W.edges_uniform(rings, 5.0), [], 0.01, 10, grid_nr=16)
         g = wm.Wake.from_workload(wk, precision="fp64")
         assert g.launch_config() == (256, -(-rings // (256 * blocks)), blocks), rings
+        assert g.launch_config() == wm.wake_gm_launch_shape(rings, "grid")  # the host-side query agrees
         g.close()
     wakes = [grid_wake(16, n=1500, steps=150, seed=101), grid_wake(40, n=260, steps=200, seed=96, two_beams=True)]
     alone = []

@@ -304,6 +304,7 @@ def test_ion_cluster_shapes_and_rejections():
         wk = W.Wake("shape", W.edges_uniform(cells, 5.0), [], 0.01, 10, ions=(1.0, 100.0))
         g = wm.Wake.from_workload(wk, precision="mixed")
         assert g.launch_config() == (512, -(-2 * cells // (512 * blocks)), blocks), cells
+        assert g.launch_config() == wm.wake_gm_launch_shape(cells, "ions")  # the host-side query agrees
         g.close()
     wk = ion_wake(n=50, steps=20)
     for bad in (-1, 9, 16):

@@ -252,6 +252,7 @@ def test_rk4_cluster_shapes_batches_and_rejections():
         wk = W.Wake("shape", W.edges_uniform(rings, 5.0), [], 0.01, 10, integrator="rk4")
         g = wm.Wake.from_workload(wk, precision="mixed")
         assert g.launch_config() == (512, -(-rings // (512 * blocks)), blocks), rings
+        assert g.launch_config() == wm.wake_gm_launch_shape(rings, "rk4")  # the host-side query agrees
         g.close()
     wakes = [rk4_wake(n=1500, steps=60, seed=88), rk4_wake(n=300, steps=80, seed=89),
              rk4_wake(n=600, steps=70, seed=90)]
