@@ -244,6 +244,13 @@ def run_ours(args):
                     ((t[1] - t[0], t[0] - t_first) for t in wt), reverse=True)[9][1] / 1e6 if len(wt) >= 10 else None,
                 "note": "device times (globaltimer) of the last timed step; the longest wake is the critical path, "
                         "sm_time_bound the throughput bound (SM shares by registers x in-batch march times / SMs)"}
+    try:  # the critical-path wake's shape and slices (for the latency roofline)
+        i_long = max(range(len(wt)), key=lambda i: wt[i][1] - wt[i][0])
+        t_c, k_c, c_c = gs[i_long].launch_config()
+        schedule["critical_wake"] = {"rings": wakes[i_long].n_rings, "slices": nexts[i_long], "threads": t_c,
+                                     "rings_per_thread": k_c, "ctas": c_c}
+    except Exception as e:  # reported, never fatal to the bench
+        schedule["critical_wake"] = {"unavailable": repr(e)}
     pev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     phase_step(pev)
     torch.cuda.synchronize()
@@ -389,7 +396,8 @@ def run_ours(args):
                 "peak_basis": "measured: FP32 FMA throughput microbenchmark (wake_measure_peaks), "
                               f"{onchip['sm_clock_mhz']:.0f} MHz",
                 "nominal_fp32_tflops": SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12,
-                "onchip_peaks": onchip, "schedule": schedule}
+                "onchip_peaks": onchip, "schedule": schedule,
+                "latency_roofline": latency_roofline(schedule, onchip)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -536,6 +544,41 @@ def rk4_bench(args, wakes, stream):
     res["ab2_same_wakes"] = {k: ref[k] for k in ("ring_slices", "ms_per_step", "value", "unit")}
     res["ab2_over_rk4_per_ring_slice"] = ref["value"] / res["value"]
     return res
+
+
+# warp instructions per ring-slice of the on-chip marches, from the ncu
+# captures summarised in profiles/ (one CTA: 2048 rings, 512 threads x 4;
+# cluster: 6000 rings, 6 CTAs of 256 x 4), and their barriers per slice
+WARP_INSTR_PER_RING_SLICE = {"one_cta": 39.7, "cluster": 48.2}
+BLOCK_BARRIERS_PER_SLICE = {"one_cta": 11, "cluster": 8}
+CLUSTER_BARRIERS_PER_SLICE = 6
+
+
+def latency_roofline(schedule, onchip):
+    """A lower bound of the critical-path wake's march time, whose slices run
+    in sequence: per slice its CTA's instructions at the issue rate its
+    warps can sustain on dependent float-float chains (a scheduler with w
+    warps issues at most min(1, w / FMA latency) per cycle, 4 schedulers per
+    SM, the CTA alone on its SM) plus the latency of its barriers, from the
+    measured on-chip peaks.  frac = bound / the wake's measured time."""
+    try:
+        cw = schedule["critical_wake"]
+        kind = "cluster" if cw["ctas"] > 1 else "one_cta"
+        warps_per_scheduler = cw["threads"] / 32 / 4
+        ipc = 4 * min(1.0, warps_per_scheduler / onchip["fma_latency_cycles"])
+        instr = WARP_INSTR_PER_RING_SLICE[kind] * cw["threads"] * cw["rings_per_thread"]
+        issue_us = instr / ipc / onchip["sm_clock_mhz"]
+        barrier_us = BLOCK_BARRIERS_PER_SLICE[kind] * onchip["syncthreads_ns"] / 1e3
+        if kind == "cluster":
+            barrier_us += CLUSTER_BARRIERS_PER_SLICE * onchip["cluster_barrier_ns"] / 1e3
+        bound_ms = cw["slices"] * (issue_us + barrier_us) / 1e3
+        return {"bound_ms": bound_ms, "measured_ms": schedule["longest_wake_ms"],
+                "frac": bound_ms / schedule["longest_wake_ms"], "kind": kind,
+                "per_slice_us": {"issue": issue_us, "barriers": barrier_us},
+                "basis": "warp instructions per ring-slice from the ncu captures in profiles/; FMA latency, "
+                         "barrier latencies and SM clock measured by wake_measure_peaks"}
+    except Exception as e:  # reported, never fatal to the bench
+        return {"unavailable": repr(e)}
 
 
 def grid_bench(args, wakes, stream):
