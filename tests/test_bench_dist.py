@@ -147,3 +147,31 @@ def test_batched_params_are_the_members_parameters():
         p, wk = W.batched_params(k), W.batched_wake(k)
         assert (p.n_rings, p.n_steps, p.n_mp) == (wk.n_rings, wk.n_steps, wk.beams[0].n)
         assert wk.edges[-1] == p.r_max
+
+
+def test_latency_roofline_of_the_critical_wake():
+    """The bench's latency bound: per slice, the critical wake's block's
+    warp instructions at min(1, warps per scheduler / FMA latency) per
+    scheduler-cycle plus its barriers' latency, times its slices; a missing
+    input is reported, not raised."""
+    import bench
+    onchip = {"fma_latency_cycles": 4.0, "syncthreads_ns": 20.0, "cluster_barrier_ns": 200.0, "sm_clock_mhz": 2000.0}
+    # one block of 512 threads x 4 rings: 4 warps per scheduler, full rate
+    one = {"critical_wake": {"rings": 2048, "slices": 100, "threads": 512, "rings_per_thread": 4, "ctas": 1},
+           "longest_wake_ms": 4.0}
+    r = bench.latency_roofline(one, onchip)
+    issue = bench.WARP_INSTR_PER_RING_SLICE["one_cta"] * 2048 / 4.0 / 2000.0
+    barriers = bench.BLOCK_BARRIERS_PER_SLICE["one_cta"] * 20.0 / 1e3
+    assert r["kind"] == "one_cta"
+    assert abs(r["per_slice_us"]["issue"] - issue) < 1e-12
+    assert abs(r["bound_ms"] - 100 * (issue + barriers) / 1e3) < 1e-12
+    assert abs(r["frac"] - r["bound_ms"] / 4.0) < 1e-12
+    # a cluster of 256-thread blocks: 2 warps per scheduler, half rate, and the cluster barriers
+    cl = {"critical_wake": {"rings": 6000, "slices": 10, "threads": 256, "rings_per_thread": 4, "ctas": 6},
+          "longest_wake_ms": 1.0}
+    r = bench.latency_roofline(cl, onchip)
+    issue = bench.WARP_INSTR_PER_RING_SLICE["cluster"] * 1024 / (4 * 2 / 4.0) / 2000.0
+    barriers = (bench.BLOCK_BARRIERS_PER_SLICE["cluster"] * 20.0 + bench.CLUSTER_BARRIERS_PER_SLICE * 200.0) / 1e3
+    assert r["kind"] == "cluster"
+    assert abs(r["bound_ms"] - 10 * (issue + barriers) / 1e3) < 1e-12
+    assert "unavailable" in bench.latency_roofline({"critical_wake": {"unavailable": "x"}}, onchip)
